@@ -1,0 +1,228 @@
+/*
+ * lisa_psd.h -- C ABI of the GB300 (sm_103a) library for the batched, spline-perturbed
+ * Whittle/Wishart log-likelihood of averaged A/E/T periodograms (arXiv:2507.06300).
+ *
+ * The library evaluates, for every walker x temperature state of a tempered ensemble at once,
+ *
+ *     log L(theta) = - sum_i nu_i sum_c [ P_c(f_i) / S_c(f_i) + ln S_c(f_i) ]          (1)
+ *
+ *     S_c(f) = S_n,cc(f | A_OMS, A_TM) 10^{P_n,c(log10 f)}
+ *            + S_h,cc(f | A, n)        10^{P_h(log10 f)}                              (2)
+ *
+ * (1) is the per-bin complex-Wishart log-density -tr(C^-1 Y) - nu log|C| with Y = nu P and a
+ * diagonal covariance C = diag(S_AA, S_EE, S_TT), summed over bins (Sec. III.D); the printed
+ * factor 1/2 in C is not applied (the periodogram is normalised to the one-sided PSD,
+ * Sec. III.A), and nu = 1 is the Whittle likelihood.  (2) is Eq. (splines) of Sec. III.A with
+ * the noise template of Eq. (noise_tdi) and the SGWB template of Eq. (pl) / Eq. (Sh).  The
+ * perturbations P are variable-knot Akima splines (Appendix A; natural cubic splines as the
+ * alternative kind) in x = log10 f, with edge knots fixed at the dataset's x_lo / x_hi and
+ * in-between knots (x_k, w_k) in any order; fewer than two in-between knots give the linear
+ * interpolant (Sec. III.A).
+ *
+ * Conventions for every entry point:
+ *  - Pointers named *_dev are DEVICE pointers (cudaMalloc'd or torch-allocated memory on the
+ *    current device); everything else is host memory.  The caller owns every array it passes;
+ *    the library owns only what lisa_data_create allocates, freed by lisa_data_destroy.
+ *  - Calls that take a cudaStream_t are asynchronous and stream-ordered: they enqueue kernels
+ *    and return; results are valid once the stream reaches them.  Only lisa_data_create and
+ *    lisa_data_set_tiling synchronise (they upload tables and work lists).
+ *  - Argument or shape errors return a non-zero lisa_status and launch nothing.  A CUDA
+ *    launch error returns LISA_ERR_CUDA.  No C++ exception crosses the ABI.
+ *  - A state whose knots or parameters are invalid is not a call failure: lisa_spline_setup
+ *    writes the knot bits (LISA_STATE_BAD_COUNT .. LISA_STATE_BAD_AMPLITUDE) to its status word;
+ *    such a state, and any state whose parameters are non-finite or whose PSD or log-likelihood
+ *    leaves the finite range of the chosen precision, gets log L = -inf and a zero gradient.
+ *  - Every layout is row-major (C order) with the shapes given.
+ */
+#ifndef LISA_PSD_H
+#define LISA_PSD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* lisa_stream_t; /* same type as cudaStream_t; NULL = legacy stream */
+
+typedef enum lisa_status {
+    LISA_SUCCESS = 0,
+    LISA_ERR_NULL = 1,        /* a required pointer is NULL */
+    LISA_ERR_VALUE = 2,       /* a scalar argument is out of range */
+    LISA_ERR_SHAPE = 3,       /* sizes disagree with the dataset object */
+    LISA_ERR_DATA = 4,        /* input table has non-finite / non-positive / unordered entries */
+    LISA_ERR_CUDA = 5,        /* a CUDA runtime call or launch failed */
+    LISA_ERR_ALLOC = 6,       /* device or host allocation failed */
+    LISA_ERR_WORKSPACE = 7,   /* workspace or spline buffer too small or misaligned */
+    LISA_ERR_TIMEOUT = 8      /* a bounded device-side wait gave up (kernel returned early) */
+} lisa_status;
+
+typedef enum lisa_precision {
+    LISA_FP32 = 0, /* FP32 tables and per-bin arithmetic, FP64 bin sums (the fast path) */
+    LISA_FP64 = 1  /* FP64 throughout (the plain reference path on the GPU) */
+} lisa_precision;
+
+typedef enum lisa_spline_kind {
+    LISA_SPLINE_AKIMA = 0,   /* Appendix A, SciPy-style end slopes */
+    LISA_SPLINE_NATURAL = 1  /* natural cubic (second derivative zero at both edges) */
+} lisa_spline_kind;
+
+typedef enum lisa_sgwb_model {
+    LISA_SGWB_NONE = 0,       /* noise-only model: no SGWB term and no SGWB spline */
+    LISA_SGWB_POWER_LAW = 1,  /* h^2 Omega = A (f / f_ref)^n1           (Eq. pl) */
+    LISA_SGWB_BROKEN = 2      /* n1 below f_ref, n2 at and above f_ref (same A at f_ref) */
+} lisa_sgwb_model;
+
+typedef enum lisa_tdi_form {
+    LISA_TDI_PRINTED = 0,  /* prefactor sin^2(u) sin^4(u) as printed in Eq. (noise_tdi) */
+    LISA_TDI_SIN2_2U = 1   /* prefactor sin^2(u) sin^2(2u) */
+} lisa_tdi_form;
+
+/* Per-state status bits (0 = valid). */
+#define LISA_STATE_BAD_COUNT 1     /* in-between knot count outside [0, kmax] */
+#define LISA_STATE_BAD_POSITION 2  /* position non-finite or not strictly inside (x_lo, x_hi) */
+#define LISA_STATE_DUPLICATE 4     /* two in-between knots share a position */
+#define LISA_STATE_BAD_AMPLITUDE 8 /* non-finite knot amplitude */
+#define LISA_STATE_BAD_THETA 16    /* non-finite template parameter (oracle-side bit; the GPU
+                                      entry points report such a state as log L = -inf) */
+#define LISA_STATE_NONFINITE 32    /* the PSD or the log-likelihood came out non-finite
+                                      (likewise reported by the GPU as log L = -inf) */
+
+#define LISA_N_THETA 5   /* theta per state: a_oms, a_tm, log10 A, n1, n2 */
+#define LISA_MAX_KNOTS 62 /* largest kmax (in-between knots per spline) */
+
+/* One or more datasets, each with its bins and the states evaluated on it.
+ * Dataset d owns bins [bin_offset[d], bin_offset[d+1]) and states
+ * [state_offset[d], state_offset[d+1]); n_bins = bin_offset[n_datasets],
+ * n_states = state_offset[n_datasets].  All arrays are HOST memory, copied at create time. */
+typedef struct lisa_data_desc {
+    int32_t n_datasets;        /* >= 1 */
+    int32_t n_channels;        /* 2 (A, E) or 3 (A, E, T) */
+    int32_t sgwb_model;        /* lisa_sgwb_model */
+    int32_t tdi_form;          /* lisa_tdi_form */
+    const int64_t* bin_offset;   /* [n_datasets+1], nondecreasing, bin_offset[0] = 0 */
+    const int64_t* state_offset; /* [n_datasets+1], nondecreasing, state_offset[0] = 0 */
+    const double* freq;        /* [n_bins] bin frequencies f_i in Hz, > 0, increasing per dataset */
+    const double* nu;          /* [n_bins] degrees of freedom n_i of the averaged periodogram, >= 0 */
+    const double* periodogram; /* [n_channels][n_bins] averaged auto-powers P_c(f_i), > 0, finite */
+    const double* response;    /* [n_channels][n_bins] SGWB response R_c(f_i) >= 0; NULL if NONE */
+    const double* x_lo;        /* [n_datasets] left edge knot position (log10 Hz) */
+    const double* x_hi;        /* [n_datasets] right edge knot position, > x_lo */
+    const double* f_ref;       /* [n_datasets] power-law reference / break frequency (Hz) > 0 */
+} lisa_data_desc;
+
+typedef struct lisa_data lisa_data; /* opaque: device tables + work decomposition */
+
+/* Per-state template parameters.  theta_dev [n_states][LISA_N_THETA] (device, FP64):
+ *   a_oms = A_OMS / 1e-12 m/sqrt(Hz), a_tm = A_TM / 1e-15 m/s^2/sqrt(Hz)   (Table I units)
+ *   log10 A, n1, n2 of the SGWB (n2 is read only by LISA_SGWB_BROKEN; for the power law the
+ *   slope is n1).  Entries the model does not use are ignored. */
+typedef struct lisa_params {
+    int32_t n_states;
+    const double* theta_dev;
+} lisa_params;
+
+/* Variable-knot perturbation splines, n_splines = n_channels + (sgwb_model != NONE):
+ * spline a = 0..n_channels-1 perturbs the noise of channel A, E (, T); the last one perturbs
+ * the SGWB (shared by all channels).  All arrays are DEVICE memory:
+ *   count_dev [n_states][n_splines]           in-between knots k (0..kmax)
+ *   x_dev     [n_states][n_splines][kmax]     in-between positions log10 f, any order
+ *   w_dev     [n_states][n_splines][kmax+2]   slot 0 = w_0 (left edge), 1+j = knot j,
+ *                                             kmax+1 = w_n (right edge)  */
+typedef struct lisa_knots {
+    int32_t n_states;
+    int32_t n_splines;
+    int32_t kmax;   /* 0..LISA_MAX_KNOTS */
+    int32_t kind;   /* lisa_spline_kind */
+    const int32_t* count_dev;
+    const double* x_dev;
+    const double* w_dev;
+} lisa_knots;
+
+/* Tiling of the fused likelihood kernels (chosen by the autotuner; defaults are sane). */
+typedef struct lisa_tiling {
+    int32_t tile_bins;      /* bins staged per work item: multiple of 32, 64..2048 */
+    int32_t states_per_cta; /* states per work item: power of two, 16..256 (<= threads) */
+    int32_t group;          /* bins processed between interval checks: 1, 2, 4 or 8 */
+    int32_t ctas_per_sm;    /* persistent grid = SMs x this (0 = occupancy limit) */
+} lisa_tiling;
+
+/* Sizes of the dataset object and the layout of the gradient. */
+typedef struct lisa_data_info {
+    int64_t n_bins, n_states;
+    int32_t n_datasets, n_channels, n_splines, sgwb_model;
+    int64_t n_items;          /* work items of the fused kernels under the current tiling */
+    int32_t n_sm;             /* SMs of the device the object lives on */
+    lisa_tiling tiling;
+} lisa_data_info;
+
+/* ---- dataset --------------------------------------------------------------------------- */
+
+/* Validates the description, uploads it, and runs the per-bin precompute on `stream`
+ * (Sec. II.B/II.C templates per bin in FP64, u = 2 pi f L / c with 1 - cos u = 2 sin^2(u/2),
+ * normalisation of the template tables by the periodogram, the constant -sum nu sum_c ln P_c).
+ * Synchronises the stream.  On success *out owns device memory until lisa_data_destroy. */
+lisa_status lisa_data_create(const lisa_data_desc* desc, lisa_stream_t stream, lisa_data** out);
+lisa_status lisa_data_destroy(lisa_data* data);
+lisa_status lisa_data_get_info(const lisa_data* data, lisa_data_info* info);
+/* Replaces the tiling (rebuilds the work list; synchronous).  Invalid fields -> LISA_ERR_VALUE. */
+lisa_status lisa_data_set_tiling(lisa_data* data, const lisa_tiling* tiling);
+
+/* ---- spline setup (knot sort + slopes + coefficients, Appendix A) ------------------------ */
+
+/* Bytes of the caller-allocated spline buffer for this dataset's states and kmax. */
+size_t lisa_spline_buf_bytes(const lisa_data* data, int32_t kmax, lisa_precision precision);
+
+/* One warp per state: sorts each spline's in-between knots, appends the edges, computes the
+ * Akima slopes (or the natural-cubic second derivatives by a warp-parallel tridiagonal
+ * solve) and the per-interval cubic coefficients, and writes them to spline_buf_dev
+ * (16-byte aligned, lisa_spline_buf_bytes long).  state_status_dev [n_states] (may be NULL)
+ * receives the LISA_STATE_* bits of each state; the buffer keeps its own copy. */
+lisa_status lisa_spline_setup(const lisa_data* data, const lisa_knots* knots,
+                              lisa_precision precision, void* spline_buf_dev, size_t spline_buf_bytes,
+                              int32_t* state_status_dev, lisa_stream_t stream);
+
+/* ---- log-likelihood ------------------------------------------------------------------------ */
+
+/* Bytes of scratch workspace the likelihood entry points need (per-state partial sums).
+ * with_grad = 0 for lisa_psd_loglike, 1 for lisa_psd_loglike_grad. */
+size_t lisa_workspace_bytes(const lisa_data* data, int32_t kmax, lisa_precision precision,
+                            int32_t with_grad);
+
+/* Eq. (1) for every state: fused spline evaluation, PSD assembly (2), per-bin terms and a
+ * deterministic FP64 reduction over bins.  loglike_dev [n_states] (FP64).  spline_buf_dev is
+ * the output of lisa_spline_setup with the same precision and kmax.  workspace_dev: at least
+ * lisa_workspace_bytes(..., 0) bytes, 256-byte aligned, contents ignored and overwritten.
+ * Calls that share a workspace must not overlap on the GPU. */
+lisa_status lisa_psd_loglike(const lisa_data* data, const lisa_params* params,
+                             const void* spline_buf_dev, size_t spline_buf_bytes, int32_t kmax,
+                             double* loglike_dev, void* workspace_dev, size_t workspace_bytes,
+                             lisa_precision precision, lisa_stream_t stream);
+
+/* log L and its gradient for every state (hand-written adjoint; the spline coefficients are
+ * recomputed from the knots, nothing per bin is stored).  grad_dev
+ * [n_states][LISA_N_THETA + n_splines*(2*kmax+2)] (FP64): d log L / d theta (a_oms, a_tm,
+ * log10 A, n1, n2), then per spline d/d(w slots 0..kmax+1) and d/d(x slots 0..kmax-1);
+ * unused slots are 0.  spline_buf_dev must come from lisa_spline_setup on the same knots. */
+lisa_status lisa_psd_loglike_grad(const lisa_data* data, const lisa_params* params,
+                                  const lisa_knots* knots, const void* spline_buf_dev,
+                                  size_t spline_buf_bytes, double* loglike_dev, double* grad_dev,
+                                  void* workspace_dev, size_t workspace_bytes,
+                                  lisa_precision precision, lisa_stream_t stream);
+
+/* Model PSD S_c(f_i) of (2) for every state in physical units (FP64):
+ * psd_dev [n_states][n_channels][n_bins_of_its_dataset], states concatenated in order
+ * (state s of dataset d starts at sum over earlier states of n_channels * their dataset's
+ * bins).  Uses the FP64 spline buffer. */
+lisa_status lisa_model_psd(const lisa_data* data, const lisa_params* params,
+                           const void* spline_buf_dev_fp64, size_t spline_buf_bytes, int32_t kmax,
+                           double* psd_dev, lisa_stream_t stream);
+
+const char* lisa_status_string(lisa_status status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LISA_PSD_H */

@@ -1,0 +1,381 @@
+"""Thin Python binding of ``include/lisa_psd.h`` (ctypes; argument marshalling only).
+
+Every step of the likelihood runs in the CUDA library ``lib/liblisa_psd.so``; this module only
+passes device pointers (from torch tensors) and the current CUDA stream.  There is no CPU
+fallback: if the library is missing or no GPU is present, calls raise.
+
+Names follow the C ABI: ``Dataset`` wraps ``lisa_data`` (create / destroy / tiling),
+``Dataset.spline_setup`` -> ``lisa_spline_setup``, ``Dataset.psd_loglike`` -> ``lisa_psd_loglike``,
+``Dataset.psd_loglike_grad`` -> ``lisa_psd_loglike_grad``, ``Dataset.model_psd`` -> ``lisa_model_psd``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+FP32, FP64 = 0, 1
+AKIMA, NATURAL = 0, 1
+SGWB_NONE, SGWB_POWER_LAW, SGWB_BROKEN = 0, 1, 2
+TDI_PRINTED, TDI_SIN2_2U = 0, 1
+N_THETA = 5
+MAX_KNOTS = 62
+
+STATE_BITS = {1: "bad_count", 2: "bad_position", 4: "duplicate", 8: "bad_amplitude", 16: "bad_theta",
+              32: "nonfinite"}
+
+_c_i32, _c_i64, _c_dbl, _c_vp, _c_sz = ctypes.c_int32, ctypes.c_int64, ctypes.c_double, ctypes.c_void_p, ctypes.c_size_t
+_P_i64 = ctypes.POINTER(_c_i64)
+_P_dbl = ctypes.POINTER(_c_dbl)
+
+
+class lisa_data_desc(ctypes.Structure):
+    _fields_ = [("n_datasets", _c_i32), ("n_channels", _c_i32), ("sgwb_model", _c_i32), ("tdi_form", _c_i32),
+                ("bin_offset", _P_i64), ("state_offset", _P_i64), ("freq", _P_dbl), ("nu", _P_dbl),
+                ("periodogram", _P_dbl), ("response", _P_dbl), ("x_lo", _P_dbl), ("x_hi", _P_dbl),
+                ("f_ref", _P_dbl)]
+
+
+class lisa_params(ctypes.Structure):
+    _fields_ = [("n_states", _c_i32), ("theta_dev", _c_vp)]
+
+
+class lisa_knots(ctypes.Structure):
+    _fields_ = [("n_states", _c_i32), ("n_splines", _c_i32), ("kmax", _c_i32), ("kind", _c_i32),
+                ("count_dev", _c_vp), ("x_dev", _c_vp), ("w_dev", _c_vp)]
+
+
+class lisa_tiling(ctypes.Structure):
+    _fields_ = [("tile_bins", _c_i32), ("states_per_cta", _c_i32), ("group", _c_i32), ("ctas_per_sm", _c_i32)]
+
+
+class lisa_data_info(ctypes.Structure):
+    _fields_ = [("n_bins", _c_i64), ("n_states", _c_i64), ("n_datasets", _c_i32), ("n_channels", _c_i32),
+                ("n_splines", _c_i32), ("sgwb_model", _c_i32), ("n_items", _c_i64), ("n_sm", _c_i32),
+                ("tiling", lisa_tiling)]
+
+
+EXPORTS = ["lisa_data_create", "lisa_data_destroy", "lisa_data_get_info", "lisa_data_set_tiling",
+           "lisa_spline_buf_bytes", "lisa_spline_setup", "lisa_workspace_bytes", "lisa_psd_loglike",
+           "lisa_psd_loglike_grad", "lisa_model_psd", "lisa_status_string"]
+
+_lock = threading.Lock()
+_lib = None
+
+
+class LisaError(RuntimeError):
+    pass
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True) -> ctypes.CDLL:
+    """Loads the CUDA library (building it in-tree if needed).  Raises if it cannot."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(_build.LIB) or not _build.up_to_date():
+            if not build_if_missing:
+                raise LisaError(f"CUDA library not built: {_build.LIB}")
+            _build.build()
+        lib = ctypes.CDLL(_build.LIB)
+        S = _c_i32  # enum lisa_status
+        lib.lisa_data_create.argtypes = [ctypes.POINTER(lisa_data_desc), _c_vp, ctypes.POINTER(_c_vp)]
+        lib.lisa_data_create.restype = S
+        lib.lisa_data_destroy.argtypes = [_c_vp]
+        lib.lisa_data_destroy.restype = S
+        lib.lisa_data_get_info.argtypes = [_c_vp, ctypes.POINTER(lisa_data_info)]
+        lib.lisa_data_get_info.restype = S
+        lib.lisa_data_set_tiling.argtypes = [_c_vp, ctypes.POINTER(lisa_tiling)]
+        lib.lisa_data_set_tiling.restype = S
+        lib.lisa_spline_buf_bytes.argtypes = [_c_vp, _c_i32, _c_i32]
+        lib.lisa_spline_buf_bytes.restype = _c_sz
+        lib.lisa_spline_setup.argtypes = [_c_vp, ctypes.POINTER(lisa_knots), _c_i32, _c_vp, _c_sz, _c_vp, _c_vp]
+        lib.lisa_spline_setup.restype = S
+        lib.lisa_workspace_bytes.argtypes = [_c_vp, _c_i32, _c_i32, _c_i32]
+        lib.lisa_workspace_bytes.restype = _c_sz
+        lib.lisa_psd_loglike.argtypes = [_c_vp, ctypes.POINTER(lisa_params), _c_vp, _c_sz, _c_i32, _c_vp, _c_vp,
+                                         _c_sz, _c_i32, _c_vp]
+        lib.lisa_psd_loglike.restype = S
+        lib.lisa_psd_loglike_grad.argtypes = [_c_vp, ctypes.POINTER(lisa_params), ctypes.POINTER(lisa_knots), _c_vp,
+                                              _c_sz, _c_vp, _c_vp, _c_vp, _c_sz, _c_i32, _c_vp]
+        lib.lisa_psd_loglike_grad.restype = S
+        lib.lisa_model_psd.argtypes = [_c_vp, ctypes.POINTER(lisa_params), _c_vp, _c_sz, _c_i32, _c_vp, _c_vp]
+        lib.lisa_model_psd.restype = S
+        lib.lisa_status_string.argtypes = [_c_i32]
+        lib.lisa_status_string.restype = ctypes.c_char_p
+        _lib = lib
+        return lib
+
+
+def _check(st: int, what: str):
+    if st != 0:
+        msg = load().lisa_status_string(st).decode()
+        raise LisaError(f"{what} failed: status {st} ({msg})")
+
+
+def _torch():
+    import torch
+    if not torch.cuda.is_available():
+        raise LisaError("no CUDA device: the lisa_psd library runs on the GPU only")
+    return torch
+
+
+def _stream_handle(stream=None):
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _np_ptr(a, ctype):
+    return a.ctypes.data_as(ctypes.POINTER(ctype))
+
+
+class Dataset:
+    """A ``lisa_data`` object: one or more datasets with their bins and states.
+
+    Host arrays (numpy, FP64): freq [N], nu [N], periodogram [C, N], response [C, N] (or None for
+    the noise-only model), bin_offset / state_offset [D+1], x_lo / x_hi / f_ref [D]."""
+
+    def __init__(self, *, n_channels, freq, nu, periodogram, response=None, bin_offset=None, state_offset=None,
+                 n_states=None, x_lo, x_hi, f_ref, sgwb_model=SGWB_POWER_LAW, tdi_form=TDI_PRINTED, stream=None):
+        lib = load()
+        torch = _torch()
+        self.device = torch.cuda.current_device()
+        freq = np.ascontiguousarray(freq, np.float64).ravel()
+        N = freq.size
+        if bin_offset is None:
+            bin_offset = np.array([0, N], np.int64)
+        if state_offset is None:
+            state_offset = np.array([0, int(n_states)], np.int64)
+        self._keep = dict(
+            bin_offset=np.ascontiguousarray(bin_offset, np.int64), state_offset=np.ascontiguousarray(state_offset, np.int64),
+            freq=freq, nu=np.ascontiguousarray(np.broadcast_to(np.asarray(nu, np.float64), (N,))),
+            P=np.ascontiguousarray(periodogram, np.float64).reshape(n_channels, N),
+            R=None if response is None else np.ascontiguousarray(response, np.float64).reshape(n_channels, N),
+            x_lo=np.atleast_1d(np.ascontiguousarray(x_lo, np.float64)),
+            x_hi=np.atleast_1d(np.ascontiguousarray(x_hi, np.float64)),
+            f_ref=np.atleast_1d(np.ascontiguousarray(f_ref, np.float64)))
+        k = self._keep
+        D = k["bin_offset"].size - 1
+        desc = lisa_data_desc(
+            n_datasets=D, n_channels=int(n_channels), sgwb_model=int(sgwb_model), tdi_form=int(tdi_form),
+            bin_offset=_np_ptr(k["bin_offset"], _c_i64), state_offset=_np_ptr(k["state_offset"], _c_i64),
+            freq=_np_ptr(k["freq"], _c_dbl), nu=_np_ptr(k["nu"], _c_dbl), periodogram=_np_ptr(k["P"], _c_dbl),
+            response=None if k["R"] is None else _np_ptr(k["R"], _c_dbl), x_lo=_np_ptr(k["x_lo"], _c_dbl),
+            x_hi=_np_ptr(k["x_hi"], _c_dbl), f_ref=_np_ptr(k["f_ref"], _c_dbl))
+        h = _c_vp()
+        _check(lib.lisa_data_create(ctypes.byref(desc), _stream_handle(stream), ctypes.byref(h)), "lisa_data_create")
+        self._h = h
+        self.n_channels = int(n_channels)
+        self.sgwb_model = int(sgwb_model)
+        self.n_splines = self.n_channels + (1 if sgwb_model else 0)
+        self.n_states = int(k["state_offset"][-1])
+        self.n_bins = N
+        self.n_datasets = D
+        self.bin_offset = k["bin_offset"]
+        self.state_offset = k["state_offset"]
+
+    @classmethod
+    def from_workload(cls, wl, periodogram, **kw):
+        """Dataset object for a ``synth.Workload`` with the given periodogram [C, N]."""
+        return cls(n_channels=wl.n_channels, freq=wl.f, nu=wl.nu, periodogram=periodogram,
+                   response=wl.R if wl.sgwb_model else None, bin_offset=wl.bin_offset, state_offset=wl.state_offset,
+                   x_lo=wl.x_lo, x_hi=wl.x_hi, f_ref=wl.f_ref, sgwb_model=wl.sgwb_model, tdi_form=wl.tdi_form, **kw)
+
+    # ---- lifetime -------------------------------------------------------------------------
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            load().lisa_data_destroy(self._h)
+            self._h = _c_vp()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def handle(self):
+        return self._h
+
+    def info(self) -> dict:
+        inf = lisa_data_info()
+        _check(load().lisa_data_get_info(self._h, ctypes.byref(inf)), "lisa_data_get_info")
+        t = inf.tiling
+        return {"n_bins": inf.n_bins, "n_states": inf.n_states, "n_datasets": inf.n_datasets,
+                "n_channels": inf.n_channels, "n_splines": inf.n_splines, "sgwb_model": inf.sgwb_model,
+                "n_items": inf.n_items, "n_sm": inf.n_sm,
+                "tiling": {"tile_bins": t.tile_bins, "states_per_cta": t.states_per_cta, "group": t.group,
+                           "ctas_per_sm": t.ctas_per_sm}}
+
+    def set_tiling(self, tile_bins=1024, states_per_cta=256, group=4, ctas_per_sm=0):
+        t = lisa_tiling(int(tile_bins), int(states_per_cta), int(group), int(ctas_per_sm))
+        _check(load().lisa_data_set_tiling(self._h, ctypes.byref(t)), "lisa_data_set_tiling")
+
+    # ---- sizes ----------------------------------------------------------------------------
+    def spline_buf_bytes(self, kmax, precision):
+        return int(load().lisa_spline_buf_bytes(self._h, int(kmax), int(precision)))
+
+    def workspace_bytes(self, kmax, precision, with_grad=False):
+        return int(load().lisa_workspace_bytes(self._h, int(kmax), int(precision), int(bool(with_grad))))
+
+    # ---- entry points -----------------------------------------------------------------------
+    def _knots(self, count, x, w, kmax, kind):
+        return lisa_knots(self.n_states, self.n_splines, int(kmax), int(kind), count.data_ptr(),
+                          x.data_ptr() if x.numel() else None, w.data_ptr())
+
+    def spline_setup(self, count, x, w, kmax, kind=AKIMA, precision=FP32, buf=None, status=None, stream=None):
+        """``lisa_spline_setup`` on device tensors count [S, nsp] int32, x [S, nsp, kmax] f64,
+        w [S, nsp, kmax+2] f64.  Returns (spline buffer, per-state status int32)."""
+        torch = _torch()
+        nb = self.spline_buf_bytes(kmax, precision)
+        if buf is None:
+            buf = torch.empty(nb, dtype=torch.uint8, device="cuda")
+        if status is None:
+            status = torch.empty(self.n_states, dtype=torch.int32, device="cuda")
+        kn = self._knots(count, x, w, kmax, kind)
+        _check(load().lisa_spline_setup(self._h, ctypes.byref(kn), int(precision), buf.data_ptr(), buf.numel(),
+                                        status.data_ptr(), _stream_handle(stream)), "lisa_spline_setup")
+        return buf, status
+
+    def psd_loglike(self, theta, buf, kmax, precision=FP32, out=None, workspace=None, stream=None):
+        """``lisa_psd_loglike``: theta [S, 5] f64 device -> log L [S] f64 device."""
+        torch = _torch()
+        if out is None:
+            out = torch.empty(self.n_states, dtype=torch.float64, device="cuda")
+        if workspace is None:
+            workspace = torch.empty(self.workspace_bytes(kmax, precision), dtype=torch.uint8, device="cuda")
+        pr = lisa_params(self.n_states, theta.data_ptr())
+        _check(load().lisa_psd_loglike(self._h, ctypes.byref(pr), buf.data_ptr(), buf.numel(), int(kmax),
+                                       out.data_ptr(), workspace.data_ptr(), workspace.numel(), int(precision),
+                                       _stream_handle(stream)), "lisa_psd_loglike")
+        return out
+
+    def psd_loglike_grad(self, theta, count, x, w, kmax, kind, buf, precision=FP32, out=None, grad=None,
+                         workspace=None, stream=None):
+        """``lisa_psd_loglike_grad``: returns (log L [S], grad [S, 5 + nsp*(2 kmax + 2)])."""
+        torch = _torch()
+        G = N_THETA + self.n_splines * (2 * int(kmax) + 2)
+        if out is None:
+            out = torch.empty(self.n_states, dtype=torch.float64, device="cuda")
+        if grad is None:
+            grad = torch.empty((self.n_states, G), dtype=torch.float64, device="cuda")
+        if workspace is None:
+            workspace = torch.empty(self.workspace_bytes(kmax, precision, True), dtype=torch.uint8, device="cuda")
+        pr = lisa_params(self.n_states, theta.data_ptr())
+        kn = self._knots(count, x, w, kmax, kind)
+        _check(load().lisa_psd_loglike_grad(self._h, ctypes.byref(pr), ctypes.byref(kn), buf.data_ptr(), buf.numel(),
+                                            out.data_ptr(), grad.data_ptr(), workspace.data_ptr(), workspace.numel(),
+                                            int(precision), _stream_handle(stream)), "lisa_psd_loglike_grad")
+        return out, grad
+
+    def model_psd(self, theta, buf64, kmax, out=None, stream=None):
+        """``lisa_model_psd``: physical S_c(f_i) per state (FP64 spline buffer)."""
+        torch = _torch()
+        n = int(sum(self.n_channels * (self.state_offset[d + 1] - self.state_offset[d]) *
+                    (self.bin_offset[d + 1] - self.bin_offset[d]) for d in range(self.n_datasets)))
+        if out is None:
+            out = torch.empty(max(n, 1), dtype=torch.float64, device="cuda")
+        pr = lisa_params(self.n_states, theta.data_ptr())
+        _check(load().lisa_model_psd(self._h, ctypes.byref(pr), buf64.data_ptr(), buf64.numel(), int(kmax),
+                                     out.data_ptr(), _stream_handle(stream)), "lisa_model_psd")
+        return out
+
+
+def knots_to_device(knots, device="cuda"):
+    """(count int32, x f64, w f64) device tensors from a synth.Knots / dict of numpy arrays."""
+    torch = _torch()
+    k = knots.as_dict() if hasattr(knots, "as_dict") else knots
+    kmax = int(k["kmax"])
+    count = torch.as_tensor(np.ascontiguousarray(k["count"], np.int32), device=device)
+    x = torch.as_tensor(np.ascontiguousarray(np.asarray(k["x"], np.float64)[..., :kmax]), device=device)
+    w = torch.as_tensor(np.ascontiguousarray(k["w"], np.float64), device=device)
+    return count, x.contiguous(), w, kmax, int(k.get("kind", 0))
+
+
+class Evaluator:
+    """Preallocated hot path for one Dataset: knots / theta in, log L out.
+
+    ``step()`` runs lisa_spline_setup + lisa_psd_loglike on device-resident inputs (the MCMC
+    inner loop when the sampler lives on the GPU); ``loglike_host()`` is the end-to-end call of a
+    host-side sampler: pinned host inputs are copied to the device, evaluated, and log L is copied
+    back into pinned host memory.  ``capture()`` records step() into a CUDA graph."""
+
+    def __init__(self, dataset: Dataset, kmax: int, kind: int = AKIMA, precision: int = FP32):
+        torch = _torch()
+        self.ds, self.kmax, self.kind, self.precision = dataset, int(kmax), int(kind), int(precision)
+        S, nsp = dataset.n_states, dataset.n_splines
+        dev = "cuda"
+        self.theta = torch.zeros((S, N_THETA), dtype=torch.float64, device=dev)
+        self.count = torch.zeros((S, nsp), dtype=torch.int32, device=dev)
+        self.x = torch.zeros((S, nsp, self.kmax), dtype=torch.float64, device=dev)
+        self.w = torch.zeros((S, nsp, self.kmax + 2), dtype=torch.float64, device=dev)
+        self.buf = torch.empty(dataset.spline_buf_bytes(kmax, precision), dtype=torch.uint8, device=dev)
+        self.status = torch.empty(S, dtype=torch.int32, device=dev)
+        self.ws = torch.empty(dataset.workspace_bytes(kmax, precision), dtype=torch.uint8, device=dev)
+        self.out = torch.empty(S, dtype=torch.float64, device=dev)
+        self.graph = None
+
+    def load(self, theta, count, x, w):
+        self.theta.copy_(theta)
+        self.count.copy_(count)
+        self.x.copy_(x)
+        self.w.copy_(w)
+
+    def setup(self, stream=None):
+        self.ds.spline_setup(self.count, self.x, self.w, self.kmax, self.kind, self.precision, buf=self.buf,
+                             status=self.status, stream=stream)
+
+    def loglike(self, stream=None):
+        return self.ds.psd_loglike(self.theta, self.buf, self.kmax, self.precision, out=self.out,
+                                   workspace=self.ws, stream=stream)
+
+    def step(self, stream=None):
+        self.setup(stream)
+        return self.loglike(stream)
+
+    def capture(self):
+        """Captures setup and log-likelihood as two CUDA graphs (so they can be timed apart)."""
+        torch = _torch()
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            self.step()  # warm (sets kernel attributes outside capture)
+        torch.cuda.current_stream().wait_stream(s)
+        torch.cuda.synchronize()
+        self.g_setup, self.g_ll = torch.cuda.CUDAGraph(), torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.g_setup):
+            self.setup()
+        with torch.cuda.graph(self.g_ll):
+            self.loglike()
+        self.graph = True
+        return self
+
+    def replay(self):
+        self.g_setup.replay()
+        self.g_ll.replay()
+        return self.out
+
+    def loglike_host(self, theta, count, x, w, out):
+        """End-to-end: pinned host tensors in (theta [S,5] f64, count [S,nsp] i32, x, w f64),
+        log L written into the pinned host tensor ``out`` [S]; returns ``out`` after the copy."""
+        torch = _torch()
+        self.theta.copy_(theta, non_blocking=True)
+        self.count.copy_(count, non_blocking=True)
+        self.x.copy_(x, non_blocking=True)
+        self.w.copy_(w, non_blocking=True)
+        if self.graph:
+            self.replay()
+        else:
+            self.step()
+        out.copy_(self.out, non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+        return out

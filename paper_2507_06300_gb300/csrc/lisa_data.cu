@@ -1,0 +1,385 @@
+// Dataset object: validation, upload, the per-bin FP64 precompute (templates of Sec. II.B and
+// Sec. II.C normalised by the periodogram) and the work decomposition of the fused kernels.
+#include <algorithm>
+#include <cmath>
+#include <new>
+
+#include "lisa_internal.cuh"
+
+namespace lisa {
+
+lisa_status check_cuda(cudaError_t e) { return e == cudaSuccess ? LISA_SUCCESS : LISA_ERR_CUDA; }
+
+namespace {
+
+__device__ __forceinline__ int dataset_of_bin(const DatasetDev* ds, int n, int64_t i) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (ds[mid].bin0 <= i) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Per-bin precompute in FP64 (one thread per bin).  With u = 2 pi f L / c:
+//   A/E noise per unit amplitude^2:  32 T(u) (2 + cos u) S_OMS1,  32 T(u) 4 (1 + cos u + cos^2 u) S_TM1
+//   T noise per unit amplitude^2:    64 T(u) (1 - cos u) S_OMS1,  64 T(u) 2 (1 - cos u)^2 S_TM1
+//   (Eq. noise_tdi; T(u) = sin^2 u sin^4 u as printed, or sin^2 u sin^2 2u; 1 - cos u is
+//   evaluated as 2 sin^2(u/2)), SGWB per unit h^2 Omega: R_c 3 (H0/h)^2 / (4 pi^2 f^3) (Eq. Sh).
+// Every table entry is divided by the channel's periodogram P_c(f_i), so the per-bin ratio
+// P/S becomes 1/S-hat and the FP32 path works on numbers of order one.
+__global__ void prep_kernel(int64_t n_bins, int C, int tdi_form, int sgwb, const double* __restrict__ f,
+                            const double* __restrict__ nu, const double* __restrict__ P,
+                            const double* __restrict__ R, const DatasetDev* __restrict__ ds,
+                            int n_ds, double* __restrict__ rec64, float* __restrict__ rec32,
+                            float* __restrict__ xlo32, float* __restrict__ elllo32, double* __restrict__ lnP) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_bins) return;
+    int d = dataset_of_bin(ds, n_ds, i);
+    double fi = f[i];
+    double u = 2.0 * kPi * fi * kArm / kClight;
+    double su, cu;
+    sincos(u, &su, &cu);
+    double pref;
+    if (tdi_form == 0) {
+        pref = su * su * su * su * su * su;
+    } else {
+        double s2u = sin(2.0 * u);
+        pref = su * su * s2u * s2u;
+    }
+    double sh = sin(0.5 * u);
+    double omc = 2.0 * sh * sh;
+    double lo = 2.0e-3 / fi, cv = 2.0 * kPi * fi / kClight;
+    double oms1 = 1.0e-24 * (1.0 + lo * lo * lo * lo) * cv * cv;
+    double l2 = 0.4e-3 / fi, h2 = fi / 8.0e-3, ct = 1.0 / (2.0 * kPi * fi * kClight);
+    double tm1 = 1.0e-30 * (1.0 + l2 * l2) * (1.0 + h2 * h2 * h2 * h2) * ct * ct;
+    double go[3], gt[3], gh[3] = {0.0, 0.0, 0.0};
+    go[0] = go[1] = 32.0 * pref * (2.0 + cu) * oms1;
+    gt[0] = gt[1] = 32.0 * pref * 4.0 * (1.0 + cu + cu * cu) * tm1;
+    go[2] = 64.0 * pref * omc * oms1;
+    gt[2] = 64.0 * pref * 2.0 * omc * omc * tm1;
+    double conv = 3.0 * kH0h * kH0h / (4.0 * kPi * kPi * fi * fi * fi);
+    double r[kRec];
+    r[0] = log10(fi);
+    r[1] = log2(fi / ds[d].f_ref);
+    r[2] = nu[i];
+    double lsum = 0.0;
+    for (int c = 0; c < 3; ++c) {
+        double g_o = 0.0, g_t = 0.0, g_h = 0.0;
+        if (c < C) {
+            double p = P[(size_t)c * n_bins + i];
+            if (sgwb) gh[c] = R[(size_t)c * n_bins + i] * conv;
+            g_o = go[c] / p;
+            g_t = gt[c] / p;
+            g_h = gh[c] / p;
+            lsum += log(p);
+        }
+        r[3 + c] = g_o;
+        r[6 + c] = g_t;
+        r[9 + c] = g_h;
+    }
+    lnP[i] = nu[i] * lsum;
+    xlo32[i] = (float)(r[0] - (double)(float)r[0]);
+    elllo32[i] = (float)(r[1] - (double)(float)r[1]);
+    for (int q = 0; q < kRec; ++q) {
+        rec64[(size_t)i * kRec + q] = r[q];
+        rec32[(size_t)i * kRec + q] = (float)r[q];
+    }
+}
+
+// Deterministic per-dataset sums (one block per dataset, fixed-order tree):
+//   K = -sum_i nu_i sum_c ln P_c,i  and  Cnu = C sum_i nu_i.
+__global__ void dataset_sums_kernel(const double* __restrict__ lnP, const double* __restrict__ nu,
+                                    DatasetDev* ds, int C) {
+    __shared__ double s1[256], s2[256];
+    DatasetDev& D = ds[blockIdx.x];
+    double a = 0.0, b = 0.0;
+    for (int64_t i = threadIdx.x; i < D.nbins; i += blockDim.x) {
+        a += lnP[D.bin0 + i];
+        b += nu[D.bin0 + i];
+    }
+    s1[threadIdx.x] = a;
+    s2[threadIdx.x] = b;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) {
+            s1[threadIdx.x] += s1[threadIdx.x + w];
+            s2[threadIdx.x] += s2[threadIdx.x + w];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        D.K = -s1[0];
+        D.Cnu = (double)C * s2[0];
+    }
+}
+
+template <class T>
+lisa_status dev_alloc(T** p, size_t n) {
+    if (n == 0) n = 1;
+    return cudaMalloc((void**)p, n * sizeof(T)) == cudaSuccess ? LISA_SUCCESS : LISA_ERR_ALLOC;
+}
+
+void release(lisa_data* d) {
+    cudaFree(d->d_ds);
+    cudaFree(d->d_state_ds);
+    cudaFree(d->d_rec32);
+    cudaFree(d->d_rec64);
+    cudaFree(d->d_P);
+    cudaFree(d->d_xlo32);
+    cudaFree(d->d_elllo32);
+    cudaFree(d->d_items);
+    d->d_ds = nullptr;
+    d->d_state_ds = nullptr;
+    d->d_rec32 = nullptr;
+    d->d_rec64 = nullptr;
+    d->d_P = nullptr;
+    d->d_xlo32 = nullptr;
+    d->d_elllo32 = nullptr;
+    d->d_items = nullptr;
+}
+
+int pow2ceil(int v) {
+    int p = 1;
+    while (p < v) p <<= 1;
+    return p;
+}
+
+}  // namespace
+
+// Builds the work list for the current tiling: per dataset, tiles of tile_bins bins times
+// chunks of sc states (sc = min(states_per_cta, next power of two >= states of the dataset)).
+lisa_status rebuild_work(lisa_data* d) {
+    const lisa_tiling& t = d->tiling;
+    std::vector<WorkItem> items;
+    int64_t pbase = 0;
+    for (int k = 0; k < d->n_datasets; ++k) {
+        DatasetDev& D = d->h_ds[k];
+        D.ntiles = (int32_t)((D.nbins + t.tile_bins - 1) / t.tile_bins);
+        D.pbase = pbase;
+        pbase += (int64_t)D.ns * D.ntiles;
+        if (D.ns == 0 || D.nbins == 0) continue;
+        int sc = std::min(t.states_per_cta, pow2ceil(D.ns));
+        sc = std::max(sc, 1);
+        for (int32_t tile = 0; tile < D.ntiles; ++tile) {
+            int64_t b0 = D.bin0 + (int64_t)tile * t.tile_bins;
+            int32_t nb = (int32_t)std::min<int64_t>(t.tile_bins, D.bin0 + D.nbins - b0);
+            for (int32_t s = 0; s < D.ns; s += sc) {
+                WorkItem w;
+                w.bin0 = b0;
+                w.nb = nb;
+                w.s0 = D.s0 + s;
+                w.ns = std::min(sc, D.ns - s);
+                w.sc = sc;
+                w.tile = tile;
+                w.ds = k;
+                items.push_back(w);
+            }
+        }
+    }
+    // Larger tiles first so that the persistent grid's static schedule ends evenly.
+    std::stable_sort(items.begin(), items.end(), [](const WorkItem& a, const WorkItem& b) {
+        return (int64_t)a.nb * a.ns > (int64_t)b.nb * b.ns;
+    });
+    d->n_partials = pbase;
+    cudaFree(d->d_items);
+    d->d_items = nullptr;
+    d->n_items = (int64_t)items.size();
+    lisa_status st = dev_alloc(&d->d_items, items.size());
+    if (st) return st;
+    if (cudaMemcpy(d->d_items, items.data(), items.size() * sizeof(WorkItem), cudaMemcpyHostToDevice) !=
+        cudaSuccess)
+        return LISA_ERR_CUDA;
+    // device copy of the dataset table (ntiles / pbase changed)
+    if (cudaMemcpy(d->d_ds, d->h_ds.data(), d->h_ds.size() * sizeof(DatasetDev),
+                   cudaMemcpyHostToDevice) != cudaSuccess)
+        return LISA_ERR_CUDA;
+    return LISA_SUCCESS;
+}
+
+}  // namespace lisa
+
+using namespace lisa;
+
+extern "C" {
+
+const char* lisa_status_string(lisa_status s) {
+    switch (s) {
+        case LISA_SUCCESS: return "success";
+        case LISA_ERR_NULL: return "a required pointer is NULL";
+        case LISA_ERR_VALUE: return "a scalar argument is out of range";
+        case LISA_ERR_SHAPE: return "sizes disagree with the dataset object";
+        case LISA_ERR_DATA: return "input table has non-finite, non-positive or unordered entries";
+        case LISA_ERR_CUDA: return "a CUDA runtime call or kernel launch failed";
+        case LISA_ERR_ALLOC: return "device or host allocation failed";
+        case LISA_ERR_WORKSPACE: return "workspace or spline buffer too small or misaligned";
+        case LISA_ERR_TIMEOUT: return "a bounded device-side wait gave up";
+    }
+    return "unknown lisa_status";
+}
+
+lisa_status lisa_data_create(const lisa_data_desc* desc, lisa_stream_t stream, lisa_data** out) {
+    if (!desc || !out) return LISA_ERR_NULL;
+    *out = nullptr;
+    const lisa_data_desc& q = *desc;
+    if (q.n_datasets < 1 || (q.n_channels != 2 && q.n_channels != 3) || q.sgwb_model < 0 ||
+        q.sgwb_model > 2 || q.tdi_form < 0 || q.tdi_form > 1)
+        return LISA_ERR_VALUE;
+    if (!q.bin_offset || !q.state_offset || !q.freq || !q.nu || !q.periodogram || !q.x_lo ||
+        !q.x_hi || !q.f_ref || (q.sgwb_model != 0 && !q.response))
+        return LISA_ERR_NULL;
+    const int D = q.n_datasets;
+    if (q.bin_offset[0] != 0 || q.state_offset[0] != 0) return LISA_ERR_SHAPE;
+    for (int k = 0; k < D; ++k)
+        if (q.bin_offset[k + 1] < q.bin_offset[k] || q.state_offset[k + 1] < q.state_offset[k])
+            return LISA_ERR_SHAPE;
+    const int64_t N = q.bin_offset[D], S = q.state_offset[D];
+    if (N < 1 || S > (int64_t)INT32_MAX) return LISA_ERR_SHAPE;
+    const int C = q.n_channels;
+    // data validation on the host
+    for (int k = 0; k < D; ++k) {
+        if (!std::isfinite(q.x_lo[k]) || !std::isfinite(q.x_hi[k]) || !(q.x_lo[k] < q.x_hi[k]) ||
+            !(q.f_ref[k] > 0.0) || !std::isfinite(q.f_ref[k]))
+            return LISA_ERR_DATA;
+        for (int64_t i = q.bin_offset[k]; i < q.bin_offset[k + 1]; ++i) {
+            if (!(q.freq[i] > 0.0) || !std::isfinite(q.freq[i])) return LISA_ERR_DATA;
+            if (i > q.bin_offset[k] && !(q.freq[i] > q.freq[i - 1])) return LISA_ERR_DATA;
+        }
+    }
+    for (int64_t i = 0; i < N; ++i)
+        if (!(q.nu[i] >= 0.0) || !std::isfinite(q.nu[i])) return LISA_ERR_DATA;
+    for (int64_t i = 0; i < (int64_t)C * N; ++i) {
+        if (!(q.periodogram[i] > 0.0) || !std::isfinite(q.periodogram[i])) return LISA_ERR_DATA;
+        if (q.sgwb_model != 0 && (!(q.response[i] >= 0.0) || !std::isfinite(q.response[i])))
+            return LISA_ERR_DATA;
+    }
+
+    lisa_data* d = new (std::nothrow) lisa_data();
+    if (!d) return LISA_ERR_ALLOC;
+    cudaGetDevice(&d->device);
+    cudaDeviceGetAttribute(&d->n_sm, cudaDevAttrMultiProcessorCount, d->device);
+    d->n_datasets = D;
+    d->C = C;
+    d->sgwb_model = q.sgwb_model;
+    d->tdi_form = q.tdi_form;
+    d->nsp = C + (q.sgwb_model != 0 ? 1 : 0);
+    d->n_bins = N;
+    d->n_states = S;
+    d->h_bin_off.assign(q.bin_offset, q.bin_offset + D + 1);
+    d->h_state_off.assign(q.state_offset, q.state_offset + D + 1);
+    d->h_ds.resize(D);
+    std::vector<int32_t> state_ds((size_t)S);
+    int64_t psd_base = 0;
+    for (int k = 0; k < D; ++k) {
+        DatasetDev& X = d->h_ds[k];
+        X.bin0 = q.bin_offset[k];
+        X.nbins = q.bin_offset[k + 1] - q.bin_offset[k];
+        X.s0 = (int32_t)q.state_offset[k];
+        X.ns = (int32_t)(q.state_offset[k + 1] - q.state_offset[k]);
+        X.x_lo = q.x_lo[k];
+        X.x_hi = q.x_hi[k];
+        X.xb_min = X.nbins ? std::log10(q.freq[X.bin0]) : 0.0;
+        X.xb_max = X.nbins ? std::log10(q.freq[X.bin0 + X.nbins - 1]) : 0.0;
+        X.f_ref = q.f_ref[k];
+        X.ntiles = 0;
+        X.pbase = 0;
+        X.psd_base = psd_base;
+        psd_base += (int64_t)C * X.ns * X.nbins;
+        X.K = 0.0;
+        X.Cnu = 0.0;
+        X.pad = 0;
+        for (int32_t s = X.s0; s < X.s0 + X.ns; ++s) state_ds[s] = k;
+    }
+    d->tiling = lisa_tiling{1024, 256, 4, 0};
+
+    lisa_status st = LISA_SUCCESS;
+    double *f = nullptr, *nu = nullptr, *R = nullptr, *lnP = nullptr;
+    auto fail = [&](lisa_status e) {
+        cudaFree(f);
+        cudaFree(nu);
+        cudaFree(R);
+        cudaFree(lnP);
+        release(d);
+        delete d;
+        return e;
+    };
+    if ((st = dev_alloc(&d->d_ds, D)) || (st = dev_alloc(&d->d_state_ds, (size_t)S)) ||
+        (st = dev_alloc(&d->d_rec32, (size_t)N * kRec)) || (st = dev_alloc(&d->d_rec64, (size_t)N * kRec)) ||
+        (st = dev_alloc(&d->d_P, (size_t)C * N)) || (st = dev_alloc(&d->d_xlo32, (size_t)N)) ||
+        (st = dev_alloc(&d->d_elllo32, (size_t)N)) ||
+        (st = dev_alloc(&f, (size_t)N)) ||
+        (st = dev_alloc(&nu, (size_t)N)) || (st = dev_alloc(&lnP, (size_t)N)) ||
+        (st = dev_alloc(&R, (size_t)C * N)))
+        return fail(st);
+    cudaStream_t sm = (cudaStream_t)stream;
+    bool ok = cudaMemcpyAsync(d->d_ds, d->h_ds.data(), D * sizeof(DatasetDev), cudaMemcpyHostToDevice, sm) == cudaSuccess &&
+              cudaMemcpyAsync(d->d_state_ds, state_ds.data(), S * sizeof(int32_t), cudaMemcpyHostToDevice, sm) == cudaSuccess &&
+              cudaMemcpyAsync(f, q.freq, N * sizeof(double), cudaMemcpyHostToDevice, sm) == cudaSuccess &&
+              cudaMemcpyAsync(nu, q.nu, N * sizeof(double), cudaMemcpyHostToDevice, sm) == cudaSuccess &&
+              cudaMemcpyAsync(d->d_P, q.periodogram, C * N * sizeof(double), cudaMemcpyHostToDevice, sm) == cudaSuccess &&
+              (q.sgwb_model == 0 || cudaMemcpyAsync(R, q.response, C * N * sizeof(double), cudaMemcpyHostToDevice, sm) == cudaSuccess);
+    if (!ok) return fail(LISA_ERR_CUDA);
+    unsigned blocks = (unsigned)((N + 255) / 256);
+    prep_kernel<<<blocks, 256, 0, sm>>>(N, C, q.tdi_form, q.sgwb_model != 0, f, nu, d->d_P, R, d->d_ds, D,
+                                        d->d_rec64, d->d_rec32, d->d_xlo32, d->d_elllo32, lnP);
+    dataset_sums_kernel<<<D, 256, 0, sm>>>(lnP, nu, d->d_ds, C);
+    if (cudaGetLastError() != cudaSuccess) return fail(LISA_ERR_CUDA);
+    if (cudaMemcpyAsync(d->h_ds.data(), d->d_ds, D * sizeof(DatasetDev), cudaMemcpyDeviceToHost, sm) != cudaSuccess ||
+        cudaStreamSynchronize(sm) != cudaSuccess)
+        return fail(LISA_ERR_CUDA);
+    cudaFree(f);
+    cudaFree(nu);
+    cudaFree(R);
+    cudaFree(lnP);
+    f = nu = R = lnP = nullptr;
+    if ((st = rebuild_work(d))) return fail(st);
+    *out = d;
+    return LISA_SUCCESS;
+}
+
+lisa_status lisa_data_destroy(lisa_data* d) {
+    if (!d) return LISA_ERR_NULL;
+    release(d);
+    delete d;
+    return LISA_SUCCESS;
+}
+
+lisa_status lisa_data_get_info(const lisa_data* d, lisa_data_info* info) {
+    if (!d || !info) return LISA_ERR_NULL;
+    info->n_bins = d->n_bins;
+    info->n_states = d->n_states;
+    info->n_datasets = d->n_datasets;
+    info->n_channels = d->C;
+    info->n_splines = d->nsp;
+    info->sgwb_model = d->sgwb_model;
+    info->n_items = d->n_items;
+    info->n_sm = d->n_sm;
+    info->tiling = d->tiling;
+    return LISA_SUCCESS;
+}
+
+lisa_status lisa_data_set_tiling(lisa_data* d, const lisa_tiling* t) {
+    if (!d || !t) return LISA_ERR_NULL;
+    int sc = t->states_per_cta;
+    bool pow2 = sc > 0 && (sc & (sc - 1)) == 0;
+    if (t->tile_bins < 64 || t->tile_bins > kMaxTileBins || (t->tile_bins % 32) != 0 || !pow2 || sc < 16 ||
+        sc > kThreads || !(t->group == 1 || t->group == 2 || t->group == 4 || t->group == 8) ||
+        t->ctas_per_sm < 0 || t->ctas_per_sm > 32)
+        return LISA_ERR_VALUE;
+    lisa_tiling old = d->tiling;
+    d->tiling = *t;
+    lisa_status st = rebuild_work(d);
+    if (st) {
+        d->tiling = old;
+        rebuild_work(d);
+    }
+    return st;
+}
+
+size_t lisa_spline_buf_bytes(const lisa_data* d, int32_t kmax, lisa_precision p) {
+    if (!d || kmax < 0 || kmax > LISA_MAX_KNOTS) return 0;
+    (void)p;
+    return spline_layout(d->n_states, d->nsp, kmax).bytes;
+}
+
+}  // extern "C"

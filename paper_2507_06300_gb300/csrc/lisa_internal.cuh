@@ -1,0 +1,123 @@
+// Internal declarations shared by the library's translation units (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <vector>
+
+#include "lisa_psd.h"
+
+namespace lisa {
+
+constexpr double kPi = 3.141592653589793238462643;
+constexpr double kArm = 2.5e9;                            // arm length L, m (Sec. II.A)
+constexpr double kClight = 299792458.0;                   // m/s
+constexpr double kH0h = 1.0e5 / 3.0856775814913673e22;   // 100 km/s/Mpc in 1/s
+constexpr double kLog2_10 = 3.321928094887362347870319;
+constexpr double kLn10 = 2.302585092994045684017991;
+constexpr double kLn2 = 0.693147180559945309417232;
+
+constexpr int kRec = 12;         // per-bin record: x, ell, nu, Goms[3], Gtm[3], Gh[3]
+constexpr int kThreads = 256;    // threads of the fused likelihood kernels
+// Per-interval records, 64 bytes in both precisions:
+//   FP64: xl, xr, a, b, c, d, 0, 0 (coefficients about xl, log10 units)
+//   FP32: [0] xr  [1] xo  [2..5] c0..c3  [6] xl  [7] conditioning T      (first 32 bytes)
+//         [8] xo_lo  [9..12] c0..c3 low parts  [13..15] 0                (second 32 bytes)
+//         coefficients about the interval midpoint xo, scaled to log2 units; hi + lo is the
+//         FP64 value split into two floats.
+constexpr int kSplineRec = 8;    // doubles per FP64 record
+constexpr int kSplineRec32 = 16; // floats per FP32 record
+// States whose FP32 perturbation spline has an interval with conditioning
+// T = |c0| + |c1| r + |c2| r^2 + |c3| r^3 (log2 units, r = largest |x - xo| of its bins) above
+// this bound are evaluated by the compensated (float-float, log-domain) kernel.
+constexpr double kRobustT = 32.0;
+constexpr int kRouted = 1 << 16;        // internal status bit: state routed to the compensated kernel
+constexpr int kUserBits = 0xffff;       // LISA_STATE_* bits
+constexpr int kStatusNonfinite = LISA_STATE_NONFINITE;
+constexpr unsigned kWaitLimit = 1u << 20;   // bounded spin on an mbarrier (then give up)
+constexpr int kMaxTileBins = 2048;          // 2 staged tiles x 48 B/bin must fit in 227 KB
+
+// One unit of work of the fused kernels: a tile of bins of one dataset and a chunk of its
+// states.  Threads map to (state lane, bin sub-range): lane = tid % sc, range = tid / sc.
+struct WorkItem {
+    int64_t bin0;   // first bin (global index)
+    int32_t nb;     // bins in the tile
+    int32_t s0;     // first state (global index)
+    int32_t ns;     // states in the chunk (<= sc)
+    int32_t sc;     // state lanes of this dataset's items (power of two, divides kThreads)
+    int32_t tile;   // tile index within the dataset
+    int32_t ds;     // dataset index
+};
+static_assert(sizeof(WorkItem) == 32, "WorkItem layout");
+
+struct DatasetDev {
+    int64_t bin0, nbins;     // bin range
+    int64_t pbase;           // first partial slot of the dataset's states
+    int64_t psd_base;        // first element of the dataset's states in a model-PSD output
+    int32_t s0, ns;          // state range
+    int32_t ntiles;          // tiles of tile_bins bins
+    int32_t pad;
+    double x_lo, x_hi;       // edge knot positions
+    double xb_min, xb_max;   // log10 f of the first and last bin
+    double f_ref;
+    double K;                // -sum_i nu_i sum_c ln P_c,i
+    double Cnu;              // C * sum_i nu_i
+};
+
+}  // namespace lisa
+
+struct lisa_data {
+    int device = 0;
+    int n_sm = 0;
+    int32_t n_datasets = 0, C = 0, nsp = 0, sgwb_model = 0, tdi_form = 0;
+    int64_t n_bins = 0, n_states = 0;
+    std::vector<int64_t> h_bin_off, h_state_off;
+    std::vector<lisa::DatasetDev> h_ds;
+    lisa::DatasetDev* d_ds = nullptr;
+    int32_t* d_state_ds = nullptr;   // [n_states] dataset of each state
+    float* d_rec32 = nullptr;        // [n_bins][kRec]
+    double* d_rec64 = nullptr;       // [n_bins][kRec]
+    double* d_P = nullptr;           // [C][n_bins] periodogram (normaliser of the tables)
+    float* d_xlo32 = nullptr;        // [n_bins] log10 f - (float)log10 f (low part of x)
+    float* d_elllo32 = nullptr;      // [n_bins] low part of ell = log2(f / f_ref)
+    lisa_tiling tiling{};
+    lisa::WorkItem* d_items = nullptr;
+    int64_t n_items = 0;
+    int64_t n_partials = 0;          // sum over datasets of states x tiles
+};
+
+namespace lisa {
+
+// Spline buffer layout (64-byte records in both precisions):
+//   int32 status[S] | int32 nint[S*nsp] | int32 route_count, route_list[S] | rec[S][nsp][kmax+1]
+// each region starting on a 256-byte boundary.  route_list holds, in no particular order, the
+// states the FP32 path sends to the compensated kernel (unused in FP64 mode).
+inline size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
+struct SplineLayout {
+    size_t off_status, off_nint, off_route, off_rec, bytes;
+};
+constexpr size_t kRecBytes = 64;
+inline SplineLayout spline_layout(int64_t S, int nsp, int kmax) {
+    SplineLayout L;
+    L.off_status = 0;
+    L.off_nint = align256(sizeof(int32_t) * (size_t)S);
+    L.off_route = L.off_nint + align256(sizeof(int32_t) * (size_t)S * nsp);
+    L.off_rec = L.off_route + align256(sizeof(int32_t) * ((size_t)S + 1));
+    L.bytes = L.off_rec + (size_t)S * nsp * (kmax + 1) * kRecBytes;
+    return L;
+}
+
+// Workspace layout of the forward entry point:
+//   int32 err flag (256 B) | double partial[n_partials]
+inline size_t ws_fwd_bytes(const lisa_data* d) {
+    return 256 + align256(sizeof(double) * (size_t)d->n_partials);
+}
+
+// Extra workspace of the adjoint entry point (after the forward region).
+size_t grad_extra_bytes(const lisa_data* d, int kmax);
+
+lisa_status rebuild_work(lisa_data* d);
+lisa_status check_cuda(cudaError_t e);
+
+}  // namespace lisa

@@ -1,0 +1,749 @@
+// Fused likelihood kernels: spline evaluation -> PSD assembly (Eq. splines) -> per-bin
+// Wishart terms -> FP64 reduction over bins (Sec. III.D), for every state at once.
+//
+// FP32 path: the bin records of a work item (a tile of bins of one dataset) are staged into
+// shared memory with one bulk asynchronous copy (cp.async.bulk + mbarrier), double-buffered
+// across the persistent grid's items, and read by all state lanes of the CTA (broadcast).
+// Each thread owns one state and a contiguous run of bins; it keeps the current interval of
+// each spline in registers and advances it only when a bin passes the interval's right knot
+// (bins are sorted in frequency, so the check is done once per group of bins).
+//
+// Per bin and state (normalised by the periodogram, so P-hat = 1, S-hat ~ 1):
+//   E_c = 2^{P'_n,c(x)},  E_h = A 2^{P'_h(x) + n ell}                  (P' = log2(10) P)
+// with each spline interval's cubic expanded about its midpoint (|x - xo| <= h/2 within the
+// knots), which keeps the FP32 Horner sums small.
+//   S_c = (a_oms^2 G_oms,c + a_tm^2 G_tm,c) E_c + E_h G_h,c
+//   term = nu [ sum_c 1/S_c + ln prod_c S_c - C ]
+// The reciprocal sum and the log are fused: sum_c 1/S_c = (sum_c prod_{c' != c} S_c') / prod S
+// and ln prod S = ln2 lg2(prod S): one MUFU rcp and one MUFU lg2 per state-bin, with a
+// per-channel fallback when the product leaves a safe FP32 range.  Terms are summed in FP32 over
+// runs of 32 bins and then in FP64; the constant -C sum nu - sum nu ln P is added in FP64 at the
+// end.
+//
+// States whose spline intervals are too ill-conditioned for FP32 (setup flags them: large
+// overshoots between close knots, |P| up to tens of decades for prior draws) are skipped here
+// and evaluated by the compensated kernel: float-float Horner sums and the per-bin term in the
+// log domain, so any exponent range is handled.
+#include <cmath>
+
+#include "lisa_internal.cuh"
+
+namespace lisa {
+namespace {
+
+__device__ __forceinline__ float ex2_approx(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float lg2_approx(float x) {
+    float y;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float rcp_approx(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__device__ __forceinline__ unsigned smem_addr(const void* p) {
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_fence_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ void fence_proxy_async() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+// One bulk global->shared copy completing on `bar` (16-byte aligned, size multiple of 16).
+__device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+// Bounded wait: gives up after kWaitLimit polls and raises the error flag.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity, int* err) {
+    for (unsigned it = 0; it < kWaitLimit; ++it)
+        if (mbar_try_wait(bar, parity)) return true;
+    atomicExch(err, 1);
+    return false;
+}
+
+// Interval of a spline containing x: the largest j in [0, n) with xl_j <= x (j = 0 below the
+// first knot; the last interval's right bound is +inf).
+template <class T, int kStride, int kXlOff>
+__device__ __forceinline__ int find_interval(const T* rec, int n, T x) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(rec + (size_t)mid * kStride + kXlOff) <= x) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+struct Iv32 {
+    float xr, xo, c0, c1, c2, c3;
+    const float* base;
+    int j, last;   // current interval, last interval index
+};
+
+__device__ __forceinline__ void load_iv(Iv32& v) {
+    const float4 A = __ldg(reinterpret_cast<const float4*>(v.base + (size_t)v.j * kSplineRec32));
+    const float4 B = __ldg(reinterpret_cast<const float4*>(v.base + (size_t)v.j * kSplineRec32 + 4));
+    v.xr = A.x;
+    v.xo = A.y;
+    v.c0 = A.z;
+    v.c1 = A.w;
+    v.c2 = B.x;
+    v.c3 = B.y;
+}
+
+template <int C, bool HAS_H, bool BROKEN>
+__device__ __forceinline__ float bin_term32(const float4* __restrict__ s4, int i, const Iv32* iv, float ao2,
+                                            float at2, float n1, float n2, float Af) {
+    constexpr int NSP = C + (HAS_H ? 1 : 0);
+    const float4 q0 = s4[3 * i], q1 = s4[3 * i + 1], q2 = s4[3 * i + 2];
+    const float x = q0.x, ell = q0.y, nu = q0.z;
+    const float go[3] = {q0.w, q1.x, q1.y};
+    const float gt[3] = {q1.z, q1.w, q2.x};
+    const float gh[3] = {q2.y, q2.z, q2.w};
+    float p[NSP];
+#pragma unroll
+    for (int a = 0; a < NSP; ++a) {
+        const float t = x - iv[a].xo;
+        p[a] = fmaf(fmaf(fmaf(iv[a].c3, t, iv[a].c2), t, iv[a].c1), t, iv[a].c0);
+    }
+    float eh = 0.f;
+    if (HAS_H) {
+        const float sl = BROKEN ? (ell < 0.f ? n1 : n2) : n1;
+        eh = Af * ex2_approx(fmaf(sl, ell, p[C]));
+    }
+    float S[C];
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+        const float nc = fmaf(ao2, go[c], at2 * gt[c]);
+        const float e = ex2_approx(p[c]);
+        S[c] = HAS_H ? fmaf(e, nc, eh * gh[c]) : e * nc;
+    }
+    float prod, num;
+    if (C == 3) {
+        const float p01 = S[0] * S[1];
+        prod = p01 * S[2];
+        num = fmaf(S[2], S[0] + S[1], p01);
+    } else {
+        prod = S[0] * S[1];
+        num = S[0] + S[1];
+    }
+    float v, lg;
+    if (prod > 1e-30f && prod < 1e30f && num < 1e30f) {
+        v = fmaf(num, rcp_approx(prod), -(float)C);
+        lg = lg2_approx(prod);
+    } else {
+        v = -(float)C;
+        lg = 0.f;
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+            v += rcp_approx(S[c]);
+            lg += lg2_approx(S[c]);
+        }
+    }
+    return nu * fmaf((float)kLn2, lg, v);
+}
+
+template <int C, bool HAS_H, bool BROKEN, int G>
+__global__ void __launch_bounds__(kThreads, 2)
+    loglike_fp32_kernel(const WorkItem* __restrict__ items, int n_items, const float* __restrict__ rec32,
+                        const double* __restrict__ theta, const int32_t* __restrict__ sstat,
+                        const int32_t* __restrict__ nint, const float* __restrict__ srec, int kmax, int nsp,
+                        const DatasetDev* __restrict__ ds, double* __restrict__ partial, int* __restrict__ err,
+                        int tile_bins) {
+    constexpr int NSP = C + (HAS_H ? 1 : 0);
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ __align__(8) uint64_t bars[2];
+    __shared__ double red[kThreads];
+    float* sbuf0 = reinterpret_cast<float*>(smem);
+    float* sbuf1 = reinterpret_cast<float*>(smem + (size_t)tile_bins * kRec * sizeof(float));
+    const int tid = threadIdx.x;
+    if (tid == 0) {
+        mbar_init(&bars[0], 1);
+        mbar_init(&bars[1], 1);
+        mbar_fence_init();
+    }
+    __syncthreads();
+    unsigned phase0 = 0, phase1 = 0;
+    int it = blockIdx.x;
+    if (it < n_items && tid == 0) {
+        const WorkItem w = items[it];
+        const unsigned bytes = (unsigned)w.nb * kRec * sizeof(float);
+        mbar_expect_tx(&bars[0], bytes);
+        bulk_copy_g2s(sbuf0, rec32 + w.bin0 * kRec, bytes, &bars[0]);
+    }
+    for (int k = 0; it < n_items; it += gridDim.x, ++k) {
+        const int b = k & 1;
+        const int nxt = it + gridDim.x;
+        if (nxt < n_items && tid == 0) {
+            const WorkItem w = items[nxt];
+            const unsigned bytes = (unsigned)w.nb * kRec * sizeof(float);
+            fence_proxy_async();
+            mbar_expect_tx(&bars[b ^ 1], bytes);
+            bulk_copy_g2s(b ? sbuf0 : sbuf1, rec32 + w.bin0 * kRec, bytes, &bars[b ^ 1]);
+        }
+        const WorkItem w = items[it];
+        if (b == 0) {
+            mbar_wait_bounded(&bars[0], phase0, err);
+            phase0 ^= 1;
+        } else {
+            mbar_wait_bounded(&bars[1], phase1, err);
+            phase1 ^= 1;
+        }
+        const float4* s4 = reinterpret_cast<const float4*>(b ? sbuf1 : sbuf0);
+
+        const int sc = w.sc;
+        const int R = kThreads / sc;
+        const int ls = tid & (sc - 1);
+        const int r = tid / sc;
+        const int s = w.s0 + ls;
+        const bool active = ls < w.ns && sstat[s] == 0;   // invalid and routed states skip
+        double acc64 = 0.0;
+        if (active) {
+            const int lo = (r * w.nb) / R, hi = ((r + 1) * w.nb) / R;
+            if (lo < hi) {
+                const double* th = theta + (size_t)s * LISA_N_THETA;
+                const float ao2 = (float)(th[0] * th[0]);
+                const float at2 = (float)(th[1] * th[1]);
+                const float Af = HAS_H ? (float)exp10(th[2]) : 0.f;
+                const float n1 = (float)th[3];
+                const float n2 = BROKEN ? (float)th[4] : n1;
+                Iv32 iv[NSP];
+                const float x0 = reinterpret_cast<const float*>(s4)[lo * kRec];
+#pragma unroll
+                for (int a = 0; a < NSP; ++a) {
+                    const int64_t sp = (int64_t)s * nsp + a;
+                    iv[a].base = srec + sp * (int64_t)(kmax + 1) * kSplineRec32;
+                    iv[a].last = nint[sp] - 1;
+                    iv[a].j = find_interval<float, kSplineRec32, 6>(iv[a].base, nint[sp], x0);
+                    load_iv(iv[a]);
+                }
+                const float* sx = reinterpret_cast<const float*>(s4);
+                int i = lo;
+                while (i < hi) {
+                    const int cend = min(i + 32, hi);
+                    float acc32 = 0.f;
+                    for (; i + G <= cend; i += G) {
+                        const float xg = sx[(i + G - 1) * kRec];
+                        bool fast = true;
+#pragma unroll
+                        for (int a = 0; a < NSP; ++a) fast &= xg < iv[a].xr;
+                        if (fast) {
+#pragma unroll
+                            for (int g = 0; g < G; ++g)
+                                acc32 += bin_term32<C, HAS_H, BROKEN>(s4, i + g, iv, ao2, at2, n1, n2, Af);
+                        } else {
+#pragma unroll 1
+                            for (int g = 0; g < G; ++g) {
+                                const float x = sx[(i + g) * kRec];
+#pragma unroll
+                                for (int a = 0; a < NSP; ++a) {
+                                    while (x >= iv[a].xr && iv[a].j < iv[a].last) {
+                                        ++iv[a].j;
+                                        load_iv(iv[a]);
+                                    }
+                                }
+                                acc32 += bin_term32<C, HAS_H, BROKEN>(s4, i + g, iv, ao2, at2, n1, n2, Af);
+                            }
+                        }
+                    }
+#pragma unroll 1
+                    for (; i < cend; ++i) {
+                        const float x = sx[i * kRec];
+#pragma unroll
+                        for (int a = 0; a < NSP; ++a) {
+                            while (x >= iv[a].xr && iv[a].j < iv[a].last) {
+                                ++iv[a].j;
+                                load_iv(iv[a]);
+                            }
+                        }
+                        acc32 += bin_term32<C, HAS_H, BROKEN>(s4, i, iv, ao2, at2, n1, n2, Af);
+                    }
+                    acc64 += (double)acc32;
+                }
+            }
+        }
+        red[tid] = acc64;
+        __syncthreads();
+        if (r == 0 && ls < w.ns && sstat[s] == 0) {
+            double sum = 0.0;
+            for (int q = 0; q < R; ++q) sum += red[ls + q * sc];
+            const DatasetDev& D = ds[w.ds];
+            partial[D.pbase + (int64_t)(s - D.s0) * D.ntiles + w.tile] = sum;
+        }
+        __syncthreads();  // the buffer read in this iteration is refilled in the next one
+    }
+}
+
+
+// ---- compensated path for states the setup routed away from the FP32 kernel --------------
+// Float-float ("double-float") arithmetic: a value is hi + lo with |lo| <= ulp(hi)/2.
+struct ff {
+    float hi, lo;
+};
+__device__ __forceinline__ ff two_sum(float a, float b) {
+    const float s = a + b;
+    const float bb = s - a;
+    return {s, (a - (s - bb)) + (b - bb)};
+}
+__device__ __forceinline__ ff fast_two_sum(float a, float b) {
+    const float s = a + b;
+    return {s, b - (s - a)};
+}
+__device__ __forceinline__ ff ff_add(ff x, ff y) {
+    const ff s = two_sum(x.hi, y.hi);
+    return fast_two_sum(s.hi, s.lo + x.lo + y.lo);
+}
+__device__ __forceinline__ ff ff_mul(ff x, ff y) {
+    const float p = x.hi * y.hi;
+    float e = fmaf(x.hi, y.hi, -p);
+    e = fmaf(x.hi, y.lo, fmaf(x.lo, y.hi, e));
+    return fast_two_sum(p, e);
+}
+__device__ __forceinline__ ff ff_from_double(double v) {
+    const float hi = (float)v;
+    return {hi, (float)(v - (double)hi)};
+}
+
+struct IvR {
+    float xr;
+    ff xo, c[4];
+    const float* base;
+    int j, last;
+};
+__device__ __forceinline__ void load_ivr(IvR& v) {
+    const float* r = v.base + (size_t)v.j * kSplineRec32;
+    v.xr = __ldg(r + 0);
+    v.xo = {__ldg(r + 1), __ldg(r + 8)};
+    for (int c = 0; c < 4; ++c) v.c[c] = {__ldg(r + 2 + c), __ldg(r + 9 + c)};
+}
+
+// log2 of a positive sum given the log2 of its two parts (either may be -inf).
+__device__ __forceinline__ ff log2_sum(ff a, ff b) {
+    if (!(b.hi > -INFINITY)) return a;
+    if (!(a.hi > -INFINITY)) return b;
+    const ff big = a.hi >= b.hi ? a : b;
+    const float d = fabsf(a.hi - b.hi);
+    const float corr = lg2_approx(1.0f + ex2_approx(-d));
+    return ff_add(big, ff{corr, 0.f});
+}
+
+// ln S + 1/S in FP64 from lS = log2 S held as float-float.
+__device__ __forceinline__ double log_and_inverse(ff lS) {
+    if (!(lS.hi > -1.0e6f)) return INFINITY;           // S underflows every format, or NaN
+    if (!(lS.hi < 1.0e6f)) return (double)lS.hi * kLn2; // S overflows: 1/S = 0
+    const float n = rintf(lS.hi);
+    const float f = (lS.hi - n) + lS.lo;                  // |f| <= 1/2 + ulp
+    const double inv = ldexp((double)ex2_approx(-f), -(int)n);
+    return inv + kLn2 * ((double)lS.hi + (double)lS.lo);
+}
+
+template <int C, bool HAS_H, bool BROKEN>
+__global__ void __launch_bounds__(128)
+    loglike_robust_kernel(const int32_t* __restrict__ route, const int32_t* __restrict__ state_ds,
+                          const DatasetDev* __restrict__ ds, int tile_bins, const float* __restrict__ rec32,
+                          const float* __restrict__ xlo32, const float* __restrict__ elllo32,
+                          const double* __restrict__ theta, const int32_t* __restrict__ nint,
+                          const float* __restrict__ srec, int kmax, int nsp, double* __restrict__ partial) {
+    constexpr int NSP = C + (HAS_H ? 1 : 0);
+    constexpr int NT = 128;
+    __shared__ double red[NT];
+    const int tid = threadIdx.x;
+    const int nr = route[0];
+    for (int r = blockIdx.y; r < nr; r += gridDim.y) {
+        const int s = route[1 + r];
+        const DatasetDev& D = ds[state_ds[s]];
+        const double* th = theta + (size_t)s * LISA_N_THETA;
+        const float ao2 = (float)(th[0] * th[0]);
+        const float at2 = (float)(th[1] * th[1]);
+        const ff lA = ff_from_double(th[2] * kLog2_10);
+        const ff n1 = ff_from_double(th[3]);
+        const ff n2 = BROKEN ? ff_from_double(th[4]) : n1;
+        for (int t = blockIdx.x; t < D.ntiles; t += gridDim.x) {
+            const int64_t b0 = D.bin0 + (int64_t)t * tile_bins;
+            const int nb = (int)min((int64_t)tile_bins, D.bin0 + D.nbins - b0);
+            const int lo = (tid * nb) / NT, hi = ((tid + 1) * nb) / NT;
+            double acc = 0.0;
+            if (lo < hi) {
+                IvR iv[NSP];
+                const float x0 = __ldg(rec32 + (b0 + lo) * kRec);
+#pragma unroll
+                for (int a = 0; a < NSP; ++a) {
+                    const int64_t sp = (int64_t)s * nsp + a;
+                    iv[a].base = srec + sp * (int64_t)(kmax + 1) * kSplineRec32;
+                    iv[a].last = nint[sp] - 1;
+                    iv[a].j = find_interval<float, kSplineRec32, 6>(iv[a].base, nint[sp], x0);
+                    load_ivr(iv[a]);
+                }
+                for (int i = lo; i < hi; ++i) {
+                    const int64_t g = b0 + i;
+                    const float* q = rec32 + g * kRec;
+                    const ff x = {__ldg(q), __ldg(xlo32 + g)};
+                    const ff ell = {__ldg(q + 1), __ldg(elllo32 + g)};
+                    const float nu = __ldg(q + 2);
+                    ff P[NSP];
+#pragma unroll
+                    for (int a = 0; a < NSP; ++a) {
+                        while (x.hi >= iv[a].xr && iv[a].j < iv[a].last) {
+                            ++iv[a].j;
+                            load_ivr(iv[a]);
+                        }
+                        const ff tt = ff_add(x, ff{-iv[a].xo.hi, -iv[a].xo.lo});
+                        ff p = iv[a].c[3];
+                        p = ff_add(ff_mul(p, tt), iv[a].c[2]);
+                        p = ff_add(ff_mul(p, tt), iv[a].c[1]);
+                        p = ff_add(ff_mul(p, tt), iv[a].c[0]);
+                        P[a] = p;
+                    }
+                    ff lEh = {-INFINITY, 0.f};
+                    if (HAS_H) {
+                        const ff sl = BROKEN ? (ell.hi < 0.f ? n1 : n2) : n1;
+                        lEh = ff_add(ff_add(P[C], ff_mul(sl, ell)), lA);
+                    }
+                    double term = 0.0;
+#pragma unroll
+                    for (int c = 0; c < C; ++c) {
+                        const float N = fmaf(ao2, __ldg(q + 3 + c), at2 * __ldg(q + 6 + c));
+                        const float lN = lg2_approx(N);
+                        const ff lNE = (lN > -INFINITY && lN < INFINITY) ? ff_add(P[c], ff{lN, 0.f}) : ff{lN, 0.f};
+                        ff lS = lNE;
+                        if (HAS_H) {
+                            const float lG = lg2_approx(__ldg(q + 9 + c));
+                            const ff lH = (lG > -INFINITY && lG < INFINITY) ? ff_add(lEh, ff{lG, 0.f}) : ff{lG, 0.f};
+                            lS = log2_sum(lNE, lH);
+                        }
+                        term += log_and_inverse(lS);
+                    }
+                    acc += (double)nu * (term - (double)C);
+                }
+            }
+            red[tid] = acc;
+            __syncthreads();
+            for (int w = NT / 2; w > 0; w >>= 1) {
+                if (tid < w) red[tid] += red[tid + w];
+                __syncthreads();
+            }
+            if (tid == 0) partial[D.pbase + (int64_t)(s - D.s0) * D.ntiles + t] = red[0];
+            __syncthreads();
+        }
+    }
+}
+
+// ---- plain FP64 path: the same decomposition, FP64 throughout, library exp10 / exp2 / log ----
+
+template <int C, bool HAS_H, bool BROKEN>
+__global__ void __launch_bounds__(kThreads)
+    loglike_fp64_kernel(const WorkItem* __restrict__ items, int n_items, const double* __restrict__ rec64,
+                        const double* __restrict__ theta, const int32_t* __restrict__ sstat,
+                        const int32_t* __restrict__ nint, const double* __restrict__ srec, int kmax, int nsp,
+                        const DatasetDev* __restrict__ ds, double* __restrict__ partial) {
+    constexpr int NSP = C + (HAS_H ? 1 : 0);
+    __shared__ double red[kThreads];
+    const int tid = threadIdx.x;
+    for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+        const WorkItem w = items[it];
+        const int sc = w.sc;
+        const int R = kThreads / sc;
+        const int ls = tid & (sc - 1);
+        const int r = tid / sc;
+        const int s = w.s0 + ls;
+        const bool active = ls < w.ns && sstat[s] == 0;
+        double acc = 0.0;
+        if (active) {
+            const int lo = (r * w.nb) / R, hi = ((r + 1) * w.nb) / R;
+            if (lo < hi) {
+                const double* th = theta + (size_t)s * LISA_N_THETA;
+                const double ao2 = th[0] * th[0], at2 = th[1] * th[1], lA = th[2], n1 = th[3];
+                const double n2 = BROKEN ? th[4] : n1;
+                const double* base[NSP];
+                int j[NSP], last[NSP];
+                double xl[NSP], xr[NSP], ca[NSP], cb[NSP], cc[NSP], cd[NSP];
+                const double* rb = rec64 + (w.bin0 + lo) * kRec;
+                for (int a = 0; a < NSP; ++a) {
+                    const int64_t sp = (int64_t)s * nsp + a;
+                    base[a] = srec + sp * (int64_t)(kmax + 1) * kSplineRec;
+                    last[a] = nint[sp] - 1;
+                    j[a] = find_interval<double, kSplineRec, 0>(base[a], nint[sp], __ldg(rb));
+                    const double* q = base[a] + (size_t)j[a] * kSplineRec;
+                    xl[a] = q[0]; xr[a] = q[1]; ca[a] = q[2]; cb[a] = q[3]; cc[a] = q[4]; cd[a] = q[5];
+                }
+                for (int i = lo; i < hi; ++i) {
+                    const double* q = rec64 + (w.bin0 + i) * kRec;
+                    const double x = __ldg(q), ell = __ldg(q + 1), nu = __ldg(q + 2);
+                    double P[NSP];
+                    for (int a = 0; a < NSP; ++a) {
+                        while (x >= xr[a] && j[a] < last[a]) {
+                            ++j[a];
+                            const double* z = base[a] + (size_t)j[a] * kSplineRec;
+                            xl[a] = z[0]; xr[a] = z[1]; ca[a] = z[2]; cb[a] = z[3]; cc[a] = z[4]; cd[a] = z[5];
+                        }
+                        const double t = x - xl[a];
+                        P[a] = ca[a] + t * (cb[a] + t * (cc[a] + t * cd[a]));
+                    }
+                    double eh = 0.0;
+                    if (HAS_H) {
+                        const double sl = BROKEN ? (ell < 0.0 ? n1 : n2) : n1;
+                        eh = exp10(lA + P[C]) * exp2(sl * ell);
+                    }
+                    double term = 0.0;
+                    for (int c = 0; c < C; ++c) {
+                        const double Sc = (ao2 * __ldg(q + 3 + c) + at2 * __ldg(q + 6 + c)) * exp10(P[c]) +
+                                          (HAS_H ? eh * __ldg(q + 9 + c) : 0.0);
+                        term += 1.0 / Sc + log(Sc);
+                    }
+                    acc += nu * term;
+                }
+            }
+        }
+        red[tid] = acc;
+        __syncthreads();
+        if (r == 0 && ls < w.ns && sstat[s] == 0) {
+            double sum = 0.0;
+            for (int q = 0; q < R; ++q) sum += red[ls + q * sc];
+            const DatasetDev& D = ds[w.ds];
+            partial[D.pbase + (int64_t)(s - D.s0) * D.ntiles + w.tile] = sum;
+        }
+        __syncthreads();
+    }
+}
+
+// Per state: fixed-order sum of its tiles' partials plus the dataset constants.
+__global__ void finalize_kernel(int S, const int32_t* __restrict__ state_ds, const DatasetDev* __restrict__ ds,
+                                const int32_t* __restrict__ sstat, const double* __restrict__ partial,
+                                const int* __restrict__ err, int fp32, double* __restrict__ out) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= S) return;
+    if (sstat[s] & kUserBits) {
+        out[s] = -INFINITY;
+        return;
+    }
+    const DatasetDev& D = ds[state_ds[s]];
+    const double* p = partial + D.pbase + (int64_t)(s - D.s0) * D.ntiles;
+    double sum = 0.0;
+    for (int t = 0; t < D.ntiles; ++t) sum += p[t];
+    double L = fp32 ? (-sum - D.Cnu + D.K) : (-sum + D.K);
+    if (!isfinite(L)) L = -INFINITY;
+    if (*err) L = NAN;
+    out[s] = L;
+}
+
+// Model PSD in physical units, FP64: one thread per (state, bin).
+template <int C>
+__global__ void model_psd_kernel(const int32_t* __restrict__ state_ds, const DatasetDev* __restrict__ ds,
+                                 const double* __restrict__ rec64, const double* __restrict__ P, int64_t n_bins,
+                                 const double* __restrict__ theta, const int32_t* __restrict__ sstat,
+                                 const int32_t* __restrict__ nint, const double* __restrict__ srec, int kmax,
+                                 int nsp, int has_h, int broken, double* __restrict__ out) {
+    const int s = blockIdx.y;
+    const DatasetDev& D = ds[state_ds[s]];
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= D.nbins) return;
+    double* o = out + D.psd_base + (int64_t)(s - D.s0) * C * D.nbins;
+    if (sstat[s] & kUserBits) {
+        for (int c = 0; c < C; ++c) o[(int64_t)c * D.nbins + i] = NAN;
+        return;
+    }
+    const int64_t g = D.bin0 + i;
+    const double* q = rec64 + g * kRec;
+    const double x = q[0], ell = q[1];
+    const double* th = theta + (size_t)s * LISA_N_THETA;
+    double Pv[4];
+    for (int a = 0; a < nsp; ++a) {
+        const int64_t sp = (int64_t)s * nsp + a;
+        const double* base = srec + sp * (int64_t)(kmax + 1) * kSplineRec;
+        const int j = find_interval<double, kSplineRec, 0>(base, nint[sp], x);
+        const double* z = base + (size_t)j * kSplineRec;
+        const double t = x - z[0];
+        Pv[a] = z[2] + t * (z[3] + t * (z[4] + t * z[5]));
+    }
+    double eh = 0.0;
+    if (has_h) {
+        const double sl = (broken && ell >= 0.0) ? th[4] : th[3];
+        eh = exp10(th[2] + Pv[C]) * exp2(sl * ell);
+    }
+    for (int c = 0; c < C; ++c) {
+        const double Sc = (th[0] * th[0] * q[3 + c] + th[1] * th[1] * q[6 + c]) * exp10(Pv[c]) + eh * q[9 + c];
+        o[(int64_t)c * D.nbins + i] = Sc * P[(int64_t)c * n_bins + g];
+    }
+}
+
+template <class K>
+int grid_for(K kernel, const lisa_data* d, size_t smem) {
+    int per_sm = d->tiling.ctas_per_sm;
+    if (per_sm <= 0) {
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kThreads, smem) != cudaSuccess ||
+            per_sm < 1)
+            per_sm = 1;
+    }
+    int64_t g = (int64_t)d->n_sm * per_sm;
+    if (g > d->n_items) g = d->n_items;
+    return (int)(g < 1 ? 1 : g);
+}
+
+template <int C, bool H, bool B, int G>
+cudaError_t launch_fp32_g(const lisa_data* d, const double* theta, const int32_t* sstat, const int32_t* nint,
+                          const int32_t* route, const float* srec, int kmax, double* partial, int* err,
+                          cudaStream_t sm) {
+    auto kern = loglike_fp32_kernel<C, H, B, G>;
+    const size_t smem = 2 * (size_t)d->tiling.tile_bins * kRec * sizeof(float);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int grid = grid_for(kern, d, smem);
+    kern<<<grid, kThreads, smem, sm>>>(d->d_items, (int)d->n_items, d->d_rec32, theta, sstat, nint, srec, kmax,
+                                       d->nsp, d->d_ds, partial, err, d->tiling.tile_bins);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    // compensated kernel for the routed states (a no-op grid when the route list is empty)
+    int max_tiles = 1;
+    for (const auto& D : d->h_ds) max_tiles = D.ntiles > max_tiles ? D.ntiles : max_tiles;
+    dim3 rgrid((unsigned)(max_tiles < 128 ? max_tiles : 128),
+               (unsigned)(d->n_states < 16 ? d->n_states : 16));
+    loglike_robust_kernel<C, H, B><<<rgrid, 128, 0, sm>>>(route, d->d_state_ds, d->d_ds, d->tiling.tile_bins,
+                                                           d->d_rec32, d->d_xlo32, d->d_elllo32, theta, nint,
+                                                           srec, kmax, d->nsp, partial);
+    return cudaGetLastError();
+}
+
+template <int C, bool H, bool B>
+cudaError_t launch_fp32(const lisa_data* d, const double* theta, const int32_t* sstat, const int32_t* nint,
+                        const int32_t* route, const float* srec, int kmax, double* partial, int* err,
+                        cudaStream_t sm) {
+    switch (d->tiling.group) {
+        case 1: return launch_fp32_g<C, H, B, 1>(d, theta, sstat, nint, route, srec, kmax, partial, err, sm);
+        case 2: return launch_fp32_g<C, H, B, 2>(d, theta, sstat, nint, route, srec, kmax, partial, err, sm);
+        case 8: return launch_fp32_g<C, H, B, 8>(d, theta, sstat, nint, route, srec, kmax, partial, err, sm);
+        default: return launch_fp32_g<C, H, B, 4>(d, theta, sstat, nint, route, srec, kmax, partial, err, sm);
+    }
+}
+
+template <int C, bool H, bool B>
+cudaError_t launch_fp64(const lisa_data* d, const double* theta, const int32_t* sstat, const int32_t* nint,
+                        const double* srec, int kmax, double* partial, cudaStream_t sm) {
+    auto kern = loglike_fp64_kernel<C, H, B>;
+    const int grid = grid_for(kern, d, 0);
+    kern<<<grid, kThreads, 0, sm>>>(d->d_items, (int)d->n_items, d->d_rec64, theta, sstat, nint, srec, kmax,
+                                    d->nsp, d->d_ds, partial);
+    return cudaGetLastError();
+}
+
+template <int C>
+cudaError_t dispatch_model(const lisa_data* d, bool fp32, const double* theta, const int32_t* sstat,
+                           const int32_t* nint, const int32_t* route, const void* srec, int kmax, double* partial,
+                           int* err, cudaStream_t sm) {
+    const int h = d->sgwb_model;
+    if (fp32) {
+        const float* r = static_cast<const float*>(srec);
+        if (h == 0) return launch_fp32<C, false, false>(d, theta, sstat, nint, route, r, kmax, partial, err, sm);
+        if (h == 1) return launch_fp32<C, true, false>(d, theta, sstat, nint, route, r, kmax, partial, err, sm);
+        return launch_fp32<C, true, true>(d, theta, sstat, nint, route, r, kmax, partial, err, sm);
+    }
+    const double* r = static_cast<const double*>(srec);
+    if (h == 0) return launch_fp64<C, false, false>(d, theta, sstat, nint, r, kmax, partial, sm);
+    if (h == 1) return launch_fp64<C, true, false>(d, theta, sstat, nint, r, kmax, partial, sm);
+    return launch_fp64<C, true, true>(d, theta, sstat, nint, r, kmax, partial, sm);
+}
+
+}  // namespace
+}  // namespace lisa
+
+using namespace lisa;
+
+extern "C" {
+
+size_t lisa_workspace_bytes(const lisa_data* d, int32_t kmax, lisa_precision p, int32_t with_grad) {
+    (void)p;
+    if (!d || kmax < 0 || kmax > LISA_MAX_KNOTS) return 0;
+    size_t b = ws_fwd_bytes(d);
+    if (with_grad) b += grad_extra_bytes(d, kmax);
+    return b;
+}
+
+lisa_status lisa_psd_loglike(const lisa_data* d, const lisa_params* params, const void* buf, size_t buf_bytes,
+                             int32_t kmax, double* out, void* ws, size_t ws_bytes, lisa_precision prec,
+                             lisa_stream_t stream) {
+    if (!d || !params || !buf || !out || !ws) return LISA_ERR_NULL;
+    if (prec != LISA_FP32 && prec != LISA_FP64) return LISA_ERR_VALUE;
+    if (kmax < 0 || kmax > LISA_MAX_KNOTS) return LISA_ERR_VALUE;
+    if (params->n_states != d->n_states) return LISA_ERR_SHAPE;
+    if (d->n_states > 0 && !params->theta_dev) return LISA_ERR_NULL;
+    const bool fp32 = prec == LISA_FP32;
+    const SplineLayout L = spline_layout(d->n_states, d->nsp, kmax);
+    if (buf_bytes < L.bytes || (reinterpret_cast<uintptr_t>(buf) & 255)) return LISA_ERR_WORKSPACE;
+    if (ws_bytes < ws_fwd_bytes(d) || (reinterpret_cast<uintptr_t>(ws) & 255)) return LISA_ERR_WORKSPACE;
+    if (d->n_states == 0) return LISA_SUCCESS;
+    cudaStream_t sm = (cudaStream_t)stream;
+    const char* base = static_cast<const char*>(buf);
+    const int32_t* sstat = reinterpret_cast<const int32_t*>(base + L.off_status);
+    const int32_t* nint = reinterpret_cast<const int32_t*>(base + L.off_nint);
+    const int32_t* route = reinterpret_cast<const int32_t*>(base + L.off_route);
+    const void* srec = base + L.off_rec;
+    int* err = static_cast<int*>(ws);
+    double* partial = reinterpret_cast<double*>(static_cast<char*>(ws) + 256);
+    if (cudaMemsetAsync(err, 0, sizeof(int), sm) != cudaSuccess) return LISA_ERR_CUDA;
+    cudaError_t e = cudaSuccess;
+    if (d->n_items > 0)
+        e = d->C == 3 ? dispatch_model<3>(d, fp32, params->theta_dev, sstat, nint, route, srec, kmax, partial, err, sm)
+                      : dispatch_model<2>(d, fp32, params->theta_dev, sstat, nint, route, srec, kmax, partial, err, sm);
+    if (e != cudaSuccess) return LISA_ERR_CUDA;
+    const int S = (int)d->n_states;
+    finalize_kernel<<<(S + 255) / 256, 256, 0, sm>>>(S, d->d_state_ds, d->d_ds, sstat, partial, err, fp32 ? 1 : 0,
+                                                     out);
+    return check_cuda(cudaGetLastError());
+}
+
+lisa_status lisa_model_psd(const lisa_data* d, const lisa_params* params, const void* buf, size_t buf_bytes,
+                           int32_t kmax, double* out, lisa_stream_t stream) {
+    if (!d || !params || !buf || !out) return LISA_ERR_NULL;
+    if (kmax < 0 || kmax > LISA_MAX_KNOTS) return LISA_ERR_VALUE;
+    if (params->n_states != d->n_states) return LISA_ERR_SHAPE;
+    if (d->n_states > 0 && !params->theta_dev) return LISA_ERR_NULL;
+    const SplineLayout L = spline_layout(d->n_states, d->nsp, kmax);
+    if (buf_bytes < L.bytes || (reinterpret_cast<uintptr_t>(buf) & 255)) return LISA_ERR_WORKSPACE;
+    if (d->n_states == 0) return LISA_SUCCESS;
+    if (d->n_states > 65535) return LISA_ERR_VALUE;
+    int64_t maxN = 0;
+    for (const auto& D : d->h_ds) maxN = D.nbins > maxN ? D.nbins : maxN;
+    const char* base = static_cast<const char*>(buf);
+    const int32_t* sstat = reinterpret_cast<const int32_t*>(base + L.off_status);
+    const int32_t* nint = reinterpret_cast<const int32_t*>(base + L.off_nint);
+    const double* srec = reinterpret_cast<const double*>(base + L.off_rec);
+    dim3 grid((unsigned)((maxN + 255) / 256), (unsigned)d->n_states);
+    cudaStream_t sm = (cudaStream_t)stream;
+    const int h = d->sgwb_model != 0, br = d->sgwb_model == 2;
+    if (d->C == 3)
+        model_psd_kernel<3><<<grid, 256, 0, sm>>>(d->d_state_ds, d->d_ds, d->d_rec64, d->d_P, d->n_bins,
+                                                  params->theta_dev, sstat, nint, srec, kmax, d->nsp, h, br, out);
+    else
+        model_psd_kernel<2><<<grid, 256, 0, sm>>>(d->d_state_ds, d->d_ds, d->d_rec64, d->d_P, d->n_bins,
+                                                  params->theta_dev, sstat, nint, srec, kmax, d->nsp, h, br, out);
+    return check_cuda(cudaGetLastError());
+}
+
+}  // extern "C"

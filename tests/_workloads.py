@@ -26,3 +26,53 @@ def oracle_dataset(wl, d=0):
     assert st[0] == 0
     ds["P"] = S[0] * wl.gamma[:, b0:b1]
     return ds
+
+
+def gpu_eval(wl, P, precision, kind=None, tiling=None, theta=None, knots=None):
+    """Runs spline setup + log-likelihood through the C ABI; returns (logL, status) as numpy."""
+    import torch
+    from paper_2507_06300_gb300 import binding as B
+    ds = B.Dataset.from_workload(wl, P)
+    if tiling:
+        ds.set_tiling(**tiling)
+    kn = wl.knots if knots is None else knots
+    th = wl.theta if theta is None else theta
+    count, x, w, kmax, kd = B.knots_to_device(kn)
+    if kind is not None:
+        kd = kind
+    theta_d = torch.as_tensor(np.ascontiguousarray(th), device="cuda")
+    buf, st = ds.spline_setup(count, x, w, kmax, kd, precision)
+    out = ds.psd_loglike(theta_d, buf, kmax, precision)
+    torch.cuda.synchronize()
+    res = out.cpu().numpy(), st.cpu().numpy()
+    ds.close()
+    return res
+
+
+def oracle_batched(wl):
+    """Per-dataset oracle periodograms [C, N_total] and log-likelihoods [S_total]."""
+    P = np.empty((wl.n_channels, wl.n_bins))
+    L = np.empty(wl.n_states)
+    St = np.empty(wl.n_states, np.int32)
+    for d in range(wl.n_datasets):
+        ds = oracle_dataset(wl, d)
+        b0, b1 = int(wl.bin_offset[d]), int(wl.bin_offset[d + 1])
+        P[:, b0:b1] = ds["P"]
+        th, kn = wl.states(d)
+        s0, s1 = int(wl.state_offset[d]), int(wl.state_offset[d + 1])
+        if s1 > s0:
+            L[s0:s1], St[s0:s1] = oracle.loglike(ds, th, kn.as_dict())
+    return P, L, St
+
+
+def fp32_tolerance(L_ref, wl, P):
+    """FP32-bulk bound: 1e-6 of the normalised log-likelihood's scale, max(|log L - K|, C sum nu)
+    with K = -sum nu sum_c ln P (the part of log L that does not depend on the state)."""
+    tol = np.empty_like(L_ref)
+    for d in range(wl.n_datasets):
+        b0, b1 = int(wl.bin_offset[d]), int(wl.bin_offset[d + 1])
+        s0, s1 = int(wl.state_offset[d]), int(wl.state_offset[d + 1])
+        K = -np.sum(wl.nu[b0:b1] * np.log(P[:, b0:b1]).sum(axis=0))
+        scale = wl.n_channels * wl.nu[b0:b1].sum()
+        tol[s0:s1] = 1e-6 * np.maximum(np.abs(L_ref[s0:s1] - K), scale)
+    return tol

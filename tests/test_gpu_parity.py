@@ -1,0 +1,209 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 CPU oracle on the same seeded
+inputs.  FP64 mode: 1e-12 relative on log L.  FP32-bulk mode: 1e-6 of the normalised
+log-likelihood's scale (see tests._workloads.fp32_tolerance), plus the absolute error in nats."""
+import dataclasses
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2507_06300_gb300 import synth
+from tests._workloads import fp32_tolerance, gpu_eval, oracle_batched, oracle_dataset
+
+pytestmark = pytest.mark.gpu
+
+FP32, FP64 = 0, 1
+
+
+def _check(wl, P, L_ref, St_ref, precision, **kw):
+    L, St = gpu_eval(wl, P, precision, **kw)
+    np.testing.assert_array_equal(St, St_ref)
+    ok = St_ref == 0
+    assert np.all(np.isneginf(L[~ok]))
+    if precision == FP64:
+        np.testing.assert_allclose(L[ok], L_ref[ok], rtol=1e-12, atol=0)
+    else:
+        tol = fp32_tolerance(L_ref, wl, P)
+        err = np.abs(L[ok] - L_ref[ok])
+        assert np.all(err <= tol[ok]), (err.max(), (err / tol[ok]).max())
+    return L
+
+
+@pytest.fixture(scope="module")
+def tiny():
+    wl = synth.workload("tiny")
+    P, L, St = oracle_batched(wl)
+    return wl, P, L, St
+
+
+@pytest.mark.parametrize("precision", [FP64, FP32])
+def test_tiny(tiny, precision):
+    wl, P, L, St = tiny
+    _check(wl, P, L, St, precision)
+
+
+@pytest.mark.parametrize("precision", [FP64, FP32])
+@pytest.mark.parametrize("tiling", [
+    dict(tile_bins=64, states_per_cta=16, group=1),
+    dict(tile_bins=96, states_per_cta=32, group=2),
+    dict(tile_bins=160, states_per_cta=256, group=8),
+    dict(tile_bins=1024, states_per_cta=64, group=4, ctas_per_sm=1),
+])
+def test_small_ae_tilings(precision, tiling):
+    wl = synth.workload("small_ae")          # A,E; 2000 bins; 128 states; ragged last tile
+    P, L, St = oracle_batched(wl)
+    _check(wl, P, L, St, precision, tiling=tiling)
+
+
+@pytest.mark.parametrize("precision", [FP64, FP32])
+@pytest.mark.parametrize("variant", ["natural", "noise_only", "broken", "sin2_2u", "kmax0", "kmax62"])
+def test_model_variants(precision, variant):
+    over = {}
+    if variant == "noise_only":
+        over = dict(sgwb_model=0)
+    elif variant == "broken":
+        over = dict(sgwb_model=2)
+    elif variant == "sin2_2u":
+        over = dict(tdi_form=1)
+    elif variant == "kmax0":
+        over = dict(kmin=0, kmax_draw=0)
+    elif variant == "kmax62":
+        over = dict(kmin=55, kmax_draw=62, n_states=40)
+    wl = synth.workload("tiny", n_bins=1500, n_states=24, **over) if variant != "kmax62" else \
+        synth.workload("tiny", n_bins=1500, **over)
+    if variant == "natural":
+        wl.knots.kind = 1
+    P, L, St = oracle_batched(wl)
+    _check(wl, P, L, St, precision)
+
+
+@pytest.mark.parametrize("precision", [FP64, FP32])
+def test_batched_uneven_datasets(precision):
+    wl = synth.workload("batched", n_datasets=7, n_min=50, n_max=3000, states_per=5, kmax_draw=12)
+    # uneven state counts too (dataset 3 keeps none): keep the first (d % 5) + 1 states of each
+    keep = [list(range(wl.state_offset[d], wl.state_offset[d] + (0 if d == 3 else d % 5 + 1)))
+            for d in range(wl.n_datasets)]
+    idx = np.concatenate([np.array(k, dtype=np.int64) for k in keep])
+    so = np.concatenate([[0], np.cumsum([len(k) for k in keep])]).astype(np.int64)
+    k = wl.knots
+    wl = dataclasses.replace(wl, theta=wl.theta[idx], state_offset=so,
+                             knots=dataclasses.replace(k, count=k.count[idx], x=k.x[idx], w=k.w[idx]))
+    P, L, St = oracle_batched(wl)
+    _check(wl, P, L, St, precision, tiling=dict(tile_bins=256, states_per_cta=16, group=4))
+
+
+@pytest.mark.parametrize("precision", [FP64, FP32])
+def test_invalid_states(tiny, precision):
+    wl, P, _, _ = tiny
+    wl = dataclasses.replace(wl, knots=dataclasses.replace(wl.knots, count=wl.knots.count.copy(),
+                                                           x=wl.knots.x.copy(), w=wl.knots.w.copy()),
+                             theta=wl.theta.copy())
+    k = wl.knots
+    k.count[1, 0] = k.kmax + 1                 # bad count
+    k.count[2, 1] = 2
+    k.x[2, 1, :2] = -3.0                       # duplicate
+    k.count[3, 2] = max(k.count[3, 2], 1)
+    k.x[3, 2, 0] = 0.0                         # outside the band
+    k.w[4, 0, 0] = np.nan                      # bad amplitude
+    wl.theta[5, 1] = np.inf                    # bad theta -> nonfinite at evaluation
+    ds = oracle_dataset(wl)
+    L_ref, St_ref = oracle.loglike(ds, wl.theta, k.as_dict())
+    L, St = gpu_eval(wl, P, precision)
+    assert St[0] == 0 and np.isfinite(L[0])
+    assert list(St[1:5]) == [1, 4, 2, 8]
+    assert list(St_ref[1:5]) == [1, 4, 2, 8]
+    assert np.all(np.isneginf(L[1:]))
+
+
+def test_spline_coefficients_fp64_match_oracle(tiny):
+    import torch
+    from paper_2507_06300_gb300 import binding as B
+    wl, P, _, _ = tiny
+    ds = B.Dataset.from_workload(wl, P)
+    for kind in (0, 1):
+        count, x, w, kmax, _ = B.knots_to_device(wl.knots)
+        buf, st = ds.spline_setup(count, x, w, kmax, kind, FP64)
+        raw = buf.cpu().numpy()
+        S, nsp = wl.n_states, wl.n_splines
+        a256 = lambda b: (b + 255) // 256 * 256
+        off_nint = a256(4 * S)
+        off_route = off_nint + a256(4 * S * nsp)
+        off_rec = off_route + a256(4 * (S + 1))
+        nint = raw[off_nint:off_nint + 4 * S * nsp].view(np.int32).reshape(S, nsp)
+        rec = raw[off_rec:].view(np.float64).reshape(S, nsp, kmax + 1, 8)
+        for s in range(S):
+            for a in range(nsp):
+                k = wl.knots.count[s, a]
+                wv = np.concatenate([[wl.knots.w[s, a, 0]], wl.knots.w[s, a, 1:1 + k], [wl.knots.w[s, a, kmax + 1]]])
+                o_st, xs, ys, coef = oracle.spline_coeffs(kind, wl.knots.x[s, a, :k], wv, wl.x_lo[0], wl.x_hi[0])
+                assert o_st == 0 and nint[s, a] == k + 1
+                r = rec[s, a, :k + 1]
+                np.testing.assert_array_equal(r[:, 0], xs[:-1])
+                np.testing.assert_array_equal(r[:-1, 1], xs[1:-1])
+                assert np.isinf(r[-1, 1])
+                np.testing.assert_allclose(r[:, 2:6], coef, rtol=1e-12, atol=1e-12 * np.abs(coef).max())
+    ds.close()
+
+
+def test_model_psd_matches_oracle(tiny):
+    import torch
+    from paper_2507_06300_gb300 import binding as B
+    wl, P, _, _ = tiny
+    ds = B.Dataset.from_workload(wl, P)
+    count, x, w, kmax, kind = B.knots_to_device(wl.knots)
+    buf, st = ds.spline_setup(count, x, w, kmax, kind, FP64)
+    th = torch.as_tensor(wl.theta, device="cuda")
+    S = ds.model_psd(th, buf, kmax).cpu().numpy().reshape(wl.n_states, wl.n_channels, wl.n_bins)
+    ref, st_ref = oracle.model_psd(oracle_dataset(wl), wl.theta, wl.knots.as_dict())
+    ok = st_ref == 0
+    np.testing.assert_allclose(S[ok], ref[ok], rtol=1e-12)
+    ds.close()
+
+
+@pytest.mark.parametrize("precision", [FP64, FP32])
+def test_paper_scale_sampled_states(precision):
+    """131,072 bins x 1,024 states (the benchmark workload and launch configuration): the oracle
+    checks 6 sampled states; every state must agree with the GPU FP64 path."""
+    wl = synth.workload("paper")
+    ds = oracle_dataset(wl)
+    P = ds["P"]
+    L, St = gpu_eval(wl, P, precision)
+    rng = np.random.default_rng(0)
+    pick = np.sort(rng.choice(wl.n_states, 6, replace=False))
+    pick[0] = 0                                 # one cold-chain state (near the injection)
+    th, kn = wl.theta[pick], {k: (v[pick] if isinstance(v, np.ndarray) else v)
+                              for k, v in wl.knots.as_dict().items()}
+    L_ref, St_ref = oracle.loglike(ds, th, kn)
+    np.testing.assert_array_equal(St[pick], St_ref)
+    ok = St_ref == 0
+    if precision == FP64:
+        np.testing.assert_allclose(L[pick][ok], L_ref[ok], rtol=1e-12)
+    else:
+        tol = fp32_tolerance(L_ref, dataclasses.replace(wl, state_offset=np.array([0, len(pick)])), P)
+        assert np.all(np.abs(L[pick][ok] - L_ref[ok]) <= tol[ok])
+        L64, _ = gpu_eval(wl, P, FP64)
+        good = St == 0
+        tol_all = fp32_tolerance(L64, wl, P)
+        assert np.all(np.abs(L[good] - L64[good]) <= tol_all[good])
+
+
+@pytest.mark.parametrize("kind", [0, 1])
+def test_ill_conditioned_splines_take_the_compensated_route(kind):
+    """Prior-drawn knots can make a spline overshoot by tens of decades between close knots
+    (Akima end slopes, or natural-cubic ringing).  The FP32 path must still agree with the
+    oracle to 1e-6 and stay finite: such states are evaluated by the compensated kernel."""
+    wl = synth.workload("tiny", n_bins=4000, n_states=40, kmin=2, kmax_draw=8)
+    wl.knots.kind = kind
+    k = wl.knots
+    rng = np.random.default_rng(7)
+    for s in range(0, 40, 2):                         # every other state: a near-duplicate pair
+        a = s % wl.n_splines
+        k.count[s, a] = max(k.count[s, a], 2)
+        x0 = rng.uniform(-3.8, -1.8)
+        k.x[s, a, 0] = x0
+        k.x[s, a, 1] = x0 + 10 ** rng.uniform(-2.5, -1.5)
+        k.w[s, a, 1], k.w[s, a, 2] = 0.3, -0.3
+    P, L, St = oracle_batched(wl)
+    assert np.all(St == 0)                            # large overshoots, still FP64-finite
+    L32 = _check(wl, P, L, St, FP32)
+    assert np.all(np.isfinite(L32))
