@@ -28,15 +28,20 @@ __device__ __forceinline__ int dataset_of_bin(const DatasetDev* ds, int n, int64
 //   evaluated as 2 sin^2(u/2)), SGWB per unit h^2 Omega: R_c 3 (H0/h)^2 / (4 pi^2 f^3) (Eq. Sh).
 // Every table entry is divided by the channel's periodogram P_c(f_i), so the per-bin ratio
 // P/S becomes 1/S-hat and the FP32 path works on numbers of order one.
-__global__ void prep_kernel(int64_t n_bins, int C, int tdi_form, int sgwb, const double* __restrict__ f,
+__global__ void prep_kernel(int64_t n_pad, int C, int tdi_form, int sgwb, const double* __restrict__ f,
                             const double* __restrict__ nu, const double* __restrict__ P,
-                            const double* __restrict__ R, const DatasetDev* __restrict__ ds,
+                            const double* __restrict__ R, int64_t n_real, const DatasetDev* __restrict__ ds,
                             int n_ds, double* __restrict__ rec64, float* __restrict__ rec32,
-                            float* __restrict__ xlo32, float* __restrict__ elllo32, double* __restrict__ lnP) {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n_bins) return;
-    int d = dataset_of_bin(ds, n_ds, i);
-    double fi = f[i];
+                            float* __restrict__ xlo32, float* __restrict__ elllo32, double* __restrict__ lnP,
+                            double* __restrict__ nu_p) {
+    int64_t ip = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (ip >= n_pad) return;
+    int d = dataset_of_bin(ds, n_ds, ip);
+    const DatasetDev& D = ds[d];
+    const int64_t i = ip - D.bin0;
+    const bool dummy = i >= D.nbins;
+    const int64_t g = D.rbin0 + (dummy ? D.nbins - 1 : i);   // caller's bin index
+    double fi = f[g];
     double u = 2.0 * kPi * fi * kArm / kClight;
     double su, cu;
     sincos(u, &su, &cu);
@@ -61,14 +66,14 @@ __global__ void prep_kernel(int64_t n_bins, int C, int tdi_form, int sgwb, const
     double conv = 3.0 * kH0h * kH0h / (4.0 * kPi * kPi * fi * fi * fi);
     double r[kRec];
     r[0] = log10(fi);
-    r[1] = log2(fi / ds[d].f_ref);
-    r[2] = nu[i];
+    r[1] = log2(fi / D.f_ref);
+    r[2] = dummy ? 0.0 : nu[g];
     double lsum = 0.0;
     for (int c = 0; c < 3; ++c) {
         double g_o = 0.0, g_t = 0.0, g_h = 0.0;
         if (c < C) {
-            double p = P[(size_t)c * n_bins + i];
-            if (sgwb) gh[c] = R[(size_t)c * n_bins + i] * conv;
+            double p = P[(size_t)c * n_real + g];
+            if (sgwb) gh[c] = R[(size_t)c * n_real + g] * conv;
             g_o = go[c] / p;
             g_t = gt[c] / p;
             g_h = gh[c] / p;
@@ -78,12 +83,14 @@ __global__ void prep_kernel(int64_t n_bins, int C, int tdi_form, int sgwb, const
         r[6 + c] = g_t;
         r[9 + c] = g_h;
     }
-    lnP[i] = nu[i] * lsum;
-    xlo32[i] = (float)(r[0] - (double)(float)r[0]);
-    elllo32[i] = (float)(r[1] - (double)(float)r[1]);
+    lnP[ip] = r[2] * lsum;
+    nu_p[ip] = r[2];
+    xlo32[ip] = (float)(r[0] - (double)(float)r[0]);
+    elllo32[ip] = (float)(r[1] - (double)(float)r[1]);
+    const int64_t pb = ip >> 1, e = ip & 1;
     for (int q = 0; q < kRec; ++q) {
-        rec64[(size_t)i * kRec + q] = r[q];
-        rec32[(size_t)i * kRec + q] = (float)r[q];
+        rec64[(size_t)ip * kRec + q] = r[q];
+        rec32[(size_t)pb * kPairRec + 2 * q + e] = (float)r[q];
     }
 }
 
@@ -94,7 +101,7 @@ __global__ void dataset_sums_kernel(const double* __restrict__ lnP, const double
     __shared__ double s1[256], s2[256];
     DatasetDev& D = ds[blockIdx.x];
     double a = 0.0, b = 0.0;
-    for (int64_t i = threadIdx.x; i < D.nbins; i += blockDim.x) {
+    for (int64_t i = threadIdx.x; i < D.npad; i += blockDim.x) {
         a += lnP[D.bin0 + i];
         b += nu[D.bin0 + i];
     }
@@ -155,15 +162,15 @@ lisa_status rebuild_work(lisa_data* d) {
     int64_t pbase = 0;
     for (int k = 0; k < d->n_datasets; ++k) {
         DatasetDev& D = d->h_ds[k];
-        D.ntiles = (int32_t)((D.nbins + t.tile_bins - 1) / t.tile_bins);
+        D.ntiles = (int32_t)((D.npad + t.tile_bins - 1) / t.tile_bins);
         D.pbase = pbase;
         pbase += (int64_t)D.ns * D.ntiles;
-        if (D.ns == 0 || D.nbins == 0) continue;
+        if (D.ns == 0 || D.npad == 0) continue;
         int sc = std::min(t.states_per_cta, pow2ceil(D.ns));
         sc = std::max(sc, 1);
         for (int32_t tile = 0; tile < D.ntiles; ++tile) {
             int64_t b0 = D.bin0 + (int64_t)tile * t.tile_bins;
-            int32_t nb = (int32_t)std::min<int64_t>(t.tile_bins, D.bin0 + D.nbins - b0);
+            int32_t nb = (int32_t)std::min<int64_t>(t.tile_bins, D.bin0 + D.npad - b0);
             for (int32_t s = 0; s < D.ns; s += sc) {
                 WorkItem w;
                 w.bin0 = b0;
@@ -269,17 +276,20 @@ lisa_status lisa_data_create(const lisa_data_desc* desc, lisa_stream_t stream, l
     d->h_state_off.assign(q.state_offset, q.state_offset + D + 1);
     d->h_ds.resize(D);
     std::vector<int32_t> state_ds((size_t)S);
-    int64_t psd_base = 0;
+    int64_t psd_base = 0, pad0 = 0;
     for (int k = 0; k < D; ++k) {
         DatasetDev& X = d->h_ds[k];
-        X.bin0 = q.bin_offset[k];
+        X.rbin0 = q.bin_offset[k];
         X.nbins = q.bin_offset[k + 1] - q.bin_offset[k];
+        X.npad = X.nbins + (X.nbins & 1);
+        X.bin0 = pad0;
+        pad0 += X.npad;
         X.s0 = (int32_t)q.state_offset[k];
         X.ns = (int32_t)(q.state_offset[k + 1] - q.state_offset[k]);
         X.x_lo = q.x_lo[k];
         X.x_hi = q.x_hi[k];
-        X.xb_min = X.nbins ? std::log10(q.freq[X.bin0]) : 0.0;
-        X.xb_max = X.nbins ? std::log10(q.freq[X.bin0 + X.nbins - 1]) : 0.0;
+        X.xb_min = X.nbins ? std::log10(q.freq[X.rbin0]) : 0.0;
+        X.xb_max = X.nbins ? std::log10(q.freq[X.rbin0 + X.nbins - 1]) : 0.0;
         X.f_ref = q.f_ref[k];
         X.ntiles = 0;
         X.pbase = 0;
@@ -290,25 +300,28 @@ lisa_status lisa_data_create(const lisa_data_desc* desc, lisa_stream_t stream, l
         X.pad = 0;
         for (int32_t s = X.s0; s < X.s0 + X.ns; ++s) state_ds[s] = k;
     }
+    d->n_pad = pad0;
     d->tiling = lisa_tiling{1024, 256, 4, 0};
+    const int64_t NP = pad0 > 0 ? pad0 : 1;
 
     lisa_status st = LISA_SUCCESS;
-    double *f = nullptr, *nu = nullptr, *R = nullptr, *lnP = nullptr;
+    double *f = nullptr, *nu = nullptr, *R = nullptr, *lnP = nullptr, *nu_p = nullptr;
     auto fail = [&](lisa_status e) {
         cudaFree(f);
         cudaFree(nu);
         cudaFree(R);
         cudaFree(lnP);
+        cudaFree(nu_p);
         release(d);
         delete d;
         return e;
     };
     if ((st = dev_alloc(&d->d_ds, D)) || (st = dev_alloc(&d->d_state_ds, (size_t)S)) ||
-        (st = dev_alloc(&d->d_rec32, (size_t)N * kRec)) || (st = dev_alloc(&d->d_rec64, (size_t)N * kRec)) ||
-        (st = dev_alloc(&d->d_P, (size_t)C * N)) || (st = dev_alloc(&d->d_xlo32, (size_t)N)) ||
-        (st = dev_alloc(&d->d_elllo32, (size_t)N)) ||
+        (st = dev_alloc(&d->d_rec32, (size_t)NP * kRec)) || (st = dev_alloc(&d->d_rec64, (size_t)NP * kRec)) ||
+        (st = dev_alloc(&d->d_P, (size_t)C * N)) || (st = dev_alloc(&d->d_xlo32, (size_t)NP)) ||
+        (st = dev_alloc(&d->d_elllo32, (size_t)NP)) || (st = dev_alloc(&nu_p, (size_t)NP)) ||
         (st = dev_alloc(&f, (size_t)N)) ||
-        (st = dev_alloc(&nu, (size_t)N)) || (st = dev_alloc(&lnP, (size_t)N)) ||
+        (st = dev_alloc(&nu, (size_t)N)) || (st = dev_alloc(&lnP, (size_t)NP)) ||
         (st = dev_alloc(&R, (size_t)C * N)))
         return fail(st);
     cudaStream_t sm = (cudaStream_t)stream;
@@ -319,10 +332,10 @@ lisa_status lisa_data_create(const lisa_data_desc* desc, lisa_stream_t stream, l
               cudaMemcpyAsync(d->d_P, q.periodogram, C * N * sizeof(double), cudaMemcpyHostToDevice, sm) == cudaSuccess &&
               (q.sgwb_model == 0 || cudaMemcpyAsync(R, q.response, C * N * sizeof(double), cudaMemcpyHostToDevice, sm) == cudaSuccess);
     if (!ok) return fail(LISA_ERR_CUDA);
-    unsigned blocks = (unsigned)((N + 255) / 256);
-    prep_kernel<<<blocks, 256, 0, sm>>>(N, C, q.tdi_form, q.sgwb_model != 0, f, nu, d->d_P, R, d->d_ds, D,
-                                        d->d_rec64, d->d_rec32, d->d_xlo32, d->d_elllo32, lnP);
-    dataset_sums_kernel<<<D, 256, 0, sm>>>(lnP, nu, d->d_ds, C);
+    unsigned blocks = (unsigned)((NP + 255) / 256);
+    prep_kernel<<<blocks, 256, 0, sm>>>(pad0, C, q.tdi_form, q.sgwb_model != 0, f, nu, d->d_P, R, N, d->d_ds, D,
+                                        d->d_rec64, d->d_rec32, d->d_xlo32, d->d_elllo32, lnP, nu_p);
+    dataset_sums_kernel<<<D, 256, 0, sm>>>(lnP, nu_p, d->d_ds, C);
     if (cudaGetLastError() != cudaSuccess) return fail(LISA_ERR_CUDA);
     if (cudaMemcpyAsync(d->h_ds.data(), d->d_ds, D * sizeof(DatasetDev), cudaMemcpyDeviceToHost, sm) != cudaSuccess ||
         cudaStreamSynchronize(sm) != cudaSuccess)
@@ -331,7 +344,8 @@ lisa_status lisa_data_create(const lisa_data_desc* desc, lisa_stream_t stream, l
     cudaFree(nu);
     cudaFree(R);
     cudaFree(lnP);
-    f = nu = R = lnP = nullptr;
+    cudaFree(nu_p);
+    f = nu = R = lnP = nu_p = nullptr;
     if ((st = rebuild_work(d))) return fail(st);
     *out = d;
     return LISA_SUCCESS;
@@ -363,7 +377,7 @@ lisa_status lisa_data_set_tiling(lisa_data* d, const lisa_tiling* t) {
     int sc = t->states_per_cta;
     bool pow2 = sc > 0 && (sc & (sc - 1)) == 0;
     if (t->tile_bins < 64 || t->tile_bins > kMaxTileBins || (t->tile_bins % 32) != 0 || !pow2 || sc < 16 ||
-        sc > kThreads || !(t->group == 1 || t->group == 2 || t->group == 4 || t->group == 8) ||
+        sc > kThreads || !(t->group == 2 || t->group == 4 || t->group == 8) ||
         t->ctas_per_sm < 0 || t->ctas_per_sm > 32)
         return LISA_ERR_VALUE;
     lisa_tiling old = d->tiling;

@@ -18,7 +18,13 @@ constexpr double kLog2_10 = 3.321928094887362347870319;
 constexpr double kLn10 = 2.302585092994045684017991;
 constexpr double kLn2 = 0.693147180559945309417232;
 
-constexpr int kRec = 12;         // per-bin record: x, ell, nu, Goms[3], Gtm[3], Gh[3]
+constexpr int kRec = 12;         // per-bin fields: x, ell, nu, Goms[3], Gtm[3], Gh[3]
+// FP64 bin table: AoS, kRec doubles per bin.  FP32 bin table: blocks of two bins, field k of
+// bin 2p+e at [p * kPairRec + 2k + e], so one 16-byte load returns two fields of both bins and
+// each field's pair sits in an aligned register pair for the packed FP32x2 instructions.
+// Both tables use padded bin indices: every dataset is padded to an even bin count with a
+// dummy bin (copy of its last bin with nu = 0).
+constexpr int kPairRec = 2 * kRec;
 constexpr int kThreads = 256;    // threads of the fused likelihood kernels
 // Per-interval records, 64 bytes in both precisions:
 //   FP64: xl, xr, a, b, c, d, 0, 0 (coefficients about xl, log10 units)
@@ -52,7 +58,9 @@ struct WorkItem {
 static_assert(sizeof(WorkItem) == 32, "WorkItem layout");
 
 struct DatasetDev {
-    int64_t bin0, nbins;     // bin range
+    int64_t bin0, nbins;     // bin range: bin0 in padded indexing, nbins real bins
+    int64_t npad;            // nbins rounded up to even (bins [bin0, bin0 + npad) in the tables)
+    int64_t rbin0;           // first bin in the caller's (unpadded) arrays
     int64_t pbase;           // first partial slot of the dataset's states
     int64_t psd_base;        // first element of the dataset's states in a model-PSD output
     int32_t s0, ns;          // state range
@@ -72,13 +80,14 @@ struct lisa_data {
     int n_sm = 0;
     int32_t n_datasets = 0, C = 0, nsp = 0, sgwb_model = 0, tdi_form = 0;
     int64_t n_bins = 0, n_states = 0;
+    int64_t n_pad = 0;               // padded bin count of the tables
     std::vector<int64_t> h_bin_off, h_state_off;
     std::vector<lisa::DatasetDev> h_ds;
     lisa::DatasetDev* d_ds = nullptr;
     int32_t* d_state_ds = nullptr;   // [n_states] dataset of each state
-    float* d_rec32 = nullptr;        // [n_bins][kRec]
-    double* d_rec64 = nullptr;       // [n_bins][kRec]
-    double* d_P = nullptr;           // [C][n_bins] periodogram (normaliser of the tables)
+    float* d_rec32 = nullptr;        // [n_pad / 2][kPairRec]
+    double* d_rec64 = nullptr;       // [n_pad][kRec]
+    double* d_P = nullptr;           // [C][n_bins] periodogram (unpadded; normaliser of the tables)
     float* d_xlo32 = nullptr;        // [n_bins] log10 f - (float)log10 f (low part of x)
     float* d_elllo32 = nullptr;      // [n_bins] low part of ell = log2(f / f_ref)
     lisa_tiling tiling{};

@@ -119,15 +119,18 @@ __device__ __forceinline__ void load_iv(Iv32& v) {
     v.c3 = B.y;
 }
 
+// Field k of bin i in a pair-block FP32 table (shared or global).
+__device__ __forceinline__ float fld(const float* __restrict__ t, int i, int k) {
+    return t[(i >> 1) * kPairRec + 2 * k + (i & 1)];
+}
+
+// One bin, scalar (used next to knots, where the two bins of a pair may sit in different
+// intervals).
 template <int C, bool HAS_H, bool BROKEN>
-__device__ __forceinline__ float bin_term32(const float4* __restrict__ s4, int i, const Iv32* iv, float ao2,
+__device__ __forceinline__ float bin_term32(const float* __restrict__ tb, int i, const Iv32* iv, float ao2,
                                             float at2, float n1, float n2, float Af) {
     constexpr int NSP = C + (HAS_H ? 1 : 0);
-    const float4 q0 = s4[3 * i], q1 = s4[3 * i + 1], q2 = s4[3 * i + 2];
-    const float x = q0.x, ell = q0.y, nu = q0.z;
-    const float go[3] = {q0.w, q1.x, q1.y};
-    const float gt[3] = {q1.z, q1.w, q2.x};
-    const float gh[3] = {q2.y, q2.z, q2.w};
+    const float x = fld(tb, i, 0), ell = fld(tb, i, 1), nu = fld(tb, i, 2);
     float p[NSP];
 #pragma unroll
     for (int a = 0; a < NSP; ++a) {
@@ -142,9 +145,9 @@ __device__ __forceinline__ float bin_term32(const float4* __restrict__ s4, int i
     float S[C];
 #pragma unroll
     for (int c = 0; c < C; ++c) {
-        const float nc = fmaf(ao2, go[c], at2 * gt[c]);
+        const float nc = fmaf(ao2, fld(tb, i, 3 + c), at2 * fld(tb, i, 6 + c));
         const float e = ex2_approx(p[c]);
-        S[c] = HAS_H ? fmaf(e, nc, eh * gh[c]) : e * nc;
+        S[c] = HAS_H ? fmaf(e, nc, eh * fld(tb, i, 9 + c)) : e * nc;
     }
     float prod, num;
     if (C == 3) {
@@ -169,6 +172,70 @@ __device__ __forceinline__ float bin_term32(const float4* __restrict__ s4, int i
         }
     }
     return nu * fmaf((float)kLn2, lg, v);
+}
+
+// Current interval of one spline duplicated into register pairs for the packed path.
+struct Iv2 {
+    float2 nxo, c0, c1, c2, c3;
+};
+__device__ __forceinline__ Iv2 dup(const Iv32& v) {
+    return Iv2{make_float2(-v.xo, -v.xo), make_float2(v.c0, v.c0), make_float2(v.c1, v.c1),
+               make_float2(v.c2, v.c2), make_float2(v.c3, v.c3)};
+}
+
+// Two consecutive bins (one pair block) with FP32x2 instructions; both bins lie in the current
+// intervals.  Returns nu * (sum_c 1/S_c + ln prod S_c - C) for both bins.
+template <int C, bool HAS_H, bool BROKEN>
+__device__ __forceinline__ float2 pair_term32(const float4* __restrict__ blk, const Iv2* iv, float2 ao2, float2 at2,
+                                              float n1, float n2, float2 Af) {
+    constexpr int NSP = C + (HAS_H ? 1 : 0);
+    const float4 q0 = blk[0], q1 = blk[1], q2 = blk[2], q3 = blk[3], q4 = blk[4], q5 = blk[5];
+    const float2 x = make_float2(q0.x, q0.y), ell = make_float2(q0.z, q0.w), nu = make_float2(q1.x, q1.y);
+    const float2 go[3] = {make_float2(q1.z, q1.w), make_float2(q2.x, q2.y), make_float2(q2.z, q2.w)};
+    const float2 gt[3] = {make_float2(q3.x, q3.y), make_float2(q3.z, q3.w), make_float2(q4.x, q4.y)};
+    const float2 gh[3] = {make_float2(q4.z, q4.w), make_float2(q5.x, q5.y), make_float2(q5.z, q5.w)};
+    float2 p[NSP];
+#pragma unroll
+    for (int a = 0; a < NSP; ++a) {
+        const float2 t = __fadd2_rn(x, iv[a].nxo);
+        p[a] = __ffma2_rn(__ffma2_rn(__ffma2_rn(iv[a].c3, t, iv[a].c2), t, iv[a].c1), t, iv[a].c0);
+    }
+    float2 eh = make_float2(0.f, 0.f);
+    if (HAS_H) {
+        const float2 sl = BROKEN ? make_float2(ell.x < 0.f ? n1 : n2, ell.y < 0.f ? n1 : n2) : make_float2(n1, n1);
+        const float2 ex = __ffma2_rn(sl, ell, p[C]);
+        eh = __fmul2_rn(Af, make_float2(ex2_approx(ex.x), ex2_approx(ex.y)));
+    }
+    float2 S[C];
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+        const float2 nc = __ffma2_rn(ao2, go[c], __fmul2_rn(at2, gt[c]));
+        const float2 e = make_float2(ex2_approx(p[c].x), ex2_approx(p[c].y));
+        S[c] = HAS_H ? __ffma2_rn(e, nc, __fmul2_rn(eh, gh[c])) : __fmul2_rn(e, nc);
+    }
+    float2 prod, num;
+    if (C == 3) {
+        const float2 p01 = __fmul2_rn(S[0], S[1]);
+        prod = __fmul2_rn(p01, S[2]);
+        num = __ffma2_rn(S[2], __fadd2_rn(S[0], S[1]), p01);
+    } else {
+        prod = __fmul2_rn(S[0], S[1]);
+        num = __fadd2_rn(S[0], S[1]);
+    }
+    float2 v, lg;
+    if (fminf(prod.x, prod.y) > 1e-30f && fmaxf(prod.x, prod.y) < 1e30f && fmaxf(num.x, num.y) < 1e30f) {
+        v = __ffma2_rn(num, make_float2(rcp_approx(prod.x), rcp_approx(prod.y)), make_float2(-(float)C, -(float)C));
+        lg = make_float2(lg2_approx(prod.x), lg2_approx(prod.y));
+    } else {
+        v = make_float2(-(float)C, -(float)C);
+        lg = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+            v = __fadd2_rn(v, make_float2(rcp_approx(S[c].x), rcp_approx(S[c].y)));
+            lg = __fadd2_rn(lg, make_float2(lg2_approx(S[c].x), lg2_approx(S[c].y)));
+        }
+    }
+    return __fmul2_rn(nu, __ffma2_rn(make_float2((float)kLn2, (float)kLn2), lg, v));
 }
 
 template <int C, bool HAS_H, bool BROKEN, int G>
@@ -197,7 +264,7 @@ __global__ void __launch_bounds__(kThreads, 2)
         const WorkItem w = items[it];
         const unsigned bytes = (unsigned)w.nb * kRec * sizeof(float);
         mbar_expect_tx(&bars[0], bytes);
-        bulk_copy_g2s(sbuf0, rec32 + w.bin0 * kRec, bytes, &bars[0]);
+        bulk_copy_g2s(sbuf0, rec32 + (w.bin0 >> 1) * kPairRec, bytes, &bars[0]);
     }
     for (int k = 0; it < n_items; it += gridDim.x, ++k) {
         const int b = k & 1;
@@ -207,7 +274,7 @@ __global__ void __launch_bounds__(kThreads, 2)
             const unsigned bytes = (unsigned)w.nb * kRec * sizeof(float);
             fence_proxy_async();
             mbar_expect_tx(&bars[b ^ 1], bytes);
-            bulk_copy_g2s(b ? sbuf0 : sbuf1, rec32 + w.bin0 * kRec, bytes, &bars[b ^ 1]);
+            bulk_copy_g2s(b ? sbuf0 : sbuf1, rec32 + (w.bin0 >> 1) * kPairRec, bytes, &bars[b ^ 1]);
         }
         const WorkItem w = items[it];
         if (b == 0) {
@@ -217,7 +284,8 @@ __global__ void __launch_bounds__(kThreads, 2)
             mbar_wait_bounded(&bars[1], phase1, err);
             phase1 ^= 1;
         }
-        const float4* s4 = reinterpret_cast<const float4*>(b ? sbuf1 : sbuf0);
+        const float* tb = b ? sbuf1 : sbuf0;
+        const float4* tb4 = reinterpret_cast<const float4*>(tb);
 
         const int sc = w.sc;
         const int R = kThreads / sc;
@@ -227,7 +295,8 @@ __global__ void __launch_bounds__(kThreads, 2)
         const bool active = ls < w.ns && sstat[s] == 0;   // invalid and routed states skip
         double acc64 = 0.0;
         if (active) {
-            const int lo = (r * w.nb) / R, hi = ((r + 1) * w.nb) / R;
+            const int np = w.nb >> 1;                          // pair blocks in the tile
+            const int lo = 2 * ((r * np) / R), hi = 2 * (((r + 1) * np) / R);
             if (lo < hi) {
                 const double* th = theta + (size_t)s * LISA_N_THETA;
                 const float ao2 = (float)(th[0] * th[0]);
@@ -235,8 +304,10 @@ __global__ void __launch_bounds__(kThreads, 2)
                 const float Af = HAS_H ? (float)exp10(th[2]) : 0.f;
                 const float n1 = (float)th[3];
                 const float n2 = BROKEN ? (float)th[4] : n1;
+                const float2 ao2_2 = make_float2(ao2, ao2), at2_2 = make_float2(at2, at2), Af2 = make_float2(Af, Af);
                 Iv32 iv[NSP];
-                const float x0 = reinterpret_cast<const float*>(s4)[lo * kRec];
+                Iv2 iv2[NSP];
+                const float x0 = fld(tb, lo, 0);
 #pragma unroll
                 for (int a = 0; a < NSP; ++a) {
                     const int64_t sp = (int64_t)s * nsp + a;
@@ -244,49 +315,56 @@ __global__ void __launch_bounds__(kThreads, 2)
                     iv[a].last = nint[sp] - 1;
                     iv[a].j = find_interval<float, kSplineRec32, 6>(iv[a].base, nint[sp], x0);
                     load_iv(iv[a]);
+                    iv2[a] = dup(iv[a]);
                 }
-                const float* sx = reinterpret_cast<const float*>(s4);
                 int i = lo;
                 while (i < hi) {
                     const int cend = min(i + 32, hi);
-                    float acc32 = 0.f;
+                    float2 acc2 = make_float2(0.f, 0.f);
                     for (; i + G <= cend; i += G) {
-                        const float xg = sx[(i + G - 1) * kRec];
+                        const float xg = fld(tb, i + G - 1, 0);
                         bool fast = true;
 #pragma unroll
                         for (int a = 0; a < NSP; ++a) fast &= xg < iv[a].xr;
                         if (fast) {
 #pragma unroll
-                            for (int g = 0; g < G; ++g)
-                                acc32 += bin_term32<C, HAS_H, BROKEN>(s4, i + g, iv, ao2, at2, n1, n2, Af);
+                            for (int g = 0; g < G; g += 2)
+                                acc2 = __fadd2_rn(acc2, pair_term32<C, HAS_H, BROKEN>(tb4 + ((i + g) >> 1) * (kPairRec / 4),
+                                                                                      iv2, ao2_2, at2_2, n1, n2, Af2));
                         } else {
 #pragma unroll 1
                             for (int g = 0; g < G; ++g) {
-                                const float x = sx[(i + g) * kRec];
+                                const float x = fld(tb, i + g, 0);
 #pragma unroll
                                 for (int a = 0; a < NSP; ++a) {
+                                    bool moved = false;
                                     while (x >= iv[a].xr && iv[a].j < iv[a].last) {
                                         ++iv[a].j;
                                         load_iv(iv[a]);
+                                        moved = true;
                                     }
+                                    if (moved) iv2[a] = dup(iv[a]);
                                 }
-                                acc32 += bin_term32<C, HAS_H, BROKEN>(s4, i + g, iv, ao2, at2, n1, n2, Af);
+                                acc2.x += bin_term32<C, HAS_H, BROKEN>(tb, i + g, iv, ao2, at2, n1, n2, Af);
                             }
                         }
                     }
 #pragma unroll 1
                     for (; i < cend; ++i) {
-                        const float x = sx[i * kRec];
+                        const float x = fld(tb, i, 0);
 #pragma unroll
                         for (int a = 0; a < NSP; ++a) {
+                            bool moved = false;
                             while (x >= iv[a].xr && iv[a].j < iv[a].last) {
                                 ++iv[a].j;
                                 load_iv(iv[a]);
+                                moved = true;
                             }
+                            if (moved) iv2[a] = dup(iv[a]);
                         }
-                        acc32 += bin_term32<C, HAS_H, BROKEN>(s4, i, iv, ao2, at2, n1, n2, Af);
+                        acc2.x += bin_term32<C, HAS_H, BROKEN>(tb, i, iv, ao2, at2, n1, n2, Af);
                     }
-                    acc64 += (double)acc32;
+                    acc64 += (double)acc2.x + (double)acc2.y;
                 }
             }
         }
@@ -333,7 +411,7 @@ __device__ __forceinline__ ff ff_from_double(double v) {
 }
 
 struct IvR {
-    float xr;
+    float xr, T;
     ff xo, c[4];
     const float* base;
     int j, last;
@@ -341,8 +419,19 @@ struct IvR {
 __device__ __forceinline__ void load_ivr(IvR& v) {
     const float* r = v.base + (size_t)v.j * kSplineRec32;
     v.xr = __ldg(r + 0);
+    v.T = __ldg(r + 7);
     v.xo = {__ldg(r + 1), __ldg(r + 8)};
     for (int c = 0; c < 4; ++c) v.c[c] = {__ldg(r + 2 + c), __ldg(r + 9 + c)};
+}
+
+// log2 of a positive float as an exact float-float pair (exponent, log2 of the mantissa):
+// the approximation then only sees arguments in [1, 2), where its absolute error is smallest.
+__device__ __forceinline__ ff lg2_split(float v) {
+    if (!(v >= 1.17549435e-38f) || !(v < INFINITY)) return ff{lg2_approx(v), 0.f};  // 0, inf, NaN, subnormal
+    const int b = __float_as_int(v);
+    const float e = (float)(((b >> 23) & 0xff) - 127);
+    const float m = __int_as_float((b & 0x007fffff) | 0x3f800000);
+    return fast_two_sum(e, lg2_approx(m));
 }
 
 // log2 of a positive sum given the log2 of its two parts (either may be -inf).
@@ -355,104 +444,145 @@ __device__ __forceinline__ ff log2_sum(ff a, ff b) {
     return ff_add(big, ff{corr, 0.f});
 }
 
-// ln S + 1/S in FP64 from lS = log2 S held as float-float.
-__device__ __forceinline__ double log_and_inverse(ff lS) {
-    if (!(lS.hi > -1.0e6f)) return INFINITY;           // S underflows every format, or NaN
-    if (!(lS.hi < 1.0e6f)) return (double)lS.hi * kLn2; // S overflows: 1/S = 0
-    const float n = rintf(lS.hi);
-    const float f = (lS.hi - n) + lS.lo;                  // |f| <= 1/2 + ulp
-    const double inv = ldexp((double)ex2_approx(-f), -(int)n);
-    return inv + kLn2 * ((double)lS.hi + (double)lS.lo);
+// 1/S + ln S from lS = log2 S (float-float).  Inside |lS| < 100 the result is a float-float
+// (2^-lS is ex2 of the fractional part scaled by an exact power of two); outside, the
+// contribution is returned through `far` in FP64 (S beyond the FP32 range: rare).
+__device__ __forceinline__ ff inv_plus_log(ff lS, double& far) {
+    const ff kLn2ff = {0.693147182f, -1.90465421e-09f};
+    if (lS.hi > -100.f && lS.hi < 100.f) {
+        const float n = rintf(lS.hi);
+        const float f = (lS.hi - n) + lS.lo;
+        const float inv = ex2_approx(-f) * __int_as_float((127 - (int)n) << 23);
+        return ff_add(ff_mul(lS, kLn2ff), ff{inv, 0.f});
+    }
+    if (!(lS.hi > -1.0e6f)) {
+        far += INFINITY;                                  // S = 0 (or NaN)
+    } else if (!(lS.hi < 1.0e6f)) {
+        far += (double)lS.hi * kLn2;                      // S overflows: 1/S = 0
+    } else {
+        const float n = rintf(lS.hi);
+        const float f = (lS.hi - n) + lS.lo;
+        far += ldexp((double)ex2_approx(-f), -(int)n) + kLn2 * ((double)lS.hi + (double)lS.lo);
+    }
+    return ff{0.f, 0.f};
 }
 
+// One warp per (routed state, tile); each lane walks a contiguous run of bins.  Spline values
+// are float-float sums where the interval is ill-conditioned; a bin whose intervals are all
+// well-conditioned uses the ordinary FP32 term, any other bin the log-domain term.
 template <int C, bool HAS_H, bool BROKEN>
 __global__ void __launch_bounds__(128)
     loglike_robust_kernel(const int32_t* __restrict__ route, const int32_t* __restrict__ state_ds,
-                          const DatasetDev* __restrict__ ds, int tile_bins, const float* __restrict__ rec32,
-                          const float* __restrict__ xlo32, const float* __restrict__ elllo32,
-                          const double* __restrict__ theta, const int32_t* __restrict__ nint,
-                          const float* __restrict__ srec, int kmax, int nsp, double* __restrict__ partial) {
+                          const DatasetDev* __restrict__ ds, int tile_bins, int max_tiles,
+                          const float* __restrict__ rec32, const float* __restrict__ xlo32,
+                          const float* __restrict__ elllo32, const double* __restrict__ theta,
+                          const int32_t* __restrict__ nint, const float* __restrict__ srec, int kmax, int nsp,
+                          double* __restrict__ partial) {
     constexpr int NSP = C + (HAS_H ? 1 : 0);
-    constexpr int NT = 128;
-    __shared__ double red[NT];
-    const int tid = threadIdx.x;
-    const int nr = route[0];
-    for (int r = blockIdx.y; r < nr; r += gridDim.y) {
+    const int lane = threadIdx.x & 31;
+    const int64_t wg = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int64_t units = (int64_t)route[0] * max_tiles;
+    for (int64_t u = wg; u < units; u += nw) {
+        const int r = (int)(u / max_tiles), t = (int)(u % max_tiles);
         const int s = route[1 + r];
         const DatasetDev& D = ds[state_ds[s]];
+        if (t >= D.ntiles) continue;                         // uniform per warp
         const double* th = theta + (size_t)s * LISA_N_THETA;
         const float ao2 = (float)(th[0] * th[0]);
         const float at2 = (float)(th[1] * th[1]);
+        const float Af = HAS_H ? (float)exp10(th[2]) : 0.f;
         const ff lA = ff_from_double(th[2] * kLog2_10);
         const ff n1 = ff_from_double(th[3]);
         const ff n2 = BROKEN ? ff_from_double(th[4]) : n1;
-        for (int t = blockIdx.x; t < D.ntiles; t += gridDim.x) {
-            const int64_t b0 = D.bin0 + (int64_t)t * tile_bins;
-            const int nb = (int)min((int64_t)tile_bins, D.bin0 + D.nbins - b0);
-            const int lo = (tid * nb) / NT, hi = ((tid + 1) * nb) / NT;
-            double acc = 0.0;
-            if (lo < hi) {
-                IvR iv[NSP];
-                const float x0 = __ldg(rec32 + (b0 + lo) * kRec);
+        const int64_t b0 = D.bin0 + (int64_t)t * tile_bins;   // even
+        const int nb = (int)min((int64_t)tile_bins, D.bin0 + D.npad - b0);
+        const int np = nb >> 1;
+        const int lo = 2 * ((lane * np) / 32), hi = 2 * (((lane + 1) * np) / 32);
+        const float* tbase = rec32 + (b0 >> 1) * kPairRec;
+        double acc = 0.0;
+        if (lo < hi) {
+            IvR iv[NSP];
+            Iv32 iv32[NSP];
+            const float x0 = fld(tbase, lo, 0);
 #pragma unroll
-                for (int a = 0; a < NSP; ++a) {
-                    const int64_t sp = (int64_t)s * nsp + a;
-                    iv[a].base = srec + sp * (int64_t)(kmax + 1) * kSplineRec32;
-                    iv[a].last = nint[sp] - 1;
-                    iv[a].j = find_interval<float, kSplineRec32, 6>(iv[a].base, nint[sp], x0);
-                    load_ivr(iv[a]);
-                }
-                for (int i = lo; i < hi; ++i) {
+            for (int a = 0; a < NSP; ++a) {
+                const int64_t sp = (int64_t)s * nsp + a;
+                iv[a].base = srec + sp * (int64_t)(kmax + 1) * kSplineRec32;
+                iv[a].last = nint[sp] - 1;
+                iv[a].j = find_interval<float, kSplineRec32, 6>(iv[a].base, nint[sp], x0);
+                load_ivr(iv[a]);
+            }
+            for (int i0 = lo; i0 < hi; i0 += 32) {
+                ff acc_ff = {0.f, 0.f};
+                double far = 0.0;
+                const int i1 = min(i0 + 32, hi);
+                for (int i = i0; i < i1; ++i) {
                     const int64_t g = b0 + i;
-                    const float* q = rec32 + g * kRec;
-                    const ff x = {__ldg(q), __ldg(xlo32 + g)};
-                    const ff ell = {__ldg(q + 1), __ldg(elllo32 + g)};
-                    const float nu = __ldg(q + 2);
+                    const ff x = {fld(tbase, i, 0), __ldg(xlo32 + g)};
+                    const float nu = fld(tbase, i, 2);
                     ff P[NSP];
+                    bool hard = false;
 #pragma unroll
                     for (int a = 0; a < NSP; ++a) {
                         while (x.hi >= iv[a].xr && iv[a].j < iv[a].last) {
                             ++iv[a].j;
                             load_ivr(iv[a]);
                         }
-                        const ff tt = ff_add(x, ff{-iv[a].xo.hi, -iv[a].xo.lo});
-                        ff p = iv[a].c[3];
-                        p = ff_add(ff_mul(p, tt), iv[a].c[2]);
-                        p = ff_add(ff_mul(p, tt), iv[a].c[1]);
-                        p = ff_add(ff_mul(p, tt), iv[a].c[0]);
-                        P[a] = p;
+                        if (!(iv[a].T <= (float)kRobustT)) {
+                            hard = true;
+                            const ff tt = ff_add(x, ff{-iv[a].xo.hi, -iv[a].xo.lo});
+                            ff p = iv[a].c[3];
+                            p = ff_add(ff_mul(p, tt), iv[a].c[2]);
+                            p = ff_add(ff_mul(p, tt), iv[a].c[1]);
+                            P[a] = ff_add(ff_mul(p, tt), iv[a].c[0]);
+                        } else {
+                            const float tt = x.hi - iv[a].xo.hi;
+                            P[a] = ff{fmaf(fmaf(fmaf(iv[a].c[3].hi, tt, iv[a].c[2].hi), tt, iv[a].c[1].hi), tt,
+                                           iv[a].c[0].hi), 0.f};
+                        }
                     }
+                    if (!hard) {
+#pragma unroll
+                        for (int a = 0; a < NSP; ++a) {
+                            iv32[a].xo = 0.f;
+                            iv32[a].c0 = P[a].hi;
+                            iv32[a].c1 = iv32[a].c2 = iv32[a].c3 = 0.f;
+                        }
+                        // the ordinary FP32 term with the spline values already evaluated
+                        acc_ff = ff_add(acc_ff, ff{bin_term32<C, HAS_H, BROKEN>(tbase, i, iv32, ao2, at2, (float)n1.hi,
+                                                                                (float)n2.hi, Af), 0.f});
+                        continue;
+                    }
+                    const ff ell = {fld(tbase, i, 1), __ldg(elllo32 + g)};
                     ff lEh = {-INFINITY, 0.f};
                     if (HAS_H) {
                         const ff sl = BROKEN ? (ell.hi < 0.f ? n1 : n2) : n1;
                         lEh = ff_add(ff_add(P[C], ff_mul(sl, ell)), lA);
                     }
-                    double term = 0.0;
+                    ff term = {-(float)C, 0.f};
 #pragma unroll
                     for (int c = 0; c < C; ++c) {
-                        const float N = fmaf(ao2, __ldg(q + 3 + c), at2 * __ldg(q + 6 + c));
-                        const float lN = lg2_approx(N);
-                        const ff lNE = (lN > -INFINITY && lN < INFINITY) ? ff_add(P[c], ff{lN, 0.f}) : ff{lN, 0.f};
+                        const float N = fmaf(ao2, fld(tbase, i, 3 + c), at2 * fld(tbase, i, 6 + c));
+                        const ff lN = lg2_split(N);
+                        const ff lNE = (lN.hi > -INFINITY && lN.hi < INFINITY) ? ff_add(P[c], lN) : lN;
                         ff lS = lNE;
                         if (HAS_H) {
-                            const float lG = lg2_approx(__ldg(q + 9 + c));
-                            const ff lH = (lG > -INFINITY && lG < INFINITY) ? ff_add(lEh, ff{lG, 0.f}) : ff{lG, 0.f};
+                            const ff lG = lg2_split(fld(tbase, i, 9 + c));
+                            const ff lH = (lG.hi > -INFINITY && lG.hi < INFINITY) ? ff_add(lEh, lG) : lG;
                             lS = log2_sum(lNE, lH);
                         }
-                        term += log_and_inverse(lS);
+                        double far_c = 0.0;
+                        term = ff_add(term, inv_plus_log(lS, far_c));
+                        far += (double)nu * far_c;
                     }
-                    acc += (double)nu * (term - (double)C);
+                    acc_ff = ff_add(acc_ff, ff_mul(term, ff{nu, 0.f}));
                 }
+                acc += ((double)acc_ff.hi + (double)acc_ff.lo) + far;
             }
-            red[tid] = acc;
-            __syncthreads();
-            for (int w = NT / 2; w > 0; w >>= 1) {
-                if (tid < w) red[tid] += red[tid + w];
-                __syncthreads();
-            }
-            if (tid == 0) partial[D.pbase + (int64_t)(s - D.s0) * D.ntiles + t] = red[0];
-            __syncthreads();
         }
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+        if (lane == 0) partial[D.pbase + (int64_t)(s - D.s0) * D.ntiles + t] = acc;
     }
 }
 
@@ -570,7 +700,8 @@ __global__ void model_psd_kernel(const int32_t* __restrict__ state_ds, const Dat
         for (int c = 0; c < C; ++c) o[(int64_t)c * D.nbins + i] = NAN;
         return;
     }
-    const int64_t g = D.bin0 + i;
+    const int64_t g = D.bin0 + i;            // padded table index
+    const int64_t gr = D.rbin0 + i;          // caller's bin index
     const double* q = rec64 + g * kRec;
     const double x = q[0], ell = q[1];
     const double* th = theta + (size_t)s * LISA_N_THETA;
@@ -590,7 +721,7 @@ __global__ void model_psd_kernel(const int32_t* __restrict__ state_ds, const Dat
     }
     for (int c = 0; c < C; ++c) {
         const double Sc = (th[0] * th[0] * q[3 + c] + th[1] * th[1] * q[6 + c]) * exp10(Pv[c]) + eh * q[9 + c];
-        o[(int64_t)c * D.nbins + i] = Sc * P[(int64_t)c * n_bins + g];
+        o[(int64_t)c * D.nbins + i] = Sc * P[(int64_t)c * n_bins + gr];
     }
 }
 
@@ -623,11 +754,9 @@ cudaError_t launch_fp32_g(const lisa_data* d, const double* theta, const int32_t
     // compensated kernel for the routed states (a no-op grid when the route list is empty)
     int max_tiles = 1;
     for (const auto& D : d->h_ds) max_tiles = D.ntiles > max_tiles ? D.ntiles : max_tiles;
-    dim3 rgrid((unsigned)(max_tiles < 128 ? max_tiles : 128),
-               (unsigned)(d->n_states < 16 ? d->n_states : 16));
-    loglike_robust_kernel<C, H, B><<<rgrid, 128, 0, sm>>>(route, d->d_state_ds, d->d_ds, d->tiling.tile_bins,
-                                                           d->d_rec32, d->d_xlo32, d->d_elllo32, theta, nint,
-                                                           srec, kmax, d->nsp, partial);
+    loglike_robust_kernel<C, H, B><<<d->n_sm * 8, 128, 0, sm>>>(route, d->d_state_ds, d->d_ds, d->tiling.tile_bins,
+                                                                 max_tiles, d->d_rec32, d->d_xlo32, d->d_elllo32,
+                                                                 theta, nint, srec, kmax, d->nsp, partial);
     return cudaGetLastError();
 }
 
@@ -636,7 +765,6 @@ cudaError_t launch_fp32(const lisa_data* d, const double* theta, const int32_t* 
                         const int32_t* route, const float* srec, int kmax, double* partial, int* err,
                         cudaStream_t sm) {
     switch (d->tiling.group) {
-        case 1: return launch_fp32_g<C, H, B, 1>(d, theta, sstat, nint, route, srec, kmax, partial, err, sm);
         case 2: return launch_fp32_g<C, H, B, 2>(d, theta, sstat, nint, route, srec, kmax, partial, err, sm);
         case 8: return launch_fp32_g<C, H, B, 8>(d, theta, sstat, nint, route, srec, kmax, partial, err, sm);
         default: return launch_fp32_g<C, H, B, 4>(d, theta, sstat, nint, route, srec, kmax, partial, err, sm);
