@@ -219,6 +219,33 @@ lisa_status lisa_model_psd(const lisa_data* data, const lisa_params* params,
                            const void* spline_buf_dev_fp64, size_t spline_buf_bytes, int32_t kmax,
                            double* psd_dev, lisa_stream_t stream);
 
+/* ---- allocation-free variant ---------------------------------------------------------------
+ * No counterpart in the paper: this is a deployment convenience.
+ *
+ * lisa_psd_loglike needs a caller-provided scratch workspace.  Some callers cannot obtain one
+ * per call: code that runs under a memory manager which forbids further device allocations once
+ * a sampler has started (a fixed budget reserved up front, or another framework owning the
+ * device heap), or a host sampler written against a C interface with no device allocator at
+ * all.  lisa_psd_loglike_noalloc computes exactly what lisa_psd_loglike computes, with the same
+ * inputs and outputs, but keeps its scratch (an error flag and the per-state partial sums) in a
+ * fixed-size array that lives in the library's own device image, so the call allocates nothing.
+ *
+ *  - The array holds LISA_NOALLOC_SCRATCH_BYTES (4 MiB): 256 bytes plus 8 bytes per
+ *    (state, tile) partial sum, i.e. lisa_workspace_bytes(data, kmax, precision, 0) must not
+ *    exceed it (the paper-scale workload needs about 1 MiB).  Larger problems get
+ *    LISA_ERR_WORKSPACE and nothing is launched; use lisa_psd_loglike for them.
+ *  - Every GPU that loads the library holds the array until the process exits.
+ *  - The first call on each device looks the array's device address up (with that device
+ *    current); make that first call before any stream capture.  Later calls only launch.
+ *  - All calls on a device share the one array, and each call overwrites it (the error flag is
+ *    cleared on the stream first).  Two calls whose kernels overlap on the GPU race on it:
+ *    serialise them (same stream, or events).
+ * Arguments, layouts and errors are otherwise those of lisa_psd_loglike. */
+#define LISA_NOALLOC_SCRATCH_BYTES (4u * 1024u * 1024u)
+lisa_status lisa_psd_loglike_noalloc(const lisa_data* data, const lisa_params* params,
+                                     const void* spline_buf_dev, size_t spline_buf_bytes, int32_t kmax,
+                                     double* loglike_dev, lisa_precision precision, lisa_stream_t stream);
+
 const char* lisa_status_string(lisa_status status);
 
 #ifdef __cplusplus

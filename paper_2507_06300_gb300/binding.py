@@ -61,7 +61,8 @@ class lisa_data_info(ctypes.Structure):
 
 EXPORTS = ["lisa_data_create", "lisa_data_destroy", "lisa_data_get_info", "lisa_data_set_tiling",
            "lisa_spline_buf_bytes", "lisa_spline_setup", "lisa_workspace_bytes", "lisa_psd_loglike",
-           "lisa_psd_loglike_grad", "lisa_model_psd", "lisa_status_string"]
+           "lisa_psd_loglike_grad", "lisa_model_psd", "lisa_psd_loglike_noalloc", "lisa_status_string"]
+NOALLOC_SCRATCH_BYTES = 4 * 1024 * 1024
 
 _lock = threading.Lock()
 _lib = None
@@ -109,6 +110,9 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         lib.lisa_psd_loglike_grad.restype = S
         lib.lisa_model_psd.argtypes = [_c_vp, ctypes.POINTER(lisa_params), _c_vp, _c_sz, _c_i32, _c_vp, _c_vp]
         lib.lisa_model_psd.restype = S
+        lib.lisa_psd_loglike_noalloc.argtypes = [_c_vp, ctypes.POINTER(lisa_params), _c_vp, _c_sz, _c_i32, _c_vp,
+                                                 _c_i32, _c_vp]
+        lib.lisa_psd_loglike_noalloc.restype = S
         lib.lisa_status_string.argtypes = [_c_i32]
         lib.lisa_status_string.restype = ctypes.c_char_p
         _lib = lib
@@ -257,6 +261,19 @@ class Dataset:
         _check(load().lisa_psd_loglike(self._h, ctypes.byref(pr), buf.data_ptr(), buf.numel(), int(kmax),
                                        out.data_ptr(), workspace.data_ptr(), workspace.numel(), int(precision),
                                        _stream_handle(stream)), "lisa_psd_loglike")
+        return out
+
+    def psd_loglike_noalloc(self, theta, buf, kmax, precision=FP32, out=None, stream=None):
+        """``lisa_psd_loglike_noalloc``: the same result as ``psd_loglike`` for callers that cannot
+        allocate a workspace; the scratch lives in a fixed 4 MiB array inside the library (shared
+        by all calls on the device, so calls must not overlap on the GPU)."""
+        torch = _torch()
+        if out is None:
+            out = torch.empty(self.n_states, dtype=torch.float64, device="cuda")
+        pr = lisa_params(self.n_states, theta.data_ptr())
+        _check(load().lisa_psd_loglike_noalloc(self._h, ctypes.byref(pr), buf.data_ptr(), buf.numel(), int(kmax),
+                                               out.data_ptr(), int(precision), _stream_handle(stream)),
+               "lisa_psd_loglike_noalloc")
         return out
 
     def psd_loglike_grad(self, theta, count, x, w, kmax, kind, buf, precision=FP32, out=None, grad=None,

@@ -25,6 +25,7 @@
 // and evaluated by the compensated kernel: float-float Horner sums and the per-bin term in the
 // log domain, so any exponent range is handled.
 #include <cmath>
+#include <mutex>
 
 #include "lisa_internal.cuh"
 
@@ -875,3 +876,36 @@ lisa_status lisa_model_psd(const lisa_data* d, const lisa_params* params, const 
 }
 
 }  // extern "C"
+
+// ---- allocation-free variant: scratch in the library's own device image --------------------
+// For callers that cannot allocate a workspace (see include/lisa_psd.h).  The array below is
+// the workspace of lisa_psd_loglike, fixed in size; host code only ever uses the device address
+// obtained from cudaGetSymbolAddress (the symbol itself names a host-side stand-in).
+static __device__ __align__(256) unsigned char g_noalloc_scratch[LISA_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+std::mutex g_noalloc_mu;
+void* g_noalloc_ptr[256] = {};   // per device ordinal
+}  // namespace
+
+extern "C" lisa_status lisa_psd_loglike_noalloc(const lisa_data* d, const lisa_params* params, const void* buf,
+                                                size_t buf_bytes, int32_t kmax, double* out, lisa_precision prec,
+                                                lisa_stream_t stream) {
+    if (!d || !params || !buf || !out) return LISA_ERR_NULL;
+    if (ws_fwd_bytes(d) > (size_t)LISA_NOALLOC_SCRATCH_BYTES) return LISA_ERR_WORKSPACE;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) return LISA_ERR_CUDA;
+    void* scratch = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_noalloc_mu);
+        if (!g_noalloc_ptr[dev]) {
+            void* p = nullptr;
+            if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return LISA_ERR_CUDA;
+            g_noalloc_ptr[dev] = p;
+        }
+        scratch = g_noalloc_ptr[dev];
+    }
+    // lisa_psd_loglike clears the error flag on the stream and overwrites the partial sums.
+    return lisa_psd_loglike(d, params, buf, buf_bytes, kmax, out, scratch, LISA_NOALLOC_SCRATCH_BYTES, prec,
+                            stream);
+}
