@@ -71,6 +71,9 @@ def _load():
             lib.lo_loglike_grad.argtypes = common + [D, D, D, c_double, c_double, c_double, c_int,
                                                      c_int, c_int, D, I, D, D, D, D, I]
             lib.lo_loglike_grad.restype = None
+            lib.lo_loglike_grad_scaled.argtypes = common + [D, D, D, c_double, c_double, c_double, c_int,
+                                                            c_int, c_int, D, I, D, D, D, D, D, I]
+            lib.lo_loglike_grad_scaled.restype = None
             _lib = lib
     return _lib
 
@@ -233,3 +236,20 @@ def loglike_grad(ds, theta, knots):
     _, pst = _i(st)
     _load().lo_loglike_grad(*pa, kind, kmax, S, *sa, po, pg, pst)
     return out, g, st
+
+
+def loglike_grad_scale(ds, theta, knots):
+    """As loglike_grad, plus per gradient component the sum over bins of the absolute values of
+    its per-bin contributions: returns (logL, grad, scale, status)."""
+    keep1, pa = _problem_args(ds)
+    keep2, S, nsp, kmax, kind, sa = _state_args(theta, knots)
+    out = np.empty(S)
+    g = np.zeros((S, grad_size(nsp, kmax)))
+    sc = np.zeros_like(g)
+    st = np.zeros(S, dtype=np.int32)
+    _, po = _d(out)
+    _, pg = _d(g)
+    _, ps = _d(sc)
+    _, pst = _i(st)
+    _load().lo_loglike_grad_scaled(*pa, kind, kmax, S, *sa, po, pg, ps, pst)
+    return out, g, sc, st

@@ -458,11 +458,31 @@ void lo_loglike(int C, int sgwb_model, int tdi_form, int64_t N, const double* f,
 // bin by the chain rule; each knot parameter is differentiated by running the spline
 // construction and evaluation in forward mode (dual numbers) with that parameter seeded.
 //   d logL / d S_c,i = nu_i (P_c,i - S_c,i) / S_c,i^2
+void lo_loglike_grad_scaled(int C, int sgwb_model, int tdi_form, int64_t N, const double* f,
+                            const double* nu, const double* P, const double* R, double x_lo,
+                            double x_hi, double f_ref, int kind, int kmax, int S,
+                            const double* theta, const int* count, const double* kx,
+                            const double* kw, double* logL, double* grad, double* gscale,
+                            int* status);
+
 void lo_loglike_grad(int C, int sgwb_model, int tdi_form, int64_t N, const double* f,
                      const double* nu, const double* P, const double* R, double x_lo,
                      double x_hi, double f_ref, int kind, int kmax, int S, const double* theta,
                      const int* count, const double* kx, const double* kw, double* logL,
                      double* grad, int* status) {
+    lo_loglike_grad_scaled(C, sgwb_model, tdi_form, N, f, nu, P, R, x_lo, x_hi, f_ref, kind, kmax, S,
+                           theta, count, kx, kw, logL, grad, nullptr, status);
+}
+
+// As lo_loglike_grad; if gscale is not NULL it also receives, per gradient component, the sum
+// over bins of the absolute values of that component's per-bin contributions (the condition
+// scale of the sum: a backward-stable evaluation errs by a small multiple of eps times it).
+void lo_loglike_grad_scaled(int C, int sgwb_model, int tdi_form, int64_t N, const double* f,
+                            const double* nu, const double* P, const double* R, double x_lo,
+                            double x_hi, double f_ref, int kind, int kmax, int S,
+                            const double* theta, const int* count, const double* kx,
+                            const double* kw, double* logL, double* grad, double* gscale,
+                            int* status) {
     Problem pb{C, sgwb_model, tdi_form, N, f, nu, P, R, x_lo, x_hi, f_ref, kind, kmax};
     int nsp = n_splines(pb);
     const int per_spline = 2 * kmax + 2;
@@ -478,6 +498,10 @@ void lo_loglike_grad(int C, int sgwb_model, int tdi_form, int64_t N, const doubl
         const double* skw = kw + (size_t)s * nsp * (kmax + 2);
         double* gs = grad + (size_t)s * G;
         for (int p = 0; p < G; ++p) gs[p] = 0.0;
+        double* ga_s = gscale ? gscale + (size_t)s * G : nullptr;
+        if (ga_s)
+            for (int p = 0; p < G; ++p) ga_s[p] = 0.0;
+        double sc_aoms = 0.0, sc_atm = 0.0, sc_lA = 0.0, sc_n1 = 0.0, sc_n2 = 0.0;
         std::vector<Spline<double>> sps;
         int st = build_state(pb, th, cnt, skx, skw, sps);
         double sum = 0.0;
@@ -502,14 +526,20 @@ void lo_loglike_grad(int C, int sgwb_model, int tdi_form, int64_t N, const doubl
                     double g = nu[i] * (Pc - Sc) / (Sc * Sc);
                     g_aoms += g * 2.0 * th[0] * u_o[c] * En;
                     g_atm += g * 2.0 * th[1] * u_t[c] * En;
+                    sc_aoms += std::fabs(g * 2.0 * th[0] * u_o[c] * En);
+                    sc_atm += std::fabs(g * 2.0 * th[1] * u_t[c] * En);
                     q[(size_t)c * N + i] = g * kLn10 * bm.sn[c] * En;
                     if (pb.sgwb_model) {
                         double shp = bm.sh[c] * Eh;
                         g_lA += g * kLn10 * shp;
-                        if (pb.sgwb_model == 2 && f[i] >= f_ref)
+                        sc_lA += std::fabs(g * kLn10 * shp);
+                        if (pb.sgwb_model == 2 && f[i] >= f_ref) {
                             g_n2 += g * lnf * shp;
-                        else
+                            sc_n2 += std::fabs(g * lnf * shp);
+                        } else {
                             g_n1 += g * lnf * shp;
+                            sc_n1 += std::fabs(g * lnf * shp);
+                        }
                         qh += g * kLn10 * shp;
                     }
                 }
@@ -526,6 +556,13 @@ void lo_loglike_grad(int C, int sgwb_model, int tdi_form, int64_t N, const doubl
         gs[2] = g_lA;
         gs[3] = g_n1;
         gs[4] = (pb.sgwb_model == 2) ? g_n2 : 0.0;
+        if (ga_s) {
+            ga_s[0] = sc_aoms;
+            ga_s[1] = sc_atm;
+            ga_s[2] = sc_lA;
+            ga_s[3] = (pb.sgwb_model == 2) ? sc_n1 : sc_n1 + sc_n2;
+            ga_s[4] = (pb.sgwb_model == 2) ? sc_n2 : 0.0;
+        }
 
         // Knot parameters: seed one at a time and differentiate the spline value per bin.
         for (int a = 0; a < nsp; ++a) {
@@ -539,18 +576,25 @@ void lo_loglike_grad(int C, int sgwb_model, int tdi_form, int64_t N, const doubl
             wslots.push_back(0);
             for (int j = 0; j < k; ++j) wslots.push_back(1 + j);
             wslots.push_back(kmax + 1);
-            auto run = [&](int seed_kind, int slot) {
+            auto run = [&](int seed_kind, int slot, double* abs_sum) {
                 for (int j = 0; j < kmax; ++j) dx[j] = Dual(ax[j], 0.0);
                 for (int j = 0; j < kmax + 2; ++j) dw[j] = Dual(aw[j], 0.0);
                 if (seed_kind == 0) dw[slot].d = 1.0; else dx[slot].d = 1.0;
                 Spline<Dual> sp;
                 build_spline<Dual>(kind, k, kmax, dx.data(), dw.data(), x_lo, x_hi, sp);
-                double acc = 0.0;
-                for (int64_t i = 0; i < N; ++i) acc += q[(size_t)a * N + i] * eval_spline(sp, xs[i]).d;
+                double acc = 0.0, aacc = 0.0;
+                for (int64_t i = 0; i < N; ++i) {
+                    const double term = q[(size_t)a * N + i] * eval_spline(sp, xs[i]).d;
+                    acc += term;
+                    aacc += std::fabs(term);
+                }
+                *abs_sum = aacc;
                 return acc;
             };
-            for (int slot : wslots) ga[slot] = run(0, slot);
-            for (int j = 0; j < k; ++j) ga[kmax + 2 + j] = run(1, j);
+            double* gsa = ga_s ? ga_s + 5 + a * per_spline : nullptr;
+            double dummy = 0.0;
+            for (int slot : wslots) ga[slot] = run(0, slot, gsa ? &gsa[slot] : &dummy);
+            for (int j = 0; j < k; ++j) ga[kmax + 2 + j] = run(1, j, gsa ? &gsa[kmax + 2 + j] : &dummy);
         }
     }
 }

@@ -396,3 +396,55 @@ class Evaluator:
         out.copy_(self.out, non_blocking=True)
         torch.cuda.current_stream().synchronize()
         return out
+
+
+def _make_autograd():
+    import torch
+
+    class PsdLogLike(torch.autograd.Function):
+        """log L(theta, knot amplitudes, knot positions) for every state, differentiable.
+
+        forward runs lisa_spline_setup and, when a gradient is wanted, lisa_psd_loglike_grad (the
+        hand-written adjoint, which also returns log L; the spline coefficients are recomputed
+        from the knots, nothing per bin is stored), else lisa_psd_loglike.  backward only scales
+        the stored per-state gradient rows by the incoming gradient.  Knot counts (the
+        reversible-jump dimension) are not differentiable."""
+
+        @staticmethod
+        def forward(ctx, theta, w, x, dataset, count, kmax, kind, precision):
+            need = ctx.needs_input_grad[0] or ctx.needs_input_grad[1] or ctx.needs_input_grad[2]
+            theta_c, w_c, x_c = theta.detach().contiguous(), w.detach().contiguous(), x.detach().contiguous()
+            buf, _ = dataset.spline_setup(count, x_c, w_c, kmax, kind, precision)
+            if not need:
+                return dataset.psd_loglike(theta_c, buf, kmax, precision)
+            out, grad = dataset.psd_loglike_grad(theta_c, count, x_c, w_c, kmax, kind, buf, precision)
+            ctx.save_for_backward(grad)
+            ctx.shape = (dataset.n_splines, int(kmax))
+            return out
+
+        @staticmethod
+        def backward(ctx, g_out):
+            (grad,) = ctx.saved_tensors
+            nsp, kmax = ctx.shape
+            S = grad.shape[0]
+            g = grad * g_out.reshape(S, 1)
+            per = 2 * kmax + 2
+            body = g[:, N_THETA:].reshape(S, nsp, per)
+            g_theta = g[:, :N_THETA]
+            g_w = body[:, :, :kmax + 2]
+            g_x = body[:, :, kmax + 2:]
+            return g_theta, g_w, g_x, None, None, None, None, None
+
+    return PsdLogLike
+
+
+_PsdLogLike = None
+
+
+def psd_loglike(dataset, theta, w, x, count, kmax, kind=AKIMA, precision=FP32):
+    """Differentiable log-likelihood of every state (see PsdLogLike): theta [S,5], w [S,nsp,kmax+2],
+    x [S,nsp,kmax] (device tensors, FP64, requires_grad allowed), count [S,nsp] int32."""
+    global _PsdLogLike
+    if _PsdLogLike is None:
+        _PsdLogLike = _make_autograd()
+    return _PsdLogLike.apply(theta, w, x, dataset, count, int(kmax), int(kind), int(precision))

@@ -136,6 +136,10 @@ void release(lisa_data* d) {
     cudaFree(d->d_xlo32);
     cudaFree(d->d_elllo32);
     cudaFree(d->d_items);
+    cudaFree(d->d_adj_units);
+    cudaFree(d->d_adj_prefix);
+    d->d_adj_units = nullptr;
+    d->d_adj_prefix = nullptr;
     d->d_ds = nullptr;
     d->d_state_ds = nullptr;
     d->d_rec32 = nullptr;
@@ -297,7 +301,7 @@ lisa_status lisa_data_create(const lisa_data_desc* desc, lisa_stream_t stream, l
         psd_base += (int64_t)C * X.ns * X.nbins;
         X.K = 0.0;
         X.Cnu = 0.0;
-        X.pad = 0;
+        X.nranges = (int32_t)((X.npad + kAdjBins - 1) / kAdjBins);
         for (int32_t s = X.s0; s < X.s0 + X.ns; ++s) state_ds[s] = k;
     }
     d->n_pad = pad0;
@@ -347,6 +351,30 @@ lisa_status lisa_data_create(const lisa_data_desc* desc, lisa_stream_t stream, l
     cudaFree(nu_p);
     f = nu = R = lnP = nu_p = nullptr;
     if ((st = rebuild_work(d))) return fail(st);
+    {
+        // adjoint decomposition (independent of the tiling): per dataset, ranges x groups of 32
+        std::vector<AdjUnit> units;
+        std::vector<int64_t> prefix((size_t)S);
+        int64_t acc = 0;
+        for (int k = 0; k < D; ++k) {
+            const DatasetDev& X = d->h_ds[k];
+            for (int32_t s2 = 0; s2 < X.ns; ++s2) {
+                prefix[(size_t)X.s0 + s2] = acc;
+                acc += X.nranges;
+            }
+            for (int32_t r = 0; r < X.nranges; ++r)
+                for (int32_t g = 0; g < X.ns; g += 32) units.push_back(AdjUnit{k, r, X.s0 + g, std::min(32, X.ns - g)});
+        }
+        d->adj_ranges = acc;
+        d->n_adj_units = (int64_t)units.size();
+        if ((st = dev_alloc(&d->d_adj_units, units.size())) || (st = dev_alloc(&d->d_adj_prefix, prefix.size())))
+            return fail(st);
+        if (cudaMemcpy(d->d_adj_units, units.data(), units.size() * sizeof(AdjUnit), cudaMemcpyHostToDevice) !=
+                cudaSuccess ||
+            cudaMemcpy(d->d_adj_prefix, prefix.data(), prefix.size() * sizeof(int64_t), cudaMemcpyHostToDevice) !=
+                cudaSuccess)
+            return fail(LISA_ERR_CUDA);
+    }
     *out = d;
     return LISA_SUCCESS;
 }

@@ -1,16 +1,690 @@
-// Adjoint of the fused likelihood (placeholder until the adjoint kernels land).
-#include "lisa_internal.cuh"
+// Adjoint of the fused likelihood: log L and d log L / d(theta, knot amplitudes, knot positions)
+// for every state.
+//
+// With S-hat = S / P (the tables are normalised by the periodogram) the per-bin term is
+// nu (1/S + ln S) up to constants, so d log L / d S_c = nu (1 - S_c) / S_c^2 =: g_c.  Then, per
+// state,
+//   d/d a_oms  = 2 a_oms sum_i sum_c g_c G_oms,c E_c          E_c = 10^{P_n,c}
+//   d/d a_tm   = 2 a_tm  sum_i sum_c g_c G_tm,c  E_c
+//   d/d log10A = ln10 sum_i H_i,      H_i = sum_c g_c E_h G_h,c    (E_h = A (f/f_ref)^n 10^{P_h})
+//   d/d n      = ln2  sum_i ell_i H_i (split at f_ref for the broken power law)
+// and each spline receives the adjoint signal q(x_i) = d log L / d P(x_i):
+//   noise spline c: q = ln10 g_c N_c E_c,   SGWB spline: q = ln10 H_i.
+// Because P(x) = a_j + b_j t + c_j t^2 + d_j t^3 (t = x - x_j) on interval j, the gradient
+// with respect to that interval's coefficients is the moment vector M_p = sum_{i in j} q_i t_i^p
+// (p = 0..3), and the knot position x_j moves t as well: dL/dx_j|direct = -(b M0 + 2c M1 + 3d M2).
+// The kernels below recompute the forward pass per bin (nothing per bin is stored), accumulate
+// the template sums and the per-interval moments, and an epilogue rebuilds each spline from its
+// knots and pushes the moments back through the spline construction (Akima slopes, natural
+// cubic system, or linear fallback) to the knot amplitudes and positions.
+//
+// FP32 mode accumulates the moments about each interval's midpoint x_o (the variable of its
+// Horner evaluation, |x - x_o| <= h/2), which keeps the FP32 partial sums small; the epilogue
+// converts them exactly (FP64 binomial expansion) to moments about the left knot.
+//
+// Determinism: a range rho of kAdjBins bins writes the moments of every interval j it touches
+// to slot rho + j of its (state, spline) row; the intervals a range touches are monotone in rho,
+// so slots never collide, and the epilogue adds them back in a fixed order.
+#include "lisa_math.cuh"
+#include "lisa_spline_dev.cuh"
 
 namespace lisa {
+
 size_t grad_extra_bytes(const lisa_data* d, int kmax) {
-    (void)d;
-    (void)kmax;
-    return 0;
+    const size_t scal = align256(sizeof(double) * 6 * (size_t)d->adj_ranges);
+    const size_t mom = align256(sizeof(double) * 4 * (size_t)d->nsp *
+                                ((size_t)d->adj_ranges + (size_t)d->n_states * (size_t)(kmax + 1)));
+    return scal + mom;
 }
+
+namespace {
+using namespace dm;
+
+constexpr unsigned kFullMask = 0xffffffffu;
+
+// Moment row of (state, spline): 4 doubles per slot, nranges + kmax + 1 slots.
+__device__ __forceinline__ double* mom_row(double* mom, int64_t prefix, int s, int a, int nsp, int kmax, int nr) {
+    return mom + 4 * ((int64_t)nsp * (prefix + (int64_t)s * (kmax + 1)) + (int64_t)a * (nr + kmax + 1));
+}
+
+// ---- FP32 adjoint: one warp per (dataset, range, up to 32 states) -----------------------------
+struct AdjIv {
+    float xl, xr, xo, xo_lo, c0, c1, c2, c3;
+    int j;
+};
+
+template <int C, bool HAS_H, bool BROKEN>
+__global__ void __launch_bounds__(128)
+    adjoint_fp32_kernel(const AdjUnit* __restrict__ units, int64_t n_units, const DatasetDev* __restrict__ ds,
+                        const float* __restrict__ rec32, const float* __restrict__ xlo32,
+                        const double* __restrict__ theta, const int32_t* __restrict__ sstat,
+                        const int32_t* __restrict__ nint, const float* __restrict__ srec, int kmax, int nsp,
+                        const int64_t* __restrict__ prefix, double* __restrict__ scal, double* __restrict__ mom) {
+    constexpr int NSP = C + (HAS_H ? 1 : 0);
+    const int lane = threadIdx.x & 31;
+    const int64_t wg = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t u = wg; u < n_units; u += nw) {
+        const AdjUnit U = units[u];
+        const DatasetDev& D = ds[U.ds];
+        const int s = U.s0 + lane;
+        if (lane >= U.ns || (sstat[s] & kUserBits)) continue;
+        const double* th = theta + (size_t)s * LISA_N_THETA;
+        const float ao2 = (float)(th[0] * th[0]), at2 = (float)(th[1] * th[1]);
+        const float Af = HAS_H ? (float)exp10(th[2]) : 0.f;
+        const float n1 = (float)th[3], n2 = BROKEN ? (float)th[4] : n1;
+        const int64_t b0 = D.bin0 + (int64_t)U.rho * kAdjBins;        // even
+        const int nb = (int)min((int64_t)kAdjBins, D.bin0 + D.npad - b0);
+        const float* tb = rec32 + (b0 >> 1) * kPairRec;
+        const int64_t pre = prefix[s];
+        AdjIv iv[NSP];
+        const float* base[NSP];
+        int last[NSP];
+        const float x0 = fld(tb, 0, 0);
+#pragma unroll
+        for (int a = 0; a < NSP; ++a) {
+            const int64_t sp = (int64_t)s * nsp + a;
+            base[a] = srec + sp * (int64_t)(kmax + 1) * kSplineRec32;
+            last[a] = nint[sp] - 1;
+            iv[a].j = find_interval<float, kSplineRec32, 6>(base[a], nint[sp], x0);
+        }
+        auto load = [&](int a) {
+            const float* r = base[a] + (size_t)iv[a].j * kSplineRec32;
+            iv[a].xr = __ldg(r + 0);
+            iv[a].xo = __ldg(r + 1);
+            iv[a].c0 = __ldg(r + 2);
+            iv[a].c1 = __ldg(r + 3);
+            iv[a].c2 = __ldg(r + 4);
+            iv[a].c3 = __ldg(r + 5);
+            iv[a].xl = __ldg(r + 6);
+            iv[a].xo_lo = __ldg(r + 8);
+        };
+#pragma unroll
+        for (int a = 0; a < NSP; ++a) load(a);
+        // accumulators: chunk sums in FP32, running sums in float-float
+        float cm[NSP][4];
+        ff am[NSP][4];
+        float cs[6];
+        ff as[6];
+#pragma unroll
+        for (int a = 0; a < NSP; ++a)
+#pragma unroll
+            for (int p = 0; p < 4; ++p) {
+                cm[a][p] = 0.f;
+                am[a][p] = ff{0.f, 0.f};
+            }
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            cs[k] = 0.f;
+            as[k] = ff{0.f, 0.f};
+        }
+        auto flush_mom = [&](int a) {
+#pragma unroll
+            for (int p = 0; p < 4; ++p) {
+                am[a][p] = ff_add(am[a][p], ff{cm[a][p], 0.f});
+                cm[a][p] = 0.f;
+            }
+        };
+        auto store_mom = [&](int a) {
+            flush_mom(a);
+            double* row = mom_row(mom, pre, s, a, nsp, kmax, D.nranges) + 4 * (int64_t)(U.rho + iv[a].j);
+#pragma unroll
+            for (int p = 0; p < 4; ++p) {
+                row[p] = (double)am[a][p].hi + (double)am[a][p].lo;
+                am[a][p] = ff{0.f, 0.f};
+            }
+        };
+        for (int i = 0; i < nb; ++i) {
+            const float x = fld(tb, i, 0), ell = fld(tb, i, 1), nu = fld(tb, i, 2);
+            const float x_lo = __ldg(xlo32 + b0 + i);
+            float P[NSP], tl[NSP];
+#pragma unroll
+            for (int a = 0; a < NSP; ++a) {
+                while (x >= iv[a].xr && iv[a].j < last[a]) {
+                    store_mom(a);
+                    ++iv[a].j;
+                    load(a);
+                }
+                // t = x - x_o from the FP64 values (hi + lo parts): the position derivatives are
+                // sensitive to the ~1e-7 rounding of FP32 positions
+                const ff tt = two_sum(x, -iv[a].xo);
+                const float t = tt.hi + (tt.lo + (x_lo - iv[a].xo_lo));
+                P[a] = fmaf(fmaf(fmaf(iv[a].c3, t, iv[a].c2), t, iv[a].c1), t, iv[a].c0);
+                tl[a] = t;
+            }
+            float eh = 0.f;
+            if (HAS_H) {
+                const float sl = BROKEN ? (ell < 0.f ? n1 : n2) : n1;
+                eh = Af * ex2_approx(fmaf(sl, ell, P[C]));
+            }
+            float fwd = -(float)C, To = 0.f, Tt = 0.f, H = 0.f;
+            float q[NSP];
+#pragma unroll
+            for (int c = 0; c < C; ++c) {
+                const float go = fld(tb, i, 3 + c), gt = fld(tb, i, 6 + c);
+                const float E = ex2_approx(P[c]);
+                const float N = fmaf(ao2, go, at2 * gt);
+                const float Eh = HAS_H ? eh * fld(tb, i, 9 + c) : 0.f;
+                const float Sc = fmaf(E, N, Eh);
+                const float r = rcp_approx(Sc);
+                const float g = nu * r * (r - 1.f);
+                fwd += r + (float)kLn2 * lg2_approx(Sc);
+                To = fmaf(g * go, E, To);
+                Tt = fmaf(g * gt, E, Tt);
+                H = fmaf(g, Eh, H);
+                q[c] = (float)kLn10 * g * N * E;
+            }
+            if (HAS_H) q[C] = (float)kLn10 * H;
+            cs[0] = fmaf(nu, fwd, cs[0]);
+            cs[1] += To;
+            cs[2] += Tt;
+            cs[3] += H;
+            if (BROKEN && ell >= 0.f)
+                cs[5] = fmaf(ell, H, cs[5]);
+            else
+                cs[4] = fmaf(ell, H, cs[4]);
+#pragma unroll
+            for (int a = 0; a < NSP; ++a) {
+                const float t = tl[a], qt = q[a] * t, qt2 = qt * t;
+                cm[a][0] += q[a];
+                cm[a][1] += qt;
+                cm[a][2] += qt2;
+                cm[a][3] = fmaf(qt2, t, cm[a][3]);
+            }
+            if ((i & 15) == 15) {
+#pragma unroll
+                for (int a = 0; a < NSP; ++a) flush_mom(a);
+#pragma unroll
+                for (int k = 0; k < 6; ++k) {
+                    as[k] = ff_add(as[k], ff{cs[k], 0.f});
+                    cs[k] = 0.f;
+                }
+            }
+        }
+#pragma unroll
+        for (int a = 0; a < NSP; ++a) store_mom(a);
+        double* sc = scal + 6 * (pre + U.rho);
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            as[k] = ff_add(as[k], ff{cs[k], 0.f});
+            sc[k] = (double)as[k].hi + (double)as[k].lo;
+        }
+    }
+}
+
+// ---- FP64 adjoint (plain): same decomposition, FP64 throughout ---------------------------------
+template <int C, bool HAS_H, bool BROKEN>
+__global__ void __launch_bounds__(128)
+    adjoint_fp64_kernel(const AdjUnit* __restrict__ units, int64_t n_units, const DatasetDev* __restrict__ ds,
+                        const double* __restrict__ rec64, const double* __restrict__ theta,
+                        const int32_t* __restrict__ sstat, const int32_t* __restrict__ nint,
+                        const double* __restrict__ srec, int kmax, int nsp, const int64_t* __restrict__ prefix,
+                        double* __restrict__ scal, double* __restrict__ mom) {
+    constexpr int NSP = C + (HAS_H ? 1 : 0);
+    const int lane = threadIdx.x & 31;
+    const int64_t wg = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t u = wg; u < n_units; u += nw) {
+        const AdjUnit U = units[u];
+        const DatasetDev& D = ds[U.ds];
+        const int s = U.s0 + lane;
+        if (lane >= U.ns || (sstat[s] & kUserBits)) continue;
+        const double* th = theta + (size_t)s * LISA_N_THETA;
+        const double ao2 = th[0] * th[0], at2 = th[1] * th[1], lA = th[2], n1 = th[3];
+        const double n2 = BROKEN ? th[4] : n1;
+        const int64_t b0 = D.bin0 + (int64_t)U.rho * kAdjBins;
+        const int nb = (int)min((int64_t)kAdjBins, D.bin0 + D.npad - b0);
+        const int64_t pre = prefix[s];
+        const double* base[NSP];
+        int j[NSP], last[NSP];
+        double xl[NSP], xr[NSP], ca[NSP], cb[NSP], cc[NSP], cd[NSP];
+        double m[NSP][4];
+        const double x0 = rec64[b0 * kRec];
+        for (int a = 0; a < NSP; ++a) {
+            const int64_t sp = (int64_t)s * nsp + a;
+            base[a] = srec + sp * (int64_t)(kmax + 1) * kSplineRec;
+            last[a] = nint[sp] - 1;
+            j[a] = find_interval<double, kSplineRec, 0>(base[a], nint[sp], x0);
+            const double* z = base[a] + (size_t)j[a] * kSplineRec;
+            xl[a] = z[0]; xr[a] = z[1]; ca[a] = z[2]; cb[a] = z[3]; cc[a] = z[4]; cd[a] = z[5];
+            for (int p = 0; p < 4; ++p) m[a][p] = 0.0;
+        }
+        double acc[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+        for (int i = 0; i < nb; ++i) {
+            const double* q = rec64 + (b0 + i) * kRec;
+            const double x = q[0], ell = q[1], nu = q[2];
+            double P[NSP], t[NSP];
+            for (int a = 0; a < NSP; ++a) {
+                while (x >= xr[a] && j[a] < last[a]) {
+                    double* row = mom_row(mom, pre, s, a, nsp, kmax, D.nranges) + 4 * (int64_t)(U.rho + j[a]);
+                    for (int p = 0; p < 4; ++p) {
+                        row[p] = m[a][p];
+                        m[a][p] = 0.0;
+                    }
+                    ++j[a];
+                    const double* z = base[a] + (size_t)j[a] * kSplineRec;
+                    xl[a] = z[0]; xr[a] = z[1]; ca[a] = z[2]; cb[a] = z[3]; cc[a] = z[4]; cd[a] = z[5];
+                }
+                t[a] = x - xl[a];
+                P[a] = ca[a] + t[a] * (cb[a] + t[a] * (cc[a] + t[a] * cd[a]));
+            }
+            double eh = 0.0;
+            if (HAS_H) {
+                const double sl = BROKEN ? (ell < 0.0 ? n1 : n2) : n1;
+                eh = exp10(lA + P[C]) * exp2(sl * ell);
+            }
+            double fwd = 0.0, To = 0.0, Tt = 0.0, H = 0.0, qv[NSP];
+            for (int c = 0; c < C; ++c) {
+                const double E = exp10(P[c]);
+                const double N = ao2 * q[3 + c] + at2 * q[6 + c];
+                const double Eh = HAS_H ? eh * q[9 + c] : 0.0;
+                const double Sc = E * N + Eh;
+                const double g = nu * (1.0 - Sc) / (Sc * Sc);
+                fwd += 1.0 / Sc + log(Sc);
+                To += g * q[3 + c] * E;
+                Tt += g * q[6 + c] * E;
+                H += g * Eh;
+                qv[c] = kLn10 * g * N * E;
+            }
+            if (HAS_H) qv[C] = kLn10 * H;
+            acc[0] += nu * (fwd - (double)C);
+            acc[1] += To;
+            acc[2] += Tt;
+            acc[3] += H;
+            if (BROKEN && ell >= 0.0) acc[5] += ell * H; else acc[4] += ell * H;
+            for (int a = 0; a < NSP; ++a) {
+                const double qt = qv[a] * t[a];
+                m[a][0] += qv[a];
+                m[a][1] += qt;
+                m[a][2] += qt * t[a];
+                m[a][3] += qt * t[a] * t[a];
+            }
+        }
+        for (int a = 0; a < NSP; ++a) {
+            double* row = mom_row(mom, pre, s, a, nsp, kmax, D.nranges) + 4 * (int64_t)(U.rho + j[a]);
+            for (int p = 0; p < 4; ++p) row[p] = m[a][p];
+        }
+        double* sc = scal + 6 * (pre + U.rho);
+        for (int k = 0; k < 6; ++k) sc[k] = acc[k];
+    }
+}
+
+// ---- epilogue: one warp per state, FP64 ----------------------------------------------------------
+
+// d s_k / d m_{k+delta}, delta = -2..1, for the Akima slope at knot k (Appendix A rules,
+// including the ends), returned in d[0..3] = delta -2, -1, 0, +1.  mm2..mp1 = m_{k-2}..m_{k+1}.
+__device__ __forceinline__ void akima_slope_grad(int k, int K, double mm2, double mm1, double m0, double mp1,
+                                                 double sk, double d[4]) {
+    d[0] = d[1] = d[2] = d[3] = 0.0;
+    if (k == 0) {                 // s_0 = (3 m_0 - m_1)/2
+        d[2] = 1.5;
+        d[3] = -0.5;
+        return;
+    }
+    if (k == K - 1) {             // s_{K-1} = (3 m_{K-2} - m_{K-3})/2
+        d[1] = 1.5;
+        d[0] = -0.5;
+        return;
+    }
+    auto sgn = [](double v) { return v > 0.0 ? 1.0 : (v < 0.0 ? -1.0 : 0.0); };
+    const double ml = mm1, mr = m0;  // slopes left and right of knot k
+    double wl, wr;
+    if (k == 1) {
+        wl = fabs(mp1 - m0);
+        wr = fabs(m0 - mm1);
+    } else if (k == K - 2) {
+        wl = fabs(m0 - mm1);
+        wr = fabs(mm1 - mm2);
+    } else {
+        wl = fabs(mp1 - m0);
+        wr = fabs(mm1 - mm2);
+    }
+    const double D = wl + wr;
+    if (D == 0.0) {
+        d[1] = 0.5;
+        d[2] = 0.5;
+        return;
+    }
+    const double dwl = (ml - sk) / D, dwr = (mr - sk) / D;   // ds/dwl, ds/dwr
+    d[1] += wl / D;   // ds/dml
+    d[2] += wr / D;   // ds/dmr
+    if (k == 1) {
+        // wl = |m_{k+1} - m_k|, wr = |m_k - m_{k-1}|
+        const double a1 = sgn(mp1 - m0), a2 = sgn(m0 - mm1);
+        d[3] += dwl * a1;
+        d[2] -= dwl * a1;
+        d[2] += dwr * a2;
+        d[1] -= dwr * a2;
+    } else if (k == K - 2) {
+        // wl = |m_k - m_{k-1}|, wr = |m_{k-1} - m_{k-2}|
+        const double a1 = sgn(m0 - mm1), a2 = sgn(mm1 - mm2);
+        d[2] += dwl * a1;
+        d[1] -= dwl * a1;
+        d[1] += dwr * a2;
+        d[0] -= dwr * a2;
+    } else {
+        // wl = |m_{k+1} - m_k|, wr = |m_{k-1} - m_{k-2}|
+        const double a1 = sgn(mp1 - m0), a2 = sgn(mm1 - mm2);
+        d[3] += dwl * a1;
+        d[2] -= dwl * a1;
+        d[1] += dwr * a2;
+        d[0] -= dwr * a2;
+    }
+}
+
+template <int C, bool HAS_H, bool BROKEN>
+__global__ void __launch_bounds__(128)
+    adjoint_epilogue_kernel(int S, const int32_t* __restrict__ state_ds, const DatasetDev* __restrict__ ds,
+                            const int32_t* __restrict__ sstat, const double* __restrict__ theta,
+                            const int32_t* __restrict__ count, const double* __restrict__ kx,
+                            const double* __restrict__ kw, int kmax, int kind, int nsp,
+                            const int64_t* __restrict__ prefix, const double* __restrict__ scal,
+                            const double* __restrict__ mom, const float* __restrict__ rec32,
+                            const double* __restrict__ rec64, const void* __restrict__ srec_v, int fp32,
+                            double* __restrict__ out_logL, double* __restrict__ grad) {
+    __shared__ double sX[4][64];
+    __shared__ double sY[4][64];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int s = blockIdx.x * 4 + warp;
+    if (s >= S) return;
+    const int G = LISA_N_THETA + nsp * (2 * kmax + 2);
+    double* gs = grad + (size_t)s * G;
+    for (int k = lane; k < G; k += 32) gs[k] = 0.0;
+    __syncwarp();
+    if (sstat[s] & kUserBits) {
+        if (lane == 0) out_logL[s] = -INFINITY;
+        return;
+    }
+    const DatasetDev& D = ds[state_ds[s]];
+    const int nr = D.nranges;
+    const int64_t pre = prefix[s];
+    double v[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    for (int r = lane; r < nr; r += 32)
+        for (int k = 0; k < 6; ++k) v[k] += scal[6 * (pre + r) + k];
+    for (int o = 16; o > 0; o >>= 1)
+        for (int k = 0; k < 6; ++k) v[k] += __shfl_down_sync(kFullMask, v[k], o);
+    for (int k = 0; k < 6; ++k) v[k] = __shfl_sync(kFullMask, v[k], 0);
+    double L = -v[0] - D.Cnu + D.K;
+    const bool finite = isfinite(L);
+    if (lane == 0) out_logL[s] = finite ? L : -INFINITY;
+    if (!finite) return;   // gradient stays zero
+    const double* th = theta + (size_t)s * LISA_N_THETA;
+    if (lane == 0) {
+        gs[0] = 2.0 * th[0] * v[1];
+        gs[1] = 2.0 * th[1] * v[2];
+        if (HAS_H) {
+            gs[2] = kLn10 * v[3];
+            gs[3] = kLn2 * (BROKEN ? v[4] : v[4] + v[5]);
+            gs[4] = BROKEN ? kLn2 * v[5] : 0.0;
+        }
+    }
+    const int per_spline = 2 * kmax + 2;
+    for (int a = 0; a < nsp; ++a) {
+        const int64_t sp = (int64_t)s * nsp + a;
+        spl::WarpSpline W;
+        spl::warp_build_spline(W, kx + sp * kmax, kw + sp * (kmax + 2), count[sp], kmax, kind, D.x_lo, D.x_hi,
+                               sX[warp], sY[warp]);
+        if (W.st) continue;
+        const int K = W.K;
+        const int nint = K - 1;
+        const double* row = mom_row(const_cast<double*>(mom), pre, s, a, nsp, kmax, nr);
+        // moments of each interval, gathered over the ranges that touched it (fixed order)
+        double M[2][4];
+        for (int q = 0; q < 2; ++q) {
+            const int jj = lane + 32 * q;
+            for (int p = 0; p < 4; ++p) M[q][p] = 0.0;
+            if (jj >= nint) continue;
+            double lo_b, hi_b;   // the interval's bounds as the likelihood kernels' walk sees them
+            if (fp32) {
+                const float* r = static_cast<const float*>(srec_v) + (sp * (int64_t)(kmax + 1) + jj) * kSplineRec32;
+                lo_b = (double)r[6];
+                hi_b = (double)r[0];
+            } else {
+                const double* r = static_cast<const double*>(srec_v) + (sp * (int64_t)(kmax + 1) + jj) * kSplineRec;
+                lo_b = r[0];
+                hi_b = r[1];
+            }
+            for (int rho = 0; rho < nr; ++rho) {
+                const int64_t b0 = D.bin0 + (int64_t)rho * kAdjBins;
+                const int nb = (int)min((int64_t)kAdjBins, D.bin0 + D.npad - b0);
+                double xf, xlb;
+                if (fp32) {
+                    const float* tb = rec32 + (b0 >> 1) * kPairRec;
+                    xf = (double)fld(tb, 0, 0);
+                    xlb = (double)fld(tb, nb - 1, 0);
+                } else {
+                    xf = rec64[b0 * kRec];
+                    xlb = rec64[(b0 + nb - 1) * kRec];
+                }
+                const bool touches = (jj == 0 || xlb >= lo_b) && (jj == nint - 1 || xf < hi_b);
+                if (touches)
+                    for (int p = 0; p < 4; ++p) M[q][p] += row[4 * (int64_t)(rho + jj) + p];
+            }
+            if (fp32) {
+                // moments about the FP32 midpoint xo -> about the left knot x_j:  t = u + mo
+                const float* r = static_cast<const float*>(srec_v) + (sp * (int64_t)(kmax + 1) + jj) * kSplineRec32;
+                const double mo = ((double)r[1] + (double)r[8]) - W.x[q];
+                const double C0 = M[q][0], C1 = M[q][1], C2 = M[q][2], C3 = M[q][3];
+                M[q][0] = C0;
+                M[q][1] = C1 + mo * C0;
+                M[q][2] = C2 + mo * (2.0 * C1 + mo * C0);
+                M[q][3] = C3 + mo * (3.0 * C2 + mo * (3.0 * C1 + mo * C0));
+            }
+        }
+        // ---- reverse through the coefficient map
+        double ybar[2], xbar[2], mbar[2], hbar[2], own[2], nxt[2];
+        for (int q = 0; q < 2; ++q) {
+            const int jj = lane + 32 * q;
+            const bool iv = jj < nint;
+            const double h = W.h[q];
+            const double M0 = M[q][0], M1 = M[q][1], M2 = M[q][2], M3 = M[q][3];
+            ybar[q] = iv ? M0 : 0.0;
+            xbar[q] = iv ? -(W.cb[q] * M0 + 2.0 * W.cc[q] * M1 + 3.0 * W.cd[q] * M2) : 0.0;
+            mbar[q] = hbar[q] = own[q] = nxt[q] = 0.0;
+            if (!iv) continue;
+            if (K < 4) {
+                mbar[q] = M1;
+            } else if (kind == LISA_SPLINE_NATURAL) {
+                const double Mj = W.d2[q];
+                own[q] = -M1 * h / 3.0 + 0.5 * M2 - M3 / (6.0 * h);   // -> d/dM_j
+                nxt[q] = -M1 * h / 6.0 + M3 / (6.0 * h);                // -> d/dM_{j+1}
+                mbar[q] = M1;
+                (void)Mj;
+            } else {
+                own[q] = M1 - 2.0 * M2 / h + M3 / (h * h);               // -> d/ds_j
+                nxt[q] = -M2 / h + M3 / (h * h);                         // -> d/ds_{j+1}
+                mbar[q] = 3.0 * M2 / h - 2.0 * M3 / (h * h);
+                hbar[q] = -W.cc[q] * M2 / h - 2.0 * W.cd[q] * M3 / h;
+            }
+        }
+        if (K >= 4 && kind == LISA_SPLINE_NATURAL) {
+            // b = m - h (2 M_j + M_{j+1}) / 6,  d = (M_{j+1} - M_j) / (6 h): h dependence
+            double Mn[2];
+            spl::shift2(W.d2[0], W.d2[1], 1, Mn[0], Mn[1]);
+            for (int q = 0; q < 2; ++q) {
+                const int jj = lane + 32 * q;
+                if (jj < nint) hbar[q] = -M[q][1] * (2.0 * W.d2[q] + Mn[q]) / 6.0 - W.cd[q] * M[q][3] / W.h[q];
+            }
+            // d/dM_k = own_k + nxt_{k-1}; M_0 and M_{K-1} are fixed
+            double nprev[2], Mbar[2];
+            spl::shift2(nxt[0], nxt[1], -1, nprev[0], nprev[1]);
+            double A[2], B[2], Cc[2], R[2];
+            double hm[2];
+            spl::shift2(W.h[0], W.h[1], -1, hm[0], hm[1]);
+            for (int q = 0; q < 2; ++q) {
+                const int k = lane + 32 * q;
+                Mbar[q] = (k >= 1 && k <= K - 2) ? own[q] + nprev[q] : 0.0;
+                if (k >= 1 && k <= K - 2) {
+                    A[q] = hm[q];
+                    B[q] = 2.0 * (hm[q] + W.h[q]);
+                    Cc[q] = W.h[q];
+                    R[q] = Mbar[q];
+                } else {
+                    A[q] = 0.0;
+                    B[q] = 1.0;
+                    Cc[q] = 0.0;
+                    R[q] = 0.0;
+                }
+            }
+            spl::pcr_solve(A, B, Cc, R, K);   // the system is symmetric: lambda = A^-1 Mbar
+            double lam[2], lamn[2], Mnn[2];
+            for (int q = 0; q < 2; ++q) lam[q] = R[q] / B[q];
+            spl::shift2(lam[0], lam[1], 1, lamn[0], lamn[1]);
+            spl::shift2(Mn[0], Mn[1], 1, Mnn[0], Mnn[1]);
+            for (int q = 0; q < 2; ++q) {
+                const int k = lane + 32 * q;
+                const double Mk = W.d2[q];
+                // r_k = 6 (m_k - m_{k-1}):  mbar_k += 6 lam_k - 6 lam_{k+1}
+                if (k >= 1 && k <= K - 2) mbar[q] += 6.0 * lam[q];
+                if (k + 1 >= 1 && k + 1 <= K - 2) mbar[q] -= 6.0 * lamn[q];
+                // row k:   h_{k-1} M_{k-1} + 2 (h_{k-1} + h_k) M_k + h_k M_{k+1}
+                //   dh_k from row k: 2 M_k + M_{k+1};  from row k+1: M_k + 2 M_{k+1}
+                if (k >= 1 && k <= K - 2) hbar[q] -= lam[q] * (2.0 * Mk + Mn[q]);
+                if (k + 1 >= 1 && k + 1 <= K - 2 && k < nint) hbar[q] -= lamn[q] * (Mk + 2.0 * Mn[q]);
+                (void)Mnn;
+            }
+        } else if (K >= 4) {
+            // Akima: d/ds_k = own_k + nxt_{k-1}, then through the slope rule to the interval slopes
+            double nprev[2], sbar[2];
+            spl::shift2(nxt[0], nxt[1], -1, nprev[0], nprev[1]);
+            double mm1[2], mm2[2], mp1[2];
+            spl::shift2(W.m[0], W.m[1], -1, mm1[0], mm1[1]);
+            spl::shift2(W.m[0], W.m[1], -2, mm2[0], mm2[1]);
+            spl::shift2(W.m[0], W.m[1], 1, mp1[0], mp1[1]);
+            double c[4][2];   // contribution of knot k to mbar_{k + delta}, delta = -2..1
+            for (int q = 0; q < 2; ++q) {
+                const int k = lane + 32 * q;
+                sbar[q] = (k < K) ? own[q] + (k >= 1 ? nprev[q] : 0.0) : 0.0;
+                double dd[4] = {0.0, 0.0, 0.0, 0.0};
+                if (k < K) akima_slope_grad(k, K, mm2[q], mm1[q], W.m[q], mp1[q], W.d2[q], dd);
+                for (int t = 0; t < 4; ++t) c[t][q] = sbar[q] * dd[t];
+            }
+            // mbar_i += c_{i+2}[-2] + c_{i+1}[-1] + c_i[0] + c_{i-1}[+1]
+            double f0[2], f1[2], f3[2];
+            spl::shift2(c[0][0], c[0][1], 2, f0[0], f0[1]);
+            spl::shift2(c[1][0], c[1][1], 1, f1[0], f1[1]);
+            spl::shift2(c[3][0], c[3][1], -1, f3[0], f3[1]);
+            for (int q = 0; q < 2; ++q) {
+                const int i = lane + 32 * q;
+                if (i >= nint) continue;
+                double add = c[2][q];
+                if (i + 2 < K) add += f0[q];
+                if (i + 1 < K) add += f1[q];
+                if (i >= 1) add += f3[q];
+                mbar[q] += add;
+            }
+        }
+        // m_j = (y_{j+1} - y_j) / h_j ;  h_j = x_{j+1} - x_j
+        double gmy[2], gmyp[2], ghp[2];
+        for (int q = 0; q < 2; ++q) {
+            const int jj = lane + 32 * q;
+            gmy[q] = (jj < nint) ? mbar[q] / W.h[q] : 0.0;
+            if (jj < nint) hbar[q] -= W.m[q] * mbar[q] / W.h[q];
+            else hbar[q] = 0.0;
+        }
+        spl::shift2(gmy[0], gmy[1], -1, gmyp[0], gmyp[1]);
+        spl::shift2(hbar[0], hbar[1], -1, ghp[0], ghp[1]);
+        for (int q = 0; q < 2; ++q) {
+            const int k = lane + 32 * q;
+            if (k >= K) {
+                ybar[q] = xbar[q] = 0.0;
+                continue;
+            }
+            ybar[q] += -gmy[q] + (k >= 1 ? gmyp[q] : 0.0);
+            xbar[q] += -hbar[q] + (k >= 1 ? ghp[q] : 0.0);
+        }
+        // scatter: sorted knot k -> caller slots
+        double* ga = gs + LISA_N_THETA + a * per_spline;
+        const double y0 = spl::bcast(ybar[0], ybar[1], 0);
+        const double yK = spl::bcast(ybar[0], ybar[1], K - 1);
+        if (lane == 0) {
+            ga[0] = y0;
+            ga[kmax + 1] = yK;
+        }
+        const int k_in = K - 2;
+        for (int half = 0; half < 2; ++half) {
+            const int i = lane + 32 * half;          // caller's in-between knot index
+            const int r = half ? W.rb : W.ra;        // its sorted position (1..K-2)
+            const int rs = (i < k_in) ? r : 0;
+            const double gy = __shfl_sync(kFullMask, rs < 32 ? ybar[0] : ybar[1], rs & 31);
+            const double gx = __shfl_sync(kFullMask, rs < 32 ? xbar[0] : xbar[1], rs & 31);
+            if (i < k_in) {
+                ga[1 + i] = gy;
+                ga[kmax + 2 + i] = gx;
+            }
+        }
+    }
+}
+
+template <int C, bool H, bool B>
+cudaError_t launch_adjoint(const lisa_data* d, bool fp32, const lisa_params* params, const lisa_knots* kn,
+                           const int32_t* sstat, const int32_t* nint, const void* srec, double* scal, double* mom,
+                           double* out, double* grad, cudaStream_t sm) {
+    const int grid = d->n_sm * 8;
+    if (d->n_adj_units > 0) {
+        if (fp32)
+            adjoint_fp32_kernel<C, H, B><<<grid, 128, 0, sm>>>(d->d_adj_units, d->n_adj_units, d->d_ds, d->d_rec32,
+                                                               d->d_xlo32, params->theta_dev, sstat, nint,
+                                                               static_cast<const float*>(srec), kn->kmax, d->nsp,
+                                                               d->d_adj_prefix, scal, mom);
+        else
+            adjoint_fp64_kernel<C, H, B><<<grid, 128, 0, sm>>>(d->d_adj_units, d->n_adj_units, d->d_ds, d->d_rec64,
+                                                               params->theta_dev, sstat, nint,
+                                                               static_cast<const double*>(srec), kn->kmax, d->nsp,
+                                                               d->d_adj_prefix, scal, mom);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    const unsigned eb = (unsigned)((d->n_states + 3) / 4);
+    adjoint_epilogue_kernel<C, H, B><<<eb, 128, 0, sm>>>(
+        (int)d->n_states, d->d_state_ds, d->d_ds, sstat, params->theta_dev, kn->count_dev, kn->x_dev, kn->w_dev,
+        kn->kmax, kn->kind, d->nsp, d->d_adj_prefix, scal, mom, d->d_rec32, d->d_rec64, srec, fp32 ? 1 : 0, out,
+        grad);
+    return cudaGetLastError();
+}
+
+template <int C>
+cudaError_t dispatch_adjoint(const lisa_data* d, bool fp32, const lisa_params* params, const lisa_knots* kn,
+                             const int32_t* sstat, const int32_t* nint, const void* srec, double* scal, double* mom,
+                             double* out, double* grad, cudaStream_t sm) {
+    if (d->sgwb_model == 0)
+        return launch_adjoint<C, false, false>(d, fp32, params, kn, sstat, nint, srec, scal, mom, out, grad, sm);
+    if (d->sgwb_model == 1)
+        return launch_adjoint<C, true, false>(d, fp32, params, kn, sstat, nint, srec, scal, mom, out, grad, sm);
+    return launch_adjoint<C, true, true>(d, fp32, params, kn, sstat, nint, srec, scal, mom, out, grad, sm);
+}
+
+}  // namespace
 }  // namespace lisa
 
-extern "C" lisa_status lisa_psd_loglike_grad(const lisa_data*, const lisa_params*, const lisa_knots*, const void*,
-                                             size_t, double*, double*, void*, size_t, lisa_precision,
-                                             lisa_stream_t) {
-    return LISA_ERR_VALUE;
+using namespace lisa;
+
+extern "C" lisa_status lisa_psd_loglike_grad(const lisa_data* d, const lisa_params* params, const lisa_knots* kn,
+                                             const void* buf, size_t buf_bytes, double* out, double* grad,
+                                             void* ws, size_t ws_bytes, lisa_precision prec, lisa_stream_t stream) {
+    if (!d || !params || !kn || !buf || !out || !grad || !ws) return LISA_ERR_NULL;
+    if (prec != LISA_FP32 && prec != LISA_FP64) return LISA_ERR_VALUE;
+    if (kn->kmax < 0 || kn->kmax > LISA_MAX_KNOTS || (kn->kind != LISA_SPLINE_AKIMA && kn->kind != LISA_SPLINE_NATURAL))
+        return LISA_ERR_VALUE;
+    if (params->n_states != d->n_states || kn->n_states != d->n_states || kn->n_splines != d->nsp)
+        return LISA_ERR_SHAPE;
+    if (d->n_states > 0 && (!params->theta_dev || !kn->count_dev || !kn->w_dev || (kn->kmax > 0 && !kn->x_dev)))
+        return LISA_ERR_NULL;
+    const SplineLayout L = spline_layout(d->n_states, d->nsp, kn->kmax);
+    if (buf_bytes < L.bytes || (reinterpret_cast<uintptr_t>(buf) & 255)) return LISA_ERR_WORKSPACE;
+    if (ws_bytes < 256 + grad_extra_bytes(d, kn->kmax) || (reinterpret_cast<uintptr_t>(ws) & 255))
+        return LISA_ERR_WORKSPACE;
+    if (d->n_states == 0) return LISA_SUCCESS;
+    const char* base = static_cast<const char*>(buf);
+    const int32_t* sstat = reinterpret_cast<const int32_t*>(base + L.off_status);
+    const int32_t* nint = reinterpret_cast<const int32_t*>(base + L.off_nint);
+    const void* srec = base + L.off_rec;
+    char* w = static_cast<char*>(ws) + 256;
+    double* scal = reinterpret_cast<double*>(w);
+    double* mom = reinterpret_cast<double*>(w + align256(sizeof(double) * 6 * (size_t)d->adj_ranges));
+    cudaStream_t sm = (cudaStream_t)stream;
+    const bool fp32 = prec == LISA_FP32;
+    cudaError_t e = d->C == 3 ? dispatch_adjoint<3>(d, fp32, params, kn, sstat, nint, srec, scal, mom, out, grad, sm)
+                              : dispatch_adjoint<2>(d, fp32, params, kn, sstat, nint, srec, scal, mom, out, grad, sm);
+    return e == cudaSuccess ? LISA_SUCCESS : LISA_ERR_CUDA;
 }

@@ -43,6 +43,7 @@ constexpr int kUserBits = 0xffff;       // LISA_STATE_* bits
 constexpr int kStatusNonfinite = LISA_STATE_NONFINITE;
 constexpr unsigned kWaitLimit = 1u << 20;   // bounded spin on an mbarrier (then give up)
 constexpr int kMaxTileBins = 2048;          // 2 staged tiles x 48 B/bin must fit in 227 KB
+constexpr int kAdjBins = 2048;              // bins per (state, range) in the adjoint
 
 // One unit of work of the fused kernels: a tile of bins of one dataset and a chunk of its
 // states.  Threads map to (state lane, bin sub-range): lane = tid % sc, range = tid / sc.
@@ -57,6 +58,12 @@ struct WorkItem {
 };
 static_assert(sizeof(WorkItem) == 32, "WorkItem layout");
 
+// One unit of the adjoint: a range of kAdjBins bins of one dataset and up to 32 of its states
+// (one warp, lanes = states).
+struct AdjUnit {
+    int32_t ds, rho, s0, ns;
+};
+
 struct DatasetDev {
     int64_t bin0, nbins;     // bin range: bin0 in padded indexing, nbins real bins
     int64_t npad;            // nbins rounded up to even (bins [bin0, bin0 + npad) in the tables)
@@ -65,7 +72,7 @@ struct DatasetDev {
     int64_t psd_base;        // first element of the dataset's states in a model-PSD output
     int32_t s0, ns;          // state range
     int32_t ntiles;          // tiles of tile_bins bins
-    int32_t pad;
+    int32_t nranges;         // adjoint ranges of kAdjBins bins
     double x_lo, x_hi;       // edge knot positions
     double xb_min, xb_max;   // log10 f of the first and last bin
     double f_ref;
@@ -92,6 +99,10 @@ struct lisa_data {
     float* d_elllo32 = nullptr;      // [n_bins] low part of ell = log2(f / f_ref)
     lisa_tiling tiling{};
     lisa::WorkItem* d_items = nullptr;
+    lisa::AdjUnit* d_adj_units = nullptr;
+    int64_t n_adj_units = 0;
+    int64_t* d_adj_prefix = nullptr; // [n_states] adjoint ranges of all earlier states
+    int64_t adj_ranges = 0;          // sum over states of their dataset's ranges
     int64_t n_items = 0;
     int64_t n_partials = 0;          // sum over datasets of states x tiles
 };
