@@ -215,6 +215,7 @@ def run_ours(args):
     ev32 = B.Evaluator(ds, kmax, kind, B.FP32)
     ev32.load(theta, count, x, w)
     ev32.capture()
+    routed = ds.routed_states(ev32.buf)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # > 129 MB L2
 
     def timed(ev, steps, warmup):
@@ -317,7 +318,7 @@ def run_ours(args):
             "speedup_fp32_vs_fp64": value / value64,
             "accuracy_fp32_vs_fp64": {"max_abs_nats": float(err.max()), "median_abs_nats": float(np.median(err)),
                                       "max_rel_to_scale": float((err / scale).max()), "states": int(ok.sum())},
-            "loglike_ms": ll_ms, "setup_ms": ms - ll_ms,
+            "loglike_ms": ll_ms, "setup_ms": ms - ll_ms, "routed_states": routed,
             "roofline": {"bound": "alu", "pipe": "MUFU (XU)", "achieved": achieved, "peak": mufu_peak,
                          "unit": "Gop/s", "frac": achieved / mufu_peak, "traffic": traffic,
                          "peak_source": f"derived: {N_SM} SMs x {MUFU_PER_SM_PER_CLK} MUFU/clk x {sm_max:.0f} MHz",

@@ -250,6 +250,13 @@ class Dataset:
                                         status.data_ptr(), _stream_handle(stream)), "lisa_spline_setup")
         return buf, status
 
+    def routed_states(self, buf):
+        """Number of states the last FP32 lisa_spline_setup on ``buf`` routed to the compensated
+        kernel (diagnostic; synchronises)."""
+        a256 = lambda b: (b + 255) // 256 * 256
+        off = a256(4 * self.n_states) + a256(4 * self.n_states * self.n_splines)
+        return int(buf[off:off + 4].cpu().view(dtype=__import__("torch").int32)[0])
+
     def psd_loglike(self, theta, buf, kmax, precision=FP32, out=None, workspace=None, stream=None):
         """``lisa_psd_loglike``: theta [S, 5] f64 device -> log L [S] f64 device."""
         torch = _torch()

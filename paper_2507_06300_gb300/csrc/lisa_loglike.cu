@@ -408,7 +408,7 @@ __device__ __forceinline__ ff inv_plus_log(ff lS, double& far) {
     return ff{0.f, 0.f};
 }
 
-// One warp per (routed state, tile); each lane walks a contiguous run of bins.  Spline values
+// One warp per (routed state, tile); lane l takes bins l, l + 32, ... of the tile.  Spline values
 // are float-float sums where the interval is ill-conditioned; a bin whose intervals are all
 // well-conditioned uses the ordinary FP32 term, any other bin the log-domain term.
 template <int C, bool HAS_H, bool BROKEN>
@@ -438,14 +438,14 @@ __global__ void __launch_bounds__(128)
         const ff n2 = BROKEN ? ff_from_double(th[4]) : n1;
         const int64_t b0 = D.bin0 + (int64_t)t * tile_bins;   // even
         const int nb = (int)min((int64_t)tile_bins, D.bin0 + D.npad - b0);
-        const int np = nb >> 1;
-        const int lo = 2 * ((lane * np) / 32), hi = 2 * (((lane + 1) * np) / 32);
         const float* tbase = rec32 + (b0 >> 1) * kPairRec;
         double acc = 0.0;
-        if (lo < hi) {
+        if (lane < nb) {
+            // lanes take consecutive bins (lane, lane + 32, ...): coalesced table reads, and the
+            // lanes of a warp mostly share their spline intervals
             IvR iv[NSP];
             Iv32 iv32[NSP];
-            const float x0 = fld(tbase, lo, 0);
+            const float x0 = fld(tbase, lane, 0);
 #pragma unroll
             for (int a = 0; a < NSP; ++a) {
                 const int64_t sp = (int64_t)s * nsp + a;
@@ -454,73 +454,70 @@ __global__ void __launch_bounds__(128)
                 iv[a].j = find_interval<float, kSplineRec32, 6>(iv[a].base, nint[sp], x0);
                 load_ivr(iv[a]);
             }
-            for (int i0 = lo; i0 < hi; i0 += 32) {
-                ff acc_ff = {0.f, 0.f};
-                double far = 0.0;
-                const int i1 = min(i0 + 32, hi);
-                for (int i = i0; i < i1; ++i) {
-                    const int64_t g = b0 + i;
-                    const ff x = {fld(tbase, i, 0), __ldg(xlo32 + g)};
-                    const float nu = fld(tbase, i, 2);
-                    ff P[NSP];
-                    bool hard = false;
+            ff acc_ff = {0.f, 0.f};
+            double far = 0.0;
+            for (int i = lane; i < nb; i += 32) {
+                const int64_t g = b0 + i;
+                const ff x = {fld(tbase, i, 0), __ldg(xlo32 + g)};
+                const float nu = fld(tbase, i, 2);
+                ff P[NSP];
+                bool hard = false;
+#pragma unroll
+                for (int a = 0; a < NSP; ++a) {
+                    while (x.hi >= iv[a].xr && iv[a].j < iv[a].last) {
+                        ++iv[a].j;
+                        load_ivr(iv[a]);
+                    }
+                    if (!(iv[a].T <= (float)kRobustT)) {
+                        hard = true;
+                        const ff tt = ff_add(x, ff{-iv[a].xo.hi, -iv[a].xo.lo});
+                        ff p = iv[a].c[3];
+                        p = ff_add(ff_mul(p, tt), iv[a].c[2]);
+                        p = ff_add(ff_mul(p, tt), iv[a].c[1]);
+                        P[a] = ff_add(ff_mul(p, tt), iv[a].c[0]);
+                    } else {
+                        const float tt = x.hi - iv[a].xo.hi;
+                        P[a] = ff{fmaf(fmaf(fmaf(iv[a].c[3].hi, tt, iv[a].c[2].hi), tt, iv[a].c[1].hi), tt,
+                                       iv[a].c[0].hi), 0.f};
+                    }
+                }
+                if (!hard) {
 #pragma unroll
                     for (int a = 0; a < NSP; ++a) {
-                        while (x.hi >= iv[a].xr && iv[a].j < iv[a].last) {
-                            ++iv[a].j;
-                            load_ivr(iv[a]);
-                        }
-                        if (!(iv[a].T <= (float)kRobustT)) {
-                            hard = true;
-                            const ff tt = ff_add(x, ff{-iv[a].xo.hi, -iv[a].xo.lo});
-                            ff p = iv[a].c[3];
-                            p = ff_add(ff_mul(p, tt), iv[a].c[2]);
-                            p = ff_add(ff_mul(p, tt), iv[a].c[1]);
-                            P[a] = ff_add(ff_mul(p, tt), iv[a].c[0]);
-                        } else {
-                            const float tt = x.hi - iv[a].xo.hi;
-                            P[a] = ff{fmaf(fmaf(fmaf(iv[a].c[3].hi, tt, iv[a].c[2].hi), tt, iv[a].c[1].hi), tt,
-                                           iv[a].c[0].hi), 0.f};
-                        }
+                        iv32[a].xo = 0.f;
+                        iv32[a].c0 = P[a].hi;
+                        iv32[a].c1 = iv32[a].c2 = iv32[a].c3 = 0.f;
                     }
-                    if (!hard) {
-#pragma unroll
-                        for (int a = 0; a < NSP; ++a) {
-                            iv32[a].xo = 0.f;
-                            iv32[a].c0 = P[a].hi;
-                            iv32[a].c1 = iv32[a].c2 = iv32[a].c3 = 0.f;
-                        }
-                        // the ordinary FP32 term with the spline values already evaluated
-                        acc_ff = ff_add(acc_ff, ff{bin_term32<C, HAS_H, BROKEN>(tbase, i, iv32, ao2, at2, (float)n1.hi,
-                                                                                (float)n2.hi, Af), 0.f});
-                        continue;
-                    }
-                    const ff ell = {fld(tbase, i, 1), __ldg(elllo32 + g)};
-                    ff lEh = {-INFINITY, 0.f};
-                    if (HAS_H) {
-                        const ff sl = BROKEN ? (ell.hi < 0.f ? n1 : n2) : n1;
-                        lEh = ff_add(ff_add(P[C], ff_mul(sl, ell)), lA);
-                    }
-                    ff term = {-(float)C, 0.f};
-#pragma unroll
-                    for (int c = 0; c < C; ++c) {
-                        const float N = fmaf(ao2, fld(tbase, i, 3 + c), at2 * fld(tbase, i, 6 + c));
-                        const ff lN = lg2_split(N);
-                        const ff lNE = (lN.hi > -INFINITY && lN.hi < INFINITY) ? ff_add(P[c], lN) : lN;
-                        ff lS = lNE;
-                        if (HAS_H) {
-                            const ff lG = lg2_split(fld(tbase, i, 9 + c));
-                            const ff lH = (lG.hi > -INFINITY && lG.hi < INFINITY) ? ff_add(lEh, lG) : lG;
-                            lS = log2_sum(lNE, lH);
-                        }
-                        double far_c = 0.0;
-                        term = ff_add(term, inv_plus_log(lS, far_c));
-                        far += (double)nu * far_c;
-                    }
-                    acc_ff = ff_add(acc_ff, ff_mul(term, ff{nu, 0.f}));
+                    // the ordinary FP32 term with the spline values already evaluated
+                    acc_ff = ff_add(acc_ff, ff{bin_term32<C, HAS_H, BROKEN>(tbase, i, iv32, ao2, at2, (float)n1.hi,
+                                                                            (float)n2.hi, Af), 0.f});
+                    continue;
                 }
-                acc += ((double)acc_ff.hi + (double)acc_ff.lo) + far;
+                const ff ell = {fld(tbase, i, 1), __ldg(elllo32 + g)};
+                ff lEh = {-INFINITY, 0.f};
+                if (HAS_H) {
+                    const ff sl = BROKEN ? (ell.hi < 0.f ? n1 : n2) : n1;
+                    lEh = ff_add(ff_add(P[C], ff_mul(sl, ell)), lA);
+                }
+                ff term = {-(float)C, 0.f};
+#pragma unroll
+                for (int c = 0; c < C; ++c) {
+                    const float N = fmaf(ao2, fld(tbase, i, 3 + c), at2 * fld(tbase, i, 6 + c));
+                    const ff lN = lg2_split(N);
+                    const ff lNE = (lN.hi > -INFINITY && lN.hi < INFINITY) ? ff_add(P[c], lN) : lN;
+                    ff lS = lNE;
+                    if (HAS_H) {
+                        const ff lG = lg2_split(fld(tbase, i, 9 + c));
+                        const ff lH = (lG.hi > -INFINITY && lG.hi < INFINITY) ? ff_add(lEh, lG) : lG;
+                        lS = log2_sum(lNE, lH);
+                    }
+                    double far_c = 0.0;
+                    term = ff_add(term, inv_plus_log(lS, far_c));
+                    far += (double)nu * far_c;
+                }
+                acc_ff = ff_add(acc_ff, ff_mul(term, ff{nu, 0.f}));
             }
+            acc = ((double)acc_ff.hi + (double)acc_ff.lo) + far;
         }
         for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
         if (lane == 0) partial[D.pbase + (int64_t)(s - D.s0) * D.ntiles + t] = acc;

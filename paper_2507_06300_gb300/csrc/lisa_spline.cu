@@ -40,7 +40,7 @@ __global__ void __launch_bounds__(128) spline_setup_kernel(
             const int K = W.K;
             double xn[2];
             spl::shift2(W.x[0], W.x[1], 1, xn[0], xn[1]);
-            for (int q = 0; q < 2; ++q) {
+            for (int q = 0; q < (K > 32 ? 2 : 1); ++q) {
                 const int j = lane + 32 * q;
                 if (j >= K - 1) continue;
                 const bool last = (j + 1 == K - 1);
@@ -67,15 +67,17 @@ __global__ void __launch_bounds__(128) spline_setup_kernel(
                     const double cs[4] = {c0 * kLog2_10, c1 * kLog2_10, c2 * kLog2_10, c3 * kLog2_10};
                     const double lo_x = (j == 0) ? fmin(xbmin, x[q]) : x[q];
                     const double hi_x = last ? fmax(xbmax, xn[q]) : xn[q];
-                    const double rr = fmax(fabs(lo_x - xo), fabs(hi_x - xo));
-                    const double Tc = fabs(cs[0]) + rr * (fabs(cs[1]) + rr * (fabs(cs[2]) + rr * fabs(cs[3])));
-                    robust |= !(Tc <= kRobustT);
+                    // the conditioning bound only steers the routing: FP32 is precise enough
+                    const float rr = (float)fmax(fabs(lo_x - xo), fabs(hi_x - xo));
+                    const float Tc = fabsf((float)cs[0]) +
+                                     rr * (fabsf((float)cs[1]) + rr * (fabsf((float)cs[2]) + rr * fabsf((float)cs[3])));
+                    robust |= !(Tc <= (float)kRobustT);
                     float* r = static_cast<float*>(rec_v) + (sp * (int64_t)(kmax + 1) + j) * kSplineRec32;
                     const float xo_hi = (float)xo;
                     r[0] = last ? INFINITY : (float)xn[q];
                     r[1] = xo_hi;
                     r[6] = (float)x[q];
-                    r[7] = (float)Tc;
+                    r[7] = Tc;
                     r[8] = (float)(xo - (double)xo_hi);
                     for (int c = 0; c < 4; ++c) {
                         const float hi = (float)cs[c];

@@ -140,17 +140,23 @@ __device__ __forceinline__ void warp_build_spline(WarpSpline& W, const double* _
         if (__any_sync(kFull, bw)) st |= LISA_STATE_BAD_AMPLITUDE;
     }
     if (!st) {
-        // rank sort (stable), duplicate detection
+        // rank sort (stable) with duplicate detection, on integer keys that order like the
+        // (finite) doubles, so the comparisons run on the integer pipes
+        auto key = [](double v) {
+            const long long b = __double_as_longlong(v);
+            return b >= 0 ? b : b ^ 0x7fffffffffffffffLL;
+        };
+        const long long ka = key(xa), kb = key(xb);
         bool dup = false;
         for (int i = 0; i < k; ++i) {
-            const double xi = bcast(xa, xb, i);
+            const long long ki = __shfl_sync(kFull, i < 32 ? ka : kb, i & 31);
             if (lane < k) {
-                ra += (xi < xa) || (xi == xa && i < lane);
-                dup |= (xi == xa) && (i != lane);
+                ra += (ki < ka) || (ki == ka && i < lane);
+                dup |= (ki == ka) && (i != lane);
             }
             if (lane + 32 < k) {
-                rb += (xi < xb) || (xi == xb && i < lane + 32);
-                dup |= (xi == xb) && (i != lane + 32);
+                rb += (ki < kb) || (ki == kb && i < lane + 32);
+                dup |= (ki == kb) && (i != lane + 32);
             }
         }
         if (__any_sync(kFull, dup)) st |= LISA_STATE_DUPLICATE;
@@ -189,13 +195,17 @@ __device__ __forceinline__ void warp_build_spline(WarpSpline& W, const double* _
     T* m = W.m;
     shift2(x[0], x[1], 1, xn[0], xn[1]);
     shift2(y[0], y[1], 1, yn[0], yn[1]);
-    for (int q = 0; q < 2; ++q) {
+    T ih[2];   // 1 / h
+    h[1] = ih[1] = T(1);
+    m[1] = T(0);
+    for (int q = 0; q < (K > 32 ? 2 : 1); ++q) {
         const int j = lane + 32 * q;
         if (j < K - 1) {
             h[q] = xn[q] - x[q];
-            m[q] = (yn[q] - y[q]) / h[q];
+            ih[q] = T(1) / h[q];
+            m[q] = (yn[q] - y[q]) * ih[q];
         } else {
-            h[q] = T(1);
+            h[q] = ih[q] = T(1);
             m[q] = T(0);
         }
     }
@@ -204,9 +214,11 @@ __device__ __forceinline__ void warp_build_spline(WarpSpline& W, const double* _
     T* cc = W.cc;
     T* cd = W.cd;
     W.d2[0] = W.d2[1] = T(0);
+    W.ca[1] = W.cb[1] = W.cc[1] = W.cd[1] = T(0);
+    const int nq = K > 32 ? 2 : 1;   // the second lane slot is only used by splines with K > 32
     if (K < 4) {
         // Sec. III.A: fewer than two in-between knots -> linear interpolant
-        for (int q = 0; q < 2; ++q) {
+        for (int q = 0; q < nq; ++q) {
             ca[q] = y[q];
             cb[q] = m[q];
             cc[q] = T(0);
@@ -236,14 +248,14 @@ __device__ __forceinline__ void warp_build_spline(WarpSpline& W, const double* _
         }
         pcr_solve(A, B, Cc, Rr, K);
         T Mn[2];
-        for (int q = 0; q < 2; ++q) W.d2[q] = Rr[q] / B[q];
+        for (int q = 0; q < nq; ++q) W.d2[q] = Rr[q] / B[q];
         shift2(W.d2[0], W.d2[1], 1, Mn[0], Mn[1]);
-        for (int q = 0; q < 2; ++q) {
+        for (int q = 0; q < nq; ++q) {
             const T M = W.d2[q];
             ca[q] = y[q];
-            cb[q] = m[q] - h[q] * (T(2) * M + Mn[q]) / T(6);
+            cb[q] = m[q] - h[q] * (T(2) * M + Mn[q]) * T(1.0 / 6.0);
             cc[q] = T(0.5) * M;
-            cd[q] = (Mn[q] - M) / (T(6) * h[q]);
+            cd[q] = (Mn[q] - M) * ih[q] * T(1.0 / 6.0);
         }
     } else {
         // Akima (Appendix A)
@@ -254,17 +266,17 @@ __device__ __forceinline__ void warp_build_spline(WarpSpline& W, const double* _
         const T m_0 = bcast(m[0], m[1], 0), m_1 = bcast(m[0], m[1], 1);
         const T m_Km2 = bcast(m[0], m[1], K - 2), m_Km3 = bcast(m[0], m[1], K - 3);
         T sn[2];
-        for (int q = 0; q < 2; ++q) {
+        for (int q = 0; q < nq; ++q) {
             const int j = lane + 32 * q;
             W.d2[q] = (j < K) ? akima_slope(j, K, mm2[q], mm1[q], m[q], mp1[q], m_0, m_1, m_Km2, m_Km3) : T(0);
         }
         shift2(W.d2[0], W.d2[1], 1, sn[0], sn[1]);
-        for (int q = 0; q < 2; ++q) {
+        for (int q = 0; q < nq; ++q) {
             const T sl = W.d2[q];
             ca[q] = y[q];
             cb[q] = sl;
-            cc[q] = (T(3) * m[q] - T(2) * sl - sn[q]) / h[q];
-            cd[q] = (sl + sn[q] - T(2) * m[q]) / (h[q] * h[q]);
+            cc[q] = (T(3) * m[q] - T(2) * sl - sn[q]) * ih[q];
+            cd[q] = (sl + sn[q] - T(2) * m[q]) * (ih[q] * ih[q]);
         }
     }
 }
