@@ -220,7 +220,7 @@ class Dataset:
                 "tiling": {"tile_bins": t.tile_bins, "states_per_cta": t.states_per_cta, "group": t.group,
                            "ctas_per_sm": t.ctas_per_sm}}
 
-    def set_tiling(self, tile_bins=1024, states_per_cta=256, group=4, ctas_per_sm=0):
+    def set_tiling(self, tile_bins=512, states_per_cta=128, group=4, ctas_per_sm=0):
         t = lisa_tiling(int(tile_bins), int(states_per_cta), int(group), int(ctas_per_sm))
         _check(load().lisa_data_set_tiling(self._h, ctypes.byref(t)), "lisa_data_set_tiling")
 

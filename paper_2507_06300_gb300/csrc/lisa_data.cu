@@ -305,7 +305,7 @@ lisa_status lisa_data_create(const lisa_data_desc* desc, lisa_stream_t stream, l
         for (int32_t s = X.s0; s < X.s0 + X.ns; ++s) state_ds[s] = k;
     }
     d->n_pad = pad0;
-    d->tiling = lisa_tiling{1024, 256, 4, 0};
+    d->tiling = lisa_tiling{512, 128, 4, 0};
     const int64_t NP = pad0 > 0 ? pad0 : 1;
 
     lisa_status st = LISA_SUCCESS;
@@ -405,7 +405,7 @@ lisa_status lisa_data_set_tiling(lisa_data* d, const lisa_tiling* t) {
     int sc = t->states_per_cta;
     bool pow2 = sc > 0 && (sc & (sc - 1)) == 0;
     if (t->tile_bins < 64 || t->tile_bins > kMaxTileBins || (t->tile_bins % 32) != 0 || !pow2 || sc < 16 ||
-        sc > kThreads || !(t->group == 2 || t->group == 4 || t->group == 8) ||
+        sc > kMaxStatesPerItem || !(t->group == 2 || t->group == 4 || t->group == 8) ||
         t->ctas_per_sm < 0 || t->ctas_per_sm > 32)
         return LISA_ERR_VALUE;
     lisa_tiling old = d->tiling;

@@ -25,7 +25,9 @@ constexpr int kRec = 12;         // per-bin fields: x, ell, nu, Goms[3], Gtm[3],
 // Both tables use padded bin indices: every dataset is padded to an even bin count with a
 // dummy bin (copy of its last bin with nu = 0).
 constexpr int kPairRec = 2 * kRec;
-constexpr int kThreads = 256;    // threads of the fused likelihood kernels
+constexpr int kThreads = 256;    // threads of the plain FP64 likelihood kernel
+constexpr int kThreads32 = 128;  // threads of the fused FP32 likelihood kernel
+constexpr int kMaxStatesPerItem = 128;  // state lanes of a work item (<= both thread counts)
 // Per-interval records, 64 bytes in both precisions:
 //   FP64: xl, xr, a, b, c, d, 0, 0 (coefficients about xl, log10 units)
 //   FP32: [0] xr  [1] xo  [2..5] c0..c3  [6] xl  [7] conditioning T      (first 32 bytes)
@@ -52,7 +54,7 @@ struct WorkItem {
     int32_t nb;     // bins in the tile
     int32_t s0;     // first state (global index)
     int32_t ns;     // states in the chunk (<= sc)
-    int32_t sc;     // state lanes of this dataset's items (power of two, divides kThreads)
+    int32_t sc;     // state lanes of this dataset's items (power of two, <= kMaxStatesPerItem)
     int32_t tile;   // tile index within the dataset
     int32_t ds;     // dataset index
 };

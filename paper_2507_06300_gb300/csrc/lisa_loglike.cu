@@ -93,31 +93,10 @@ __device__ __forceinline__ void load_iv(Iv32& v) {
     v.c3 = B.y;
 }
 
-// One bin, scalar (used next to knots, where the two bins of a pair may sit in different
-// intervals).
-template <int C, bool HAS_H, bool BROKEN>
-__device__ __forceinline__ float bin_term32(const float* __restrict__ tb, int i, const Iv32* iv, float ao2,
-                                            float at2, float n1, float n2, float Af) {
-    constexpr int NSP = C + (HAS_H ? 1 : 0);
-    const float x = fld(tb, i, 0), ell = fld(tb, i, 1), nu = fld(tb, i, 2);
-    float p[NSP];
-#pragma unroll
-    for (int a = 0; a < NSP; ++a) {
-        const float t = x - iv[a].xo;
-        p[a] = fmaf(fmaf(fmaf(iv[a].c3, t, iv[a].c2), t, iv[a].c1), t, iv[a].c0);
-    }
-    float eh = 0.f;
-    if (HAS_H) {
-        const float sl = BROKEN ? (ell < 0.f ? n1 : n2) : n1;
-        eh = Af * ex2_approx(fmaf(sl, ell, p[C]));
-    }
-    float S[C];
-#pragma unroll
-    for (int c = 0; c < C; ++c) {
-        const float nc = fmaf(ao2, fld(tb, i, 3 + c), at2 * fld(tb, i, 6 + c));
-        const float e = ex2_approx(p[c]);
-        S[c] = HAS_H ? fmaf(e, nc, eh * fld(tb, i, 9 + c)) : e * nc;
-    }
+// nu * (sum_c 1/S_c + ln prod_c S_c - C) in FP32: one reciprocal and one lg2 of the product,
+// per-channel when the product leaves [1e-30, 1e30].
+template <int C>
+__device__ __forceinline__ float term_from_S(const float* S, float nu) {
     float prod, num;
     if (C == 3) {
         const float p01 = S[0] * S[1];
@@ -143,10 +122,55 @@ __device__ __forceinline__ float bin_term32(const float* __restrict__ tb, int i,
     return nu * fmaf((float)kLn2, lg, v);
 }
 
+// One bin, scalar (used next to knots, where the two bins of a pair may sit in different
+// intervals).
+template <int C, bool HAS_H, bool BROKEN>
+__device__ __forceinline__ float bin_term32(const float* __restrict__ tb, int i, const Iv32* iv, float ao2,
+                                            float at2, float n1, float n2, float Af) {
+    constexpr int NSP = C + (HAS_H ? 1 : 0);
+    const float x = fld(tb, i, 0), ell = fld(tb, i, 1), nu = fld(tb, i, 2);
+    float p[NSP];
+#pragma unroll
+    for (int a = 0; a < NSP; ++a) {
+        const float t = x - iv[a].xo;
+        p[a] = fmaf(fmaf(fmaf(iv[a].c3, t, iv[a].c2), t, iv[a].c1), t, iv[a].c0);
+    }
+    float eh = 0.f;
+    if (HAS_H) {
+        const float sl = BROKEN ? (ell < 0.f ? n1 : n2) : n1;
+        eh = Af * ex2_approx(fmaf(sl, ell, p[C]));
+    }
+    float S[C];
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+        const float nc = fmaf(ao2, fld(tb, i, 3 + c), at2 * fld(tb, i, 6 + c));
+        const float e = ex2_approx(p[c]);
+        S[c] = HAS_H ? fmaf(e, nc, eh * fld(tb, i, 9 + c)) : e * nc;
+    }
+    return term_from_S<C>(S, nu);
+}
+
 // Current interval of one spline duplicated into register pairs for the packed path.
 struct Iv2 {
     float2 nxo, c0, c1, c2, c3;
 };
+
+// One bin, scalar, with the intervals held as duplicated pairs (their .x halves).
+template <int C, bool HAS_H, bool BROKEN>
+__device__ __forceinline__ float bin_term32p(const float* __restrict__ tb, int i, const Iv2* iv, float ao2, float at2,
+                                             float n1, float n2, float Af) {
+    constexpr int NSP = C + (HAS_H ? 1 : 0);
+    Iv32 v[NSP];
+#pragma unroll
+    for (int a = 0; a < NSP; ++a) {
+        v[a].xo = -iv[a].nxo.x;
+        v[a].c0 = iv[a].c0.x;
+        v[a].c1 = iv[a].c1.x;
+        v[a].c2 = iv[a].c2.x;
+        v[a].c3 = iv[a].c3.x;
+    }
+    return bin_term32<C, HAS_H, BROKEN>(tb, i, v, ao2, at2, n1, n2, Af);
+}
 __device__ __forceinline__ Iv2 dup(const Iv32& v) {
     return Iv2{make_float2(-v.xo, -v.xo), make_float2(v.c0, v.c0), make_float2(v.c1, v.c1),
                make_float2(v.c2, v.c2), make_float2(v.c3, v.c3)};
@@ -208,7 +232,7 @@ __device__ __forceinline__ float2 pair_term32(const float4* __restrict__ blk, co
 }
 
 template <int C, bool HAS_H, bool BROKEN, int G>
-__global__ void __launch_bounds__(kThreads, 2)
+__global__ void __launch_bounds__(kThreads32, 5)
     loglike_fp32_kernel(const WorkItem* __restrict__ items, int n_items, const float* __restrict__ rec32,
                         const double* __restrict__ theta, const int32_t* __restrict__ sstat,
                         const int32_t* __restrict__ nint, const float* __restrict__ srec, int kmax, int nsp,
@@ -217,7 +241,7 @@ __global__ void __launch_bounds__(kThreads, 2)
     constexpr int NSP = C + (HAS_H ? 1 : 0);
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ __align__(8) uint64_t bars[2];
-    __shared__ double red[kThreads];
+    __shared__ double red[kThreads32];
     float* sbuf0 = reinterpret_cast<float*>(smem);
     float* sbuf1 = reinterpret_cast<float*>(smem + (size_t)tile_bins * kRec * sizeof(float));
     const int tid = threadIdx.x;
@@ -257,7 +281,7 @@ __global__ void __launch_bounds__(kThreads, 2)
         const float4* tb4 = reinterpret_cast<const float4*>(tb);
 
         const int sc = w.sc;
-        const int R = kThreads / sc;
+        const int R = kThreads32 / sc;
         const int ls = tid & (sc - 1);
         const int r = tid / sc;
         const int s = w.s0 + ls;
@@ -274,17 +298,38 @@ __global__ void __launch_bounds__(kThreads, 2)
                 const float n1 = (float)th[3];
                 const float n2 = BROKEN ? (float)th[4] : n1;
                 const float2 ao2_2 = make_float2(ao2, ao2), at2_2 = make_float2(at2, at2), Af2 = make_float2(Af, Af);
-                Iv32 iv[NSP];
+                // per spline: right knot of the current interval, its index, and the interval's
+                // cubic duplicated into register pairs (the scalar path reads the .x halves)
+                float xr[NSP];
+                int jj[NSP];
                 Iv2 iv2[NSP];
                 const float x0 = fld(tb, lo, 0);
+                const int64_t sp0 = (int64_t)s * nsp;
+                auto reload = [&](int a) {
+                    const float* r = srec + ((sp0 + a) * (int64_t)(kmax + 1) + jj[a]) * kSplineRec32;
+                    const float4 A = __ldg(reinterpret_cast<const float4*>(r));
+                    const float4 B = __ldg(reinterpret_cast<const float4*>(r + 4));
+                    xr[a] = A.x;
+                    iv2[a] = Iv2{make_float2(-A.y, -A.y), make_float2(A.z, A.z), make_float2(A.w, A.w),
+                                 make_float2(B.x, B.x), make_float2(B.y, B.y)};
+                };
+                auto advance = [&](int a, float x) {
+                    if (x >= xr[a]) {
+                        const int last = nint[sp0 + a] - 1;
+                        bool moved = false;
+                        while (x >= xr[a] && jj[a] < last) {
+                            ++jj[a];
+                            xr[a] = __ldg(srec + ((sp0 + a) * (int64_t)(kmax + 1) + jj[a]) * kSplineRec32);
+                            moved = true;
+                        }
+                        if (moved) reload(a);
+                    }
+                };
 #pragma unroll
                 for (int a = 0; a < NSP; ++a) {
-                    const int64_t sp = (int64_t)s * nsp + a;
-                    iv[a].base = srec + sp * (int64_t)(kmax + 1) * kSplineRec32;
-                    iv[a].last = nint[sp] - 1;
-                    iv[a].j = find_interval<float, kSplineRec32, 6>(iv[a].base, nint[sp], x0);
-                    load_iv(iv[a]);
-                    iv2[a] = dup(iv[a]);
+                    const float* base = srec + (sp0 + a) * (int64_t)(kmax + 1) * kSplineRec32;
+                    jj[a] = find_interval<float, kSplineRec32, 6>(base, nint[sp0 + a], x0);
+                    reload(a);
                 }
                 int i = lo;
                 while (i < hi) {
@@ -294,7 +339,7 @@ __global__ void __launch_bounds__(kThreads, 2)
                         const float xg = fld(tb, i + G - 1, 0);
                         bool fast = true;
 #pragma unroll
-                        for (int a = 0; a < NSP; ++a) fast &= xg < iv[a].xr;
+                        for (int a = 0; a < NSP; ++a) fast &= xg < xr[a];
                         if (fast) {
 #pragma unroll
                             for (int g = 0; g < G; g += 2)
@@ -305,16 +350,8 @@ __global__ void __launch_bounds__(kThreads, 2)
                             for (int g = 0; g < G; ++g) {
                                 const float x = fld(tb, i + g, 0);
 #pragma unroll
-                                for (int a = 0; a < NSP; ++a) {
-                                    bool moved = false;
-                                    while (x >= iv[a].xr && iv[a].j < iv[a].last) {
-                                        ++iv[a].j;
-                                        load_iv(iv[a]);
-                                        moved = true;
-                                    }
-                                    if (moved) iv2[a] = dup(iv[a]);
-                                }
-                                acc2.x += bin_term32<C, HAS_H, BROKEN>(tb, i + g, iv, ao2, at2, n1, n2, Af);
+                                for (int a = 0; a < NSP; ++a) advance(a, x);
+                                acc2.x += bin_term32p<C, HAS_H, BROKEN>(tb, i + g, iv2, ao2, at2, n1, n2, Af);
                             }
                         }
                     }
@@ -322,16 +359,8 @@ __global__ void __launch_bounds__(kThreads, 2)
                     for (; i < cend; ++i) {
                         const float x = fld(tb, i, 0);
 #pragma unroll
-                        for (int a = 0; a < NSP; ++a) {
-                            bool moved = false;
-                            while (x >= iv[a].xr && iv[a].j < iv[a].last) {
-                                ++iv[a].j;
-                                load_iv(iv[a]);
-                                moved = true;
-                            }
-                            if (moved) iv2[a] = dup(iv[a]);
-                        }
-                        acc2.x += bin_term32<C, HAS_H, BROKEN>(tb, i, iv, ao2, at2, n1, n2, Af);
+                        for (int a = 0; a < NSP; ++a) advance(a, x);
+                        acc2.x += bin_term32p<C, HAS_H, BROKEN>(tb, i, iv2, ao2, at2, n1, n2, Af);
                     }
                     acc64 += (double)acc2.x + (double)acc2.y;
                 }
@@ -499,6 +528,24 @@ __global__ void __launch_bounds__(128)
                     const ff sl = BROKEN ? (ell.hi < 0.f ? n1 : n2) : n1;
                     lEh = ff_add(ff_add(P[C], ff_mul(sl, ell)), lA);
                 }
+                bool moderate = true;
+#pragma unroll
+                for (int c = 0; c < C; ++c) moderate &= fabsf(P[c].hi) < 60.f;
+                if (HAS_H) moderate &= fabsf(P[C].hi) < 60.f && lEh.hi > -120.f && lEh.hi < 60.f;
+                if (moderate) {
+                    // exponents within FP32 range: 2^(hi + lo) = ex2(hi) (1 + lo ln2), accurate to
+                    // a few ulp because hi is exact; then the ordinary FP32 term
+                    float S[C];
+                    const float eh = HAS_H ? ex2_approx(lEh.hi) * fmaf(lEh.lo, (float)kLn2, 1.f) : 0.f;
+#pragma unroll
+                    for (int c = 0; c < C; ++c) {
+                        const float E = ex2_approx(P[c].hi) * fmaf(P[c].lo, (float)kLn2, 1.f);
+                        const float N = fmaf(ao2, fld(tbase, i, 3 + c), at2 * fld(tbase, i, 6 + c));
+                        S[c] = HAS_H ? fmaf(E, N, eh * fld(tbase, i, 9 + c)) : E * N;
+                    }
+                    acc_ff = ff_add(acc_ff, ff{term_from_S<C>(S, nu), 0.f});
+                    continue;
+                }
                 ff term = {-(float)C, 0.f};
 #pragma unroll
                 for (int c = 0; c < C; ++c) {
@@ -664,10 +711,10 @@ __global__ void model_psd_kernel(const int32_t* __restrict__ state_ds, const Dat
 }
 
 template <class K>
-int grid_for(K kernel, const lisa_data* d, size_t smem) {
+int grid_for(K kernel, const lisa_data* d, size_t smem, int threads) {
     int per_sm = d->tiling.ctas_per_sm;
     if (per_sm <= 0) {
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kThreads, smem) != cudaSuccess ||
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem) != cudaSuccess ||
             per_sm < 1)
             per_sm = 1;
     }
@@ -684,8 +731,8 @@ cudaError_t launch_fp32_g(const lisa_data* d, const double* theta, const int32_t
     const size_t smem = 2 * (size_t)d->tiling.tile_bins * kRec * sizeof(float);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    const int grid = grid_for(kern, d, smem);
-    kern<<<grid, kThreads, smem, sm>>>(d->d_items, (int)d->n_items, d->d_rec32, theta, sstat, nint, srec, kmax,
+    const int grid = grid_for(kern, d, smem, kThreads32);
+    kern<<<grid, kThreads32, smem, sm>>>(d->d_items, (int)d->n_items, d->d_rec32, theta, sstat, nint, srec, kmax,
                                        d->nsp, d->d_ds, partial, err, d->tiling.tile_bins);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -713,7 +760,7 @@ template <int C, bool H, bool B>
 cudaError_t launch_fp64(const lisa_data* d, const double* theta, const int32_t* sstat, const int32_t* nint,
                         const double* srec, int kmax, double* partial, cudaStream_t sm) {
     auto kern = loglike_fp64_kernel<C, H, B>;
-    const int grid = grid_for(kern, d, 0);
+    const int grid = grid_for(kern, d, 0, kThreads);
     kern<<<grid, kThreads, 0, sm>>>(d->d_items, (int)d->n_items, d->d_rec64, theta, sstat, nint, srec, kmax,
                                     d->nsp, d->d_ds, partial);
     return cudaGetLastError();

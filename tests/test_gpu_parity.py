@@ -46,7 +46,7 @@ def test_tiny(tiny, precision):
 @pytest.mark.parametrize("tiling", [
     dict(tile_bins=64, states_per_cta=16, group=2),
     dict(tile_bins=96, states_per_cta=32, group=2),
-    dict(tile_bins=160, states_per_cta=256, group=8),
+    dict(tile_bins=160, states_per_cta=128, group=8),
     dict(tile_bins=1024, states_per_cta=64, group=4, ctas_per_sm=1),
 ])
 def test_small_ae_tilings(precision, tiling):

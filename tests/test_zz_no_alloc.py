@@ -42,7 +42,7 @@ def test_noalloc_rejects_problems_beyond_its_scratch():
     from paper_2507_06300_gb300 import binding as B
     wl = synth.workload("tiny", n_bins=131072, n_states=256)
     ds = B.Dataset.from_workload(wl, np.ones((3, wl.n_bins)))
-    ds.set_tiling(tile_bins=64, states_per_cta=256, group=2)   # 2,048 tiles x 256 states
+    ds.set_tiling(tile_bins=64, states_per_cta=128, group=2)   # 2,048 tiles x 256 states
     assert ds.workspace_bytes(wl.knots.kmax, 0) > B.NOALLOC_SCRATCH_BYTES
     count, x, w, kmax, kind = B.knots_to_device(wl.knots)
     theta = torch.as_tensor(wl.theta, device="cuda")
