@@ -70,7 +70,7 @@ struct DatasetDev {
     int64_t bin0, nbins;     // bin range: bin0 in padded indexing, nbins real bins
     int64_t npad;            // nbins rounded up to even (bins [bin0, bin0 + npad) in the tables)
     int64_t rbin0;           // first bin in the caller's (unpadded) arrays
-    int64_t pbase;           // first partial slot of the dataset's states
+    int64_t pbase;           // first partial slot of the dataset (partials are [tile][state])
     int64_t psd_base;        // first element of the dataset's states in a model-PSD output
     int32_t s0, ns;          // state range
     int32_t ntiles;          // tiles of tile_bins bins

@@ -150,6 +150,17 @@ __device__ __forceinline__ float bin_term32(const float* __restrict__ tb, int i,
     return term_from_S<C>(S, nu);
 }
 
+// 10^v as a float without the FP64 exp10: 2^(v log2 10) split into an exact integer power of
+// two and a fractional part in [0, 1) handled by ex2 (one FP64 multiply, ~2 ulp).
+__device__ __forceinline__ float exp10_to_float(double v) {
+    const double e = v * kLog2_10;
+    const double n = floor(e);
+    if (n < -149.0) return 0.f;
+    if (n > 127.0) return INFINITY;
+    const float f = ex2_approx((float)(e - n));
+    return n >= -126.0 ? f * __int_as_float(((int)n + 127) << 23) : ldexpf(f, (int)n);
+}
+
 // Current interval of one spline duplicated into register pairs for the packed path.
 struct Iv2 {
     float2 nxo, c0, c1, c2, c3;
@@ -294,7 +305,7 @@ __global__ void __launch_bounds__(kThreads32, 5)
                 const double* th = theta + (size_t)s * LISA_N_THETA;
                 const float ao2 = (float)(th[0] * th[0]);
                 const float at2 = (float)(th[1] * th[1]);
-                const float Af = HAS_H ? (float)exp10(th[2]) : 0.f;
+                const float Af = HAS_H ? exp10_to_float(th[2]) : 0.f;
                 const float n1 = (float)th[3];
                 const float n2 = BROKEN ? (float)th[4] : n1;
                 const float2 ao2_2 = make_float2(ao2, ao2), at2_2 = make_float2(at2, at2), Af2 = make_float2(Af, Af);
@@ -331,6 +342,7 @@ __global__ void __launch_bounds__(kThreads32, 5)
                     jj[a] = find_interval<float, kSplineRec32, 6>(base, nint[sp0 + a], x0);
                     reload(a);
                 }
+                ff accf = {0.f, 0.f};
                 int i = lo;
                 while (i < hi) {
                     const int cend = min(i + 32, hi);
@@ -362,8 +374,9 @@ __global__ void __launch_bounds__(kThreads32, 5)
                         for (int a = 0; a < NSP; ++a) advance(a, x);
                         acc2.x += bin_term32p<C, HAS_H, BROKEN>(tb, i, iv2, ao2, at2, n1, n2, Af);
                     }
-                    acc64 += (double)acc2.x + (double)acc2.y;
+                    accf = ff_add(accf, two_sum(acc2.x, acc2.y));
                 }
+                acc64 = (double)accf.hi + (double)accf.lo;
             }
         }
         red[tid] = acc64;
@@ -415,9 +428,10 @@ __device__ __forceinline__ ff log2_sum(ff a, ff b) {
 }
 
 // 1/S + ln S from lS = log2 S (float-float).  Inside |lS| < 100 the result is a float-float
-// (2^-lS is ex2 of the fractional part scaled by an exact power of two); outside, the
-// contribution is returned through `far` in FP64 (S beyond the FP32 range: rare).
-__device__ __forceinline__ ff inv_plus_log(ff lS, double& far) {
+// (2^-lS is ex2 of the fractional part scaled by an exact power of two); outside, nu times the
+// contribution is added to `far` in FP64 (S beyond the FP32 range: rare, so the FP64 pipe is
+// only used there).
+__device__ __forceinline__ ff inv_plus_log(ff lS, float nu, double& far) {
     const ff kLn2ff = {0.693147182f, -1.90465421e-09f};
     if (lS.hi > -100.f && lS.hi < 100.f) {
         const float n = rintf(lS.hi);
@@ -425,15 +439,17 @@ __device__ __forceinline__ ff inv_plus_log(ff lS, double& far) {
         const float inv = ex2_approx(-f) * __int_as_float((127 - (int)n) << 23);
         return ff_add(ff_mul(lS, kLn2ff), ff{inv, 0.f});
     }
+    double v;
     if (!(lS.hi > -1.0e6f)) {
-        far += INFINITY;                                  // S = 0 (or NaN)
+        v = INFINITY;                                     // S = 0 (or NaN)
     } else if (!(lS.hi < 1.0e6f)) {
-        far += (double)lS.hi * kLn2;                      // S overflows: 1/S = 0
+        v = (double)lS.hi * kLn2;                         // S overflows: 1/S = 0
     } else {
         const float n = rintf(lS.hi);
         const float f = (lS.hi - n) + lS.lo;
-        far += ldexp((double)ex2_approx(-f), -(int)n) + kLn2 * ((double)lS.hi + (double)lS.lo);
+        v = ldexp((double)ex2_approx(-f), -(int)n) + kLn2 * ((double)lS.hi + (double)lS.lo);
     }
+    if (nu != 0.f) far += (double)nu * v;                 // a padding bin (nu = 0) adds nothing
     return ff{0.f, 0.f};
 }
 
@@ -461,7 +477,7 @@ __global__ void __launch_bounds__(128)
         const double* th = theta + (size_t)s * LISA_N_THETA;
         const float ao2 = (float)(th[0] * th[0]);
         const float at2 = (float)(th[1] * th[1]);
-        const float Af = HAS_H ? (float)exp10(th[2]) : 0.f;
+        const float Af = HAS_H ? exp10_to_float(th[2]) : 0.f;
         const ff lA = ff_from_double(th[2] * kLog2_10);
         const ff n1 = ff_from_double(th[3]);
         const ff n2 = BROKEN ? ff_from_double(th[4]) : n1;
@@ -558,9 +574,7 @@ __global__ void __launch_bounds__(128)
                         const ff lH = (lG.hi > -INFINITY && lG.hi < INFINITY) ? ff_add(lEh, lG) : lG;
                         lS = log2_sum(lNE, lH);
                     }
-                    double far_c = 0.0;
-                    term = ff_add(term, inv_plus_log(lS, far_c));
-                    far += (double)nu * far_c;
+                    term = ff_add(term, inv_plus_log(lS, nu, far));
                 }
                 acc_ff = ff_add(acc_ff, ff_mul(term, ff{nu, 0.f}));
             }
@@ -649,24 +663,29 @@ __global__ void __launch_bounds__(kThreads)
     }
 }
 
-// Per state: fixed-order sum of its tiles' partials plus the dataset constants.
+// Per state (one warp): fixed-order sum of its tiles' partials (lane-strided, then a shuffle
+// tree) plus the dataset constants.
 __global__ void finalize_kernel(int S, const int32_t* __restrict__ state_ds, const DatasetDev* __restrict__ ds,
                                 const int32_t* __restrict__ sstat, const double* __restrict__ partial,
                                 const int* __restrict__ err, int fp32, double* __restrict__ out) {
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= S) return;
+    const int s = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (s >= S) return;   // uniform per warp
     if (sstat[s] & kUserBits) {
-        out[s] = -INFINITY;
+        if (lane == 0) out[s] = -INFINITY;
         return;
     }
     const DatasetDev& D = ds[state_ds[s]];
     const double* p = partial + D.pbase + (int64_t)(s - D.s0) * D.ntiles;
     double sum = 0.0;
-    for (int t = 0; t < D.ntiles; ++t) sum += p[t];
-    double L = fp32 ? (-sum - D.Cnu + D.K) : (-sum + D.K);
-    if (!isfinite(L)) L = -INFINITY;
-    if (*err) L = NAN;
-    out[s] = L;
+    for (int t = lane; t < D.ntiles; t += 32) sum += p[t];
+    for (int o = 16; o > 0; o >>= 1) sum += __shfl_down_sync(0xffffffffu, sum, o);
+    if (lane == 0) {
+        double L = fp32 ? (-sum - D.Cnu + D.K) : (-sum + D.K);
+        if (!isfinite(L)) L = -INFINITY;
+        if (*err) L = NAN;
+        out[s] = L;
+    }
 }
 
 // Model PSD in physical units, FP64: one thread per (state, bin).
@@ -826,8 +845,7 @@ lisa_status lisa_psd_loglike(const lisa_data* d, const lisa_params* params, cons
                       : dispatch_model<2>(d, fp32, params->theta_dev, sstat, nint, route, srec, kmax, partial, err, sm);
     if (e != cudaSuccess) return LISA_ERR_CUDA;
     const int S = (int)d->n_states;
-    finalize_kernel<<<(S + 255) / 256, 256, 0, sm>>>(S, d->d_state_ds, d->d_ds, sstat, partial, err, fp32 ? 1 : 0,
-                                                     out);
+    finalize_kernel<<<(S + 7) / 8, 256, 0, sm>>>(S, d->d_state_ds, d->d_ds, sstat, partial, err, fp32 ? 1 : 0, out);
     return check_cuda(cudaGetLastError());
 }
 
