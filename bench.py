@@ -32,11 +32,17 @@ METRIC = "Whittle logL state-bins/s: batched FP32 vs plain FP64, % of roofline"
 UNIT = "state-bins/s"
 WORKLOAD = ("paper-scale: A,E,T; 131,072 uniform bins 0.1-29 mHz; Nseg=64; OMS 15 pm + TM 3 fm/s^2 + "
             "power-law SGWB log10 Omega=-12, n_t=2/3; 64 walkers x 16 temps = 1,024 states; 0-20 knots per spline")
-# Algorithmic MUFU (SFU) operations per state-bin of the fused FP32 kernel as implemented for
-# A,E,T with an SGWB: 4 ex2 (three noise perturbations, one SGWB perturbation x power law),
-# 1 rcp (fused reciprocal sum), 1 lg2 (fused log of the product).
-MUFU_PER_STATE_BIN = 6
-MUFU_PER_SM_PER_CLK = 16           # XU lanes per SM per clock
+# Algorithmic operations per state-bin of the fused FP32 kernel as implemented for A,E,T with an
+# SGWB.  MUFU: 4 ex2 (three noise perturbations, one SGWB perturbation x power law), 1 rcp (fused
+# reciprocal sum), 1 lg2 (fused log of the product).  FP32 (FMA pipe, an FMA counted once):
+# 4 splines x (1 shift + 3 Horner FMA) = 16, SGWB exponent and amplitude 2, per channel noise
+# (2) and PSD (2) = 12, channel product and reciprocal-sum numerator 4, reciprocal-sum FMA,
+# log FMA and nu scale 3, accumulation 1.
+MUFU_EX2, MUFU_RCP, MUFU_LG2 = 4, 1, 1
+MUFU_PER_STATE_BIN = MUFU_EX2 + MUFU_RCP + MUFU_LG2
+FP32_PER_STATE_BIN = 38
+TABLE_BYTES_PER_BIN = 12 * 4          # FP32 bin table: x, ell, nu, 3 x (G_oms, G_tm, G_h)
+SPLINE_RECORD_BYTES = 64
 N_SM = 152
 
 
@@ -114,21 +120,66 @@ def _traffic_from_profile(kernel_src):
 
 
 def make_periodogram_gpu(wl, B, torch):
-    """P = S_model(theta_true) x Gamma(nu)/nu with the model PSD from the library (FP64 path)."""
-    ones = np.ones((wl.n_channels, wl.n_bins))
-    ds0 = B.Dataset(n_channels=wl.n_channels, freq=wl.f, nu=wl.nu, periodogram=ones,
-                    response=wl.R if wl.sgwb_model else None, n_states=1, x_lo=wl.x_lo, x_hi=wl.x_hi,
+    """P = S_model(theta_true of its dataset) x Gamma(nu)/nu for every dataset of the workload,
+    the model PSD from the library's FP64 path; returns a host array [C, N_total]."""
+    D, C, N = wl.n_datasets, wl.n_channels, wl.n_bins
+    ds0 = B.Dataset(n_channels=C, freq=wl.f, nu=wl.nu, periodogram=wl.gamma,
+                    response=wl.R if wl.sgwb_model else None, bin_offset=wl.bin_offset,
+                    state_offset=np.arange(D + 1, dtype=np.int64), x_lo=wl.x_lo, x_hi=wl.x_hi,
                     f_ref=wl.f_ref, sgwb_model=wl.sgwb_model, tdi_form=wl.tdi_form)
     nsp = wl.n_splines
-    c = torch.zeros((1, nsp), dtype=torch.int32, device="cuda")
-    x = torch.zeros((1, nsp, 0), dtype=torch.float64, device="cuda")
-    w = torch.zeros((1, nsp, 2), dtype=torch.float64, device="cuda")
+    c = torch.zeros((D, nsp), dtype=torch.int32, device="cuda")
+    x = torch.zeros((D, nsp, 0), dtype=torch.float64, device="cuda")
+    w = torch.zeros((D, nsp, 2), dtype=torch.float64, device="cuda")
     buf, _ = ds0.spline_setup(c, x, w, 0, 0, B.FP64)
-    th = torch.as_tensor(wl.theta_true[:1], device="cuda")
-    S = ds0.model_psd(th, buf, 0).reshape(wl.n_channels, wl.n_bins)
-    P = (S * torch.as_tensor(wl.gamma, device="cuda")).cpu().numpy()
+    th = torch.as_tensor(wl.theta_true, device="cuda")
+    S = ds0.model_psd(th, buf, 0)                 # dataset d: [C][N_d] at offset C * b0
+    P = torch.empty((C, N), dtype=torch.float64, device="cuda")
+    for d in range(D):
+        b0, b1 = int(wl.bin_offset[d]), int(wl.bin_offset[d + 1])
+        P[:, b0:b1] = S[C * b0:C * b1].view(C, b1 - b0)
+    del S
+    P *= torch.as_tensor(wl.gamma, device="cuda")
+    out = P.cpu().numpy()
     ds0.close()
-    return P
+    return out
+
+
+def host_mem_available_gb():
+    try:
+        for line in open("/proc/meminfo"):
+            if line.startswith("MemAvailable:"):
+                return int(line.split()[1]) / 1e6
+    except OSError:
+        pass
+    return float("inf")
+
+
+def roofs(rates, hbm_gbs, bytes_per_state_bin):
+    """Ceilings in state-bins/s of the fused kernel from the measured pipe rates: the MUFU pipe
+    (the kernel's mix of 4 ex2, 1 rcp, 1 lg2), the FP32 FMA pipe (38 ops, packed FMAs counted as
+    two lane operations) and HBM (algorithmic bytes per state-bin)."""
+    t_ex2, t_rcp = 1.0 / rates["ex2"], 1.0 / rates["rcp"]
+    t_lg2 = 2.0 / rates["lg2_ex2"] - t_ex2
+    if not t_lg2 > 0:
+        t_lg2 = t_ex2
+    mufu = 1.0 / (MUFU_EX2 * t_ex2 + MUFU_RCP * t_rcp + MUFU_LG2 * t_lg2)
+    fp32_rate = max(rates["ffma"], rates["ffma2"])
+    return {"mufu": mufu, "mufu_rate": MUFU_PER_STATE_BIN * mufu, "fp32": fp32_rate / FP32_PER_STATE_BIN,
+            "fp32_rate": fp32_rate, "hbm": hbm_gbs * 1e9 / bytes_per_state_bin}
+
+
+def roofline_entry(sb_per_s, R, hbm_gbs, bytes_per_state_bin):
+    """Roofline object of the binding ceiling for a measured state-bin rate."""
+    bind = min(("fp32", "mufu", "hbm"), key=lambda k: R[k])
+    if bind == "hbm":
+        ach = sb_per_s * bytes_per_state_bin / 1e9
+        return {"bound": "hbm", "achieved": ach, "peak": hbm_gbs, "unit": "GB/s", "frac": ach / hbm_gbs}
+    ops, rate, pipe = ((FP32_PER_STATE_BIN, R["fp32_rate"], "FP32 (FMA pipe)") if bind == "fp32"
+                       else (MUFU_PER_STATE_BIN, R["mufu_rate"], "MUFU (XU pipe)"))
+    ach = ops * sb_per_s / 1e9
+    return {"bound": "alu", "pipe": pipe, "achieved": ach, "peak": rate / 1e9, "unit": "Gop/s",
+            "frac": ach / (rate / 1e9), "ops_per_state_bin": ops}
 
 
 def cpu_oracle_rate(wl, P, budget_s):
@@ -194,8 +245,9 @@ def run_ours(args):
     import torch
     import torch.distributed as dist
 
+    from paper_2507_06300_gb300 import autotune
     from paper_2507_06300_gb300 import binding as B
-    from paper_2507_06300_gb300 import synth
+    from paper_2507_06300_gb300 import replicas, synth
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -204,30 +256,45 @@ def run_ours(args):
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
-    wl = synth.workload("paper")
-    P = make_periodogram_gpu(wl, B, torch)
-    ds = B.Dataset.from_workload(wl, P)
-    count, x, w, kmax, kind = B.knots_to_device(wl.knots)
-    theta = torch.as_tensor(wl.theta, device="cuda")
-    S, N = wl.n_states, wl.n_bins
-    sb_per_step = S * N
+    def rank_max(vals):
+        """Max over ranks of each value (timings: the slowest replica sets the job's time)."""
+        return replicas.max_over_ranks(vals, dist if world > 1 else None, device="cuda")
 
-    # tile shapes picked by the autotuner on these inputs (outside the timed region)
-    from paper_2507_06300_gb300 import autotune
-    if args.tiling:
-        tb, sc, g = (int(v) for v in args.tiling.split(","))
-        best = dict(tile_bins=tb, states_per_cta=sc, group=g, ctas_per_sm=0)
-        ds.set_tiling(**best)
-        table = [(best, float("nan"))]
-    else:
-        best, table = autotune.autotune(ds, theta, count, x, w, kmax, kind, B.FP32)
-        table.sort(key=lambda r: r[1])
-
-    ev32 = B.Evaluator(ds, kmax, kind, B.FP32)
-    ev32.load(theta, count, x, w)
-    ev32.capture()
-    routed = ds.routed_states(ev32.buf)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # > 129 MB L2
+    peaks, peak_kind = _peaks()
+    rates = B.pipe_rates()            # measured MUFU / FP32 pipe rates (outside any timed region)
+    try:
+        gpu_id = "GPU-" + str(torch.cuda.get_device_properties(local).uuid)
+    except Exception:
+        vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+        gpu_id = vis.split(",")[local] if vis else str(local)
+
+    def prepare(wl, tiling):
+        P = make_periodogram_gpu(wl, B, torch)
+        ds = B.Dataset.from_workload(wl, P)
+        count, x, w, kmax, kind = B.knots_to_device(wl.knots)
+        theta = torch.as_tensor(wl.theta, device="cuda")
+        if tiling:
+            tb, sc, g = (int(v) for v in tiling.split(","))
+            best = dict(tile_bins=tb, states_per_cta=sc, group=g, ctas_per_sm=0)
+            ds.set_tiling(**best)
+            table = [(best, float("nan"))]
+        else:
+            # tile shapes picked by the autotuner on these inputs (outside the timed region)
+            best, table = autotune.autotune(ds, theta, count, x, w, kmax, kind, B.FP32)
+            table.sort(key=lambda r: r[1])
+        so, bo = wl.state_offset, wl.bin_offset
+        nbin_state = np.repeat(np.diff(bo), np.diff(so))           # bins of each state's dataset
+        alg_bytes = (TABLE_BYTES_PER_BIN * wl.n_bins + wl.n_states * 8 * B.N_THETA +
+                     wl.n_states * wl.n_splines * (kmax + 1) * SPLINE_RECORD_BYTES)
+        return dict(wl=wl, P=P, ds=ds, count=count, x=x, w=w, kmax=kmax, kind=kind, theta=theta, tiling=best,
+                    table=table, sb=int(nbin_state.sum()), nbin_state=nbin_state, alg_bytes=alg_bytes)
+
+    def release(I):
+        I["ds"].close()
+        I.clear()
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
 
     def timed(ev, steps, warmup):
         for _ in range(warmup):
@@ -254,63 +321,99 @@ def run_ours(args):
         ll_ms = [b.elapsed_time(c) for a, b, c in e]
         return sum(step_ms) / steps, sum(ll_ms) / steps
 
-    peaks, peak_kind = _peaks()
-    try:
-        gpu_id = "GPU-" + str(torch.cuda.get_device_properties(local).uuid)
-    except Exception:
-        vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
-        gpu_id = vis.split(",")[local] if vis else str(local)
-    with ClockSampler(gpu_id) as clk:
-        ms, ll_ms = timed(ev32, args.steps, args.warmup)
-    clocks = clk.summary()
-    if world > 1:
-        t = torch.tensor([ms, ll_ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms, ll_ms = t.tolist()
-    value = world * sb_per_step / (ms / 1e3)
+    def kernel_times(I, ev, steps):
+        """Device time of each likelihood kernel (events recorded by the library on the launching
+        stream around each kernel) over uncaptured calls, L2 flushed before each."""
+        ds = I["ds"]
+        ds.set_profiling(True)
+        acc = np.zeros(3)
+        for k in range(steps):
+            flush.fill_(float(k))
+            ev.setup()
+            ev.loglike()
+            acc += np.array(ds.kernel_ms())
+        ds.set_profiling(False)
+        return (acc / steps).tolist()
 
-    # plain FP64 path on the same inputs (fewer steps: it is much slower)
-    ev64 = B.Evaluator(ds, kmax, kind, B.FP64)
-    ev64.load(theta, count, x, w)
-    ev64.capture()
-    ms64, ll64 = timed(ev64, max(1, args.fp64_steps), 1)
-    value64 = world * sb_per_step / (ms64 / 1e3)
-
-    # adjoint (log L and its gradient for every state), FP32 and plain FP64, eager launches
-    def timed_grad(prec, steps):
-        gbuf = torch.empty(ds.spline_buf_bytes(kmax, prec), dtype=torch.uint8, device="cuda")
-        gws = torch.empty(ds.workspace_bytes(kmax, prec, True), dtype=torch.uint8, device="cuda")
-        gout = torch.empty(S, dtype=torch.float64, device="cuda")
-        ggr = torch.empty((S, B.N_THETA + ds.n_splines * (2 * kmax + 2)), dtype=torch.float64, device="cuda")
-        def one():
-            ds.spline_setup(count, x, w, kmax, kind, prec, buf=gbuf)
-            ds.psd_loglike_grad(theta, count, x, w, kmax, kind, gbuf, prec, out=gout, grad=ggr, workspace=gws)
-        for _ in range(2):
-            one()
+    def forward(I, steps, warmup, fp64_steps, sample_clocks=False, sharded=False):
+        """FP32 (graphs, timed) and plain FP64 on the same inputs, per-kernel times, accuracy.
+        Replicas (sharded=False) each run the whole workload; sharded runs split it."""
+        ds, wl, kmax, kind = I["ds"], I["wl"], I["kmax"], I["kind"]
+        ev32 = B.Evaluator(ds, kmax, kind, B.FP32)
+        ev32.load(I["theta"], I["count"], I["x"], I["w"])
+        ev32.capture()
+        routed = ds.routed_list(ev32.buf)
+        clocks = None
+        if sample_clocks:
+            with ClockSampler(gpu_id) as clk:
+                ms, ll_ms = timed(ev32, steps, warmup)
+            clocks = clk.summary()
+        else:
+            ms, ll_ms = timed(ev32, steps, warmup)
+        ms, ll_ms = rank_max([ms, ll_ms])
+        kt = rank_max(kernel_times(I, ev32, max(3, steps // 2)))
+        ev64 = B.Evaluator(ds, kmax, kind, B.FP64)
+        ev64.load(I["theta"], I["count"], I["x"], I["w"])
+        ev64.capture()
+        ms64, ll64 = rank_max(timed(ev64, max(1, fp64_steps), 1))
+        # accuracy of the FP32 path against the FP64 GPU path on every state
+        L32 = ev32.replay().clone()
+        L64 = ev64.replay().clone()
         torch.cuda.synchronize()
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record()
-        for _ in range(steps):
-            one()
-        b.record()
-        torch.cuda.synchronize()
-        return a.elapsed_time(b) / steps
-    grad32_ms = timed_grad(B.FP32, max(3, args.steps // 2))
-    grad64_ms = timed_grad(B.FP64, 1)
+        L32, L64 = L32.cpu().numpy(), L64.cpu().numpy()
+        bo, so, P = wl.bin_offset, wl.state_offset, I["P"]
+        lnP = wl.nu * np.log(P).sum(axis=0)
+        K_d = -np.add.reduceat(lnP, bo[:-1])
+        Cnu_d = wl.n_channels * np.add.reduceat(wl.nu, bo[:-1])
+        ds_of = np.repeat(np.arange(wl.n_datasets), np.diff(so))
+        ok = np.isfinite(L64)
+        scale = np.maximum(np.abs(L64 - K_d[ds_of]), Cnu_d[ds_of])[ok]
+        err = np.abs(L32[ok] - L64[ok])
+        sb = I["sb"]
+        sb_fused = sb - int(I["nbin_state"][routed].sum())
+        sb_job = (replicas.sum_over_ranks([sb], dist if world > 1 else None, device="cuda")[0] if sharded
+                  else world * sb)
+        r = {"value": sb_job / (ms / 1e3), "unit": UNIT, "ms_per_step": ms, "loglike_ms": ll_ms,
+             "setup_ms": ms - ll_ms, "state_bins_per_step": sb, "routed_states": len(routed),
+             "kernel_ms": {"fused_fp32": kt[0], "compensated": kt[1], "finalize": kt[2]},
+             "fused_state_bins": sb_fused,
+             "fp64_plain": {"value": sb_job / (ms64 / 1e3), "unit": UNIT, "ms_per_step": ms64,
+                            "loglike_ms": ll64, "steps": max(1, fp64_steps)},
+             "accuracy_fp32_vs_fp64": {"max_abs_nats": float(err.max()), "median_abs_nats": float(np.median(err)),
+                                       "max_rel_to_scale": float((err / scale).max()), "states": int(ok.sum())},
+             "tiling": I["tiling"], "autotune_top": [[t, round(v, 4)] for t, v in I["table"][:5]]}
+        r["speedup_fp32_vs_fp64"] = r["value"] / r["fp64_plain"]["value"]
+        return r, ev32, clocks
 
-    # accuracy of the FP32 path against the FP64 GPU path on every state
-    L32 = ev32.replay().clone()
-    L64 = ev64.replay().clone()
-    torch.cuda.synchronize()
-    L32, L64 = L32.cpu().numpy(), L64.cpu().numpy()
-    ok = np.isfinite(L64)
-    K = -np.sum(wl.nu * np.log(P).sum(axis=0))
-    scale = np.maximum(np.abs(L64[ok] - K), wl.n_channels * wl.nu.sum())
-    err = np.abs(L32[ok] - L64[ok])
+    def roofline_of(I, r):
+        bpsb = I["alg_bytes"] / I["sb"]
+        R = roofs(rates, peaks["hbm_gbs"], bpsb)
+        fused_rate = r["fused_state_bins"] / (r["kernel_ms"]["fused_fp32"] / 1e3)
+        ent = roofline_entry(fused_rate, R, peaks["hbm_gbs"], bpsb)
+        ent.update({"kernel": "loglike_fp32_kernel (fused FP32 likelihood)",
+                    "ceilings_state_bins_per_s": {"fp32": R["fp32"], "mufu": R["mufu"], "hbm": R["hbm"]},
+                    "mufu_frac": fused_rate / R["mufu"], "hbm_frac": fused_rate / R["hbm"],
+                    "step_frac": (r["value"] / world) / min(R["fp32"], R["mufu"], R["hbm"]),
+                    "hbm_algorithmic_bytes_per_state_bin": bpsb})
+        return ent
+
+    # ---- the headline: paper-scale workload ----------------------------------------------------
+    wl = synth.workload("paper")
+    I = prepare(wl, args.tiling)
+    head, ev32, clocks = forward(I, args.steps, args.warmup, args.fp64_steps, sample_clocks=True)
+    roof = roofline_of(I, head)
+    roof["peak_source"] = ("measured live by lisa_pipe_rates: FP32 = max(fma.rn.f32, fma.rn.f32x2) lane-op rate, "
+                           "MUFU = the kernel's 4 ex2 + 1 rcp + 1 lg2 mix; HBM = MEASURED_PEAKS.json "
+                           f"({peak_kind})")
+    roof["nominal_fp32_gops"] = N_SM * 128 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e9
+    roof["traffic"] = _traffic_from_profile(os.path.join(ROOT, "paper_2507_06300_gb300", "csrc", "lisa_loglike.cu"))
+    if roof["traffic"] is not None:
+        roof["traffic_vs_algorithmic_bytes"] = roof["traffic"] / I["alg_bytes"]
 
     # end to end through the public API: pinned host inputs -> device -> log L back in pinned memory
+    S = wl.n_states
     pin = lambda t: t.cpu().pin_memory()
-    h_theta, h_count, h_x, h_w = pin(theta), pin(count), pin(x), pin(w)
+    h_theta, h_count, h_x, h_w = pin(I["theta"]), pin(I["count"]), pin(I["x"]), pin(I["w"])
     h_out = torch.empty(S, dtype=torch.float64).pin_memory()
     for _ in range(args.warmup):
         ev32.loglike_host(h_theta, h_count, h_x, h_w, h_out)
@@ -324,58 +427,104 @@ def run_ours(args):
         b.record()
         torch.cuda.synchronize()
         e2e_ms.append(a.elapsed_time(b))
-    e2e = sum(e2e_ms) / len(e2e_ms)
-    if world > 1:
-        t = torch.tensor([e2e], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e = t.item()
+    e2e = rank_max([sum(e2e_ms) / len(e2e_ms)])[0]
     h2d = sum(t.numel() * t.element_size() for t in (h_theta, h_count, h_x, h_w))
     d2h = h_out.numel() * h_out.element_size()
+    P_head = I["P"]
+    release(I)
 
-    # roofline of the dominant kernel (fused FP32 likelihood): MUFU issue bound
-    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    mufu_peak = N_SM * MUFU_PER_SM_PER_CLK * sm_max * 1e6 / 1e9   # Gop/s
-    achieved = MUFU_PER_STATE_BIN * sb_per_step / (ll_ms / 1e3) / 1e9
-    traffic = _traffic_from_profile(os.path.join(ROOT, "paper_2507_06300_gb300", "csrc", "lisa_loglike.cu"))
-    hbm_alg = N * 12 * 4 + S * 8 + S * wl.n_splines * (kmax + 1) * 32   # bytes per launch (algorithmic)
-
-    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "n_bins": N, "n_states": S, "n_channels": wl.n_channels,
-                       "kmax": kmax, "precision": "fp32-bulk, fp64 sums", "l2": "flushed (256 MB write) "
-                       "between timed steps", "cuda_graph": True,
+    line = {"metric": METRIC, "value": head["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": head["ms_per_step"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n_bins": wl.n_bins, "n_states": S, "n_channels": wl.n_channels,
+                       "kmax": int(wl.knots.kmax), "precision": "fp32-bulk, fp64 sums",
+                       "l2": "flushed (256 MB write) between timed steps", "cuda_graph": True,
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
-                       "tiling": best, "autotune_top": [[t, round(ms, 4)] for t, ms in table[:5]]},
-            "fp64_plain": {"value": value64, "unit": UNIT, "ms_per_step": ms64, "steps": max(1, args.fp64_steps),
-                           "loglike_ms": ll64},
-            "speedup_fp32_vs_fp64": value / value64,
-            "adjoint": {"unit": UNIT, "fp32_value": world * sb_per_step / (grad32_ms / 1e3), "fp32_ms_per_step": grad32_ms,
-                        "fp64_value": world * sb_per_step / (grad64_ms / 1e3), "fp64_ms_per_step": grad64_ms,
-                        "what": "spline setup + log L and gradient for every state (lisa_psd_loglike_grad)"},
-            "accuracy_fp32_vs_fp64": {"max_abs_nats": float(err.max()), "median_abs_nats": float(np.median(err)),
-                                      "max_rel_to_scale": float((err / scale).max()), "states": int(ok.sum())},
-            "loglike_ms": ll_ms, "setup_ms": ms - ll_ms, "routed_states": routed,
-            "roofline": {"bound": "alu", "pipe": "MUFU (XU)", "achieved": achieved, "peak": mufu_peak,
-                         "unit": "Gop/s", "frac": achieved / mufu_peak, "traffic": traffic,
-                         "peak_source": f"derived: {N_SM} SMs x {MUFU_PER_SM_PER_CLK} MUFU/clk x {sm_max:.0f} MHz",
-                         "ops_per_state_bin": MUFU_PER_STATE_BIN,
-                         "hbm_algorithmic_bytes_per_launch": hbm_alg,
-                         "hbm_frac": (hbm_alg / (ll_ms / 1e3) / 1e9) / peaks["hbm_gbs"],
-                         "hbm_peak_gbs": peaks["hbm_gbs"], "hbm_peak_kind": peak_kind},
-            "e2e": {"value": world * sb_per_step / (e2e / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
-                    "d2h_bytes_per_step": d2h, "ms_per_step": e2e},
-            # per step: spline_setup_kernel (setup graph), then the fused, compensated and finalize
-            # kernels (likelihood graph)
-            "gpu_launches": 4 * args.steps,
+                       "tiling": head["tiling"], "autotune_top": head["autotune_top"]},
+            "fp64_plain": head["fp64_plain"], "speedup_fp32_vs_fp64": head["speedup_fp32_vs_fp64"],
+            "accuracy_fp32_vs_fp64": head["accuracy_fp32_vs_fp64"],
+            "loglike_ms": head["loglike_ms"], "setup_ms": head["setup_ms"], "routed_states": head["routed_states"],
+            "kernel_ms": head["kernel_ms"], "roofline": roof, "pipe_rates_lane_ops_per_s": rates,
+            "e2e": {"value": world * head["state_bins_per_step"] / (e2e / 1e3), "unit": UNIT,
+                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e},
+            # per step: spline_setup_kernel (setup graph), then the state-parameter, fused,
+            # compensated and finalize kernels (likelihood graph)
+            "gpu_launches": 5 * args.steps,
             "clocks": clocks}
+
+    # ---- adjoint: 256 walkers x 8 temperatures, 12 + 8 knots ------------------------------------
+    if not args.no_extras:
+        wla = synth.workload("adjoint")
+        Ia = prepare(wla, "")
+        ds, kmax, kind = Ia["ds"], Ia["kmax"], Ia["kind"]
+        Sa = wla.n_states
+
+        def timed_grad(prec, steps):
+            gbuf = torch.empty(ds.spline_buf_bytes(kmax, prec), dtype=torch.uint8, device="cuda")
+            gws = torch.empty(ds.workspace_bytes(kmax, prec, True), dtype=torch.uint8, device="cuda")
+            gout = torch.empty(Sa, dtype=torch.float64, device="cuda")
+            ggr = torch.empty((Sa, B.N_THETA + ds.n_splines * (2 * kmax + 2)), dtype=torch.float64, device="cuda")
+
+            def one():
+                ds.spline_setup(Ia["count"], Ia["x"], Ia["w"], kmax, kind, prec, buf=gbuf)
+                ds.psd_loglike_grad(Ia["theta"], Ia["count"], Ia["x"], Ia["w"], kmax, kind, gbuf, prec, out=gout,
+                                    grad=ggr, workspace=gws)
+            for _ in range(2):
+                one()
+            torch.cuda.synchronize()
+            tot = 0.0
+            for k in range(steps):
+                flush.fill_(float(k))
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record()
+                one()
+                b.record()
+                torch.cuda.synchronize()
+                tot += a.elapsed_time(b)
+            return rank_max([tot / steps])[0], gout.cpu().numpy(), ggr.cpu().numpy()
+
+        g32_ms, L32, G32 = timed_grad(B.FP32, max(3, args.steps // 2))
+        g64_ms, L64, G64 = timed_grad(B.FP64, 1)
+        ok = np.isfinite(L64)
+        gscale = np.maximum(np.abs(G64[ok]).max(axis=1, keepdims=True), 1e-300)
+        line["adjoint"] = {
+            "workload": "A,E,T; 131,072 bins; 256 walkers x 8 temps = 2,048 states; 12 noise + 8 SGWB knots",
+            "what": "spline setup + log L and its gradient for every state (lisa_psd_loglike_grad)",
+            "unit": UNIT, "fp32_value": world * Ia["sb"] / (g32_ms / 1e3), "fp32_ms_per_step": g32_ms,
+            "fp64_value": world * Ia["sb"] / (g64_ms / 1e3), "fp64_ms_per_step": g64_ms,
+            "speedup_fp32_vs_fp64": g64_ms / g32_ms,
+            "grad_fp32_vs_fp64_max_rel_to_state_max": float((np.abs(G32[ok] - G64[ok]) / gscale).max()),
+            "l2": "flushed between timed steps"}
+        release(Ia)
+
+    # ---- batched datasets and the full-form workload ----------------------------------------------
+    line["workloads"] = {}
+    if not args.no_extras:
+        for name, desc in (("batched", "1,024 A,E,T datasets of 8k-262k bins, 4 x 4 states each, 0-30 knots; "
+                                        "one persistent launch per kernel, CUDA graphs"),
+                           ("full", "A,E,T; 524,288 bins; Nseg=128; 32 temps x 256 walkers = 8,192 states; "
+                                    "broken power-law SGWB (knee 3 mHz); 0-40 knots")):
+            if name == "batched" and host_mem_available_gb() < 48:
+                line["workloads"][name] = {"workload": desc, "skipped": "less than 48 GB of host memory free"}
+                continue
+            wlx = synth.workload(name)
+            if world > 1:             # a fixed total split across the replicas
+                wlx = replicas.shard_workload(wlx, rank, world)
+            Ix = prepare(wlx, "")
+            rx, _, _ = forward(Ix, max(5, args.steps // 2), args.warmup, 1, sharded=world > 1)
+            rx["roofline"] = roofline_of(Ix, rx)
+            rx["workload"] = desc
+            rx["scaling"] = "strong" if world > 1 else "single GPU"
+            line["workloads"][name] = rx
+            release(Ix)
+            del wlx
+
     if rank == 0 and not args.no_cpu_baseline:
-        rate, n, el = cpu_oracle_rate(wl, P, args.cpu_seconds)
+        rate, n, el = cpu_oracle_rate(wl, P_head, args.cpu_seconds)
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
-                                "sample": f"{n} whole state(s) x {N} bins of the same workload, {el:.1f} s"}
+                                "sample": f"{n} whole state(s) x {wl.n_bins} bins of the same workload, {el:.1f} s"}
     if rank == 0:
         print(json.dumps(line), flush=True)
-    ds.close()
     if world > 1:
         dist.destroy_process_group()
     return 0
@@ -392,6 +541,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-states", type=int, default=4, help="states per reference step")
     ap.add_argument("--tiling", default="", help="tile_bins,states_per_cta,group (skips the autotuner)")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the adjoint, batched-dataset and full-form workloads")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -185,7 +185,8 @@ lisa_status lisa_spline_setup(const lisa_data* data, const lisa_knots* knots,
 
 /* ---- log-likelihood ------------------------------------------------------------------------ */
 
-/* Bytes of scratch workspace the likelihood entry points need (per-state partial sums).
+/* Bytes of scratch workspace the likelihood entry points need (per-(state, tile) partial sums
+ * and per-state FP32 parameters).
  * with_grad = 0 for lisa_psd_loglike, 1 for lisa_psd_loglike_grad. */
 size_t lisa_workspace_bytes(const lisa_data* data, int32_t kmax, lisa_precision precision,
                             int32_t with_grad);
@@ -231,8 +232,9 @@ lisa_status lisa_model_psd(const lisa_data* data, const lisa_params* params,
  * fixed-size array that lives in the library's own device image, so the call allocates nothing.
  *
  *  - The array holds LISA_NOALLOC_SCRATCH_BYTES (4 MiB): 256 bytes plus 8 bytes per
- *    (state, tile) partial sum, i.e. lisa_workspace_bytes(data, kmax, precision, 0) must not
- *    exceed it (the paper-scale workload needs about 1 MiB).  Larger problems get
+ *    (state, tile) partial sum plus 48 bytes of FP32 parameters per state (each region rounded
+ *    up to 256 bytes), i.e. lisa_workspace_bytes(data, kmax, precision, 0) must not exceed it
+ *    (the paper-scale workload needs about 1 MiB).  Larger problems get
  *    LISA_ERR_WORKSPACE and nothing is launched; use lisa_psd_loglike for them.
  *  - Every GPU that loads the library holds the array until the process exits.
  *  - The first call on each device looks the array's device address up (with that device

@@ -12,7 +12,7 @@ import itertools
 
 from . import binding as B
 
-DEFAULT_TILES = (256, 384, 448, 512, 768, 1024)
+DEFAULT_TILES = (256, 320, 384, 448, 512, 768, 1024)
 DEFAULT_STATES = (64, 128)
 DEFAULT_GROUPS = (2, 4, 8)
 

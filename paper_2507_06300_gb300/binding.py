@@ -61,7 +61,9 @@ class lisa_data_info(ctypes.Structure):
 
 EXPORTS = ["lisa_data_create", "lisa_data_destroy", "lisa_data_get_info", "lisa_data_set_tiling",
            "lisa_spline_buf_bytes", "lisa_spline_setup", "lisa_workspace_bytes", "lisa_psd_loglike",
-           "lisa_psd_loglike_grad", "lisa_model_psd", "lisa_psd_loglike_noalloc", "lisa_status_string"]
+           "lisa_psd_loglike_grad", "lisa_model_psd", "lisa_psd_loglike_noalloc", "lisa_status_string",
+           "lisa_pipe_rates", "lisa_data_set_profiling", "lisa_data_kernel_ms"]
+PIPE_OPS = ("ex2", "rcp", "lg2_ex2", "ffma", "ffma2")   # order of lisa_pipe_op
 NOALLOC_SCRATCH_BYTES = 4 * 1024 * 1024
 
 _lock = threading.Lock()
@@ -115,6 +117,12 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         lib.lisa_psd_loglike_noalloc.restype = S
         lib.lisa_status_string.argtypes = [_c_i32]
         lib.lisa_status_string.restype = ctypes.c_char_p
+        lib.lisa_pipe_rates.argtypes = [_c_i32, _c_i32, ctypes.POINTER(_c_dbl), _c_vp]
+        lib.lisa_pipe_rates.restype = S
+        lib.lisa_data_set_profiling.argtypes = [_c_vp, _c_i32]
+        lib.lisa_data_set_profiling.restype = S
+        lib.lisa_data_kernel_ms.argtypes = [_c_vp, ctypes.POINTER(ctypes.c_float)]
+        lib.lisa_data_kernel_ms.restype = S
         _lib = lib
         return lib
 
@@ -224,6 +232,16 @@ class Dataset:
         t = lisa_tiling(int(tile_bins), int(states_per_cta), int(group), int(ctas_per_sm))
         _check(load().lisa_data_set_tiling(self._h, ctypes.byref(t)), "lisa_data_set_tiling")
 
+    def set_profiling(self, enable=True):
+        """``lisa_data_set_profiling``: record per-kernel events in uncaptured likelihood calls."""
+        _check(load().lisa_data_set_profiling(self._h, int(bool(enable))), "lisa_data_set_profiling")
+
+    def kernel_ms(self):
+        """``lisa_data_kernel_ms`` of the last recorded call: (main, compensated, finalize) in ms."""
+        ms = (ctypes.c_float * 3)()
+        _check(load().lisa_data_kernel_ms(self._h, ms), "lisa_data_kernel_ms")
+        return tuple(float(v) for v in ms)
+
     # ---- sizes ----------------------------------------------------------------------------
     def spline_buf_bytes(self, kmax, precision):
         return int(load().lisa_spline_buf_bytes(self._h, int(kmax), int(precision)))
@@ -256,6 +274,15 @@ class Dataset:
         a256 = lambda b: (b + 255) // 256 * 256
         off = a256(4 * self.n_states) + a256(4 * self.n_states * self.n_splines)
         return int(buf[off:off + 4].cpu().view(dtype=__import__("torch").int32)[0])
+
+    def routed_list(self, buf):
+        """State indices the last FP32 lisa_spline_setup on ``buf`` routed to the compensated
+        kernel, ascending (diagnostic; synchronises)."""
+        torch = _torch()
+        a256 = lambda b: (b + 255) // 256 * 256
+        off = a256(4 * self.n_states) + a256(4 * self.n_states * self.n_splines)
+        words = buf[off:off + 4 * (self.n_states + 1)].cpu().view(dtype=torch.int32).numpy()
+        return np.sort(words[1:1 + int(words[0])]).astype(np.int64)
 
     def psd_loglike(self, theta, buf, kmax, precision=FP32, out=None, workspace=None, stream=None):
         """``lisa_psd_loglike``: theta [S, 5] f64 device -> log L [S] f64 device."""
@@ -312,6 +339,14 @@ class Dataset:
         _check(load().lisa_model_psd(self._h, ctypes.byref(pr), buf64.data_ptr(), buf64.numel(), int(kmax),
                                      out.data_ptr(), _stream_handle(stream)), "lisa_model_psd")
         return out
+
+
+def pipe_rates(iters=2048, reps=3, stream=None) -> dict:
+    """``lisa_pipe_rates``: measured lane operations per second of the MUFU and FP32 pipes on the
+    current device, keyed by PIPE_OPS (a packed FMA counts two).  Synchronises."""
+    out = (_c_dbl * len(PIPE_OPS))()
+    _check(load().lisa_pipe_rates(int(iters), int(reps), out, _stream_handle(stream)), "lisa_pipe_rates")
+    return {k: float(out[i]) for i, k in enumerate(PIPE_OPS)}
 
 
 def knots_to_device(knots, device="cuda"):

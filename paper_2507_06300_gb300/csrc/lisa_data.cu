@@ -128,6 +128,11 @@ lisa_status dev_alloc(T** p, size_t n) {
 }
 
 void release(lisa_data* d) {
+    for (auto& e : d->prof_ev) {
+        if (e) cudaEventDestroy(e);
+        e = nullptr;
+    }
+    d->prof_on = false;
     cudaFree(d->d_ds);
     cudaFree(d->d_state_ds);
     cudaFree(d->d_rec32);
@@ -383,6 +388,17 @@ lisa_status lisa_data_destroy(lisa_data* d) {
     if (!d) return LISA_ERR_NULL;
     release(d);
     delete d;
+    return LISA_SUCCESS;
+}
+
+lisa_status lisa_data_set_profiling(lisa_data* d, int32_t enable) {
+    if (!d) return LISA_ERR_NULL;
+    if (enable && !d->prof_on) {
+        for (auto& e : d->prof_ev)
+            if (!e && cudaEventCreate(&e) != cudaSuccess) return LISA_ERR_CUDA;
+    }
+    d->prof_on = enable != 0;
+    d->prof_valid = false;
     return LISA_SUCCESS;
 }
 

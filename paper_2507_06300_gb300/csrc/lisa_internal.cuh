@@ -97,8 +97,8 @@ struct lisa_data {
     float* d_rec32 = nullptr;        // [n_pad / 2][kPairRec]
     double* d_rec64 = nullptr;       // [n_pad][kRec]
     double* d_P = nullptr;           // [C][n_bins] periodogram (unpadded; normaliser of the tables)
-    float* d_xlo32 = nullptr;        // [n_bins] log10 f - (float)log10 f (low part of x)
-    float* d_elllo32 = nullptr;      // [n_bins] low part of ell = log2(f / f_ref)
+    float* d_xlo32 = nullptr;        // [n_pad] log10 f - (float)log10 f (low part of x)
+    float* d_elllo32 = nullptr;      // [n_pad] low part of ell = log2(f / f_ref)
     lisa_tiling tiling{};
     lisa::WorkItem* d_items = nullptr;
     lisa::AdjUnit* d_adj_units = nullptr;
@@ -107,6 +107,11 @@ struct lisa_data {
     int64_t adj_ranges = 0;          // sum over states of their dataset's ranges
     int64_t n_items = 0;
     int64_t n_partials = 0;          // sum over datasets of states x tiles
+    // per-kernel timing of lisa_psd_loglike (lisa_data_set_profiling): events around the main,
+    // compensated and finalize kernels of the most recent uncaptured call
+    cudaEvent_t prof_ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    bool prof_on = false;
+    mutable bool prof_valid = false;
 };
 
 namespace lisa {
@@ -132,8 +137,20 @@ inline SplineLayout spline_layout(int64_t S, int nsp, int kmax) {
 
 // Workspace layout of the forward entry point:
 //   int32 err flag (256 B) | double partial[n_partials]
+// Per-state FP32 parameters, derived once per likelihood call from theta (FP64) so that the
+// per-bin kernels touch no FP64 arithmetic: a_oms^2, a_tm^2, A = 10^log10A, the SGWB slopes,
+// and log2 A and the slopes as float-float pairs for the compensated kernel.
+struct StateParams {
+    float ao2, at2, Af, n1;
+    float n2, lA_hi, lA_lo, n1_lo;
+    float n2_lo, pad0, pad1, pad2;
+};
+static_assert(sizeof(StateParams) == 48, "three float4");
+
+// Forward workspace: error flag | FP64 partial sums [state][tile] | StateParams [S].
+inline size_t ws_partials_bytes(const lisa_data* d) { return align256(sizeof(double) * (size_t)d->n_partials); }
 inline size_t ws_fwd_bytes(const lisa_data* d) {
-    return 256 + align256(sizeof(double) * (size_t)d->n_partials);
+    return 256 + ws_partials_bytes(d) + align256(sizeof(StateParams) * (size_t)d->n_states);
 }
 
 // Extra workspace of the adjoint entry point (after the forward region).

@@ -150,6 +150,11 @@ __device__ __forceinline__ float bin_term32(const float* __restrict__ tb, int i,
     return term_from_S<C>(S, nu);
 }
 
+// Safe range of the unguarded pair form: the channel product within 2^(+-99), so that its
+// reciprocal and log2 are accurate and normal.  An overflowing reciprocal-sum numerator (one
+// channel far below the others) makes the chunk sum infinite, which is checked as well.
+constexpr float kPairLg2Max = 99.0f;
+
 // 10^v as a float without the FP64 exp10: 2^(v log2 10) split into an exact integer power of
 // two and a fractional part in [0, 1) handled by ex2 (one FP64 multiply, ~2 ulp).
 __device__ __forceinline__ float exp10_to_float(double v) {
@@ -159,6 +164,29 @@ __device__ __forceinline__ float exp10_to_float(double v) {
     if (n > 127.0) return INFINITY;
     const float f = ex2_approx((float)(e - n));
     return n >= -126.0 ? f * __int_as_float(((int)n + 127) << 23) : ldexpf(f, (int)n);
+}
+
+// Per-state FP32 parameters from theta (FP64), once per call: the per-bin kernels then need no
+// FP64 arithmetic.  Non-finite theta propagates (the state's log L becomes -inf).
+__global__ void state_prep_kernel(int S, const double* __restrict__ theta, StateParams* __restrict__ prm) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= S) return;
+    const double* th = theta + (size_t)s * LISA_N_THETA;
+    StateParams p;
+    p.ao2 = (float)(th[0] * th[0]);
+    p.at2 = (float)(th[1] * th[1]);
+    p.Af = exp10_to_float(th[2]);
+    const ff lA = ff_from_double(th[2] * kLog2_10);
+    const ff n1 = ff_from_double(th[3]);
+    const ff n2 = ff_from_double(th[4]);
+    p.n1 = n1.hi;
+    p.n1_lo = n1.lo;
+    p.n2 = n2.hi;
+    p.n2_lo = n2.lo;
+    p.lA_hi = lA.hi;
+    p.lA_lo = lA.lo;
+    p.pad0 = p.pad1 = p.pad2 = 0.f;
+    prm[s] = p;
 }
 
 // Current interval of one spline duplicated into register pairs for the packed path.
@@ -187,11 +215,26 @@ __device__ __forceinline__ Iv2 dup(const Iv32& v) {
                make_float2(v.c2, v.c2), make_float2(v.c3, v.c3)};
 }
 
+// Three-input maximum / minimum (one instruction on sm_100 and later).
+__device__ __forceinline__ float fmax3(float a, float b, float c) {
+    float d;
+    asm("max.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+    return d;
+}
+__device__ __forceinline__ float fmin3(float a, float b, float c) {
+    float d;
+    asm("min.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+    return d;
+}
+
 // Two consecutive bins (one pair block) with FP32x2 instructions; both bins lie in the current
-// intervals.  Returns nu * (sum_c 1/S_c + ln prod S_c - C) for both bins.
+// intervals.  Returns nu * (sum_c 1/S_c + ln prod S_c - C) for both bins, formed from one
+// reciprocal and one log2 of the channel product without a range test: the caller keeps the
+// running maximum (mx) and minimum (mi) of log2 prod and recomputes the chunk on the guarded
+// scalar path when either left +-kPairLg2Max or the chunk sum is not finite.
 template <int C, bool HAS_H, bool BROKEN>
 __device__ __forceinline__ float2 pair_term32(const float4* __restrict__ blk, const Iv2* iv, float2 ao2, float2 at2,
-                                              float n1, float n2, float2 Af) {
+                                              float n1, float n2, float2 Af, float& mx, float& mi) {
     constexpr int NSP = C + (HAS_H ? 1 : 0);
     const float4 q0 = blk[0], q1 = blk[1], q2 = blk[2], q3 = blk[3], q4 = blk[4], q5 = blk[5];
     const float2 x = make_float2(q0.x, q0.y), ell = make_float2(q0.z, q0.w), nu = make_float2(q1.x, q1.y);
@@ -226,33 +269,25 @@ __device__ __forceinline__ float2 pair_term32(const float4* __restrict__ blk, co
         prod = __fmul2_rn(S[0], S[1]);
         num = __fadd2_rn(S[0], S[1]);
     }
-    float2 v, lg;
-    if (fminf(prod.x, prod.y) > 1e-30f && fmaxf(prod.x, prod.y) < 1e30f && fmaxf(num.x, num.y) < 1e30f) {
-        v = __ffma2_rn(num, make_float2(rcp_approx(prod.x), rcp_approx(prod.y)), make_float2(-(float)C, -(float)C));
-        lg = make_float2(lg2_approx(prod.x), lg2_approx(prod.y));
-    } else {
-        v = make_float2(-(float)C, -(float)C);
-        lg = make_float2(0.f, 0.f);
-#pragma unroll
-        for (int c = 0; c < C; ++c) {
-            v = __fadd2_rn(v, make_float2(rcp_approx(S[c].x), rcp_approx(S[c].y)));
-            lg = __fadd2_rn(lg, make_float2(lg2_approx(S[c].x), lg2_approx(S[c].y)));
-        }
-    }
+    const float2 v = __ffma2_rn(num, make_float2(rcp_approx(prod.x), rcp_approx(prod.y)),
+                                make_float2(-(float)C, -(float)C));
+    const float2 lg = make_float2(lg2_approx(prod.x), lg2_approx(prod.y));
+    mx = fmax3(mx, lg.x, lg.y);
+    mi = fmin3(mi, lg.x, lg.y);
     return __fmul2_rn(nu, __ffma2_rn(make_float2((float)kLn2, (float)kLn2), lg, v));
 }
 
 template <int C, bool HAS_H, bool BROKEN, int G>
-__global__ void __launch_bounds__(kThreads32, 5)
+__global__ void __launch_bounds__(kThreads32, G == 8 ? 5 : 6)
     loglike_fp32_kernel(const WorkItem* __restrict__ items, int n_items, const float* __restrict__ rec32,
-                        const double* __restrict__ theta, const int32_t* __restrict__ sstat,
+                        const StateParams* __restrict__ prm, const int32_t* __restrict__ sstat,
                         const int32_t* __restrict__ nint, const float* __restrict__ srec, int kmax, int nsp,
                         const DatasetDev* __restrict__ ds, double* __restrict__ partial, int* __restrict__ err,
                         int tile_bins) {
     constexpr int NSP = C + (HAS_H ? 1 : 0);
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ __align__(8) uint64_t bars[2];
-    __shared__ double red[kThreads32];
+    __shared__ float2 red[kThreads32];
     float* sbuf0 = reinterpret_cast<float*>(smem);
     float* sbuf1 = reinterpret_cast<float*>(smem + (size_t)tile_bins * kRec * sizeof(float));
     const int tid = threadIdx.x;
@@ -296,33 +331,46 @@ __global__ void __launch_bounds__(kThreads32, 5)
         const int ls = tid & (sc - 1);
         const int r = tid / sc;
         const int s = w.s0 + ls;
-        const bool active = ls < w.ns && sstat[s] == 0;   // invalid and routed states skip
-        double acc64 = 0.0;
+        // every valid state, routed ones included: the bins of an ill-conditioned interval are
+        // masked out here (the compensated kernel adds them), all other bins are summed here
+        const bool active = ls < w.ns && (sstat[s] & kUserBits) == 0;
+        ff accf = {0.f, 0.f};
         if (active) {
             const int np = w.nb >> 1;                          // pair blocks in the tile
-            const int lo = 2 * ((r * np) / R), hi = 2 * (((r + 1) * np) / R);
-            if (lo < hi) {
-                const double* th = theta + (size_t)s * LISA_N_THETA;
-                const float ao2 = (float)(th[0] * th[0]);
-                const float at2 = (float)(th[1] * th[1]);
-                const float Af = HAS_H ? exp10_to_float(th[2]) : 0.f;
-                const float n1 = (float)th[3];
-                const float n2 = BROKEN ? (float)th[4] : n1;
+            const int plo = (r * np) / R, phi = ((r + 1) * np) / R;
+            if (plo < phi) {
+                const float4 q0 = __ldg(reinterpret_cast<const float4*>(prm + s));
+                const float ao2 = q0.x, at2 = q0.y, Af = HAS_H ? q0.z : 0.f, n1 = q0.w;
+                const float n2 = BROKEN ? __ldg(&prm[s].n2) : n1;
                 const float2 ao2_2 = make_float2(ao2, ao2), at2_2 = make_float2(at2, at2), Af2 = make_float2(Af, Af);
                 // per spline: right knot of the current interval, its index, and the interval's
-                // cubic duplicated into register pairs (the scalar path reads the .x halves)
+                // cubic duplicated into register pairs (the scalar path reads the .x halves);
+                // xmin = the nearest right knot.  An ill-conditioned interval (T > kRobustT, routed
+                // states only) is loaded as the zero cubic, which keeps its bins' arithmetic benign,
+                // and sets its bit in hm; keep2 = 0 while any bit is set, 1 otherwise, and scales
+                // each pair's contribution.
                 float xr[NSP];
                 int jj[NSP];
                 Iv2 iv2[NSP];
-                const float x0 = fld(tb, lo, 0);
+                float xmin = INFINITY;
+                unsigned hm = 0;
+                float2 keep2 = make_float2(1.f, 1.f);
                 const int64_t sp0 = (int64_t)s * nsp;
                 auto reload = [&](int a) {
-                    const float* r = srec + ((sp0 + a) * (int64_t)(kmax + 1) + jj[a]) * kSplineRec32;
-                    const float4 A = __ldg(reinterpret_cast<const float4*>(r));
-                    const float4 B = __ldg(reinterpret_cast<const float4*>(r + 4));
+                    const float* rr = srec + ((sp0 + a) * (int64_t)(kmax + 1) + jj[a]) * kSplineRec32;
+                    const float4 A = __ldg(reinterpret_cast<const float4*>(rr));
+                    const float4 B = __ldg(reinterpret_cast<const float4*>(rr + 4));
                     xr[a] = A.x;
-                    iv2[a] = Iv2{make_float2(-A.y, -A.y), make_float2(A.z, A.z), make_float2(A.w, A.w),
-                                 make_float2(B.x, B.x), make_float2(B.y, B.y)};
+                    if (B.w <= (float)kRobustT) {
+                        iv2[a] = Iv2{make_float2(-A.y, -A.y), make_float2(A.z, A.z), make_float2(A.w, A.w),
+                                     make_float2(B.x, B.x), make_float2(B.y, B.y)};
+                        hm &= ~(1u << a);
+                    } else {
+                        const float2 z = make_float2(0.f, 0.f);
+                        iv2[a] = Iv2{z, z, z, z, z};
+                        hm |= 1u << a;
+                    }
+                    keep2 = hm ? make_float2(0.f, 0.f) : make_float2(1.f, 1.f);
                 };
                 auto advance = [&](int a, float x) {
                     if (x >= xr[a]) {
@@ -336,63 +384,86 @@ __global__ void __launch_bounds__(kThreads32, 5)
                         if (moved) reload(a);
                     }
                 };
+                auto locate = [&](float x) {
 #pragma unroll
-                for (int a = 0; a < NSP; ++a) {
-                    const float* base = srec + (sp0 + a) * (int64_t)(kmax + 1) * kSplineRec32;
-                    jj[a] = find_interval<float, kSplineRec32, 6>(base, nint[sp0 + a], x0);
-                    reload(a);
-                }
-                ff accf = {0.f, 0.f};
-                int i = lo;
-                while (i < hi) {
-                    const int cend = min(i + 32, hi);
+                    for (int a = 0; a < NSP; ++a) {
+                        jj[a] = find_interval<float, kSplineRec32, 6>(
+                            srec + (sp0 + a) * (int64_t)(kmax + 1) * kSplineRec32, nint[sp0 + a], x);
+                        reload(a);
+                    }
+                };
+                auto nearest = [&]() {
+                    float m = xr[0];
+#pragma unroll
+                    for (int a = 1; a < NSP; ++a) m = fminf(m, xr[a]);
+                    return m;
+                };
+                // one bin on the scalar path (next to knots): advance, then the guarded term
+                auto scalar_bin = [&](int i) {
+                    const float x = fld(tb, i, 0);
+#pragma unroll
+                    for (int a = 0; a < NSP; ++a) advance(a, x);
+                    const float v = bin_term32p<C, HAS_H, BROKEN>(tb, i, iv2, ao2, at2, n1, n2, Af);
+                    return hm ? 0.f : v;
+                };
+                locate(fld(tb, 2 * plo, 0));
+                xmin = nearest();
+                int ip = plo;
+                while (ip < phi) {
+                    const int pc0 = ip;
+                    const int pcend = min(ip + 16, phi);
                     float2 acc2 = make_float2(0.f, 0.f);
-                    for (; i + G <= cend; i += G) {
-                        const float xg = fld(tb, i + G - 1, 0);
-                        bool fast = true;
+                    float mx = 0.f, mi = 0.f;
+                    for (; ip + G / 2 <= pcend; ip += G / 2) {
+                        const float4* blk = tb4 + ip * (kPairRec / 4);
+                        // x of the group's last bin (odd bin of its last pair block)
+                        const float xg = reinterpret_cast<const float*>(blk + (G / 2 - 1) * (kPairRec / 4))[1];
+                        if (xg < xmin) {
 #pragma unroll
-                        for (int a = 0; a < NSP; ++a) fast &= xg < xr[a];
-                        if (fast) {
-#pragma unroll
-                            for (int g = 0; g < G; g += 2)
-                                acc2 = __fadd2_rn(acc2, pair_term32<C, HAS_H, BROKEN>(tb4 + ((i + g) >> 1) * (kPairRec / 4),
-                                                                                      iv2, ao2_2, at2_2, n1, n2, Af2));
+                            for (int g = 0; g < G / 2; ++g)
+                                acc2 = __ffma2_rn(keep2, pair_term32<C, HAS_H, BROKEN>(blk + g * (kPairRec / 4), iv2,
+                                                                                       ao2_2, at2_2, n1, n2, Af2, mx, mi),
+                                                  acc2);
                         } else {
 #pragma unroll 1
-                            for (int g = 0; g < G; ++g) {
-                                const float x = fld(tb, i + g, 0);
-#pragma unroll
-                                for (int a = 0; a < NSP; ++a) advance(a, x);
-                                acc2.x += bin_term32p<C, HAS_H, BROKEN>(tb, i + g, iv2, ao2, at2, n1, n2, Af);
-                            }
+                            for (int i = 2 * ip; i < 2 * ip + G; ++i) acc2.x += scalar_bin(i);
+                            xmin = nearest();
                         }
                     }
 #pragma unroll 1
-                    for (; i < cend; ++i) {
-                        const float x = fld(tb, i, 0);
-#pragma unroll
-                        for (int a = 0; a < NSP; ++a) advance(a, x);
-                        acc2.x += bin_term32p<C, HAS_H, BROKEN>(tb, i, iv2, ao2, at2, n1, n2, Af);
+                    for (; ip < pcend; ++ip) {
+                        acc2.x += scalar_bin(2 * ip);
+                        acc2.x += scalar_bin(2 * ip + 1);
+                        xmin = nearest();
+                    }
+                    if (!(mx <= kPairLg2Max && mi >= -kPairLg2Max && fabsf(acc2.x + acc2.y) < INFINITY)) {
+                        // a channel product left the range of the one-reciprocal form (or the
+                        // reciprocal-sum numerator overflowed): redo the chunk bin by bin on the
+                        // guarded path, intervals re-found at its start
+                        locate(fld(tb, 2 * pc0, 0));
+                        acc2 = make_float2(0.f, 0.f);
+#pragma unroll 1
+                        for (int i = 2 * pc0; i < 2 * pcend; ++i) acc2.x += scalar_bin(i);
+                        xmin = nearest();
                     }
                     accf = ff_add(accf, two_sum(acc2.x, acc2.y));
                 }
-                acc64 = (double)accf.hi + (double)accf.lo;
             }
         }
-        red[tid] = acc64;
+        red[tid] = make_float2(accf.hi, accf.lo);
         __syncthreads();
-        if (r == 0 && ls < w.ns && sstat[s] == 0) {
-            double sum = 0.0;
-            for (int q = 0; q < R; ++q) sum += red[ls + q * sc];
+        if (r == 0 && active) {
+            ff sum = {red[ls].x, red[ls].y};
+            for (int q = 1; q < R; ++q) sum = ff_add(sum, ff{red[ls + q * sc].x, red[ls + q * sc].y});
             const DatasetDev& D = ds[w.ds];
-            partial[D.pbase + (int64_t)(s - D.s0) * D.ntiles + w.tile] = sum;
+            partial[D.pbase + (int64_t)(s - D.s0) * D.ntiles + w.tile] = (double)sum.hi + (double)sum.lo;
         }
         __syncthreads();  // the buffer read in this iteration is refilled in the next one
     }
 }
 
 
-// ---- compensated path for states the setup routed away from the FP32 kernel --------------
+// ---- compensated path: the ill-conditioned intervals of the states the setup routed ------
 struct IvR {
     float xr, T;
     ff xo, c[4];
@@ -453,44 +524,154 @@ __device__ __forceinline__ ff inv_plus_log(ff lS, float nu, double& far) {
     return ff{0.f, 0.f};
 }
 
-// One warp per (routed state, tile); lane l takes bins l, l + 32, ... of the tile.  Spline values
-// are float-float sums where the interval is ill-conditioned; a bin whose intervals are all
-// well-conditioned uses the ordinary FP32 term, any other bin the log-domain term.
+// Compensated kernel staging: each warp copies its tile in chunks of kRobChunk bins (pair-block
+// table plus the low parts of x and ell) into its own shared-memory slice with coalesced loads,
+// then evaluates the chunk from shared memory.
+constexpr int kRobWarps = 4;
+constexpr int kRobChunk = 256;                                    // even
+constexpr int kRobChunkF4 = kRobChunk / 2 * (kPairRec / 4);       // float4 of table per chunk
+constexpr int kRobSliceF4 = kRobChunkF4 + 2 * kRobChunk / 4;      // + x lo, ell lo
+constexpr size_t kRobSmem = (size_t)kRobWarps * kRobSliceF4 * sizeof(float4);
+constexpr int kRobTiles = 1;                                      // tiles per warp unit
+
+// One bin of a routed state (i: bin within the staged chunk tb, with the low parts of x and ell
+// in xs / es), evaluated only if one of its spline intervals is ill-conditioned (the fused kernel
+// masks exactly those bins and sums all others): spline values as float-float sums on the
+// ill-conditioned intervals, then the moderate-exponent or the log-domain term.
 template <int C, bool HAS_H, bool BROKEN>
-__global__ void __launch_bounds__(128)
+__device__ __forceinline__ void robust_bin(const float* __restrict__ tb, int i, const float* __restrict__ xs,
+                                           const float* __restrict__ es, IvR* iv, float ao2, float at2, ff n1,
+                                           ff n2, ff lA, ff& acc_ff, double& far) {
+    constexpr int NSP = C + (HAS_H ? 1 : 0);
+    const float x_hi = fld(tb, i, 0);
+    bool hard = false;
+#pragma unroll
+    for (int a = 0; a < NSP; ++a) {
+        while (x_hi >= iv[a].xr && iv[a].j < iv[a].last) {
+            ++iv[a].j;
+            load_ivr(iv[a]);
+        }
+        hard |= !(iv[a].T <= (float)kRobustT);
+    }
+    if (!hard) return;
+    const float nu = fld(tb, i, 2);
+    const ff x = {x_hi, xs[i]};
+    ff P[NSP];
+#pragma unroll
+    for (int a = 0; a < NSP; ++a) {
+        if (!(iv[a].T <= (float)kRobustT)) {
+            const ff tt = ff_add(x, ff{-iv[a].xo.hi, -iv[a].xo.lo});
+            ff p = iv[a].c[3];
+            p = ff_add(ff_mul(p, tt), iv[a].c[2]);
+            p = ff_add(ff_mul(p, tt), iv[a].c[1]);
+            P[a] = ff_add(ff_mul(p, tt), iv[a].c[0]);
+        } else {
+            const float tt = x.hi - iv[a].xo.hi;
+            P[a] = ff{fmaf(fmaf(fmaf(iv[a].c[3].hi, tt, iv[a].c[2].hi), tt, iv[a].c[1].hi), tt, iv[a].c[0].hi), 0.f};
+        }
+    }
+    const ff ell = {fld(tb, i, 1), es[i]};
+    ff lEh = {-INFINITY, 0.f};
+    if (HAS_H) {
+        const ff sl = BROKEN ? (ell.hi < 0.f ? n1 : n2) : n1;
+        lEh = ff_add(ff_add(P[C], ff_mul(sl, ell)), lA);
+    }
+    bool moderate = true;
+#pragma unroll
+    for (int c = 0; c < C; ++c) moderate &= fabsf(P[c].hi) < 60.f;
+    if (HAS_H) moderate &= fabsf(P[C].hi) < 60.f && lEh.hi > -120.f && lEh.hi < 60.f;
+    if (moderate) {
+        // exponents within FP32 range: 2^(hi + lo) = ex2(hi) (1 + lo ln2), accurate to a few ulp
+        // because hi is exact; then the ordinary FP32 term
+        float S[C];
+        const float eh = HAS_H ? ex2_approx(lEh.hi) * fmaf(lEh.lo, (float)kLn2, 1.f) : 0.f;
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+            const float E = ex2_approx(P[c].hi) * fmaf(P[c].lo, (float)kLn2, 1.f);
+            const float N = fmaf(ao2, fld(tb, i, 3 + c), at2 * fld(tb, i, 6 + c));
+            S[c] = HAS_H ? fmaf(E, N, eh * fld(tb, i, 9 + c)) : E * N;
+        }
+        acc_ff = ff_add(acc_ff, ff{term_from_S<C>(S, nu), 0.f});
+        return;
+    }
+    ff term = {-(float)C, 0.f};
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+        const float N = fmaf(ao2, fld(tb, i, 3 + c), at2 * fld(tb, i, 6 + c));
+        const ff lN = lg2_split(N);
+        const ff lNE = (lN.hi > -INFINITY && lN.hi < INFINITY) ? ff_add(P[c], lN) : lN;
+        ff lS = lNE;
+        if (HAS_H) {
+            const ff lG = lg2_split(fld(tb, i, 9 + c));
+            const ff lH = (lG.hi > -INFINITY && lG.hi < INFINITY) ? ff_add(lEh, lG) : lG;
+            lS = log2_sum(lNE, lH);
+        }
+        term = ff_add(term, inv_plus_log(lS, nu, far));
+    }
+    acc_ff = ff_add(acc_ff, ff_mul(term, ff{nu, 0.f}));
+}
+
+// One warp per (routed state, run of kRobTiles consecutive tiles), kRobWarps warps per CTA.  A
+// run that no ill-conditioned interval of the state overlaps is skipped.  Otherwise the warp
+// stages each tile chunk by chunk into its shared-memory slice; lane l then takes bins l, l + 32,
+// ... of the chunk (the lanes of a warp mostly share their spline intervals), so a lane's bins
+// come in increasing order and its intervals carry over from tile to tile.  Each tile's sum of
+// ill-conditioned bins is added to the (state, tile) partial the fused kernel wrote.
+template <int C, bool HAS_H, bool BROKEN>
+__global__ void __launch_bounds__(kRobWarps * 32)
     loglike_robust_kernel(const int32_t* __restrict__ route, const int32_t* __restrict__ state_ds,
-                          const DatasetDev* __restrict__ ds, int tile_bins, int max_tiles,
+                          const DatasetDev* __restrict__ ds, int tile_bins, int max_runs,
                           const float* __restrict__ rec32, const float* __restrict__ xlo32,
-                          const float* __restrict__ elllo32, const double* __restrict__ theta,
+                          const float* __restrict__ elllo32, const StateParams* __restrict__ prm,
                           const int32_t* __restrict__ nint, const float* __restrict__ srec, int kmax, int nsp,
                           double* __restrict__ partial) {
     constexpr int NSP = C + (HAS_H ? 1 : 0);
+    extern __shared__ float4 rsm[];
     const int lane = threadIdx.x & 31;
+    float4* slice = rsm + (threadIdx.x >> 5) * kRobSliceF4;
+    const float* tb = reinterpret_cast<const float*>(slice);
+    float* xs = reinterpret_cast<float*>(slice + kRobChunkF4);
+    float* es = xs + kRobChunk;
     const int64_t wg = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    const int64_t units = (int64_t)route[0] * max_tiles;
+    const int64_t units = (int64_t)route[0] * max_runs;
     for (int64_t u = wg; u < units; u += nw) {
-        const int r = (int)(u / max_tiles), t = (int)(u % max_tiles);
+        const int r = (int)(u / max_runs), t0 = (int)(u % max_runs) * kRobTiles;
         const int s = route[1 + r];
         const DatasetDev& D = ds[state_ds[s]];
-        if (t >= D.ntiles) continue;                         // uniform per warp
-        const double* th = theta + (size_t)s * LISA_N_THETA;
-        const float ao2 = (float)(th[0] * th[0]);
-        const float at2 = (float)(th[1] * th[1]);
-        const float Af = HAS_H ? exp10_to_float(th[2]) : 0.f;
-        const ff lA = ff_from_double(th[2] * kLog2_10);
-        const ff n1 = ff_from_double(th[3]);
-        const ff n2 = BROKEN ? ff_from_double(th[4]) : n1;
-        const int64_t b0 = D.bin0 + (int64_t)t * tile_bins;   // even
-        const int nb = (int)min((int64_t)tile_bins, D.bin0 + D.npad - b0);
-        const float* tbase = rec32 + (b0 >> 1) * kPairRec;
-        double acc = 0.0;
-        if (lane < nb) {
-            // lanes take consecutive bins (lane, lane + 32, ...): coalesced table reads, and the
-            // lanes of a warp mostly share their spline intervals
-            IvR iv[NSP];
-            Iv32 iv32[NSP];
-            const float x0 = fld(tbase, lane, 0);
+        if (t0 >= D.ntiles) continue;                        // uniform per warp
+        const int t1 = min(t0 + kRobTiles, D.ntiles);
+        const float4 q0 = __ldg(reinterpret_cast<const float4*>(prm + s));
+        const float4 q1 = __ldg(reinterpret_cast<const float4*>(prm + s) + 1);
+        const float4 q2 = __ldg(reinterpret_cast<const float4*>(prm + s) + 2);
+        const float ao2 = q0.x, at2 = q0.y;
+        const ff n1 = {q0.w, q1.w};
+        const ff n2 = BROKEN ? ff{q1.x, q2.x} : n1;
+        const ff lA = {q1.y, q1.z};
+        {
+            // does any ill-conditioned interval overlap the run's bins?  (lanes over intervals)
+            const int64_t bA = D.bin0 + (int64_t)t0 * tile_bins;
+            const int64_t bB = min(D.bin0 + (int64_t)t1 * tile_bins, D.bin0 + D.npad) - 1;
+            const float xA = fld(rec32 + (bA >> 1) * kPairRec, (int)(bA & 1), 0);
+            const float xB = fld(rec32 + (bB >> 1) * kPairRec, (int)(bB & 1), 0);
+            bool hit = false;
+            for (int a = 0; a < NSP; ++a) {
+                const int64_t sp = (int64_t)s * nsp + a;
+                const float* base = srec + sp * (int64_t)(kmax + 1) * kSplineRec32;
+                const int n = nint[sp];
+                for (int j = lane; j < n; j += 32) {
+                    const float* rr = base + (size_t)j * kSplineRec32;
+                    const float xl = j == 0 ? -INFINITY : __ldg(rr + 6);
+                    hit |= !(__ldg(rr + 7) <= (float)kRobustT) && xl <= xB && __ldg(rr) > xA;
+                }
+            }
+            if (!__any_sync(0xffffffffu, hit)) continue;
+        }
+        IvR iv[NSP];
+        {
+            const int64_t b0 = D.bin0 + (int64_t)t0 * tile_bins;
+            const int nb = (int)min((int64_t)tile_bins, D.bin0 + D.npad - b0);
+            const float x0 = fld(rec32 + (b0 >> 1) * kPairRec, min(lane, nb - 1), 0);
 #pragma unroll
             for (int a = 0; a < NSP; ++a) {
                 const int64_t sp = (int64_t)s * nsp + a;
@@ -499,89 +680,36 @@ __global__ void __launch_bounds__(128)
                 iv[a].j = find_interval<float, kSplineRec32, 6>(iv[a].base, nint[sp], x0);
                 load_ivr(iv[a]);
             }
+        }
+        for (int t = t0; t < t1; ++t) {
+            const int64_t b0 = D.bin0 + (int64_t)t * tile_bins;   // even
+            const int nb = (int)min((int64_t)tile_bins, D.bin0 + D.npad - b0);
+            const float* tbase = rec32 + (b0 >> 1) * kPairRec;
             ff acc_ff = {0.f, 0.f};
             double far = 0.0;
-            for (int i = lane; i < nb; i += 32) {
-                const int64_t g = b0 + i;
-                const ff x = {fld(tbase, i, 0), __ldg(xlo32 + g)};
-                const float nu = fld(tbase, i, 2);
-                ff P[NSP];
-                bool hard = false;
-#pragma unroll
-                for (int a = 0; a < NSP; ++a) {
-                    while (x.hi >= iv[a].xr && iv[a].j < iv[a].last) {
-                        ++iv[a].j;
-                        load_ivr(iv[a]);
-                    }
-                    if (!(iv[a].T <= (float)kRobustT)) {
-                        hard = true;
-                        const ff tt = ff_add(x, ff{-iv[a].xo.hi, -iv[a].xo.lo});
-                        ff p = iv[a].c[3];
-                        p = ff_add(ff_mul(p, tt), iv[a].c[2]);
-                        p = ff_add(ff_mul(p, tt), iv[a].c[1]);
-                        P[a] = ff_add(ff_mul(p, tt), iv[a].c[0]);
-                    } else {
-                        const float tt = x.hi - iv[a].xo.hi;
-                        P[a] = ff{fmaf(fmaf(fmaf(iv[a].c[3].hi, tt, iv[a].c[2].hi), tt, iv[a].c[1].hi), tt,
-                                       iv[a].c[0].hi), 0.f};
-                    }
+            for (int c0 = 0; c0 < nb; c0 += kRobChunk) {
+                const int nbc = min(kRobChunk, nb - c0);
+                const float4* src = reinterpret_cast<const float4*>(tbase + (c0 >> 1) * kPairRec);
+                __syncwarp();                                // the previous chunk is consumed
+                for (int q = lane; q < (nbc >> 1) * (kPairRec / 4); q += 32) slice[q] = __ldg(src + q);
+                for (int q = lane; q < nbc; q += 32) {
+                    xs[q] = __ldg(xlo32 + b0 + c0 + q);
+                    es[q] = __ldg(elllo32 + b0 + c0 + q);
                 }
-                if (!hard) {
-#pragma unroll
-                    for (int a = 0; a < NSP; ++a) {
-                        iv32[a].xo = 0.f;
-                        iv32[a].c0 = P[a].hi;
-                        iv32[a].c1 = iv32[a].c2 = iv32[a].c3 = 0.f;
-                    }
-                    // the ordinary FP32 term with the spline values already evaluated
-                    acc_ff = ff_add(acc_ff, ff{bin_term32<C, HAS_H, BROKEN>(tbase, i, iv32, ao2, at2, (float)n1.hi,
-                                                                            (float)n2.hi, Af), 0.f});
-                    continue;
-                }
-                const ff ell = {fld(tbase, i, 1), __ldg(elllo32 + g)};
-                ff lEh = {-INFINITY, 0.f};
-                if (HAS_H) {
-                    const ff sl = BROKEN ? (ell.hi < 0.f ? n1 : n2) : n1;
-                    lEh = ff_add(ff_add(P[C], ff_mul(sl, ell)), lA);
-                }
-                bool moderate = true;
-#pragma unroll
-                for (int c = 0; c < C; ++c) moderate &= fabsf(P[c].hi) < 60.f;
-                if (HAS_H) moderate &= fabsf(P[C].hi) < 60.f && lEh.hi > -120.f && lEh.hi < 60.f;
-                if (moderate) {
-                    // exponents within FP32 range: 2^(hi + lo) = ex2(hi) (1 + lo ln2), accurate to
-                    // a few ulp because hi is exact; then the ordinary FP32 term
-                    float S[C];
-                    const float eh = HAS_H ? ex2_approx(lEh.hi) * fmaf(lEh.lo, (float)kLn2, 1.f) : 0.f;
-#pragma unroll
-                    for (int c = 0; c < C; ++c) {
-                        const float E = ex2_approx(P[c].hi) * fmaf(P[c].lo, (float)kLn2, 1.f);
-                        const float N = fmaf(ao2, fld(tbase, i, 3 + c), at2 * fld(tbase, i, 6 + c));
-                        S[c] = HAS_H ? fmaf(E, N, eh * fld(tbase, i, 9 + c)) : E * N;
-                    }
-                    acc_ff = ff_add(acc_ff, ff{term_from_S<C>(S, nu), 0.f});
-                    continue;
-                }
-                ff term = {-(float)C, 0.f};
-#pragma unroll
-                for (int c = 0; c < C; ++c) {
-                    const float N = fmaf(ao2, fld(tbase, i, 3 + c), at2 * fld(tbase, i, 6 + c));
-                    const ff lN = lg2_split(N);
-                    const ff lNE = (lN.hi > -INFINITY && lN.hi < INFINITY) ? ff_add(P[c], lN) : lN;
-                    ff lS = lNE;
-                    if (HAS_H) {
-                        const ff lG = lg2_split(fld(tbase, i, 9 + c));
-                        const ff lH = (lG.hi > -INFINITY && lG.hi < INFINITY) ? ff_add(lEh, lG) : lG;
-                        lS = log2_sum(lNE, lH);
-                    }
-                    term = ff_add(term, inv_plus_log(lS, nu, far));
-                }
-                acc_ff = ff_add(acc_ff, ff_mul(term, ff{nu, 0.f}));
+                __syncwarp();
+                for (int i = lane; i < nbc; i += 32)
+                    robust_bin<C, HAS_H, BROKEN>(tb, i, xs, es, iv, ao2, at2, n1, n2, lA, acc_ff, far);
             }
-            acc = ((double)acc_ff.hi + (double)acc_ff.lo) + far;
+            // warp sum: float-float tree; the FP64 spill-over only when some lane has one
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1)
+                acc_ff = ff_add(acc_ff, ff{__shfl_down_sync(0xffffffffu, acc_ff.hi, o),
+                                           __shfl_down_sync(0xffffffffu, acc_ff.lo, o)});
+            if (__any_sync(0xffffffffu, far != 0.0))
+                for (int o = 16; o > 0; o >>= 1) far += __shfl_down_sync(0xffffffffu, far, o);
+            const double acc = ((double)acc_ff.hi + (double)acc_ff.lo) + far;
+            if (lane == 0 && !(acc == 0.0)) partial[D.pbase + (int64_t)(s - D.s0) * D.ntiles + t] += acc;
         }
-        for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
-        if (lane == 0) partial[D.pbase + (int64_t)(s - D.s0) * D.ntiles + t] = acc;
     }
 }
 
@@ -742,64 +870,79 @@ int grid_for(K kernel, const lisa_data* d, size_t smem, int threads) {
     return (int)(g < 1 ? 1 : g);
 }
 
+// Marks a point of the stream for lisa_data_kernel_ms (only when profiling an uncaptured call).
+inline void prof_mark(const lisa_data* d, bool on, int k, cudaStream_t sm) {
+    if (on) cudaEventRecord(d->prof_ev[k], sm);
+}
+
 template <int C, bool H, bool B, int G>
-cudaError_t launch_fp32_g(const lisa_data* d, const double* theta, const int32_t* sstat, const int32_t* nint,
+cudaError_t launch_fp32_g(const lisa_data* d, const StateParams* prm, const int32_t* sstat, const int32_t* nint,
                           const int32_t* route, const float* srec, int kmax, double* partial, int* err,
-                          cudaStream_t sm) {
+                          cudaStream_t sm, bool prof) {
     auto kern = loglike_fp32_kernel<C, H, B, G>;
     const size_t smem = 2 * (size_t)d->tiling.tile_bins * kRec * sizeof(float);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const int grid = grid_for(kern, d, smem, kThreads32);
-    kern<<<grid, kThreads32, smem, sm>>>(d->d_items, (int)d->n_items, d->d_rec32, theta, sstat, nint, srec, kmax,
+    kern<<<grid, kThreads32, smem, sm>>>(d->d_items, (int)d->n_items, d->d_rec32, prm, sstat, nint, srec, kmax,
                                        d->nsp, d->d_ds, partial, err, d->tiling.tile_bins);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
+    prof_mark(d, prof, 1, sm);
     // compensated kernel for the routed states (a no-op grid when the route list is empty)
     int max_tiles = 1;
     for (const auto& D : d->h_ds) max_tiles = D.ntiles > max_tiles ? D.ntiles : max_tiles;
-    loglike_robust_kernel<C, H, B><<<d->n_sm * 8, 128, 0, sm>>>(route, d->d_state_ds, d->d_ds, d->tiling.tile_bins,
-                                                                 max_tiles, d->d_rec32, d->d_xlo32, d->d_elllo32,
-                                                                 theta, nint, srec, kmax, d->nsp, partial);
-    return cudaGetLastError();
+    const int max_runs = (max_tiles + kRobTiles - 1) / kRobTiles;
+    auto rk = loglike_robust_kernel<C, H, B>;
+    e = cudaFuncSetAttribute(rk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRobSmem);
+    if (e != cudaSuccess) return e;
+    rk<<<d->n_sm * 8, kRobWarps * 32, kRobSmem, sm>>>(route, d->d_state_ds, d->d_ds, d->tiling.tile_bins, max_runs,
+                                                     d->d_rec32, d->d_xlo32, d->d_elllo32, prm, nint, srec, kmax,
+                                                     d->nsp, partial);
+    e = cudaGetLastError();
+    prof_mark(d, prof, 2, sm);
+    return e;
 }
 
 template <int C, bool H, bool B>
-cudaError_t launch_fp32(const lisa_data* d, const double* theta, const int32_t* sstat, const int32_t* nint,
+cudaError_t launch_fp32(const lisa_data* d, const StateParams* prm, const int32_t* sstat, const int32_t* nint,
                         const int32_t* route, const float* srec, int kmax, double* partial, int* err,
-                        cudaStream_t sm) {
+                        cudaStream_t sm, bool prof) {
     switch (d->tiling.group) {
-        case 2: return launch_fp32_g<C, H, B, 2>(d, theta, sstat, nint, route, srec, kmax, partial, err, sm);
-        case 8: return launch_fp32_g<C, H, B, 8>(d, theta, sstat, nint, route, srec, kmax, partial, err, sm);
-        default: return launch_fp32_g<C, H, B, 4>(d, theta, sstat, nint, route, srec, kmax, partial, err, sm);
+        case 2: return launch_fp32_g<C, H, B, 2>(d, prm, sstat, nint, route, srec, kmax, partial, err, sm, prof);
+        case 8: return launch_fp32_g<C, H, B, 8>(d, prm, sstat, nint, route, srec, kmax, partial, err, sm, prof);
+        default: return launch_fp32_g<C, H, B, 4>(d, prm, sstat, nint, route, srec, kmax, partial, err, sm, prof);
     }
 }
 
 template <int C, bool H, bool B>
 cudaError_t launch_fp64(const lisa_data* d, const double* theta, const int32_t* sstat, const int32_t* nint,
-                        const double* srec, int kmax, double* partial, cudaStream_t sm) {
+                        const double* srec, int kmax, double* partial, cudaStream_t sm, bool prof) {
     auto kern = loglike_fp64_kernel<C, H, B>;
     const int grid = grid_for(kern, d, 0, kThreads);
     kern<<<grid, kThreads, 0, sm>>>(d->d_items, (int)d->n_items, d->d_rec64, theta, sstat, nint, srec, kmax,
                                     d->nsp, d->d_ds, partial);
-    return cudaGetLastError();
+    const cudaError_t e = cudaGetLastError();
+    prof_mark(d, prof, 1, sm);
+    prof_mark(d, prof, 2, sm);   // no compensated kernel in FP64 mode
+    return e;
 }
 
 template <int C>
-cudaError_t dispatch_model(const lisa_data* d, bool fp32, const double* theta, const int32_t* sstat,
-                           const int32_t* nint, const int32_t* route, const void* srec, int kmax, double* partial,
-                           int* err, cudaStream_t sm) {
+cudaError_t dispatch_model(const lisa_data* d, bool fp32, const double* theta, const StateParams* prm,
+                           const int32_t* sstat, const int32_t* nint, const int32_t* route, const void* srec, int kmax,
+                           double* partial, int* err, cudaStream_t sm, bool prof) {
     const int h = d->sgwb_model;
     if (fp32) {
         const float* r = static_cast<const float*>(srec);
-        if (h == 0) return launch_fp32<C, false, false>(d, theta, sstat, nint, route, r, kmax, partial, err, sm);
-        if (h == 1) return launch_fp32<C, true, false>(d, theta, sstat, nint, route, r, kmax, partial, err, sm);
-        return launch_fp32<C, true, true>(d, theta, sstat, nint, route, r, kmax, partial, err, sm);
+        if (h == 0) return launch_fp32<C, false, false>(d, prm, sstat, nint, route, r, kmax, partial, err, sm, prof);
+        if (h == 1) return launch_fp32<C, true, false>(d, prm, sstat, nint, route, r, kmax, partial, err, sm, prof);
+        return launch_fp32<C, true, true>(d, prm, sstat, nint, route, r, kmax, partial, err, sm, prof);
     }
     const double* r = static_cast<const double*>(srec);
-    if (h == 0) return launch_fp64<C, false, false>(d, theta, sstat, nint, r, kmax, partial, sm);
-    if (h == 1) return launch_fp64<C, true, false>(d, theta, sstat, nint, r, kmax, partial, sm);
-    return launch_fp64<C, true, true>(d, theta, sstat, nint, r, kmax, partial, sm);
+    if (h == 0) return launch_fp64<C, false, false>(d, theta, sstat, nint, r, kmax, partial, sm, prof);
+    if (h == 1) return launch_fp64<C, true, false>(d, theta, sstat, nint, r, kmax, partial, sm, prof);
+    return launch_fp64<C, true, true>(d, theta, sstat, nint, r, kmax, partial, sm, prof);
 }
 
 }  // namespace
@@ -838,15 +981,44 @@ lisa_status lisa_psd_loglike(const lisa_data* d, const lisa_params* params, cons
     const void* srec = base + L.off_rec;
     int* err = static_cast<int*>(ws);
     double* partial = reinterpret_cast<double*>(static_cast<char*>(ws) + 256);
+    StateParams* prm = reinterpret_cast<StateParams*>(static_cast<char*>(ws) + 256 + ws_partials_bytes(d));
     if (cudaMemsetAsync(err, 0, sizeof(int), sm) != cudaSuccess) return LISA_ERR_CUDA;
+    const int S = (int)d->n_states;
+    if (fp32) {
+        state_prep_kernel<<<(S + 127) / 128, 128, 0, sm>>>(S, params->theta_dev, prm);
+        if (cudaGetLastError() != cudaSuccess) return LISA_ERR_CUDA;
+    }
+    bool prof = false;
+    if (d->prof_on) {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        prof = cudaStreamIsCapturing(sm, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusNone;
+    }
+    prof_mark(d, prof, 0, sm);
     cudaError_t e = cudaSuccess;
     if (d->n_items > 0)
-        e = d->C == 3 ? dispatch_model<3>(d, fp32, params->theta_dev, sstat, nint, route, srec, kmax, partial, err, sm)
-                      : dispatch_model<2>(d, fp32, params->theta_dev, sstat, nint, route, srec, kmax, partial, err, sm);
+        e = d->C == 3 ? dispatch_model<3>(d, fp32, params->theta_dev, prm, sstat, nint, route, srec, kmax, partial,
+                                          err, sm, prof)
+                      : dispatch_model<2>(d, fp32, params->theta_dev, prm, sstat, nint, route, srec, kmax, partial,
+                                          err, sm, prof);
+    else {
+        prof_mark(d, prof, 1, sm);
+        prof_mark(d, prof, 2, sm);
+    }
     if (e != cudaSuccess) return LISA_ERR_CUDA;
-    const int S = (int)d->n_states;
     finalize_kernel<<<(S + 7) / 8, 256, 0, sm>>>(S, d->d_state_ds, d->d_ds, sstat, partial, err, fp32 ? 1 : 0, out);
-    return check_cuda(cudaGetLastError());
+    e = cudaGetLastError();
+    prof_mark(d, prof, 3, sm);
+    if (prof) d->prof_valid = true;
+    return check_cuda(e);
+}
+
+lisa_status lisa_data_kernel_ms(const lisa_data* d, float* ms) {
+    if (!d || !ms) return LISA_ERR_NULL;
+    if (!d->prof_on || !d->prof_valid) return LISA_ERR_VALUE;
+    if (cudaEventSynchronize(d->prof_ev[3]) != cudaSuccess) return LISA_ERR_CUDA;
+    for (int k = 0; k < 3; ++k)
+        if (cudaEventElapsedTime(&ms[k], d->prof_ev[k], d->prof_ev[k + 1]) != cudaSuccess) return LISA_ERR_CUDA;
+    return LISA_SUCCESS;
 }
 
 lisa_status lisa_model_psd(const lisa_data* d, const lisa_params* params, const void* buf, size_t buf_bytes,

@@ -1,4 +1,4 @@
-// Spline setup: one warp per state builds all of the state's perturbation splines
+// Spline setup: one CTA per state, one warp per perturbation spline
 // (Sec. III.A knot scheme, Appendix A Akima, natural cubic as the alternative kind) with the
 // warp-level construction of lisa_spline_dev.cuh and writes the interval records.
 #include "lisa_spline_dev.cuh"
@@ -6,7 +6,7 @@
 namespace lisa {
 namespace {
 
-// One warp per state.  The spline is built in FP64 for both output precisions:
+// One CTA per state, one warp per spline.  The spline is built in FP64 for both output precisions:
 //  kF32 = false: FP64 records {xl, xr, a, b, c, d} about the left knot (the plain path);
 //  kF32 = true:  FP32 records about the interval midpoint xo, coefficients scaled to log2 units
 //                and split into hi + lo floats, plus the interval's conditioning bound T; a state
@@ -20,17 +20,18 @@ __global__ void __launch_bounds__(128) spline_setup_kernel(
     using T = double;
     __shared__ T sX[4][64];
     __shared__ T sY[4][64];
+    __shared__ int sSt[4], sRob[4];
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
-    const int s = blockIdx.x * 4 + warp;
-    if (s >= S) return;  // uniform per warp
+    const int s = blockIdx.x;
     const int dsi = state_ds[s];
     const double xlo = ds[dsi].x_lo, xhi = ds[dsi].x_hi;
     const double xbmin = ds[dsi].xb_min, xbmax = ds[dsi].xb_max;
     int st_all = 0;
     bool robust = false;
 
-    for (int a = 0; a < nsp; ++a) {
+    {
+        const int a = warp;   // blockDim.x = 32 * nsp
         const int64_t sp = (int64_t)s * nsp + a;
         spl::WarpSpline W;
         spl::warp_build_spline(W, kx + sp * kmax, kw + sp * (kmax + 2), count[sp], kmax, kind, xlo, xhi, sX[warp],
@@ -94,6 +95,17 @@ __global__ void __launch_bounds__(128) spline_setup_kernel(
     }
     robust = __any_sync(spl::kFull, robust);
     if (lane == 0) {
+        sSt[warp] = st_all;
+        sRob[warp] = robust ? 1 : 0;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        robust = false;
+        st_all = 0;
+        for (int a = 0; a < nsp; ++a) {
+            st_all |= sSt[a];
+            robust |= sRob[a] != 0;
+        }
         int word = st_all;
         if (kF32 && robust && st_all == 0) {
             word |= kRouted;
@@ -126,15 +138,16 @@ extern "C" lisa_status lisa_spline_setup(const lisa_data* d, const lisa_knots* k
     int32_t* status_buf = reinterpret_cast<int32_t*>(base + L.off_status);
     int32_t* nint_buf = reinterpret_cast<int32_t*>(base + L.off_nint);
     int32_t* route = reinterpret_cast<int32_t*>(base + L.off_route);
-    const unsigned blocks = (unsigned)((d->n_states + 3) / 4);
+    const unsigned blocks = (unsigned)d->n_states;
+    const unsigned threads = 32u * (unsigned)d->nsp;
     cudaStream_t sm = (cudaStream_t)stream;
     if (cudaMemsetAsync(route, 0, sizeof(int32_t), sm) != cudaSuccess) return LISA_ERR_CUDA;
     if (prec == LISA_FP64)
-        spline_setup_kernel<false><<<blocks, 128, 0, sm>>>(kn->count_dev, kn->x_dev, kn->w_dev, (int)d->n_states,
+        spline_setup_kernel<false><<<blocks, threads, 0, sm>>>(kn->count_dev, kn->x_dev, kn->w_dev, (int)d->n_states,
                                                            d->nsp, kn->kmax, kn->kind, d->d_state_ds, d->d_ds,
                                                            status_buf, nint_buf, route, base + L.off_rec, status_out);
     else
-        spline_setup_kernel<true><<<blocks, 128, 0, sm>>>(kn->count_dev, kn->x_dev, kn->w_dev, (int)d->n_states,
+        spline_setup_kernel<true><<<blocks, threads, 0, sm>>>(kn->count_dev, kn->x_dev, kn->w_dev, (int)d->n_states,
                                                           d->nsp, kn->kmax, kn->kind, d->d_state_ds, d->d_ds,
                                                           status_buf, nint_buf, route, base + L.off_rec, status_out);
     return check_cuda(cudaGetLastError());

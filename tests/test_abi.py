@@ -1,18 +1,19 @@
 """C ABI checks that need no GPU: the library builds and loads, exports every function that
-include/lisa_psd.h declares, and its host-side argument validation returns the documented status
+the headers under include/ declare, and its host-side argument validation returns the documented status
 codes without touching the device."""
 import ctypes
+import glob
 import os
 import re
 
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-HEADER = os.path.join(ROOT, "include", "lisa_psd.h")
+HEADERS = sorted(glob.glob(os.path.join(ROOT, "include", "*.h")))
 
 
 def declared_functions():
-    txt = open(HEADER).read()
+    txt = "".join(open(h).read() for h in HEADERS)
     return sorted(set(re.findall(r"^(?:lisa_status|size_t|const char\*)\s+(lisa_\w+)\(", txt, re.M)))
 
 
@@ -52,6 +53,16 @@ def test_null_arguments_are_rejected_on_the_host(lib):
     assert lib.lisa_model_psd(None, None, None, 0, 0, None, None) == LISA_ERR_NULL
     assert lib.lisa_spline_buf_bytes(None, 4, 0) == 0
     assert lib.lisa_workspace_bytes(None, 4, 0, 0) == 0
+    assert lib.lisa_pipe_rates(2048, 1, None, None) == LISA_ERR_NULL
+    assert lib.lisa_data_set_profiling(None, 1) == LISA_ERR_NULL
+    assert lib.lisa_data_kernel_ms(None, None) == LISA_ERR_NULL
+
+
+def test_pipe_rates_validates_before_touching_the_device(lib):
+    LISA_ERR_VALUE = 2
+    out = (ctypes.c_double * 5)()
+    assert lib.lisa_pipe_rates(8, 1, out, None) == LISA_ERR_VALUE
+    assert lib.lisa_pipe_rates(2048, 0, out, None) == LISA_ERR_VALUE
 
 
 def test_bad_descriptions_are_rejected_before_any_device_work(lib):

@@ -207,3 +207,40 @@ def test_ill_conditioned_splines_take_the_compensated_route(kind):
     assert np.all(St == 0)                            # large overshoots, still FP64-finite
     L32 = _check(wl, P, L, St, FP32)
     assert np.all(np.isfinite(L32))
+
+
+def test_extreme_noise_amplitudes_take_the_guarded_path():
+    """Noise amplitudes decades away from the injection push the product of the three channel
+    PSDs outside the range of the one-reciprocal pair form (|log2 prod| > 99); the fused kernel
+    must detect that per chunk and redo the chunk on the guarded per-channel path."""
+    wl = synth.workload("tiny", n_bins=3000, n_states=32, kmin=0, kmax_draw=4)
+    th = wl.theta.copy()
+    amps = [1e-5, 1e-3, 3e3, 1e5, 1e6]
+    for s in range(32):
+        th[s, 0] = amps[s % 5] * (1.0 + 0.1 * s)
+        th[s, 1] = amps[(s // 5) % 5]
+    wl = dataclasses.replace(wl, theta=th)
+    P, L, St = oracle_batched(wl)
+    assert np.all(St == 0)
+    L32 = _check(wl, P, L, St, FP32)
+    assert np.all(np.isfinite(L32))
+    _check(wl, P, L, St, FP64)
+
+
+@pytest.mark.parametrize("precision", [FP64, FP32])
+def test_common_rescaling_of_data_and_model(precision):
+    """Periodogram x sigma with noise amplitudes x sqrt(sigma) (noise-only model): the library
+    normalises its tables by the data, so the normalised sums are unchanged and log L shifts by
+    -C sum(nu) ln sigma, as the oracle says."""
+    import math
+    wl = synth.workload("tiny", n_bins=1200, n_states=16, sgwb_model=0)
+    P, L, St = oracle_batched(wl)
+    sigma = 1.0e6
+    th2 = wl.theta.copy()
+    th2[:, :2] *= math.sqrt(sigma)
+    wl2 = dataclasses.replace(wl, theta=th2)
+    ds2 = oracle_dataset(wl)
+    ds2["P"] = P * sigma
+    L2_ref, St2 = oracle.loglike(ds2, th2, wl.knots.as_dict())
+    np.testing.assert_array_equal(St2, St)
+    _check(wl2, P * sigma, L2_ref, St2, precision)

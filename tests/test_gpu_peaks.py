@@ -1,0 +1,43 @@
+"""Measurement helpers of the library: pipe-rate microbenchmark and per-kernel timing."""
+import numpy as np
+import pytest
+
+from paper_2507_06300_gb300 import synth
+from tests._workloads import oracle_batched
+
+pytestmark = pytest.mark.gpu
+
+
+def test_pipe_rates_are_positive_and_plausible():
+    from paper_2507_06300_gb300 import binding as B
+    r = B.pipe_rates(iters=256, reps=1)
+    assert set(r) == set(B.PIPE_OPS)
+    for k, v in r.items():
+        # lane operations per second on a whole GPU: well above 1e11 and below 1e15
+        assert 1e11 < v < 1e15, (k, v)
+    assert r["ffma2"] >= 0.5 * r["ffma"]
+
+
+def test_kernel_times_of_a_recorded_call():
+    import torch
+    from paper_2507_06300_gb300 import binding as B
+    wl = synth.workload("tiny", n_bins=3000, n_states=24)
+    P, _, _ = oracle_batched(wl)
+    ds = B.Dataset.from_workload(wl, P)
+    count, x, w, kmax, kind = B.knots_to_device(wl.knots)
+    theta = torch.as_tensor(wl.theta, device="cuda")
+    with pytest.raises(B.LisaError):
+        ds.kernel_ms()                                  # profiling is off
+    for prec in (B.FP32, B.FP64):
+        buf, _ = ds.spline_setup(count, x, w, kmax, kind, prec)
+        ref = ds.psd_loglike(theta, buf, kmax, prec).clone()
+        ds.set_profiling(True)
+        out = ds.psd_loglike(theta, buf, kmax, prec)
+        ms = ds.kernel_ms()
+        ds.set_profiling(False)
+        assert len(ms) == 3 and ms[0] > 0 and ms[2] > 0 and ms[1] >= 0
+        if prec == B.FP64:
+            assert ms[1] < 0.05                         # no compensated kernel in FP64 mode
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(out.cpu().numpy(), ref.cpu().numpy())
+    ds.close()

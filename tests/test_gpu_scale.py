@@ -1,0 +1,75 @@
+"""Parity at the full sizes of the batched-dataset and full-form workloads, in the launch
+configuration the benchmark uses (default tiling after the data object is built): the oracle
+checks sampled states one by one; every state's FP32 result must agree with the GPU FP64 path
+within the FP32 tolerance."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2507_06300_gb300 import synth
+from tests._workloads import fp32_tolerance, gpu_eval, oracle_dataset
+
+pytestmark = pytest.mark.gpu
+
+FP32, FP64 = 0, 1
+
+
+def _sampled_oracle(wl, picks_by_dataset, P):
+    """Oracle log L and status for the picked (dataset, local state) pairs."""
+    L, St = [], []
+    for d, locs in picks_by_dataset:
+        ds = wl.dataset(d)
+        b0, b1 = int(wl.bin_offset[d]), int(wl.bin_offset[d + 1])
+        ds["P"] = P[:, b0:b1]
+        th, kn = wl.states(d)
+        sel = np.asarray(locs)
+        l, st = oracle.loglike(ds, th[sel], {k: (v[sel] if isinstance(v, np.ndarray) else v)
+                                             for k, v in kn.as_dict().items()})
+        L.append(l)
+        St.append(st)
+    return np.concatenate(L), np.concatenate(St)
+
+
+def _check_scale(wl, P, picks_by_dataset):
+    gidx = np.concatenate([wl.state_offset[d] + np.asarray(l) for d, l in picks_by_dataset])
+    L_ref, St_ref = _sampled_oracle(wl, picks_by_dataset, P)
+    L64, St = gpu_eval(wl, P, FP64)
+    L32, St32 = gpu_eval(wl, P, FP32)
+    np.testing.assert_array_equal(St, St32)
+    np.testing.assert_array_equal(St[gidx], St_ref)
+    ok = St_ref == 0
+    np.testing.assert_allclose(L64[gidx][ok], L_ref[ok], rtol=1e-12)
+    tol_ref = np.empty(len(gidx))
+    for k, g in enumerate(gidx):
+        d = int(np.searchsorted(wl.state_offset, g, side="right") - 1)
+        b0, b1 = int(wl.bin_offset[d]), int(wl.bin_offset[d + 1])
+        K = -np.sum(wl.nu[b0:b1] * np.log(P[:, b0:b1]).sum(axis=0))
+        tol_ref[k] = 1e-6 * max(abs(L_ref[k] - K), wl.n_channels * wl.nu[b0:b1].sum())
+    assert np.all(np.abs(L32[gidx][ok] - L_ref[ok]) <= tol_ref[ok])
+    good = St == 0
+    tol_all = fp32_tolerance(L64, wl, P)
+    assert np.all(np.isfinite(L32[good]))
+    assert np.all(np.abs(L32[good] - L64[good]) <= tol_all[good])
+
+
+def test_full_form_workload_sampled_states():
+    """A,E,T x 524,288 bins, 8,192 states, broken power law (knee 3 mHz), 0-40 knots."""
+    wl = synth.workload("full")
+    P = oracle_dataset(wl)["P"]
+    rng = np.random.default_rng(1)
+    picks = np.sort(rng.choice(wl.n_states, 4, replace=False))
+    picks[0] = 0
+    _check_scale(wl, P, [(0, picks)])
+
+
+def test_batched_workload_sampled_states():
+    """1,024 datasets of 8k-262k bins, 16 states each (uneven knot counts 0-30)."""
+    wl = synth.workload("batched")
+    P = np.empty((wl.n_channels, wl.n_bins))
+    for d in range(wl.n_datasets):
+        b0, b1 = int(wl.bin_offset[d]), int(wl.bin_offset[d + 1])
+        P[:, b0:b1] = oracle_dataset(wl, d)["P"]
+    rng = np.random.default_rng(2)
+    ds_pick = np.sort(rng.choice(wl.n_datasets, 4, replace=False))
+    picks = [(int(d), np.sort(rng.choice(16, 2, replace=False))) for d in ds_pick]
+    _check_scale(wl, P, picks)

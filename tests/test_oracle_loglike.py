@@ -86,6 +86,23 @@ def test_whittle_scale_maximiser(nu):
     assert abs(g[1, 0]) < 1e-6 * abs(g[0, 0])
 
 
+@pytest.mark.parametrize("sigma", [1e-3, 7.5, 1e4])
+def test_common_rescaling_shifts_by_log_sigma(sigma):
+    """Sec. III.D: with P and S both multiplied by sigma (noise-only model: amplitudes by
+    sqrt(sigma)), every ratio P/S is unchanged and log L shifts by exactly -C sum(nu) ln sigma."""
+    wl = synth.workload("tiny", sgwb_model=0)
+    ds = oracle_dataset(wl)
+    th, kn = wl.states(0)
+    L, st = oracle.loglike(ds, th, kn.as_dict())
+    th2 = th.copy()
+    th2[:, :2] *= math.sqrt(sigma)
+    L2, st2 = oracle.loglike(dict(ds, P=ds["P"] * sigma), th2, kn.as_dict())
+    np.testing.assert_array_equal(st, st2)
+    ok = st == 0
+    shift = -3 * ds["nu"].sum() * math.log(sigma)
+    np.testing.assert_allclose(L2[ok] - L[ok], shift, rtol=1e-9, atol=1e-9 * np.abs(L[ok]).max())
+
+
 def test_brute_force_mpmath_few_bins(tiny):
     mp = pytest.importorskip("mpmath")
     mp.mp.dps = 50
