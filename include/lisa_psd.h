@@ -174,11 +174,15 @@ lisa_status lisa_data_set_tiling(lisa_data* data, const lisa_tiling* tiling);
 /* Bytes of the caller-allocated spline buffer for this dataset's states and kmax. */
 size_t lisa_spline_buf_bytes(const lisa_data* data, int32_t kmax, lisa_precision precision);
 
-/* One warp per state: sorts each spline's in-between knots, appends the edges, computes the
- * Akima slopes (or the natural-cubic second derivatives by a warp-parallel tridiagonal
- * solve) and the per-interval cubic coefficients, and writes them to spline_buf_dev
- * (16-byte aligned, lisa_spline_buf_bytes long).  state_status_dev [n_states] (may be NULL)
- * receives the LISA_STATE_* bits of each state; the buffer keeps its own copy. */
+/* Sec. III.A knot scheme and Appendix A (one warp per spline): sorts each spline's in-between
+ * knots, appends the edges, computes the Akima slopes (or the natural-cubic second derivatives
+ * by a warp-parallel tridiagonal solve) and the per-interval cubic coefficients, and writes
+ * them to spline_buf_dev (256-byte aligned, at least lisa_spline_buf_bytes long; the layout is
+ * private to the library and depends on the precision).  In FP32 mode it also decides which
+ * states need the compensated evaluation (ill-conditioned intervals) and records them in the
+ * buffer.  state_status_dev [n_states] (may be NULL) receives the LISA_STATE_* bits of each
+ * state; the buffer keeps its own copy.  Errors: LISA_ERR_NULL, LISA_ERR_VALUE (kmax or kind),
+ * LISA_ERR_SHAPE (n_states / n_splines differ from the data object), LISA_ERR_WORKSPACE. */
 lisa_status lisa_spline_setup(const lisa_data* data, const lisa_knots* knots,
                               lisa_precision precision, void* spline_buf_dev, size_t spline_buf_bytes,
                               int32_t* state_status_dev, lisa_stream_t stream);

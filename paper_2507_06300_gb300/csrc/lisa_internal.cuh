@@ -118,11 +118,14 @@ namespace lisa {
 
 // Spline buffer layout (64-byte records in both precisions):
 //   int32 status[S] | int32 nint[S*nsp] | int32 route_count, route_list[S] | rec[S][nsp][kmax+1]
+//   | float2 hull[S]
 // each region starting on a 256-byte boundary.  route_list holds, in no particular order, the
-// states the FP32 path sends to the compensated kernel (unused in FP64 mode).
+// states the FP32 path sends to the compensated kernel; hull[s] = (lowest left end, highest right
+// end) in x of state s's ill-conditioned intervals, (+inf, -inf) when it has none (both unused
+// in FP64 mode).
 inline size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 struct SplineLayout {
-    size_t off_status, off_nint, off_route, off_rec, bytes;
+    size_t off_status, off_nint, off_route, off_rec, off_hull, bytes;
 };
 constexpr size_t kRecBytes = 64;
 inline SplineLayout spline_layout(int64_t S, int nsp, int kmax) {
@@ -131,7 +134,8 @@ inline SplineLayout spline_layout(int64_t S, int nsp, int kmax) {
     L.off_nint = align256(sizeof(int32_t) * (size_t)S);
     L.off_route = L.off_nint + align256(sizeof(int32_t) * (size_t)S * nsp);
     L.off_rec = L.off_route + align256(sizeof(int32_t) * ((size_t)S + 1));
-    L.bytes = L.off_rec + (size_t)S * nsp * (kmax + 1) * kRecBytes;
+    L.off_hull = L.off_rec + align256((size_t)S * nsp * (kmax + 1) * kRecBytes);
+    L.bytes = L.off_hull + sizeof(float) * 2 * (size_t)S;
     return L;
 }
 

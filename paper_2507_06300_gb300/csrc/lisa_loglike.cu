@@ -233,10 +233,11 @@ __device__ __forceinline__ float fmin3(float a, float b, float c) {
 // running maximum (mx) and minimum (mi) of log2 prod and recomputes the chunk on the guarded
 // scalar path when either left +-kPairLg2Max or the chunk sum is not finite.
 template <int C, bool HAS_H, bool BROKEN>
-__device__ __forceinline__ float2 pair_term32(const float4* __restrict__ blk, const Iv2* iv, float2 ao2, float2 at2,
-                                              float n1, float n2, float2 Af, float& mx, float& mi) {
+__device__ __forceinline__ float2 pair_term32(const float4 q0, const float4* __restrict__ blk, const Iv2* iv,
+                                              float2 ao2, float2 at2, float n1, float n2, float2 Af, float& mx,
+                                              float& mi) {
     constexpr int NSP = C + (HAS_H ? 1 : 0);
-    const float4 q0 = blk[0], q1 = blk[1], q2 = blk[2], q3 = blk[3], q4 = blk[4], q5 = blk[5];
+    const float4 q1 = blk[1], q2 = blk[2], q3 = blk[3], q4 = blk[4], q5 = blk[5];
     const float2 x = make_float2(q0.x, q0.y), ell = make_float2(q0.z, q0.w), nu = make_float2(q1.x, q1.y);
     const float2 go[3] = {make_float2(q1.z, q1.w), make_float2(q2.x, q2.y), make_float2(q2.z, q2.w)};
     const float2 gt[3] = {make_float2(q3.x, q3.y), make_float2(q3.z, q3.w), make_float2(q4.x, q4.y)};
@@ -416,14 +417,18 @@ __global__ void __launch_bounds__(kThreads32, G == 8 ? 5 : 6)
                     float mx = 0.f, mi = 0.f;
                     for (; ip + G / 2 <= pcend; ip += G / 2) {
                         const float4* blk = tb4 + ip * (kPairRec / 4);
-                        // x of the group's last bin (odd bin of its last pair block)
-                        const float xg = reinterpret_cast<const float*>(blk + (G / 2 - 1) * (kPairRec / 4))[1];
-                        if (xg < xmin) {
+                        // first float4 of the group's last pair block: (x, x, ell, ell); its .y is
+                        // the x of the group's last bin
+                        const float4 qg = blk[(G / 2 - 1) * (kPairRec / 4)];
+                        if (qg.y < xmin) {
 #pragma unroll
-                            for (int g = 0; g < G / 2; ++g)
-                                acc2 = __ffma2_rn(keep2, pair_term32<C, HAS_H, BROKEN>(blk + g * (kPairRec / 4), iv2,
-                                                                                       ao2_2, at2_2, n1, n2, Af2, mx, mi),
+                            for (int g = 0; g < G / 2; ++g) {
+                                const float4* pb = blk + g * (kPairRec / 4);
+                                const float4 q0 = g == G / 2 - 1 ? qg : pb[0];
+                                acc2 = __ffma2_rn(keep2, pair_term32<C, HAS_H, BROKEN>(q0, pb, iv2, ao2_2, at2_2, n1,
+                                                                                       n2, Af2, mx, mi),
                                                   acc2);
+                            }
                         } else {
 #pragma unroll 1
                             for (int i = 2 * ip; i < 2 * ip + G; ++i) acc2.x += scalar_bin(i);
@@ -471,11 +476,16 @@ struct IvR {
     int j, last;
 };
 __device__ __forceinline__ void load_ivr(IvR& v) {
-    const float* r = v.base + (size_t)v.j * kSplineRec32;
-    v.xr = __ldg(r + 0);
-    v.T = __ldg(r + 7);
-    v.xo = {__ldg(r + 1), __ldg(r + 8)};
-    for (int c = 0; c < 4; ++c) v.c[c] = {__ldg(r + 2 + c), __ldg(r + 9 + c)};
+    const float4* r = reinterpret_cast<const float4*>(v.base + (size_t)v.j * kSplineRec32);
+    const float4 A = __ldg(r), B = __ldg(r + 1), Cq = __ldg(r + 2), Dq = __ldg(r + 3);
+    // A = (xr, xo, c0, c1), B = (c2, c3, xl, T), Cq = (xo_lo, c0_lo, c1_lo, c2_lo), Dq.x = c3_lo
+    v.xr = A.x;
+    v.T = B.w;
+    v.xo = {A.y, Cq.x};
+    v.c[0] = {A.z, Cq.y};
+    v.c[1] = {A.w, Cq.z};
+    v.c[2] = {B.x, Cq.w};
+    v.c[3] = {B.y, Dq.x};
 }
 
 // log2 of a positive float as an exact float-float pair (exponent, log2 of the mantissa):
@@ -612,7 +622,7 @@ __device__ __forceinline__ void robust_bin(const float* __restrict__ tb, int i, 
 }
 
 // One warp per (routed state, run of kRobTiles consecutive tiles), kRobWarps warps per CTA.  A
-// run that no ill-conditioned interval of the state overlaps is skipped.  Otherwise the warp
+// run outside the x-hull of the state's ill-conditioned intervals (from the setup) is skipped.  Otherwise the warp
 // stages each tile chunk by chunk into its shared-memory slice; lane l then takes bins l, l + 32,
 // ... of the chunk (the lanes of a warp mostly share their spline intervals), so a lane's bins
 // come in increasing order and its intervals carry over from tile to tile.  Each tile's sum of
@@ -623,8 +633,8 @@ __global__ void __launch_bounds__(kRobWarps * 32)
                           const DatasetDev* __restrict__ ds, int tile_bins, int max_runs,
                           const float* __restrict__ rec32, const float* __restrict__ xlo32,
                           const float* __restrict__ elllo32, const StateParams* __restrict__ prm,
-                          const int32_t* __restrict__ nint, const float* __restrict__ srec, int kmax, int nsp,
-                          double* __restrict__ partial) {
+                          const int32_t* __restrict__ nint, const float* __restrict__ srec,
+                          const float2* __restrict__ hull, int kmax, int nsp, double* __restrict__ partial) {
     constexpr int NSP = C + (HAS_H ? 1 : 0);
     extern __shared__ float4 rsm[];
     const int lane = threadIdx.x & 31;
@@ -649,23 +659,13 @@ __global__ void __launch_bounds__(kRobWarps * 32)
         const ff n2 = BROKEN ? ff{q1.x, q2.x} : n1;
         const ff lA = {q1.y, q1.z};
         {
-            // does any ill-conditioned interval overlap the run's bins?  (lanes over intervals)
+            // skip a run that the state's ill-conditioned intervals do not reach
             const int64_t bA = D.bin0 + (int64_t)t0 * tile_bins;
             const int64_t bB = min(D.bin0 + (int64_t)t1 * tile_bins, D.bin0 + D.npad) - 1;
             const float xA = fld(rec32 + (bA >> 1) * kPairRec, (int)(bA & 1), 0);
             const float xB = fld(rec32 + (bB >> 1) * kPairRec, (int)(bB & 1), 0);
-            bool hit = false;
-            for (int a = 0; a < NSP; ++a) {
-                const int64_t sp = (int64_t)s * nsp + a;
-                const float* base = srec + sp * (int64_t)(kmax + 1) * kSplineRec32;
-                const int n = nint[sp];
-                for (int j = lane; j < n; j += 32) {
-                    const float* rr = base + (size_t)j * kSplineRec32;
-                    const float xl = j == 0 ? -INFINITY : __ldg(rr + 6);
-                    hit |= !(__ldg(rr + 7) <= (float)kRobustT) && xl <= xB && __ldg(rr) > xA;
-                }
-            }
-            if (!__any_sync(0xffffffffu, hit)) continue;
+            const float2 h = __ldg(hull + s);
+            if (!(h.x <= xB && h.y > xA)) continue;          // uniform per warp
         }
         IvR iv[NSP];
         {
@@ -877,8 +877,8 @@ inline void prof_mark(const lisa_data* d, bool on, int k, cudaStream_t sm) {
 
 template <int C, bool H, bool B, int G>
 cudaError_t launch_fp32_g(const lisa_data* d, const StateParams* prm, const int32_t* sstat, const int32_t* nint,
-                          const int32_t* route, const float* srec, int kmax, double* partial, int* err,
-                          cudaStream_t sm, bool prof) {
+                          const int32_t* route, const float* srec, const float2* hull, int kmax, double* partial,
+                          int* err, cudaStream_t sm, bool prof) {
     auto kern = loglike_fp32_kernel<C, H, B, G>;
     const size_t smem = 2 * (size_t)d->tiling.tile_bins * kRec * sizeof(float);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -897,8 +897,8 @@ cudaError_t launch_fp32_g(const lisa_data* d, const StateParams* prm, const int3
     e = cudaFuncSetAttribute(rk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRobSmem);
     if (e != cudaSuccess) return e;
     rk<<<d->n_sm * 8, kRobWarps * 32, kRobSmem, sm>>>(route, d->d_state_ds, d->d_ds, d->tiling.tile_bins, max_runs,
-                                                     d->d_rec32, d->d_xlo32, d->d_elllo32, prm, nint, srec, kmax,
-                                                     d->nsp, partial);
+                                                     d->d_rec32, d->d_xlo32, d->d_elllo32, prm, nint, srec, hull,
+                                                     kmax, d->nsp, partial);
     e = cudaGetLastError();
     prof_mark(d, prof, 2, sm);
     return e;
@@ -906,12 +906,13 @@ cudaError_t launch_fp32_g(const lisa_data* d, const StateParams* prm, const int3
 
 template <int C, bool H, bool B>
 cudaError_t launch_fp32(const lisa_data* d, const StateParams* prm, const int32_t* sstat, const int32_t* nint,
-                        const int32_t* route, const float* srec, int kmax, double* partial, int* err,
-                        cudaStream_t sm, bool prof) {
+                        const int32_t* route, const float* srec, const float2* hull, int kmax, double* partial,
+                        int* err, cudaStream_t sm, bool prof) {
     switch (d->tiling.group) {
-        case 2: return launch_fp32_g<C, H, B, 2>(d, prm, sstat, nint, route, srec, kmax, partial, err, sm, prof);
-        case 8: return launch_fp32_g<C, H, B, 8>(d, prm, sstat, nint, route, srec, kmax, partial, err, sm, prof);
-        default: return launch_fp32_g<C, H, B, 4>(d, prm, sstat, nint, route, srec, kmax, partial, err, sm, prof);
+        case 2: return launch_fp32_g<C, H, B, 2>(d, prm, sstat, nint, route, srec, hull, kmax, partial, err, sm, prof);
+        case 8: return launch_fp32_g<C, H, B, 8>(d, prm, sstat, nint, route, srec, hull, kmax, partial, err, sm, prof);
+        default:
+            return launch_fp32_g<C, H, B, 4>(d, prm, sstat, nint, route, srec, hull, kmax, partial, err, sm, prof);
     }
 }
 
@@ -930,14 +931,16 @@ cudaError_t launch_fp64(const lisa_data* d, const double* theta, const int32_t* 
 
 template <int C>
 cudaError_t dispatch_model(const lisa_data* d, bool fp32, const double* theta, const StateParams* prm,
-                           const int32_t* sstat, const int32_t* nint, const int32_t* route, const void* srec, int kmax,
-                           double* partial, int* err, cudaStream_t sm, bool prof) {
+                           const int32_t* sstat, const int32_t* nint, const int32_t* route, const void* srec,
+                           const float2* hull, int kmax, double* partial, int* err, cudaStream_t sm, bool prof) {
     const int h = d->sgwb_model;
     if (fp32) {
         const float* r = static_cast<const float*>(srec);
-        if (h == 0) return launch_fp32<C, false, false>(d, prm, sstat, nint, route, r, kmax, partial, err, sm, prof);
-        if (h == 1) return launch_fp32<C, true, false>(d, prm, sstat, nint, route, r, kmax, partial, err, sm, prof);
-        return launch_fp32<C, true, true>(d, prm, sstat, nint, route, r, kmax, partial, err, sm, prof);
+        if (h == 0)
+            return launch_fp32<C, false, false>(d, prm, sstat, nint, route, r, hull, kmax, partial, err, sm, prof);
+        if (h == 1)
+            return launch_fp32<C, true, false>(d, prm, sstat, nint, route, r, hull, kmax, partial, err, sm, prof);
+        return launch_fp32<C, true, true>(d, prm, sstat, nint, route, r, hull, kmax, partial, err, sm, prof);
     }
     const double* r = static_cast<const double*>(srec);
     if (h == 0) return launch_fp64<C, false, false>(d, theta, sstat, nint, r, kmax, partial, sm, prof);
@@ -979,6 +982,7 @@ lisa_status lisa_psd_loglike(const lisa_data* d, const lisa_params* params, cons
     const int32_t* nint = reinterpret_cast<const int32_t*>(base + L.off_nint);
     const int32_t* route = reinterpret_cast<const int32_t*>(base + L.off_route);
     const void* srec = base + L.off_rec;
+    const float2* hull = reinterpret_cast<const float2*>(base + L.off_hull);
     int* err = static_cast<int*>(ws);
     double* partial = reinterpret_cast<double*>(static_cast<char*>(ws) + 256);
     StateParams* prm = reinterpret_cast<StateParams*>(static_cast<char*>(ws) + 256 + ws_partials_bytes(d));
@@ -996,10 +1000,10 @@ lisa_status lisa_psd_loglike(const lisa_data* d, const lisa_params* params, cons
     prof_mark(d, prof, 0, sm);
     cudaError_t e = cudaSuccess;
     if (d->n_items > 0)
-        e = d->C == 3 ? dispatch_model<3>(d, fp32, params->theta_dev, prm, sstat, nint, route, srec, kmax, partial,
-                                          err, sm, prof)
-                      : dispatch_model<2>(d, fp32, params->theta_dev, prm, sstat, nint, route, srec, kmax, partial,
-                                          err, sm, prof);
+        e = d->C == 3 ? dispatch_model<3>(d, fp32, params->theta_dev, prm, sstat, nint, route, srec, hull, kmax,
+                                          partial, err, sm, prof)
+                      : dispatch_model<2>(d, fp32, params->theta_dev, prm, sstat, nint, route, srec, hull, kmax,
+                                          partial, err, sm, prof);
     else {
         prof_mark(d, prof, 1, sm);
         prof_mark(d, prof, 2, sm);

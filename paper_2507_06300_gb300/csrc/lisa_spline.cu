@@ -16,11 +16,13 @@ __global__ void __launch_bounds__(128) spline_setup_kernel(
     const int32_t* __restrict__ count, const double* __restrict__ kx, const double* __restrict__ kw,
     int S, int nsp, int kmax, int kind, const int32_t* __restrict__ state_ds,
     const DatasetDev* __restrict__ ds, int32_t* __restrict__ status_buf, int32_t* __restrict__ nint_buf,
-    int32_t* __restrict__ route, void* __restrict__ rec_v, int32_t* __restrict__ status_out) {
+    int32_t* __restrict__ route, void* __restrict__ rec_v, float2* __restrict__ hull,
+    int32_t* __restrict__ status_out) {
     using T = double;
     __shared__ T sX[4][64];
     __shared__ T sY[4][64];
     __shared__ int sSt[4], sRob[4];
+    __shared__ float sHlo[4], sHhi[4];
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
     const int s = blockIdx.x;
@@ -29,6 +31,7 @@ __global__ void __launch_bounds__(128) spline_setup_kernel(
     const double xbmin = ds[dsi].xb_min, xbmax = ds[dsi].xb_max;
     int st_all = 0;
     bool robust = false;
+    float hlo = INFINITY, hhi = -INFINITY;   // x-extent of this spline's ill-conditioned intervals
 
     {
         const int a = warp;   // blockDim.x = 32 * nsp
@@ -72,7 +75,11 @@ __global__ void __launch_bounds__(128) spline_setup_kernel(
                     const float rr = (float)fmax(fabs(lo_x - xo), fabs(hi_x - xo));
                     const float Tc = fabsf((float)cs[0]) +
                                      rr * (fabsf((float)cs[1]) + rr * (fabsf((float)cs[2]) + rr * fabsf((float)cs[3])));
-                    robust |= !(Tc <= (float)kRobustT);
+                    if (!(Tc <= (float)kRobustT)) {
+                        robust = true;
+                        hlo = fminf(hlo, j == 0 ? -INFINITY : (float)x[q]);
+                        hhi = fmaxf(hhi, last ? INFINITY : (float)xn[q]);
+                    }
                     float* r = static_cast<float*>(rec_v) + (sp * (int64_t)(kmax + 1) + j) * kSplineRec32;
                     const float xo_hi = (float)xo;
                     r[0] = last ? INFINITY : (float)xn[q];
@@ -94,18 +101,29 @@ __global__ void __launch_bounds__(128) spline_setup_kernel(
         st_all |= st;
     }
     robust = __any_sync(spl::kFull, robust);
+    for (int o = 16; o > 0; o >>= 1) {
+        hlo = fminf(hlo, __shfl_xor_sync(spl::kFull, hlo, o));
+        hhi = fmaxf(hhi, __shfl_xor_sync(spl::kFull, hhi, o));
+    }
     if (lane == 0) {
         sSt[warp] = st_all;
         sRob[warp] = robust ? 1 : 0;
+        sHlo[warp] = hlo;
+        sHhi[warp] = hhi;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
         robust = false;
         st_all = 0;
+        hlo = INFINITY;
+        hhi = -INFINITY;
         for (int a = 0; a < nsp; ++a) {
             st_all |= sSt[a];
             robust |= sRob[a] != 0;
+            hlo = fminf(hlo, sHlo[a]);
+            hhi = fmaxf(hhi, sHhi[a]);
         }
+        if (kF32) hull[s] = make_float2(hlo, hhi);
         int word = st_all;
         if (kF32 && robust && st_all == 0) {
             word |= kRouted;
@@ -145,10 +163,12 @@ extern "C" lisa_status lisa_spline_setup(const lisa_data* d, const lisa_knots* k
     if (prec == LISA_FP64)
         spline_setup_kernel<false><<<blocks, threads, 0, sm>>>(kn->count_dev, kn->x_dev, kn->w_dev, (int)d->n_states,
                                                            d->nsp, kn->kmax, kn->kind, d->d_state_ds, d->d_ds,
-                                                           status_buf, nint_buf, route, base + L.off_rec, status_out);
+                                                           status_buf, nint_buf, route, base + L.off_rec,
+                                                           reinterpret_cast<float2*>(base + L.off_hull), status_out);
     else
         spline_setup_kernel<true><<<blocks, threads, 0, sm>>>(kn->count_dev, kn->x_dev, kn->w_dev, (int)d->n_states,
                                                           d->nsp, kn->kmax, kn->kind, d->d_state_ds, d->d_ds,
-                                                          status_buf, nint_buf, route, base + L.off_rec, status_out);
+                                                          status_buf, nint_buf, route, base + L.off_rec,
+                                                          reinterpret_cast<float2*>(base + L.off_hull), status_out);
     return check_cuda(cudaGetLastError());
 }

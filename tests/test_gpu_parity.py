@@ -130,7 +130,7 @@ def test_spline_coefficients_fp64_match_oracle(tiny):
         off_route = off_nint + a256(4 * S * nsp)
         off_rec = off_route + a256(4 * (S + 1))
         nint = raw[off_nint:off_nint + 4 * S * nsp].view(np.int32).reshape(S, nsp)
-        rec = raw[off_rec:].view(np.float64).reshape(S, nsp, kmax + 1, 8)
+        rec = raw[off_rec:off_rec + 64 * S * nsp * (kmax + 1)].view(np.float64).reshape(S, nsp, kmax + 1, 8)
         for s in range(S):
             for a in range(nsp):
                 k = wl.knots.count[s, a]
