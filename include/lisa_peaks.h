@@ -46,13 +46,17 @@ lisa_status lisa_pipe_rates(int32_t iters, int32_t reps, double* rates, lisa_str
  *
  * lisa_data_set_profiling(data, 1) creates four CUDA events owned by `data` (destroyed with it);
  * while enabled, every lisa_psd_loglike call on `data` that is not being captured into a CUDA
- * graph records them on its stream around its kernels.  Captured calls record nothing.
+ * graph records them on its stream around its kernels (the state-parameter kernel of an FP32
+ * call runs before the first event).  Captured calls record nothing.
  * enable = 0 stops the recording.  Errors: LISA_ERR_NULL, LISA_ERR_CUDA (event creation).
  *
+ * lisa_psd_loglike_grad calls are recorded the same way.
+ *
  * lisa_data_kernel_ms waits for the most recent recorded call to finish (host synchronisation on
- * its last event) and writes ms[3] (HOST, caller-owned): [0] the main likelihood kernel (fused
- * FP32 or plain FP64), [1] the compensated kernel for routed states (0 in FP64 mode), [2] the
- * finalize kernel, in milliseconds.  Errors: LISA_ERR_NULL; LISA_ERR_VALUE when profiling is off
+ * its last event) and writes ms[3] (HOST, caller-owned), in milliseconds.  After
+ * lisa_psd_loglike: [0] the main likelihood kernel (fused FP32 or plain FP64), [1] the
+ * compensated kernel for routed states (0 in FP64 mode), [2] the finalize kernel.  After
+ * lisa_psd_loglike_grad: [0] the adjoint kernel, [1] 0, [2] the adjoint epilogue.  Errors: LISA_ERR_NULL; LISA_ERR_VALUE when profiling is off
  * or no call has been recorded since it was enabled; LISA_ERR_CUDA. */
 lisa_status lisa_data_set_profiling(lisa_data* data, int32_t enable);
 lisa_status lisa_data_kernel_ms(const lisa_data* data, float* ms);

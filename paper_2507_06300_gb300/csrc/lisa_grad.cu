@@ -621,6 +621,8 @@ cudaError_t launch_adjoint(const lisa_data* d, bool fp32, const lisa_params* par
                            const int32_t* sstat, const int32_t* nint, const void* srec, double* scal, double* mom,
                            double* out, double* grad, cudaStream_t sm) {
     const int grid = d->n_sm * 8;
+    const bool prof = prof_active(d, sm);
+    prof_mark(d, prof, 0, sm);
     if (d->n_adj_units > 0) {
         if (fp32)
             adjoint_fp32_kernel<C, H, B><<<grid, 128, 0, sm>>>(d->d_adj_units, d->n_adj_units, d->d_ds, d->d_rec32,
@@ -635,12 +637,17 @@ cudaError_t launch_adjoint(const lisa_data* d, bool fp32, const lisa_params* par
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
+    prof_mark(d, prof, 1, sm);
+    prof_mark(d, prof, 2, sm);
     const unsigned eb = (unsigned)((d->n_states + 3) / 4);
     adjoint_epilogue_kernel<C, H, B><<<eb, 128, 0, sm>>>(
         (int)d->n_states, d->d_state_ds, d->d_ds, sstat, params->theta_dev, kn->count_dev, kn->x_dev, kn->w_dev,
         kn->kmax, kn->kind, d->nsp, d->d_adj_prefix, scal, mom, d->d_rec32, d->d_rec64, srec, fp32 ? 1 : 0, out,
         grad);
-    return cudaGetLastError();
+    const cudaError_t e = cudaGetLastError();
+    prof_mark(d, prof, 3, sm);
+    if (prof) d->prof_valid = true;
+    return e;
 }
 
 template <int C>

@@ -161,6 +161,17 @@ inline size_t ws_fwd_bytes(const lisa_data* d) {
 size_t grad_extra_bytes(const lisa_data* d, int kmax);
 
 lisa_status rebuild_work(lisa_data* d);
+
+// Per-kernel timing (lisa_data_set_profiling): whether this call records events (profiling on
+// and the stream not capturing), and an event record at point k of the call.
+inline bool prof_active(const lisa_data* d, cudaStream_t sm) {
+    if (!d->prof_on) return false;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    return cudaStreamIsCapturing(sm, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusNone;
+}
+inline void prof_mark(const lisa_data* d, bool on, int k, cudaStream_t sm) {
+    if (on) cudaEventRecord(d->prof_ev[k], sm);
+}
 lisa_status check_cuda(cudaError_t e);
 
 }  // namespace lisa

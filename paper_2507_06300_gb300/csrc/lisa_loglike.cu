@@ -870,11 +870,6 @@ int grid_for(K kernel, const lisa_data* d, size_t smem, int threads) {
     return (int)(g < 1 ? 1 : g);
 }
 
-// Marks a point of the stream for lisa_data_kernel_ms (only when profiling an uncaptured call).
-inline void prof_mark(const lisa_data* d, bool on, int k, cudaStream_t sm) {
-    if (on) cudaEventRecord(d->prof_ev[k], sm);
-}
-
 template <int C, bool H, bool B, int G>
 cudaError_t launch_fp32_g(const lisa_data* d, const StateParams* prm, const int32_t* sstat, const int32_t* nint,
                           const int32_t* route, const float* srec, const float2* hull, int kmax, double* partial,
@@ -992,11 +987,7 @@ lisa_status lisa_psd_loglike(const lisa_data* d, const lisa_params* params, cons
         state_prep_kernel<<<(S + 127) / 128, 128, 0, sm>>>(S, params->theta_dev, prm);
         if (cudaGetLastError() != cudaSuccess) return LISA_ERR_CUDA;
     }
-    bool prof = false;
-    if (d->prof_on) {
-        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
-        prof = cudaStreamIsCapturing(sm, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusNone;
-    }
+    const bool prof = prof_active(d, sm);
     prof_mark(d, prof, 0, sm);
     cudaError_t e = cudaSuccess;
     if (d->n_items > 0)

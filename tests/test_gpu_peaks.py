@@ -41,3 +41,25 @@ def test_kernel_times_of_a_recorded_call():
         torch.cuda.synchronize()
         np.testing.assert_array_equal(out.cpu().numpy(), ref.cpu().numpy())
     ds.close()
+
+
+def test_kernel_times_of_a_recorded_gradient_call():
+    import torch
+    from paper_2507_06300_gb300 import binding as B
+    wl = synth.workload("tiny", n_bins=3000, n_states=24)
+    P, _, _ = oracle_batched(wl)
+    ds = B.Dataset.from_workload(wl, P)
+    count, x, w, kmax, kind = B.knots_to_device(wl.knots)
+    theta = torch.as_tensor(wl.theta, device="cuda")
+    buf, _ = ds.spline_setup(count, x, w, kmax, kind, B.FP32)
+    L0, G0 = ds.psd_loglike_grad(theta, count, x, w, kmax, kind, buf, B.FP32)
+    L0, G0 = L0.clone(), G0.clone()
+    ds.set_profiling(True)
+    L1, G1 = ds.psd_loglike_grad(theta, count, x, w, kmax, kind, buf, B.FP32)
+    ms = ds.kernel_ms()
+    ds.set_profiling(False)
+    assert ms[0] > 0 and ms[2] > 0 and ms[1] < 0.05
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(L1.cpu().numpy(), L0.cpu().numpy())
+    np.testing.assert_array_equal(G1.cpu().numpy(), G0.cpu().numpy())
+    ds.close()
