@@ -33,17 +33,15 @@ UNIT = "state-bins/s"
 WORKLOAD = ("paper-scale: A,E,T; 131,072 uniform bins 0.1-29 mHz; Nseg=64; OMS 15 pm + TM 3 fm/s^2 + "
             "power-law SGWB log10 Omega=-12, n_t=2/3; 64 walkers x 16 temps = 1,024 states; 0-20 knots per spline")
 # Algorithmic operations per state-bin of the fused FP32 kernel as implemented for A,E,T with an
-# SGWB, on its packed path (pair blocks of two bins with equal nu).  MUFU: 4 ex2 (three noise
-# perturbations, one SGWB perturbation with the power law folded in), 1/2 rcp and 1/2 lg2 (one of
-# each per pair block: the reciprocal sum and the log of the product of both bins' channel PSDs).
-# FP32 (FMA pipe, an FMA counted once): 4 splines x 3 FMA (d0 + d1 u + d2 u^2 + d3 u^3) = 12,
-# SGWB amplitude 1, per channel noise (2) and PSD (2) = 12, channel product and reciprocal-sum
-# numerator 4, per pair block: product, numerator (2), reciprocal-sum FMA, mask x nu, two
-# accumulating FMAs = 7, i.e. 3.5 per state-bin -- 32.5 in all.
-MUFU_EX2, MUFU_RCP, MUFU_LG2 = 4, 0.5, 0.5
+# SGWB.  MUFU: 4 ex2 (three noise perturbations, one SGWB perturbation x power law), 1 rcp (fused
+# reciprocal sum), 1 lg2 (fused log of the product).  FP32 (FMA pipe, an FMA counted once):
+# 4 splines x (1 shift + 3 Horner FMA) = 16, SGWB exponent and amplitude 2, per channel noise
+# (2) and PSD (2) = 12, channel product and reciprocal-sum numerator 4, reciprocal-sum FMA,
+# log FMA and nu scale 3, accumulation 1.
+MUFU_EX2, MUFU_RCP, MUFU_LG2 = 4, 1, 1
 MUFU_PER_STATE_BIN = MUFU_EX2 + MUFU_RCP + MUFU_LG2
-FP32_PER_STATE_BIN = 32.5
-TABLE_BYTES_PER_BIN = 14 * 4          # tile table: u, u^2, u^3, nu, 3 x (G_oms, G_tm, G_h), x
+FP32_PER_STATE_BIN = 38
+TABLE_BYTES_PER_BIN = 12 * 4          # FP32 bin table: x, ell, nu, 3 x (G_oms, G_tm, G_h)
 # The FP32 adjoint kernel per state-bin, as implemented: per spline a compensated t (two-sum and
 # low parts, 9) and Horner (3) = 48; SGWB exponent and amplitude 2; per channel noise 2, SGWB 1,
 # PSD 1, g = nu r (r - 1) 3, forward term 2, template sums 5, spline signal 3 = 51; SGWB signal,
@@ -165,7 +163,7 @@ def host_mem_available_gb():
 
 def roofs(rates, hbm_gbs, bytes_per_state_bin):
     """Ceilings in state-bins/s of the fused kernel from the measured pipe rates: the MUFU pipe
-    (the kernel's mix of 4 ex2, 1/2 rcp, 1/2 lg2), the FP32 FMA pipe (32.5 ops, packed FMAs counted as
+    (the kernel's mix of 4 ex2, 1 rcp, 1 lg2), the FP32 FMA pipe (38 ops, packed FMAs counted as
     two lane operations) and HBM (algorithmic bytes per state-bin)."""
     t_ex2, t_rcp = 1.0 / rates["ex2"], 1.0 / rates["rcp"]
     t_lg2 = 2.0 / rates["lg2_ex2"] - t_ex2
@@ -411,7 +409,7 @@ def run_ours(args):
     head, ev32, clocks = forward(I, args.steps, args.warmup, args.fp64_steps, sample_clocks=True)
     roof = roofline_of(I, head)
     roof["peak_source"] = ("measured live by lisa_pipe_rates: FP32 = max(fma.rn.f32, fma.rn.f32x2) lane-op rate, "
-                           "MUFU = the kernel's 4 ex2 + 1/2 rcp + 1/2 lg2 mix; HBM = MEASURED_PEAKS.json "
+                           "MUFU = the kernel's 4 ex2 + 1 rcp + 1 lg2 mix; HBM = MEASURED_PEAKS.json "
                            f"({peak_kind})")
     roof["nominal_fp32_gops"] = N_SM * 128 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e9
     roof["traffic"] = _traffic_from_profile(os.path.join(ROOT, "paper_2507_06300_gb300", "csrc", "lisa_loglike.cu"))

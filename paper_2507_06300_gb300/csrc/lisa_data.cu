@@ -3,8 +3,6 @@
 #include <algorithm>
 #include <cmath>
 #include <new>
-#include <queue>
-#include <utility>
 
 #include "lisa_internal.cuh"
 
@@ -143,16 +141,6 @@ void release(lisa_data* d) {
     cudaFree(d->d_xlo32);
     cudaFree(d->d_elllo32);
     cudaFree(d->d_items);
-    cudaFree(d->d_tabu);
-    cudaFree(d->d_thdr);
-    cudaFree(d->d_tpos);
-    cudaFree(d->d_fitems);
-    cudaFree(d->d_cta_first);
-    d->d_tabu = nullptr;
-    d->d_thdr = nullptr;
-    d->d_tpos = nullptr;
-    d->d_fitems = nullptr;
-    d->d_cta_first = nullptr;
     cudaFree(d->d_adj_units);
     cudaFree(d->d_adj_prefix);
     d->d_adj_units = nullptr;
@@ -175,238 +163,53 @@ int pow2ceil(int v) {
 
 }  // namespace
 
-namespace {
-
-// Per tile: centre x_c (FP32), log2(f_c / f_ref) as hi + lo, the largest |x - x_c| of its bins
-// (rounded up) and, in its sign bit, whether some pair block's two bins have different nu.
-__global__ void tile_header_kernel(int64_t n_tiles, const TilePos* __restrict__ tpos, const DatasetDev* __restrict__ ds,
-                                   int n_ds, const double* __restrict__ rec64, float4* __restrict__ hdr) {
-    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= n_tiles) return;
-    int lo = 0, hi = n_ds - 1;   // dataset of tile g: the last one whose first tile is <= g
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (ds[mid].tbase <= g) lo = mid; else hi = mid - 1;
-    }
-    const DatasetDev& D = ds[lo];
-    const TilePos tp = tpos[g];
-    const int64_t b = D.bin0 + tp.start;
-    const double xa = rec64[b * kRec], xb = rec64[(b + tp.nb - 1) * kRec];
-    const float xc = (float)(0.5 * (xa + xb));
-    const double r = fmax(fabs(xa - (double)xc), fabs(xb - (double)xc)) * (1.0 + 1e-6);
-    const double lc = (double)xc * kLog2_10 - log2(D.f_ref);
-    const float lc_hi = (float)lc;
-    bool eq = true;
-    for (int i = 0; i < tp.nb; i += 2) eq &= rec64[(b + i) * kRec + 2] == rec64[(b + i + 1) * kRec + 2];
-    const float rf = (float)r;
-    hdr[g] = make_float4(xc, lc_hi, (float)(lc - (double)lc_hi), eq ? rf : -rf - 0.0f);
-}
-
-// Tile table (see kRecU): one thread per padded bin, after the headers.
-__global__ void tile_table_kernel(int64_t n_pad, const TilePos* __restrict__ tpos, const DatasetDev* __restrict__ ds,
-                                  int n_ds, const double* __restrict__ rec64, const float4* __restrict__ hdr,
-                                  float* __restrict__ tabu) {
-    const int64_t ip = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (ip >= n_pad) return;
-    const DatasetDev& D = ds[dataset_of_bin(ds, n_ds, ip)];
-    const int64_t i = ip - D.bin0;
-    int lo = 0, hi = D.ntiles - 1;   // tile of bin i
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (tpos[D.tbase + mid].start <= i) lo = mid; else hi = mid - 1;
-    }
-    const double* r = rec64 + ip * kRec;
-    const double u = r[0] - (double)hdr[D.tbase + lo].x;
-    float v[kRecU];
-    v[0] = (float)u;
-    v[1] = (float)(u * u);
-    v[2] = (float)(u * u * u);
-    v[3] = (float)r[2];
-    for (int q = 0; q < 9; ++q) v[4 + q] = (float)r[3 + q];
-    v[13] = (float)r[0];
-    float* o = tabu + (ip >> 1) * kPairRecU + (ip & 1);
-    for (int q = 0; q < kRecU; ++q) o[2 * q] = v[q];
-}
-
-// Longest-processing-time-first assignment of items with the given costs to `grid` CTAs;
-// returns the largest load.  owner[k] receives the CTA of item k.
-int64_t lpt_assign(const std::vector<int64_t>& cost, int grid, std::vector<int32_t>& owner) {
-    std::vector<int32_t> order(cost.size());
-    for (size_t k = 0; k < order.size(); ++k) order[k] = (int32_t)k;
-    std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return cost[a] > cost[b]; });
-    using E = std::pair<int64_t, int32_t>;   // (load, cta)
-    std::priority_queue<E, std::vector<E>, std::greater<E>> heap;
-    for (int b = 0; b < grid; ++b) heap.push(E(0, b));
-    owner.assign(cost.size(), 0);
-    int64_t mx = 0;
-    for (int32_t k : order) {
-        E e = heap.top();
-        heap.pop();
-        owner[k] = e.second;
-        e.first += cost[k];
-        mx = std::max(mx, e.first);
-        heap.push(e);
-    }
-    return mx;
-}
-
-}  // namespace
-
-// Builds the work decomposition for the current tiling.
-//  1. Ranges: the bins of each dataset are split into n_r equal ranges (even bounds), with n_r
-//     chosen so that the (range, state chunk) items, assigned to the fused kernel's persistent
-//     grid by LPT, load every CTA evenly (smallest items-per-CTA target m whose largest load is
-//     within 3 % of the mean, else the best).
-//  2. Tiles: each range is cut into tiles of at most tile_bins bins; partial sums are per
-//     (state, tile).  The tile headers and the tile table of the fused kernel are rebuilt.
-//  3. Work lists: FP64 kernel items per (tile, chunk); fused items per (range, chunk), grouped
-//     per CTA in (dataset, chunk, range) order so a CTA's intervals carry over between ranges.
+// Builds the work list for the current tiling: per dataset, tiles of tile_bins bins times
+// chunks of sc states (sc = min(states_per_cta, next power of two >= states of the dataset)).
 lisa_status rebuild_work(lisa_data* d) {
     const lisa_tiling& t = d->tiling;
-    const int occ = t.ctas_per_sm > 0 ? t.ctas_per_sm : fused_ctas_per_sm(d, t);
-    const int grid = std::max(1, d->n_sm * std::max(occ, 1));
-    const int nd = d->n_datasets;
-    constexpr int64_t kMinRangeBins = 64;
-    auto chunk_sc = [&](const DatasetDev& D) { return std::max(1, std::min(t.states_per_cta, pow2ceil(D.ns))); };
-    int64_t total = 0;
-    for (const auto& D : d->h_ds) total += D.npad * D.ns;
-    std::vector<int64_t> nr((size_t)nd, 1), best_nr((size_t)nd, 1);
-    double best_ratio = 1e300;
-    for (int m : {1, 2, 3, 4, 6, 8}) {
-        const double Tm = std::max(1.0, (double)total / ((double)m * grid));
-        std::vector<int64_t> cost;
-        for (int k = 0; k < nd; ++k) {
-            const DatasetDev& D = d->h_ds[k];
-            if (D.ns == 0 || D.npad == 0) {
-                nr[k] = 1;
-                continue;
-            }
-            const int sc = chunk_sc(D);
-            int64_t r = llround((double)D.npad * std::min(sc, D.ns) / Tm);
-            r = std::max<int64_t>(1, std::min<int64_t>(r, std::max<int64_t>(1, D.npad / kMinRangeBins)));
-            nr[k] = r;
-            const int64_t np = D.npad / 2;
-            for (int64_t q = 0; q < r; ++q) {
-                const int64_t len = 2 * (((q + 1) * np) / r - (q * np) / r);
-                for (int s = 0; s < D.ns; s += sc) cost.push_back(len * std::min(sc, D.ns - s));
-            }
-        }
-        std::vector<int32_t> owner;
-        const int64_t mx = cost.empty() ? 0 : lpt_assign(cost, grid, owner);
-        const double ratio = total > 0 ? (double)mx * grid / (double)total : 1.0;
-        if (ratio < best_ratio - 1e-9) {
-            best_ratio = ratio;
-            best_nr = nr;
-        }
-        if (ratio <= 1.03) break;
-    }
-    nr = best_nr;
-    // tiles
-    std::vector<TilePos> tpos;
-    std::vector<std::vector<int32_t>> range_t0((size_t)nd), range_nt((size_t)nd);
+    std::vector<WorkItem> items;
     int64_t pbase = 0;
-    int32_t max_tiles = 1;
-    for (int k = 0; k < nd; ++k) {
+    for (int k = 0; k < d->n_datasets; ++k) {
         DatasetDev& D = d->h_ds[k];
-        D.tbase = (int32_t)tpos.size();
-        const int64_t np = D.npad / 2;
-        int32_t nt = 0;
-        for (int64_t q = 0; q < nr[k]; ++q) {
-            const int64_t a = 2 * ((q * np) / nr[k]), b = 2 * (((q + 1) * np) / nr[k]);
-            range_t0[k].push_back(nt);
-            int32_t c = 0;
-            for (int64_t x = a; x < b; x += t.tile_bins, ++c)
-                tpos.push_back(TilePos{(int32_t)x, (int32_t)std::min<int64_t>(t.tile_bins, b - x)});
-            range_nt[k].push_back(c);
-            nt += c;
-        }
-        D.ntiles = nt;
+        D.ntiles = (int32_t)((D.npad + t.tile_bins - 1) / t.tile_bins);
         D.pbase = pbase;
         pbase += (int64_t)D.ns * D.ntiles;
-        max_tiles = std::max(max_tiles, nt);
-    }
-    d->n_partials = pbase;
-    d->n_tiles = (int64_t)tpos.size();
-    d->max_tiles = max_tiles;
-    // FP64 items: (tile, chunk)
-    std::vector<WorkItem> items;
-    for (int k = 0; k < nd; ++k) {
-        const DatasetDev& D = d->h_ds[k];
         if (D.ns == 0 || D.npad == 0) continue;
-        const int sc = chunk_sc(D);
-        for (int32_t tt = 0; tt < D.ntiles; ++tt) {
-            const TilePos& p = tpos[(size_t)D.tbase + tt];
-            for (int32_t s = 0; s < D.ns; s += sc)
-                items.push_back(WorkItem{D.bin0 + p.start, p.nb, D.s0 + s, std::min(sc, D.ns - s), sc, tt, k});
+        int sc = std::min(t.states_per_cta, pow2ceil(D.ns));
+        sc = std::max(sc, 1);
+        for (int32_t tile = 0; tile < D.ntiles; ++tile) {
+            int64_t b0 = D.bin0 + (int64_t)tile * t.tile_bins;
+            int32_t nb = (int32_t)std::min<int64_t>(t.tile_bins, D.bin0 + D.npad - b0);
+            for (int32_t s = 0; s < D.ns; s += sc) {
+                WorkItem w;
+                w.bin0 = b0;
+                w.nb = nb;
+                w.s0 = D.s0 + s;
+                w.ns = std::min(sc, D.ns - s);
+                w.sc = sc;
+                w.tile = tile;
+                w.ds = k;
+                items.push_back(w);
+            }
         }
     }
-    // fused items: (range, chunk), LPT over the grid, then grouped per CTA
-    std::vector<FusedItem> fi;
-    std::vector<int64_t> cost;
-    for (int k = 0; k < nd; ++k) {
-        const DatasetDev& D = d->h_ds[k];
-        if (D.ns == 0 || D.npad == 0) continue;
-        const int sc = chunk_sc(D);
-        for (int32_t s = 0; s < D.ns; s += sc)
-            for (size_t q = 0; q < range_t0[k].size(); ++q) {
-                const int32_t t0 = range_t0[k][q], ntl = range_nt[k][q];
-                if (ntl == 0) continue;
-                int64_t len = 0;
-                for (int32_t x = 0; x < ntl; ++x) len += tpos[(size_t)D.tbase + t0 + x].nb;
-                fi.push_back(FusedItem{k, D.s0 + s, std::min(sc, D.ns - s), sc, t0, ntl});
-                cost.push_back(len * std::min(sc, D.ns - s));
-            }
-    }
-    std::vector<int32_t> owner;
-    if (!fi.empty()) lpt_assign(cost, grid, owner);
-    std::vector<int32_t> order(fi.size());
-    for (size_t k = 0; k < order.size(); ++k) order[k] = (int32_t)k;
-    std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return owner[a] < owner[b]; });
-    std::vector<FusedItem> fsorted;
-    std::vector<int32_t> cta_first((size_t)grid + 1, 0);
-    for (int32_t k : order) {
-        fsorted.push_back(fi[k]);
-        cta_first[(size_t)owner[k] + 1]++;
-    }
-    for (int b = 0; b < grid; ++b) cta_first[(size_t)b + 1] += cta_first[b];
-    d->fgrid = grid;
-    d->n_items = (int64_t)items.size();
-
+    // Larger tiles first so that the persistent grid's static schedule ends evenly.
+    std::stable_sort(items.begin(), items.end(), [](const WorkItem& a, const WorkItem& b) {
+        return (int64_t)a.nb * a.ns > (int64_t)b.nb * b.ns;
+    });
+    d->n_partials = pbase;
     cudaFree(d->d_items);
-    cudaFree(d->d_tpos);
-    cudaFree(d->d_thdr);
-    cudaFree(d->d_tabu);
-    cudaFree(d->d_fitems);
-    cudaFree(d->d_cta_first);
     d->d_items = nullptr;
-    d->d_tpos = nullptr;
-    d->d_thdr = nullptr;
-    d->d_tabu = nullptr;
-    d->d_fitems = nullptr;
-    d->d_cta_first = nullptr;
-    lisa_status st;
-    if ((st = dev_alloc(&d->d_items, items.size())) || (st = dev_alloc(&d->d_tpos, tpos.size())) ||
-        (st = dev_alloc(&d->d_thdr, tpos.size())) || (st = dev_alloc(&d->d_tabu, (size_t)(d->n_pad / 2) * kPairRecU)) ||
-        (st = dev_alloc(&d->d_fitems, fsorted.size())) || (st = dev_alloc(&d->d_cta_first, cta_first.size())))
-        return st;
-    if (cudaMemcpy(d->d_items, items.data(), items.size() * sizeof(WorkItem), cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemcpy(d->d_tpos, tpos.data(), tpos.size() * sizeof(TilePos), cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemcpy(d->d_fitems, fsorted.data(), fsorted.size() * sizeof(FusedItem), cudaMemcpyHostToDevice) !=
-            cudaSuccess ||
-        cudaMemcpy(d->d_cta_first, cta_first.data(), cta_first.size() * sizeof(int32_t), cudaMemcpyHostToDevice) !=
-            cudaSuccess)
-        return LISA_ERR_CUDA;
-    // device copy of the dataset table (ntiles / pbase / tbase changed), then the tile tables
-    if (cudaMemcpy(d->d_ds, d->h_ds.data(), d->h_ds.size() * sizeof(DatasetDev), cudaMemcpyHostToDevice) !=
+    d->n_items = (int64_t)items.size();
+    lisa_status st = dev_alloc(&d->d_items, items.size());
+    if (st) return st;
+    if (cudaMemcpy(d->d_items, items.data(), items.size() * sizeof(WorkItem), cudaMemcpyHostToDevice) !=
         cudaSuccess)
         return LISA_ERR_CUDA;
-    if (d->n_tiles > 0) {
-        tile_header_kernel<<<(unsigned)((d->n_tiles + 255) / 256), 256>>>(d->n_tiles, d->d_tpos, d->d_ds, nd,
-                                                                          d->d_rec64, d->d_thdr);
-        tile_table_kernel<<<(unsigned)((d->n_pad + 255) / 256), 256>>>(d->n_pad, d->d_tpos, d->d_ds, nd, d->d_rec64,
-                                                                       d->d_thdr, d->d_tabu);
-        if (cudaGetLastError() != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) return LISA_ERR_CUDA;
-    }
+    // device copy of the dataset table (ntiles / pbase changed)
+    if (cudaMemcpy(d->d_ds, d->h_ds.data(), d->h_ds.size() * sizeof(DatasetDev),
+                   cudaMemcpyHostToDevice) != cudaSuccess)
+        return LISA_ERR_CUDA;
     return LISA_SUCCESS;
 }
 
@@ -497,9 +300,7 @@ lisa_status lisa_data_create(const lisa_data_desc* desc, lisa_stream_t stream, l
         X.xb_min = X.nbins ? std::log10(q.freq[X.rbin0]) : 0.0;
         X.xb_max = X.nbins ? std::log10(q.freq[X.rbin0 + X.nbins - 1]) : 0.0;
         X.f_ref = q.f_ref[k];
-        X.xref = (float)std::log10(q.f_ref[k]);
         X.ntiles = 0;
-        X.tbase = 0;
         X.pbase = 0;
         X.psd_base = psd_base;
         psd_base += (int64_t)C * X.ns * X.nbins;

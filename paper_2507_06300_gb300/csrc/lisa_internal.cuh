@@ -25,15 +25,6 @@ constexpr int kRec = 12;         // per-bin fields: x, ell, nu, Goms[3], Gtm[3],
 // Both tables use padded bin indices: every dataset is padded to an even bin count with a
 // dummy bin (copy of its last bin with nu = 0).
 constexpr int kPairRec = 2 * kRec;
-// Tile table of the fused FP32 kernel (rebuilt with the tiling): blocks of two bins like the FP32
-// table, with the fields
-//   0 u = x - x_c, 1 u^2, 2 u^3, 3 nu, 4-6 G_oms,c, 7-9 G_tm,c, 10-12 G_h,c, 13 x (FP32)
-// where x_c (an FP32 number) is the centre of the bin's tile, u is formed in FP64 and rounded.
-// Each spline interval's cubic is re-expanded about x_c once per tile, so a bin's perturbation
-// is d0 + d1 u + d2 u^2 + d3 u^3: three FMAs with no shift, and well conditioned because |u| is
-// at most half a tile wide.
-constexpr int kRecU = 14;
-constexpr int kPairRecU = 2 * kRecU;   // 28 floats = 7 x 16 bytes per pair block
 constexpr int kThreads = 256;    // threads of the plain FP64 likelihood kernel
 constexpr int kThreads32 = 128;  // threads of the fused FP32 likelihood kernel
 constexpr int kMaxStatesPerItem = 128;  // state lanes of a work item (<= both thread counts)
@@ -53,15 +44,11 @@ constexpr int kRouted = 1 << 16;        // internal status bit: state routed to 
 constexpr int kUserBits = 0xffff;       // LISA_STATE_* bits
 constexpr int kStatusNonfinite = LISA_STATE_NONFINITE;
 constexpr unsigned kWaitLimit = 1u << 20;   // bounded spin on an mbarrier (then give up)
-constexpr int kMaxTileBins = 1984;          // 2 staged tiles x 56 B/bin must fit in 227 KB
+constexpr int kMaxTileBins = 2048;          // 2 staged tiles x 48 B/bin must fit in 227 KB
 constexpr int kAdjBins = 2048;              // bins per (state, range) in the adjoint
 
-// Bins of each dataset are cut into ranges (balanced across the persistent grid of the fused
-// FP32 kernel) and each range into tiles of at most tile_bins bins; log L partial sums are kept
-// per (state, tile).
-//
-// One unit of work of the plain FP64 kernel: a tile of one dataset and a chunk of its states.
-// Threads map to (state lane, bin sub-range): lane = tid % sc, range = tid / sc.
+// One unit of work of the fused kernels: a tile of bins of one dataset and a chunk of its
+// states.  Threads map to (state lane, bin sub-range): lane = tid % sc, range = tid / sc.
 struct WorkItem {
     int64_t bin0;   // first bin (global index)
     int32_t nb;     // bins in the tile
@@ -72,19 +59,6 @@ struct WorkItem {
     int32_t ds;     // dataset index
 };
 static_assert(sizeof(WorkItem) == 32, "WorkItem layout");
-
-// One unit of work of the fused FP32 kernel: a range of nt consecutive tiles (from tile t0 of
-// its dataset) and a chunk of the dataset's states.  Each CTA of the persistent grid runs a
-// contiguous list of these, balanced by state-bins; within a range a thread's spline intervals
-// carry over from tile to tile.
-struct FusedItem {
-    int32_t ds, s0, ns, sc;   // dataset, first state, states in the chunk, state lanes (power of 2)
-    int32_t t0, nt;           // first tile (dataset-local index), tiles in the range
-};
-// Per tile: bins [bin0 + start, bin0 + start + nb) of its dataset (start, nb even).
-struct TilePos {
-    int32_t start, nb;
-};
 
 // One unit of the adjoint: a range of kAdjBins bins of one dataset and up to 32 of its states
 // (one warp, lanes = states).
@@ -99,10 +73,8 @@ struct DatasetDev {
     int64_t pbase;           // first partial slot of the dataset (partials are [tile][state])
     int64_t psd_base;        // first element of the dataset's states in a model-PSD output
     int32_t s0, ns;          // state range
-    int32_t ntiles;          // tiles (partial sums per state)
+    int32_t ntiles;          // tiles of tile_bins bins
     int32_t nranges;         // adjoint ranges of kAdjBins bins
-    int32_t tbase;           // global index of the dataset's first tile
-    float xref;              // log10 f_ref rounded to FP32 (break of the broken power law)
     double x_lo, x_hi;       // edge knot positions
     double xb_min, xb_max;   // log10 f of the first and last bin
     double f_ref;
@@ -129,17 +101,6 @@ struct lisa_data {
     float* d_elllo32 = nullptr;      // [n_pad] low part of ell = log2(f / f_ref)
     lisa_tiling tiling{};
     lisa::WorkItem* d_items = nullptr;
-    // fused FP32 kernel: tile table, per-tile header (x_c, log2(f_c / f_ref) as hi + lo, largest
-    // |u|, with the sign bit set when some pair block's two bins have different nu) and bin
-    // positions, the range items and the first item of each CTA (fgrid + 1 entries)
-    float* d_tabu = nullptr;
-    float4* d_thdr = nullptr;
-    lisa::TilePos* d_tpos = nullptr;
-    lisa::FusedItem* d_fitems = nullptr;
-    int32_t* d_cta_first = nullptr;
-    int64_t n_tiles = 0;
-    int32_t fgrid = 0;               // CTAs of the fused FP32 launch
-    int32_t max_tiles = 0;           // largest tile count of a dataset
     lisa::AdjUnit* d_adj_units = nullptr;
     int64_t n_adj_units = 0;
     int64_t* d_adj_prefix = nullptr; // [n_states] adjoint ranges of all earlier states
@@ -200,8 +161,6 @@ inline size_t ws_fwd_bytes(const lisa_data* d) {
 size_t grad_extra_bytes(const lisa_data* d, int kmax);
 
 lisa_status rebuild_work(lisa_data* d);
-// Resident CTAs per SM of the fused FP32 kernel under tiling t (its registers and shared memory).
-int fused_ctas_per_sm(const lisa_data* d, const lisa_tiling& t);
 
 // Per-kernel timing (lisa_data_set_profiling): whether this call records events (profiling on
 // and the stream not capturing), and an event record at point k of the call.

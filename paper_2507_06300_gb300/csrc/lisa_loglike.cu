@@ -1,35 +1,31 @@
 // Fused likelihood kernels: spline evaluation -> PSD assembly (Eq. splines) -> per-bin
 // Wishart terms -> FP64 reduction over bins (Sec. III.D), for every state at once.
 //
-// FP32 path: each CTA of a persistent grid runs a host-balanced list of (bin range, state chunk)
-// items tile by tile; a tile of the tile table (u = x - x_c, u^2, u^3, nu and the templates per
-// bin) is staged into shared memory with one bulk asynchronous copy (cp.async.bulk + mbarrier),
-// double-buffered, and read by all state lanes of the CTA (broadcast).  Each thread owns one
-// state and a run of bins of every tile; it keeps the current interval of each spline in
-// registers, re-expanded about the tile centre x_c once per tile, and advances it only when a
-// bin passes the interval's right knot (bins are sorted in frequency, so the check is done once
-// per group of bins).
+// FP32 path: the bin records of a work item (a tile of bins of one dataset) are staged into
+// shared memory with one bulk asynchronous copy (cp.async.bulk + mbarrier), double-buffered
+// across the persistent grid's items, and read by all state lanes of the CTA (broadcast).
+// Each thread owns one state and a contiguous run of bins; it keeps the current interval of
+// each spline in registers and advances it only when a bin passes the interval's right knot
+// (bins are sorted in frequency, so the check is done once per group of bins).
 //
 // Per bin and state (normalised by the periodogram, so P-hat = 1, S-hat ~ 1):
-//   E_c = 2^{P'_n,c},  E_h = A 2^{P'_h + n ell}                          (P' = log2(10) P)
-// where P' = d0 + d1 u + d2 u^2 + d3 u^3 with |u| at most half a tile wide, and for the SGWB
-// spline the power law n ell = n (ell_c + log2(10) u) is folded into d0 and d1.
+//   E_c = 2^{P'_n,c(x)},  E_h = A 2^{P'_h(x) + n ell}                  (P' = log2(10) P)
+// with each spline interval's cubic expanded about its midpoint (|x - xo| <= h/2 within the
+// knots), which keeps the FP32 Horner sums small.
 //   S_c = (a_oms^2 G_oms,c + a_tm^2 G_tm,c) E_c + E_h G_h,c
 //   term = nu [ sum_c 1/S_c + ln prod_c S_c - C ]
-// The reciprocal sums and the logs are fused over the two bins of a pair block (equal nu):
-// sum 1/S = N / P with P the product of all 2C channel PSDs, and sum ln S = ln2 lg2 P, so a
-// state-bin takes half a MUFU rcp and half a MUFU lg2, with a guarded per-bin, per-channel
-// fallback when the product leaves a safe FP32 range.  Terms are summed in FP32 over runs of 32
-// bins, then in float-float per tile and FP64 across tiles; the constant -C sum nu - sum nu ln P
-// is added in FP64 at the end.
+// The reciprocal sum and the log are fused: sum_c 1/S_c = (sum_c prod_{c' != c} S_c') / prod S
+// and ln prod S = ln2 lg2(prod S): one MUFU rcp and one MUFU lg2 per state-bin, with a
+// per-channel fallback when the product leaves a safe FP32 range.  Terms are summed in FP32 over
+// runs of 32 bins and then in FP64; the constant -C sum nu - sum nu ln P is added in FP64 at the
+// end.
 //
 // States whose spline intervals are too ill-conditioned for FP32 (setup flags them: large
-// overshoots between close knots, |P| up to tens of decades for prior draws) have those
-// intervals' bins masked here and evaluated by the compensated kernel: float-float Horner sums
-// and the per-bin term in the log domain, so any exponent range is handled.
+// overshoots between close knots, |P| up to tens of decades for prior draws) are skipped here
+// and evaluated by the compensated kernel: float-float Horner sums and the per-bin term in the
+// log domain, so any exponent range is handled.
 #include <cmath>
 #include <mutex>
-#include <type_traits>
 
 #include "lisa_math.cuh"
 
@@ -80,6 +76,23 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity
     return false;
 }
 
+struct Iv32 {
+    float xr, xo, c0, c1, c2, c3;
+    const float* base;
+    int j, last;   // current interval, last interval index
+};
+
+__device__ __forceinline__ void load_iv(Iv32& v) {
+    const float4 A = __ldg(reinterpret_cast<const float4*>(v.base + (size_t)v.j * kSplineRec32));
+    const float4 B = __ldg(reinterpret_cast<const float4*>(v.base + (size_t)v.j * kSplineRec32 + 4));
+    v.xr = A.x;
+    v.xo = A.y;
+    v.c0 = A.z;
+    v.c1 = A.w;
+    v.c2 = B.x;
+    v.c3 = B.y;
+}
+
 // nu * (sum_c 1/S_c + ln prod_c S_c - C) in FP32: one reciprocal and one lg2 of the product,
 // per-channel when the product leaves [1e-30, 1e30].
 template <int C>
@@ -107,6 +120,34 @@ __device__ __forceinline__ float term_from_S(const float* S, float nu) {
         }
     }
     return nu * fmaf((float)kLn2, lg, v);
+}
+
+// One bin, scalar (used next to knots, where the two bins of a pair may sit in different
+// intervals).
+template <int C, bool HAS_H, bool BROKEN>
+__device__ __forceinline__ float bin_term32(const float* __restrict__ tb, int i, const Iv32* iv, float ao2,
+                                            float at2, float n1, float n2, float Af) {
+    constexpr int NSP = C + (HAS_H ? 1 : 0);
+    const float x = fld(tb, i, 0), ell = fld(tb, i, 1), nu = fld(tb, i, 2);
+    float p[NSP];
+#pragma unroll
+    for (int a = 0; a < NSP; ++a) {
+        const float t = x - iv[a].xo;
+        p[a] = fmaf(fmaf(fmaf(iv[a].c3, t, iv[a].c2), t, iv[a].c1), t, iv[a].c0);
+    }
+    float eh = 0.f;
+    if (HAS_H) {
+        const float sl = BROKEN ? (ell < 0.f ? n1 : n2) : n1;
+        eh = Af * ex2_approx(fmaf(sl, ell, p[C]));
+    }
+    float S[C];
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+        const float nc = fmaf(ao2, fld(tb, i, 3 + c), at2 * fld(tb, i, 6 + c));
+        const float e = ex2_approx(p[c]);
+        S[c] = HAS_H ? fmaf(e, nc, eh * fld(tb, i, 9 + c)) : e * nc;
+    }
+    return term_from_S<C>(S, nu);
 }
 
 // Safe range of the unguarded pair form: the channel product within 2^(+-99), so that its
@@ -148,76 +189,71 @@ __global__ void state_prep_kernel(int S, const double* __restrict__ theta, State
     prm[s] = p;
 }
 
-// Three-input maximum (one instruction on sm_100 and later).
+// Current interval of one spline duplicated into register pairs for the packed path.
+struct Iv2 {
+    float2 nxo, c0, c1, c2, c3;
+};
+
+// One bin, scalar, with the intervals held as duplicated pairs (their .x halves).
+template <int C, bool HAS_H, bool BROKEN>
+__device__ __forceinline__ float bin_term32p(const float* __restrict__ tb, int i, const Iv2* iv, float ao2, float at2,
+                                             float n1, float n2, float Af) {
+    constexpr int NSP = C + (HAS_H ? 1 : 0);
+    Iv32 v[NSP];
+#pragma unroll
+    for (int a = 0; a < NSP; ++a) {
+        v[a].xo = -iv[a].nxo.x;
+        v[a].c0 = iv[a].c0.x;
+        v[a].c1 = iv[a].c1.x;
+        v[a].c2 = iv[a].c2.x;
+        v[a].c3 = iv[a].c3.x;
+    }
+    return bin_term32<C, HAS_H, BROKEN>(tb, i, v, ao2, at2, n1, n2, Af);
+}
+__device__ __forceinline__ Iv2 dup(const Iv32& v) {
+    return Iv2{make_float2(-v.xo, -v.xo), make_float2(v.c0, v.c0), make_float2(v.c1, v.c1),
+               make_float2(v.c2, v.c2), make_float2(v.c3, v.c3)};
+}
+
+// Three-input maximum / minimum (one instruction on sm_100 and later).
 __device__ __forceinline__ float fmax3(float a, float b, float c) {
     float d;
     asm("max.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
     return d;
 }
-
-// Field k of bin i of a tile-table block (shared memory).
-__device__ __forceinline__ float fldu(const float* __restrict__ t, int i, int k) {
-    return t[(i >> 1) * kPairRecU + 2 * k + (i & 1)];
+__device__ __forceinline__ float fmin3(float a, float b, float c) {
+    float d;
+    asm("min.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+    return d;
 }
 
-// The current interval of one spline, re-expanded about the tile centre x_c:
-// P = d0 + d1 u + d2 u^2 + d3 u^3 (log2 units), each coefficient duplicated into a register pair
-// so that both bins of a pair block are evaluated by one FP32x2 instruction.
-struct Dq {
-    float2 d0, d1, d2, d3;
-};
-
-// Pieces of the per-bin term, guarded: v = sum_c 1/S_c - C and l = log2 prod_c S_c from one
-// reciprocal and one log2 of the channel product, per channel when the product leaves
-// [1e-30, 1e30].
-template <int C>
-__device__ __forceinline__ void term_parts(const float* S, float& v, float& l) {
-    float prod, num;
-    if (C == 3) {
-        const float p01 = S[0] * S[1];
-        prod = p01 * S[2];
-        num = fmaf(S[2], S[0] + S[1], p01);
-    } else {
-        prod = S[0] * S[1];
-        num = S[0] + S[1];
-    }
-    if (prod > 1e-30f && prod < 1e30f && num < 1e30f) {
-        v = fmaf(num, rcp_approx(prod), -(float)C);
-        l = lg2_approx(prod);
-    } else {
-        v = -(float)C;
-        l = 0.f;
-#pragma unroll
-        for (int c = 0; c < C; ++c) {
-            v += rcp_approx(S[c]);
-            l += lg2_approx(S[c]);
-        }
-    }
-}
-
-// One pair block (two consecutive bins) in FP32x2, both bins inside the current intervals.
-// EQ (the two bins have the same nu): the pair's reciprocal sum and log come from one reciprocal
-// and one log2 of the product P of all 2C channel PSDs,
-//   sum 1/S = N / P  with  N = num_a prod_b + num_b prod_a,   sum ln S = ln2 lg2 P,
-// otherwise per bin.  No range test here: mx keeps the largest |lg2| of a product and the caller
-// redoes the chunk on the guarded path when it left +-kPairLg2Max or the chunk sum is not finite.
-// keep = 0 drops the pair (an interval of a routed state that the compensated kernel evaluates).
-template <int C, bool HAS_H, bool EQ>
-__device__ __forceinline__ void pair_u(const float4* __restrict__ blk, const float4 q6, const Dq* dq, float2 ao2,
-                                       float2 at2, float2 Af, float keep, float2& av, float2& al, float& mx) {
+// Two consecutive bins (one pair block) with FP32x2 instructions; both bins lie in the current
+// intervals.  Returns nu * (sum_c 1/S_c + ln prod S_c - C) for both bins, formed from one
+// reciprocal and one log2 of the channel product without a range test: the caller keeps the
+// running maximum (mx) and minimum (mi) of log2 prod and recomputes the chunk on the guarded
+// scalar path when either left +-kPairLg2Max or the chunk sum is not finite.
+template <int C, bool HAS_H, bool BROKEN>
+__device__ __forceinline__ float2 pair_term32(const float4 q0, const float4* __restrict__ blk, const Iv2* iv,
+                                              float2 ao2, float2 at2, float n1, float n2, float2 Af, float& mx,
+                                              float& mi) {
     constexpr int NSP = C + (HAS_H ? 1 : 0);
-    const float4 q0 = blk[0], q1 = blk[1], q2 = blk[2], q3 = blk[3], q4 = blk[4], q5 = blk[5];
-    const float2 u = make_float2(q0.x, q0.y), u2 = make_float2(q0.z, q0.w), u3 = make_float2(q1.x, q1.y);
-    const float2 nu = make_float2(q1.z, q1.w);
-    const float2 go[3] = {make_float2(q2.x, q2.y), make_float2(q2.z, q2.w), make_float2(q3.x, q3.y)};
-    const float2 gt[3] = {make_float2(q3.z, q3.w), make_float2(q4.x, q4.y), make_float2(q4.z, q4.w)};
-    const float2 gh[3] = {make_float2(q5.x, q5.y), make_float2(q5.z, q5.w), make_float2(q6.x, q6.y)};
+    const float4 q1 = blk[1], q2 = blk[2], q3 = blk[3], q4 = blk[4], q5 = blk[5];
+    const float2 x = make_float2(q0.x, q0.y), ell = make_float2(q0.z, q0.w), nu = make_float2(q1.x, q1.y);
+    const float2 go[3] = {make_float2(q1.z, q1.w), make_float2(q2.x, q2.y), make_float2(q2.z, q2.w)};
+    const float2 gt[3] = {make_float2(q3.x, q3.y), make_float2(q3.z, q3.w), make_float2(q4.x, q4.y)};
+    const float2 gh[3] = {make_float2(q4.z, q4.w), make_float2(q5.x, q5.y), make_float2(q5.z, q5.w)};
     float2 p[NSP];
 #pragma unroll
-    for (int a = 0; a < NSP; ++a)
-        p[a] = __ffma2_rn(dq[a].d3, u3, __ffma2_rn(dq[a].d2, u2, __ffma2_rn(dq[a].d1, u, dq[a].d0)));
+    for (int a = 0; a < NSP; ++a) {
+        const float2 t = __fadd2_rn(x, iv[a].nxo);
+        p[a] = __ffma2_rn(__ffma2_rn(__ffma2_rn(iv[a].c3, t, iv[a].c2), t, iv[a].c1), t, iv[a].c0);
+    }
     float2 eh = make_float2(0.f, 0.f);
-    if (HAS_H) eh = __fmul2_rn(Af, make_float2(ex2_approx(p[C].x), ex2_approx(p[C].y)));
+    if (HAS_H) {
+        const float2 sl = BROKEN ? make_float2(ell.x < 0.f ? n1 : n2, ell.y < 0.f ? n1 : n2) : make_float2(n1, n1);
+        const float2 ex = __ffma2_rn(sl, ell, p[C]);
+        eh = __fmul2_rn(Af, make_float2(ex2_approx(ex.x), ex2_approx(ex.y)));
+    }
     float2 S[C];
 #pragma unroll
     for (int c = 0; c < C; ++c) {
@@ -234,319 +270,200 @@ __device__ __forceinline__ void pair_u(const float4* __restrict__ blk, const flo
         prod = __fmul2_rn(S[0], S[1]);
         num = __fadd2_rn(S[0], S[1]);
     }
-    if (EQ) {
-        const float P = prod.x * prod.y;
-        const float N = fmaf(num.x, prod.y, num.y * prod.x);
-        const float lg = lg2_approx(P);
-        const float v = fmaf(N, rcp_approx(P), -2.f * C);
-        const float nk = nu.x * keep;
-        av.x = fmaf(nk, v, av.x);
-        al.x = fmaf(nk, lg, al.x);
-        mx = fmax3(mx, lg, -lg);
-    } else {
-        const float2 v = __ffma2_rn(num, make_float2(rcp_approx(prod.x), rcp_approx(prod.y)),
-                                    make_float2(-(float)C, -(float)C));
-        const float2 lg = make_float2(lg2_approx(prod.x), lg2_approx(prod.y));
-        const float2 nk = __fmul2_rn(nu, make_float2(keep, keep));
-        av = __ffma2_rn(nk, v, av);
-        al = __ffma2_rn(nk, lg, al);
-        mx = fmax3(mx, fabsf(lg.x), fabsf(lg.y));
-    }
+    const float2 v = __ffma2_rn(num, make_float2(rcp_approx(prod.x), rcp_approx(prod.y)),
+                                make_float2(-(float)C, -(float)C));
+    const float2 lg = make_float2(lg2_approx(prod.x), lg2_approx(prod.y));
+    mx = fmax3(mx, lg.x, lg.y);
+    mi = fmin3(mi, lg.x, lg.y);
+    return __fmul2_rn(nu, __ffma2_rn(make_float2((float)kLn2, (float)kLn2), lg, v));
 }
 
-// Fused FP32 likelihood.  Persistent grid: CTA b runs the range items [cta_first[b],
-// cta_first[b + 1]) (balanced by the host), tile by tile; each tile of the tile table is staged
-// into shared memory by one bulk asynchronous copy completing on an mbarrier, double-buffered
-// across the CTA's tile sequence (bounded waits raise the error flag).  Thread = (state lane,
-// sub-range of each tile).  Per tile a thread re-expands its current interval of each spline
-// about the tile centre; a group of G bins whose last bin lies left of every current interval's
-// right knot takes the packed path, otherwise it runs bin by bin with interval advances and the
-// guarded per-bin term.  Intervals carry over between the tiles and ranges of one state chunk.
 template <int C, bool HAS_H, bool BROKEN, int G>
-__global__ void __launch_bounds__(kThreads32, 6)
-    loglike_fp32_kernel(const FusedItem* __restrict__ fitems, const int32_t* __restrict__ cta_first,
-                        const float* __restrict__ tabu, const float4* __restrict__ thdr,
-                        const TilePos* __restrict__ tpos, const StateParams* __restrict__ prm,
-                        const int32_t* __restrict__ sstat, const int32_t* __restrict__ nint,
-                        const float* __restrict__ srec, int kmax, int nsp, const DatasetDev* __restrict__ ds,
-                        double* __restrict__ partial, int* __restrict__ err, int tile_bins) {
+__global__ void __launch_bounds__(kThreads32, G == 8 ? 5 : 6)
+    loglike_fp32_kernel(const WorkItem* __restrict__ items, int n_items, const float* __restrict__ rec32,
+                        const StateParams* __restrict__ prm, const int32_t* __restrict__ sstat,
+                        const int32_t* __restrict__ nint, const float* __restrict__ srec, int kmax, int nsp,
+                        const DatasetDev* __restrict__ ds, double* __restrict__ partial, int* __restrict__ err,
+                        int tile_bins) {
     constexpr int NSP = C + (HAS_H ? 1 : 0);
-    constexpr int Q = kPairRecU / 4;   // float4 per pair block
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ __align__(8) uint64_t bars[2];
     __shared__ float2 red[kThreads32];
-    float* const sbuf0 = reinterpret_cast<float*>(smem);
-    float* const sbuf1 = reinterpret_cast<float*>(smem + (size_t)(tile_bins / 2) * kPairRecU * sizeof(float));
+    float* sbuf0 = reinterpret_cast<float*>(smem);
+    float* sbuf1 = reinterpret_cast<float*>(smem + (size_t)tile_bins * kRec * sizeof(float));
     const int tid = threadIdx.x;
-    const int kb = cta_first[blockIdx.x], ke = cta_first[blockIdx.x + 1];
-    if (kb >= ke) return;   // uniform per CTA
     if (tid == 0) {
         mbar_init(&bars[0], 1);
         mbar_init(&bars[1], 1);
         mbar_fence_init();
     }
     __syncthreads();
-    auto issue = [&](int k, int j, int b) {   // thread 0: stage tile j of item k into buffer b
-        const FusedItem f = fitems[k];
-        const DatasetDev& D = ds[f.ds];
-        const TilePos p = tpos[D.tbase + f.t0 + j];
-        const unsigned bytes = (unsigned)(p.nb >> 1) * kPairRecU * sizeof(float);
-        fence_proxy_async();
-        mbar_expect_tx(&bars[b], bytes);
-        bulk_copy_g2s(b ? sbuf1 : sbuf0, tabu + ((D.bin0 + p.start) >> 1) * kPairRecU, bytes, &bars[b]);
-    };
-    if (tid == 0) issue(kb, 0, 0);
-
-    // per-thread interval state (carried across the tiles of one state chunk)
-    int jj[NSP];
-    float xr[NSP];          // right bound of the current interval (the f_ref break included)
-    Dq dq[NSP];
-    unsigned hm = 0;        // intervals loaded as the zero cubic (ill-conditioned: masked)
-    unsigned bad = 0;       // intervals ill-conditioned about the tile centre (guarded path)
-    bool above = false;     // broken power law: current bins at or above f_ref
-    bool located = false;
-    int prev_ds = -1, prev_s0 = -1;
-    unsigned ph0 = 0, ph1 = 0;
-    FusedItem f = fitems[kb];
-    int k = kb, j = 0;
-    for (int step = 0; k < ke; ++step) {
-        const int b = step & 1;
-        int kn = k, jn = j + 1;
-        if (jn >= f.nt) {
-            kn = k + 1;
-            jn = 0;
+    unsigned phase0 = 0, phase1 = 0;
+    int it = blockIdx.x;
+    if (it < n_items && tid == 0) {
+        const WorkItem w = items[it];
+        const unsigned bytes = (unsigned)w.nb * kRec * sizeof(float);
+        mbar_expect_tx(&bars[0], bytes);
+        bulk_copy_g2s(sbuf0, rec32 + (w.bin0 >> 1) * kPairRec, bytes, &bars[0]);
+    }
+    for (int k = 0; it < n_items; it += gridDim.x, ++k) {
+        const int b = k & 1;
+        const int nxt = it + gridDim.x;
+        if (nxt < n_items && tid == 0) {
+            const WorkItem w = items[nxt];
+            const unsigned bytes = (unsigned)w.nb * kRec * sizeof(float);
+            fence_proxy_async();
+            mbar_expect_tx(&bars[b ^ 1], bytes);
+            bulk_copy_g2s(b ? sbuf0 : sbuf1, rec32 + (w.bin0 >> 1) * kPairRec, bytes, &bars[b ^ 1]);
         }
-        if (kn < ke && tid == 0) issue(kn, jn, b ^ 1);
+        const WorkItem w = items[it];
         if (b == 0) {
-            mbar_wait_bounded(&bars[0], ph0, err);
-            ph0 ^= 1;
+            mbar_wait_bounded(&bars[0], phase0, err);
+            phase0 ^= 1;
         } else {
-            mbar_wait_bounded(&bars[1], ph1, err);
-            ph1 ^= 1;
+            mbar_wait_bounded(&bars[1], phase1, err);
+            phase1 ^= 1;
         }
         const float* tb = b ? sbuf1 : sbuf0;
         const float4* tb4 = reinterpret_cast<const float4*>(tb);
-        const DatasetDev& D = ds[f.ds];
-        const int g = D.tbase + f.t0 + j;
-        const int nbt = tpos[g].nb;
-        const int sc = f.sc;
+
+        const int sc = w.sc;
         const int R = kThreads32 / sc;
         const int ls = tid & (sc - 1);
         const int r = tid / sc;
-        const int s = f.s0 + ls;
-        if (!(f.ds == prev_ds && f.s0 == prev_s0)) located = false;
-        prev_ds = f.ds;
-        prev_s0 = f.s0;
+        const int s = w.s0 + ls;
         // every valid state, routed ones included: the bins of an ill-conditioned interval are
         // masked out here (the compensated kernel adds them), all other bins are summed here
-        const bool active = ls < f.ns && (sstat[s] & kUserBits) == 0;
+        const bool active = ls < w.ns && (sstat[s] & kUserBits) == 0;
         ff accf = {0.f, 0.f};
-        const int np = nbt >> 1;
-        const int plo = (r * np) / R, phi = ((r + 1) * np) / R;
-        if (active && plo < phi) {
-            const float4 H = __ldg(thdr + g);
-            const float xc = H.x, lch = H.y, lcl = H.z, rt = fabsf(H.w);
-            const bool nu_eq = !signbit(H.w);
-            const float xref = BROKEN ? D.xref : 0.f;
-            const int64_t sp0 = (int64_t)s * nsp;
-            const float4 P0 = __ldg(reinterpret_cast<const float4*>(prm + s));
-            const float ao2 = P0.x, at2 = P0.y, Af = HAS_H ? P0.z : 0.f;
-            const float2 ao2_2 = make_float2(ao2, ao2), at2_2 = make_float2(at2, at2), Af2 = make_float2(Af, Af);
-            // the record of interval jj[a] -> right bound and the cubic about x_c (+ the SGWB
-            // power law n log2(f / f_ref) = n (l_c + log2(10) u), with the slope of the side of
-            // f_ref for the broken law); ill-conditioned records are masked, intervals whose
-            // expansion about x_c is ill-conditioned (T' > kRobustT over the tile) go to the
-            // guarded path
-            auto expand = [&](int a) {
-                const float* rr = srec + ((sp0 + a) * (int64_t)(kmax + 1) + jj[a]) * kSplineRec32;
-                const float4 A = __ldg(reinterpret_cast<const float4*>(rr));
-                const float4 B = __ldg(reinterpret_cast<const float4*>(rr + 4));
-                const unsigned bit = 1u << a;
-                float xrt = A.x;
-                if (BROKEN && a == C && !above) xrt = fminf(xrt, xref);
-                xr[a] = xrt;
-                if (!(B.w <= (float)kRobustT)) {
-                    const float2 z = make_float2(0.f, 0.f);
-                    dq[a] = Dq{z, z, z, z};
-                    hm |= bit;
-                    bad &= ~bit;
-                    return;
-                }
-                hm &= ~bit;
-                const float dl = (xc - A.y) - __ldg(rr + 8);
-                const float c0 = A.z, c1 = A.w, c2 = B.x, c3 = B.y;
-                const float t3 = 3.f * c3;
-                const float e2 = fmaf(t3, dl, c2);
-                float e1 = fmaf(dl, fmaf(t3, dl, 2.f * c2), c1);
-                float e0 = fmaf(dl, fmaf(dl, fmaf(dl, c3, c2), c1), c0);
-                const float Tp = fabsf(e0) + rt * (fabsf(e1) + rt * (fabsf(e2) + rt * fabsf(c3)));
-                if (Tp <= (float)kRobustT) bad &= ~bit; else bad |= bit;
-                if (HAS_H && a == C) {
-                    const float4 Q1 = __ldg(reinterpret_cast<const float4*>(prm + s) + 1);
-                    float nh = P0.w, nl = Q1.w;
-                    if (BROKEN && above) {
-                        nh = Q1.x;
-                        nl = __ldg(&prm[s].n2_lo);
+        if (active) {
+            const int np = w.nb >> 1;                          // pair blocks in the tile
+            const int plo = (r * np) / R, phi = ((r + 1) * np) / R;
+            if (plo < phi) {
+                const float4 q0 = __ldg(reinterpret_cast<const float4*>(prm + s));
+                const float ao2 = q0.x, at2 = q0.y, Af = HAS_H ? q0.z : 0.f, n1 = q0.w;
+                const float n2 = BROKEN ? __ldg(&prm[s].n2) : n1;
+                const float2 ao2_2 = make_float2(ao2, ao2), at2_2 = make_float2(at2, at2), Af2 = make_float2(Af, Af);
+                // per spline: right knot of the current interval, its index, and the interval's
+                // cubic duplicated into register pairs (the scalar path reads the .x halves);
+                // xmin = the nearest right knot.  An ill-conditioned interval (T > kRobustT, routed
+                // states only) is loaded as the zero cubic, which keeps its bins' arithmetic benign,
+                // and sets its bit in hm; keep2 = 0 while any bit is set, 1 otherwise, and scales
+                // each pair's contribution.
+                float xr[NSP];
+                int jj[NSP];
+                Iv2 iv2[NSP];
+                float xmin = INFINITY;
+                unsigned hm = 0;
+                float2 keep2 = make_float2(1.f, 1.f);
+                const int64_t sp0 = (int64_t)s * nsp;
+                auto reload = [&](int a) {
+                    const float* rr = srec + ((sp0 + a) * (int64_t)(kmax + 1) + jj[a]) * kSplineRec32;
+                    const float4 A = __ldg(reinterpret_cast<const float4*>(rr));
+                    const float4 B = __ldg(reinterpret_cast<const float4*>(rr + 4));
+                    xr[a] = A.x;
+                    if (B.w <= (float)kRobustT) {
+                        iv2[a] = Iv2{make_float2(-A.y, -A.y), make_float2(A.z, A.z), make_float2(A.w, A.w),
+                                     make_float2(B.x, B.x), make_float2(B.y, B.y)};
+                        hm &= ~(1u << a);
+                    } else {
+                        const float2 z = make_float2(0.f, 0.f);
+                        iv2[a] = Iv2{z, z, z, z, z};
+                        hm |= 1u << a;
                     }
-                    const float pr = nh * lch;
-                    const float pe = fmaf(nh, lch, -pr);
-                    e0 = pr + (e0 + (pe + fmaf(nh, lcl, nl * lch)));
-                    e1 = fmaf(nh, (float)kLog2_10, e1);
-                }
-                dq[a] = Dq{make_float2(e0, e0), make_float2(e1, e1), make_float2(e2, e2), make_float2(c3, c3)};
-            };
-            // x >= xr[a]: move interval a forward to the one holding x (index only)
-            auto step_to = [&](int a, float x) {
-                if (BROKEN && a == C && !above && x >= xref) above = true;
-                const int last = __ldg(nint + sp0 + a) - 1;
-                const float* base = srec + (sp0 + a) * (int64_t)(kmax + 1) * kSplineRec32;
-                while (jj[a] < last && x >= __ldg(base + (size_t)jj[a] * kSplineRec32)) ++jj[a];
-            };
-            auto locate = [&](float x) {
-                if (BROKEN) above = x >= xref;
-#pragma unroll
-                for (int a = 0; a < NSP; ++a)
-                    jj[a] = find_interval<float, kSplineRec32, 6>(srec + (sp0 + a) * (int64_t)(kmax + 1) * kSplineRec32,
-                                                                  __ldg(nint + sp0 + a), x);
-            };
-            auto nearest = [&]() {
-                float m = xr[0];
-#pragma unroll
-                for (int a = 1; a < NSP; ++a) m = fminf(m, xr[a]);
-                return bad ? -INFINITY : m;
-            };
-            // spline a at bin x (u from the table) from its record about the interval midpoint
-            // (the intervals that are ill-conditioned about the tile centre)
-            auto midpoint = [&](int a, float x, float u) {
-                const float* rr = srec + ((sp0 + a) * (int64_t)(kmax + 1) + jj[a]) * kSplineRec32;
-                const float4 A = __ldg(reinterpret_cast<const float4*>(rr));
-                const float4 B = __ldg(reinterpret_cast<const float4*>(rr + 4));
-                const float tt = x - A.y;
-                float pv = fmaf(fmaf(fmaf(B.y, tt, B.x), tt, A.w), tt, A.z);
-                if (HAS_H && a == C) {
-                    const float nh = (BROKEN && above) ? __ldg(&prm[s].n2) : P0.w;
-                    pv = fmaf(nh, fmaf((float)kLog2_10, u, lch + lcl), pv);
-                }
-                return pv;
-            };
-            // one bin on the guarded path: advance, then the per-bin term (masked bins add nothing)
-            auto scalar_bin = [&](int i, float2& av, float2& al) {
-                const float x = fldu(tb, i, 13);
-#pragma unroll
-                for (int a = 0; a < NSP; ++a)
+                    keep2 = hm ? make_float2(0.f, 0.f) : make_float2(1.f, 1.f);
+                };
+                auto advance = [&](int a, float x) {
                     if (x >= xr[a]) {
-                        step_to(a, x);
-                        expand(a);
+                        const int last = nint[sp0 + a] - 1;
+                        bool moved = false;
+                        while (x >= xr[a] && jj[a] < last) {
+                            ++jj[a];
+                            xr[a] = __ldg(srec + ((sp0 + a) * (int64_t)(kmax + 1) + jj[a]) * kSplineRec32);
+                            moved = true;
+                        }
+                        if (moved) reload(a);
                     }
-                if (hm) return;
-                const float u = fldu(tb, i, 0), u2 = fldu(tb, i, 1), u3 = fldu(tb, i, 2), nu = fldu(tb, i, 3);
-                float p[NSP];
+                };
+                auto locate = [&](float x) {
 #pragma unroll
-                for (int a = 0; a < NSP; ++a)
-                    p[a] = (bad >> a) & 1u ? midpoint(a, x, u)
-                                           : fmaf(dq[a].d3.x, u3, fmaf(dq[a].d2.x, u2, fmaf(dq[a].d1.x, u, dq[a].d0.x)));
-                const float eh = HAS_H ? Af * ex2_approx(p[C]) : 0.f;
-                float S[C];
+                    for (int a = 0; a < NSP; ++a) {
+                        jj[a] = find_interval<float, kSplineRec32, 6>(
+                            srec + (sp0 + a) * (int64_t)(kmax + 1) * kSplineRec32, nint[sp0 + a], x);
+                        reload(a);
+                    }
+                };
+                auto nearest = [&]() {
+                    float m = xr[0];
 #pragma unroll
-                for (int c = 0; c < C; ++c) {
-                    const float nc = fmaf(ao2, fldu(tb, i, 4 + c), at2 * fldu(tb, i, 7 + c));
-                    const float e = ex2_approx(p[c]);
-                    S[c] = HAS_H ? fmaf(e, nc, eh * fldu(tb, i, 10 + c)) : e * nc;
-                }
-                float v, l;
-                term_parts<C>(S, v, l);
-                av.x = fmaf(nu, v, av.x);
-                al.x = fmaf(nu, l, al.x);
-            };
-
-            const float x0 = fldu(tb, 2 * plo, 13);
-            if (!located) {
-                locate(x0);
-                located = true;
-            } else {
+                    for (int a = 1; a < NSP; ++a) m = fminf(m, xr[a]);
+                    return m;
+                };
+                // one bin on the scalar path (next to knots): advance, then the guarded term
+                auto scalar_bin = [&](int i) {
+                    const float x = fld(tb, i, 0);
 #pragma unroll
-                for (int a = 0; a < NSP; ++a)
-                    if (x0 >= xr[a]) step_to(a, x0);
-            }
-#pragma unroll
-            for (int a = 0; a < NSP; ++a) expand(a);
-            float xmin = nearest();
-            float keep = hm ? 0.f : 1.f;
-
-            auto run = [&](auto eq_tag) {
-                constexpr bool EQ = decltype(eq_tag)::value;
+                    for (int a = 0; a < NSP; ++a) advance(a, x);
+                    const float v = bin_term32p<C, HAS_H, BROKEN>(tb, i, iv2, ao2, at2, n1, n2, Af);
+                    return hm ? 0.f : v;
+                };
+                locate(fld(tb, 2 * plo, 0));
+                xmin = nearest();
                 int ip = plo;
                 while (ip < phi) {
                     const int pc0 = ip;
                     const int pcend = min(ip + 16, phi);
-                    float2 av = make_float2(0.f, 0.f), al = make_float2(0.f, 0.f);
-                    float mx = 0.f;
+                    float2 acc2 = make_float2(0.f, 0.f);
+                    float mx = 0.f, mi = 0.f;
                     for (; ip + G / 2 <= pcend; ip += G / 2) {
-                        const float4* blk = tb4 + ip * Q;
-                        // float4 6 of the group's last pair block: (G_h,T, G_h,T, x, x); .w is the
-                        // x of the group's last bin
-                        const float4 qg = blk[(G / 2 - 1) * Q + 6];
-                        if (qg.w < xmin) {
+                        const float4* blk = tb4 + ip * (kPairRec / 4);
+                        // first float4 of the group's last pair block: (x, x, ell, ell); its .y is
+                        // the x of the group's last bin
+                        const float4 qg = blk[(G / 2 - 1) * (kPairRec / 4)];
+                        if (qg.y < xmin) {
 #pragma unroll
-                            for (int gg = 0; gg < G / 2; ++gg) {
-                                const float4* pb = blk + gg * Q;
-                                pair_u<C, HAS_H, EQ>(pb, gg == G / 2 - 1 ? qg : pb[6], dq, ao2_2, at2_2, Af2, keep,
-                                                     av, al, mx);
+                            for (int g = 0; g < G / 2; ++g) {
+                                const float4* pb = blk + g * (kPairRec / 4);
+                                const float4 q0 = g == G / 2 - 1 ? qg : pb[0];
+                                acc2 = __ffma2_rn(keep2, pair_term32<C, HAS_H, BROKEN>(q0, pb, iv2, ao2_2, at2_2, n1,
+                                                                                       n2, Af2, mx, mi),
+                                                  acc2);
                             }
                         } else {
 #pragma unroll 1
-                            for (int i = 2 * ip; i < 2 * ip + G; ++i) scalar_bin(i, av, al);
+                            for (int i = 2 * ip; i < 2 * ip + G; ++i) acc2.x += scalar_bin(i);
                             xmin = nearest();
-                            keep = hm ? 0.f : 1.f;
                         }
                     }
 #pragma unroll 1
                     for (; ip < pcend; ++ip) {
-                        scalar_bin(2 * ip, av, al);
-                        scalar_bin(2 * ip + 1, av, al);
+                        acc2.x += scalar_bin(2 * ip);
+                        acc2.x += scalar_bin(2 * ip + 1);
                         xmin = nearest();
-                        keep = hm ? 0.f : 1.f;
                     }
-                    float sv = av.x + av.y, sl = (float)kLn2 * (al.x + al.y);
-                    if (!(mx <= kPairLg2Max && fabsf(sv + sl) < INFINITY)) {
-                        // a product left the range of the one-reciprocal form (or the numerator
-                        // overflowed): redo the chunk bin by bin on the guarded path, intervals
-                        // re-found at its start
-                        locate(fldu(tb, 2 * pc0, 13));
-#pragma unroll
-                        for (int a = 0; a < NSP; ++a) expand(a);
-                        av = make_float2(0.f, 0.f);
-                        al = make_float2(0.f, 0.f);
+                    if (!(mx <= kPairLg2Max && mi >= -kPairLg2Max && fabsf(acc2.x + acc2.y) < INFINITY)) {
+                        // a channel product left the range of the one-reciprocal form (or the
+                        // reciprocal-sum numerator overflowed): redo the chunk bin by bin on the
+                        // guarded path, intervals re-found at its start
+                        locate(fld(tb, 2 * pc0, 0));
+                        acc2 = make_float2(0.f, 0.f);
 #pragma unroll 1
-                        for (int i = 2 * pc0; i < 2 * pcend; ++i) scalar_bin(i, av, al);
+                        for (int i = 2 * pc0; i < 2 * pcend; ++i) acc2.x += scalar_bin(i);
                         xmin = nearest();
-                        keep = hm ? 0.f : 1.f;
-                        sv = av.x + av.y;
-                        sl = (float)kLn2 * (al.x + al.y);
                     }
-                    accf = ff_add(accf, two_sum(sv, sl));
+                    accf = ff_add(accf, two_sum(acc2.x, acc2.y));
                 }
-            };
-            if (nu_eq) run(std::true_type{});
-            else run(std::false_type{});
-        }
-        // per-tile partial sum of each state (R threads per state combined in float-float)
-        const int64_t slot = D.pbase + (int64_t)(s - D.s0) * D.ntiles + f.t0 + j;
-        if (R == 1) {
-            if (active) partial[slot] = (double)accf.hi + (double)accf.lo;
-        } else {
-            red[tid] = make_float2(accf.hi, accf.lo);
-            __syncthreads();
-            if (r == 0 && active) {
-                ff sum = {red[ls].x, red[ls].y};
-                for (int q = 1; q < R; ++q) sum = ff_add(sum, ff{red[ls + q * sc].x, red[ls + q * sc].y});
-                partial[slot] = (double)sum.hi + (double)sum.lo;
             }
         }
-        __syncthreads();   // this buffer is refilled by the next step's copy; red is reused
-        k = kn;
-        j = jn;
-        if (jn == 0 && k < ke) f = fitems[k];
+        red[tid] = make_float2(accf.hi, accf.lo);
+        __syncthreads();
+        if (r == 0 && active) {
+            ff sum = {red[ls].x, red[ls].y};
+            for (int q = 1; q < R; ++q) sum = ff_add(sum, ff{red[ls + q * sc].x, red[ls + q * sc].y});
+            const DatasetDev& D = ds[w.ds];
+            partial[D.pbase + (int64_t)(s - D.s0) * D.ntiles + w.tile] = (double)sum.hi + (double)sum.lo;
+        }
+        __syncthreads();  // the buffer read in this iteration is refilled in the next one
     }
 }
 
@@ -713,12 +630,11 @@ __device__ __forceinline__ void robust_bin(const float* __restrict__ tb, int i, 
 template <int C, bool HAS_H, bool BROKEN>
 __global__ void __launch_bounds__(kRobWarps * 32)
     loglike_robust_kernel(const int32_t* __restrict__ route, const int32_t* __restrict__ state_ds,
-                          const DatasetDev* __restrict__ ds, int max_runs,
+                          const DatasetDev* __restrict__ ds, int tile_bins, int max_runs,
                           const float* __restrict__ rec32, const float* __restrict__ xlo32,
                           const float* __restrict__ elllo32, const StateParams* __restrict__ prm,
                           const int32_t* __restrict__ nint, const float* __restrict__ srec,
-                          const float2* __restrict__ hull, const TilePos* __restrict__ tpos, int kmax, int nsp,
-                          double* __restrict__ partial) {
+                          const float2* __restrict__ hull, int kmax, int nsp, double* __restrict__ partial) {
     constexpr int NSP = C + (HAS_H ? 1 : 0);
     extern __shared__ float4 rsm[];
     const int lane = threadIdx.x & 31;
@@ -744,9 +660,8 @@ __global__ void __launch_bounds__(kRobWarps * 32)
         const ff lA = {q1.y, q1.z};
         {
             // skip a run that the state's ill-conditioned intervals do not reach
-            const TilePos pB = tpos[D.tbase + t1 - 1];
-            const int64_t bA = D.bin0 + tpos[D.tbase + t0].start;
-            const int64_t bB = D.bin0 + pB.start + pB.nb - 1;
+            const int64_t bA = D.bin0 + (int64_t)t0 * tile_bins;
+            const int64_t bB = min(D.bin0 + (int64_t)t1 * tile_bins, D.bin0 + D.npad) - 1;
             const float xA = fld(rec32 + (bA >> 1) * kPairRec, (int)(bA & 1), 0);
             const float xB = fld(rec32 + (bB >> 1) * kPairRec, (int)(bB & 1), 0);
             const float2 h = __ldg(hull + s);
@@ -754,9 +669,9 @@ __global__ void __launch_bounds__(kRobWarps * 32)
         }
         IvR iv[NSP];
         {
-            const TilePos p0 = tpos[D.tbase + t0];
-            const int64_t b0 = D.bin0 + p0.start;
-            const float x0 = fld(rec32 + (b0 >> 1) * kPairRec, min(lane, p0.nb - 1), 0);
+            const int64_t b0 = D.bin0 + (int64_t)t0 * tile_bins;
+            const int nb = (int)min((int64_t)tile_bins, D.bin0 + D.npad - b0);
+            const float x0 = fld(rec32 + (b0 >> 1) * kPairRec, min(lane, nb - 1), 0);
 #pragma unroll
             for (int a = 0; a < NSP; ++a) {
                 const int64_t sp = (int64_t)s * nsp + a;
@@ -767,9 +682,8 @@ __global__ void __launch_bounds__(kRobWarps * 32)
             }
         }
         for (int t = t0; t < t1; ++t) {
-            const TilePos pt = tpos[D.tbase + t];
-            const int64_t b0 = D.bin0 + pt.start;   // even
-            const int nb = pt.nb;
+            const int64_t b0 = D.bin0 + (int64_t)t * tile_bins;   // even
+            const int nb = (int)min((int64_t)tile_bins, D.bin0 + D.npad - b0);
             const float* tbase = rec32 + (b0 >> 1) * kPairRec;
             ff acc_ff = {0.f, 0.f};
             double far = 0.0;
@@ -943,11 +857,6 @@ __global__ void model_psd_kernel(const int32_t* __restrict__ state_ds, const Dat
     }
 }
 
-// Dynamic shared memory of the fused FP32 kernel: two staged tiles of the tile table.
-inline size_t fused_smem_bytes(const lisa_tiling& t) {
-    return 2 * (size_t)(t.tile_bins / 2) * kPairRecU * sizeof(float);
-}
-
 template <class K>
 int grid_for(K kernel, const lisa_data* d, size_t smem, int threads) {
     int per_sm = d->tiling.ctas_per_sm;
@@ -966,57 +875,28 @@ cudaError_t launch_fp32_g(const lisa_data* d, const StateParams* prm, const int3
                           const int32_t* route, const float* srec, const float2* hull, int kmax, double* partial,
                           int* err, cudaStream_t sm, bool prof) {
     auto kern = loglike_fp32_kernel<C, H, B, G>;
-    const size_t smem = fused_smem_bytes(d->tiling);
+    const size_t smem = 2 * (size_t)d->tiling.tile_bins * kRec * sizeof(float);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    kern<<<d->fgrid, kThreads32, smem, sm>>>(d->d_fitems, d->d_cta_first, d->d_tabu, d->d_thdr, d->d_tpos, prm, sstat,
-                                              nint, srec, kmax, d->nsp, d->d_ds, partial, err, d->tiling.tile_bins);
+    const int grid = grid_for(kern, d, smem, kThreads32);
+    kern<<<grid, kThreads32, smem, sm>>>(d->d_items, (int)d->n_items, d->d_rec32, prm, sstat, nint, srec, kmax,
+                                       d->nsp, d->d_ds, partial, err, d->tiling.tile_bins);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     prof_mark(d, prof, 1, sm);
     // compensated kernel for the routed states (a no-op grid when the route list is empty)
-    const int max_runs = (d->max_tiles + kRobTiles - 1) / kRobTiles;
+    int max_tiles = 1;
+    for (const auto& D : d->h_ds) max_tiles = D.ntiles > max_tiles ? D.ntiles : max_tiles;
+    const int max_runs = (max_tiles + kRobTiles - 1) / kRobTiles;
     auto rk = loglike_robust_kernel<C, H, B>;
     e = cudaFuncSetAttribute(rk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRobSmem);
     if (e != cudaSuccess) return e;
-    rk<<<d->n_sm * 8, kRobWarps * 32, kRobSmem, sm>>>(route, d->d_state_ds, d->d_ds, max_runs, d->d_rec32,
-                                                     d->d_xlo32, d->d_elllo32, prm, nint, srec, hull, d->d_tpos,
+    rk<<<d->n_sm * 8, kRobWarps * 32, kRobSmem, sm>>>(route, d->d_state_ds, d->d_ds, d->tiling.tile_bins, max_runs,
+                                                     d->d_rec32, d->d_xlo32, d->d_elllo32, prm, nint, srec, hull,
                                                      kmax, d->nsp, partial);
     e = cudaGetLastError();
     prof_mark(d, prof, 2, sm);
     return e;
-}
-
-template <int C, bool H, bool B, int G>
-int occupancy_g(const lisa_tiling& t) {
-    auto kern = loglike_fp32_kernel<C, H, B, G>;
-    const size_t smem = fused_smem_bytes(t);
-    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
-        cudaGetLastError();
-        return 1;
-    }
-    int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, kThreads32, smem) != cudaSuccess || n < 1) {
-        cudaGetLastError();
-        n = 1;
-    }
-    return n;
-}
-
-template <int C, bool H, bool B>
-int occupancy_m(const lisa_tiling& t) {
-    switch (t.group) {
-        case 2: return occupancy_g<C, H, B, 2>(t);
-        case 8: return occupancy_g<C, H, B, 8>(t);
-        default: return occupancy_g<C, H, B, 4>(t);
-    }
-}
-
-template <int C>
-int occupancy_c(int sgwb, const lisa_tiling& t) {
-    if (sgwb == 0) return occupancy_m<C, false, false>(t);
-    if (sgwb == 1) return occupancy_m<C, true, false>(t);
-    return occupancy_m<C, true, true>(t);
 }
 
 template <int C, bool H, bool B>
@@ -1064,11 +944,6 @@ cudaError_t dispatch_model(const lisa_data* d, bool fp32, const double* theta, c
 }
 
 }  // namespace
-
-int fused_ctas_per_sm(const lisa_data* d, const lisa_tiling& t) {
-    return d->C == 3 ? occupancy_c<3>(d->sgwb_model, t) : occupancy_c<2>(d->sgwb_model, t);
-}
-
 }  // namespace lisa
 
 using namespace lisa;
