@@ -535,6 +535,42 @@ def run_ours(args):
             "l2": "flushed between timed steps"}
         release(Ia)
 
+    # ---- RJ-PT sampler: A,E; 2,000 bins; 32 walkers x 4 temperatures; 200 sweeps ------------------
+    if "rjpt" in args.extras and rank == 0:
+        from paper_2507_06300_gb300 import rjpt
+        wlr = synth.workload("small_ae")
+        P_r = make_periodogram_gpu(wlr, B, torch)
+        ds_r = B.Dataset.from_workload(wlr, P_r)
+        Tr, Wr, kmax_r, n_sw = 4, 32, 4, 200
+        x_lo_r, x_hi_r = float(wlr.x_lo[0]), float(wlr.x_hi[0])
+        res = {}
+        for prec_name, prec in (("fp64", B.FP64), ("fp32", B.FP32)):
+            smp = rjpt.RJPTSampler(rjpt.GpuLikelihood(ds_r, kmax_r, precision=prec), betas=rjpt.paper_ladder(Tr),
+                                   n_walkers=Wr, n_splines=wlr.n_splines, kmax=kmax_r, k_max_rj=kmax_r, x_lo=x_lo_r,
+                                   x_hi=x_hi_r, sgwb_model=1, seed=20250706)
+            smp.init_from_prior(theta_center=wlr.theta_true[0], rel=0.01, k0=1)
+            smp.run(5, n_adapt=5)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            rec = smp.run(n_sw, n_adapt=n_sw // 2)
+            torch.cuda.synchronize()
+            el = time.perf_counter() - t0
+            acc = smp.acceptance()
+            lz, _ = rjpt.stepping_stone_log_z(smp.betas, rec["logL"].reshape(-1, Tr, Wr).transpose(0, 2, 1)
+                                              .reshape(-1, Tr))
+            res[prec_name] = {"sweeps_per_s": n_sw / el, "s_per_run": el,
+                              "likelihood_calls_per_sweep": 2,
+                              "state_bins_per_s_through_sampler": 2 * n_sw * Tr * Wr * wlr.n_bins / el,
+                              "acceptance": {k: [round(float(v), 3) for v in acc[k]] for k in acc},
+                              "cold_chain_mean_knots": float(rec["count"].mean()),
+                              "log_z_stepping_stone": lz}
+        line["rjpt"] = {"workload": "A,E; 2,000 bins 0.1-29 mHz; Nseg=16; 32 walkers x 4 temperatures "
+                                    "(paper ladder); 0-4 in-between knots per spline; 200 sweeps (100 adapting)",
+                        "what": "host-side RJ-PT sampler: MALA (gradient from lisa_psd_loglike_grad), knot birth/"
+                                "death, PT swaps; every state's log L and gradient in one library call per move",
+                        **res}
+        ds_r.close()
+
     # ---- batched datasets and the full-form workload ----------------------------------------------
     line["workloads"] = {}
     for name, desc in (("batched", "1,024 A,E,T datasets of 8k-262k bins, 4 x 4 states each, 0-30 knots; "
@@ -580,15 +616,15 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-states", type=int, default=4, help="states per reference step")
     ap.add_argument("--tiling", default="", help="tile_bins,states_per_cta,group (skips the autotuner)")
-    ap.add_argument("--extras", default="adjoint,batched,full",
-                    help="comma-separated extra workloads to measure: adjoint, batched, full")
+    ap.add_argument("--extras", default="adjoint,rjpt,batched,full",
+                    help="comma-separated extra workloads to measure: adjoint, rjpt, batched, full")
     ap.add_argument("--no-extras", action="store_true", help="measure the headline workload only")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     args.extras = set() if args.no_extras else {e.strip() for e in args.extras.split(",") if e.strip()}
-    if not args.extras <= {"adjoint", "batched", "full"}:
-        ap.error("--extras takes adjoint, batched, full")
+    if not args.extras <= {"adjoint", "rjpt", "batched", "full"}:
+        ap.error("--extras takes adjoint, rjpt, batched, full")
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)
