@@ -5,7 +5,7 @@
  *
  * The fused FP32 likelihood does no dense contraction and moves few bytes per state-bin, so its
  * roofline is set by the MUFU (special-function) pipe -- ex2, rcp, lg2 -- and by the FP32 FMA
- * pipe.  Their per-SM rates are not printed on any data sheet this library can rely on, so
+ * pipe; the FP64 paths and the FP64 data preparation are bound by the FP64 pipe.  Their per-SM rates are not printed on any data sheet this library can rely on, so
  * lisa_pipe_rates measures them: one kernel per operation runs many independent dependency
  * chains of that single instruction on every SM (8 CTAs of 256 threads per SM, 8 chains per
  * thread) and is timed with CUDA events.  lisa_data_set_profiling / lisa_data_kernel_ms time
@@ -26,11 +26,13 @@ typedef enum lisa_pipe_op {
     LISA_PIPE_LG2_EX2 = 2,  /* lg2.approx.ftz.f32 then ex2.approx.ftz.f32: chain x <- 2^-(log2 x) */
     LISA_PIPE_FFMA = 3,     /* fma.rn.f32: chain x <- x a + b */
     LISA_PIPE_FFMA2 = 4,    /* fma.rn.f32x2 (packed pair): chain x <- x a + b on both halves */
-    LISA_PIPE_N_OPS = 5
+    LISA_PIPE_DFMA = 5,     /* fma.rn.f64: chain x <- x a + b (the FP64 pipe that bounds the FP64
+                               paths and the data preparation; iters / 8 steps per chain) */
+    LISA_PIPE_N_OPS = 6
 } lisa_pipe_op;
 
 /* Measures, on the current device, the sustained rate of each lisa_pipe_op in lane operations
- * per second (one lane operation = one f32 result: an ex2, a reciprocal, a log2 or an FMA; a
+ * per second (one lane operation = one result: an ex2, a reciprocal, a log2 or an FMA; a
  * packed FMA counts two) and writes them to rates[LISA_PIPE_N_OPS] (HOST array, caller-owned).
  *  - iters: chain steps per thread (>= 16; 2048 runs each kernel for roughly a millisecond).
  *  - Each kernel is launched once untimed, then timed over `reps` (>= 1) launches on `stream`;

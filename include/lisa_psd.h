@@ -224,6 +224,33 @@ lisa_status lisa_model_psd(const lisa_data* data, const lisa_params* params,
                            const void* spline_buf_dev_fp64, size_t spline_buf_bytes, int32_t kmax,
                            double* psd_dev, lisa_stream_t stream);
 
+/* ---- data preparation ------------------------------------------------------------------------
+ * The inputs of lisa_data_create from frequency-domain data (Sec. III.D).  Frequency samples are
+ * uniform, f_k = f0 + k df (the grid of a discrete Fourier transform), and complex values are
+ * interleaved (re, im) FP64 pairs. */
+
+/* Synthetic frequency-domain data of a stationary Gaussian process with one-sided PSD S
+ * (Sec. II.D: generated directly in the frequency domain, normalised so that E|d(f)|^2 = S(f)):
+ *     d_c(f_k) = sqrt(S_c(f_k) / 2) (z_c,k,0 + i z_c,k,1).
+ * psd_dev [n_channels][n_freq] (FP64, >= 0), normal_dev [n_channels][n_freq][2] standard normal
+ * draws supplied by the caller, d_dev [n_channels][n_freq][2] out (may alias normal_dev).
+ * Errors: LISA_ERR_NULL, LISA_ERR_VALUE (n_channels < 1, n_freq < 0). */
+lisa_status lisa_fd_synthesize(const double* psd_dev, const double* normal_dev, int32_t n_channels,
+                               int64_t n_freq, double* d_dev, lisa_stream_t stream);
+
+/* Averaged periodogram (Sec. III.D): bin i holds the frequency samples
+ * [bin_offset[i], bin_offset[i+1]) and
+ *     P_c(f_i) = (1 / n_i) sum_k |d_c(f_k)|^2,   nu_i = n_i,   f_i = f0 + df (b0 + b1 - 1) / 2
+ * (the diagonal of the averaged periodogram matrix: the A, E, T covariance is diagonal), so that
+ * nu_i P_c(f_i) follows the 1x1 complex Wishart (Gamma) law of the likelihood (1).
+ * d_dev [n_channels][n_freq][2]; bin_offset_dev [n_bins + 1] (int64, non-decreasing; entries are
+ * clamped to [0, n_freq]); out: p_dev [n_channels][n_bins], f_dev [n_bins], nu_dev [n_bins]
+ * (FP64).  A bin with no samples gets P = NaN and nu = 0.  Sums are FP64 in a fixed order.
+ * Errors: LISA_ERR_NULL, LISA_ERR_VALUE (n_channels < 1, n_freq < 0, n_bins < 0, df <= 0). */
+lisa_status lisa_averaged_periodogram(const double* d_dev, int32_t n_channels, int64_t n_freq, double f0,
+                                      double df, const int64_t* bin_offset_dev, int64_t n_bins,
+                                      double* p_dev, double* f_dev, double* nu_dev, lisa_stream_t stream);
+
 /* ---- allocation-free variant ---------------------------------------------------------------
  * No counterpart in the paper: this is a deployment convenience.
  *

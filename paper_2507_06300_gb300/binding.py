@@ -62,8 +62,9 @@ class lisa_data_info(ctypes.Structure):
 EXPORTS = ["lisa_data_create", "lisa_data_destroy", "lisa_data_get_info", "lisa_data_set_tiling",
            "lisa_spline_buf_bytes", "lisa_spline_setup", "lisa_workspace_bytes", "lisa_psd_loglike",
            "lisa_psd_loglike_grad", "lisa_model_psd", "lisa_psd_loglike_noalloc", "lisa_status_string",
-           "lisa_pipe_rates", "lisa_data_set_profiling", "lisa_data_kernel_ms"]
-PIPE_OPS = ("ex2", "rcp", "lg2_ex2", "ffma", "ffma2")   # order of lisa_pipe_op
+           "lisa_pipe_rates", "lisa_data_set_profiling", "lisa_data_kernel_ms", "lisa_fd_synthesize",
+           "lisa_averaged_periodogram"]
+PIPE_OPS = ("ex2", "rcp", "lg2_ex2", "ffma", "ffma2", "dfma")   # order of lisa_pipe_op
 NOALLOC_SCRATCH_BYTES = 4 * 1024 * 1024
 
 _lock = threading.Lock()
@@ -123,6 +124,11 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         lib.lisa_data_set_profiling.restype = S
         lib.lisa_data_kernel_ms.argtypes = [_c_vp, ctypes.POINTER(ctypes.c_float)]
         lib.lisa_data_kernel_ms.restype = S
+        lib.lisa_fd_synthesize.argtypes = [_c_vp, _c_vp, _c_i32, _c_i64, _c_vp, _c_vp]
+        lib.lisa_fd_synthesize.restype = S
+        lib.lisa_averaged_periodogram.argtypes = [_c_vp, _c_i32, _c_i64, _c_dbl, _c_dbl, _c_vp, _c_i64, _c_vp, _c_vp,
+                                                  _c_vp, _c_vp]
+        lib.lisa_averaged_periodogram.restype = S
         _lib = lib
         return lib
 
@@ -341,9 +347,36 @@ class Dataset:
         return out
 
 
+def fd_synthesize(psd, normal, out=None, stream=None):
+    """``lisa_fd_synthesize``: frequency-domain data d = sqrt(S/2) (z0 + i z1).  psd [C, N] and
+    normal [C, N, 2] FP64 device tensors; returns d [C, N, 2] (FP64, interleaved re/im)."""
+    torch = _torch()
+    C, N = psd.shape
+    if out is None:
+        out = torch.empty((C, N, 2), dtype=torch.float64, device="cuda")
+    _check(load().lisa_fd_synthesize(psd.data_ptr(), normal.data_ptr(), int(C), int(N), out.data_ptr(),
+                                     _stream_handle(stream)), "lisa_fd_synthesize")
+    return out
+
+
+def averaged_periodogram(d, f0, df, bin_offset, stream=None):
+    """``lisa_averaged_periodogram``: d [C, N, 2] FP64 device tensor, bin_offset [n_bins + 1]
+    int64 device tensor; returns (P [C, n_bins], f [n_bins], nu [n_bins]) device tensors."""
+    torch = _torch()
+    C, N = d.shape[0], d.shape[1]
+    nb = bin_offset.numel() - 1
+    P = torch.empty((C, max(nb, 0)), dtype=torch.float64, device="cuda")
+    f = torch.empty(max(nb, 0), dtype=torch.float64, device="cuda")
+    nu = torch.empty(max(nb, 0), dtype=torch.float64, device="cuda")
+    _check(load().lisa_averaged_periodogram(d.data_ptr(), int(C), int(N), float(f0), float(df), bin_offset.data_ptr(),
+                                            int(nb), P.data_ptr(), f.data_ptr(), nu.data_ptr(),
+                                            _stream_handle(stream)), "lisa_averaged_periodogram")
+    return P, f, nu
+
+
 def pipe_rates(iters=2048, reps=3, stream=None) -> dict:
-    """``lisa_pipe_rates``: measured lane operations per second of the MUFU and FP32 pipes on the
-    current device, keyed by PIPE_OPS (a packed FMA counts two).  Synchronises."""
+    """``lisa_pipe_rates``: measured lane operations per second of the MUFU, FP32 and FP64 pipes on
+    the current device, keyed by PIPE_OPS (a packed FMA counts two).  Synchronises."""
     out = (_c_dbl * len(PIPE_OPS))()
     _check(load().lisa_pipe_rates(int(iters), int(reps), out, _stream_handle(stream)), "lisa_pipe_rates")
     return {k: float(out[i]) for i, k in enumerate(PIPE_OPS)}

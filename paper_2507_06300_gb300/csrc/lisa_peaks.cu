@@ -14,6 +14,21 @@ constexpr int kBlocksPerSm = 8;
 template <int OP>
 __global__ void __launch_bounds__(kBlock) pipe_rate_kernel(int iters, float a, float b, float* __restrict__ out) {
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (OP == LISA_PIPE_DFMA) {
+        double v[kChains];
+#pragma unroll
+        for (int u = 0; u < kChains; ++u) v[u] = 0.25 + 0.01 * u + 1e-6 * (g & 1023);
+        const double ad = a, bd = b;
+        for (int i = 0; i < iters; ++i) {
+#pragma unroll
+            for (int u = 0; u < kChains; ++u) v[u] = fma(v[u], ad, bd);
+        }
+        double s = 0.0;
+#pragma unroll
+        for (int u = 0; u < kChains; ++u) s += v[u];
+        out[g] = (float)s;
+        return;
+    }
     if (OP == LISA_PIPE_FFMA2) {
         float2 v[kChains];
 #pragma unroll
@@ -62,6 +77,7 @@ __global__ void __launch_bounds__(kBlock) pipe_rate_kernel(int iters, float a, f
 
 template <int OP>
 lisa_status time_op(int iters, int reps, int n_sm, float* buf, cudaStream_t sm, double* rate) {
+    if (OP == LISA_PIPE_DFMA) iters = iters / 8 > 2 ? iters / 8 : 2;   // the FP64 pipe is slow
     const unsigned blocks = (unsigned)(n_sm * kBlocksPerSm);
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess) return LISA_ERR_CUDA;
@@ -114,6 +130,7 @@ extern "C" lisa_status lisa_pipe_rates(int32_t iters, int32_t reps, double* rate
     if (st == LISA_SUCCESS) st = time_op<LISA_PIPE_LG2_EX2>(iters, reps, n_sm, buf, sm, &rates[LISA_PIPE_LG2_EX2]);
     if (st == LISA_SUCCESS) st = time_op<LISA_PIPE_FFMA>(iters, reps, n_sm, buf, sm, &rates[LISA_PIPE_FFMA]);
     if (st == LISA_SUCCESS) st = time_op<LISA_PIPE_FFMA2>(iters, reps, n_sm, buf, sm, &rates[LISA_PIPE_FFMA2]);
+    if (st == LISA_SUCCESS) st = time_op<LISA_PIPE_DFMA>(iters, reps, n_sm, buf, sm, &rates[LISA_PIPE_DFMA]);
     cudaStreamSynchronize(sm);
     cudaFree(buf);
     return st;
