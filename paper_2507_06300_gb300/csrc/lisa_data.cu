@@ -141,6 +141,8 @@ void release(lisa_data* d) {
     cudaFree(d->d_xlo32);
     cudaFree(d->d_elllo32);
     cudaFree(d->d_items);
+    cudaFree(d->d_cta_first);
+    d->d_cta_first = nullptr;
     cudaFree(d->d_adj_units);
     cudaFree(d->d_adj_prefix);
     d->d_adj_units = nullptr;
@@ -163,8 +165,11 @@ int pow2ceil(int v) {
 
 }  // namespace
 
-// Builds the work list for the current tiling: per dataset, tiles of tile_bins bins times
-// chunks of sc states (sc = min(states_per_cta, next power of two >= states of the dataset)).
+// Builds the work list for the current tiling: per dataset, chunks of sc states (sc =
+// min(states_per_cta, next power of two >= states of the dataset)) times tiles of tile_bins bins.
+// With many items per CTA the list is in (dataset, chunk, tile) order and the fused kernel gives
+// each CTA a contiguous, cost-balanced block of it, so a CTA mostly walks consecutive tiles of
+// the same states; otherwise it is in (dataset, tile, chunk) order and CTAs stride over it.
 lisa_status rebuild_work(lisa_data* d) {
     const lisa_tiling& t = d->tiling;
     std::vector<WorkItem> items;
@@ -177,10 +182,10 @@ lisa_status rebuild_work(lisa_data* d) {
         if (D.ns == 0 || D.npad == 0) continue;
         int sc = std::min(t.states_per_cta, pow2ceil(D.ns));
         sc = std::max(sc, 1);
-        for (int32_t tile = 0; tile < D.ntiles; ++tile) {
-            int64_t b0 = D.bin0 + (int64_t)tile * t.tile_bins;
-            int32_t nb = (int32_t)std::min<int64_t>(t.tile_bins, D.bin0 + D.npad - b0);
-            for (int32_t s = 0; s < D.ns; s += sc) {
+        for (int32_t s = 0; s < D.ns; s += sc) {
+            for (int32_t tile = 0; tile < D.ntiles; ++tile) {
+                int64_t b0 = D.bin0 + (int64_t)tile * t.tile_bins;
+                int32_t nb = (int32_t)std::min<int64_t>(t.tile_bins, D.bin0 + D.npad - b0);
                 WorkItem w;
                 w.bin0 = b0;
                 w.nb = nb;
@@ -193,18 +198,69 @@ lisa_status rebuild_work(lisa_data* d) {
             }
         }
     }
-    // Larger tiles first so that the persistent grid's static schedule ends evenly.
-    std::stable_sort(items.begin(), items.end(), [](const WorkItem& a, const WorkItem& b) {
-        return (int64_t)a.nb * a.ns > (int64_t)b.nb * b.ns;
-    });
     d->n_partials = pbase;
+    const int occ = t.ctas_per_sm > 0 ? t.ctas_per_sm : fused_ctas_per_sm(d, t);
+    const int grid = std::max(1, d->n_sm * std::max(occ, 1));
+    // contiguous blocks pay off when a CTA has many items and each thread takes few bins from an
+    // item (small state chunks: the per-item interval search dominates); with a few items per CTA
+    // or wide items, striding over a (dataset, tile,
+    // chunk)-ordered list mixes tiles from the whole band into every CTA, which balances better
+    // than cutting a handful of tiles by cost
+    double thread_bins = 0.0, weight = 0.0;   // bins one thread takes from an item, state-weighted
+    for (const WorkItem& w : items) {
+        thread_bins += (double)w.nb * w.sc / kThreads32 * w.ns;
+        weight += w.ns;
+    }
+    d->fblocks = items.size() >= (size_t)kBlockItemsPerCta * (size_t)grid &&
+                 thread_bins < kBlockThreadBins * weight;
+    if (!d->fblocks) {
+        // (dataset, tile, chunk) order, larger items first so that the static stride ends evenly
+        std::stable_sort(items.begin(), items.end(), [](const WorkItem& a, const WorkItem& b) {
+            if (a.ds != b.ds) return a.ds < b.ds;
+            if (a.tile != b.tile) return a.tile < b.tile;
+            return a.s0 < b.s0;
+        });
+        std::stable_sort(items.begin(), items.end(), [](const WorkItem& a, const WorkItem& b) {
+            return (int64_t)a.nb * a.ns > (int64_t)b.nb * b.ns;
+        });
+    }
+    // contiguous blocks of the work list for the fused kernel's persistent grid, cut so that every
+    // CTA gets the same knot-aware cost (item boundaries at cost midpoints); used when there are at
+    // least kBlockItemsPerCta items per CTA
+    auto x_at = [&](int k, int64_t b) {   // log10 f of bin b of dataset k (b a multiple of
+        const double* xs = d->h_xs.data() + d->h_xs_off[k];   // kXsStride, or past the end)
+        const int64_t nxs = d->h_xs_off[k + 1] - d->h_xs_off[k];
+        const int64_t j = b / kXsStride;
+        return j < nxs - 1 ? xs[j] : xs[nxs - 1];
+    };
+    std::vector<double> pre(items.size() + 1, 0.0);
+    for (size_t q = 0; q < items.size(); ++q) {
+        const WorkItem& w = items[q];
+        const DatasetDev& D = d->h_ds[w.ds];
+        const int64_t a = w.bin0 - D.bin0, e = a + w.nb;
+        const double dx = D.nbins > 0 ? x_at(w.ds, e) - x_at(w.ds, a) : 0.0;
+        pre[q + 1] = pre[q] + ((double)w.nb + kKnotBinsPerDecade * dx) * (double)w.ns;
+    }
+    std::vector<int32_t> cta_first((size_t)grid + 1, 0);
+    size_t q = 0;
+    for (int b = 1; b <= grid; ++b) {
+        const double target = pre.back() * (double)b / (double)grid;
+        while (q < items.size() && 0.5 * (pre[q] + pre[q + 1]) < target) ++q;
+        cta_first[b] = (int32_t)(b == grid ? items.size() : q);
+    }
+    d->fgrid = grid;
     cudaFree(d->d_items);
+    cudaFree(d->d_cta_first);
     d->d_items = nullptr;
+    d->d_cta_first = nullptr;
     d->n_items = (int64_t)items.size();
-    lisa_status st = dev_alloc(&d->d_items, items.size());
-    if (st) return st;
+    lisa_status st;
+    if ((st = dev_alloc(&d->d_items, items.size())) || (st = dev_alloc(&d->d_cta_first, cta_first.size())))
+        return st;
     if (cudaMemcpy(d->d_items, items.data(), items.size() * sizeof(WorkItem), cudaMemcpyHostToDevice) !=
-        cudaSuccess)
+            cudaSuccess ||
+        cudaMemcpy(d->d_cta_first, cta_first.data(), cta_first.size() * sizeof(int32_t), cudaMemcpyHostToDevice) !=
+            cudaSuccess)
         return LISA_ERR_CUDA;
     // device copy of the dataset table (ntiles / pbase changed)
     if (cudaMemcpy(d->d_ds, d->h_ds.data(), d->h_ds.size() * sizeof(DatasetDev),
@@ -282,6 +338,13 @@ lisa_status lisa_data_create(const lisa_data_desc* desc, lisa_stream_t stream, l
     d->n_bins = N;
     d->n_states = S;
     d->h_bin_off.assign(q.bin_offset, q.bin_offset + D + 1);
+    for (int k = 0; k < D; ++k) {
+        d->h_xs_off.push_back((int64_t)d->h_xs.size());
+        const int64_t n = q.bin_offset[k + 1] - q.bin_offset[k];
+        for (int64_t i = 0; i < n; i += kXsStride) d->h_xs.push_back(std::log10(q.freq[q.bin_offset[k] + i]));
+        if (n > 0) d->h_xs.push_back(std::log10(q.freq[q.bin_offset[k] + n - 1]));
+    }
+    d->h_xs_off.push_back((int64_t)d->h_xs.size());
     d->h_state_off.assign(q.state_offset, q.state_offset + D + 1);
     d->h_ds.resize(D);
     std::vector<int32_t> state_ds((size_t)S);

@@ -46,6 +46,14 @@ constexpr int kStatusNonfinite = LISA_STATE_NONFINITE;
 constexpr unsigned kWaitLimit = 1u << 20;   // bounded spin on an mbarrier (then give up)
 constexpr int kMaxTileBins = 2048;          // 2 staged tiles x 48 B/bin must fit in 227 KB
 constexpr int kAdjBins = 2048;              // bins per (state, range) in the adjoint
+// Work balance of the fused kernel: an item (a tile of bins x a chunk of states) costs
+// (bins + kKnotBinsPerDecade x its width in log10 f) per state.  The second term stands for the
+// interval advances: knots are drawn uniformly in log10 f, so the low-frequency tiles (few bins,
+// wide in log10 f) hold most of them, and each advance stalls its warp on record loads.
+constexpr double kKnotBinsPerDecade = 2500.0;
+constexpr int kXsStride = 32;               // bins between the host copies of log10 f
+constexpr int kBlockItemsPerCta = 16;       // contiguous blocks need this many items per CTA
+constexpr double kBlockThreadBins = 128.0;  // and fewer bins per thread and item than this
 
 // One unit of work of the fused kernels: a tile of bins of one dataset and a chunk of its
 // states.  Threads map to (state lane, bin sub-range): lane = tid % sc, range = tid / sc.
@@ -91,6 +99,10 @@ struct lisa_data {
     int64_t n_bins = 0, n_states = 0;
     int64_t n_pad = 0;               // padded bin count of the tables
     std::vector<int64_t> h_bin_off, h_state_off;
+    // log10 f of every kXsStride-th bin of each dataset and of its last bin (host copy for the
+    // work balance), dataset k's entries from h_xs_off[k]
+    std::vector<double> h_xs;
+    std::vector<int64_t> h_xs_off;
     std::vector<lisa::DatasetDev> h_ds;
     lisa::DatasetDev* d_ds = nullptr;
     int32_t* d_state_ds = nullptr;   // [n_states] dataset of each state
@@ -101,6 +113,9 @@ struct lisa_data {
     float* d_elllo32 = nullptr;      // [n_pad] low part of ell = log2(f / f_ref)
     lisa_tiling tiling{};
     lisa::WorkItem* d_items = nullptr;
+    int32_t* d_cta_first = nullptr;  // fused kernel: first item of each CTA (fgrid + 1 entries)
+    int32_t fgrid = 0;               // CTAs of the fused FP32 launch
+    bool fblocks = false;            // contiguous cost-balanced blocks (else every fgrid-th item)
     lisa::AdjUnit* d_adj_units = nullptr;
     int64_t n_adj_units = 0;
     int64_t* d_adj_prefix = nullptr; // [n_states] adjoint ranges of all earlier states
@@ -161,6 +176,8 @@ inline size_t ws_fwd_bytes(const lisa_data* d) {
 size_t grad_extra_bytes(const lisa_data* d, int kmax);
 
 lisa_status rebuild_work(lisa_data* d);
+// Resident CTAs per SM of the fused FP32 kernel under tiling t (its registers and shared memory).
+int fused_ctas_per_sm(const lisa_data* d, const lisa_tiling& t);
 
 // Per-kernel timing (lisa_data_set_profiling): whether this call records events (profiling on
 // and the stream not capturing), and an event record at point k of the call.

@@ -280,7 +280,8 @@ __device__ __forceinline__ float2 pair_term32(const float4 q0, const float4* __r
 
 template <int C, bool HAS_H, bool BROKEN, int G>
 __global__ void __launch_bounds__(kThreads32, G == 8 ? 5 : 6)
-    loglike_fp32_kernel(const WorkItem* __restrict__ items, int n_items, const float* __restrict__ rec32,
+    loglike_fp32_kernel(const WorkItem* __restrict__ items, int n_items, const int32_t* __restrict__ cta_first,
+                        const float* __restrict__ rec32,
                         const StateParams* __restrict__ prm, const int32_t* __restrict__ sstat,
                         const int32_t* __restrict__ nint, const float* __restrict__ srec, int kmax, int nsp,
                         const DatasetDev* __restrict__ ds, double* __restrict__ partial, int* __restrict__ err,
@@ -299,17 +300,38 @@ __global__ void __launch_bounds__(kThreads32, G == 8 ? 5 : 6)
     }
     __syncthreads();
     unsigned phase0 = 0, phase1 = 0;
-    int it = blockIdx.x;
-    if (it < n_items && tid == 0) {
+    // the CTA's items: with cta_first, a contiguous block of the (dataset, state chunk,
+    // tile)-ordered work list, cut by the host so that every CTA gets the same knot-aware cost
+    // (consecutive items are mostly consecutive tiles of the same states, whose intervals carry
+    // over); without it (few items per CTA), every gridDim.x-th item, which mixes tiles from the
+    // whole band into each CTA
+    const int step = cta_first ? 1 : (int)gridDim.x;
+    int it = cta_first ? cta_first[blockIdx.x] : (int)blockIdx.x;
+    const int i_end = cta_first ? cta_first[blockIdx.x + 1] : n_items;
+    if (it < i_end && tid == 0) {
         const WorkItem w = items[it];
         const unsigned bytes = (unsigned)w.nb * kRec * sizeof(float);
         mbar_expect_tx(&bars[0], bytes);
         bulk_copy_g2s(sbuf0, rec32 + (w.bin0 >> 1) * kPairRec, bytes, &bars[0]);
     }
-    for (int k = 0; it < n_items; it += gridDim.x, ++k) {
+    // per spline: right knot of the current interval, its index, and the interval's cubic
+    // duplicated into register pairs (the scalar path reads the .x halves); xmin = the nearest
+    // right knot.  An ill-conditioned interval (T > kRobustT, routed states only) is loaded as the
+    // zero cubic, which keeps its bins' arithmetic benign, and sets its bit in hm; keep2 = 0 while
+    // any bit is set, 1 otherwise, and scales each pair's contribution.  All of it carries over
+    // to the next item when that is the next tile of the same state chunk (bins only move right).
+    float xr[NSP];
+    int jj[NSP];
+    Iv2 iv2[NSP];
+    float xmin = INFINITY;
+    unsigned hm = 0;
+    float2 keep2 = make_float2(1.f, 1.f);
+    bool located = false;
+    int prev_ds = -1, prev_s0 = -1, prev_tile = -2;
+    for (int k = 0; it < i_end; it += step, ++k) {
         const int b = k & 1;
-        const int nxt = it + gridDim.x;
-        if (nxt < n_items && tid == 0) {
+        const int nxt = it + step;
+        if (nxt < i_end && tid == 0) {
             const WorkItem w = items[nxt];
             const unsigned bytes = (unsigned)w.nb * kRec * sizeof(float);
             fence_proxy_async();
@@ -327,6 +349,10 @@ __global__ void __launch_bounds__(kThreads32, G == 8 ? 5 : 6)
         const float* tb = b ? sbuf1 : sbuf0;
         const float4* tb4 = reinterpret_cast<const float4*>(tb);
 
+        if (!(w.ds == prev_ds && w.s0 == prev_s0 && w.tile == prev_tile + 1)) located = false;
+        prev_ds = w.ds;
+        prev_s0 = w.s0;
+        prev_tile = w.tile;
         const int sc = w.sc;
         const int R = kThreads32 / sc;
         const int ls = tid & (sc - 1);
@@ -344,18 +370,6 @@ __global__ void __launch_bounds__(kThreads32, G == 8 ? 5 : 6)
                 const float ao2 = q0.x, at2 = q0.y, Af = HAS_H ? q0.z : 0.f, n1 = q0.w;
                 const float n2 = BROKEN ? __ldg(&prm[s].n2) : n1;
                 const float2 ao2_2 = make_float2(ao2, ao2), at2_2 = make_float2(at2, at2), Af2 = make_float2(Af, Af);
-                // per spline: right knot of the current interval, its index, and the interval's
-                // cubic duplicated into register pairs (the scalar path reads the .x halves);
-                // xmin = the nearest right knot.  An ill-conditioned interval (T > kRobustT, routed
-                // states only) is loaded as the zero cubic, which keeps its bins' arithmetic benign,
-                // and sets its bit in hm; keep2 = 0 while any bit is set, 1 otherwise, and scales
-                // each pair's contribution.
-                float xr[NSP];
-                int jj[NSP];
-                Iv2 iv2[NSP];
-                float xmin = INFINITY;
-                unsigned hm = 0;
-                float2 keep2 = make_float2(1.f, 1.f);
                 const int64_t sp0 = (int64_t)s * nsp;
                 auto reload = [&](int a) {
                     const float* rr = srec + ((sp0 + a) * (int64_t)(kmax + 1) + jj[a]) * kSplineRec32;
@@ -407,8 +421,11 @@ __global__ void __launch_bounds__(kThreads32, G == 8 ? 5 : 6)
                     const float v = bin_term32p<C, HAS_H, BROKEN>(tb, i, iv2, ao2, at2, n1, n2, Af);
                     return hm ? 0.f : v;
                 };
-                locate(fld(tb, 2 * plo, 0));
-                xmin = nearest();
+                if (!located) {
+                    locate(fld(tb, 2 * plo, 0));
+                    xmin = nearest();
+                    located = true;
+                }
                 int ip = plo;
                 while (ip < phi) {
                     const int pc0 = ip;
@@ -878,9 +895,9 @@ cudaError_t launch_fp32_g(const lisa_data* d, const StateParams* prm, const int3
     const size_t smem = 2 * (size_t)d->tiling.tile_bins * kRec * sizeof(float);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    const int grid = grid_for(kern, d, smem, kThreads32);
-    kern<<<grid, kThreads32, smem, sm>>>(d->d_items, (int)d->n_items, d->d_rec32, prm, sstat, nint, srec, kmax,
-                                       d->nsp, d->d_ds, partial, err, d->tiling.tile_bins);
+    kern<<<d->fgrid, kThreads32, smem, sm>>>(d->d_items, (int)d->n_items, d->fblocks ? d->d_cta_first : nullptr,
+                                              d->d_rec32, prm, sstat, nint, srec, kmax, d->nsp, d->d_ds, partial, err,
+                                              d->tiling.tile_bins);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     prof_mark(d, prof, 1, sm);
@@ -897,6 +914,38 @@ cudaError_t launch_fp32_g(const lisa_data* d, const StateParams* prm, const int3
     e = cudaGetLastError();
     prof_mark(d, prof, 2, sm);
     return e;
+}
+
+template <int C, bool H, bool B, int G>
+int occupancy_g(const lisa_tiling& t) {
+    auto kern = loglike_fp32_kernel<C, H, B, G>;
+    const size_t smem = 2 * (size_t)t.tile_bins * kRec * sizeof(float);
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+        cudaGetLastError();
+        return 1;
+    }
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, kThreads32, smem) != cudaSuccess || n < 1) {
+        cudaGetLastError();
+        n = 1;
+    }
+    return n;
+}
+
+template <int C, bool H, bool B>
+int occupancy_m(const lisa_tiling& t) {
+    switch (t.group) {
+        case 2: return occupancy_g<C, H, B, 2>(t);
+        case 8: return occupancy_g<C, H, B, 8>(t);
+        default: return occupancy_g<C, H, B, 4>(t);
+    }
+}
+
+template <int C>
+int occupancy_c(int sgwb, const lisa_tiling& t) {
+    if (sgwb == 0) return occupancy_m<C, false, false>(t);
+    if (sgwb == 1) return occupancy_m<C, true, false>(t);
+    return occupancy_m<C, true, true>(t);
 }
 
 template <int C, bool H, bool B>
@@ -944,6 +993,11 @@ cudaError_t dispatch_model(const lisa_data* d, bool fp32, const double* theta, c
 }
 
 }  // namespace
+
+int fused_ctas_per_sm(const lisa_data* d, const lisa_tiling& t) {
+    return d->C == 3 ? occupancy_c<3>(d->sgwb_model, t) : occupancy_c<2>(d->sgwb_model, t);
+}
+
 }  // namespace lisa
 
 using namespace lisa;
