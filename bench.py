@@ -44,10 +44,11 @@ FP32_PER_STATE_BIN = 38
 TABLE_BYTES_PER_BIN = 12 * 4          # FP32 bin table: x, ell, nu, 3 x (G_oms, G_tm, G_h)
 # The FP32 adjoint kernel per state-bin, as implemented: per spline a compensated t (two-sum and
 # low parts, 9) and Horner (3) = 48; SGWB exponent and amplitude 2; per channel noise 2, SGWB 1,
-# PSD 1, g = nu r (r - 1) 3, forward term 2, template sums 5, spline signal 3 = 51; SGWB signal,
-# log L and template accumulators 6; moments 6 per spline = 24.  MUFU: 4 ex2, 3 rcp, 3 lg2.
-ADJ_FP32_PER_STATE_BIN = 131
-ADJ_MUFU = (4, 3, 3)
+# PSD 1, g = nu r (r - 1) 3, forward term and channel product 2, template sums 5, spline signal 3
+# = 51; the log of the product 1; SGWB signal, log L and template accumulators 6; moments 6 per
+# spline = 24.  MUFU: 4 ex2, 3 rcp, 1 lg2 (of the channel product).
+ADJ_FP32_PER_STATE_BIN = 132
+ADJ_MUFU = (4, 3, 1)
 SPLINE_RECORD_BYTES = 64
 N_SM = 152
 
@@ -527,8 +528,8 @@ def run_ours(args):
             "roofline": {"bound": "alu", "pipe": "FP32 (FMA pipe)" if ceil_fp32 <= ceil_mufu else "MUFU (XU pipe)",
                          "kernel": "adjoint_fp32_kernel",
                          "achieved": ADJ_FP32_PER_STATE_BIN * adj_rate / 1e9 if ceil_fp32 <= ceil_mufu
-                         else 10 * adj_rate / 1e9,
-                         "peak": fp32_rate / 1e9 if ceil_fp32 <= ceil_mufu else 10 * ceil_mufu / 1e9,
+                         else sum(ADJ_MUFU) * adj_rate / 1e9,
+                         "peak": fp32_rate / 1e9 if ceil_fp32 <= ceil_mufu else sum(ADJ_MUFU) * ceil_mufu / 1e9,
                          "unit": "Gop/s", "frac": adj_rate / min(ceil_fp32, ceil_mufu),
                          "ops_per_state_bin": ADJ_FP32_PER_STATE_BIN,
                          "ceilings_state_bins_per_s": {"fp32": ceil_fp32, "mufu": ceil_mufu}},

@@ -54,13 +54,19 @@ struct AdjIv {
 };
 
 template <int C, bool HAS_H, bool BROKEN>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(128, 4)
     adjoint_fp32_kernel(const AdjUnit* __restrict__ units, int64_t n_units, const DatasetDev* __restrict__ ds,
                         const float* __restrict__ rec32, const float* __restrict__ xlo32,
                         const double* __restrict__ theta, const int32_t* __restrict__ sstat,
                         const int32_t* __restrict__ nint, const float* __restrict__ srec, int kmax, int nsp,
                         const int64_t* __restrict__ prefix, double* __restrict__ scal, double* __restrict__ mom) {
     constexpr int NSP = C + (HAS_H ? 1 : 0);
+    // float-float running sums (moments and template sums), touched once per 16 bins and at
+    // interval ends: kept in shared memory, [slot][thread], so that the per-bin loop has room
+    // for four CTAs per SM
+    __shared__ float2 s_am[NSP * 4][128];
+    __shared__ float2 s_as[6][128];
+    const int tid = threadIdx.x;
     const int lane = threadIdx.x & 31;
     const int64_t wg = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -78,18 +84,15 @@ __global__ void __launch_bounds__(128)
         const float* tb = rec32 + (b0 >> 1) * kPairRec;
         const int64_t pre = prefix[s];
         AdjIv iv[NSP];
-        const float* base[NSP];
-        int last[NSP];
+        auto base = [&](int a) { return srec + ((int64_t)s * nsp + a) * (int64_t)(kmax + 1) * kSplineRec32; };
         const float x0 = fld(tb, 0, 0);
 #pragma unroll
         for (int a = 0; a < NSP; ++a) {
             const int64_t sp = (int64_t)s * nsp + a;
-            base[a] = srec + sp * (int64_t)(kmax + 1) * kSplineRec32;
-            last[a] = nint[sp] - 1;
-            iv[a].j = find_interval<float, kSplineRec32, 6>(base[a], nint[sp], x0);
+            iv[a].j = find_interval<float, kSplineRec32, 6>(base(a), nint[sp], x0);
         }
         auto load = [&](int a) {
-            const float* r = base[a] + (size_t)iv[a].j * kSplineRec32;
+            const float* r = base(a) + (size_t)iv[a].j * kSplineRec32;
             iv[a].xr = __ldg(r + 0);
             iv[a].xo = __ldg(r + 1);
             iv[a].c0 = __ldg(r + 2);
@@ -101,27 +104,27 @@ __global__ void __launch_bounds__(128)
         };
 #pragma unroll
         for (int a = 0; a < NSP; ++a) load(a);
-        // accumulators: chunk sums in FP32, running sums in float-float
+        // accumulators: chunk sums in FP32 (registers), running sums in float-float (shared)
         float cm[NSP][4];
-        ff am[NSP][4];
         float cs[6];
-        ff as[6];
 #pragma unroll
         for (int a = 0; a < NSP; ++a)
 #pragma unroll
             for (int p = 0; p < 4; ++p) {
                 cm[a][p] = 0.f;
-                am[a][p] = ff{0.f, 0.f};
+                s_am[4 * a + p][tid] = make_float2(0.f, 0.f);
             }
 #pragma unroll
         for (int k = 0; k < 6; ++k) {
             cs[k] = 0.f;
-            as[k] = ff{0.f, 0.f};
+            s_as[k][tid] = make_float2(0.f, 0.f);
         }
         auto flush_mom = [&](int a) {
 #pragma unroll
             for (int p = 0; p < 4; ++p) {
-                am[a][p] = ff_add(am[a][p], ff{cm[a][p], 0.f});
+                const float2 v = s_am[4 * a + p][tid];
+                const ff r = ff_add(ff{v.x, v.y}, ff{cm[a][p], 0.f});
+                s_am[4 * a + p][tid] = make_float2(r.hi, r.lo);
                 cm[a][p] = 0.f;
             }
         };
@@ -130,17 +133,19 @@ __global__ void __launch_bounds__(128)
             double* row = mom_row(mom, pre, s, a, nsp, kmax, D.nranges) + 4 * (int64_t)(U.rho + iv[a].j);
 #pragma unroll
             for (int p = 0; p < 4; ++p) {
-                row[p] = (double)am[a][p].hi + (double)am[a][p].lo;
-                am[a][p] = ff{0.f, 0.f};
+                const float2 v = s_am[4 * a + p][tid];
+                row[p] = (double)v.x + (double)v.y;
+                s_am[4 * a + p][tid] = make_float2(0.f, 0.f);
             }
         };
-        for (int i = 0; i < nb; ++i) {
-            const float x = fld(tb, i, 0), ell = fld(tb, i, 1), nu = fld(tb, i, 2);
-            const float x_lo = __ldg(xlo32 + b0 + i);
+        // one bin: fields f[0..11] of the pair-block table (x, ell, nu, G_oms, G_tm, G_h) and the
+        // low part of x
+        auto bin = [&](int i, const float* f, float x_lo) {
+            const float x = f[0], ell = f[1], nu = f[2];
             float P[NSP], tl[NSP];
 #pragma unroll
             for (int a = 0; a < NSP; ++a) {
-                while (x >= iv[a].xr && iv[a].j < last[a]) {
+                while (x >= iv[a].xr && iv[a].j < __ldg(nint + (int64_t)s * nsp + a) - 1) {
                     store_mom(a);
                     ++iv[a].j;
                     load(a);
@@ -157,22 +162,31 @@ __global__ void __launch_bounds__(128)
                 const float sl = BROKEN ? (ell < 0.f ? n1 : n2) : n1;
                 eh = Af * ex2_approx(fmaf(sl, ell, P[C]));
             }
-            float fwd = -(float)C, To = 0.f, Tt = 0.f, H = 0.f;
-            float q[NSP];
+            float fwd = -(float)C, To = 0.f, Tt = 0.f, H = 0.f, prod = 1.f;
+            float q[NSP], S[C];
 #pragma unroll
             for (int c = 0; c < C; ++c) {
-                const float go = fld(tb, i, 3 + c), gt = fld(tb, i, 6 + c);
+                const float go = f[3 + c], gt = f[6 + c];
                 const float E = ex2_approx(P[c]);
                 const float N = fmaf(ao2, go, at2 * gt);
-                const float Eh = HAS_H ? eh * fld(tb, i, 9 + c) : 0.f;
+                const float Eh = HAS_H ? eh * f[9 + c] : 0.f;
                 const float Sc = fmaf(E, N, Eh);
                 const float r = rcp_approx(Sc);
                 const float g = nu * r * (r - 1.f);
-                fwd += r + (float)kLn2 * lg2_approx(Sc);
+                fwd += r;
+                prod *= Sc;
+                S[c] = Sc;
                 To = fmaf(g * go, E, To);
                 Tt = fmaf(g * gt, E, Tt);
                 H = fmaf(g, Eh, H);
                 q[c] = (float)kLn10 * g * N * E;
+            }
+            // sum_c ln S_c from one log2 of the channel product, per channel outside a safe range
+            if (prod > 1e-30f && prod < 1e30f) {
+                fwd = fmaf((float)kLn2, lg2_approx(prod), fwd);
+            } else {
+#pragma unroll
+                for (int c = 0; c < C; ++c) fwd = fmaf((float)kLn2, lg2_approx(S[c]), fwd);
             }
             if (HAS_H) q[C] = (float)kLn10 * H;
             cs[0] = fmaf(nu, fwd, cs[0]);
@@ -196,18 +210,40 @@ __global__ void __launch_bounds__(128)
                 for (int a = 0; a < NSP; ++a) flush_mom(a);
 #pragma unroll
                 for (int k = 0; k < 6; ++k) {
-                    as[k] = ff_add(as[k], ff{cs[k], 0.f});
+                    const float2 v = s_as[k][tid];
+                    const ff r = ff_add(ff{v.x, v.y}, ff{cs[k], 0.f});
+                    s_as[k][tid] = make_float2(r.hi, r.lo);
                     cs[k] = 0.f;
                 }
             }
+        };
+        // the range's bins two at a time: one pair block of the table is six 16-byte loads (the
+        // same address in every lane of the warp), the low parts of x one 8-byte load
+        const float4* tb4 = reinterpret_cast<const float4*>(tb);
+        const float2* xl2 = reinterpret_cast<const float2*>(xlo32 + b0);
+        for (int ip = 0; ip < (nb >> 1); ++ip) {
+            float4 q4[kPairRec / 4];
+#pragma unroll
+            for (int k = 0; k < kPairRec / 4; ++k) q4[k] = __ldg(tb4 + ip * (kPairRec / 4) + k);
+            const float2 xl = __ldg(xl2 + ip);
+            const float* fq = reinterpret_cast<const float*>(q4);
+            float f0[kRec], f1[kRec];
+#pragma unroll
+            for (int k = 0; k < kRec; ++k) {
+                f0[k] = fq[2 * k];
+                f1[k] = fq[2 * k + 1];
+            }
+            bin(2 * ip, f0, xl.x);
+            bin(2 * ip + 1, f1, xl.y);
         }
 #pragma unroll
         for (int a = 0; a < NSP; ++a) store_mom(a);
         double* sc = scal + 6 * (pre + U.rho);
 #pragma unroll
         for (int k = 0; k < 6; ++k) {
-            as[k] = ff_add(as[k], ff{cs[k], 0.f});
-            sc[k] = (double)as[k].hi + (double)as[k].lo;
+            const float2 v = s_as[k][tid];
+            const ff r = ff_add(ff{v.x, v.y}, ff{cs[k], 0.f});
+            sc[k] = (double)r.hi + (double)r.lo;
         }
     }
 }
