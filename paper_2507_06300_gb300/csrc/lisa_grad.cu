@@ -346,6 +346,7 @@ __global__ void __launch_bounds__(128)
 }
 
 // ---- epilogue: one warp per state, FP64 ----------------------------------------------------------
+constexpr int kEpiRanges = 256;   // adjoint ranges whose bounds the epilogue stages (524,288 bins)
 
 // d s_k / d m_{k+delta}, delta = -2..1, for the Akima slope at knot k (Appendix A rules,
 // including the ends), returned in d[0..3] = delta -2, -1, 0, +1.  mm2..mp1 = m_{k-2}..m_{k+1}.
@@ -420,6 +421,9 @@ __global__ void __launch_bounds__(128)
                             double* __restrict__ out_logL, double* __restrict__ grad) {
     __shared__ double sX[4][64];
     __shared__ double sY[4][64];
+    // first and last bin's x of each adjoint range of the warp's dataset (the same for all its
+    // states and splines), for datasets of up to kEpiRanges ranges
+    __shared__ double sRf[4][kEpiRanges], sRl[4][kEpiRanges];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int s = blockIdx.x * 4 + warp;
     if (s >= S) return;
@@ -444,6 +448,24 @@ __global__ void __launch_bounds__(128)
     const bool finite = isfinite(L);
     if (lane == 0) out_logL[s] = finite ? L : -INFINITY;
     if (!finite) return;   // gradient stays zero
+    // range bounds: in shared memory when they fit, else read per range below
+    const bool staged = nr <= kEpiRanges;
+    auto range_x = [&](int rho, double& xf, double& xlb) {
+        const int64_t b0 = D.bin0 + (int64_t)rho * kAdjBins;
+        const int nb = (int)min((int64_t)kAdjBins, D.bin0 + D.npad - b0);
+        if (fp32) {
+            const float* tb = rec32 + (b0 >> 1) * kPairRec;
+            xf = (double)fld(tb, 0, 0);
+            xlb = (double)fld(tb, nb - 1, 0);
+        } else {
+            xf = rec64[b0 * kRec];
+            xlb = rec64[(b0 + nb - 1) * kRec];
+        }
+    };
+    if (staged) {
+        for (int rho = lane; rho < nr; rho += 32) range_x(rho, sRf[warp][rho], sRl[warp][rho]);
+        __syncwarp();
+    }
     const double* th = theta + (size_t)s * LISA_N_THETA;
     if (lane == 0) {
         gs[0] = 2.0 * th[0] * v[1];
@@ -480,21 +502,36 @@ __global__ void __launch_bounds__(128)
                 lo_b = r[0];
                 hi_b = r[1];
             }
-            for (int rho = 0; rho < nr; ++rho) {
-                const int64_t b0 = D.bin0 + (int64_t)rho * kAdjBins;
-                const int nb = (int)min((int64_t)kAdjBins, D.bin0 + D.npad - b0);
-                double xf, xlb;
-                if (fp32) {
-                    const float* tb = rec32 + (b0 >> 1) * kPairRec;
-                    xf = (double)fld(tb, 0, 0);
-                    xlb = (double)fld(tb, nb - 1, 0);
-                } else {
-                    xf = rec64[b0 * kRec];
-                    xlb = rec64[(b0 + nb - 1) * kRec];
+            if (staged) {
+                // the ranges that touch the interval are the contiguous span [r0, r1] (bins are
+                // sorted): first range whose last bin reaches lo_b, last one that starts below hi_b
+                int r0 = 0, r1 = nr - 1;
+                if (jj != 0) {
+                    int lo = 0, hi = nr;
+                    while (lo < hi) {
+                        const int mid = (lo + hi) >> 1;
+                        if (sRl[warp][mid] >= lo_b) hi = mid; else lo = mid + 1;
+                    }
+                    r0 = lo;
                 }
-                const bool touches = (jj == 0 || xlb >= lo_b) && (jj == nint - 1 || xf < hi_b);
-                if (touches)
+                if (jj != nint - 1) {
+                    int lo = 0, hi = nr;
+                    while (lo < hi) {
+                        const int mid = (lo + hi) >> 1;
+                        if (sRf[warp][mid] < hi_b) lo = mid + 1; else hi = mid;
+                    }
+                    r1 = lo - 1;
+                }
+                for (int rho = r0; rho <= r1; ++rho)
                     for (int p = 0; p < 4; ++p) M[q][p] += row[4 * (int64_t)(rho + jj) + p];
+            } else {
+                for (int rho = 0; rho < nr; ++rho) {
+                    double xf, xlb;
+                    range_x(rho, xf, xlb);
+                    const bool touches = (jj == 0 || xlb >= lo_b) && (jj == nint - 1 || xf < hi_b);
+                    if (touches)
+                        for (int p = 0; p < 4; ++p) M[q][p] += row[4 * (int64_t)(rho + jj) + p];
+                }
             }
             if (fp32) {
                 // moments about the FP32 midpoint xo -> about the left knot x_j:  t = u + mo
