@@ -53,7 +53,10 @@ struct AdjIv {
     int j;
 };
 
-template <int C, bool HAS_H, bool BROKEN>
+// EXACT_T: every bin lies inside the knot band and the band satisfies |x_lo| <= 2.9 |x_hi| (same
+// sign), so that within any interval |x - x_o| <= 2 |x| and |x_o| <= 2 |x| and the FP32 difference
+// x - x_o is exact (Sterbenz); t then needs no two-sum (the same value as the compensated form).
+template <int C, bool HAS_H, bool BROKEN, bool EXACT_T>
 __global__ void __launch_bounds__(128, 4)
     adjoint_fp32_kernel(const AdjUnit* __restrict__ units, int64_t n_units, const DatasetDev* __restrict__ ds,
                         const float* __restrict__ rec32, const float* __restrict__ xlo32,
@@ -152,8 +155,13 @@ __global__ void __launch_bounds__(128, 4)
                 }
                 // t = x - x_o from the FP64 values (hi + lo parts): the position derivatives are
                 // sensitive to the ~1e-7 rounding of FP32 positions
-                const ff tt = two_sum(x, -iv[a].xo);
-                const float t = tt.hi + (tt.lo + (x_lo - iv[a].xo_lo));
+                float t;
+                if (EXACT_T) {
+                    t = (x - iv[a].xo) + (x_lo - iv[a].xo_lo);
+                } else {
+                    const ff tt = two_sum(x, -iv[a].xo);
+                    t = tt.hi + (tt.lo + (x_lo - iv[a].xo_lo));
+                }
                 P[a] = fmaf(fmaf(fmaf(iv[a].c3, t, iv[a].c2), t, iv[a].c1), t, iv[a].c0);
                 tl[a] = t;
             }
@@ -689,6 +697,19 @@ __global__ void __launch_bounds__(128)
     }
 }
 
+// Whether every dataset meets the EXACT_T condition of adjoint_fp32_kernel.
+inline bool adj_exact_t(const lisa_data* d) {
+    for (const auto& D : d->h_ds) {
+        if (D.nbins == 0) continue;
+        if (!(D.x_lo <= D.xb_min && D.xb_max <= D.x_hi)) return false;
+        const bool neg = D.x_hi < 0.0, pos = D.x_lo > 0.0;
+        if (neg && !(-D.x_lo <= 2.9 * -D.x_hi)) return false;
+        if (pos && !(D.x_hi <= 2.9 * D.x_lo)) return false;
+        if (!neg && !pos) return false;
+    }
+    return true;
+}
+
 template <int C, bool H, bool B>
 cudaError_t launch_adjoint(const lisa_data* d, bool fp32, const lisa_params* params, const lisa_knots* kn,
                            const int32_t* sstat, const int32_t* nint, const void* srec, double* scal, double* mom,
@@ -697,11 +718,14 @@ cudaError_t launch_adjoint(const lisa_data* d, bool fp32, const lisa_params* par
     const bool prof = prof_active(d, sm);
     prof_mark(d, prof, 0, sm);
     if (d->n_adj_units > 0) {
-        if (fp32)
-            adjoint_fp32_kernel<C, H, B><<<grid, 128, 0, sm>>>(d->d_adj_units, d->n_adj_units, d->d_ds, d->d_rec32,
-                                                               d->d_xlo32, params->theta_dev, sstat, nint,
-                                                               static_cast<const float*>(srec), kn->kmax, d->nsp,
-                                                               d->d_adj_prefix, scal, mom);
+        if (fp32 && adj_exact_t(d))
+            adjoint_fp32_kernel<C, H, B, true><<<grid, 128, 0, sm>>>(
+                d->d_adj_units, d->n_adj_units, d->d_ds, d->d_rec32, d->d_xlo32, params->theta_dev, sstat, nint,
+                static_cast<const float*>(srec), kn->kmax, d->nsp, d->d_adj_prefix, scal, mom);
+        else if (fp32)
+            adjoint_fp32_kernel<C, H, B, false><<<grid, 128, 0, sm>>>(
+                d->d_adj_units, d->n_adj_units, d->d_ds, d->d_rec32, d->d_xlo32, params->theta_dev, sstat, nint,
+                static_cast<const float*>(srec), kn->kmax, d->nsp, d->d_adj_prefix, scal, mom);
         else
             adjoint_fp64_kernel<C, H, B><<<grid, 128, 0, sm>>>(d->d_adj_units, d->n_adj_units, d->d_ds, d->d_rec64,
                                                                params->theta_dev, sstat, nint,

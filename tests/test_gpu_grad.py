@@ -57,9 +57,12 @@ def check_grad(G, G_ref, ok, precision, scale=None):
 
 
 @pytest.mark.parametrize("precision", [FP64, FP32])
-@pytest.mark.parametrize("variant", ["akima", "natural", "broken", "noise_only", "ae"])
+@pytest.mark.parametrize("variant", ["akima", "natural", "broken", "noise_only", "ae", "wide_band"])
 def test_adjoint_matches_oracle_gradient(precision, variant):
     over = dict(n_bins=3000, n_states=16, kmin=0, kmax_draw=8)
+    if variant == "wide_band":
+        # |log10 f_min| > 2.9 |log10 f_max|: the FP32 adjoint forms t = x - x_o with a two-sum
+        over.update(f_min=2e-5, f_max=2.5e-2)
     if variant == "broken":
         over["sgwb_model"] = 2
     if variant == "noise_only":
