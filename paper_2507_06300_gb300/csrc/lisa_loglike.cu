@@ -76,22 +76,10 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity
     return false;
 }
 
+// One spline interval's cubic about its midpoint xo, for the scalar per-bin path.
 struct Iv32 {
-    float xr, xo, c0, c1, c2, c3;
-    const float* base;
-    int j, last;   // current interval, last interval index
+    float xo, c0, c1, c2, c3;
 };
-
-__device__ __forceinline__ void load_iv(Iv32& v) {
-    const float4 A = __ldg(reinterpret_cast<const float4*>(v.base + (size_t)v.j * kSplineRec32));
-    const float4 B = __ldg(reinterpret_cast<const float4*>(v.base + (size_t)v.j * kSplineRec32 + 4));
-    v.xr = A.x;
-    v.xo = A.y;
-    v.c0 = A.z;
-    v.c1 = A.w;
-    v.c2 = B.x;
-    v.c3 = B.y;
-}
 
 // nu * (sum_c 1/S_c + ln prod_c S_c - C) in FP32: one reciprocal and one lg2 of the product,
 // per-channel when the product leaves [1e-30, 1e30].
@@ -210,11 +198,6 @@ __device__ __forceinline__ float bin_term32p(const float* __restrict__ tb, int i
     }
     return bin_term32<C, HAS_H, BROKEN>(tb, i, v, ao2, at2, n1, n2, Af);
 }
-__device__ __forceinline__ Iv2 dup(const Iv32& v) {
-    return Iv2{make_float2(-v.xo, -v.xo), make_float2(v.c0, v.c0), make_float2(v.c1, v.c1),
-               make_float2(v.c2, v.c2), make_float2(v.c3, v.c3)};
-}
-
 // Three-input maximum / minimum (one instruction on sm_100 and later).
 __device__ __forceinline__ float fmax3(float a, float b, float c) {
     float d;
