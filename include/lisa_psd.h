@@ -189,8 +189,8 @@ lisa_status lisa_spline_setup(const lisa_data* data, const lisa_knots* knots,
 
 /* ---- log-likelihood ------------------------------------------------------------------------ */
 
-/* Bytes of scratch workspace the likelihood entry points need (per-(state, tile) partial sums
- * and per-state FP32 parameters).
+/* Bytes of scratch workspace the likelihood entry points need (per-(state, tile) partial sums,
+ * per-state FP32 parameters and the compensated kernel's per-state work list).
  * with_grad = 0 for lisa_psd_loglike, 1 for lisa_psd_loglike_grad. */
 size_t lisa_workspace_bytes(const lisa_data* data, int32_t kmax, lisa_precision precision,
                             int32_t with_grad);
@@ -199,7 +199,8 @@ size_t lisa_workspace_bytes(const lisa_data* data, int32_t kmax, lisa_precision 
  * deterministic FP64 reduction over bins.  loglike_dev [n_states] (FP64).  spline_buf_dev is
  * the output of lisa_spline_setup with the same precision and kmax.  workspace_dev: at least
  * lisa_workspace_bytes(..., 0) bytes, 256-byte aligned, contents ignored and overwritten.
- * Calls that share a workspace must not overlap on the GPU. */
+ * Calls that share a workspace must not overlap on the GPU.  FP32 mode returns LISA_ERR_SHAPE
+ * when the states times tiles of the current tiling exceed 2^32 - 1. */
 lisa_status lisa_psd_loglike(const lisa_data* data, const lisa_params* params,
                              const void* spline_buf_dev, size_t spline_buf_bytes, int32_t kmax,
                              double* loglike_dev, void* workspace_dev, size_t workspace_bytes,
@@ -263,9 +264,10 @@ lisa_status lisa_averaged_periodogram(const double* d_dev, int32_t n_channels, i
  * fixed-size array that lives in the library's own device image, so the call allocates nothing.
  *
  *  - The array holds LISA_NOALLOC_SCRATCH_BYTES (4 MiB): 256 bytes plus 8 bytes per
- *    (state, tile) partial sum plus 48 bytes of FP32 parameters per state (each region rounded
- *    up to 256 bytes), i.e. lisa_workspace_bytes(data, kmax, precision, 0) must not exceed it
- *    (the paper-scale workload needs about 1 MiB).  Larger problems get
+ *    (state, tile) partial sum plus 48 bytes of FP32 parameters and 32 bytes of work list per
+ *    state (each region rounded up to 256 bytes), i.e.
+ *    lisa_workspace_bytes(data, kmax, precision, 0) must not exceed it (the paper-scale
+ *    workload needs about 2.1 MiB at the default 512-bin tiles).  Larger problems get
  *    LISA_ERR_WORKSPACE and nothing is launched; use lisa_psd_loglike for them.
  *  - Every GPU that loads the library holds the array until the process exits.
  *  - The first call on each device looks the array's device address up (with that device

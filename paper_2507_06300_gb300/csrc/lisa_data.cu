@@ -249,6 +249,7 @@ lisa_status rebuild_work(lisa_data* d) {
         cta_first[b] = (int32_t)(b == grid ? items.size() : q);
     }
     d->fgrid = grid;
+    d->rgrid = std::max(1, d->n_sm * robust_ctas_per_sm(d));
     cudaFree(d->d_items);
     cudaFree(d->d_cta_first);
     d->d_items = nullptr;

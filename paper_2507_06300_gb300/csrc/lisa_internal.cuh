@@ -115,6 +115,7 @@ struct lisa_data {
     lisa::WorkItem* d_items = nullptr;
     int32_t* d_cta_first = nullptr;  // fused kernel: first item of each CTA (fgrid + 1 entries)
     int32_t fgrid = 0;               // CTAs of the fused FP32 launch
+    int32_t rgrid = 0;               // CTAs of the compensated kernel's persistent launch
     bool fblocks = false;            // contiguous cost-balanced blocks (else every fgrid-th item)
     lisa::AdjUnit* d_adj_units = nullptr;
     int64_t n_adj_units = 0;
@@ -166,10 +167,27 @@ struct StateParams {
 };
 static_assert(sizeof(StateParams) == 48, "three float4");
 
-// Forward workspace: error flag | FP64 partial sums [state][tile] | StateParams [S].
+// Work list of the compensated kernel, built per call by the state-parameter kernel: one entry
+// per routed state with at least one tile inside the x-extent of its ill-conditioned intervals.
+// A unit is one (state, tile); the entries are in the order of a single 64-bit counter,
+// (entries << 32) + units, advanced by one atomic add per entry, so u0 increases along the list.
+struct RobustEntry {
+    int32_t s, t0;      // state, first live tile
+    uint32_t u0;        // first unit
+    int32_t nt;         // live tiles (>= 1)
+    int64_t b0;         // first bin of tile t0 (padded global index)
+    uint32_t p0;        // partial slot of (s, t0); tile t0 + k has slot p0 + k
+    int32_t nb_last;    // bins in tile t0 + nt - 1 (all earlier tiles hold tile_bins)
+};
+static_assert(sizeof(RobustEntry) == 32, "two int4");
+
+// Forward workspace: error flag (int32 at 0) and work-list counter (uint64 at 8) in the first
+// 256 bytes | FP64 partial sums [state][tile] | StateParams [S] | RobustEntry [S].
+constexpr size_t kWsCounterOff = 8;
 inline size_t ws_partials_bytes(const lisa_data* d) { return align256(sizeof(double) * (size_t)d->n_partials); }
+inline size_t ws_prm_bytes(const lisa_data* d) { return align256(sizeof(StateParams) * (size_t)d->n_states); }
 inline size_t ws_fwd_bytes(const lisa_data* d) {
-    return 256 + ws_partials_bytes(d) + align256(sizeof(StateParams) * (size_t)d->n_states);
+    return 256 + ws_partials_bytes(d) + ws_prm_bytes(d) + align256(sizeof(RobustEntry) * (size_t)d->n_states);
 }
 
 // Extra workspace of the adjoint entry point (after the forward region).
@@ -178,6 +196,8 @@ size_t grad_extra_bytes(const lisa_data* d, int kmax);
 lisa_status rebuild_work(lisa_data* d);
 // Resident CTAs per SM of the fused FP32 kernel under tiling t (its registers and shared memory).
 int fused_ctas_per_sm(const lisa_data* d, const lisa_tiling& t);
+// Resident CTAs per SM of the compensated kernel for this data object's model.
+int robust_ctas_per_sm(const lisa_data* d);
 
 // Per-kernel timing (lisa_data_set_profiling): whether this call records events (profiling on
 // and the stream not capturing), and an event record at point k of the call.

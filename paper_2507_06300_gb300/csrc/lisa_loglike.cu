@@ -154,27 +154,94 @@ __device__ __forceinline__ float exp10_to_float(double v) {
     return n >= -126.0 ? f * __int_as_float(((int)n + 127) << 23) : ldexpf(f, (int)n);
 }
 
+// One step of a warp-wide search for the first t in [lo, hi) where a monotone predicate holds
+// (hi when it holds nowhere): lane k sampled t = lo + k*step (step = ceil((hi - lo) / 32); lanes
+// past hi count as true) and m is the ballot.  The answer lies after the last false sample and
+// at or before the first true one, a range of at most step - 1 candidates.
+__device__ __forceinline__ void search_narrow(int& lo, int& hi, int step, unsigned m) {
+    if (m == 0u) {
+        lo += 31 * step + 1;
+        return;
+    }
+    const int k = __ffs(m) - 1;
+    if (k == 0) {
+        hi = lo;
+        return;
+    }
+    const int first_true = lo + k * step;
+    lo += (k - 1) * step + 1;
+    hi = min(hi, first_true);
+}
+
+// log10 f (FP32) of padded bin b of the pair-block table.
+__device__ __forceinline__ float bin_x(const float* __restrict__ rec32, int64_t b) {
+    return __ldg(rec32 + (b >> 1) * kPairRec + (b & 1));
+}
+
 // Per-state FP32 parameters from theta (FP64), once per call: the per-bin kernels then need no
 // FP64 arithmetic.  Non-finite theta propagates (the state's log L becomes -inf).
-__global__ void state_prep_kernel(int S, const double* __restrict__ theta, StateParams* __restrict__ prm) {
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= S) return;
-    const double* th = theta + (size_t)s * LISA_N_THETA;
-    StateParams p;
-    p.ao2 = (float)(th[0] * th[0]);
-    p.at2 = (float)(th[1] * th[1]);
-    p.Af = exp10_to_float(th[2]);
-    const ff lA = ff_from_double(th[2] * kLog2_10);
-    const ff n1 = ff_from_double(th[3]);
-    const ff n2 = ff_from_double(th[4]);
-    p.n1 = n1.hi;
-    p.n1_lo = n1.lo;
-    p.n2 = n2.hi;
-    p.n2_lo = n2.lo;
-    p.lA_hi = lA.hi;
-    p.lA_lo = lA.lo;
-    p.pad0 = p.pad1 = p.pad2 = 0.f;
-    prm[s] = p;
+// One warp per state.  For a state the spline setup routed to the compensated kernel, the warp
+// also finds the tiles that overlap the x-extent [h.x, h.y) of its ill-conditioned intervals --
+// tile t with first-bin x < h.y and last-bin x >= h.x, a contiguous range because x increases
+// with the bin -- and appends {state, first tile, first unit, tiles} to the work list.
+__global__ void state_prep_kernel(int S, const double* __restrict__ theta, StateParams* __restrict__ prm,
+                                  const int32_t* __restrict__ sstat, const float2* __restrict__ hull,
+                                  const int32_t* __restrict__ state_ds, const DatasetDev* __restrict__ ds,
+                                  const float* __restrict__ rec32, int tile_bins,
+                                  unsigned long long* __restrict__ rcount, RobustEntry* __restrict__ rlist) {
+    const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t s64 = gt >> 5;
+    const int lane = threadIdx.x & 31;
+    if (s64 >= S) return;   // warp-uniform (blockDim is a multiple of 32)
+    const int s = (int)s64;
+    if (lane == 0) {
+        const double* th = theta + (size_t)s * LISA_N_THETA;
+        StateParams p;
+        p.ao2 = (float)(th[0] * th[0]);
+        p.at2 = (float)(th[1] * th[1]);
+        p.Af = exp10_to_float(th[2]);
+        const ff lA = ff_from_double(th[2] * kLog2_10);
+        const ff n1 = ff_from_double(th[3]);
+        const ff n2 = ff_from_double(th[4]);
+        p.n1 = n1.hi;
+        p.n1_lo = n1.lo;
+        p.n2 = n2.hi;
+        p.n2_lo = n2.lo;
+        p.lA_hi = lA.hi;
+        p.lA_lo = lA.lo;
+        p.pad0 = p.pad1 = p.pad2 = 0.f;
+        prm[s] = p;
+    }
+    if (!(__ldg(sstat + s) & kRouted)) return;   // the same word in every lane
+    const DatasetDev& D = ds[__ldg(state_ds + s)];
+    const float2 h = __ldg(hull + s);
+    const int nt = D.ntiles;
+    const int64_t bend = D.bin0 + D.npad;
+    // ta = first tile whose last bin has x >= h.x, tb = first tile whose first bin has x >= h.y;
+    // the live tiles are [ta, tb).  Both searches run together, 32 samples per round.
+    int alo = 0, ahi = nt, blo = 0, bhi = nt;
+    while (alo < ahi || blo < bhi) {
+        const int sa = (ahi - alo + 31) >> 5, sb = (bhi - blo + 31) >> 5;
+        const int tA = alo + lane * sa, tB = blo + lane * sb;
+        bool pa = true, pb = true;
+        if (alo < ahi && tA < ahi) pa = bin_x(rec32, min(D.bin0 + (int64_t)(tA + 1) * tile_bins, bend) - 1) >= h.x;
+        if (blo < bhi && tB < bhi) pb = bin_x(rec32, D.bin0 + (int64_t)tB * tile_bins) >= h.y;
+        const unsigned ma = __ballot_sync(0xffffffffu, pa), mb = __ballot_sync(0xffffffffu, pb);
+        if (alo < ahi) search_narrow(alo, ahi, sa, ma);
+        if (blo < bhi) search_narrow(blo, bhi, sb, mb);
+    }
+    if (lane == 0 && blo > alo) {
+        const unsigned long long old = atomicAdd(rcount, (1ull << 32) | (unsigned long long)(blo - alo));
+        RobustEntry e;
+        e.s = s;
+        e.t0 = alo;
+        e.u0 = (uint32_t)(old & 0xffffffffull);
+        e.nt = blo - alo;
+        e.b0 = D.bin0 + (int64_t)alo * tile_bins;
+        e.p0 = (uint32_t)(D.pbase + (int64_t)(s - D.s0) * nt + alo);
+        e.nb_last = (int32_t)min((int64_t)tile_bins, D.npad - (int64_t)(blo - 1) * tile_bins);
+        rlist[old >> 32] = e;
+    }
 }
 
 // Current interval of one spline duplicated into register pairs for the packed path.
@@ -537,12 +604,11 @@ __device__ __forceinline__ ff inv_plus_log(ff lS, float nu, double& far) {
 // Compensated kernel staging: each warp copies its tile in chunks of kRobChunk bins (pair-block
 // table plus the low parts of x and ell) into its own shared-memory slice with coalesced loads,
 // then evaluates the chunk from shared memory.
-constexpr int kRobWarps = 4;
+constexpr int kRobWarps = 8;
 constexpr int kRobChunk = 256;                                    // even
 constexpr int kRobChunkF4 = kRobChunk / 2 * (kPairRec / 4);       // float4 of table per chunk
 constexpr int kRobSliceF4 = kRobChunkF4 + 2 * kRobChunk / 4;      // + x lo, ell lo
 constexpr size_t kRobSmem = (size_t)kRobWarps * kRobSliceF4 * sizeof(float4);
-constexpr int kRobTiles = 1;                                      // tiles per warp unit
 
 // One bin of a routed state (i: bin within the staged chunk tb, with the low parts of x and ell
 // in xs / es), evaluated only if one of its spline intervals is ill-conditioned (the fused kernel
@@ -621,36 +687,68 @@ __device__ __forceinline__ void robust_bin(const float* __restrict__ tb, int i, 
     acc_ff = ff_add(acc_ff, ff_mul(term, ff{nu, 0.f}));
 }
 
-// One warp per (routed state, run of kRobTiles consecutive tiles), kRobWarps warps per CTA.  A
-// run outside the x-hull of the state's ill-conditioned intervals (from the setup) is skipped.  Otherwise the warp
-// stages each tile chunk by chunk into its shared-memory slice; lane l then takes bins l, l + 32,
-// ... of the chunk (the lanes of a warp mostly share their spline intervals), so a lane's bins
-// come in increasing order and its intervals carry over from tile to tile.  Each tile's sum of
-// ill-conditioned bins is added to the (state, tile) partial the fused kernel wrote.
+// One warp per unit (routed state, tile) of the work list the state-parameter kernel built, on a
+// persistent grid.  As soon as the warp knows its tile it starts one bulk asynchronous copy of
+// the tile's first chunk of the pair-block table into its shared-memory slice; meanwhile it
+// locates each spline's interval at the tile's first bin with one ballot over the interval right
+// ends (lane k holds interval k) and loads the low parts of x and ell of the chunk (each lane
+// reads back only the entries it wrote).  Lane l takes bins l, l + 32, ... of a chunk, so a
+// lane's bins come in increasing order and its intervals only move right.  The tile's sum of
+// ill-conditioned bins is added to the (state, tile) partial the fused kernel wrote (one warp per
+// partial: deterministic).
 template <int C, bool HAS_H, bool BROKEN>
-__global__ void __launch_bounds__(kRobWarps * 32)
-    loglike_robust_kernel(const int32_t* __restrict__ route, const int32_t* __restrict__ state_ds,
-                          const DatasetDev* __restrict__ ds, int tile_bins, int max_runs,
-                          const float* __restrict__ rec32, const float* __restrict__ xlo32,
+__global__ void __launch_bounds__(kRobWarps * 32, 2)
+    loglike_robust_kernel(const unsigned long long* __restrict__ rcount, const RobustEntry* __restrict__ rlist,
+                          int tile_bins, const float* __restrict__ rec32, const float* __restrict__ xlo32,
                           const float* __restrict__ elllo32, const StateParams* __restrict__ prm,
-                          const int32_t* __restrict__ nint, const float* __restrict__ srec,
-                          const float2* __restrict__ hull, int kmax, int nsp, double* __restrict__ partial) {
+                          const int32_t* __restrict__ nint, const float* __restrict__ srec, int kmax, int nsp,
+                          double* __restrict__ partial, int* __restrict__ err) {
     constexpr int NSP = C + (HAS_H ? 1 : 0);
     extern __shared__ float4 rsm[];
+    __shared__ __align__(8) uint64_t rbar[kRobWarps];
     const int lane = threadIdx.x & 31;
-    float4* slice = rsm + (threadIdx.x >> 5) * kRobSliceF4;
+    const int warp = threadIdx.x >> 5;
+    float4* slice = rsm + warp * kRobSliceF4;
     const float* tb = reinterpret_cast<const float*>(slice);
     float* xs = reinterpret_cast<float*>(slice + kRobChunkF4);
     float* es = xs + kRobChunk;
+    uint64_t* bar = &rbar[warp];
+    const unsigned long long cnt = __ldg(rcount);
+    const int n_ent = (int)(cnt >> 32);
+    const int64_t units = (int64_t)(cnt & 0xffffffffull);
     const int64_t wg = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    const int64_t units = (int64_t)route[0] * max_runs;
+    if (wg >= units) return;   // warp-uniform
+    if (lane == 0) {
+        mbar_init(bar, 1);
+        mbar_fence_init();
+    }
+    __syncwarp();
+    unsigned phase = 0;
+    // a static assignment: handing units out through one global counter was slower here (the
+    // requests of all warps serialise on its address)
     for (int64_t u = wg; u < units; u += nw) {
-        const int r = (int)(u / max_runs), t0 = (int)(u % max_runs) * kRobTiles;
-        const int s = route[1 + r];
-        const DatasetDev& D = ds[state_ds[s]];
-        if (t0 >= D.ntiles) continue;                        // uniform per warp
-        const int t1 = min(t0 + kRobTiles, D.ntiles);
+        // the entry holding unit u: the last one whose first unit is <= u
+        int lo = 0, hi = n_ent - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if ((int64_t)__ldg(&rlist[mid].u0) <= u) lo = mid; else hi = mid - 1;
+        }
+        const int4 ea = __ldg(reinterpret_cast<const int4*>(rlist + lo));
+        const int4 eb = __ldg(reinterpret_cast<const int4*>(rlist + lo) + 1);
+        const int s = ea.x;
+        const int k_t = (int)(u - (int64_t)(uint32_t)ea.z);   // tile t0 + k_t
+        const int64_t b0 = (int64_t)(((uint64_t)(uint32_t)eb.y << 32) | (uint32_t)eb.x) + (int64_t)k_t * tile_bins;
+        const int nb = k_t == ea.w - 1 ? eb.w : tile_bins;
+        const int64_t pslot = (int64_t)(uint32_t)eb.z + k_t;
+        const float* tbase = rec32 + (b0 >> 1) * kPairRec;   // b0 even
+        __syncwarp();   // every lane is done with the previous unit's table
+        if (lane == 0) {
+            const unsigned bytes = (unsigned)min(kRobChunk, nb) * kRec * sizeof(float);   // even bin count
+            fence_proxy_async();
+            mbar_expect_tx(bar, bytes);
+            bulk_copy_g2s(slice, tbase, bytes, bar);
+        }
         const float4 q0 = __ldg(reinterpret_cast<const float4*>(prm + s));
         const float4 q1 = __ldg(reinterpret_cast<const float4*>(prm + s) + 1);
         const float4 q2 = __ldg(reinterpret_cast<const float4*>(prm + s) + 2);
@@ -658,58 +756,72 @@ __global__ void __launch_bounds__(kRobWarps * 32)
         const ff n1 = {q0.w, q1.w};
         const ff n2 = BROKEN ? ff{q1.x, q2.x} : n1;
         const ff lA = {q1.y, q1.z};
-        {
-            // skip a run that the state's ill-conditioned intervals do not reach
-            const int64_t bA = D.bin0 + (int64_t)t0 * tile_bins;
-            const int64_t bB = min(D.bin0 + (int64_t)t1 * tile_bins, D.bin0 + D.npad) - 1;
-            const float xA = fld(rec32 + (bA >> 1) * kPairRec, (int)(bA & 1), 0);
-            const float xB = fld(rec32 + (bB >> 1) * kPairRec, (int)(bB & 1), 0);
-            const float2 h = __ldg(hull + s);
-            if (!(h.x <= xB && h.y > xA)) continue;          // uniform per warp
-        }
+        // intervals at the tile's first bin: j = number of right ends <= x among intervals
+        // 0 .. last-1 (the right ends increase with j)
+        const float xf = __ldg(tbase);
         IvR iv[NSP];
-        {
-            const int64_t b0 = D.bin0 + (int64_t)t0 * tile_bins;
-            const int nb = (int)min((int64_t)tile_bins, D.bin0 + D.npad - b0);
-            const float x0 = fld(rec32 + (b0 >> 1) * kPairRec, min(lane, nb - 1), 0);
+        float xr0[NSP];
 #pragma unroll
-            for (int a = 0; a < NSP; ++a) {
-                const int64_t sp = (int64_t)s * nsp + a;
-                iv[a].base = srec + sp * (int64_t)(kmax + 1) * kSplineRec32;
-                iv[a].last = nint[sp] - 1;
-                iv[a].j = find_interval<float, kSplineRec32, 6>(iv[a].base, nint[sp], x0);
-                load_ivr(iv[a]);
-            }
+        for (int a = 0; a < NSP; ++a) {
+            const int64_t sp = (int64_t)s * nsp + a;
+            iv[a].base = srec + sp * (int64_t)(kmax + 1) * kSplineRec32;
+            iv[a].last = __ldg(nint + sp) - 1;
+            xr0[a] = lane <= kmax ? __ldg(iv[a].base + (size_t)lane * kSplineRec32) : INFINITY;
         }
-        for (int t = t0; t < t1; ++t) {
-            const int64_t b0 = D.bin0 + (int64_t)t * tile_bins;   // even
-            const int nb = (int)min((int64_t)tile_bins, D.bin0 + D.npad - b0);
-            const float* tbase = rec32 + (b0 >> 1) * kPairRec;
-            ff acc_ff = {0.f, 0.f};
-            double far = 0.0;
-            for (int c0 = 0; c0 < nb; c0 += kRobChunk) {
-                const int nbc = min(kRobChunk, nb - c0);
-                const float4* src = reinterpret_cast<const float4*>(tbase + (c0 >> 1) * kPairRec);
-                __syncwarp();                                // the previous chunk is consumed
-                for (int q = lane; q < (nbc >> 1) * (kPairRec / 4); q += 32) slice[q] = __ldg(src + q);
-                for (int q = lane; q < nbc; q += 32) {
-                    xs[q] = __ldg(xlo32 + b0 + c0 + q);
-                    es[q] = __ldg(elllo32 + b0 + c0 + q);
+#pragma unroll
+        for (int a = 0; a < NSP; ++a) {
+            int j = __popc(__ballot_sync(0xffffffffu, lane < iv[a].last && xr0[a] <= xf));
+            if (kmax >= 32) {   // warp-uniform
+                const int k = 32 + lane;
+                const float xr1 = k <= kmax ? __ldg(iv[a].base + (size_t)k * kSplineRec32) : INFINITY;
+                j += __popc(__ballot_sync(0xffffffffu, k < iv[a].last && xr1 <= xf));
+            }
+            iv[a].j = j;
+            load_ivr(iv[a]);
+        }
+        ff acc_ff = {0.f, 0.f};
+        double far = 0.0;
+        for (int c0 = 0; c0 < nb; c0 += kRobChunk) {
+            const int nbc = min(kRobChunk, nb - c0);
+            if (c0 > 0) {
+                __syncwarp();   // every lane is done with the previous chunk's table
+                if (lane == 0) {
+                    const unsigned bytes = (unsigned)nbc * kRec * sizeof(float);
+                    fence_proxy_async();
+                    mbar_expect_tx(bar, bytes);
+                    bulk_copy_g2s(slice, tbase + (c0 >> 1) * kPairRec, bytes, bar);
                 }
-                __syncwarp();
-                for (int i = lane; i < nbc; i += 32)
-                    robust_bin<C, HAS_H, BROKEN>(tb, i, xs, es, iv, ao2, at2, n1, n2, lA, acc_ff, far);
             }
-            // warp sum: float-float tree; the FP64 spill-over only when some lane has one
+            float vx[kRobChunk / 32], ve[kRobChunk / 32];
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1)
-                acc_ff = ff_add(acc_ff, ff{__shfl_down_sync(0xffffffffu, acc_ff.hi, o),
-                                           __shfl_down_sync(0xffffffffu, acc_ff.lo, o)});
-            if (__any_sync(0xffffffffu, far != 0.0))
-                for (int o = 16; o > 0; o >>= 1) far += __shfl_down_sync(0xffffffffu, far, o);
-            const double acc = ((double)acc_ff.hi + (double)acc_ff.lo) + far;
-            if (lane == 0 && !(acc == 0.0)) partial[D.pbase + (int64_t)(s - D.s0) * D.ntiles + t] += acc;
+            for (int k = 0; k < kRobChunk / 32; ++k) {
+                const int q = lane + 32 * k;
+                vx[k] = q < nbc ? __ldg(xlo32 + b0 + c0 + q) : 0.f;
+                ve[k] = q < nbc ? __ldg(elllo32 + b0 + c0 + q) : 0.f;
+            }
+#pragma unroll
+            for (int k = 0; k < kRobChunk / 32; ++k) {
+                xs[lane + 32 * k] = vx[k];
+                es[lane + 32 * k] = ve[k];
+            }
+            const bool ok = mbar_wait_bounded(bar, phase, err);
+            if (!__all_sync(0xffffffffu, ok)) {
+                mbar_wait_bounded(bar, phase, err);   // let the copy in flight land, then stop
+                return;
+            }
+            phase ^= 1;
+            for (int i = lane; i < nbc; i += 32)
+                robust_bin<C, HAS_H, BROKEN>(tb, i, xs, es, iv, ao2, at2, n1, n2, lA, acc_ff, far);
         }
+        // warp sum: float-float tree; the FP64 spill-over only when some lane has one
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+            acc_ff = ff_add(acc_ff, ff{__shfl_down_sync(0xffffffffu, acc_ff.hi, o),
+                                       __shfl_down_sync(0xffffffffu, acc_ff.lo, o)});
+        if (__any_sync(0xffffffffu, far != 0.0))
+            for (int o = 16; o > 0; o >>= 1) far += __shfl_down_sync(0xffffffffu, far, o);
+        const double acc = ((double)acc_ff.hi + (double)acc_ff.lo) + far;
+        if (lane == 0 && !(acc == 0.0)) partial[pslot] += acc;
     }
 }
 
@@ -872,8 +984,8 @@ int grid_for(K kernel, const lisa_data* d, size_t smem, int threads) {
 
 template <int C, bool H, bool B, int G>
 cudaError_t launch_fp32_g(const lisa_data* d, const StateParams* prm, const int32_t* sstat, const int32_t* nint,
-                          const int32_t* route, const float* srec, const float2* hull, int kmax, double* partial,
-                          int* err, cudaStream_t sm, bool prof) {
+                          unsigned long long* rcount, const RobustEntry* rlist, const float* srec, int kmax,
+                          double* partial, int* err, cudaStream_t sm, bool prof) {
     auto kern = loglike_fp32_kernel<C, H, B, G>;
     const size_t smem = 2 * (size_t)d->tiling.tile_bins * kRec * sizeof(float);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -884,19 +996,28 @@ cudaError_t launch_fp32_g(const lisa_data* d, const StateParams* prm, const int3
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     prof_mark(d, prof, 1, sm);
-    // compensated kernel for the routed states (a no-op grid when the route list is empty)
-    int max_tiles = 1;
-    for (const auto& D : d->h_ds) max_tiles = D.ntiles > max_tiles ? D.ntiles : max_tiles;
-    const int max_runs = (max_tiles + kRobTiles - 1) / kRobTiles;
+    // compensated kernel for the routed states' work list (its warps return at once when the list
+    // is empty)
     auto rk = loglike_robust_kernel<C, H, B>;
     e = cudaFuncSetAttribute(rk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRobSmem);
     if (e != cudaSuccess) return e;
-    rk<<<d->n_sm * 8, kRobWarps * 32, kRobSmem, sm>>>(route, d->d_state_ds, d->d_ds, d->tiling.tile_bins, max_runs,
-                                                     d->d_rec32, d->d_xlo32, d->d_elllo32, prm, nint, srec, hull,
-                                                     kmax, d->nsp, partial);
+    rk<<<d->rgrid, kRobWarps * 32, kRobSmem, sm>>>(rcount, rlist, d->tiling.tile_bins, d->d_rec32, d->d_xlo32,
+                                                   d->d_elllo32, prm, nint, srec, kmax, d->nsp, partial, err);
     e = cudaGetLastError();
     prof_mark(d, prof, 2, sm);
     return e;
+}
+
+template <int C, bool H, bool B>
+int robust_occupancy() {
+    auto rk = loglike_robust_kernel<C, H, B>;
+    int n = 0;
+    if (cudaFuncSetAttribute(rk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRobSmem) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, rk, kRobWarps * 32, kRobSmem) != cudaSuccess || n < 1) {
+        cudaGetLastError();
+        n = 1;
+    }
+    return n;
 }
 
 template <int C, bool H, bool B, int G>
@@ -933,13 +1054,13 @@ int occupancy_c(int sgwb, const lisa_tiling& t) {
 
 template <int C, bool H, bool B>
 cudaError_t launch_fp32(const lisa_data* d, const StateParams* prm, const int32_t* sstat, const int32_t* nint,
-                        const int32_t* route, const float* srec, const float2* hull, int kmax, double* partial,
-                        int* err, cudaStream_t sm, bool prof) {
+                        unsigned long long* rcount, const RobustEntry* rlist, const float* srec, int kmax,
+                        double* partial, int* err, cudaStream_t sm, bool prof) {
     switch (d->tiling.group) {
-        case 2: return launch_fp32_g<C, H, B, 2>(d, prm, sstat, nint, route, srec, hull, kmax, partial, err, sm, prof);
-        case 8: return launch_fp32_g<C, H, B, 8>(d, prm, sstat, nint, route, srec, hull, kmax, partial, err, sm, prof);
+        case 2: return launch_fp32_g<C, H, B, 2>(d, prm, sstat, nint, rcount, rlist, srec, kmax, partial, err, sm, prof);
+        case 8: return launch_fp32_g<C, H, B, 8>(d, prm, sstat, nint, rcount, rlist, srec, kmax, partial, err, sm, prof);
         default:
-            return launch_fp32_g<C, H, B, 4>(d, prm, sstat, nint, route, srec, hull, kmax, partial, err, sm, prof);
+            return launch_fp32_g<C, H, B, 4>(d, prm, sstat, nint, rcount, rlist, srec, kmax, partial, err, sm, prof);
     }
 }
 
@@ -958,16 +1079,17 @@ cudaError_t launch_fp64(const lisa_data* d, const double* theta, const int32_t* 
 
 template <int C>
 cudaError_t dispatch_model(const lisa_data* d, bool fp32, const double* theta, const StateParams* prm,
-                           const int32_t* sstat, const int32_t* nint, const int32_t* route, const void* srec,
-                           const float2* hull, int kmax, double* partial, int* err, cudaStream_t sm, bool prof) {
+                           const int32_t* sstat, const int32_t* nint, unsigned long long* rcount,
+                           const RobustEntry* rlist, const void* srec, int kmax, double* partial, int* err,
+                           cudaStream_t sm, bool prof) {
     const int h = d->sgwb_model;
     if (fp32) {
         const float* r = static_cast<const float*>(srec);
         if (h == 0)
-            return launch_fp32<C, false, false>(d, prm, sstat, nint, route, r, hull, kmax, partial, err, sm, prof);
+            return launch_fp32<C, false, false>(d, prm, sstat, nint, rcount, rlist, r, kmax, partial, err, sm, prof);
         if (h == 1)
-            return launch_fp32<C, true, false>(d, prm, sstat, nint, route, r, hull, kmax, partial, err, sm, prof);
-        return launch_fp32<C, true, true>(d, prm, sstat, nint, route, r, hull, kmax, partial, err, sm, prof);
+            return launch_fp32<C, true, false>(d, prm, sstat, nint, rcount, rlist, r, kmax, partial, err, sm, prof);
+        return launch_fp32<C, true, true>(d, prm, sstat, nint, rcount, rlist, r, kmax, partial, err, sm, prof);
     }
     const double* r = static_cast<const double*>(srec);
     if (h == 0) return launch_fp64<C, false, false>(d, theta, sstat, nint, r, kmax, partial, sm, prof);
@@ -979,6 +1101,17 @@ cudaError_t dispatch_model(const lisa_data* d, bool fp32, const double* theta, c
 
 int fused_ctas_per_sm(const lisa_data* d, const lisa_tiling& t) {
     return d->C == 3 ? occupancy_c<3>(d->sgwb_model, t) : occupancy_c<2>(d->sgwb_model, t);
+}
+
+template <int C>
+int robust_occupancy_c(int sgwb) {
+    if (sgwb == 0) return robust_occupancy<C, false, false>();
+    if (sgwb == 1) return robust_occupancy<C, true, false>();
+    return robust_occupancy<C, true, true>();
+}
+
+int robust_ctas_per_sm(const lisa_data* d) {
+    return d->C == 3 ? robust_occupancy_c<3>(d->sgwb_model) : robust_occupancy_c<2>(d->sgwb_model);
 }
 
 }  // namespace lisa
@@ -1007,30 +1140,39 @@ lisa_status lisa_psd_loglike(const lisa_data* d, const lisa_params* params, cons
     const SplineLayout L = spline_layout(d->n_states, d->nsp, kmax);
     if (buf_bytes < L.bytes || (reinterpret_cast<uintptr_t>(buf) & 255)) return LISA_ERR_WORKSPACE;
     if (ws_bytes < ws_fwd_bytes(d) || (reinterpret_cast<uintptr_t>(ws) & 255)) return LISA_ERR_WORKSPACE;
+    // the compensated kernel's unit counter holds up to 2^32 - 1 (state, tile) units
+    if (fp32 && d->n_partials > (int64_t)0xffffffffLL) return LISA_ERR_SHAPE;
     if (d->n_states == 0) return LISA_SUCCESS;
     cudaStream_t sm = (cudaStream_t)stream;
     const char* base = static_cast<const char*>(buf);
     const int32_t* sstat = reinterpret_cast<const int32_t*>(base + L.off_status);
     const int32_t* nint = reinterpret_cast<const int32_t*>(base + L.off_nint);
-    const int32_t* route = reinterpret_cast<const int32_t*>(base + L.off_route);
     const void* srec = base + L.off_rec;
     const float2* hull = reinterpret_cast<const float2*>(base + L.off_hull);
-    int* err = static_cast<int*>(ws);
-    double* partial = reinterpret_cast<double*>(static_cast<char*>(ws) + 256);
-    StateParams* prm = reinterpret_cast<StateParams*>(static_cast<char*>(ws) + 256 + ws_partials_bytes(d));
-    if (cudaMemsetAsync(err, 0, sizeof(int), sm) != cudaSuccess) return LISA_ERR_CUDA;
+    char* wsb = static_cast<char*>(ws);
+    int* err = reinterpret_cast<int*>(wsb);
+    unsigned long long* rcount = reinterpret_cast<unsigned long long*>(wsb + kWsCounterOff);
+    double* partial = reinterpret_cast<double*>(wsb + 256);
+    StateParams* prm = reinterpret_cast<StateParams*>(wsb + 256 + ws_partials_bytes(d));
+    RobustEntry* rlist = reinterpret_cast<RobustEntry*>(wsb + 256 + ws_partials_bytes(d) + ws_prm_bytes(d));
+    // the error flag and the work-list counter
+    if (cudaMemsetAsync(wsb, 0, kWsCounterOff + sizeof(unsigned long long), sm) != cudaSuccess)
+        return LISA_ERR_CUDA;
     const int S = (int)d->n_states;
     if (fp32) {
-        state_prep_kernel<<<(S + 127) / 128, 128, 0, sm>>>(S, params->theta_dev, prm);
+        const int64_t threads = 32 * (int64_t)S;
+        state_prep_kernel<<<(unsigned)((threads + 127) / 128), 128, 0, sm>>>(
+            S, params->theta_dev, prm, sstat, hull, d->d_state_ds, d->d_ds, d->d_rec32, d->tiling.tile_bins, rcount,
+            rlist);
         if (cudaGetLastError() != cudaSuccess) return LISA_ERR_CUDA;
     }
     const bool prof = prof_active(d, sm);
     prof_mark(d, prof, 0, sm);
     cudaError_t e = cudaSuccess;
     if (d->n_items > 0)
-        e = d->C == 3 ? dispatch_model<3>(d, fp32, params->theta_dev, prm, sstat, nint, route, srec, hull, kmax,
+        e = d->C == 3 ? dispatch_model<3>(d, fp32, params->theta_dev, prm, sstat, nint, rcount, rlist, srec, kmax,
                                           partial, err, sm, prof)
-                      : dispatch_model<2>(d, fp32, params->theta_dev, prm, sstat, nint, route, srec, hull, kmax,
+                      : dispatch_model<2>(d, fp32, params->theta_dev, prm, sstat, nint, rcount, rlist, srec, kmax,
                                           partial, err, sm, prof);
     else {
         prof_mark(d, prof, 1, sm);
