@@ -187,11 +187,17 @@ def test_paper_scale_sampled_states(precision):
         assert np.all(np.abs(L[good] - L64[good]) <= tol_all[good])
 
 
-@pytest.mark.parametrize("kind", [0, 1])
-def test_ill_conditioned_splines_take_the_compensated_route(kind):
+@pytest.mark.parametrize("kind,tiling", [
+    (0, None),
+    (1, None),
+    (0, dict(tile_bins=64, states_per_cta=16, group=2)),      # many one-chunk units, ragged tail
+    (1, dict(tile_bins=2048, states_per_cta=64, group=4)),    # eight staged chunks per unit
+])
+def test_ill_conditioned_splines_take_the_compensated_route(kind, tiling):
     """Prior-drawn knots can make a spline overshoot by tens of decades between close knots
     (Akima end slopes, or natural-cubic ringing).  The FP32 path must still agree with the
-    oracle to 1e-6 and stay finite: such states are evaluated by the compensated kernel."""
+    oracle to 1e-6 and stay finite: such states are evaluated by the compensated kernel, whose
+    work list covers the tiles that the ill-conditioned intervals overlap under any tiling."""
     wl = synth.workload("tiny", n_bins=4000, n_states=40, kmin=2, kmax_draw=8)
     wl.knots.kind = kind
     k = wl.knots
@@ -205,7 +211,7 @@ def test_ill_conditioned_splines_take_the_compensated_route(kind):
         k.w[s, a, 1], k.w[s, a, 2] = 0.3, -0.3
     P, L, St = oracle_batched(wl)
     assert np.all(St == 0)                            # large overshoots, still FP64-finite
-    L32 = _check(wl, P, L, St, FP32)
+    L32 = _check(wl, P, L, St, FP32, **({"tiling": tiling} if tiling else {}))
     assert np.all(np.isfinite(L32))
 
 
