@@ -33,7 +33,9 @@ constexpr int kMaxStatesPerItem = 128;  // state lanes of a work item (<= both t
 //   FP32: [0] xr  [1] xo  [2..5] c0..c3  [6] xl  [7] conditioning T      (first 32 bytes)
 //         [8] xo_lo  [9..12] c0..c3 low parts  [13..15] 0                (second 32 bytes)
 //         coefficients about the interval midpoint xo, scaled to log2 units; hi + lo is the
-//         FP64 value split into two floats.
+//         FP64 value split into two floats (the coefficients' lo parts only where the
+//         compensated kernel reads them: in the setup pass of an ill-conditioned interval,
+//         zero elsewhere).
 constexpr int kSplineRec = 8;    // doubles per FP64 record
 constexpr int kSplineRec32 = 16; // floats per FP32 record
 // States whose FP32 perturbation spline has an interval with conditioning

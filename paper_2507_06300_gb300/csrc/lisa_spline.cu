@@ -9,10 +9,15 @@ namespace {
 // One CTA per state, one warp per spline.  The spline is built in FP64 for both output precisions:
 //  kF32 = false: FP64 records {xl, xr, a, b, c, d} about the left knot (the plain path);
 //  kF32 = true:  FP32 records about the interval midpoint xo, coefficients scaled to log2 units
-//                and split into hi + lo floats, plus the interval's conditioning bound T; a state
-//                with any T > kRobustT is appended to the route list (compensated kernel).
+//                as hi floats, plus the interval's conditioning bound T; a state with any
+//                T > kRobustT is appended to the route list (compensated kernel).  The lo floats
+//                of the coefficients (FP64 value - hi) are formed only for the intervals handled
+//                in the same pass (intervals 0-31, 32-63) as an ill-conditioned one, the only
+//                ones that read them, and are zero elsewhere.
+// The kernel is bound by the FP64 pipe; 7 CTAs per SM (at most 72 registers) keep 1,064 states
+// resident at once.
 template <bool kF32>
-__global__ void __launch_bounds__(128) spline_setup_kernel(
+__global__ void __launch_bounds__(128, 7) spline_setup_kernel(
     const int32_t* __restrict__ count, const double* __restrict__ kx, const double* __restrict__ kw,
     int S, int nsp, int kmax, int kind, const int32_t* __restrict__ state_ds,
     const DatasetDev* __restrict__ ds, int32_t* __restrict__ status_buf, int32_t* __restrict__ nint_buf,
@@ -28,7 +33,7 @@ __global__ void __launch_bounds__(128) spline_setup_kernel(
     const int s = blockIdx.x;
     const int dsi = state_ds[s];
     const double xlo = ds[dsi].x_lo, xhi = ds[dsi].x_hi;
-    const double xbmin = ds[dsi].xb_min, xbmax = ds[dsi].xb_max;
+    const float xbmin_f = (float)ds[dsi].xb_min, xbmax_f = (float)ds[dsi].xb_max;
     int st_all = 0;
     bool robust = false;
     float hlo = INFINITY, hhi = -INFINITY;   // x-extent of this spline's ill-conditioned intervals
@@ -44,13 +49,14 @@ __global__ void __launch_bounds__(128) spline_setup_kernel(
             const int K = W.K;
             double xn[2];
             spl::shift2(W.x[0], W.x[1], 1, xn[0], xn[1]);
-            for (int q = 0; q < (K > 32 ? 2 : 1); ++q) {
+            for (int q = 0; q < (K > 32 ? 2 : 1); ++q) {   // warp-uniform
                 const int j = lane + 32 * q;
-                if (j >= K - 1) continue;
+                const bool valid = j < K - 1;
                 const bool last = (j + 1 == K - 1);
                 const double* x = W.x;
                 const double *ca = W.ca, *cb = W.cb, *cc = W.cc, *cd = W.cd, *h = W.h;
                 if (!kF32) {
+                    if (!valid) continue;
                     double* r = static_cast<double*>(rec_v) + (sp * (int64_t)(kmax + 1) + j) * kSplineRec;
                     r[0] = x[q];
                     r[1] = last ? INFINITY : xn[q];
@@ -61,7 +67,9 @@ __global__ void __launch_bounds__(128) spline_setup_kernel(
                     r[6] = 0.0;
                     r[7] = 0.0;
                 } else {
-                    // re-expand about the midpoint and scale to log2 units
+                    // re-expand about the midpoint and scale to log2 units (every lane computes,
+                    // lanes past the last interval on finite placeholder values, and only valid
+                    // lanes write)
                     const double hm = 0.5 * h[q];
                     const double xo = x[q] + hm;
                     const double c3 = cd[q];
@@ -69,28 +77,35 @@ __global__ void __launch_bounds__(128) spline_setup_kernel(
                     const double c1 = cb[q] + hm * (2.0 * cc[q] + 3.0 * hm * cd[q]);
                     const double c0 = ca[q] + hm * (cb[q] + hm * (cc[q] + hm * cd[q]));
                     const double cs[4] = {c0 * kLog2_10, c1 * kLog2_10, c2 * kLog2_10, c3 * kLog2_10};
-                    const double lo_x = (j == 0) ? fmin(xbmin, x[q]) : x[q];
-                    const double hi_x = last ? fmax(xbmax, xn[q]) : xn[q];
-                    // the conditioning bound only steers the routing: FP32 is precise enough
-                    const float rr = (float)fmax(fabs(lo_x - xo), fabs(hi_x - xo));
-                    const float Tc = fabsf((float)cs[0]) +
-                                     rr * (fabsf((float)cs[1]) + rr * (fabsf((float)cs[2]) + rr * fabsf((float)cs[3])));
-                    if (!(Tc <= (float)kRobustT)) {
-                        robust = true;
-                        hlo = fminf(hlo, j == 0 ? -INFINITY : (float)x[q]);
-                        hhi = fmaxf(hhi, last ? INFINITY : (float)xn[q]);
-                    }
-                    float* r = static_cast<float*>(rec_v) + (sp * (int64_t)(kmax + 1) + j) * kSplineRec32;
+                    float chi[4];
+                    for (int c = 0; c < 4; ++c) chi[c] = (float)cs[c];
                     const float xo_hi = (float)xo;
-                    r[0] = last ? INFINITY : (float)xn[q];
+                    const float xl_f = (float)x[q], xr_f = (float)xn[q];
+                    // the conditioning bound only steers the routing: FP32 is precise enough (and
+                    // keeps these steps off the FP64 pipe, which bounds this kernel)
+                    const float lo_x = (j == 0) ? fminf(xbmin_f, xl_f) : xl_f;
+                    const float hi_x = last ? fmaxf(xbmax_f, xr_f) : xr_f;
+                    const float rr = fmaxf(fabsf(lo_x - xo_hi), fabsf(hi_x - xo_hi));
+                    const float Tc = fabsf(chi[0]) + rr * (fabsf(chi[1]) + rr * (fabsf(chi[2]) + rr * fabsf(chi[3])));
+                    const bool hard = valid && !(Tc <= (float)kRobustT);
+                    if (hard) {
+                        robust = true;
+                        hlo = fminf(hlo, j == 0 ? -INFINITY : xl_f);
+                        hhi = fmaxf(hhi, last ? INFINITY : xr_f);
+                    }
+                    // the coefficients' low parts are read only on ill-conditioned intervals:
+                    // formed when the warp has one, zero otherwise
+                    const bool any_hard = __any_sync(spl::kFull, hard);
+                    if (!valid) continue;
+                    float* r = static_cast<float*>(rec_v) + (sp * (int64_t)(kmax + 1) + j) * kSplineRec32;
+                    r[0] = last ? INFINITY : xr_f;
                     r[1] = xo_hi;
-                    r[6] = (float)x[q];
+                    r[6] = xl_f;
                     r[7] = Tc;
                     r[8] = (float)(xo - (double)xo_hi);
                     for (int c = 0; c < 4; ++c) {
-                        const float hi = (float)cs[c];
-                        r[2 + c] = hi;
-                        r[9 + c] = (float)(cs[c] - (double)hi);
+                        r[2 + c] = chi[c];
+                        r[9 + c] = any_hard ? (float)(cs[c] - (double)chi[c]) : 0.f;
                     }
                     r[13] = r[14] = r[15] = 0.f;
                 }
