@@ -138,9 +138,10 @@ namespace lisa {
 //   int32 status[S] | int32 nint[S*nsp] | int32 route_count, route_list[S] | rec[S][nsp][kmax+1]
 //   | float2 hull[S]
 // each region starting on a 256-byte boundary.  route_list holds, in no particular order, the
-// states the FP32 path sends to the compensated kernel; hull[s] = (lowest left end, highest right
-// end) in x of state s's ill-conditioned intervals, (+inf, -inf) when it has none (both unused
-// in FP64 mode).
+// states the FP32 path sends to the compensated kernel (a record for inspection: the likelihood
+// call finds them by their status bit and builds its own work list); hull[s] = (lowest left end,
+// highest right end) in x of state s's ill-conditioned intervals, (+inf, -inf) when it has none
+// (both unused in FP64 mode).
 inline size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 struct SplineLayout {
     size_t off_status, off_nint, off_route, off_rec, off_hull, bytes;

@@ -20,10 +20,11 @@
 // runs of 32 bins and then in FP64; the constant -C sum nu - sum nu ln P is added in FP64 at the
 // end.
 //
-// States whose spline intervals are too ill-conditioned for FP32 (setup flags them: large
-// overshoots between close knots, |P| up to tens of decades for prior draws) are skipped here
-// and evaluated by the compensated kernel: float-float Horner sums and the per-bin term in the
-// log domain, so any exponent range is handled.
+// Bins in a spline interval too ill-conditioned for FP32 (the setup flags such intervals and
+// routes their states: large overshoots between close knots, |P| up to tens of decades for prior
+// draws) are masked here and evaluated by the compensated kernel, from a per-call work list of
+// the tiles they overlap: float-float Horner sums and the per-bin term in the log domain, so any
+// exponent range is handled.
 #include <cmath>
 #include <mutex>
 
@@ -183,7 +184,7 @@ __device__ __forceinline__ float bin_x(const float* __restrict__ rec32, int64_t 
 // One warp per state.  For a state the spline setup routed to the compensated kernel, the warp
 // also finds the tiles that overlap the x-extent [h.x, h.y) of its ill-conditioned intervals --
 // tile t with first-bin x < h.y and last-bin x >= h.x, a contiguous range because x increases
-// with the bin -- and appends {state, first tile, first unit, tiles} to the work list.
+// with the bin -- and appends its entry (RobustEntry) to the work list.
 __global__ void state_prep_kernel(int S, const double* __restrict__ theta, StateParams* __restrict__ prm,
                                   const int32_t* __restrict__ sstat, const float2* __restrict__ hull,
                                   const int32_t* __restrict__ state_ds, const DatasetDev* __restrict__ ds,
@@ -601,9 +602,10 @@ __device__ __forceinline__ ff inv_plus_log(ff lS, float nu, double& far) {
     return ff{0.f, 0.f};
 }
 
-// Compensated kernel staging: each warp copies its tile in chunks of kRobChunk bins (pair-block
-// table plus the low parts of x and ell) into its own shared-memory slice with coalesced loads,
-// then evaluates the chunk from shared memory.
+// Compensated kernel staging: each warp stages its tile in chunks of kRobChunk bins into its own
+// shared-memory slice (the pair-block table by one bulk asynchronous copy, the low parts of x and
+// ell by lane loads), then evaluates the chunk from shared memory.  8 warps per CTA: two CTAs
+// fill an SM's shared memory (and registers), 16 warps.
 constexpr int kRobWarps = 8;
 constexpr int kRobChunk = 256;                                    // even
 constexpr int kRobChunkF4 = kRobChunk / 2 * (kPairRec / 4);       // float4 of table per chunk
@@ -688,7 +690,7 @@ __device__ __forceinline__ void robust_bin(const float* __restrict__ tb, int i, 
 }
 
 // One warp per unit (routed state, tile) of the work list the state-parameter kernel built, on a
-// persistent grid.  As soon as the warp knows its tile it starts one bulk asynchronous copy of
+// persistent grid, units assigned statically (warp w takes units w, w + warps, ...).  As soon as the warp knows its tile it starts one bulk asynchronous copy of
 // the tile's first chunk of the pair-block table into its shared-memory slice; meanwhile it
 // locates each spline's interval at the tile's first bin with one ballot over the interval right
 // ends (lane k holds interval k) and loads the low parts of x and ell of the chunk (each lane
