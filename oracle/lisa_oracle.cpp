@@ -16,7 +16,7 @@
 //   Akima slopes and coefficients ...... Appendix A
 //   per-bin Wishart term, bin sum ...... Sec. III.D (Wishart log-density, sum over bins)
 //
-// Readings taken where the paper is ambiguous or garbled (all also listed in the design doc):
+// Readings taken where the paper is ambiguous or garbled:
 //   R1  covariance: C_c = S_c (the printed factor 1/2 is dropped; the periodogram is normalised
 //       to the one-sided PSD), so the per-bin term is -nu * sum_c (P_c/S_c + ln S_c).
 //   R2  TDI prefactor: default exactly as printed, sin^2(u) * sin^4(u); tdi_form=1 selects
