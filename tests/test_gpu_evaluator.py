@@ -1,0 +1,44 @@
+"""The preallocated Evaluator (the path bench.py times): device-resident steps, the two captured
+CUDA graphs (FP32) and the end-to-end call from pinned host buffers all give the same log L,
+bit for bit (the reductions are deterministic), and that log L agrees with the oracle."""
+import numpy as np
+import pytest
+
+from paper_2507_06300_gb300 import synth
+from tests._workloads import fp32_tolerance, oracle_batched
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("precision", [1, 0])
+def test_evaluator_step_graph_and_host_paths_agree(precision):
+    import torch
+    from paper_2507_06300_gb300 import binding as B
+    wl = synth.workload("small_ae")
+    P, L_or, St_or = oracle_batched(wl)
+    ds = B.Dataset.from_workload(wl, P)
+    count, x, w, kmax, kind = B.knots_to_device(wl.knots)
+    theta = torch.as_tensor(wl.theta, device="cuda")
+    ev = B.Evaluator(ds, kmax, kind, precision)
+    ev.load(theta, count, x, w)
+    stepped = ev.step().cpu().numpy().copy()
+    replayed = stepped
+    if precision == 0:                                   # the FP32 path is the one bench.py captures
+        ev.capture()
+        ev.out.fill_(0.0)
+        replayed = ev.replay().cpu().numpy().copy()
+    pin = lambda t: t.cpu().pin_memory()
+    h_out = torch.empty(wl.n_states, dtype=torch.float64).pin_memory()
+    ev.out.fill_(0.0)
+    ev.theta.zero_()                                     # the host call must bring the inputs in
+    got = ev.loglike_host(pin(theta), pin(count), pin(x), pin(w), h_out).numpy().copy()
+    np.testing.assert_array_equal(replayed, stepped)
+    np.testing.assert_array_equal(got, stepped)
+    ok = St_or == 0
+    assert np.array_equal(np.isneginf(stepped), ~ok)
+    if precision == 1:
+        np.testing.assert_allclose(stepped[ok], L_or[ok], rtol=1e-12, atol=0)
+    else:
+        tol = fp32_tolerance(L_or, wl, P)
+        assert np.all(np.abs(stepped[ok] - L_or[ok]) <= tol[ok])
+    ds.close()
