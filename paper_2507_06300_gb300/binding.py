@@ -399,7 +399,8 @@ class Evaluator:
     ``step()`` runs lisa_spline_setup + lisa_psd_loglike on device-resident inputs (the MCMC
     inner loop when the sampler lives on the GPU); ``loglike_host()`` is the end-to-end call of a
     host-side sampler: pinned host inputs are copied to the device, evaluated, and log L is copied
-    back into pinned host memory.  ``capture()`` records step() into a CUDA graph."""
+    back into pinned host memory.  ``capture()`` records step() into a CUDA graph;
+    ``capture_host()`` records the whole host call (copies included) into one."""
 
     def __init__(self, dataset: Dataset, kmax: int, kind: int = AKIMA, precision: int = FP32):
         torch = _torch()
@@ -456,19 +457,44 @@ class Evaluator:
         self.g_ll.replay()
         return self.out
 
-    def loglike_host(self, theta, count, x, w, out):
-        """End-to-end: pinned host tensors in (theta [S,5] f64, count [S,nsp] i32, x, w f64),
-        log L written into the pinned host tensor ``out`` [S]; returns ``out`` after the copy."""
-        torch = _torch()
+    def _host_step(self, theta, count, x, w, out, eager=False):
         self.theta.copy_(theta, non_blocking=True)
         self.count.copy_(count, non_blocking=True)
         self.x.copy_(x, non_blocking=True)
         self.w.copy_(w, non_blocking=True)
-        if self.graph:
+        if self.graph and not eager:
             self.replay()
         else:
             self.step()
         out.copy_(self.out, non_blocking=True)
+
+    def capture_host(self, theta, count, x, w, out):
+        """Captures the whole end-to-end call for these pinned host tensors as one CUDA graph:
+        the copies in, spline setup, log-likelihood and the copy of log L into ``out``.  Later
+        ``loglike_host`` calls with the same tensors replay it (one launch); the copies read
+        whatever the tensors hold at that time, so a sampler refills them in place each step."""
+        torch = _torch()
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            self._host_step(theta, count, x, w, out, eager=True)   # warm (kernel attributes set outside capture)
+        torch.cuda.current_stream().wait_stream(s)
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            self._host_step(theta, count, x, w, out, eager=True)
+        self.g_host, self.host_args = g, (theta, count, x, w, out)
+        return self
+
+    def loglike_host(self, theta, count, x, w, out):
+        """End-to-end: pinned host tensors in (theta [S,5] f64, count [S,nsp] i32, x, w f64),
+        log L written into the pinned host tensor ``out`` [S]; returns ``out`` after the copy."""
+        torch = _torch()
+        held = getattr(self, "host_args", None)
+        if held is not None and all(a is b for a, b in zip(held, (theta, count, x, w, out))):
+            self.g_host.replay()
+        else:
+            self._host_step(theta, count, x, w, out)
         torch.cuda.current_stream().synchronize()
         return out
 

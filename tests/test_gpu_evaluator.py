@@ -42,3 +42,29 @@ def test_evaluator_step_graph_and_host_paths_agree(precision):
         tol = fp32_tolerance(L_or, wl, P)
         assert np.all(np.abs(stepped[ok] - L_or[ok]) <= tol[ok])
     ds.close()
+
+
+def test_captured_host_call_copies_fresh_inputs_every_replay():
+    import torch
+    from paper_2507_06300_gb300 import binding as B
+    wl = synth.workload("small_ae")
+    P, _, _ = oracle_batched(wl)
+    ds = B.Dataset.from_workload(wl, P)
+    count, x, w, kmax, kind = B.knots_to_device(wl.knots)
+    theta = torch.as_tensor(wl.theta, device="cuda")
+    ev = B.Evaluator(ds, kmax, kind, 0).capture()
+    pin = lambda t: t.cpu().pin_memory()
+    h_theta, h_count, h_x, h_w = pin(theta), pin(count), pin(x), pin(w)
+    h_out = torch.empty(wl.n_states, dtype=torch.float64).pin_memory()
+    ev.capture_host(h_theta, h_count, h_x, h_w, h_out)
+    first = ev.loglike_host(h_theta, h_count, h_x, h_w, h_out).numpy().copy()
+    ev.load(theta, count, x, w)
+    np.testing.assert_array_equal(first, ev.replay().cpu().numpy())
+    # new values in the same pinned buffers: the replay must read them
+    h_theta[:, 0] *= 1.25
+    h_w[:, 0, 0] += 0.05
+    second = ev.loglike_host(h_theta, h_count, h_x, h_w, h_out).numpy().copy()
+    ev.load(h_theta.cuda(), count, x, h_w.cuda())
+    np.testing.assert_array_equal(second, ev.replay().cpu().numpy())
+    assert not np.array_equal(first, second)
+    ds.close()
