@@ -407,15 +407,35 @@ class Evaluator:
         self.ds, self.kmax, self.kind, self.precision = dataset, int(kmax), int(kind), int(precision)
         S, nsp = dataset.n_states, dataset.n_splines
         dev = "cuda"
-        self.theta = torch.zeros((S, N_THETA), dtype=torch.float64, device=dev)
-        self.count = torch.zeros((S, nsp), dtype=torch.int32, device=dev)
-        self.x = torch.zeros((S, nsp, self.kmax), dtype=torch.float64, device=dev)
-        self.w = torch.zeros((S, nsp, self.kmax + 2), dtype=torch.float64, device=dev)
+        # the inputs live in one device block (and, for host callers, one pinned host block with
+        # the same layout, see host_inputs), so the end-to-end call copies them in one transfer
+        shapes = [((S, N_THETA), torch.float64), ((S, nsp), torch.int32), ((S, nsp, self.kmax), torch.float64),
+                  ((S, nsp, self.kmax + 2), torch.float64)]
+        self._in_layout, off = [], 0
+        for shape, dt in shapes:
+            n = int(np.prod(shape)) * torch.empty((), dtype=dt).element_size()
+            self._in_layout.append((off, n, shape, dt))
+            off += (n + 255) // 256 * 256
+        self.inputs = torch.zeros(max(off, 256), dtype=torch.uint8, device=dev)
+        self.theta, self.count, self.x, self.w = self._views(self.inputs)
+        self.h_inputs = None
         self.buf = torch.empty(dataset.spline_buf_bytes(kmax, precision), dtype=torch.uint8, device=dev)
         self.status = torch.empty(S, dtype=torch.int32, device=dev)
         self.ws = torch.empty(dataset.workspace_bytes(kmax, precision), dtype=torch.uint8, device=dev)
         self.out = torch.empty(S, dtype=torch.float64, device=dev)
         self.graph = None
+
+    def _views(self, block):
+        return tuple(block[o:o + n].view(dt).view(shape) for o, n, shape, dt in self._in_layout)
+
+    def host_inputs(self):
+        """Pinned host tensors (theta, count, x, w) laid out like the device inputs: a host sampler
+        that writes its proposals into them gets them to the device in one copy per call."""
+        torch = _torch()
+        if self.h_inputs is None:
+            self.h_inputs = torch.zeros(self.inputs.numel(), dtype=torch.uint8).pin_memory()
+            self.h_views = self._views(self.h_inputs)
+        return self.h_views
 
     def load(self, theta, count, x, w):
         self.theta.copy_(theta)
@@ -458,10 +478,14 @@ class Evaluator:
         return self.out
 
     def _host_step(self, theta, count, x, w, out, eager=False):
-        self.theta.copy_(theta, non_blocking=True)
-        self.count.copy_(count, non_blocking=True)
-        self.x.copy_(x, non_blocking=True)
-        self.w.copy_(w, non_blocking=True)
+        mine = self.h_inputs is not None and all(a is b for a, b in zip(self.h_views, (theta, count, x, w)))
+        if mine:
+            self.inputs.copy_(self.h_inputs, non_blocking=True)
+        else:
+            self.theta.copy_(theta, non_blocking=True)
+            self.count.copy_(count, non_blocking=True)
+            self.x.copy_(x, non_blocking=True)
+            self.w.copy_(w, non_blocking=True)
         if self.graph and not eager:
             self.replay()
         else:

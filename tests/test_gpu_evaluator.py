@@ -68,3 +68,31 @@ def test_captured_host_call_copies_fresh_inputs_every_replay():
     np.testing.assert_array_equal(second, ev.replay().cpu().numpy())
     assert not np.array_equal(first, second)
     ds.close()
+
+
+def test_host_input_block_is_copied_in_one_transfer_with_the_same_result():
+    import torch
+    from paper_2507_06300_gb300 import binding as B
+    wl = synth.workload("small_ae")
+    P, _, _ = oracle_batched(wl)
+    ds = B.Dataset.from_workload(wl, P)
+    count, x, w, kmax, kind = B.knots_to_device(wl.knots)
+    theta = torch.as_tensor(wl.theta, device="cuda")
+    ev = B.Evaluator(ds, kmax, kind, 0).capture()
+    ev.load(theta, count, x, w)
+    ref = ev.replay().cpu().numpy().copy()
+    h = ev.host_inputs()
+    for dst, src in zip(h, (theta, count, x, w)):
+        dst.copy_(src.cpu())
+    h_out = torch.empty(wl.n_states, dtype=torch.float64).pin_memory()
+    ev.inputs.zero_()
+    np.testing.assert_array_equal(ev.loglike_host(*h, h_out).numpy(), ref)      # eager, one copy
+    ev.capture_host(*h, h_out)
+    ev.inputs.zero_()
+    np.testing.assert_array_equal(ev.loglike_host(*h, h_out).numpy(), ref)      # captured
+    h[0][:, 1] *= 0.8
+    got = ev.loglike_host(*h, h_out).numpy().copy()
+    ev.load(h[0].cuda(), count, x, w)
+    np.testing.assert_array_equal(got, ev.replay().cpu().numpy())
+    assert not np.array_equal(got, ref)
+    ds.close()
