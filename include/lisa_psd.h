@@ -10,7 +10,7 @@
  *            + S_h,cc(f | A, n)        10^{P_h(log10 f)}                              (2)
  *
  * (1) is the per-bin complex-Wishart log-density -tr(C^-1 Y) - nu log|C| with Y = nu P and a
- * diagonal covariance C = diag(S_AA, S_EE, S_TT), summed over bins (Sec. III.D); the printed
+ * diagonal covariance C = diag(S_AA, S_EE, S_TT), summed over bins (Sec. III.C); the printed
  * factor 1/2 in C is not applied (the periodogram is normalised to the one-sided PSD,
  * Sec. III.A), and nu = 1 is the Whittle likelihood.  (2) is Eq. (splines) of Sec. III.A with
  * the noise template of Eq. (noise_tdi) and the SGWB template of Eq. (pl) / Eq. (Sh).  The
@@ -226,7 +226,7 @@ lisa_status lisa_model_psd(const lisa_data* data, const lisa_params* params,
                            double* psd_dev, lisa_stream_t stream);
 
 /* ---- data preparation ------------------------------------------------------------------------
- * The inputs of lisa_data_create from frequency-domain data (Sec. III.D).  Frequency samples are
+ * The inputs of lisa_data_create from frequency-domain data (Sec. III.C).  Frequency samples are
  * uniform, f_k = f0 + k df (the grid of a discrete Fourier transform), and complex values are
  * interleaved (re, im) FP64 pairs. */
 
@@ -239,7 +239,7 @@ lisa_status lisa_model_psd(const lisa_data* data, const lisa_params* params,
 lisa_status lisa_fd_synthesize(const double* psd_dev, const double* normal_dev, int32_t n_channels,
                                int64_t n_freq, double* d_dev, lisa_stream_t stream);
 
-/* Averaged periodogram (Sec. III.D): bin i holds the frequency samples
+/* Averaged periodogram (Sec. III.C): bin i holds the frequency samples
  * [bin_offset[i], bin_offset[i+1]) and
  *     P_c(f_i) = (1 / n_i) sum_k |d_c(f_k)|^2,   nu_i = n_i,   f_i = f0 + df (b0 + b1 - 1) / 2
  * (the diagonal of the averaged periodogram matrix: the A, E, T covariance is diagonal), so that

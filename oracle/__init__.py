@@ -209,7 +209,7 @@ def model_psd(ds, theta, knots):
 
 
 def loglike(ds, theta, knots):
-    """Sec. III.D log-likelihood for every state: returns (logL [S], status [S])."""
+    """Sec. III.C log-likelihood for every state: returns (logL [S], status [S])."""
     keep1, pa = _problem_args(ds)
     keep2, S, nsp, kmax, kind, sa = _state_args(theta, knots)
     out = np.empty(S)

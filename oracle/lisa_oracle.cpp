@@ -14,7 +14,7 @@
 //   knot layout (edges + in-between) ... Sec. III.A, knot placement scheme
 //   linear fallback ................... Sec. III.A (fewer than two in-between knots)
 //   Akima slopes and coefficients ...... Appendix A
-//   per-bin Wishart term, bin sum ...... Sec. III.D (Wishart log-density, sum over bins)
+//   per-bin Wishart term, bin sum ...... Sec. III.C (Wishart log-density, sum over bins)
 //
 // Readings taken where the paper is ambiguous or garbled:
 //   R1  covariance: C_c = S_c (the printed factor 1/2 is dropped; the periodogram is normalised
@@ -421,7 +421,7 @@ void lo_model_psd(int C, int sgwb_model, int tdi_form, int64_t N, const double* 
     }
 }
 
-// Sec. III.D: log L = sum_i log p(Y(f_i)), log p = -tr(C^-1 Y) - nu log|C| with Y = nu P and
+// Sec. III.C: log L = sum_i log p(Y(f_i)), log p = -tr(C^-1 Y) - nu log|C| with Y = nu P and
 // C = diag(S_c) (reading R1):  log L = -sum_i nu_i sum_c (P_c,i / S_c,i + ln S_c,i).
 void lo_loglike(int C, int sgwb_model, int tdi_form, int64_t N, const double* f, const double* nu,
                 const double* P, const double* R, double x_lo, double x_hi, double f_ref,
@@ -475,8 +475,10 @@ void lo_loglike_grad(int C, int sgwb_model, int tdi_form, int64_t N, const doubl
 }
 
 // As lo_loglike_grad; if gscale is not NULL it also receives, per gradient component, the sum
-// over bins of the absolute values of that component's per-bin contributions (the condition
-// scale of the sum: a backward-stable evaluation errs by a small multiple of eps times it).
+// of the absolute values of the terms that component's sum is made of (the condition scale of
+// the sum: a backward-stable evaluation errs by a small multiple of eps times it).  The terms
+// are one per (bin, channel) for the template parameters and one per bin for the knot
+// parameters (q_i dP(x_i)/d(knot), q_i summed over channels for the SGWB spline).
 void lo_loglike_grad_scaled(int C, int sgwb_model, int tdi_form, int64_t N, const double* f,
                             const double* nu, const double* P, const double* R, double x_lo,
                             double x_hi, double f_ref, int kind, int kmax, int S,

@@ -7,7 +7,7 @@ product package.
   in the frequency domain (Sec. II.D), normalised so that the periodogram is comparable to the
   one-sided PSD (Sec. III.A): d = sqrt(S / 2) (z0 + i z1) with z0, z1 standard normal, so that
   E|d|^2 = S.
-* ``averaged_periodogram`` -- Sec. III.D: the periodogram averaged over the n_i consecutive,
+* ``averaged_periodogram`` -- Sec. III.C: the periodogram averaged over the n_i consecutive,
   non-overlapping frequency samples of bin i, P(f_i) = (1/n_i) sum_k |d(f_k)|^2 (the diagonal of
   d d^dagger: the A, E, T covariance is diagonal), nu_i = n_i degrees of freedom, and f_i the
   centre of the bin.

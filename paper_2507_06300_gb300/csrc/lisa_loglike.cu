@@ -1,5 +1,5 @@
 // Fused likelihood kernels: spline evaluation -> PSD assembly (Eq. splines) -> per-bin
-// Wishart terms -> FP64 reduction over bins (Sec. III.D), for every state at once.
+// Wishart terms -> FP64 reduction over bins (Sec. III.C), for every state at once.
 //
 // FP32 path: the bin records of a work item (a tile of bins of one dataset) are staged into
 // shared memory with one bulk asynchronous copy (cp.async.bulk + mbarrier), double-buffered

@@ -1,4 +1,4 @@
-// Data preparation (Sec. III.D): synthetic frequency-domain data and the averaged periodogram,
+// Data preparation (Sec. III.C): synthetic frequency-domain data and the averaged periodogram,
 // the inputs of lisa_data_create.  Both are streaming kernels bound by HBM bandwidth.
 #include <cmath>
 

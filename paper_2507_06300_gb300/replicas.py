@@ -1,7 +1,7 @@
 """Multi-GPU layout: independent replicas, one process per GPU.
 
 The states of a tempered ensemble, and the datasets of a batch, are independent: the
-log-likelihood of one needs nothing from another (Sec. III.D sums over the bins of one
+log-likelihood of one needs nothing from another (Sec. III.C sums over the bins of one
 dataset for one parameter point).  The path therefore shards with no exchange step: each rank
 evaluates a contiguous block of datasets (or, for a single dataset, of states) on its own GPU
 through the same C ABI.  The only collectives are host-side bookkeeping -- the maximum over

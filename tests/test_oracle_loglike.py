@@ -1,4 +1,4 @@
-"""Pins for the oracle's log-likelihood and gradient (Sec. III.D; Eq. splines).
+"""Pins for the oracle's log-likelihood and gradient (Sec. III.C; Eq. splines).
 
 * Each per-bin term is the log-density of a 1x1 complex Wishart variate, i.e. a Gamma(nu,
   scale S) density of Y = nu P: differences of log L between states must equal differences of
@@ -88,7 +88,7 @@ def test_whittle_scale_maximiser(nu):
 
 @pytest.mark.parametrize("sigma", [1e-3, 7.5, 1e4])
 def test_common_rescaling_shifts_by_log_sigma(sigma):
-    """Sec. III.D: with P and S both multiplied by sigma (noise-only model: amplitudes by
+    """Sec. III.C: with P and S both multiplied by sigma (noise-only model: amplitudes by
     sqrt(sigma)), every ratio P/S is unchanged and log L shifts by exactly -C sum(nu) ln sigma."""
     wl = synth.workload("tiny", sgwb_model=0)
     ds = oracle_dataset(wl)

@@ -1,4 +1,4 @@
-"""Pins of the data-preparation oracle (oracle.prep): Sec. II.D synthesis and the Sec. III.D
+"""Pins of the data-preparation oracle (oracle.prep): Sec. II.D synthesis and the Sec. III.C
 averaged periodogram."""
 import numpy as np
 from scipy import stats
