@@ -63,6 +63,16 @@ lisa_status lisa_pipe_rates(int32_t iters, int32_t reps, double* rates, lisa_str
 lisa_status lisa_data_set_profiling(lisa_data* data, int32_t enable);
 lisa_status lisa_data_kernel_ms(const lisa_data* data, float* ms);
 
+/* Test of the timeout path; no counterpart in the paper.  The fused and compensated likelihood
+ * kernels stage bin tables by asynchronous bulk copies and wait for them on mbarriers with a
+ * bounded number of polls; a wait that runs out raises the workspace's error word (see
+ * lisa_workspace_status), lets the copies already issued land and stops the CTA.
+ * wait_limit (>= 1, default 2^20) sets the number of polls for later calls on `data`;
+ * skip_copies != 0 makes the fused FP32 kernel issue no copies at all, so its first wait runs
+ * out with nothing in flight -- for tests only: the log-likelihoods are then NaN.  Calls already
+ * enqueued are not affected.  Errors: LISA_ERR_NULL, LISA_ERR_VALUE (wait_limit 0). */
+lisa_status lisa_data_set_test_wait(lisa_data* data, int32_t skip_copies, uint32_t wait_limit);
+
 #ifdef __cplusplus
 }
 #endif

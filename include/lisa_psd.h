@@ -206,6 +206,15 @@ lisa_status lisa_psd_loglike(const lisa_data* data, const lisa_params* params,
                              double* loglike_dev, void* workspace_dev, size_t workspace_bytes,
                              lisa_precision precision, lisa_stream_t stream);
 
+/* Device-side status of the most recent lisa_psd_loglike or lisa_psd_loglike_grad call that
+ * used workspace_dev: synchronises `stream` (the stream that call ran on), reads the
+ * workspace's error word and returns LISA_SUCCESS, or LISA_ERR_TIMEOUT when a bounded wait of
+ * the fused or compensated kernel gave up (that call's kernels stopped early and every log L it
+ * wrote is NaN; the CUDA context stays usable).  The likelihood calls themselves are
+ * asynchronous and cannot return a device-side status.  Errors: LISA_ERR_NULL,
+ * LISA_ERR_WORKSPACE (misaligned), LISA_ERR_CUDA. */
+lisa_status lisa_workspace_status(const void* workspace_dev, lisa_stream_t stream);
+
 /* log L and its gradient for every state (hand-written adjoint; the spline coefficients are
  * recomputed from the knots, nothing per bin is stored).  grad_dev
  * [n_states][LISA_N_THETA + n_splines*(2*kmax+2)] (FP64): d log L / d theta (a_oms, a_tm,
@@ -266,12 +275,17 @@ lisa_status lisa_averaged_periodogram(const double* d_dev, int32_t n_channels, i
  *  - The array holds LISA_NOALLOC_SCRATCH_BYTES (4 MiB): 256 bytes plus 8 bytes per
  *    (state, tile) partial sum plus 48 bytes of FP32 parameters and 32 bytes of work list per
  *    state (each region rounded up to 256 bytes), i.e.
- *    lisa_workspace_bytes(data, kmax, precision, 0) must not exceed it (the paper-scale
- *    workload needs about 2.1 MiB at the default 512-bin tiles).  Larger problems get
- *    LISA_ERR_WORKSPACE and nothing is launched; use lisa_psd_loglike for them.
+ *    lisa_workspace_bytes(data, kmax, precision, 0) must not exceed it.  The paper-scale
+ *    workload (131,072 bins, 1,024 states) needs about 2.1 MiB at 512-bin tiles and 3.3 MiB at
+ *    320-bin tiles, but 4.1 MiB at 256-bin tiles, which is rejected: the size depends on the
+ *    tiling (lisa_data_set_tiling).  Larger problems get LISA_ERR_WORKSPACE and nothing is
+ *    launched; use lisa_psd_loglike for them.
  *  - Every GPU that loads the library holds the array until the process exits.
- *  - The first call on each device looks the array's device address up (with that device
- *    current); make that first call before any stream capture.  Later calls only launch.
+ *  - The device that holds `data` must be current: the array exists once per device, and a
+ *    call made with another device current returns LISA_ERR_VALUE.
+ *  - Every call looks the array's device address up (cudaGetSymbolAddress, which enqueues
+ *    nothing).  The first call on a device may load the library's device code there, so make
+ *    it before any stream capture.
  *  - All calls on a device share the one array, and each call overwrites it (the error flag is
  *    cleared on the stream first).  Two calls whose kernels overlap on the GPU race on it:
  *    serialise them (same stream, or events).

@@ -63,7 +63,7 @@ EXPORTS = ["lisa_data_create", "lisa_data_destroy", "lisa_data_get_info", "lisa_
            "lisa_spline_buf_bytes", "lisa_spline_setup", "lisa_workspace_bytes", "lisa_psd_loglike",
            "lisa_psd_loglike_grad", "lisa_model_psd", "lisa_psd_loglike_noalloc", "lisa_status_string",
            "lisa_pipe_rates", "lisa_data_set_profiling", "lisa_data_kernel_ms", "lisa_fd_synthesize",
-           "lisa_averaged_periodogram"]
+           "lisa_averaged_periodogram", "lisa_workspace_status", "lisa_data_set_test_wait"]
 PIPE_OPS = ("ex2", "rcp", "lg2_ex2", "ffma", "ffma2", "dfma")   # order of lisa_pipe_op
 NOALLOC_SCRATCH_BYTES = 4 * 1024 * 1024
 
@@ -129,6 +129,10 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         lib.lisa_averaged_periodogram.argtypes = [_c_vp, _c_i32, _c_i64, _c_dbl, _c_dbl, _c_vp, _c_i64, _c_vp, _c_vp,
                                                   _c_vp, _c_vp]
         lib.lisa_averaged_periodogram.restype = S
+        lib.lisa_workspace_status.argtypes = [_c_vp, _c_vp]
+        lib.lisa_workspace_status.restype = S
+        lib.lisa_data_set_test_wait.argtypes = [_c_vp, _c_i32, ctypes.c_uint32]
+        lib.lisa_data_set_test_wait.restype = S
         _lib = lib
         return lib
 
@@ -302,6 +306,16 @@ class Dataset:
                                        out.data_ptr(), workspace.data_ptr(), workspace.numel(), int(precision),
                                        _stream_handle(stream)), "lisa_psd_loglike")
         return out
+
+    def workspace_status(self, workspace, stream=None):
+        """``lisa_workspace_status``: synchronises the stream and returns the device-side status
+        of the last likelihood call that used ``workspace`` (0, or 8 = LISA_ERR_TIMEOUT)."""
+        return int(load().lisa_workspace_status(workspace.data_ptr(), _stream_handle(stream)))
+
+    def set_test_wait(self, skip_copies=False, wait_limit=1 << 20):
+        """``lisa_data_set_test_wait`` (tests of the timeout path only)."""
+        _check(load().lisa_data_set_test_wait(self._h, int(bool(skip_copies)), int(wait_limit)),
+               "lisa_data_set_test_wait")
 
     def psd_loglike_noalloc(self, theta, buf, kmax, precision=FP32, out=None, stream=None):
         """``lisa_psd_loglike_noalloc``: the same result as ``psd_loglike`` for callers that cannot
@@ -477,6 +491,15 @@ class Evaluator:
         self.g_ll.replay()
         return self.out
 
+    @staticmethod
+    def _require_pinned(*ts):
+        # asynchronous copies from pageable memory silently become synchronous (eager calls) or
+        # fail partway through a graph capture: the host path takes pinned tensors only
+        for t in ts:
+            if t.device.type != "cpu" or not t.is_pinned():
+                raise LisaError("host tensors of the end-to-end call must be pinned CPU tensors "
+                                "(torch.Tensor.pin_memory(), or the views host_inputs() returns)")
+
     def _host_step(self, theta, count, x, w, out, eager=False):
         mine = self.h_inputs is not None and all(a is b for a, b in zip(self.h_views, (theta, count, x, w)))
         if mine:
@@ -498,6 +521,7 @@ class Evaluator:
         ``loglike_host`` calls with the same tensors replay it (one launch); the copies read
         whatever the tensors hold at that time, so a sampler refills them in place each step."""
         torch = _torch()
+        self._require_pinned(theta, count, x, w, out)
         s = torch.cuda.Stream()
         s.wait_stream(torch.cuda.current_stream())
         with torch.cuda.stream(s):
@@ -514,6 +538,7 @@ class Evaluator:
         """End-to-end: pinned host tensors in (theta [S,5] f64, count [S,nsp] i32, x, w f64),
         log L written into the pinned host tensor ``out`` [S]; returns ``out`` after the copy."""
         torch = _torch()
+        self._require_pinned(theta, count, x, w, out)
         held = getattr(self, "host_args", None)
         if held is not None and all(a is b for a, b in zip(held, (theta, count, x, w, out))):
             self.g_host.replay()

@@ -1,10 +1,13 @@
 // Dataset object: validation, upload, the per-bin FP64 precompute (templates of Sec. II.B and
 // Sec. II.C normalised by the periodogram) and the work decomposition of the fused kernels.
 #include <algorithm>
+#include <queue>
+#include <utility>
 #include <cmath>
 #include <new>
 
 #include "lisa_internal.cuh"
+#include "lisa_peaks.h"
 
 namespace lisa {
 
@@ -169,7 +172,8 @@ int pow2ceil(int v) {
 // min(states_per_cta, next power of two >= states of the dataset)) times tiles of tile_bins bins.
 // With many items per CTA the list is in (dataset, chunk, tile) order and the fused kernel gives
 // each CTA a contiguous, cost-balanced block of it, so a CTA mostly walks consecutive tiles of
-// the same states; otherwise it is in (dataset, tile, chunk) order and CTAs stride over it.
+// the same states; otherwise the items are assigned longest-first (knot-aware cost) to the
+// least-loaded CTA and each CTA's share is laid out contiguously.
 lisa_status rebuild_work(lisa_data* d) {
     const lisa_tiling& t = d->tiling;
     std::vector<WorkItem> items;
@@ -203,9 +207,8 @@ lisa_status rebuild_work(lisa_data* d) {
     const int grid = std::max(1, d->n_sm * std::max(occ, 1));
     // contiguous blocks pay off when a CTA has many items and each thread takes few bins from an
     // item (small state chunks: the per-item interval search dominates); with a few items per CTA
-    // or wide items, striding over a (dataset, tile,
-    // chunk)-ordered list mixes tiles from the whole band into every CTA, which balances better
-    // than cutting a handful of tiles by cost
+    // or wide items, cutting a handful of tiles by cost balances poorly, and a longest-first
+    // assignment of the items does better
     double thread_bins = 0.0, weight = 0.0;   // bins one thread takes from an item, state-weighted
     for (const WorkItem& w : items) {
         thread_bins += (double)w.nb * w.sc / kThreads32 * w.ns;
@@ -213,40 +216,69 @@ lisa_status rebuild_work(lisa_data* d) {
     }
     d->fblocks = items.size() >= (size_t)kBlockItemsPerCta * (size_t)grid &&
                  thread_bins < kBlockThreadBins * weight;
-    if (!d->fblocks) {
-        // (dataset, tile, chunk) order, larger items first so that the static stride ends evenly
-        std::stable_sort(items.begin(), items.end(), [](const WorkItem& a, const WorkItem& b) {
-            if (a.ds != b.ds) return a.ds < b.ds;
-            if (a.tile != b.tile) return a.tile < b.tile;
-            return a.s0 < b.s0;
-        });
-        std::stable_sort(items.begin(), items.end(), [](const WorkItem& a, const WorkItem& b) {
-            return (int64_t)a.nb * a.ns > (int64_t)b.nb * b.ns;
-        });
-    }
-    // contiguous blocks of the work list for the fused kernel's persistent grid, cut so that every
-    // CTA gets the same knot-aware cost (item boundaries at cost midpoints); used when there are at
-    // least kBlockItemsPerCta items per CTA
+    // knot-aware cost of each item
     auto x_at = [&](int k, int64_t b) {   // log10 f of bin b of dataset k (b a multiple of
         const double* xs = d->h_xs.data() + d->h_xs_off[k];   // kXsStride, or past the end)
         const int64_t nxs = d->h_xs_off[k + 1] - d->h_xs_off[k];
         const int64_t j = b / kXsStride;
         return j < nxs - 1 ? xs[j] : xs[nxs - 1];
     };
-    std::vector<double> pre(items.size() + 1, 0.0);
-    for (size_t q = 0; q < items.size(); ++q) {
-        const WorkItem& w = items[q];
+    auto cost_of = [&](const WorkItem& w) {
         const DatasetDev& D = d->h_ds[w.ds];
         const int64_t a = w.bin0 - D.bin0, e = a + w.nb;
         const double dx = D.nbins > 0 ? x_at(w.ds, e) - x_at(w.ds, a) : 0.0;
-        pre[q + 1] = pre[q] + ((double)w.nb + kKnotBinsPerDecade * dx) * (double)w.ns;
-    }
+        return ((double)w.nb + kKnotBinsPerDecade * dx) * (double)w.ns;
+    };
     std::vector<int32_t> cta_first((size_t)grid + 1, 0);
-    size_t q = 0;
-    for (int b = 1; b <= grid; ++b) {
-        const double target = pre.back() * (double)b / (double)grid;
-        while (q < items.size() && 0.5 * (pre[q] + pre[q + 1]) < target) ++q;
-        cta_first[b] = (int32_t)(b == grid ? items.size() : q);
+    if (d->fblocks) {
+        // contiguous blocks of the (dataset, chunk, tile)-ordered list, cut so that every CTA gets
+        // the same cost (item boundaries at cost midpoints)
+        std::vector<double> pre(items.size() + 1, 0.0);
+        for (size_t q = 0; q < items.size(); ++q) pre[q + 1] = pre[q] + cost_of(items[q]);
+        size_t q = 0;
+        for (int b = 1; b <= grid; ++b) {
+            const double target = pre.back() * (double)b / (double)grid;
+            while (q < items.size() && 0.5 * (pre[q] + pre[q + 1]) < target) ++q;
+            cta_first[b] = (int32_t)(b == grid ? items.size() : q);
+        }
+    } else {
+        // few items per CTA: longest-processing-time-first assignment (costliest item to the
+        // least loaded CTA), then each CTA's items laid out contiguously in (dataset, chunk,
+        // tile) order, so that consecutive tiles of the same states still carry their intervals
+        std::vector<double> cost(items.size());
+        std::vector<size_t> order(items.size());
+        for (size_t q = 0; q < items.size(); ++q) {
+            cost[q] = cost_of(items[q]);
+            order[q] = q;
+        }
+        std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t b) { return cost[a] > cost[b]; });
+        using Load = std::pair<double, int>;
+        std::priority_queue<Load, std::vector<Load>, std::greater<Load>> heap;
+        for (int c = 0; c < grid; ++c) heap.push({0.0, c});
+        std::vector<int> owner(items.size());
+        for (size_t q : order) {
+            Load l = heap.top();
+            heap.pop();
+            owner[q] = l.second;
+            l.first += cost[q];
+            heap.push(l);
+        }
+        std::vector<size_t> perm(items.size());
+        for (size_t q = 0; q < items.size(); ++q) perm[q] = q;
+        std::stable_sort(perm.begin(), perm.end(), [&](size_t a, size_t b) {
+            if (owner[a] != owner[b]) return owner[a] < owner[b];
+            const WorkItem &x = items[a], &y = items[b];
+            if (x.ds != y.ds) return x.ds < y.ds;
+            if (x.s0 != y.s0) return x.s0 < y.s0;
+            return x.tile < y.tile;
+        });
+        std::vector<WorkItem> sorted(items.size());
+        for (size_t q = 0; q < items.size(); ++q) {
+            sorted[q] = items[perm[q]];
+            ++cta_first[(size_t)owner[perm[q]] + 1];
+        }
+        for (int c = 0; c < grid; ++c) cta_first[c + 1] += cta_first[c];
+        items.swap(sorted);
     }
     d->fgrid = grid;
     d->rgrid = std::max(1, d->n_sm * robust_ctas_per_sm(d));
@@ -463,6 +495,14 @@ lisa_status lisa_data_set_profiling(lisa_data* d, int32_t enable) {
     }
     d->prof_on = enable != 0;
     d->prof_valid = false;
+    return LISA_SUCCESS;
+}
+
+lisa_status lisa_data_set_test_wait(lisa_data* d, int32_t skip_copies, uint32_t wait_limit) {
+    if (!d) return LISA_ERR_NULL;
+    if (wait_limit < 1) return LISA_ERR_VALUE;
+    d->test_skip_copies = skip_copies != 0;
+    d->wait_limit = wait_limit;
     return LISA_SUCCESS;
 }
 

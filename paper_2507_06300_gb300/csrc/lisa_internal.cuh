@@ -46,6 +46,7 @@ constexpr int kRouted = 1 << 16;        // internal status bit: state routed to 
 constexpr int kUserBits = 0xffff;       // LISA_STATE_* bits
 constexpr int kStatusNonfinite = LISA_STATE_NONFINITE;
 constexpr unsigned kWaitLimit = 1u << 20;   // bounded spin on an mbarrier (then give up)
+constexpr int kErrTimeout = 1;              // workspace error word: a bounded wait gave up
 constexpr int kMaxTileBins = 2048;          // 2 staged tiles x 48 B/bin must fit in 227 KB
 constexpr int kAdjBins = 2048;              // bins per (state, range) in the adjoint
 // Work balance of the fused kernel: an item (a tile of bins x a chunk of states) costs
@@ -118,7 +119,7 @@ struct lisa_data {
     int32_t* d_cta_first = nullptr;  // fused kernel: first item of each CTA (fgrid + 1 entries)
     int32_t fgrid = 0;               // CTAs of the fused FP32 launch
     int32_t rgrid = 0;               // CTAs of the compensated kernel's persistent launch
-    bool fblocks = false;            // contiguous cost-balanced blocks (else every fgrid-th item)
+    bool fblocks = false;            // contiguous cost-balanced blocks (else longest-first assignment)
     lisa::AdjUnit* d_adj_units = nullptr;
     int64_t n_adj_units = 0;
     int64_t* d_adj_prefix = nullptr; // [n_states] adjoint ranges of all earlier states
@@ -130,23 +131,31 @@ struct lisa_data {
     cudaEvent_t prof_ev[4] = {nullptr, nullptr, nullptr, nullptr};
     bool prof_on = false;
     mutable bool prof_valid = false;
+    // polls of a bounded mbarrier wait before the fused and compensated kernels give up, and the
+    // test-only switch that makes the fused kernel issue no copies (lisa_data_set_test_wait)
+    uint32_t wait_limit = lisa::kWaitLimit;
+    int32_t test_skip_copies = 0;
 };
 
 namespace lisa {
 
 // Spline buffer layout (64-byte records in both precisions):
 //   int32 status[S] | int32 nint[S*nsp] | int32 route_count, route_list[S] | rec[S][nsp][kmax+1]
-//   | float2 hull[S]
-// each region starting on a 256-byte boundary.  route_list holds, in no particular order, the
+//   | float2 hull[S] | float xr[S][nsp][kxr_stride(kmax)]
+// each region starting on a 256-byte boundary.  xr (FP32 mode) repeats each interval's right end
+// contiguously, +inf for the last interval and the padding, so that the interval holding x is
+// the number of entries <= x, found from a few independent 16-byte loads.  route_list holds, in no particular order, the
 // states the FP32 path sends to the compensated kernel (a record for inspection: the likelihood
 // call finds them by their status bit and builds its own work list); hull[s] = (lowest left end,
 // highest right end) in x of state s's ill-conditioned intervals, (+inf, -inf) when it has none
 // (both unused in FP64 mode).
 inline size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 struct SplineLayout {
-    size_t off_status, off_nint, off_route, off_rec, off_hull, bytes;
+    size_t off_status, off_nint, off_route, off_rec, off_hull, off_kxr, bytes;
 };
 constexpr size_t kRecBytes = 64;
+// entries per spline of the right-end table: kmax + 1 rounded up to a multiple of 4
+__host__ __device__ inline int kxr_stride(int kmax) { return (kmax + 4) & ~3; }
 inline SplineLayout spline_layout(int64_t S, int nsp, int kmax) {
     SplineLayout L;
     L.off_status = 0;
@@ -154,7 +163,8 @@ inline SplineLayout spline_layout(int64_t S, int nsp, int kmax) {
     L.off_route = L.off_nint + align256(sizeof(int32_t) * (size_t)S * nsp);
     L.off_rec = L.off_route + align256(sizeof(int32_t) * ((size_t)S + 1));
     L.off_hull = L.off_rec + align256((size_t)S * nsp * (kmax + 1) * kRecBytes);
-    L.bytes = L.off_hull + sizeof(float) * 2 * (size_t)S;
+    L.off_kxr = L.off_hull + align256(sizeof(float) * 2 * (size_t)S);
+    L.bytes = L.off_kxr + sizeof(float) * (size_t)S * nsp * kxr_stride(kmax);
     return L;
 }
 

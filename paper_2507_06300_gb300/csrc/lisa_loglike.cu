@@ -26,7 +26,6 @@
 // the tiles they overlap: float-float Horner sums and the per-bin term in the log domain, so any
 // exponent range is handled.
 #include <cmath>
-#include <mutex>
 
 #include "lisa_math.cuh"
 
@@ -69,11 +68,11 @@ __device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, unsign
         "l"(src), "r"(bytes), "r"(smem_addr(bar))
         : "memory");
 }
-// Bounded wait: gives up after kWaitLimit polls and raises the error flag.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity, int* err) {
-    for (unsigned it = 0; it < kWaitLimit; ++it)
+// Bounded wait: true once the phase with this parity has completed, false after `limit` polls
+// (the caller raises the error flag and stops issuing work).
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity, unsigned limit) {
+    for (unsigned it = 0; it < limit; ++it)
         if (mbar_try_wait(bar, parity)) return true;
-    atomicExch(err, 1);
     return false;
 }
 
@@ -139,10 +138,14 @@ __device__ __forceinline__ float bin_term32(const float* __restrict__ tb, int i,
     return term_from_S<C>(S, nu);
 }
 
-// Safe range of the unguarded pair form: the channel product within 2^(+-99), so that its
-// reciprocal and log2 are accurate and normal.  An overflowing reciprocal-sum numerator (one
-// channel far below the others) makes the chunk sum infinite, which is checked as well.
-constexpr float kPairLg2Max = 99.0f;
+// Safe range of the unguarded pair form.  Above 2^126 the reciprocal of the channel product is
+// subnormal and flushed to zero, which would silently drop sum_c 1/S_c: the caller tracks the
+// largest log2 of the product and redoes the chunk on the guarded path past this bound.  Below,
+// every failure is loud: a product under 2^-126 is flushed to zero (infinite reciprocal, log2 =
+// -inf), and an overflowing reciprocal-sum numerator or term is infinite, so the non-finite
+// chunk sum that the caller also checks catches them; a normal product has an accurate
+// reciprocal and log2.
+constexpr float kPairLg2Max = 125.0f;
 
 // 10^v as a float without the FP64 exp10: 2^(v log2 10) split into an exact integer power of
 // two and a fractional part in [0, 1) handled by ex2 (one FP64 multiply, ~2 ulp).
@@ -266,27 +269,21 @@ __device__ __forceinline__ float bin_term32p(const float* __restrict__ tb, int i
     }
     return bin_term32<C, HAS_H, BROKEN>(tb, i, v, ao2, at2, n1, n2, Af);
 }
-// Three-input maximum / minimum (one instruction on sm_100 and later).
+// Three-input maximum (one instruction on sm_100 and later).
 __device__ __forceinline__ float fmax3(float a, float b, float c) {
     float d;
     asm("max.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
-    return d;
-}
-__device__ __forceinline__ float fmin3(float a, float b, float c) {
-    float d;
-    asm("min.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
     return d;
 }
 
 // Two consecutive bins (one pair block) with FP32x2 instructions; both bins lie in the current
 // intervals.  Returns nu * (sum_c 1/S_c + ln prod S_c - C) for both bins, formed from one
 // reciprocal and one log2 of the channel product without a range test: the caller keeps the
-// running maximum (mx) and minimum (mi) of log2 prod and recomputes the chunk on the guarded
-// scalar path when either left +-kPairLg2Max or the chunk sum is not finite.
+// running maximum (mx) of log2 prod and recomputes the chunk on the guarded scalar path when it
+// passed kPairLg2Max or the chunk sum is not finite.
 template <int C, bool HAS_H, bool BROKEN>
 __device__ __forceinline__ float2 pair_term32(const float4 q0, const float4* __restrict__ blk, const Iv2* iv,
-                                              float2 ao2, float2 at2, float n1, float n2, float2 Af, float& mx,
-                                              float& mi) {
+                                              float2 ao2, float2 at2, float n1, float n2, float2 Af, float& mx) {
     constexpr int NSP = C + (HAS_H ? 1 : 0);
     const float4 q1 = blk[1], q2 = blk[2], q3 = blk[3], q4 = blk[4], q5 = blk[5];
     const float2 x = make_float2(q0.x, q0.y), ell = make_float2(q0.z, q0.w), nu = make_float2(q1.x, q1.y);
@@ -325,85 +322,104 @@ __device__ __forceinline__ float2 pair_term32(const float4 q0, const float4* __r
                                 make_float2(-(float)C, -(float)C));
     const float2 lg = make_float2(lg2_approx(prod.x), lg2_approx(prod.y));
     mx = fmax3(mx, lg.x, lg.y);
-    mi = fmin3(mi, lg.x, lg.y);
     return __fmul2_rn(nu, __ffma2_rn(make_float2((float)kLn2, (float)kLn2), lg, v));
 }
 
+// Work-item pipeline: the bin table of item k is staged into buffer k % kStages by one bulk
+// copy completing on full[k % kStages].  Warps do not wait for one another between items: after
+// its last read of a buffer each warp adds one to that buffer's counter, and the warp that
+// completes the count (the last reader) issues the copy of the item kStages further on into it.
+// Items with one state per thread write their partial sums directly; items that split a state's
+// bins over several threads (rows) combine the rows in shared memory between two barriers.
+constexpr int kStages = 2;
+constexpr int kWarps32 = kThreads32 / 32;
+
 template <int C, bool HAS_H, bool BROKEN, int G>
-__global__ void __launch_bounds__(kThreads32, G == 8 ? 5 : 6)
+__global__ void __launch_bounds__(kThreads32, G == 8 ? 4 : (G == 4 ? 5 : 6))
     loglike_fp32_kernel(const WorkItem* __restrict__ items, int n_items, const int32_t* __restrict__ cta_first,
                         const float* __restrict__ rec32,
                         const StateParams* __restrict__ prm, const int32_t* __restrict__ sstat,
-                        const int32_t* __restrict__ nint, const float* __restrict__ srec, int kmax, int nsp,
+                        const float* __restrict__ kxr, const float* __restrict__ srec, int kmax, int nsp,
                         const DatasetDev* __restrict__ ds, double* __restrict__ partial, int* __restrict__ err,
-                        int tile_bins) {
+                        int tile_bins, unsigned wait_limit, int skip_copies) {
     constexpr int NSP = C + (HAS_H ? 1 : 0);
+    constexpr int U = G / 2;                  // pair blocks per iteration of the knot-free loop
+    constexpr int kChunkPairs = 32;           // pair blocks per FP32 partial sum (64 bins)
+    constexpr unsigned kLocated = 1u << 31;   // s_hm: this thread's intervals have been located
+    constexpr unsigned kSplineBits = (1u << NSP) - 1u;
     extern __shared__ __align__(128) unsigned char smem[];
-    __shared__ __align__(8) uint64_t bars[2];
+    __shared__ __align__(8) uint64_t full[kStages];
+    __shared__ unsigned s_done[kStages];
+    __shared__ int s_fail;                    // a bounded wait of this CTA ran out: stage nothing more
     __shared__ float2 red[kThreads32];
-    float* sbuf0 = reinterpret_cast<float*>(smem);
-    float* sbuf1 = reinterpret_cast<float*>(smem + (size_t)tile_bins * kRec * sizeof(float));
+    // per thread: right end and index of the current interval of each spline, and the bits of
+    // the ill-conditioned ones (touched only at knots, so they live here and not in registers)
+    __shared__ float s_xr[NSP][kThreads32];
+    __shared__ int s_jj[NSP][kThreads32];
+    __shared__ unsigned s_hm[kThreads32];     // bit a: spline a ill-conditioned; kLocated: set up
     const int tid = threadIdx.x;
+    const int lane = tid & 31;
+    const size_t stage_floats = (size_t)tile_bins * kRec;
+    s_hm[tid] = 0u;
+    // the CTA's items, [cta_first[c], cta_first[c + 1]) of the work list: with many items per
+    // CTA a contiguous, cost-balanced block of the (dataset, state chunk, tile)-ordered list
+    // (consecutive items are mostly consecutive tiles of the same states, whose intervals carry
+    // over); with few, the items a longest-first assignment of the knot-aware costs gave the CTA
+    // (without cta_first: every gridDim.x-th item)
+    const int step = cta_first ? 1 : (int)gridDim.x;
+    const int i_begin = cta_first ? cta_first[blockIdx.x] : (int)blockIdx.x;
+    const int i_end = cta_first ? cta_first[blockIdx.x + 1] : n_items;
+    auto stage = [&](int q, int item) {   // one bulk copy of item's bin table into buffer q
+        const WorkItem w = items[item];
+        const unsigned bytes = (unsigned)w.nb * kRec * sizeof(float);
+        mbar_expect_tx(&full[q], bytes);
+        bulk_copy_g2s(reinterpret_cast<float*>(smem) + q * stage_floats, rec32 + (w.bin0 >> 1) * kPairRec, bytes,
+                      &full[q]);
+    };
     if (tid == 0) {
-        mbar_init(&bars[0], 1);
-        mbar_init(&bars[1], 1);
+        s_fail = 0;
+        for (int q = 0; q < kStages; ++q) {
+            mbar_init(&full[q], 1);
+            s_done[q] = 0u;
+        }
         mbar_fence_init();
+        // skip_copies (a test of the timeout path only): no copy is issued, so every wait runs
+        // out with nothing in flight
+        if (!skip_copies)
+            for (int q = 0; q < kStages; ++q)
+                if (i_begin + q * step < i_end) stage(q, i_begin + q * step);
     }
     __syncthreads();
-    unsigned phase0 = 0, phase1 = 0;
-    // the CTA's items: with cta_first, a contiguous block of the (dataset, state chunk,
-    // tile)-ordered work list, cut by the host so that every CTA gets the same knot-aware cost
-    // (consecutive items are mostly consecutive tiles of the same states, whose intervals carry
-    // over); without it (few items per CTA), every gridDim.x-th item, which mixes tiles from the
-    // whole band into each CTA
-    const int step = cta_first ? 1 : (int)gridDim.x;
-    int it = cta_first ? cta_first[blockIdx.x] : (int)blockIdx.x;
-    const int i_end = cta_first ? cta_first[blockIdx.x + 1] : n_items;
-    if (it < i_end && tid == 0) {
-        const WorkItem w = items[it];
-        const unsigned bytes = (unsigned)w.nb * kRec * sizeof(float);
-        mbar_expect_tx(&bars[0], bytes);
-        bulk_copy_g2s(sbuf0, rec32 + (w.bin0 >> 1) * kPairRec, bytes, &bars[0]);
-    }
-    // per spline: right knot of the current interval, its index, and the interval's cubic
-    // duplicated into register pairs (the scalar path reads the .x halves); xmin = the nearest
-    // right knot.  An ill-conditioned interval (T > kRobustT, routed states only) is loaded as the
-    // zero cubic, which keeps its bins' arithmetic benign, and sets its bit in hm; keep2 = 0 while
-    // any bit is set, 1 otherwise, and scales each pair's contribution.  All of it carries over
-    // to the next item when that is the next tile of the same state chunk (bins only move right).
-    float xr[NSP];
-    int jj[NSP];
+    // per spline, the current interval's cubic duplicated into register pairs (the scalar path
+    // reads the .x halves); xmin = the nearest right knot over the splines.  An ill-conditioned
+    // interval (T > kRobustT, routed states only) is loaded as the zero cubic, which keeps its
+    // bins' arithmetic benign, and sets its bit in s_hm; keep2 = 0 while any bit is set, 1
+    // otherwise, and scales each bin's contribution.  All of it carries over to the next item
+    // when that is the next tile of the same state chunk (bins only move right).
     Iv2 iv2[NSP];
     float xmin = INFINITY;
-    unsigned hm = 0;
     float2 keep2 = make_float2(1.f, 1.f);
-    bool located = false;
-    int prev_ds = -1, prev_s0 = -1, prev_tile = -2;
-    for (int k = 0; it < i_end; it += step, ++k) {
-        const int b = k & 1;
-        const int nxt = it + step;
-        if (nxt < i_end && tid == 0) {
-            const WorkItem w = items[nxt];
-            const unsigned bytes = (unsigned)w.nb * kRec * sizeof(float);
-            fence_proxy_async();
-            mbar_expect_tx(&bars[b ^ 1], bytes);
-            bulk_copy_g2s(b ? sbuf0 : sbuf1, rec32 + (w.bin0 >> 1) * kPairRec, bytes, &bars[b ^ 1]);
-        }
+    int k = 0;
+    for (int it = i_begin; it < i_end; it += step, ++k) {
+        const int b = k % kStages;
         const WorkItem w = items[it];
-        if (b == 0) {
-            mbar_wait_bounded(&bars[0], phase0, err);
-            phase0 ^= 1;
-        } else {
-            mbar_wait_bounded(&bars[1], phase1, err);
-            phase1 ^= 1;
+        // buffer b's barrier has completed k / kStages phases before this item's
+        const bool ok = mbar_wait_bounded(&full[b], (unsigned)(k / kStages) & 1u, wait_limit);
+        // a wait that ran out: this thread skips the item (its table may never arrive or be
+        // partly written) and raises the flag (finalize turns every log L into NaN and
+        // lisa_workspace_status reports LISA_ERR_TIMEOUT); the CTA stages no further copy, since
+        // the late one could still be landing in this buffer, and its later waits run out too
+        if (!ok) {
+            s_fail = 1;
+            atomicOr(err, kErrTimeout);
         }
-        const float* tb = b ? sbuf1 : sbuf0;
+        const float* tb = reinterpret_cast<const float*>(smem) + b * stage_floats;
         const float4* tb4 = reinterpret_cast<const float4*>(tb);
-
-        if (!(w.ds == prev_ds && w.s0 == prev_s0 && w.tile == prev_tile + 1)) located = false;
-        prev_ds = w.ds;
-        prev_s0 = w.s0;
-        prev_tile = w.tile;
+        bool carry = false;
+        if (k > 0) {
+            const WorkItem pw = items[it - step];
+            carry = w.ds == pw.ds && w.s0 == pw.s0 && w.tile == pw.tile + 1;
+        }
         const int sc = w.sc;
         const int R = kThreads32 / sc;
         const int ls = tid & (sc - 1);
@@ -411,7 +427,7 @@ __global__ void __launch_bounds__(kThreads32, G == 8 ? 5 : 6)
         const int s = w.s0 + ls;
         // every valid state, routed ones included: the bins of an ill-conditioned interval are
         // masked out here (the compensated kernel adds them), all other bins are summed here
-        const bool active = ls < w.ns && (sstat[s] & kUserBits) == 0;
+        const bool active = ok && ls < w.ns && (sstat[s] & kUserBits) == 0;
         ff accf = {0.f, 0.f};
         if (active) {
             const int np = w.nb >> 1;                          // pair blocks in the tile
@@ -421,12 +437,17 @@ __global__ void __launch_bounds__(kThreads32, G == 8 ? 5 : 6)
                 const float ao2 = q0.x, at2 = q0.y, Af = HAS_H ? q0.z : 0.f, n1 = q0.w;
                 const float n2 = BROKEN ? __ldg(&prm[s].n2) : n1;
                 const float2 ao2_2 = make_float2(ao2, ao2), at2_2 = make_float2(at2, at2), Af2 = make_float2(Af, Af);
-                const int64_t sp0 = (int64_t)s * nsp;
-                auto reload = [&](int a) {
-                    const float* rr = srec + ((sp0 + a) * (int64_t)(kmax + 1) + jj[a]) * kSplineRec32;
-                    const float4 A = __ldg(reinterpret_cast<const float4*>(rr));
-                    const float4 B = __ldg(reinterpret_cast<const float4*>(rr + 4));
-                    xr[a] = A.x;
+                // the records of this state's splines: spline a, interval j at rec(a, j)
+                auto rec = [&](int a, int j) {
+                    return reinterpret_cast<const float4*>(
+                        srec + (((int64_t)s * nsp + a) * (int64_t)(kmax + 1) + j) * kSplineRec32);
+                };
+                // installs interval j of spline a from its record (A = xr, xo, c0, c1; B = c2, c3,
+                // xl, T)
+                auto install = [&](int a, int j, float4 A, float4 B) {
+                    s_xr[a][tid] = A.x;
+                    s_jj[a][tid] = j;
+                    unsigned hm = s_hm[tid];
                     if (B.w <= (float)kRobustT) {
                         iv2[a] = Iv2{make_float2(-A.y, -A.y), make_float2(A.z, A.z), make_float2(A.w, A.w),
                                      make_float2(B.x, B.x), make_float2(B.y, B.y)};
@@ -436,102 +457,147 @@ __global__ void __launch_bounds__(kThreads32, G == 8 ? 5 : 6)
                         iv2[a] = Iv2{z, z, z, z, z};
                         hm |= 1u << a;
                     }
-                    keep2 = hm ? make_float2(0.f, 0.f) : make_float2(1.f, 1.f);
+                    s_hm[tid] = hm;
+                    keep2 = (hm & kSplineBits) ? make_float2(0.f, 0.f) : make_float2(1.f, 1.f);
                 };
+                // moves spline a to the interval holding x: one dependent load per interval
+                // passed (the whole record at once); the last interval's right end is +inf, and
+                // the index never leaves the spline's kmax + 1 record slots
                 auto advance = [&](int a, float x) {
-                    if (x >= xr[a]) {
-                        const int last = nint[sp0 + a] - 1;
-                        bool moved = false;
-                        while (x >= xr[a] && jj[a] < last) {
-                            ++jj[a];
-                            xr[a] = __ldg(srec + ((sp0 + a) * (int64_t)(kmax + 1) + jj[a]) * kSplineRec32);
-                            moved = true;
-                        }
-                        if (moved) reload(a);
-                    }
-                };
-                auto locate = [&](float x) {
-#pragma unroll
-                    for (int a = 0; a < NSP; ++a) {
-                        jj[a] = find_interval<float, kSplineRec32, 6>(
-                            srec + (sp0 + a) * (int64_t)(kmax + 1) * kSplineRec32, nint[sp0 + a], x);
-                        reload(a);
+                    if (x >= s_xr[a][tid]) {
+                        int j = s_jj[a][tid];
+                        float4 A, B;
+                        do {
+                            ++j;
+                            A = __ldg(rec(a, j));
+                            B = __ldg(rec(a, j) + 1);
+                        } while (x >= A.x && j < kmax);
+                        install(a, j, A, B);
                     }
                 };
                 auto nearest = [&]() {
-                    float m = xr[0];
+                    float m = s_xr[0][tid];
 #pragma unroll
-                    for (int a = 1; a < NSP; ++a) m = fminf(m, xr[a]);
+                    for (int a = 1; a < NSP; ++a) m = fminf(m, s_xr[a][tid]);
                     return m;
                 };
-                // one bin on the scalar path (next to knots): advance, then the guarded term
+                // the interval of each spline holding x: the count of right ends <= x in the
+                // spline's right-end table (independent 16-byte loads), then its record
+                auto locate = [&](float x) {
+                    s_hm[tid] = kLocated;
+                    const int kxs = kxr_stride(kmax);
+#pragma unroll
+                    for (int a = 0; a < NSP; ++a) {
+                        const float4* kq = reinterpret_cast<const float4*>(kxr + ((int64_t)s * nsp + a) * kxs);
+                        int j = 0;
+#pragma unroll 4
+                        for (int q = 0; q < kxs / 4; ++q) {
+                            const float4 v = __ldg(kq + q);
+                            j += (v.x <= x) + (v.y <= x) + (v.z <= x) + (v.w <= x);
+                        }
+                        j = min(j, kmax);
+                        install(a, j, __ldg(rec(a, j)), __ldg(rec(a, j) + 1));
+                    }
+                    xmin = nearest();
+                };
+                // one bin on the scalar path (at knots, and for the guarded redo): advance this
+                // thread's intervals if the bin passed a knot, then the guarded term
                 auto scalar_bin = [&](int i) {
                     const float x = fld(tb, i, 0);
+                    if (x >= xmin) {
 #pragma unroll
-                    for (int a = 0; a < NSP; ++a) advance(a, x);
-                    const float v = bin_term32p<C, HAS_H, BROKEN>(tb, i, iv2, ao2, at2, n1, n2, Af);
-                    return hm ? 0.f : v;
+                        for (int a = 0; a < NSP; ++a) advance(a, x);
+                        xmin = nearest();
+                    }
+                    return keep2.x * bin_term32p<C, HAS_H, BROKEN>(tb, i, iv2, ao2, at2, n1, n2, Af);
                 };
-                if (!located) {
-                    locate(fld(tb, 2 * plo, 0));
-                    xmin = nearest();
-                    located = true;
-                }
+                // intervals carry over from this thread's previous item when it held the
+                // preceding tile of the same states (a thread whose row was empty there keeps
+                // those of an earlier tile, which lie to the left: advancing finds the new ones)
+                if (!(carry && (s_hm[tid] & kLocated))) locate(fld(tb, 2 * plo, 0));
                 int ip = plo;
                 while (ip < phi) {
                     const int pc0 = ip;
-                    const int pcend = min(ip + 16, phi);
+                    const int pcend = min(ip + kChunkPairs, phi);
+                    const float4* blk = tb4 + ip * (kPairRec / 4);
                     float2 acc2 = make_float2(0.f, 0.f);
-                    float mx = 0.f, mi = 0.f;
-                    for (; ip + G / 2 <= pcend; ip += G / 2) {
-                        const float4* blk = tb4 + ip * (kPairRec / 4);
-                        // first float4 of the group's last pair block: (x, x, ell, ell); its .y is
-                        // the x of the group's last bin
-                        const float4 qg = blk[(G / 2 - 1) * (kPairRec / 4)];
-                        if (qg.y < xmin) {
+                    float mx = -INFINITY;
+                    // one decision per chunk for the warp: no lane passes a knot inside it (the
+                    // common case away from the lowest frequencies) -> no checks at all
+                    const float x_last = tb4[(pcend - 1) * (kPairRec / 4)].y;
+                    if (!__any_sync(__activemask(), x_last >= xmin)) {
+                        for (; ip + U <= pcend; ip += U, blk += U * (kPairRec / 4)) {
 #pragma unroll
-                            for (int g = 0; g < G / 2; ++g) {
-                                const float4* pb = blk + g * (kPairRec / 4);
-                                const float4 q0 = g == G / 2 - 1 ? qg : pb[0];
-                                acc2 = __ffma2_rn(keep2, pair_term32<C, HAS_H, BROKEN>(q0, pb, iv2, ao2_2, at2_2, n1,
-                                                                                       n2, Af2, mx, mi),
+                            for (int u = 0; u < U; ++u) {
+                                const float4* pb = blk + u * (kPairRec / 4);
+                                acc2 = __ffma2_rn(keep2, pair_term32<C, HAS_H, BROKEN>(pb[0], pb, iv2, ao2_2, at2_2,
+                                                                                       n1, n2, Af2, mx),
                                                   acc2);
                             }
-                        } else {
+                        }
 #pragma unroll 1
-                            for (int i = 2 * ip; i < 2 * ip + G; ++i) acc2.x += scalar_bin(i);
-                            xmin = nearest();
+                        for (; ip < pcend; ++ip, blk += kPairRec / 4)
+                            acc2 = __ffma2_rn(keep2, pair_term32<C, HAS_H, BROKEN>(blk[0], blk, iv2, ao2_2, at2_2, n1,
+                                                                                   n2, Af2, mx),
+                                              acc2);
+                    } else {
+                        // pair block by pair block: a lane whose block reaches a knot takes its two
+                        // bins on the scalar path (advancing its intervals between them), the
+                        // others stay packed
+#pragma unroll 1
+                        for (; ip < pcend; ++ip, blk += kPairRec / 4) {
+                            const float4 q0 = blk[0];
+                            if (q0.y >= xmin) {
+                                acc2.x += scalar_bin(2 * ip);
+                                acc2.x += scalar_bin(2 * ip + 1);
+                            } else {
+                                acc2 = __ffma2_rn(keep2, pair_term32<C, HAS_H, BROKEN>(q0, blk, iv2, ao2_2, at2_2, n1,
+                                                                                       n2, Af2, mx),
+                                                  acc2);
+                            }
                         }
                     }
-#pragma unroll 1
-                    for (; ip < pcend; ++ip) {
-                        acc2.x += scalar_bin(2 * ip);
-                        acc2.x += scalar_bin(2 * ip + 1);
-                        xmin = nearest();
-                    }
-                    if (!(mx <= kPairLg2Max && mi >= -kPairLg2Max && fabsf(acc2.x + acc2.y) < INFINITY)) {
-                        // a channel product left the range of the one-reciprocal form (or the
-                        // reciprocal-sum numerator overflowed): redo the chunk bin by bin on the
-                        // guarded path, intervals re-found at its start
+                    if (!(mx <= kPairLg2Max && fabsf(acc2.x + acc2.y) < INFINITY)) {
+                        // a channel product passed the range of the one-reciprocal form (or the
+                        // sum overflowed): redo the chunk bin by bin on the guarded path,
+                        // intervals re-found at its start
                         locate(fld(tb, 2 * pc0, 0));
                         acc2 = make_float2(0.f, 0.f);
 #pragma unroll 1
                         for (int i = 2 * pc0; i < 2 * pcend; ++i) acc2.x += scalar_bin(i);
-                        xmin = nearest();
                     }
                     accf = ff_add(accf, two_sum(acc2.x, acc2.y));
                 }
             }
         }
-        red[tid] = make_float2(accf.hi, accf.lo);
-        __syncthreads();
-        if (r == 0 && active) {
-            ff sum = {red[ls].x, red[ls].y};
-            for (int q = 1; q < R; ++q) sum = ff_add(sum, ff{red[ls + q * sc].x, red[ls + q * sc].y});
-            const DatasetDev& D = ds[w.ds];
-            partial[D.pbase + (int64_t)(s - D.s0) * D.ntiles + w.tile] = (double)sum.hi + (double)sum.lo;
+        const DatasetDev& D = ds[w.ds];
+        if (R == 1) {
+            if (active) partial[D.pbase + (int64_t)(s - D.s0) * D.ntiles + w.tile] = (double)accf.hi + (double)accf.lo;
+        } else {
+            red[tid] = make_float2(accf.hi, accf.lo);
+            __syncthreads();
+            if (r == 0 && active) {
+                ff sum = {red[ls].x, red[ls].y};
+                for (int q = 1; q < R; ++q) sum = ff_add(sum, ff{red[ls + q * sc].x, red[ls + q * sc].y});
+                partial[D.pbase + (int64_t)(s - D.s0) * D.ntiles + w.tile] = (double)sum.hi + (double)sum.lo;
+            }
+            __syncthreads();   // red is rewritten by the next item
         }
-        __syncthreads();  // the buffer read in this iteration is refilled in the next one
+        // release buffer b: the last of the CTA's warps to finish reading it stages item
+        // it + kStages * step into it (the count of buffer b reaches kWarps32 * (k / kStages + 1))
+        __syncwarp();
+        if (lane == 0) {
+            __threadfence_block();
+            const unsigned done = atomicAdd(&s_done[b], 1u) + 1u;
+            if (done == kWarps32 * (unsigned)(k / kStages + 1)) {
+                __threadfence_block();
+                const int nx = it + kStages * step;
+                if (nx < i_end && !skip_copies && !*reinterpret_cast<volatile int*>(&s_fail)) {
+                    fence_proxy_async();
+                    stage(b, nx);
+                }
+            }
+        }
     }
 }
 
@@ -704,7 +770,7 @@ __global__ void __launch_bounds__(kRobWarps * 32, 2)
                           int tile_bins, const float* __restrict__ rec32, const float* __restrict__ xlo32,
                           const float* __restrict__ elllo32, const StateParams* __restrict__ prm,
                           const int32_t* __restrict__ nint, const float* __restrict__ srec, int kmax, int nsp,
-                          double* __restrict__ partial, int* __restrict__ err) {
+                          double* __restrict__ partial, int* __restrict__ err, unsigned wait_limit) {
     constexpr int NSP = C + (HAS_H ? 1 : 0);
     extern __shared__ float4 rsm[];
     __shared__ __align__(8) uint64_t rbar[kRobWarps];
@@ -806,9 +872,13 @@ __global__ void __launch_bounds__(kRobWarps * 32, 2)
                 xs[lane + 32 * k] = vx[k];
                 es[lane + 32 * k] = ve[k];
             }
-            const bool ok = mbar_wait_bounded(bar, phase, err);
+            const bool ok = mbar_wait_bounded(bar, phase, wait_limit);
             if (!__all_sync(0xffffffffu, ok)) {
-                mbar_wait_bounded(bar, phase, err);   // let the copy in flight land, then stop
+                // timed out: raise the flag, let the warp's one copy in flight land, then stop
+                if (lane == 0) {
+                    atomicOr(err, kErrTimeout);
+                    mbar_wait_bounded(bar, phase, wait_limit);
+                }
                 return;
             }
             phase ^= 1;
@@ -986,15 +1056,16 @@ int grid_for(K kernel, const lisa_data* d, size_t smem, int threads) {
 
 template <int C, bool H, bool B, int G>
 cudaError_t launch_fp32_g(const lisa_data* d, const StateParams* prm, const int32_t* sstat, const int32_t* nint,
-                          unsigned long long* rcount, const RobustEntry* rlist, const float* srec, int kmax,
+                          const float* kxr, unsigned long long* rcount, const RobustEntry* rlist, const float* srec,
+                          int kmax,
                           double* partial, int* err, cudaStream_t sm, bool prof) {
     auto kern = loglike_fp32_kernel<C, H, B, G>;
     const size_t smem = 2 * (size_t)d->tiling.tile_bins * kRec * sizeof(float);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    kern<<<d->fgrid, kThreads32, smem, sm>>>(d->d_items, (int)d->n_items, d->fblocks ? d->d_cta_first : nullptr,
-                                              d->d_rec32, prm, sstat, nint, srec, kmax, d->nsp, d->d_ds, partial, err,
-                                              d->tiling.tile_bins);
+    kern<<<d->fgrid, kThreads32, smem, sm>>>(d->d_items, (int)d->n_items, d->d_cta_first,
+                                              d->d_rec32, prm, sstat, kxr, srec, kmax, d->nsp, d->d_ds, partial, err,
+                                              d->tiling.tile_bins, d->wait_limit, d->test_skip_copies);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     prof_mark(d, prof, 1, sm);
@@ -1004,7 +1075,8 @@ cudaError_t launch_fp32_g(const lisa_data* d, const StateParams* prm, const int3
     e = cudaFuncSetAttribute(rk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRobSmem);
     if (e != cudaSuccess) return e;
     rk<<<d->rgrid, kRobWarps * 32, kRobSmem, sm>>>(rcount, rlist, d->tiling.tile_bins, d->d_rec32, d->d_xlo32,
-                                                   d->d_elllo32, prm, nint, srec, kmax, d->nsp, partial, err);
+                                                   d->d_elllo32, prm, nint, srec, kmax, d->nsp, partial, err,
+                                                   d->wait_limit);
     e = cudaGetLastError();
     prof_mark(d, prof, 2, sm);
     return e;
@@ -1056,13 +1128,13 @@ int occupancy_c(int sgwb, const lisa_tiling& t) {
 
 template <int C, bool H, bool B>
 cudaError_t launch_fp32(const lisa_data* d, const StateParams* prm, const int32_t* sstat, const int32_t* nint,
-                        unsigned long long* rcount, const RobustEntry* rlist, const float* srec, int kmax,
-                        double* partial, int* err, cudaStream_t sm, bool prof) {
+                        const float* kxr, unsigned long long* rcount, const RobustEntry* rlist, const float* srec,
+                        int kmax, double* partial, int* err, cudaStream_t sm, bool prof) {
     switch (d->tiling.group) {
-        case 2: return launch_fp32_g<C, H, B, 2>(d, prm, sstat, nint, rcount, rlist, srec, kmax, partial, err, sm, prof);
-        case 8: return launch_fp32_g<C, H, B, 8>(d, prm, sstat, nint, rcount, rlist, srec, kmax, partial, err, sm, prof);
+        case 2: return launch_fp32_g<C, H, B, 2>(d, prm, sstat, nint, kxr, rcount, rlist, srec, kmax, partial, err, sm, prof);
+        case 8: return launch_fp32_g<C, H, B, 8>(d, prm, sstat, nint, kxr, rcount, rlist, srec, kmax, partial, err, sm, prof);
         default:
-            return launch_fp32_g<C, H, B, 4>(d, prm, sstat, nint, rcount, rlist, srec, kmax, partial, err, sm, prof);
+            return launch_fp32_g<C, H, B, 4>(d, prm, sstat, nint, kxr, rcount, rlist, srec, kmax, partial, err, sm, prof);
     }
 }
 
@@ -1081,17 +1153,17 @@ cudaError_t launch_fp64(const lisa_data* d, const double* theta, const int32_t* 
 
 template <int C>
 cudaError_t dispatch_model(const lisa_data* d, bool fp32, const double* theta, const StateParams* prm,
-                           const int32_t* sstat, const int32_t* nint, unsigned long long* rcount,
+                           const int32_t* sstat, const int32_t* nint, const float* kxr, unsigned long long* rcount,
                            const RobustEntry* rlist, const void* srec, int kmax, double* partial, int* err,
                            cudaStream_t sm, bool prof) {
     const int h = d->sgwb_model;
     if (fp32) {
         const float* r = static_cast<const float*>(srec);
         if (h == 0)
-            return launch_fp32<C, false, false>(d, prm, sstat, nint, rcount, rlist, r, kmax, partial, err, sm, prof);
+            return launch_fp32<C, false, false>(d, prm, sstat, nint, kxr, rcount, rlist, r, kmax, partial, err, sm, prof);
         if (h == 1)
-            return launch_fp32<C, true, false>(d, prm, sstat, nint, rcount, rlist, r, kmax, partial, err, sm, prof);
-        return launch_fp32<C, true, true>(d, prm, sstat, nint, rcount, rlist, r, kmax, partial, err, sm, prof);
+            return launch_fp32<C, true, false>(d, prm, sstat, nint, kxr, rcount, rlist, r, kmax, partial, err, sm, prof);
+        return launch_fp32<C, true, true>(d, prm, sstat, nint, kxr, rcount, rlist, r, kmax, partial, err, sm, prof);
     }
     const double* r = static_cast<const double*>(srec);
     if (h == 0) return launch_fp64<C, false, false>(d, theta, sstat, nint, r, kmax, partial, sm, prof);
@@ -1151,6 +1223,7 @@ lisa_status lisa_psd_loglike(const lisa_data* d, const lisa_params* params, cons
     const int32_t* nint = reinterpret_cast<const int32_t*>(base + L.off_nint);
     const void* srec = base + L.off_rec;
     const float2* hull = reinterpret_cast<const float2*>(base + L.off_hull);
+    const float* kxr = reinterpret_cast<const float*>(base + L.off_kxr);
     char* wsb = static_cast<char*>(ws);
     int* err = reinterpret_cast<int*>(wsb);
     unsigned long long* rcount = reinterpret_cast<unsigned long long*>(wsb + kWsCounterOff);
@@ -1172,9 +1245,9 @@ lisa_status lisa_psd_loglike(const lisa_data* d, const lisa_params* params, cons
     prof_mark(d, prof, 0, sm);
     cudaError_t e = cudaSuccess;
     if (d->n_items > 0)
-        e = d->C == 3 ? dispatch_model<3>(d, fp32, params->theta_dev, prm, sstat, nint, rcount, rlist, srec, kmax,
+        e = d->C == 3 ? dispatch_model<3>(d, fp32, params->theta_dev, prm, sstat, nint, kxr, rcount, rlist, srec, kmax,
                                           partial, err, sm, prof)
-                      : dispatch_model<2>(d, fp32, params->theta_dev, prm, sstat, nint, rcount, rlist, srec, kmax,
+                      : dispatch_model<2>(d, fp32, params->theta_dev, prm, sstat, nint, kxr, rcount, rlist, srec, kmax,
                                           partial, err, sm, prof);
     else {
         prof_mark(d, prof, 1, sm);
@@ -1186,6 +1259,16 @@ lisa_status lisa_psd_loglike(const lisa_data* d, const lisa_params* params, cons
     prof_mark(d, prof, 3, sm);
     if (prof) d->prof_valid = true;
     return check_cuda(e);
+}
+
+lisa_status lisa_workspace_status(const void* ws, lisa_stream_t stream) {
+    if (!ws) return LISA_ERR_NULL;
+    if (reinterpret_cast<uintptr_t>(ws) & 255) return LISA_ERR_WORKSPACE;
+    cudaStream_t sm = (cudaStream_t)stream;
+    int flag = 0;
+    if (cudaMemcpyAsync(&flag, ws, sizeof(int), cudaMemcpyDeviceToHost, sm) != cudaSuccess) return LISA_ERR_CUDA;
+    if (cudaStreamSynchronize(sm) != cudaSuccess) return LISA_ERR_CUDA;
+    return (flag & kErrTimeout) ? LISA_ERR_TIMEOUT : LISA_SUCCESS;
 }
 
 lisa_status lisa_data_kernel_ms(const lisa_data* d, float* ms) {
@@ -1233,28 +1316,19 @@ lisa_status lisa_model_psd(const lisa_data* d, const lisa_params* params, const 
 // obtained from cudaGetSymbolAddress (the symbol itself names a host-side stand-in).
 static __device__ __align__(256) unsigned char g_noalloc_scratch[LISA_NOALLOC_SCRATCH_BYTES];
 
-namespace {
-std::mutex g_noalloc_mu;
-void* g_noalloc_ptr[256] = {};   // per device ordinal
-}  // namespace
-
 extern "C" lisa_status lisa_psd_loglike_noalloc(const lisa_data* d, const lisa_params* params, const void* buf,
                                                 size_t buf_bytes, int32_t kmax, double* out, lisa_precision prec,
                                                 lisa_stream_t stream) {
     if (!d || !params || !buf || !out) return LISA_ERR_NULL;
     if (ws_fwd_bytes(d) > (size_t)LISA_NOALLOC_SCRATCH_BYTES) return LISA_ERR_WORKSPACE;
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) return LISA_ERR_CUDA;
+    // the array exists once per device: use the copy on the device that holds the data object
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) return LISA_ERR_CUDA;
+    if (dev != d->device) return LISA_ERR_VALUE;
+    // looked up on every call (a query that enqueues nothing), so that a device reset, which
+    // reloads the library's device code at a new address, never leaves a stale pointer behind
     void* scratch = nullptr;
-    {
-        std::lock_guard<std::mutex> lock(g_noalloc_mu);
-        if (!g_noalloc_ptr[dev]) {
-            void* p = nullptr;
-            if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return LISA_ERR_CUDA;
-            g_noalloc_ptr[dev] = p;
-        }
-        scratch = g_noalloc_ptr[dev];
-    }
+    if (cudaGetSymbolAddress(&scratch, g_noalloc_scratch) != cudaSuccess || !scratch) return LISA_ERR_CUDA;
     // lisa_psd_loglike clears the error flag on the stream and overwrites the partial sums.
     return lisa_psd_loglike(d, params, buf, buf_bytes, kmax, out, scratch, LISA_NOALLOC_SCRATCH_BYTES, prec,
                             stream);

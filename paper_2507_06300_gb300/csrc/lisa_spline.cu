@@ -22,7 +22,7 @@ __global__ void __launch_bounds__(128, 7) spline_setup_kernel(
     int S, int nsp, int kmax, int kind, const int32_t* __restrict__ state_ds,
     const DatasetDev* __restrict__ ds, int32_t* __restrict__ status_buf, int32_t* __restrict__ nint_buf,
     int32_t* __restrict__ route, void* __restrict__ rec_v, float2* __restrict__ hull,
-    int32_t* __restrict__ status_out) {
+    float* __restrict__ kxr, int32_t* __restrict__ status_out) {
     using T = double;
     __shared__ T sX[4][64];
     __shared__ T sY[4][64];
@@ -99,6 +99,7 @@ __global__ void __launch_bounds__(128, 7) spline_setup_kernel(
                     if (!valid) continue;
                     float* r = static_cast<float*>(rec_v) + (sp * (int64_t)(kmax + 1) + j) * kSplineRec32;
                     r[0] = last ? INFINITY : xr_f;
+                    kxr[sp * kxr_stride(kmax) + j] = r[0];
                     r[1] = xo_hi;
                     r[6] = xl_f;
                     r[7] = Tc;
@@ -113,6 +114,12 @@ __global__ void __launch_bounds__(128, 7) spline_setup_kernel(
             if (lane == 0) nint_buf[sp] = K - 1;
         }
         if (st && lane == 0) nint_buf[sp] = 0;
+        if (kF32) {
+            // right-end table past the last interval (all of it for an invalid spline): +inf
+            const int first_pad = st ? 0 : W.K - 1;
+            for (int j = lane; j < kxr_stride(kmax); j += 32)
+                if (j >= first_pad) kxr[sp * kxr_stride(kmax) + j] = INFINITY;
+        }
         st_all |= st;
     }
     robust = __any_sync(spl::kFull, robust);
@@ -179,11 +186,13 @@ extern "C" lisa_status lisa_spline_setup(const lisa_data* d, const lisa_knots* k
         spline_setup_kernel<false><<<blocks, threads, 0, sm>>>(kn->count_dev, kn->x_dev, kn->w_dev, (int)d->n_states,
                                                            d->nsp, kn->kmax, kn->kind, d->d_state_ds, d->d_ds,
                                                            status_buf, nint_buf, route, base + L.off_rec,
-                                                           reinterpret_cast<float2*>(base + L.off_hull), status_out);
+                                                           reinterpret_cast<float2*>(base + L.off_hull),
+                                                           reinterpret_cast<float*>(base + L.off_kxr), status_out);
     else
         spline_setup_kernel<true><<<blocks, threads, 0, sm>>>(kn->count_dev, kn->x_dev, kn->w_dev, (int)d->n_states,
                                                           d->nsp, kn->kmax, kn->kind, d->d_state_ds, d->d_ds,
                                                           status_buf, nint_buf, route, base + L.off_rec,
-                                                          reinterpret_cast<float2*>(base + L.off_hull), status_out);
+                                                          reinterpret_cast<float2*>(base + L.off_hull),
+                                                          reinterpret_cast<float*>(base + L.off_kxr), status_out);
     return check_cuda(cudaGetLastError());
 }

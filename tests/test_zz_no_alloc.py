@@ -26,14 +26,16 @@ def test_noalloc_matches_workspace_entry_point_twice(precision):
     buf, st = ds.spline_setup(count, x, w, kmax, kind, precision)
     ref = ds.psd_loglike(theta, buf, kmax, precision).cpu().numpy()
     ok = St_or == 0
-    tol = fp32_tolerance(ref, wl, P)
+    assert ok.sum() > 100
+    # the workspace entry point against the oracle, in the tolerance of its precision
+    if precision == 1:
+        np.testing.assert_allclose(ref[ok], L_or[ok], rtol=1e-12, atol=0)
+    else:
+        assert np.all(np.abs(ref[ok] - L_or[ok]) <= fp32_tolerance(L_or, wl, P)[ok])
     for _ in range(2):                      # two calls in a row share (and reuse) the scratch
         got = ds.psd_loglike_noalloc(theta, buf, kmax, precision).cpu().numpy()
-        assert np.array_equal(np.isneginf(got), np.isneginf(ref))
-        if precision == 1:
-            np.testing.assert_allclose(got[ok], ref[ok], rtol=1e-12, atol=0)
-        else:
-            assert np.all(np.abs(got[ok] - ref[ok]) <= tol[ok])
+        # same kernels, same work decomposition, fixed-order sums: the same bits
+        np.testing.assert_array_equal(got, ref)
     ds.close()
 
 
