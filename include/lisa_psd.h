@@ -189,8 +189,9 @@ lisa_status lisa_spline_setup(const lisa_data* data, const lisa_knots* knots,
 
 /* ---- log-likelihood ------------------------------------------------------------------------ */
 
-/* Bytes of scratch workspace the likelihood entry points need (per-(state, tile) partial sums,
- * per-state FP32 parameters and the compensated kernel's per-state work list).
+/* Bytes of scratch workspace the likelihood entry points need (per-(state, tile) partial sums of
+ * the fused and of the compensated kernel, per-state FP32 parameters and the compensated
+ * kernel's per-state work list).
  * with_grad = 0 for lisa_psd_loglike, 1 for lisa_psd_loglike_grad. */
 size_t lisa_workspace_bytes(const lisa_data* data, int32_t kmax, lisa_precision precision,
                             int32_t with_grad);
@@ -272,14 +273,14 @@ lisa_status lisa_averaged_periodogram(const double* d_dev, int32_t n_channels, i
  * inputs and outputs, but keeps its scratch (an error flag and the per-state partial sums) in a
  * fixed-size array that lives in the library's own device image, so the call allocates nothing.
  *
- *  - The array holds LISA_NOALLOC_SCRATCH_BYTES (4 MiB): 256 bytes plus 8 bytes per
- *    (state, tile) partial sum plus 48 bytes of FP32 parameters and 32 bytes of work list per
- *    state (each region rounded up to 256 bytes), i.e.
- *    lisa_workspace_bytes(data, kmax, precision, 0) must not exceed it.  The paper-scale
- *    workload (131,072 bins, 1,024 states) needs about 2.1 MiB at 512-bin tiles and 3.3 MiB at
- *    320-bin tiles, but 4.1 MiB at 256-bin tiles, which is rejected: the size depends on the
- *    tiling (lisa_data_set_tiling).  Larger problems get LISA_ERR_WORKSPACE and nothing is
- *    launched; use lisa_psd_loglike for them.
+ *  - The array holds LISA_NOALLOC_SCRATCH_BYTES (4 MiB): 256 bytes plus 16 bytes per
+ *    (state, tile) (the fused and the compensated kernels' partial sums) plus 84 bytes per state
+ *    (FP32 parameters, work list), each region rounded up to 256 bytes, i.e.
+ *    lisa_workspace_bytes(data, kmax, precision, 0) must not exceed it.  The size depends on the
+ *    tiling (lisa_data_set_tiling): the paper-scale workload (131,072 bins, 1,024 states) needs
+ *    about 2.1 MiB at 1,024-bin tiles, which fits, but 4.1 MiB at 512-bin tiles, which does not.
+ *    Larger problems get LISA_ERR_WORKSPACE and nothing is launched; use lisa_psd_loglike for
+ *    them.
  *  - Every GPU that loads the library holds the array until the process exits.
  *  - The device that holds `data` must be current: the array exists once per device, and a
  *    call made with another device current returns LISA_ERR_VALUE.

@@ -195,13 +195,30 @@ struct RobustEntry {
 static_assert(sizeof(RobustEntry) == 32, "two int4");
 
 // Forward workspace: error flag (int32 at 0) and work-list counter (uint64 at 8) in the first
-// 256 bytes | FP64 partial sums [state][tile] | StateParams [S] | RobustEntry [S].
+// 256 bytes | FP64 partial sums [state][tile] of the fused kernel | StateParams [S] |
+// RobustEntry [S] | int32 entry of each state in the work list (-1: none) [S] | FP64 sums of the
+// compensated kernel, one per (state, tile) unit of the work list [up to states x tiles].  The
+// two kinds of partial sums live apart, so the two kernels may run at the same time; the
+// finalize kernel adds both in a fixed order.
 constexpr size_t kWsCounterOff = 8;
 inline size_t ws_partials_bytes(const lisa_data* d) { return align256(sizeof(double) * (size_t)d->n_partials); }
 inline size_t ws_prm_bytes(const lisa_data* d) { return align256(sizeof(StateParams) * (size_t)d->n_states); }
-inline size_t ws_fwd_bytes(const lisa_data* d) {
-    return 256 + ws_partials_bytes(d) + ws_prm_bytes(d) + align256(sizeof(RobustEntry) * (size_t)d->n_states);
+inline size_t ws_rlist_bytes(const lisa_data* d) { return align256(sizeof(RobustEntry) * (size_t)d->n_states); }
+inline size_t ws_rent_bytes(const lisa_data* d) { return align256(sizeof(int32_t) * (size_t)d->n_states); }
+struct WsLayout {
+    size_t off_partial, off_prm, off_rlist, off_rent, off_rpart, bytes;
+};
+inline WsLayout ws_layout(const lisa_data* d) {
+    WsLayout L;
+    L.off_partial = 256;
+    L.off_prm = L.off_partial + ws_partials_bytes(d);
+    L.off_rlist = L.off_prm + ws_prm_bytes(d);
+    L.off_rent = L.off_rlist + ws_rlist_bytes(d);
+    L.off_rpart = L.off_rent + ws_rent_bytes(d);
+    L.bytes = L.off_rpart + ws_partials_bytes(d);
+    return L;
 }
+inline size_t ws_fwd_bytes(const lisa_data* d) { return ws_layout(d).bytes; }
 
 // Extra workspace of the adjoint entry point (after the forward region).
 size_t grad_extra_bytes(const lisa_data* d, int kmax);

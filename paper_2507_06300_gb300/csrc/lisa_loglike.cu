@@ -187,12 +187,14 @@ __device__ __forceinline__ float bin_x(const float* __restrict__ rec32, int64_t 
 // One warp per state.  For a state the spline setup routed to the compensated kernel, the warp
 // also finds the tiles that overlap the x-extent [h.x, h.y) of its ill-conditioned intervals --
 // tile t with first-bin x < h.y and last-bin x >= h.x, a contiguous range because x increases
-// with the bin -- and appends its entry (RobustEntry) to the work list.
+// with the bin -- appends its entry (RobustEntry) to the work list and records the entry's
+// position in rent[s] (-1 for every other state).
 __global__ void state_prep_kernel(int S, const double* __restrict__ theta, StateParams* __restrict__ prm,
                                   const int32_t* __restrict__ sstat, const float2* __restrict__ hull,
                                   const int32_t* __restrict__ state_ds, const DatasetDev* __restrict__ ds,
                                   const float* __restrict__ rec32, int tile_bins,
-                                  unsigned long long* __restrict__ rcount, RobustEntry* __restrict__ rlist) {
+                                  unsigned long long* __restrict__ rcount, RobustEntry* __restrict__ rlist,
+                                  int32_t* __restrict__ rent) {
     const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t s64 = gt >> 5;
     const int lane = threadIdx.x & 31;
@@ -215,6 +217,7 @@ __global__ void state_prep_kernel(int S, const double* __restrict__ theta, State
         p.lA_lo = lA.lo;
         p.pad0 = p.pad1 = p.pad2 = 0.f;
         prm[s] = p;
+        rent[s] = -1;
     }
     if (!(__ldg(sstat + s) & kRouted)) return;   // the same word in every lane
     const DatasetDev& D = ds[__ldg(state_ds + s)];
@@ -245,6 +248,7 @@ __global__ void state_prep_kernel(int S, const double* __restrict__ theta, State
         e.p0 = (uint32_t)(D.pbase + (int64_t)(s - D.s0) * nt + alo);
         e.nb_last = (int32_t)min((int64_t)tile_bins, D.npad - (int64_t)(blo - 1) * tile_bins);
         rlist[old >> 32] = e;
+        rent[s] = (int32_t)(old >> 32);
     }
 }
 
@@ -360,6 +364,9 @@ __global__ void __launch_bounds__(kThreads32, G == 8 ? 4 : (G == 4 ? 5 : 6))
     const int tid = threadIdx.x;
     const int lane = tid & 31;
     const size_t stage_floats = (size_t)tile_bins * kRec;
+    // the compensated kernel, launched next as a programmatic dependent, may place its CTAs as
+    // soon as this grid's CTAs leave SMs (it does not read what this kernel writes)
+    asm volatile("griddepcontrol.launch_dependents;");
     s_hm[tid] = 0u;
     // the CTA's items, [cta_first[c], cta_first[c + 1]) of the work list: with many items per
     // CTA a contiguous, cost-balanced block of the (dataset, state chunk, tile)-ordered list
@@ -765,12 +772,13 @@ __device__ __forceinline__ void robust_bin(const float* __restrict__ tb, int i, 
 // ill-conditioned bins is added to the (state, tile) partial the fused kernel wrote (one warp per
 // partial: deterministic).
 template <int C, bool HAS_H, bool BROKEN>
-__global__ void __launch_bounds__(kRobWarps * 32, 2)
-    loglike_robust_kernel(const unsigned long long* __restrict__ rcount, const RobustEntry* __restrict__ rlist,
-                          int tile_bins, const float* __restrict__ rec32, const float* __restrict__ xlo32,
-                          const float* __restrict__ elllo32, const StateParams* __restrict__ prm,
-                          const int32_t* __restrict__ nint, const float* __restrict__ srec, int kmax, int nsp,
-                          double* __restrict__ partial, int* __restrict__ err, unsigned wait_limit) {
+__device__ __forceinline__ void robust_units(const unsigned long long* __restrict__ rcount,
+                                             const RobustEntry* __restrict__ rlist, int tile_bins,
+                                             const float* __restrict__ rec32, const float* __restrict__ xlo32,
+                                             const float* __restrict__ elllo32, const StateParams* __restrict__ prm,
+                                             const int32_t* __restrict__ nint, const float* __restrict__ srec,
+                                             int kmax, int nsp, double* __restrict__ rpart, int* __restrict__ err,
+                                             unsigned wait_limit) {
     constexpr int NSP = C + (HAS_H ? 1 : 0);
     extern __shared__ float4 rsm[];
     __shared__ __align__(8) uint64_t rbar[kRobWarps];
@@ -808,7 +816,6 @@ __global__ void __launch_bounds__(kRobWarps * 32, 2)
         const int k_t = (int)(u - (int64_t)(uint32_t)ea.z);   // tile t0 + k_t
         const int64_t b0 = (int64_t)(((uint64_t)(uint32_t)eb.y << 32) | (uint32_t)eb.x) + (int64_t)k_t * tile_bins;
         const int nb = k_t == ea.w - 1 ? eb.w : tile_bins;
-        const int64_t pslot = (int64_t)(uint32_t)eb.z + k_t;
         const float* tbase = rec32 + (b0 >> 1) * kPairRec;   // b0 even
         __syncwarp();   // every lane is done with the previous unit's table
         if (lane == 0) {
@@ -893,9 +900,25 @@ __global__ void __launch_bounds__(kRobWarps * 32, 2)
         if (__any_sync(0xffffffffu, far != 0.0))
             for (int o = 16; o > 0; o >>= 1) far += __shfl_down_sync(0xffffffffu, far, o);
         const double acc = ((double)acc_ff.hi + (double)acc_ff.lo) + far;
-        if (lane == 0 && !(acc == 0.0)) partial[pslot] += acc;
+        if (lane == 0) rpart[u] = acc;
     }
 }
+
+template <int C, bool HAS_H, bool BROKEN>
+__global__ void __launch_bounds__(kRobWarps * 32, 2)
+    loglike_robust_kernel(const unsigned long long* __restrict__ rcount, const RobustEntry* __restrict__ rlist,
+                          int tile_bins, const float* __restrict__ rec32, const float* __restrict__ xlo32,
+                          const float* __restrict__ elllo32, const StateParams* __restrict__ prm,
+                          const int32_t* __restrict__ nint, const float* __restrict__ srec, int kmax, int nsp,
+                          double* __restrict__ rpart, int* __restrict__ err, unsigned wait_limit) {
+    robust_units<C, HAS_H, BROKEN>(rcount, rlist, tile_bins, rec32, xlo32, elllo32, prm, nint, srec, kmax, nsp, rpart,
+                                   err, wait_limit);
+    // launched as a programmatic dependent of the fused kernel, so that its CTAs can start on SMs
+    // the fused kernel's CTAs have left; it reads nothing the fused kernel writes, but it does not
+    // complete before the fused kernel has (the finalize kernel after it then sees both)
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
 
 // ---- plain FP64 path: the same decomposition, FP64 throughout, library exp10 / exp2 / log ----
 
@@ -979,7 +1002,9 @@ __global__ void __launch_bounds__(kThreads)
 // tree) plus the dataset constants.
 __global__ void finalize_kernel(int S, const int32_t* __restrict__ state_ds, const DatasetDev* __restrict__ ds,
                                 const int32_t* __restrict__ sstat, const double* __restrict__ partial,
-                                const int* __restrict__ err, int fp32, double* __restrict__ out) {
+                                const int32_t* __restrict__ rent, const RobustEntry* __restrict__ rlist,
+                                const double* __restrict__ rpart, const int* __restrict__ err, int fp32,
+                                double* __restrict__ out) {
     const int s = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (s >= S) return;   // uniform per warp
@@ -991,6 +1016,13 @@ __global__ void finalize_kernel(int S, const int32_t* __restrict__ state_ds, con
     const double* p = partial + D.pbase + (int64_t)(s - D.s0) * D.ntiles;
     double sum = 0.0;
     for (int t = lane; t < D.ntiles; t += 32) sum += p[t];
+    // FP32 mode: the compensated kernel's sums of this state's units, if it has any
+    const int e = fp32 ? rent[s] : -1;
+    if (e >= 0) {
+        const int4 ea = __ldg(reinterpret_cast<const int4*>(rlist + e));   // (s, t0, u0, nt)
+        const int64_t u0 = (int64_t)(uint32_t)ea.z;
+        for (int u = lane; u < ea.w; u += 32) sum += rpart[u0 + u];
+    }
     for (int o = 16; o > 0; o >>= 1) sum += __shfl_down_sync(0xffffffffu, sum, o);
     if (lane == 0) {
         double L = fp32 ? (-sum - D.Cnu + D.K) : (-sum + D.K);
@@ -1058,7 +1090,7 @@ template <int C, bool H, bool B, int G>
 cudaError_t launch_fp32_g(const lisa_data* d, const StateParams* prm, const int32_t* sstat, const int32_t* nint,
                           const float* kxr, unsigned long long* rcount, const RobustEntry* rlist, const float* srec,
                           int kmax,
-                          double* partial, int* err, cudaStream_t sm, bool prof) {
+                          double* partial, double* rpart, int* err, cudaStream_t sm, bool prof) {
     auto kern = loglike_fp32_kernel<C, H, B, G>;
     const size_t smem = 2 * (size_t)d->tiling.tile_bins * kRec * sizeof(float);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -1074,10 +1106,22 @@ cudaError_t launch_fp32_g(const lisa_data* d, const StateParams* prm, const int3
     auto rk = loglike_robust_kernel<C, H, B>;
     e = cudaFuncSetAttribute(rk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRobSmem);
     if (e != cudaSuccess) return e;
-    rk<<<d->rgrid, kRobWarps * 32, kRobSmem, sm>>>(rcount, rlist, d->tiling.tile_bins, d->d_rec32, d->d_xlo32,
-                                                   d->d_elllo32, prm, nint, srec, kmax, d->nsp, partial, err,
-                                                   d->wait_limit);
-    e = cudaGetLastError();
+    // launched as a programmatic dependent of the fused kernel (except when each kernel is timed
+    // on its own), so that its CTAs take the SMs the fused kernel's last CTAs leave idle
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)d->rgrid);
+    cfg.blockDim = dim3(kRobWarps * 32);
+    cfg.dynamicSmemBytes = kRobSmem;
+    cfg.stream = sm;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = prof ? 0 : 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    e = cudaLaunchKernelEx(&cfg, rk, rcount, rlist, d->tiling.tile_bins, (const float*)d->d_rec32,
+                           (const float*)d->d_xlo32, (const float*)d->d_elllo32, prm, nint, srec, kmax, d->nsp, rpart,
+                           err, d->wait_limit);
+    if (e == cudaSuccess) e = cudaGetLastError();
     prof_mark(d, prof, 2, sm);
     return e;
 }
@@ -1129,12 +1173,15 @@ int occupancy_c(int sgwb, const lisa_tiling& t) {
 template <int C, bool H, bool B>
 cudaError_t launch_fp32(const lisa_data* d, const StateParams* prm, const int32_t* sstat, const int32_t* nint,
                         const float* kxr, unsigned long long* rcount, const RobustEntry* rlist, const float* srec,
-                        int kmax, double* partial, int* err, cudaStream_t sm, bool prof) {
+                        int kmax, double* partial, double* rpart, int* err, cudaStream_t sm, bool prof) {
     switch (d->tiling.group) {
-        case 2: return launch_fp32_g<C, H, B, 2>(d, prm, sstat, nint, kxr, rcount, rlist, srec, kmax, partial, err, sm, prof);
-        case 8: return launch_fp32_g<C, H, B, 8>(d, prm, sstat, nint, kxr, rcount, rlist, srec, kmax, partial, err, sm, prof);
+        case 2: return launch_fp32_g<C, H, B, 2>(d, prm, sstat, nint, kxr, rcount, rlist, srec, kmax, partial, rpart, err, sm,
+                                                    prof);
+        case 8: return launch_fp32_g<C, H, B, 8>(d, prm, sstat, nint, kxr, rcount, rlist, srec, kmax, partial, rpart, err, sm,
+                                                    prof);
         default:
-            return launch_fp32_g<C, H, B, 4>(d, prm, sstat, nint, kxr, rcount, rlist, srec, kmax, partial, err, sm, prof);
+            return launch_fp32_g<C, H, B, 4>(d, prm, sstat, nint, kxr, rcount, rlist, srec, kmax, partial, rpart, err, sm,
+                                                    prof);
     }
 }
 
@@ -1154,16 +1201,19 @@ cudaError_t launch_fp64(const lisa_data* d, const double* theta, const int32_t* 
 template <int C>
 cudaError_t dispatch_model(const lisa_data* d, bool fp32, const double* theta, const StateParams* prm,
                            const int32_t* sstat, const int32_t* nint, const float* kxr, unsigned long long* rcount,
-                           const RobustEntry* rlist, const void* srec, int kmax, double* partial, int* err,
-                           cudaStream_t sm, bool prof) {
+                           const RobustEntry* rlist, const void* srec, int kmax, double* partial, double* rpart,
+                           int* err, cudaStream_t sm, bool prof) {
     const int h = d->sgwb_model;
     if (fp32) {
         const float* r = static_cast<const float*>(srec);
         if (h == 0)
-            return launch_fp32<C, false, false>(d, prm, sstat, nint, kxr, rcount, rlist, r, kmax, partial, err, sm, prof);
+            return launch_fp32<C, false, false>(d, prm, sstat, nint, kxr, rcount, rlist, r, kmax, partial, rpart, err, sm,
+                                                 prof);
         if (h == 1)
-            return launch_fp32<C, true, false>(d, prm, sstat, nint, kxr, rcount, rlist, r, kmax, partial, err, sm, prof);
-        return launch_fp32<C, true, true>(d, prm, sstat, nint, kxr, rcount, rlist, r, kmax, partial, err, sm, prof);
+            return launch_fp32<C, true, false>(d, prm, sstat, nint, kxr, rcount, rlist, r, kmax, partial, rpart, err, sm,
+                                                 prof);
+        return launch_fp32<C, true, true>(d, prm, sstat, nint, kxr, rcount, rlist, r, kmax, partial, rpart, err, sm,
+                                                 prof);
     }
     const double* r = static_cast<const double*>(srec);
     if (h == 0) return launch_fp64<C, false, false>(d, theta, sstat, nint, r, kmax, partial, sm, prof);
@@ -1227,9 +1277,12 @@ lisa_status lisa_psd_loglike(const lisa_data* d, const lisa_params* params, cons
     char* wsb = static_cast<char*>(ws);
     int* err = reinterpret_cast<int*>(wsb);
     unsigned long long* rcount = reinterpret_cast<unsigned long long*>(wsb + kWsCounterOff);
-    double* partial = reinterpret_cast<double*>(wsb + 256);
-    StateParams* prm = reinterpret_cast<StateParams*>(wsb + 256 + ws_partials_bytes(d));
-    RobustEntry* rlist = reinterpret_cast<RobustEntry*>(wsb + 256 + ws_partials_bytes(d) + ws_prm_bytes(d));
+    const WsLayout W = ws_layout(d);
+    double* partial = reinterpret_cast<double*>(wsb + W.off_partial);
+    StateParams* prm = reinterpret_cast<StateParams*>(wsb + W.off_prm);
+    RobustEntry* rlist = reinterpret_cast<RobustEntry*>(wsb + W.off_rlist);
+    int32_t* rent = reinterpret_cast<int32_t*>(wsb + W.off_rent);
+    double* rpart = reinterpret_cast<double*>(wsb + W.off_rpart);
     // the error flag and the work-list counter
     if (cudaMemsetAsync(wsb, 0, kWsCounterOff + sizeof(unsigned long long), sm) != cudaSuccess)
         return LISA_ERR_CUDA;
@@ -1238,7 +1291,7 @@ lisa_status lisa_psd_loglike(const lisa_data* d, const lisa_params* params, cons
         const int64_t threads = 32 * (int64_t)S;
         state_prep_kernel<<<(unsigned)((threads + 127) / 128), 128, 0, sm>>>(
             S, params->theta_dev, prm, sstat, hull, d->d_state_ds, d->d_ds, d->d_rec32, d->tiling.tile_bins, rcount,
-            rlist);
+            rlist, rent);
         if (cudaGetLastError() != cudaSuccess) return LISA_ERR_CUDA;
     }
     const bool prof = prof_active(d, sm);
@@ -1246,15 +1299,16 @@ lisa_status lisa_psd_loglike(const lisa_data* d, const lisa_params* params, cons
     cudaError_t e = cudaSuccess;
     if (d->n_items > 0)
         e = d->C == 3 ? dispatch_model<3>(d, fp32, params->theta_dev, prm, sstat, nint, kxr, rcount, rlist, srec, kmax,
-                                          partial, err, sm, prof)
+                                          partial, rpart, err, sm, prof)
                       : dispatch_model<2>(d, fp32, params->theta_dev, prm, sstat, nint, kxr, rcount, rlist, srec, kmax,
-                                          partial, err, sm, prof);
+                                          partial, rpart, err, sm, prof);
     else {
         prof_mark(d, prof, 1, sm);
         prof_mark(d, prof, 2, sm);
     }
     if (e != cudaSuccess) return LISA_ERR_CUDA;
-    finalize_kernel<<<(S + 7) / 8, 256, 0, sm>>>(S, d->d_state_ds, d->d_ds, sstat, partial, err, fp32 ? 1 : 0, out);
+    finalize_kernel<<<(S + 7) / 8, 256, 0, sm>>>(S, d->d_state_ds, d->d_ds, sstat, partial, rent, rlist, rpart, err,
+                                                 fp32 ? 1 : 0, out);
     e = cudaGetLastError();
     prof_mark(d, prof, 3, sm);
     if (prof) d->prof_valid = true;
