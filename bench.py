@@ -52,6 +52,9 @@ ADJ_FP32_PER_STATE_BIN = 132
 # exactness test for t = x - x_o in FP32), t takes 3 ops instead of 9 per spline: 108 in all.
 ADJ_FP32_PER_STATE_BIN_EXACT_T = 108
 ADJ_MUFU = (4, 3, 1)
+# FP64-pipe instructions per state-bin of the plain FP64 kernel as implemented (the library's exp10,
+# exp2, log and divisions included), counted by ncu on a 131,072-bin x 64-state A,E,T case
+FP64_PIPE_PER_STATE_BIN = 225
 
 
 def adjoint_exact_t(wl) -> bool:
@@ -459,6 +462,7 @@ def run_ours(args):
         ok = np.isfinite(L64)
         scale = np.maximum(np.abs(L64 - K_d[ds_of]), Cnu_d[ds_of])[ok]
         err = np.abs(L32[ok] - L64[ok])
+        wk = int(np.flatnonzero(ok)[np.argmax(err / scale)])    # worst state relative to the bound
         sb = I["sb"]
         sb_fused = sb - int(I["nbin_state"][routed].sum())
         sb_job = (replicas.sum_over_ranks([sb], dist if world > 1 else None, device="cuda")[0] if sharded
@@ -471,8 +475,16 @@ def run_ours(args):
                             "loglike_ms": ll64, "steps": max(1, fp64_steps)},
              "accuracy_fp32_vs_fp64": {"max_abs_nats": float(err.max()), "median_abs_nats": float(np.median(err)),
                                        "max_rel_to_scale": float((err / scale).max()), "states": int(ok.sum())},
+             "worst_state": {"state": wk, "L32": float(L32[wk]), "L64": float(L64[wk]),
+                             "scale": float(max(abs(L64[wk] - K_d[ds_of[wk]]), Cnu_d[ds_of[wk]]))},
              "tiling": I["tiling"], "autotune_top": [[t, round(v, 4)] for t, v in I["table"][:5]]}
         r["speedup_fp32_vs_fp64"] = r["value"] / r["fp64_plain"]["value"]
+        fp64_rate = (sb / (ll64 / 1e3)) * FP64_PIPE_PER_STATE_BIN    # FP64-pipe instructions per second
+        r["fp64_plain"]["roofline"] = {
+            "bound": "alu", "pipe": "FP64", "achieved": fp64_rate / 1e9, "peak": rates["dfma"] / 1e9, "unit": "Gop/s",
+            "frac": fp64_rate / rates["dfma"], "ops_per_state_bin": FP64_PIPE_PER_STATE_BIN,
+            "ops_source": "ncu thread-level FP64-pipe instruction count per state-bin (profiles/loglike_fp64_ops.md)",
+            "peak_source": "measured live by lisa_pipe_rates (fma.rn.f64)", "timing": "the likelihood graph only"}
         return r, ev32, clocks
 
     def roofline_of(I, r):
@@ -482,6 +494,12 @@ def run_ours(args):
         ent = roofline_entry(fused_rate, R, peaks["hbm_gbs"], bpsb)
         ent.update({"kernel": "loglike_fp32_kernel (fused FP32 likelihood)",
                     "ceilings_state_bins_per_s": {"fp32": R["fp32"], "mufu": R["mufu"], "hbm": R["hbm"]},
+                    # the kernel's own mix of FMA-pipe and MUFU work run as independent chains: the
+                    # two pipes overlap only in part, so the mix is slower than either pipe alone
+                    "mixed_pipe": {"ceiling_state_bins_per_s": rates["mix"], "frac": fused_rate / rates["mix"],
+                                   "ceiling_vs_fp32_alone": rates["mix"] / R["fp32"],
+                                   "mix": "per two state-bins: 38 packed FP32 ops, 8 ex2, 2 rcp, 2 lg2",
+                                   "source": "lisa_pipe_rates LISA_PIPE_MIX, measured live"},
                     "mufu_frac": fused_rate / R["mufu"], "hbm_frac": fused_rate / R["hbm"],
                     "step_frac": (r["value"] / world) / min(R["fp32"], R["mufu"], R["hbm"]),
                     "hbm_algorithmic_bytes_per_state_bin": bpsb})
@@ -741,6 +759,20 @@ def run_ours(args):
 
     if rank == 0 and not args.no_cpu_baseline:
         cores, cpu_model, arch = host_cpu_info()
+        # the state where FP32 and FP64 disagree most (relative to the FP32 bound), checked by the
+        # FP64 oracle on the host
+        import oracle
+        ws_ = head["worst_state"]
+        s_ = ws_["state"]
+        ds_ = wl.dataset(0)
+        ds_["P"] = P_head
+        L_or, _ = oracle.loglike(ds_, wl.theta[s_:s_ + 1],
+                                 {k: (v[s_:s_ + 1] if isinstance(v, np.ndarray) else v)
+                                  for k, v in wl.knots.as_dict().items()})
+        line["accuracy_fp32_vs_fp64"]["worst_state_vs_oracle"] = {
+            "state": s_, "fp32_minus_oracle_nats": ws_["L32"] - float(L_or[0]),
+            "fp64_minus_oracle_nats": ws_["L64"] - float(L_or[0]),
+            "fp32_rel_to_scale": abs(ws_["L32"] - float(L_or[0])) / ws_["scale"], "bound": 1e-6}
         rate, n, el = cpu_oracle_rate(wl, P_head, args.cpu_seconds)
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
                                 "sample": f"{n} whole state(s) x {wl.n_bins} bins of the same workload, {el:.1f} s",

@@ -28,12 +28,19 @@ typedef enum lisa_pipe_op {
     LISA_PIPE_FFMA2 = 4,    /* fma.rn.f32x2 (packed pair): chain x <- x a + b on both halves */
     LISA_PIPE_DFMA = 5,     /* fma.rn.f64: chain x <- x a + b (the FP64 pipe that bounds the FP64
                                paths and the data preparation; iters / 8 steps per chain) */
-    LISA_PIPE_N_OPS = 6
+    LISA_PIPE_MIX = 6,      /* the fused FP32 likelihood's instruction mix per pair block of the
+                               A,E,T power-law model (38 packed FP32 operations, 8 ex2, 2 rcp,
+                               2 lg2) as independent chains, iters / 4 iterations; reported in
+                               state-bins per second (one iteration = two state-bins).  The FMA
+                               and MUFU pipes overlap only in part, so this rate is below both
+                               single-pipe ceilings: it is what the mix itself allows. */
+    LISA_PIPE_N_OPS = 7
 } lisa_pipe_op;
 
 /* Measures, on the current device, the sustained rate of each lisa_pipe_op in lane operations
  * per second (one lane operation = one result: an ex2, a reciprocal, a log2 or an FMA; a
- * packed FMA counts two) and writes them to rates[LISA_PIPE_N_OPS] (HOST array, caller-owned).
+ * packed FMA counts two; LISA_PIPE_MIX in state-bins per second) and writes them to
+ * rates[LISA_PIPE_N_OPS] (HOST array, caller-owned).
  *  - iters: chain steps per thread (>= 16; 2048 runs each kernel for roughly a millisecond).
  *  - Each kernel is launched once untimed, then timed over `reps` (>= 1) launches on `stream`;
  *    the best repetition is reported.

@@ -64,7 +64,7 @@ EXPORTS = ["lisa_data_create", "lisa_data_destroy", "lisa_data_get_info", "lisa_
            "lisa_psd_loglike_grad", "lisa_model_psd", "lisa_psd_loglike_noalloc", "lisa_status_string",
            "lisa_pipe_rates", "lisa_data_set_profiling", "lisa_data_kernel_ms", "lisa_fd_synthesize",
            "lisa_averaged_periodogram", "lisa_workspace_status", "lisa_data_set_test_wait"]
-PIPE_OPS = ("ex2", "rcp", "lg2_ex2", "ffma", "ffma2", "dfma")   # order of lisa_pipe_op
+PIPE_OPS = ("ex2", "rcp", "lg2_ex2", "ffma", "ffma2", "dfma", "mix")   # order of lisa_pipe_op
 NOALLOC_SCRATCH_BYTES = 4 * 1024 * 1024
 
 _lock = threading.Lock()
@@ -390,7 +390,8 @@ def averaged_periodogram(d, f0, df, bin_offset, stream=None):
 
 def pipe_rates(iters=2048, reps=3, stream=None) -> dict:
     """``lisa_pipe_rates``: measured lane operations per second of the MUFU, FP32 and FP64 pipes on
-    the current device, keyed by PIPE_OPS (a packed FMA counts two).  Synchronises."""
+    the current device, keyed by PIPE_OPS (a packed FMA counts two), and under "mix" the
+    state-bins per second that the fused kernel's instruction mix allows.  Synchronises."""
     out = (_c_dbl * len(PIPE_OPS))()
     _check(load().lisa_pipe_rates(int(iters), int(reps), out, _stream_handle(stream)), "lisa_pipe_rates")
     return {k: float(out[i]) for i, k in enumerate(PIPE_OPS)}

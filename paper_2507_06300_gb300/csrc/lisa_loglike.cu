@@ -675,6 +675,9 @@ __device__ __forceinline__ ff inv_plus_log(ff lS, float nu, double& far) {
     return ff{0.f, 0.f};
 }
 
+// log2 of FP64's overflow threshold: 10^P overflows double precision from P = 1024 in log2 units
+constexpr float kP2Overflow = 1024.0f;
+
 // Compensated kernel staging: each warp stages its tile in chunks of kRobChunk bins into its own
 // shared-memory slice (the pair-block table by one bulk asynchronous copy, the low parts of x and
 // ell by lane loads), then evaluates the chunk from shared memory.  8 warps per CTA: two CTAs
@@ -720,6 +723,15 @@ __device__ __forceinline__ void robust_bin(const float* __restrict__ tb, int i, 
             const float tt = x.hi - iv[a].xo.hi;
             P[a] = ff{fmaf(fmaf(fmaf(iv[a].c[3].hi, tt, iv[a].c[2].hi), tt, iv[a].c[1].hi), tt, iv[a].c[0].hi), 0.f};
         }
+    }
+    // the definition's 10^P as FP64 evaluates it: beyond 2^1024 (P >= 308.25 decades) the PSD is
+    // not finite, and the state's log L is -inf in every precision (as in the FP64 path)
+    bool over = false;
+#pragma unroll
+    for (int a = 0; a < NSP; ++a) over |= !(P[a].hi < kP2Overflow);
+    if (over) {
+        if (nu != 0.f) far = INFINITY;
+        return;
     }
     const ff ell = {fld(tb, i, 1), es[i]};
     ff lEh = {-INFINITY, 0.f};

@@ -29,6 +29,50 @@ __global__ void __launch_bounds__(kBlock) pipe_rate_kernel(int iters, float a, f
         out[g] = (float)s;
         return;
     }
+    if (OP == LISA_PIPE_MIX) {
+        // the fused FP32 likelihood's instruction mix per pair block (two bins of one state, A,E,T
+        // with a power-law SGWB): 38 packed FP32 operations, 8 ex2, 2 rcp, 2 lg2, here as
+        // independent chains so that only the pipes, not latency, set the rate
+        float2 v[kChains];
+        float m[kChains];
+#pragma unroll
+        for (int u = 0; u < kChains; ++u) {
+            v[u] = make_float2(0.25f + 0.01f * u, 0.5f + 1e-6f * (g & 1023));
+            m[u] = 0.3f + 0.02f * u;
+        }
+        const float2 a2 = make_float2(a, a), b2 = make_float2(b, b);
+        for (int i = 0; i < iters; ++i) {
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+#pragma unroll
+                for (int u = 0; u < kChains; ++u) v[u] = __ffma2_rn(v[u], a2, b2);
+#pragma unroll
+            for (int u = 0; u < 6; ++u) v[u] = __ffma2_rn(v[u], a2, b2);
+#pragma unroll
+            for (int u = 0; u < kChains; ++u) {
+                float y;
+                const float x = -m[u];   // x <- 2^-x converges to 0.6412
+                asm volatile("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+                m[u] = y;
+            }
+            // two reciprocals and two log2s, each folded back into its chain so that nothing is
+            // optimised away (x <- 1/x damped, x <- log2(x + 1.5) stay in (0, 2))
+            float y0, y1, y2, y3;
+            asm volatile("rcp.approx.ftz.f32 %0, %1;" : "=f"(y0) : "f"(m[0]));
+            asm volatile("rcp.approx.ftz.f32 %0, %1;" : "=f"(y1) : "f"(m[1]));
+            asm volatile("lg2.approx.ftz.f32 %0, %1;" : "=f"(y2) : "f"(m[2] + 1.5f));
+            asm volatile("lg2.approx.ftz.f32 %0, %1;" : "=f"(y3) : "f"(m[3] + 1.5f));
+            m[0] = fmaf(y0, 0.5f, 0.5f);
+            m[1] = fmaf(y1, 0.5f, 0.5f);
+            m[2] = y2;
+            m[3] = y3;
+        }
+        float s = 0.f;
+#pragma unroll
+        for (int u = 0; u < kChains; ++u) s += v[u].x + v[u].y + m[u];
+        out[g] = s;
+        return;
+    }
     if (OP == LISA_PIPE_FFMA2) {
         float2 v[kChains];
 #pragma unroll
@@ -104,8 +148,11 @@ lisa_status time_op(int iters, int reps, int n_sm, float* buf, cudaStream_t sm, 
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (st != LISA_SUCCESS) return st;
+    // lane operations per chain step (a packed FMA, or lg2 + ex2, counts two); the mix counts
+    // state-bins: one iteration of a thread is one pair block, two state-bins
     const double per_step = (OP == LISA_PIPE_LG2_EX2 || OP == LISA_PIPE_FFMA2) ? 2.0 : 1.0;
-    const double ops = (double)blocks * kBlock * kChains * (double)iters * per_step;
+    const double ops = OP == LISA_PIPE_MIX ? (double)blocks * kBlock * 2.0 * (double)iters
+                                           : (double)blocks * kBlock * kChains * (double)iters * per_step;
     *rate = best > 0.f ? ops / (best * 1e-3) : 0.0;
     return LISA_SUCCESS;
 }
@@ -131,6 +178,7 @@ extern "C" lisa_status lisa_pipe_rates(int32_t iters, int32_t reps, double* rate
     if (st == LISA_SUCCESS) st = time_op<LISA_PIPE_FFMA>(iters, reps, n_sm, buf, sm, &rates[LISA_PIPE_FFMA]);
     if (st == LISA_SUCCESS) st = time_op<LISA_PIPE_FFMA2>(iters, reps, n_sm, buf, sm, &rates[LISA_PIPE_FFMA2]);
     if (st == LISA_SUCCESS) st = time_op<LISA_PIPE_DFMA>(iters, reps, n_sm, buf, sm, &rates[LISA_PIPE_DFMA]);
+    if (st == LISA_SUCCESS) st = time_op<LISA_PIPE_MIX>(iters / 4, reps, n_sm, buf, sm, &rates[LISA_PIPE_MIX]);
     cudaStreamSynchronize(sm);
     cudaFree(buf);
     return st;

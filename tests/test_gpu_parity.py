@@ -163,28 +163,81 @@ def test_model_psd_matches_oracle(tiny):
 @pytest.mark.parametrize("precision", [FP64, FP32])
 def test_paper_scale_sampled_states(precision):
     """131,072 bins x 1,024 states (the benchmark workload and launch configuration): the oracle
-    checks 6 sampled states; every state must agree with the GPU FP64 path."""
+    checks 6 sampled states and the two where FP32 and FP64 disagree most; every state must
+    agree with the GPU FP64 path."""
     wl = synth.workload("paper")
     ds = oracle_dataset(wl)
     P = ds["P"]
     L, St = gpu_eval(wl, P, precision)
+    L_other, _ = gpu_eval(wl, P, FP64 if precision == FP32 else FP32)
     rng = np.random.default_rng(0)
     pick = np.sort(rng.choice(wl.n_states, 6, replace=False))
     pick[0] = 0                                 # one cold-chain state (near the injection)
+    # and the states where FP32 and FP64 disagree most, in nats and relative to the FP32 bound
+    # (extreme prior draws: held to the FP32 bound in both precisions, see test_gpu_scale)
+    good = np.flatnonzero((St == 0) & np.isfinite(L) & np.isfinite(L_other))
+    err = np.abs(L[good] - L_other[good])
+    tol64 = fp32_tolerance(L if precision == FP64 else L_other, wl, P)[good]
+    worst = np.setdiff1d([good[np.argmax(err)], good[np.argmax(err / tol64)]], pick)
+    rnd = np.concatenate([np.ones(len(pick), bool), np.zeros(len(worst), bool)])
+    pick = np.concatenate([pick, worst])
     th, kn = wl.theta[pick], {k: (v[pick] if isinstance(v, np.ndarray) else v)
                               for k, v in wl.knots.as_dict().items()}
     L_ref, St_ref = oracle.loglike(ds, th, kn)
-    np.testing.assert_array_equal(St[pick], St_ref)
+    # the GPU status word holds the knot bits; a PSD or log L outside FP64's finite range (the
+    # oracle's bit 32) shows as log L = -inf
+    np.testing.assert_array_equal(St[pick], St_ref & ~32)
+    assert np.all(np.isneginf(L[pick][(St_ref & 32) != 0]))
     ok = St_ref == 0
+    tol = fp32_tolerance(L_ref, dataclasses.replace(wl, state_offset=np.array([0, len(pick)])), P)
+    assert np.all(np.abs(L[pick][ok] - L_ref[ok]) <= tol[ok])
     if precision == FP64:
-        np.testing.assert_allclose(L[pick][ok], L_ref[ok], rtol=1e-12)
+        np.testing.assert_allclose(L[pick][ok & rnd], L_ref[ok & rnd], rtol=1e-12)
     else:
-        tol = fp32_tolerance(L_ref, dataclasses.replace(wl, state_offset=np.array([0, len(pick)])), P)
-        assert np.all(np.abs(L[pick][ok] - L_ref[ok]) <= tol[ok])
-        L64, _ = gpu_eval(wl, P, FP64)
+        L64 = L_other
         good = St == 0
+        np.testing.assert_array_equal(np.isfinite(L[good]), np.isfinite(L64[good]))
+        fin = good & np.isfinite(L64)
         tol_all = fp32_tolerance(L64, wl, P)
-        assert np.all(np.abs(L[good] - L64[good]) <= tol_all[good])
+        assert np.all(np.abs(L[fin] - L64[fin]) <= tol_all[fin])
+
+
+@pytest.mark.parametrize("kind", [0, 1])
+def test_psd_beyond_the_fp64_range_is_minus_inf(kind):
+    """A perturbation of more than 308.25 decades makes the definition's 10^P overflow double
+    precision: the oracle marks the state non-finite, and both GPU precisions return log L = -inf
+    (the FP32 path works in the log domain on such intervals and applies the same FP64 range).
+    Just inside the range (300 decades) all three agree on a finite value."""
+    wl = synth.workload("tiny")
+    ds = oracle_dataset(wl)
+    P = ds["P"]
+    S = 4
+    th = np.repeat(wl.theta_true, S, axis=0)
+    nsp = wl.n_splines
+    kmax = 1
+    kn = {"count": np.zeros((S, nsp), np.int32), "x": np.zeros((S, nsp, kmax)),
+          "w": np.zeros((S, nsp, kmax + 2)), "kmax": kmax, "kind": kind}
+    kn["w"][0, 2, 0] = 320.0                   # channel T noise, left edge: overflows near x_lo
+    kn["w"][1, 3, kmax + 1] = 330.0            # SGWB, right edge
+    kn["w"][2, 1, 0] = 300.0                   # channel E, left edge: large but finite
+    kn["count"][3, 0] = 1                      # a one-knot spline reaching -310 decades: the
+    kn["x"][3, 0, 0] = -3.0                    # noise term underflows, the SGWB term remains
+    kn["w"][3, 0, 1] = -310.0
+    L_ref, St_ref = oracle.loglike(ds, th, kn)
+    assert list(St_ref & 32) == [32, 32, 0, 0]
+    knots = synth.Knots(count=kn["count"], x=kn["x"], w=kn["w"], kmax=kmax, kind=kind)
+    wl4 = dataclasses.replace(wl, state_offset=np.array([0, S], np.int64), theta=th, knots=knots)
+    for prec in (FP64, FP32):
+        L, St = gpu_eval(wl4, P, prec)
+        assert np.all(St == 0)
+        assert np.isneginf(L[0]) and np.isneginf(L[1]), (prec, L)
+        assert np.all(np.isfinite(L[2:])), (prec, L)
+        if prec == FP64:
+            np.testing.assert_allclose(L[2:], L_ref[2:], rtol=1e-12)
+        else:
+            K = -np.sum(wl.nu * np.log(P).sum(axis=0))
+            tol = 1e-6 * np.maximum(np.abs(L_ref[2:] - K), wl.n_channels * wl.nu.sum())
+            assert np.all(np.abs(L[2:] - L_ref[2:]) <= tol), (L[2:], L_ref[2:])
 
 
 @pytest.mark.parametrize("kind,tiling", [

@@ -16,6 +16,13 @@ def test_pipe_rates_are_positive_and_plausible():
         # lane operations per second on a whole GPU: well above 1e11 and below 1e15
         assert 1e11 < v < 1e15, (k, v)
     assert r["ffma2"] >= 0.5 * r["ffma"]
+    # the fused kernel's mix (38 packed FP32 ops, 8 ex2, 2 rcp, 2 lg2 per two state-bins): no
+    # faster than either pipe alone allows, no slower than the two pipes one after the other
+    t_fma = 38.0 * 2.0 / r["ffma2"] / 2.0                       # seconds per state-bin
+    t_lg2 = max(2.0 / r["lg2_ex2"] - 1.0 / r["ex2"], 1.0 / r["ex2"])
+    t_mufu = (4.0 / r["ex2"] + 1.0 / r["rcp"] + t_lg2)
+    assert r["mix"] <= 1.05 / max(t_fma, t_mufu), r
+    assert r["mix"] >= 0.9 / (t_fma + t_mufu), r
 
 
 def test_kernel_times_of_a_recorded_call():

@@ -1,6 +1,7 @@
 """Parity at the full sizes of the batched-dataset and full-form workloads, in the launch
 configuration the benchmark uses (default tiling after the data object is built): the oracle
-checks sampled states one by one; every state's FP32 result must agree with the GPU FP64 path
+checks sampled states one by one, and the two states where FP32 and FP64 disagree most (in nats,
+and relative to the FP32 bound); every state's FP32 result must agree with the GPU FP64 path
 within the FP32 tolerance."""
 import numpy as np
 import pytest
@@ -30,15 +31,38 @@ def _sampled_oracle(wl, picks_by_dataset, P):
     return np.concatenate(L), np.concatenate(St)
 
 
+def _worst_states(wl, P, L32, L64, St):
+    """The states where FP32 and FP64 disagree most, in nats and relative to the FP32 bound, as
+    (dataset, local state) pairs: the oracle checks them too (Sec. III.C sum over bins)."""
+    good = np.flatnonzero((St == 0) & np.isfinite(L64) & np.isfinite(L32))
+    err = np.abs(L32[good] - L64[good])
+    tol = fp32_tolerance(L64, wl, P)[good]
+    out = []
+    for g in {int(good[np.argmax(err)]), int(good[np.argmax(err / tol)])}:
+        d = int(np.searchsorted(wl.state_offset, g, side="right") - 1)
+        out.append((d, np.array([g - int(wl.state_offset[d])])))
+    return out
+
+
 def _check_scale(wl, P, picks_by_dataset):
-    gidx = np.concatenate([wl.state_offset[d] + np.asarray(l) for d, l in picks_by_dataset])
-    L_ref, St_ref = _sampled_oracle(wl, picks_by_dataset, P)
     L64, St = gpu_eval(wl, P, FP64)
     L32, St32 = gpu_eval(wl, P, FP32)
+    n_random = sum(len(l) for _, l in picks_by_dataset)
+    picks_by_dataset = list(picks_by_dataset) + _worst_states(wl, P, L32, L64, St)
+    gidx = np.concatenate([wl.state_offset[d] + np.asarray(l) for d, l in picks_by_dataset])
+    L_ref, St_ref = _sampled_oracle(wl, picks_by_dataset, P)
+    # the worst states are extreme prior draws whose cubic intervals cancel strongly: two correct
+    # FP64 evaluations of such a spline differ by ~(conditioning) x eps, so they are held to the
+    # FP32 bound below; the random picks to 1e-12 in FP64
+    rnd = np.arange(len(gidx)) < n_random
     np.testing.assert_array_equal(St, St32)
-    np.testing.assert_array_equal(St[gidx], St_ref)
+    # the GPU status word holds the knot bits; a PSD or log L outside FP64's finite range (the
+    # oracle's bit 32) shows as log L = -inf in both precisions
+    np.testing.assert_array_equal(St[gidx], St_ref & ~32)
+    nonfin = (St_ref & 32) != 0
+    assert np.all(np.isneginf(L64[gidx][nonfin])) and np.all(np.isneginf(L32[gidx][nonfin]))
     ok = St_ref == 0
-    np.testing.assert_allclose(L64[gidx][ok], L_ref[ok], rtol=1e-12)
+    np.testing.assert_allclose(L64[gidx][ok & rnd], L_ref[ok & rnd], rtol=1e-12)
     tol_ref = np.empty(len(gidx))
     for k, g in enumerate(gidx):
         d = int(np.searchsorted(wl.state_offset, g, side="right") - 1)
@@ -46,10 +70,14 @@ def _check_scale(wl, P, picks_by_dataset):
         K = -np.sum(wl.nu[b0:b1] * np.log(P[:, b0:b1]).sum(axis=0))
         tol_ref[k] = 1e-6 * max(abs(L_ref[k] - K), wl.n_channels * wl.nu[b0:b1].sum())
     assert np.all(np.abs(L32[gidx][ok] - L_ref[ok]) <= tol_ref[ok])
+    assert np.all(np.abs(L64[gidx][ok] - L_ref[ok]) <= tol_ref[ok])
     good = St == 0
+    # every valid state: finite in FP32 exactly where it is finite in FP64, and within the bound
+    np.testing.assert_array_equal(np.isfinite(L32[good]), np.isfinite(L64[good]))
+    fin = good & np.isfinite(L64)
+    assert np.all(np.isneginf(L32[good & ~fin]))
     tol_all = fp32_tolerance(L64, wl, P)
-    assert np.all(np.isfinite(L32[good]))
-    assert np.all(np.abs(L32[good] - L64[good]) <= tol_all[good])
+    assert np.all(np.abs(L32[fin] - L64[fin]) <= tol_all[fin])
 
 
 def test_full_form_workload_sampled_states():
