@@ -74,6 +74,13 @@ def _load():
             lib.lo_loglike_grad_scaled.argtypes = common + [D, D, D, c_double, c_double, c_double, c_int,
                                                             c_int, c_int, D, I, D, D, D, D, D, I]
             lib.lo_loglike_grad_scaled.restype = None
+            full = [c_int, c_int, i64, D]
+            lib.lo_model_cov_full.argtypes = full + [D, c_double, c_double, c_double, c_int, c_int, c_int, D, I, D, D,
+                                                     D, I]
+            lib.lo_model_cov_full.restype = None
+            lib.lo_loglike_full.argtypes = full + [D, D, D, c_double, c_double, c_double, c_int, c_int, c_int, D, I,
+                                                   D, D, D, D, I]
+            lib.lo_loglike_full.restype = None
             _lib = lib
     return _lib
 
@@ -253,3 +260,60 @@ def loglike_grad_scale(ds, theta, knots):
     _, pst = _i(st)
     _load().lo_loglike_grad_scaled(*pa, kind, kmax, S, *sa, po, pg, ps, pst)
     return out, g, sc, st
+
+
+# ---- full covariance (reading R16: the dense 3x3 covariance of Sec. III.A) -------------------------
+
+def n_splines_full(ds):
+    """3 noise splines, the SGWB spline if present, then z_AE, z_AT, z_ET."""
+    return 3 + (1 if int(ds.get("sgwb_model", 1)) != 0 else 0) + 3
+
+
+def _full_args(ds):
+    f, pf = _d(ds["f"])
+    N = f.size
+    nu = np.ascontiguousarray(np.broadcast_to(np.asarray(ds.get("nu", 1.0), dtype=np.float64), (N,)))
+    nu, pnu = _d(nu)
+    P9 = ds.get("P9")
+    P9 = np.zeros((9, N)) if P9 is None else P9
+    P9, pP = _d(np.asarray(P9).reshape(9, N))
+    R = ds.get("R")
+    R = np.zeros((3, N)) if R is None else R
+    R, pR = _d(np.asarray(R).reshape(3, N))
+    keep = (f, nu, P9, R)
+    return keep, N, pf, pnu, pP, pR
+
+
+def model_cov_full(ds, theta, knots):
+    """Full-covariance model C for every state: returns (cov [S, 6, N] = C00, C11, C22, C01, C02,
+    C12 in physical units, status [S])."""
+    keep1, N, pf, pnu, pP, pR = _full_args(ds)
+    keep2, S, nsp, kmax, kind, sa = _state_args(theta, knots)
+    assert nsp == n_splines_full(ds)
+    out = np.empty((S, 6, N))
+    st = np.zeros(S, dtype=np.int32)
+    _, po = _d(out)
+    _, pst = _i(st)
+    _load().lo_model_cov_full(int(ds.get("sgwb_model", 1)), int(ds.get("tdi_form", 0)), N, pf, pR,
+                              float(ds["x_lo"]), float(ds["x_hi"]), float(ds.get("f_ref", 1e-3)), kind, kmax, S,
+                              *sa, po, pst)
+    return out, st
+
+
+def loglike_full(ds, theta, knots, return_im=False):
+    """Sec. III.C log-likelihood with the dense covariance, every state: returns (logL [S], status
+    [S]) (and, with return_im, the largest |Im tr(C^-1 P)| / |Re tr| over bins).  ds["P9"] [9, N]:
+    P_AA, P_EE, P_TT, Re/Im P_AE, Re/Im P_AT, Re/Im P_ET."""
+    keep1, N, pf, pnu, pP, pR = _full_args(ds)
+    keep2, S, nsp, kmax, kind, sa = _state_args(theta, knots)
+    assert nsp == n_splines_full(ds)
+    out = np.empty(S)
+    im = np.zeros(S)
+    st = np.zeros(S, dtype=np.int32)
+    _, po = _d(out)
+    _, pim = _d(im)
+    _, pst = _i(st)
+    _load().lo_loglike_full(int(ds.get("sgwb_model", 1)), int(ds.get("tdi_form", 0)), N, pf, pnu, pP, pR,
+                            float(ds["x_lo"]), float(ds["x_hi"]), float(ds.get("f_ref", 1e-3)), kind, kmax, S,
+                            *sa, po, pim, pst)
+    return (out, st, im) if return_im else (out, st)

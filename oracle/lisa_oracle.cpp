@@ -15,6 +15,9 @@
 //   linear fallback ................... Sec. III.A (fewer than two in-between knots)
 //   Akima slopes and coefficients ...... Appendix A
 //   per-bin Wishart term, bin sum ...... Sec. III.C (Wishart log-density, sum over bins)
+//   full 3x3 covariance ................ Sec. III.A (the complete analysis with six flexible
+//                                        noise terms), Sec. III.C (the same Wishart term with a
+//                                        dense C), reading R16 below
 //
 // Readings taken where the paper is ambiguous or garbled:
 //   R1  covariance: C_c = S_c (the printed factor 1/2 is dropped; the periodogram is normalised
@@ -37,6 +40,17 @@
 //   R9  broken power law (sgwb_model 2): slope n1 below f_ref, n2 at and above it.
 //   R10 natural cubic spline (kind 1) is the C^2 alternative named next to Akima; its
 //       coefficients come from the textbook second-derivative tridiagonal system.
+//   R16 full covariance (the paper defers the construction of a positive-definite matrix from six
+//       flexible terms to another reference): in the A, E, T basis,
+//         C = D^{1/2} R D^{1/2} + H,  D = diag(S_n,cc 10^{P_n,c}),  H = diag(S_h,cc 10^{P_h}),
+//         R = L L^T,  L = [[1, 0, 0], [r_AE, s_AE, 0], [r_AT, r_ET s_AT, s_AT s_ET]],
+//         r = z / sqrt(1 + z^2),  s = 1 / sqrt(1 + z^2)  (= sqrt(1 - r^2)),
+//       with z_AE, z_AT, z_ET three more variable-knot splines whose values (not exponents) are
+//       the flexible off-diagonal terms: three diagonal and three correlation terms, C positive
+//       definite for any spline values, and the diagonal model exactly when z = 0.  C is real, so
+//       only the real parts of the averaged periodogram's off-diagonal entries enter
+//       tr(C^-1 P); the oracle forms the complex trace and checks that its imaginary part
+//       vanishes only through the Hermitian symmetry of P.
 //
 // Layouts (all row-major, caller-owned):
 //   theta [S][5]              a_oms = A_OMS/1e-12, a_tm = A_TM/1e-15, log10 A, n1, n2
@@ -54,6 +68,7 @@
 // An invalid state gets logL = -inf and a zero gradient.
 
 #include <algorithm>
+#include <complex>
 #include <cmath>
 #include <cstdint>
 #include <limits>
@@ -598,6 +613,146 @@ void lo_loglike_grad_scaled(int C, int sgwb_model, int tdi_form, int64_t N, cons
             for (int slot : wslots) ga[slot] = run(0, slot, gsa ? &gsa[slot] : &dummy);
             for (int j = 0; j < k; ++j) ga[kmax + 2 + j] = run(1, j, gsa ? &gsa[kmax + 2 + j] : &dummy);
         }
+    }
+}
+
+}  // extern "C"
+
+namespace {
+// Full covariance (reading R16).  Splines: 0..2 noise of A, E, T (exponents), 3 the SGWB (if the
+// model has one), then z_AE, z_AT, z_ET (values).  cov layout per bin: C00, C11, C22, C01, C02, C12.
+int n_splines_full(const Problem& pb) { return 3 + (pb.sgwb_model != 0 ? 1 : 0) + 3; }
+
+// The 3x3 model covariance of one state at bin i (physical units).
+void full_cov(const Problem& pb, const double* th, const std::vector<Spline<double>>& sps, int64_t i,
+              double cov[6]) {
+    const double f = pb.f[i];
+    const double x = std::log10(f);
+    double sn[3];
+    noise_aet(pb.tdi_form, f, th[0] * 1e-12, th[1] * 1e-15, sn);
+    const int zb = 3 + (pb.sgwb_model != 0 ? 1 : 0);   // first correlation spline
+    double D[3], H[3] = {0.0, 0.0, 0.0};
+    for (int c = 0; c < 3; ++c) D[c] = sn[c] * std::pow(10.0, eval_spline(sps[c], x));
+    if (pb.sgwb_model) {
+        const double h2 = h2omega(pb.sgwb_model, f, th[2], th[3], th[4], pb.f_ref);
+        const double eh = std::pow(10.0, eval_spline(sps[3], x));
+        for (int c = 0; c < 3; ++c) H[c] = sgwb_psd(pb.R[(size_t)c * pb.N + i], h2, f) * eh;
+    }
+    double r[3], sq[3];   // AE, AT, ET
+    for (int k = 0; k < 3; ++k) {
+        const double z = eval_spline(sps[zb + k], x);
+        sq[k] = 1.0 / std::sqrt(1.0 + z * z);
+        r[k] = z * sq[k];
+    }
+    // L rows (unit norm): R = L L^T
+    const double L[3][3] = {{1.0, 0.0, 0.0},
+                            {r[0], sq[0], 0.0},
+                            {r[1], r[2] * sq[1], sq[1] * sq[2]}};
+    double R[3][3];
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) {
+            double acc = 0.0;
+            for (int k = 0; k < 3; ++k) acc += L[a][k] * L[b][k];
+            R[a][b] = acc;
+        }
+    double C[3][3];
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) C[a][b] = std::sqrt(D[a]) * R[a][b] * std::sqrt(D[b]) + (a == b ? H[a] : 0.0);
+    cov[0] = C[0][0];
+    cov[1] = C[1][1];
+    cov[2] = C[2][2];
+    cov[3] = C[0][1];
+    cov[4] = C[0][2];
+    cov[5] = C[1][2];
+}
+
+}  // namespace
+
+extern "C" {
+
+// Full-covariance model for every state: out [S][6][N] (C00, C11, C22, C01, C02, C12).
+void lo_model_cov_full(int sgwb_model, int tdi_form, int64_t N, const double* f, const double* R,
+                       double x_lo, double x_hi, double f_ref, int kind, int kmax, int S,
+                       const double* theta, const int* count, const double* kx, const double* kw,
+                       double* out, int* status) {
+    Problem pb{3, sgwb_model, tdi_form, N, f, nullptr, nullptr, R, x_lo, x_hi, f_ref, kind, kmax};
+    const int nsp = n_splines_full(pb);
+    for (int s = 0; s < S; ++s) {
+        const double* th = theta + 5 * (size_t)s;
+        int st = 0;
+        for (int q = 0; q < 5; ++q)
+            if (!std::isfinite(th[q])) st |= 16;
+        std::vector<Spline<double>> sps(nsp);
+        for (int a = 0; a < nsp; ++a)
+            st |= build_spline<double>(kind, count[(size_t)s * nsp + a], kmax, kx + ((size_t)s * nsp + a) * kmax,
+                                       kw + ((size_t)s * nsp + a) * (kmax + 2), x_lo, x_hi, sps[a]);
+        status[s] = st;
+        for (int64_t i = 0; i < N; ++i) {
+            double cov[6];
+            if (!st) full_cov(pb, th, sps, i, cov);
+            for (int e = 0; e < 6; ++e)
+                out[((size_t)s * 6 + e) * N + i] = st ? std::numeric_limits<double>::quiet_NaN() : cov[e];
+        }
+    }
+}
+
+// Sec. III.C with the dense covariance: log L = sum_i [ -tr(C^-1 Y) - nu log|C| ], Y = nu P, with
+// P the averaged Hermitian periodogram, given as P9 [9][N] = P_AA, P_EE, P_TT, then real and
+// imaginary parts of P_AE, P_AT, P_ET (P_EA = conj(P_AE) and so on).  C^-1 = adj(C) / det(C).
+void lo_loglike_full(int sgwb_model, int tdi_form, int64_t N, const double* f, const double* nu,
+                     const double* P9, const double* R, double x_lo, double x_hi, double f_ref,
+                     int kind, int kmax, int S, const double* theta, const int* count,
+                     const double* kx, const double* kw, double* logL, double* im_trace_max,
+                     int* status) {
+    Problem pb{3, sgwb_model, tdi_form, N, f, nu, nullptr, R, x_lo, x_hi, f_ref, kind, kmax};
+    const int nsp = n_splines_full(pb);
+    for (int s = 0; s < S; ++s) {
+        const double* th = theta + 5 * (size_t)s;
+        int st = 0;
+        for (int q = 0; q < 5; ++q)
+            if (!std::isfinite(th[q])) st |= 16;
+        std::vector<Spline<double>> sps(nsp);
+        for (int a = 0; a < nsp; ++a)
+            st |= build_spline<double>(kind, count[(size_t)s * nsp + a], kmax, kx + ((size_t)s * nsp + a) * kmax,
+                                       kw + ((size_t)s * nsp + a) * (kmax + 2), x_lo, x_hi, sps[a]);
+        double sum = 0.0, imax = 0.0;
+        if (!st) {
+            for (int64_t i = 0; i < N; ++i) {
+                double cv[6];
+                full_cov(pb, th, sps, i, cv);
+                const double C[3][3] = {{cv[0], cv[3], cv[4]}, {cv[3], cv[1], cv[5]}, {cv[4], cv[5], cv[2]}};
+                // adjugate (cofactor transpose) and determinant of the symmetric C
+                double A[3][3];
+                for (int a = 0; a < 3; ++a)
+                    for (int b = 0; b < 3; ++b) {
+                        const int a1 = (b + 1) % 3, a2 = (b + 2) % 3, b1 = (a + 1) % 3, b2 = (a + 2) % 3;
+                        A[a][b] = C[a1][b1] * C[a2][b2] - C[a1][b2] * C[a2][b1];
+                    }
+                const double det = C[0][0] * A[0][0] + C[0][1] * A[1][0] + C[0][2] * A[2][0];
+                if (!(det > 0.0) || !std::isfinite(det)) {
+                    st |= 32;
+                    break;
+                }
+                std::complex<double> Pm[3][3];
+                for (int c = 0; c < 3; ++c) Pm[c][c] = std::complex<double>(P9[(size_t)c * N + i], 0.0);
+                const int pr[3][2] = {{0, 1}, {0, 2}, {1, 2}};
+                for (int k = 0; k < 3; ++k) {
+                    const std::complex<double> v(P9[(size_t)(3 + 2 * k) * N + i], P9[(size_t)(4 + 2 * k) * N + i]);
+                    Pm[pr[k][0]][pr[k][1]] = v;
+                    Pm[pr[k][1]][pr[k][0]] = std::conj(v);
+                }
+                // tr(C^-1 P) = sum_ab (C^-1)_ab P_ba
+                std::complex<double> tr(0.0, 0.0);
+                for (int a = 0; a < 3; ++a)
+                    for (int b = 0; b < 3; ++b) tr += (A[a][b] / det) * Pm[b][a];
+                imax = std::max(imax, std::fabs(tr.imag()) / std::max(std::fabs(tr.real()), 1e-300));
+                sum -= nu[i] * (tr.real() + std::log(det));
+            }
+            if (!std::isfinite(sum)) st |= 32;
+        }
+        status[s] = st;
+        logL[s] = st ? -std::numeric_limits<double>::infinity() : sum;
+        if (im_trace_max) im_trace_max[s] = imax;
     }
 }
 

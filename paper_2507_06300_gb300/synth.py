@@ -59,6 +59,28 @@ def gamma_multipliers(rng: np.random.Generator, n_channels: int, nu: np.ndarray)
     return rng.gamma(shape=np.broadcast_to(nu, (n_channels, nu.size)), scale=1.0) / nu
 
 
+def complex_wishart_unit(rng: np.random.Generator, nu: np.ndarray) -> np.ndarray:
+    """Per bin, W = A A^dagger / nu with A lower triangular (Bartlett decomposition of a 3x3
+    complex Wishart matrix with nu degrees of freedom and unit covariance): |A_kk|^2 ~
+    Gamma(nu - k, 1), A_jk (j > k) complex normal with unit variance.  E[W] = I, and for a
+    covariance C = L L^T the averaged periodogram of nu Gaussian samples is distributed as
+    L W L^T.  Returns [9, N]: W_AA, W_EE, W_TT, then real and imaginary parts of W_AE, W_AT, W_ET."""
+    nu = np.asarray(nu, dtype=np.float64)
+    n = nu.size
+    diag = np.sqrt(np.stack([rng.gamma(np.maximum(nu - k, 1e-9), 1.0) for k in range(3)]))
+    off = (rng.standard_normal((3, n)) + 1j * rng.standard_normal((3, n))) / np.sqrt(2.0)   # A10, A20, A21
+    A = np.zeros((n, 3, 3), dtype=np.complex128)
+    A[:, 0, 0], A[:, 1, 1], A[:, 2, 2] = diag
+    A[:, 1, 0], A[:, 2, 0], A[:, 2, 1] = off
+    W = A @ np.conj(np.transpose(A, (0, 2, 1))) / nu[:, None, None]
+    out = np.empty((9, n))
+    out[0], out[1], out[2] = W[:, 0, 0].real, W[:, 1, 1].real, W[:, 2, 2].real
+    for k, (a, b) in enumerate(((0, 1), (0, 2), (1, 2))):
+        out[3 + 2 * k] = W[:, a, b].real
+        out[4 + 2 * k] = W[:, a, b].imag
+    return out
+
+
 @dataclasses.dataclass
 class Knots:
     """Variable-knot perturbation splines for S states (plain arrays, caller layout).

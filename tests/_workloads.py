@@ -76,3 +76,39 @@ def fp32_tolerance(L_ref, wl, P):
         scale = wl.n_channels * wl.nu[b0:b1].sum()
         tol[s0:s1] = 1e-6 * np.maximum(np.abs(L_ref[s0:s1] - K), scale)
     return tol
+
+
+def colour_wishart(cov6, W9):
+    """P = L W L^T per bin, with L the Cholesky factor of the model covariance (cov6 [6, N]:
+    C00, C11, C22, C01, C02, C12) and W the unit complex Wishart draws (W9 [9, N]): the averaged
+    periodogram of data with covariance C.  Returns P9 [9, N] in the oracle's layout."""
+    N = cov6.shape[1]
+    C = np.empty((N, 3, 3))
+    C[:, 0, 0], C[:, 1, 1], C[:, 2, 2] = cov6[0], cov6[1], cov6[2]
+    C[:, 0, 1] = C[:, 1, 0] = cov6[3]
+    C[:, 0, 2] = C[:, 2, 0] = cov6[4]
+    C[:, 1, 2] = C[:, 2, 1] = cov6[5]
+    L = np.linalg.cholesky(C)
+    W = np.zeros((N, 3, 3), dtype=np.complex128)
+    W[:, 0, 0], W[:, 1, 1], W[:, 2, 2] = W9[0], W9[1], W9[2]
+    for k, (a, b) in enumerate(((0, 1), (0, 2), (1, 2))):
+        W[:, a, b] = W9[3 + 2 * k] + 1j * W9[4 + 2 * k]
+        W[:, b, a] = np.conj(W[:, a, b])
+    P = L @ W @ np.transpose(L, (0, 2, 1))
+    out = np.empty((9, N))
+    out[0], out[1], out[2] = P[:, 0, 0].real, P[:, 1, 1].real, P[:, 2, 2].real
+    for k, (a, b) in enumerate(((0, 1), (0, 2), (1, 2))):
+        out[3 + 2 * k] = P[:, a, b].real
+        out[4 + 2 * k] = P[:, a, b].imag
+    return out
+
+
+def hermitian(P9):
+    """[N, 3, 3] complex Hermitian matrices from the oracle's P9 layout."""
+    N = P9.shape[1]
+    P = np.zeros((N, 3, 3), dtype=np.complex128)
+    P[:, 0, 0], P[:, 1, 1], P[:, 2, 2] = P9[0], P9[1], P9[2]
+    for k, (a, b) in enumerate(((0, 1), (0, 2), (1, 2))):
+        P[:, a, b] = P9[3 + 2 * k] + 1j * P9[4 + 2 * k]
+        P[:, b, a] = np.conj(P[:, a, b])
+    return P
