@@ -698,7 +698,12 @@ void lo_model_cov_full(int sgwb_model, int tdi_form, int64_t N, const double* f,
 
 // Sec. III.C with the dense covariance: log L = sum_i [ -tr(C^-1 Y) - nu log|C| ], Y = nu P, with
 // P the averaged Hermitian periodogram, given as P9 [9][N] = P_AA, P_EE, P_TT, then real and
-// imaginary parts of P_AE, P_AT, P_ET (P_EA = conj(P_AE) and so on).  C^-1 = adj(C) / det(C).
+// imaginary parts of P_AE, P_AT, P_ET (P_EA = conj(P_AE) and so on).  Evaluated through the
+// diagonal scaling sigma_c = sqrt(C_cc), which changes nothing in exact arithmetic and keeps
+// every intermediate of order one over the whole range of the perturbations:
+//   K = C / (sigma sigma^T) (unit diagonal),  P' = P / (sigma sigma^T),
+//   tr(C^-1 P) = tr(K^-1 P'),  log|C| = sum_c log C_cc + log|K|,  K^-1 = adj(K) / det(K).
+// A state with a C_cc that is not finite and positive, or det(K) <= 0, is invalid (bit 32).
 void lo_loglike_full(int sgwb_model, int tdi_form, int64_t N, const double* f, const double* nu,
                      const double* P9, const double* R, double x_lo, double x_hi, double f_ref,
                      int kind, int kmax, int S, const double* theta, const int* count,
@@ -721,14 +726,27 @@ void lo_loglike_full(int sgwb_model, int tdi_form, int64_t N, const double* f, c
                 double cv[6];
                 full_cov(pb, th, sps, i, cv);
                 const double C[3][3] = {{cv[0], cv[3], cv[4]}, {cv[3], cv[1], cv[5]}, {cv[4], cv[5], cv[2]}};
-                // adjugate (cofactor transpose) and determinant of the symmetric C
+                double sg[3];
+                bool good = true;
+                for (int c = 0; c < 3; ++c) {
+                    good = good && C[c][c] > 0.0 && std::isfinite(C[c][c]);
+                    sg[c] = std::sqrt(C[c][c]);
+                }
+                if (!good) {
+                    st |= 32;
+                    break;
+                }
+                double K[3][3];
+                for (int a = 0; a < 3; ++a)
+                    for (int b = 0; b < 3; ++b) K[a][b] = C[a][b] / (sg[a] * sg[b]);
+                // adjugate (cofactor transpose) and determinant of K
                 double A[3][3];
                 for (int a = 0; a < 3; ++a)
                     for (int b = 0; b < 3; ++b) {
                         const int a1 = (b + 1) % 3, a2 = (b + 2) % 3, b1 = (a + 1) % 3, b2 = (a + 2) % 3;
-                        A[a][b] = C[a1][b1] * C[a2][b2] - C[a1][b2] * C[a2][b1];
+                        A[a][b] = K[a1][b1] * K[a2][b2] - K[a1][b2] * K[a2][b1];
                     }
-                const double det = C[0][0] * A[0][0] + C[0][1] * A[1][0] + C[0][2] * A[2][0];
+                const double det = K[0][0] * A[0][0] + K[0][1] * A[1][0] + K[0][2] * A[2][0];
                 if (!(det > 0.0) || !std::isfinite(det)) {
                     st |= 32;
                     break;
@@ -741,12 +759,13 @@ void lo_loglike_full(int sgwb_model, int tdi_form, int64_t N, const double* f, c
                     Pm[pr[k][0]][pr[k][1]] = v;
                     Pm[pr[k][1]][pr[k][0]] = std::conj(v);
                 }
-                // tr(C^-1 P) = sum_ab (C^-1)_ab P_ba
+                // tr(K^-1 P') = sum_ab (K^-1)_ab P'_ba
                 std::complex<double> tr(0.0, 0.0);
                 for (int a = 0; a < 3; ++a)
-                    for (int b = 0; b < 3; ++b) tr += (A[a][b] / det) * Pm[b][a];
+                    for (int b = 0; b < 3; ++b) tr += (A[a][b] / det) * (Pm[b][a] / (sg[b] * sg[a]));
                 imax = std::max(imax, std::fabs(tr.imag()) / std::max(std::fabs(tr.real()), 1e-300));
-                sum -= nu[i] * (tr.real() + std::log(det));
+                const double logdet = std::log(C[0][0]) + std::log(C[1][1]) + std::log(C[2][2]) + std::log(det);
+                sum -= nu[i] * (tr.real() + logdet);
             }
             if (!std::isfinite(sum)) st |= 32;
         }
