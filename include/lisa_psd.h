@@ -79,6 +79,24 @@ typedef enum lisa_tdi_form {
     LISA_TDI_SIN2_2U = 1   /* prefactor sin^2(u) sin^2(2u) */
 } lisa_tdi_form;
 
+/* Covariance of the A, E, T data per bin.
+ *  LISA_COV_DIAGONAL: C = diag(S_AA, S_EE, S_TT) (Sec. III.A, the paper's analysis).
+ *  LISA_COV_FULL: the dense covariance Sec. III.A names as the complete analysis, with six
+ *    flexible noise terms (the paper leaves its positive-definite construction to another
+ *    reference; this library's reading):
+ *      C = D^1/2 R D^1/2 + H,  D = diag(S_n,cc 10^{P_n,c}),  H = diag(S_h,cc 10^{P_h}),
+ *      R = L L^T,  L = [[1, 0, 0], [r_AE, s_AE, 0], [r_AT, r_ET s_AT, s_AT s_ET]],
+ *      r = z / sqrt(1 + z^2),  s = 1 / sqrt(1 + z^2),
+ *    where z_AE, z_AT, z_ET are three more variable-knot splines whose values (not exponents) set
+ *    the correlations: positive definite for any spline values, the diagonal model at z = 0.
+ *    Requires n_channels = 3; the per-bin term is -nu [tr(C^-1 P) + ln det C] with the Hermitian
+ *    averaged periodogram P, of which only the real parts of the off-diagonal entries enter (C is
+ *    real). */
+typedef enum lisa_cov_model {
+    LISA_COV_DIAGONAL = 0,
+    LISA_COV_FULL = 1
+} lisa_cov_model;
+
 /* Per-state status bits (0 = valid). */
 #define LISA_STATE_BAD_COUNT 1     /* in-between knot count outside [0, kmax] */
 #define LISA_STATE_BAD_POSITION 2  /* position non-finite or not strictly inside (x_lo, x_hi) */
@@ -110,6 +128,9 @@ typedef struct lisa_data_desc {
     const double* x_lo;        /* [n_datasets] left edge knot position (log10 Hz) */
     const double* x_hi;        /* [n_datasets] right edge knot position, > x_lo */
     const double* f_ref;       /* [n_datasets] power-law reference / break frequency (Hz) > 0 */
+    int32_t cov_model;         /* lisa_cov_model */
+    const double* periodogram_cross; /* LISA_COV_FULL: [3][n_bins] real parts of the averaged
+                                        periodogram's P_AE, P_AT, P_ET (finite); NULL otherwise */
 } lisa_data_desc;
 
 typedef struct lisa_data lisa_data; /* opaque: device tables + work decomposition */
@@ -123,9 +144,11 @@ typedef struct lisa_params {
     const double* theta_dev;
 } lisa_params;
 
-/* Variable-knot perturbation splines, n_splines = n_channels + (sgwb_model != NONE):
- * spline a = 0..n_channels-1 perturbs the noise of channel A, E (, T); the last one perturbs
- * the SGWB (shared by all channels).  All arrays are DEVICE memory:
+/* Variable-knot perturbation splines, n_splines = n_channels + (sgwb_model != NONE)
+ * + (cov_model == LISA_COV_FULL ? 3 : 0): spline a = 0..n_channels-1 perturbs the noise of
+ * channel A, E (, T); spline n_channels perturbs the SGWB (shared by all channels) when the model
+ * has one; with the full covariance the last three are z_AE, z_AT, z_ET.  All arrays are DEVICE
+ * memory:
  *   count_dev [n_states][n_splines]           in-between knots k (0..kmax)
  *   x_dev     [n_states][n_splines][kmax]     in-between positions log10 f, any order
  *   w_dev     [n_states][n_splines][kmax+2]   slot 0 = w_0 (left edge), 1+j = knot j,
@@ -197,7 +220,9 @@ size_t lisa_workspace_bytes(const lisa_data* data, int32_t kmax, lisa_precision 
                             int32_t with_grad);
 
 /* Eq. (1) for every state: fused spline evaluation, PSD assembly (2), per-bin terms and a
- * deterministic FP64 reduction over bins.  loglike_dev [n_states] (FP64).  spline_buf_dev is
+ * deterministic FP64 reduction over bins (with LISA_COV_FULL, the dense covariance's per-bin term
+ * -nu [tr(C^-1 P) + ln det C], from a per-bin 3x3 solve and log-determinant of C scaled to unit
+ * diagonal).  loglike_dev [n_states] (FP64).  spline_buf_dev is
  * the output of lisa_spline_setup with the same precision and kmax.  workspace_dev: at least
  * lisa_workspace_bytes(..., 0) bytes, 256-byte aligned, contents ignored and overwritten.
  * Calls that share a workspace must not overlap on the GPU.  FP32 mode returns LISA_ERR_SHAPE
@@ -216,7 +241,8 @@ lisa_status lisa_psd_loglike(const lisa_data* data, const lisa_params* params,
  * LISA_ERR_WORKSPACE (misaligned), LISA_ERR_CUDA. */
 lisa_status lisa_workspace_status(const void* workspace_dev, lisa_stream_t stream);
 
-/* log L and its gradient for every state (hand-written adjoint; the spline coefficients are
+/* log L and its gradient for every state (hand-written adjoint; LISA_COV_DIAGONAL data only,
+ * LISA_ERR_VALUE for the full covariance; the spline coefficients are
  * recomputed from the knots, nothing per bin is stored).  grad_dev
  * [n_states][LISA_N_THETA + n_splines*(2*kmax+2)] (FP64): d log L / d theta (a_oms, a_tm,
  * log10 A, n1, n2), then per spline d/d(w slots 0..kmax+1) and d/d(x slots 0..kmax-1);
@@ -227,7 +253,8 @@ lisa_status lisa_psd_loglike_grad(const lisa_data* data, const lisa_params* para
                                   void* workspace_dev, size_t workspace_bytes,
                                   lisa_precision precision, lisa_stream_t stream);
 
-/* Model PSD S_c(f_i) of (2) for every state in physical units (FP64):
+/* Model PSD S_c(f_i) of (2) for every state in physical units (FP64; with the full covariance,
+ * the diagonal C_cc = S_n,cc 10^{P_n,c} + S_h,cc 10^{P_h}):
  * psd_dev [n_states][n_channels][n_bins_of_its_dataset], states concatenated in order
  * (state s of dataset d starts at sum over earlier states of n_channels * their dataset's
  * bins).  Uses the FP64 spline buffer. */

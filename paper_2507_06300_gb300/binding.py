@@ -22,6 +22,7 @@ FP32, FP64 = 0, 1
 AKIMA, NATURAL = 0, 1
 SGWB_NONE, SGWB_POWER_LAW, SGWB_BROKEN = 0, 1, 2
 TDI_PRINTED, TDI_SIN2_2U = 0, 1
+COV_DIAGONAL, COV_FULL = 0, 1
 N_THETA = 5
 MAX_KNOTS = 62
 
@@ -37,7 +38,7 @@ class lisa_data_desc(ctypes.Structure):
     _fields_ = [("n_datasets", _c_i32), ("n_channels", _c_i32), ("sgwb_model", _c_i32), ("tdi_form", _c_i32),
                 ("bin_offset", _P_i64), ("state_offset", _P_i64), ("freq", _P_dbl), ("nu", _P_dbl),
                 ("periodogram", _P_dbl), ("response", _P_dbl), ("x_lo", _P_dbl), ("x_hi", _P_dbl),
-                ("f_ref", _P_dbl)]
+                ("f_ref", _P_dbl), ("cov_model", _c_i32), ("periodogram_cross", _P_dbl)]
 
 
 class lisa_params(ctypes.Structure):
@@ -164,10 +165,12 @@ class Dataset:
     """A ``lisa_data`` object: one or more datasets with their bins and states.
 
     Host arrays (numpy, FP64): freq [N], nu [N], periodogram [C, N], response [C, N] (or None for
-    the noise-only model), bin_offset / state_offset [D+1], x_lo / x_hi / f_ref [D]."""
+    the noise-only model), bin_offset / state_offset [D+1], x_lo / x_hi / f_ref [D]; with
+    cov_model=COV_FULL also periodogram_cross [3, N], the real parts of P_AE, P_AT, P_ET."""
 
     def __init__(self, *, n_channels, freq, nu, periodogram, response=None, bin_offset=None, state_offset=None,
-                 n_states=None, x_lo, x_hi, f_ref, sgwb_model=SGWB_POWER_LAW, tdi_form=TDI_PRINTED, stream=None):
+                 n_states=None, x_lo, x_hi, f_ref, sgwb_model=SGWB_POWER_LAW, tdi_form=TDI_PRINTED,
+                 cov_model=COV_DIAGONAL, periodogram_cross=None, stream=None):
         lib = load()
         torch = _torch()
         self.device = torch.cuda.current_device()
@@ -184,7 +187,8 @@ class Dataset:
             R=None if response is None else np.ascontiguousarray(response, np.float64).reshape(n_channels, N),
             x_lo=np.atleast_1d(np.ascontiguousarray(x_lo, np.float64)),
             x_hi=np.atleast_1d(np.ascontiguousarray(x_hi, np.float64)),
-            f_ref=np.atleast_1d(np.ascontiguousarray(f_ref, np.float64)))
+            f_ref=np.atleast_1d(np.ascontiguousarray(f_ref, np.float64)),
+            X=None if periodogram_cross is None else np.ascontiguousarray(periodogram_cross, np.float64).reshape(3, N))
         k = self._keep
         D = k["bin_offset"].size - 1
         desc = lisa_data_desc(
@@ -192,13 +196,15 @@ class Dataset:
             bin_offset=_np_ptr(k["bin_offset"], _c_i64), state_offset=_np_ptr(k["state_offset"], _c_i64),
             freq=_np_ptr(k["freq"], _c_dbl), nu=_np_ptr(k["nu"], _c_dbl), periodogram=_np_ptr(k["P"], _c_dbl),
             response=None if k["R"] is None else _np_ptr(k["R"], _c_dbl), x_lo=_np_ptr(k["x_lo"], _c_dbl),
-            x_hi=_np_ptr(k["x_hi"], _c_dbl), f_ref=_np_ptr(k["f_ref"], _c_dbl))
+            x_hi=_np_ptr(k["x_hi"], _c_dbl), f_ref=_np_ptr(k["f_ref"], _c_dbl), cov_model=int(cov_model),
+            periodogram_cross=None if k["X"] is None else _np_ptr(k["X"], _c_dbl))
         h = _c_vp()
         _check(lib.lisa_data_create(ctypes.byref(desc), _stream_handle(stream), ctypes.byref(h)), "lisa_data_create")
         self._h = h
         self.n_channels = int(n_channels)
         self.sgwb_model = int(sgwb_model)
-        self.n_splines = self.n_channels + (1 if sgwb_model else 0)
+        self.cov_model = int(cov_model)
+        self.n_splines = self.n_channels + (1 if sgwb_model else 0) + (3 if cov_model == COV_FULL else 0)
         self.n_states = int(k["state_offset"][-1])
         self.n_bins = N
         self.n_datasets = D
@@ -207,8 +213,15 @@ class Dataset:
 
     @classmethod
     def from_workload(cls, wl, periodogram, **kw):
-        """Dataset object for a ``synth.Workload`` with the given periodogram [C, N]."""
-        return cls(n_channels=wl.n_channels, freq=wl.f, nu=wl.nu, periodogram=periodogram,
+        """Dataset object for a ``synth.Workload`` with the given periodogram: [C, N] (diagonal
+        covariance) or, for the full covariance, the nine rows P_AA, P_EE, P_TT, Re / Im of P_AE,
+        P_AT, P_ET (only the real parts are passed on)."""
+        P = np.asarray(periodogram)
+        if P.shape[0] == 9:
+            kw.setdefault("cov_model", COV_FULL)
+            kw.setdefault("periodogram_cross", P[[3, 5, 7]])
+            P = P[:3]
+        return cls(n_channels=wl.n_channels, freq=wl.f, nu=wl.nu, periodogram=P,
                    response=wl.R if wl.sgwb_model else None, bin_offset=wl.bin_offset, state_offset=wl.state_offset,
                    x_lo=wl.x_lo, x_hi=wl.x_hi, f_ref=wl.f_ref, sgwb_model=wl.sgwb_model, tdi_form=wl.tdi_form, **kw)
 

@@ -97,6 +97,29 @@ __global__ void prep_kernel(int64_t n_pad, int C, int tdi_form, int sgwb, const 
     }
 }
 
+// Full covariance: per padded bin the real parts of P_AE, P_AT, P_ET divided by sqrt(P_aa P_bb),
+// the off-diagonal entries of the periodogram scaled like the template tables (P-hat_cc = 1).
+__global__ void cross_prep_kernel(int64_t n_pad, const double* __restrict__ P, const double* __restrict__ X,
+                                  int64_t n_real, const DatasetDev* __restrict__ ds, int n_ds,
+                                  double* __restrict__ cross64, float* __restrict__ cross32) {
+    const int64_t ip = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (ip >= n_pad) return;
+    const int d = dataset_of_bin(ds, n_ds, ip);
+    const DatasetDev& D = ds[d];
+    const int64_t i = ip - D.bin0;
+    const int64_t g = D.rbin0 + (i >= D.nbins ? D.nbins - 1 : i);
+    const int pr[3][2] = {{0, 1}, {0, 2}, {1, 2}};
+    const int64_t pb = ip >> 1, e = ip & 1;
+    for (int k = 0; k < 3; ++k) {
+        const double v = X[(size_t)k * n_real + g] /
+                         sqrt(P[(size_t)pr[k][0] * n_real + g] * P[(size_t)pr[k][1] * n_real + g]);
+        cross64[(size_t)ip * kCross + k] = v;
+        cross32[(size_t)pb * kPairCross + 2 * k + e] = (float)v;
+    }
+    cross64[(size_t)ip * kCross + 3] = 0.0;
+    cross32[(size_t)pb * kPairCross + 6 + e] = 0.f;
+}
+
 // Deterministic per-dataset sums (one block per dataset, fixed-order tree):
 //   K = -sum_i nu_i sum_c ln P_c,i  and  Cnu = C sum_i nu_i.
 __global__ void dataset_sums_kernel(const double* __restrict__ lnP, const double* __restrict__ nu,
@@ -143,6 +166,8 @@ void release(lisa_data* d) {
     cudaFree(d->d_P);
     cudaFree(d->d_xlo32);
     cudaFree(d->d_elllo32);
+    cudaFree(d->d_cross64);
+    cudaFree(d->d_cross32);
     cudaFree(d->d_items);
     cudaFree(d->d_cta_first);
     d->d_cta_first = nullptr;
@@ -157,6 +182,8 @@ void release(lisa_data* d) {
     d->d_P = nullptr;
     d->d_xlo32 = nullptr;
     d->d_elllo32 = nullptr;
+    d->d_cross64 = nullptr;
+    d->d_cross32 = nullptr;
     d->d_items = nullptr;
 }
 
@@ -328,8 +355,10 @@ lisa_status lisa_data_create(const lisa_data_desc* desc, lisa_stream_t stream, l
     *out = nullptr;
     const lisa_data_desc& q = *desc;
     if (q.n_datasets < 1 || (q.n_channels != 2 && q.n_channels != 3) || q.sgwb_model < 0 ||
-        q.sgwb_model > 2 || q.tdi_form < 0 || q.tdi_form > 1)
+        q.sgwb_model > 2 || q.tdi_form < 0 || q.tdi_form > 1 || q.cov_model < 0 || q.cov_model > 1 ||
+        (q.cov_model == LISA_COV_FULL && q.n_channels != 3))
         return LISA_ERR_VALUE;
+    if (q.cov_model == LISA_COV_FULL && !q.periodogram_cross) return LISA_ERR_NULL;
     if (!q.bin_offset || !q.state_offset || !q.freq || !q.nu || !q.periodogram || !q.x_lo ||
         !q.x_hi || !q.f_ref || (q.sgwb_model != 0 && !q.response))
         return LISA_ERR_NULL;
@@ -358,6 +387,9 @@ lisa_status lisa_data_create(const lisa_data_desc* desc, lisa_stream_t stream, l
         if (q.sgwb_model != 0 && (!(q.response[i] >= 0.0) || !std::isfinite(q.response[i])))
             return LISA_ERR_DATA;
     }
+    if (q.cov_model == LISA_COV_FULL)
+        for (int64_t i = 0; i < 3 * N; ++i)
+            if (!std::isfinite(q.periodogram_cross[i])) return LISA_ERR_DATA;
 
     lisa_data* d = new (std::nothrow) lisa_data();
     if (!d) return LISA_ERR_ALLOC;
@@ -367,7 +399,8 @@ lisa_status lisa_data_create(const lisa_data_desc* desc, lisa_stream_t stream, l
     d->C = C;
     d->sgwb_model = q.sgwb_model;
     d->tdi_form = q.tdi_form;
-    d->nsp = C + (q.sgwb_model != 0 ? 1 : 0);
+    d->cov = q.cov_model;
+    d->nsp = C + (q.sgwb_model != 0 ? 1 : 0) + (q.cov_model == LISA_COV_FULL ? 3 : 0);
     d->n_bins = N;
     d->n_states = S;
     d->h_bin_off.assign(q.bin_offset, q.bin_offset + D + 1);
@@ -410,8 +443,9 @@ lisa_status lisa_data_create(const lisa_data_desc* desc, lisa_stream_t stream, l
     const int64_t NP = pad0 > 0 ? pad0 : 1;
 
     lisa_status st = LISA_SUCCESS;
-    double *f = nullptr, *nu = nullptr, *R = nullptr, *lnP = nullptr, *nu_p = nullptr;
+    double *f = nullptr, *nu = nullptr, *R = nullptr, *lnP = nullptr, *nu_p = nullptr, *X = nullptr;
     auto fail = [&](lisa_status e) {
+        cudaFree(X);
         cudaFree(f);
         cudaFree(nu);
         cudaFree(R);
@@ -442,6 +476,15 @@ lisa_status lisa_data_create(const lisa_data_desc* desc, lisa_stream_t stream, l
                                         d->d_rec64, d->d_rec32, d->d_xlo32, d->d_elllo32, lnP, nu_p);
     dataset_sums_kernel<<<D, 256, 0, sm>>>(lnP, nu_p, d->d_ds, C);
     if (cudaGetLastError() != cudaSuccess) return fail(LISA_ERR_CUDA);
+    if (d->cov == LISA_COV_FULL) {
+        if ((st = dev_alloc(&X, (size_t)3 * N)) || (st = dev_alloc(&d->d_cross64, (size_t)NP * kCross)) ||
+            (st = dev_alloc(&d->d_cross32, (size_t)((NP + 1) / 2) * kPairCross)))
+            return fail(st);
+        if (cudaMemcpyAsync(X, q.periodogram_cross, 3 * N * sizeof(double), cudaMemcpyHostToDevice, sm) != cudaSuccess)
+            return fail(LISA_ERR_CUDA);
+        cross_prep_kernel<<<blocks, 256, 0, sm>>>(pad0, d->d_P, X, N, d->d_ds, D, d->d_cross64, d->d_cross32);
+        if (cudaGetLastError() != cudaSuccess) return fail(LISA_ERR_CUDA);
+    }
     if (cudaMemcpyAsync(d->h_ds.data(), d->d_ds, D * sizeof(DatasetDev), cudaMemcpyDeviceToHost, sm) != cudaSuccess ||
         cudaStreamSynchronize(sm) != cudaSuccess)
         return fail(LISA_ERR_CUDA);
@@ -450,7 +493,8 @@ lisa_status lisa_data_create(const lisa_data_desc* desc, lisa_stream_t stream, l
     cudaFree(R);
     cudaFree(lnP);
     cudaFree(nu_p);
-    f = nu = R = lnP = nu_p = nullptr;
+    cudaFree(X);
+    f = nu = R = lnP = nu_p = X = nullptr;
     if ((st = rebuild_work(d))) return fail(st);
     {
         // adjoint decomposition (independent of the tiling): per dataset, ranges x groups of 32

@@ -768,6 +768,7 @@ extern "C" lisa_status lisa_psd_loglike_grad(const lisa_data* d, const lisa_para
                                              void* ws, size_t ws_bytes, lisa_precision prec, lisa_stream_t stream) {
     if (!d || !params || !kn || !buf || !out || !grad || !ws) return LISA_ERR_NULL;
     if (prec != LISA_FP32 && prec != LISA_FP64) return LISA_ERR_VALUE;
+    if (d->cov != LISA_COV_DIAGONAL) return LISA_ERR_VALUE;   // the adjoint covers the diagonal model
     if (kn->kmax < 0 || kn->kmax > LISA_MAX_KNOTS || (kn->kind != LISA_SPLINE_AKIMA && kn->kind != LISA_SPLINE_NATURAL))
         return LISA_ERR_VALUE;
     if (params->n_states != d->n_states || kn->n_states != d->n_states || kn->n_splines != d->nsp)

@@ -25,6 +25,8 @@ constexpr int kRec = 12;         // per-bin fields: x, ell, nu, Goms[3], Gtm[3],
 // Both tables use padded bin indices: every dataset is padded to an even bin count with a
 // dummy bin (copy of its last bin with nu = 0).
 constexpr int kPairRec = 2 * kRec;
+constexpr int kCross = 4;        // FP64 cross-spectral fields per bin (three and a pad)
+constexpr int kPairCross = 8;    // FP32 cross-spectral floats per pair block
 constexpr int kThreads = 256;    // threads of the plain FP64 likelihood kernel
 constexpr int kThreads32 = 128;  // threads of the fused FP32 likelihood kernel
 constexpr int kMaxStatesPerItem = 128;  // state lanes of a work item (<= both thread counts)
@@ -99,6 +101,12 @@ struct lisa_data {
     int device = 0;
     int n_sm = 0;
     int32_t n_datasets = 0, C = 0, nsp = 0, sgwb_model = 0, tdi_form = 0;
+    int32_t cov = 0;                 // lisa_cov_model
+    // LISA_COV_FULL: per bin the real parts of P_AE, P_AT, P_ET over sqrt(P_aa P_bb):
+    // FP64 [n_pad][4] (last entry 0), FP32 in blocks of two bins [n_pad / 2][8]
+    // (field k of bin 2p+e at [p * 8 + 2k + e], entries 6, 7 zero)
+    double* d_cross64 = nullptr;
+    float* d_cross32 = nullptr;
     int64_t n_bins = 0, n_states = 0;
     int64_t n_pad = 0;               // padded bin count of the tables
     std::vector<int64_t> h_bin_off, h_state_off;
@@ -224,6 +232,10 @@ inline size_t ws_fwd_bytes(const lisa_data* d) { return ws_layout(d).bytes; }
 size_t grad_extra_bytes(const lisa_data* d, int kmax);
 
 lisa_status rebuild_work(lisa_data* d);
+// The dense-covariance likelihood kernel (LISA_COV_FULL) for the model of d, FP32 bulk or FP64.
+cudaError_t launch_full_cov(const lisa_data* d, bool fp32, const double* theta, const StateParams* prm,
+                            const int32_t* sstat, const int32_t* nint, const float* kxr, const void* srec, int kmax,
+                            double* partial, int* err, cudaStream_t sm);
 // Resident CTAs per SM of the fused FP32 kernel under tiling t (its registers and shared memory).
 int fused_ctas_per_sm(const lisa_data* d, const lisa_tiling& t);
 // Resident CTAs per SM of the compensated kernel for this data object's model.

@@ -1066,7 +1066,7 @@ __global__ void model_psd_kernel(const int32_t* __restrict__ state_ds, const Dat
     const double x = q[0], ell = q[1];
     const double* th = theta + (size_t)s * LISA_N_THETA;
     double Pv[4];
-    for (int a = 0; a < nsp; ++a) {
+    for (int a = 0; a < C + has_h; ++a) {   // the noise and SGWB splines (not the correlations)
         const int64_t sp = (int64_t)s * nsp + a;
         const double* base = srec + sp * (int64_t)(kmax + 1) * kSplineRec;
         const int j = find_interval<double, kSplineRec, 0>(base, nint[sp], x);
@@ -1309,7 +1309,13 @@ lisa_status lisa_psd_loglike(const lisa_data* d, const lisa_params* params, cons
     const bool prof = prof_active(d, sm);
     prof_mark(d, prof, 0, sm);
     cudaError_t e = cudaSuccess;
-    if (d->n_items > 0)
+    if (d->cov == LISA_COV_FULL) {
+        // one kernel evaluates every bin (ill-conditioned intervals included)
+        if (d->n_items > 0)
+            e = launch_full_cov(d, fp32, params->theta_dev, prm, sstat, nint, kxr, srec, kmax, partial, err, sm);
+        prof_mark(d, prof, 1, sm);
+        prof_mark(d, prof, 2, sm);
+    } else if (d->n_items > 0)
         e = d->C == 3 ? dispatch_model<3>(d, fp32, params->theta_dev, prm, sstat, nint, kxr, rcount, rlist, srec, kmax,
                                           partial, rpart, err, sm, prof)
                       : dispatch_model<2>(d, fp32, params->theta_dev, prm, sstat, nint, kxr, rcount, rlist, srec, kmax,

@@ -16,18 +16,21 @@ namespace {
 //                ones that read them, and are zero elsewhere.
 // The kernel is bound by the FP64 pipe; 7 CTAs per SM (at most 72 registers) keep 1,064 states
 // resident at once.
-template <bool kF32>
-__global__ void __launch_bounds__(128, 7) spline_setup_kernel(
+// kMaxSp: splines per state the launch allows (4 for the diagonal covariance, 8 for the full one,
+// which has seven); do_route = 0 leaves the routing bit unset (the full-covariance FP32 kernel
+// evaluates ill-conditioned intervals itself).
+template <bool kF32, int kMaxSp>
+__global__ void __launch_bounds__(32 * kMaxSp, kMaxSp == 4 ? 7 : 3) spline_setup_kernel(
     const int32_t* __restrict__ count, const double* __restrict__ kx, const double* __restrict__ kw,
     int S, int nsp, int kmax, int kind, const int32_t* __restrict__ state_ds,
     const DatasetDev* __restrict__ ds, int32_t* __restrict__ status_buf, int32_t* __restrict__ nint_buf,
     int32_t* __restrict__ route, void* __restrict__ rec_v, float2* __restrict__ hull,
-    float* __restrict__ kxr, int32_t* __restrict__ status_out) {
+    float* __restrict__ kxr, int32_t* __restrict__ status_out, int do_route) {
     using T = double;
-    __shared__ T sX[4][64];
-    __shared__ T sY[4][64];
-    __shared__ int sSt[4], sRob[4];
-    __shared__ float sHlo[4], sHhi[4];
+    __shared__ T sX[kMaxSp][64];
+    __shared__ T sY[kMaxSp][64];
+    __shared__ int sSt[kMaxSp], sRob[kMaxSp];
+    __shared__ float sHlo[kMaxSp], sHhi[kMaxSp];
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
     const int s = blockIdx.x;
@@ -147,7 +150,7 @@ __global__ void __launch_bounds__(128, 7) spline_setup_kernel(
         }
         if (kF32) hull[s] = make_float2(hlo, hhi);
         int word = st_all;
-        if (kF32 && robust && st_all == 0) {
+        if (kF32 && do_route && robust && st_all == 0) {
             word |= kRouted;
             const int slot = atomicAdd(route, 1);
             route[1 + slot] = s;
@@ -182,17 +185,28 @@ extern "C" lisa_status lisa_spline_setup(const lisa_data* d, const lisa_knots* k
     const unsigned threads = 32u * (unsigned)d->nsp;
     cudaStream_t sm = (cudaStream_t)stream;
     if (cudaMemsetAsync(route, 0, sizeof(int32_t), sm) != cudaSuccess) return LISA_ERR_CUDA;
-    if (prec == LISA_FP64)
-        spline_setup_kernel<false><<<blocks, threads, 0, sm>>>(kn->count_dev, kn->x_dev, kn->w_dev, (int)d->n_states,
-                                                           d->nsp, kn->kmax, kn->kind, d->d_state_ds, d->d_ds,
-                                                           status_buf, nint_buf, route, base + L.off_rec,
-                                                           reinterpret_cast<float2*>(base + L.off_hull),
-                                                           reinterpret_cast<float*>(base + L.off_kxr), status_out);
-    else
-        spline_setup_kernel<true><<<blocks, threads, 0, sm>>>(kn->count_dev, kn->x_dev, kn->w_dev, (int)d->n_states,
-                                                          d->nsp, kn->kmax, kn->kind, d->d_state_ds, d->d_ds,
-                                                          status_buf, nint_buf, route, base + L.off_rec,
-                                                          reinterpret_cast<float2*>(base + L.off_hull),
-                                                          reinterpret_cast<float*>(base + L.off_kxr), status_out);
+    const int do_route = d->cov == LISA_COV_DIAGONAL;
+    float2* hull = reinterpret_cast<float2*>(base + L.off_hull);
+    float* kxr = reinterpret_cast<float*>(base + L.off_kxr);
+    void* rec = base + L.off_rec;
+    if (d->nsp <= 4) {
+        if (prec == LISA_FP64)
+            spline_setup_kernel<false, 4><<<blocks, threads, 0, sm>>>(
+                kn->count_dev, kn->x_dev, kn->w_dev, (int)d->n_states, d->nsp, kn->kmax, kn->kind, d->d_state_ds,
+                d->d_ds, status_buf, nint_buf, route, rec, hull, kxr, status_out, do_route);
+        else
+            spline_setup_kernel<true, 4><<<blocks, threads, 0, sm>>>(
+                kn->count_dev, kn->x_dev, kn->w_dev, (int)d->n_states, d->nsp, kn->kmax, kn->kind, d->d_state_ds,
+                d->d_ds, status_buf, nint_buf, route, rec, hull, kxr, status_out, do_route);
+    } else {
+        if (prec == LISA_FP64)
+            spline_setup_kernel<false, 8><<<blocks, threads, 0, sm>>>(
+                kn->count_dev, kn->x_dev, kn->w_dev, (int)d->n_states, d->nsp, kn->kmax, kn->kind, d->d_state_ds,
+                d->d_ds, status_buf, nint_buf, route, rec, hull, kxr, status_out, do_route);
+        else
+            spline_setup_kernel<true, 8><<<blocks, threads, 0, sm>>>(
+                kn->count_dev, kn->x_dev, kn->w_dev, (int)d->n_states, d->nsp, kn->kmax, kn->kind, d->d_state_ds,
+                d->d_ds, status_buf, nint_buf, route, rec, hull, kxr, status_out, do_route);
+    }
     return check_cuda(cudaGetLastError());
 }

@@ -185,6 +185,8 @@ class Workload:
     theta: np.ndarray           # [S_total, 5]
     knots: Knots
     true_knots: Knots | None = None  # [D] injected perturbations (None = no perturbation)
+    cov_model: int = 0          # 1: dense covariance, knots carry z_AE, z_AT, z_ET after the others
+    wishart: np.ndarray | None = None  # cov_model 1: unit complex Wishart draws [9, N_total]
 
     @property
     def n_datasets(self):
@@ -200,7 +202,7 @@ class Workload:
 
     @property
     def n_splines(self):
-        return self.n_channels + (1 if self.sgwb_model else 0)
+        return self.n_channels + (1 if self.sgwb_model else 0) + (3 if self.cov_model else 0)
 
     def dataset(self, d: int) -> dict:
         """Plain dict view of dataset d (no periodogram: the consumer forms it)."""
@@ -217,8 +219,13 @@ class Workload:
                                        kmax=k.kmax, kind=k.kind)
 
 
+# Correlations injected into the dense-covariance workloads: constant z_AE, z_AT, z_ET (r ~ z,
+# a few per cent, the size the paper quotes for cross-correlations of the noise)
+Z_INJ = (0.05, 0.03, -0.04)
+
+
 def _single(name, rng, n_bins, nu, n_channels, sgwb_model, n_states, kmin, kmax_draw, kmax=None,
-            theta_mode="mixed", tdi_form=0, kind=0, f_min=F_MIN, f_max=F_MAX, theta_true=THETA_INJ):
+            theta_mode="mixed", tdi_form=0, kind=0, f_min=F_MIN, f_max=F_MAX, theta_true=THETA_INJ, cov_model=0):
     f = freq_grid(n_bins, f_min, f_max)
     nu_a = np.full(n_bins, float(nu))
     R = response_standin(f, n_channels) if sgwb_model else np.zeros((n_channels, n_bins))
@@ -233,12 +240,29 @@ def _single(name, rng, n_bins, nu, n_channels, sgwb_model, n_states, kmin, kmax_
                                 draw_theta(rng, n_states - h, "prior", theta_true, sgwb_model)])
     else:
         theta = draw_theta(rng, n_states, theta_mode, theta_true, sgwb_model)
+    if cov_model:
+        if n_channels != 3:
+            raise ValueError("the dense covariance needs the A, E, T channels")
+        nsp += 3
+        if not isinstance(kmin, (int, np.integer)):
+            kmin = list(kmin) + [0, 0, 0]
+        if not isinstance(kmax_draw, (int, np.integer)):
+            kmax_draw = list(kmax_draw) + [max(kmax_draw)] * 3
     knots = draw_knots(rng, n_states, nsp, kmin, kmax_draw, x_lo, x_hi, kmax=kmax, kind=kind)
+    true_knots, wishart = None, None
+    if cov_model:
+        km = knots.kmax
+        true_knots = Knots(count=np.zeros((1, nsp), np.int32), x=np.zeros((1, nsp, km)),
+                           w=np.zeros((1, nsp, km + 2)), kmax=km, kind=kind)
+        for q in range(3):
+            true_knots.w[0, nsp - 3 + q, :] = Z_INJ[q]
+        wishart = complex_wishart_unit(rng, nu_a)
     return Workload(name=name, n_channels=n_channels, sgwb_model=sgwb_model, tdi_form=tdi_form,
                     f=f, nu=nu_a, R=R, gamma=gam, bin_offset=np.array([0, n_bins], np.int64),
                     state_offset=np.array([0, n_states], np.int64), x_lo=np.array([x_lo]),
                     x_hi=np.array([x_hi]), f_ref=np.array([1.0e-3]),
-                    theta_true=np.array([theta_true], dtype=np.float64), theta=theta, knots=knots)
+                    theta_true=np.array([theta_true], dtype=np.float64), theta=theta, knots=knots,
+                    true_knots=true_knots, cov_model=cov_model, wishart=wishart)
 
 
 def workload(name: str, seed: int = SEED, **over) -> Workload:
@@ -253,6 +277,11 @@ def workload(name: str, seed: int = SEED, **over) -> Workload:
     full       A,E,T; 524,288 bins; nu=128; 32x256 = 8,192 states; broken power law
                (knee 3 mHz, slopes 2/3 and -1); 0-40 in-between knots.
     tiny       A,E,T; 300 bins; nu=4; 6 states; 0-6 knots (unit tests).
+
+    cov_model=1 (A,E,T workloads) adds the dense covariance: three more splines per state, the
+    correlations z_AE, z_AT, z_ET (drawn like the others), constant correlations Z_INJ in the
+    injection, and unit complex Wishart draws from which the consumer forms the averaged
+    periodogram matrix around its own model covariance.
     """
     rng = np.random.default_rng(seed)
     if name == "small_ae":

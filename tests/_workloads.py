@@ -112,3 +112,22 @@ def hermitian(P9):
         P[:, a, b] = P9[3 + 2 * k] + 1j * P9[4 + 2 * k]
         P[:, b, a] = np.conj(P[:, a, b])
     return P
+
+
+def oracle_dataset_full(wl):
+    """Dense-covariance dataset of a cov_model=1 workload: the averaged periodogram matrix P9
+    [9, N] = L W L^T around the oracle's model covariance of the injection (constant
+    correlations), W the workload's unit complex Wishart draws."""
+    ds = wl.dataset(0)
+    tk = wl.true_knots
+    C6, st = oracle.model_cov_full(ds, wl.theta_true[:1], tk.as_dict())
+    assert st[0] == 0
+    ds["P9"] = colour_wishart(C6[0], wl.wishart)
+    return ds
+
+
+def fp32_tolerance_full(L_ref, wl, P9):
+    """The FP32-bulk bound for the dense covariance: 1e-6 of max(|log L - K|, 3 sum nu), with
+    K = -sum nu sum_c ln P_cc."""
+    K = -np.sum(wl.nu * np.log(P9[:3]).sum(axis=0))
+    return 1e-6 * np.maximum(np.abs(L_ref - K), 3 * wl.nu.sum())
