@@ -13,6 +13,7 @@ only other place this script executes ``oracle/``), on bounded samples of the sa
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import hashlib
 import json
 import math
@@ -176,6 +177,42 @@ def make_periodogram_gpu(wl, B, torch):
     P *= torch.as_tensor(wl.gamma, device="cuda")
     out = P.cpu().numpy()
     ds0.close()
+    return out
+
+
+# The dense-covariance FP32 kernel per state-bin as implemented (A,E,T, power-law SGWB, fast path),
+# FP32-pipe instructions: seven splines x (shift + 3 Horner FMA) = 28; SGWB exponent and amplitude 3;
+# per channel D 4, H 1, C_cc 1 and the two range checks = 24; 1 / C_cc from one reciprocal 8; g^2, h 6;
+# r, s from z 9; R_ET 3; e, s_AT s_ET, the 2x2 minors and s0 s1 s2 9; adjugate diagonal and det K 21;
+# off-diagonal adjugate brackets 11; sqrt(D_a D_b) and the off-diagonal trace terms 18; diagonal
+# trace terms and numerator 6; cancellation and det checks 8; the log's product, term and nu 6;
+# accumulation 1 -- 161.  MUFU: 4 ex2, 6 rsqrt (z -> r, s and sqrt(D_a D_b)), 2 rcp (the product
+# of the C_cc, det K), 1 lg2.
+FULL_FP32_PER_STATE_BIN = 161
+FULL_MUFU = {"ex2": 4, "rsqrt": 6, "rcp": 2, "lg2": 1}
+
+
+def colour_periodogram(cov6, W9):
+    """The averaged periodogram matrix L W L^T per bin (L the Cholesky factor of the injected
+    covariance, W the workload's unit complex Wishart draws), as [9, N]: P_AA, P_EE, P_TT and the
+    real and imaginary parts of P_AE, P_AT, P_ET."""
+    N = cov6.shape[1]
+    C = np.empty((N, 3, 3))
+    C[:, 0, 0], C[:, 1, 1], C[:, 2, 2] = cov6[0], cov6[1], cov6[2]
+    C[:, 0, 1] = C[:, 1, 0] = cov6[3]
+    C[:, 0, 2] = C[:, 2, 0] = cov6[4]
+    C[:, 1, 2] = C[:, 2, 1] = cov6[5]
+    L = np.linalg.cholesky(C)
+    W = np.zeros((N, 3, 3), dtype=np.complex128)
+    W[:, 0, 0], W[:, 1, 1], W[:, 2, 2] = W9[0], W9[1], W9[2]
+    for k, (a, b) in enumerate(((0, 1), (0, 2), (1, 2))):
+        W[:, a, b] = W9[3 + 2 * k] + 1j * W9[4 + 2 * k]
+        W[:, b, a] = np.conj(W[:, a, b])
+    Pm = L @ W @ np.transpose(L, (0, 2, 1))
+    out = np.empty((9, N))
+    out[0], out[1], out[2] = Pm[:, 0, 0].real, Pm[:, 1, 1].real, Pm[:, 2, 2].real
+    for k, (a, b) in enumerate(((0, 1), (0, 2), (1, 2))):
+        out[3 + 2 * k], out[4 + 2 * k] = Pm[:, a, b].real, Pm[:, a, b].imag
     return out
 
 
@@ -351,8 +388,8 @@ def run_ours(args):
         vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
         gpu_id = vis.split(",")[local] if vis else str(local)
 
-    def prepare(wl, tiling):
-        P = make_periodogram_gpu(wl, B, torch)
+    def prepare(wl, tiling, P=None, groups=autotune.DEFAULT_GROUPS):
+        P = make_periodogram_gpu(wl, B, torch) if P is None else P
         ds = B.Dataset.from_workload(wl, P)
         count, x, w, kmax, kind = B.knots_to_device(wl.knots)
         theta = torch.as_tensor(wl.theta, device="cuda")
@@ -363,12 +400,13 @@ def run_ours(args):
             table = [(best, float("nan"))]
         else:
             # tile shapes picked by the autotuner on these inputs (outside the timed region)
-            best, table = autotune.autotune(ds, theta, count, x, w, kmax, kind, B.FP32)
+            best, table = autotune.autotune(ds, theta, count, x, w, kmax, kind, B.FP32, groups=groups)
             table.sort(key=lambda r: r[1])
         so, bo = wl.state_offset, wl.bin_offset
         nbin_state = np.repeat(np.diff(bo), np.diff(so))           # bins of each state's dataset
         alg_bytes = (TABLE_BYTES_PER_BIN * wl.n_bins + wl.n_states * 8 * B.N_THETA +
                      wl.n_states * wl.n_splines * (kmax + 1) * SPLINE_RECORD_BYTES)
+        P = P[:3] if P.shape[0] == 9 else P      # the diagonal: normalisation and the scale of the bound
         return dict(wl=wl, P=P, ds=ds, count=count, x=x, w=w, kmax=kmax, kind=kind, theta=theta, tiling=best,
                     table=table, sb=int(nbin_state.sum()), nbin_state=nbin_state, alg_bytes=alg_bytes)
 
@@ -736,6 +774,40 @@ def run_ours(args):
 
     # ---- batched datasets and the full-form workload ----------------------------------------------
     line["workloads"] = {}
+    if "full_cov" in args.extras:
+        # the dense 3x3 covariance (six flexible noise terms) on the paper-scale workload
+        wlc = synth.workload("paper", cov_model=1)
+        wdiag = synth.workload("paper")                   # same bins, noise and SGWB injection
+        S_true = make_periodogram_gpu(dataclasses.replace(wdiag, gamma=np.ones_like(wdiag.gamma)), B, torch)
+        z = np.asarray(synth.Z_INJ)
+        rz, sz = z / np.sqrt(1 + z * z), 1 / np.sqrt(1 + z * z)
+        Rm = {(0, 1): rz[0], (0, 2): rz[1], (1, 2): rz[0] * rz[1] + sz[0] * sz[1] * rz[2]}
+        cov6 = np.empty((6, wlc.n_bins))
+        cov6[:3] = S_true
+        for k, (a, b) in enumerate(((0, 1), (0, 2), (1, 2))):
+            cov6[3 + k] = np.sqrt(S_true[a] * S_true[b]) * Rm[(a, b)]
+        P9 = colour_periodogram(cov6, wlc.wishart)
+        Ic = prepare(wlc, "", P=P9, groups=(4,))
+        rc, _, _ = forward(Ic, max(5, min(args.steps // 2, 200)), args.warmup, 1)
+        rate = rc["state_bins_per_step"] / (rc["kernel_ms"]["fused_fp32"] / 1e3)
+        fp32_rate = max(rates["ffma"], rates["ffma2"])
+        t_lg2 = max(2.0 / rates["lg2_ex2"] - 1.0 / rates["ex2"], 1.0 / rates["ex2"])
+        t_mufu = (FULL_MUFU["ex2"] / rates["ex2"] + (FULL_MUFU["rsqrt"] + FULL_MUFU["rcp"]) / rates["rcp"] +
+                  FULL_MUFU["lg2"] * t_lg2)
+        c32, cmu = fp32_rate / FULL_FP32_PER_STATE_BIN, 1.0 / t_mufu
+        rc["roofline"] = {
+            "bound": "alu", "pipe": "FP32 (FMA pipe)" if c32 <= cmu else "MUFU (XU pipe)",
+            "kernel": "full_fp32_kernel (dense covariance)",
+            "achieved": FULL_FP32_PER_STATE_BIN * rate / 1e9 if c32 <= cmu else sum(FULL_MUFU.values()) * rate / 1e9,
+            "peak": fp32_rate / 1e9 if c32 <= cmu else sum(FULL_MUFU.values()) * cmu / 1e9, "unit": "Gop/s",
+            "frac": rate / min(c32, cmu), "ops_per_state_bin": FULL_FP32_PER_STATE_BIN,
+            "ceilings_state_bins_per_s": {"fp32": c32, "mufu": cmu},
+            "mufu_ops_per_state_bin": FULL_MUFU, "note": "rsqrt taken at the measured rcp rate"}
+        rc["workload"] = ("A,E,T; 131,072 bins; Nseg=64; 1,024 states; dense 3x3 covariance per bin: three "
+                          "noise, one SGWB and three correlation splines per state (0-20 knots); data: complex "
+                          "Wishart draws around the model PSD with constant correlations")
+        line["workloads"]["full_cov"] = rc
+        release(Ic)
     for name, desc in (("batched", "1,024 A,E,T datasets of 8k-262k bins, 4 x 4 states each, 0-30 knots; "
                                     "one persistent launch per kernel, CUDA graphs"),
                        ("full", "A,E,T; 524,288 bins; Nseg=128; 32 temps x 256 walkers = 8,192 states; "
@@ -802,15 +874,15 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-states", type=int, default=4, help="states per reference step")
     ap.add_argument("--tiling", default="", help="tile_bins,states_per_cta,group (skips the autotuner)")
-    ap.add_argument("--extras", default="adjoint,prep,rjpt,batched,full",
-                    help="comma-separated extra workloads to measure: adjoint, prep, rjpt, batched, full")
+    ap.add_argument("--extras", default="adjoint,prep,rjpt,batched,full,full_cov",
+                    help="comma-separated extra workloads to measure: adjoint, prep, rjpt, batched, full, full_cov")
     ap.add_argument("--no-extras", action="store_true", help="measure the headline workload only")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     args.extras = set() if args.no_extras else {e.strip() for e in args.extras.split(",") if e.strip()}
-    if not args.extras <= {"adjoint", "prep", "rjpt", "batched", "full"}:
-        ap.error("--extras takes adjoint, prep, rjpt, batched, full")
+    if not args.extras <= {"adjoint", "prep", "rjpt", "batched", "full", "full_cov"}:
+        ap.error("--extras takes adjoint, prep, rjpt, batched, full, full_cov")
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

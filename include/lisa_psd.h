@@ -165,7 +165,8 @@ typedef struct lisa_knots {
 
 /* Tiling of the fused likelihood kernels (chosen by the autotuner; defaults are sane). */
 typedef struct lisa_tiling {
-    int32_t tile_bins;      /* bins staged per work item: multiple of 32, 64..2048 */
+    int32_t tile_bins;      /* bins staged per work item: multiple of 32, 64..2048 (..1024 for
+                               the dense covariance) */
     int32_t states_per_cta; /* states per work item: power of two, 16..128 */
     int32_t group;          /* bins processed between interval checks: 2, 4 or 8 */
     int32_t ctas_per_sm;    /* persistent grid = SMs x this (0 = occupancy limit) */

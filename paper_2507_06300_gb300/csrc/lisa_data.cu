@@ -570,7 +570,7 @@ lisa_status lisa_data_set_tiling(lisa_data* d, const lisa_tiling* t) {
     bool pow2 = sc > 0 && (sc & (sc - 1)) == 0;
     if (t->tile_bins < 64 || t->tile_bins > kMaxTileBins || (t->tile_bins % 32) != 0 || !pow2 || sc < 16 ||
         sc > kMaxStatesPerItem || !(t->group == 2 || t->group == 4 || t->group == 8) ||
-        t->ctas_per_sm < 0 || t->ctas_per_sm > 32)
+        t->ctas_per_sm < 0 || t->ctas_per_sm > 32 || (d->cov == LISA_COV_FULL && t->tile_bins > kMaxTileBinsFull))
         return LISA_ERR_VALUE;
     lisa_tiling old = d->tiling;
     d->tiling = *t;

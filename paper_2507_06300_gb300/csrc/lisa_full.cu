@@ -179,14 +179,74 @@ __device__ __forceinline__ void stage_item(float* dst, const float* rec32, const
         : "memory");
 }
 
-constexpr float kFullSafe = 120.0f;   // FP32 path: exponents (log2) and PSD scale within 2^+-120
+constexpr float kFullLo = 9.094947e-13f;   // 2^-40: FP32 path, D_c above and C_cc below 2^+-40
+constexpr float kFullHi = 1.0995116e12f;   // 2^40
+constexpr float kFullMinDet = 0.0625f;     // FP32 path: det K at least 1/16
+
+constexpr int kFullChunk = 16;   // bins per thread between two passes over the careful queue
+
+// The FP64 term of one careful bin (queued by the bin loop): the state's intervals at the bin are
+// found again in the right-end table, the spline values formed in float-float from the records'
+// hi + lo parts, and the term evaluated by full_term64, the same code as the plain path.
+template <bool HAS_H, bool BROKEN>
+__device__ __noinline__ double full_careful_term(int s, int bin, const float* tb, const float* tx, int i,
+                                                 const float* __restrict__ xlo32, const float* __restrict__ elllo32,
+                                                 const double* __restrict__ theta, const float* __restrict__ kxr,
+                                                 const float* __restrict__ srec, int kmax, int nsp) {
+    constexpr int NSP = 3 + (HAS_H ? 1 : 0) + 3;
+    constexpr int ZB = 3 + (HAS_H ? 1 : 0);
+    const float x = fld(tb, i, 0);
+    const int kxs = kxr_stride(kmax);
+    double pd[NSP];
+#pragma unroll 1
+    for (int a = 0; a < NSP; ++a) {
+        const int64_t sp = (int64_t)s * nsp + a;
+        const float4* kq = reinterpret_cast<const float4*>(kxr + sp * kxs);
+        int j = 0;
+        for (int q = 0; q < kxs / 4; ++q) {
+            const float4 v = __ldg(kq + q);
+            j += (v.x <= x) + (v.y <= x) + (v.z <= x) + (v.w <= x);
+        }
+        const float4* rr = reinterpret_cast<const float4*>(srec + (sp * (int64_t)(kmax + 1) + min(j, kmax)) *
+                                                                      kSplineRec32);
+        const float4 A = __ldg(rr), B = __ldg(rr + 1), Cq = __ldg(rr + 2), Dq = __ldg(rr + 3);
+        const ff t = ff_add(ff{x, __ldg(xlo32 + bin)}, ff{-A.y, -Cq.x});
+        ff v = {B.y, Dq.x};
+        v = ff_add(ff_mul(v, t), ff{B.x, Cq.w});
+        v = ff_add(ff_mul(v, t), ff{A.w, Cq.z});
+        v = ff_add(ff_mul(v, t), ff{A.z, Cq.y});
+        pd[a] = ((double)v.hi + (double)v.lo) * (1.0 / kLog2_10);   // log10 units
+    }
+    double qd[kRec];
+    qd[1] = (double)fld(tb, i, 1) + (double)__ldg(elllo32 + bin);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        qd[3 + c] = fld(tb, i, 3 + c);
+        qd[6 + c] = fld(tb, i, 6 + c);
+        qd[9 + c] = fld(tb, i, 9 + c);
+    }
+    const int pb = (i >> 1) * kPairCross + (i & 1);
+    const double xcd[3] = {tx[pb], tx[pb + 2], tx[pb + 4]};
+    const double* th = theta + (size_t)s * LISA_N_THETA;
+    const double sl = BROKEN ? (qd[1] < 0.0 ? th[3] : th[4]) : th[3];
+    const double pn[3] = {pd[0], pd[1], pd[2]};
+    const double zv[3] = {pd[ZB], pd[ZB + 1], pd[ZB + 2]};
+    return full_term64<HAS_H>(pn, HAS_H ? pd[3] : 0.0, zv, qd, xcd, th[0] * th[0], th[1] * th[1], th[2], sl);
+}
 
 // One thread per state and contiguous bins of the item, one bin at a time.  The current interval of
 // each spline (cubic about its midpoint, log2 units, as the setup writes FP32 records) is kept in
-// registers, its right end and index in shared memory.  A bin is evaluated in FP32 when every
-// interval it uses is well conditioned and every exponent and diagonal entry stays within 2^+-120;
-// otherwise ("careful" bins, rare) the spline values are formed in float-float from the records'
-// low parts and the term in FP64 by full_term64, the same code as the plain path.
+// registers, its right end and index in shared memory.  On an ill-conditioned interval (prior
+// draws with close knots) the spline value is formed in float-float from the record's low parts
+// and 2^P as ex2(hi) (1 + lo ln2); the rest of the bin stays in FP32.  The 3x3 algebra is written
+// in the factored parameters (g_c^2 = D_c / C_cc, h_c = H_c / C_cc and the correlations' r, s), so
+// that det K and the adjugate's diagonal are sums of non-negative products, accurate to a few
+// rounding errors whatever the conditioning.  A bin whose diagonal entries leave 2^+-40, whose
+// det K is below 1/16 or whose trace cancels by more than a factor 8 ("careful" bins: extreme
+// states, rare) is queued in shared memory instead; after every chunk of kFullChunk bins the whole
+// CTA evaluates the queued bins in FP64, one bin per thread, so that they cost full warps rather
+// than a divergent branch in the bin loop.  The queue holds a chunk's worth of bins of every
+// thread and cannot overflow.
 template <bool HAS_H, bool BROKEN>
 __global__ void __launch_bounds__(kFullThreads, 4)
     full_fp32_kernel(const WorkItem* __restrict__ items, int n_items, const float* __restrict__ rec32,
@@ -204,12 +264,16 @@ __global__ void __launch_bounds__(kFullThreads, 4)
     __shared__ float s_xr[NSP][kFullThreads];
     __shared__ int s_jj[NSP][kFullThreads];
     __shared__ double red[kFullThreads];
+    __shared__ double s_far[kFullThreads];                 // FP64 sums of the queued bins, per thread
+    __shared__ uint32_t s_q[kFullThreads * kFullChunk];   // careful queue: thread << 16 | bin
+    __shared__ int s_nq[2];
     __shared__ int s_fail;   // a bounded wait ran out: stage nothing more (a late copy may still land)
     const int tid = threadIdx.x;
     const size_t stage_floats = (size_t)tile_bins * kRec + (size_t)(tile_bins >> 1) * kPairCross;
     float* sb[2] = {reinterpret_cast<float*>(smem), reinterpret_cast<float*>(smem) + stage_floats};
     if (tid == 0) {
         s_fail = 0;
+        s_nq[0] = s_nq[1] = 0;
         bar_init(&bars[0]);
         bar_init(&bars[1]);
         if ((int)blockIdx.x < n_items) stage_item(sb[0], rec32, cross32, items[blockIdx.x], tile_bins, &bars[0]);
@@ -219,6 +283,7 @@ __global__ void __launch_bounds__(kFullThreads, 4)
     float cxo[NSP], c0[NSP], c1[NSP], c2[NSP], c3[NSP];
     unsigned hm = 0;
     int k = 0;
+    unsigned gch = 0;   // chunks run so far (uniform over the CTA): picks the queue counter
     for (int it = blockIdx.x; it < n_items; it += gridDim.x, ++k) {
         const int b = k & 1;
         const int nxt = it + gridDim.x;
@@ -238,51 +303,54 @@ __global__ void __launch_bounds__(kFullThreads, 4)
         const int r = tid / sc;
         const int s = w.s0 + ls;
         const bool active = ok && ls < w.ns && (sstat[s] & kUserBits) == 0;
+        const int lo = (r * w.nb) / R, hi = ((r + 1) * w.nb) / R;
+        const bool run_bins = active && lo < hi;
+        const int nch = ((w.nb + R - 1) / R + kFullChunk - 1) / kFullChunk;   // uniform over the CTA
+        s_far[tid] = 0.0;
         ff accf = {0.f, 0.f};
-        double far = 0.0;
-        if (active) {
-            const int lo = (r * w.nb) / R, hi = ((r + 1) * w.nb) / R;
-            if (lo < hi) {
-                const StateParams p = prm[s];
-                const float ao2 = p.ao2, at2 = p.at2, Af = HAS_H ? p.Af : 0.f;
-                const double* th = theta + (size_t)s * LISA_N_THETA;
-                auto rec = [&](int a, int j) {
-                    return srec + (((int64_t)s * nsp + a) * (int64_t)(kmax + 1) + j) * kSplineRec32;
-                };
-                auto install = [&](int a, int j) {
-                    const float4 A = __ldg(reinterpret_cast<const float4*>(rec(a, j)));
-                    const float4 B = __ldg(reinterpret_cast<const float4*>(rec(a, j)) + 1);
-                    s_xr[a][tid] = A.x;
-                    s_jj[a][tid] = j;
-                    cxo[a] = A.y;
-                    c0[a] = A.z;
-                    c1[a] = A.w;
-                    c2[a] = B.x;
-                    c3[a] = B.y;
-                    hm = B.w <= (float)kRobustT ? (hm & ~(1u << a)) : (hm | (1u << a));
-                };
-                // intervals at the first bin: the count of right ends <= x in the right-end table
-                {
-                    const float x = fld(tb, lo, 0);
-                    const int kxs = kxr_stride(kmax);
-                    hm = 0;
+        const StateParams p = prm[run_bins ? s : w.s0];
+        const float ao2 = p.ao2, at2 = p.at2, Af = HAS_H ? p.Af : 0.f;
+        auto rec = [&](int a, int j) {
+            return srec + (((int64_t)s * nsp + a) * (int64_t)(kmax + 1) + j) * kSplineRec32;
+        };
+        auto install = [&](int a, int j) {
+            const float4 A = __ldg(reinterpret_cast<const float4*>(rec(a, j)));
+            const float4 B = __ldg(reinterpret_cast<const float4*>(rec(a, j)) + 1);
+            s_xr[a][tid] = A.x;
+            s_jj[a][tid] = j;
+            cxo[a] = A.y;
+            c0[a] = A.z;
+            c1[a] = A.w;
+            c2[a] = B.x;
+            c3[a] = B.y;
+            hm = B.w <= (float)kRobustT ? (hm & ~(1u << a)) : (hm | (1u << a));
+        };
+        float xmin = 0.f;
+        if (run_bins) {
+            // intervals at the first bin: the count of right ends <= x in the right-end table
+            const float x = fld(tb, lo, 0);
+            const int kxs = kxr_stride(kmax);
+            hm = 0;
 #pragma unroll
-                    for (int a = 0; a < NSP; ++a) {
-                        const float4* kq = reinterpret_cast<const float4*>(kxr + ((int64_t)s * nsp + a) * kxs);
-                        int j = 0;
-                        for (int q = 0; q < kxs / 4; ++q) {
-                            const float4 v = __ldg(kq + q);
-                            j += (v.x <= x) + (v.y <= x) + (v.z <= x) + (v.w <= x);
-                        }
-                        install(a, min(j, kmax));
-                    }
+            for (int a = 0; a < NSP; ++a) {
+                const float4* kq = reinterpret_cast<const float4*>(kxr + ((int64_t)s * nsp + a) * kxs);
+                int j = 0;
+                for (int q = 0; q < kxs / 4; ++q) {
+                    const float4 v = __ldg(kq + q);
+                    j += (v.x <= x) + (v.y <= x) + (v.z <= x) + (v.w <= x);
                 }
-                float xmin = s_xr[0][tid];
+                install(a, min(j, kmax));
+            }
+            xmin = s_xr[0][tid];
 #pragma unroll
-                for (int a = 1; a < NSP; ++a) xmin = fminf(xmin, s_xr[a][tid]);
+            for (int a = 1; a < NSP; ++a) xmin = fminf(xmin, s_xr[a][tid]);
+        }
+        for (int ch = 0; ch < nch; ++ch, ++gch) {
+            int* nq = &s_nq[gch & 1];
+            if (run_bins) {
                 float acc = 0.f;
-                int run = 0;
-                for (int i = lo; i < hi; ++i) {
+                const int iend = min(hi, lo + (ch + 1) * kFullChunk);
+                for (int i = lo + ch * kFullChunk; i < iend; ++i) {
                     const float x = fld(tb, i, 0);
                     if (x >= xmin) {
 #pragma unroll
@@ -306,109 +374,154 @@ __global__ void __launch_bounds__(kFullThreads, 4)
                         const float t = x - cxo[a];
                         pv[a] = fmaf(fmaf(fmaf(c3[a], t, c2[a]), t, c1[a]), t, c0[a]);
                     }
-                    bool careful = hm != 0;
-                    float term = 0.f;
-                    if (!careful) {
-                        float D[3], Cc[3];
-                        float eh = 0.f;
-                        if (HAS_H) {
-                            const float sl = BROKEN ? (ell < 0.f ? p.n1 : p.n2) : p.n1;
-                            const float ex = fmaf(sl, ell, pv[3]);
-                            careful |= !(fabsf(ex) < kFullSafe);
-                            eh = Af * ex2_approx(ex);
-                        }
-#pragma unroll
-                        for (int c = 0; c < 3; ++c) {
-                            careful |= !(fabsf(pv[c]) < kFullSafe);
-                            D[c] = fmaf(ao2, fld(tb, i, 3 + c), at2 * fld(tb, i, 6 + c)) * ex2_approx(pv[c]);
-                            Cc[c] = HAS_H ? fmaf(eh, fld(tb, i, 9 + c), D[c]) : D[c];
-                        }
-                        const float dmin = fminf(fminf(D[0], D[1]), D[2]);
-                        const float cmax = fmaxf(fmaxf(Cc[0], Cc[1]), Cc[2]);
-                        careful |= !(dmin > 1e-36f && cmax < 1e36f);
-                        if (!careful) {
-                            float rr[3], ss[3];
-#pragma unroll
-                            for (int q = 0; q < 3; ++q) {
-                                const float zq = pv[ZB + q];   // z log2(10)
-                                const float iq = rsqrtf(fmaf(zq, zq, kL2 * kL2));
-                                rr[q] = zq * iq;
-                                ss[q] = kL2 * iq;
-                            }
-                            const float R12 = fmaf(rr[0], rr[1], ss[0] * ss[1] * rr[2]);
-                            float u[3], g[3];
-#pragma unroll
-                            for (int c = 0; c < 3; ++c) {
-                                u[c] = rsqrtf(Cc[c]);
-                                g[c] = D[c] * rsqrtf(D[c]) * u[c];
-                            }
-                            const float K01 = rr[0] * g[0] * g[1], K02 = rr[1] * g[0] * g[2], K12 = R12 * g[1] * g[2];
-                            const float A00 = fmaf(-K12, K12, 1.f), A11 = fmaf(-K02, K02, 1.f), A22 = fmaf(-K01, K01, 1.f);
-                            const float A01 = fmaf(K02, K12, -K01), A02 = fmaf(K01, K12, -K02), A12 = fmaf(K01, K02, -K12);
-                            const float det = fmaf(K02, A02, fmaf(K01, A01, A00));
-                            const int pb = (i >> 1) * kPairCross + (i & 1);
-                            const float x01 = tx[pb], x02 = tx[pb + 2], x12 = tx[pb + 4];
-                            float num = fmaf(A00, u[0] * u[0], fmaf(A11, u[1] * u[1], A22 * (u[2] * u[2])));
-                            const float off = fmaf(A01 * x01, u[0] * u[1], fmaf(A02 * x02, u[0] * u[2], A12 * x12 * (u[1] * u[2])));
-                            num = fmaf(2.f, off, num);
-                            const float prod = det * Cc[0] * Cc[1] * Cc[2];
-                            float lg;
-                            if (prod > 1e-36f && prod < 1e36f)
-                                lg = lg2_approx(prod);
-                            else
-                                lg = lg2_approx(det) + lg2_approx(Cc[0]) + lg2_approx(Cc[1]) + lg2_approx(Cc[2]);
-                            term = nu * (fmaf(num, rcp_approx(det), -3.f) + (float)kLn2 * lg);
-                            careful |= !(fabsf(term) < 1e30f) || !(det > 0.f);
-                        }
-                    }
-                    if (careful) {
-                        // spline values in float-float from the records (hi + lo parts) and the
-                        // FP64 term; its -3 nu goes to the FP64 spill-over like the term itself
-                        const double xd = (double)x + (double)__ldg(xlo32 + w.bin0 + i);
-                        double pd[NSP];
+                    // the SGWB exponent sl ell + p_h (log2 A is in Af) and, per exponential, a
+                    // correction factor 1 + lo ln2 for an exponent known as hi + lo
+                    const float sl = BROKEN ? (ell < 0.f ? p.n1 : p.n2) : p.n1;
+                    float exh = HAS_H ? fmaf(sl, ell, pv[3]) : 0.f;
+                    float ah = Af;
+                    float corr[3] = {1.f, 1.f, 1.f}, corrh = 1.f;
+                    if (hm) {
+                        // an ill-conditioned interval (prior draws with close knots, rare and
+                        // divergent): its spline value in float-float from the record's low parts,
+                        // and the exponent as an exact hi + lo pair
+                        const ff xf = {x, __ldg(xlo32 + w.bin0 + i)};
 #pragma unroll
                         for (int a = 0; a < NSP; ++a) {
-                            const float* rr = rec(a, s_jj[a][tid]);
-                            const float4 A = __ldg(reinterpret_cast<const float4*>(rr));
-                            const float4 B = __ldg(reinterpret_cast<const float4*>(rr) + 1);
-                            const float4 Cq = __ldg(reinterpret_cast<const float4*>(rr) + 2);
-                            const float4 Dq = __ldg(reinterpret_cast<const float4*>(rr) + 3);
-                            const ff t = ff_add(ff{(float)xd, (float)(xd - (double)(float)xd)}, ff{-A.y, -Cq.x});
+                            if (!((hm >> a) & 1u)) continue;
+                            const float4* rr = reinterpret_cast<const float4*>(rec(a, s_jj[a][tid]));
+                            const float4 A = __ldg(rr), B = __ldg(rr + 1), Cq = __ldg(rr + 2), Dq = __ldg(rr + 3);
+                            const ff t = ff_add(xf, ff{-A.y, -Cq.x});
                             ff v = {B.y, Dq.x};
                             v = ff_add(ff_mul(v, t), ff{B.x, Cq.w});
                             v = ff_add(ff_mul(v, t), ff{A.w, Cq.z});
                             v = ff_add(ff_mul(v, t), ff{A.z, Cq.y});
-                            pd[a] = ((double)v.hi + (double)v.lo) * (1.0 / kLog2_10);   // log10 units
+                            if (a < 3) {
+                                pv[a] = v.hi;
+                                corr[a] = fmaf(v.lo, (float)kLn2, 1.f);
+                            } else if (HAS_H && a == 3) {
+                                const ff sf = BROKEN ? (ell < 0.f ? ff{p.n1, p.n1_lo} : ff{p.n2, p.n2_lo})
+                                                     : ff{p.n1, p.n1_lo};
+                                const ff ef = {ell, __ldg(elllo32 + w.bin0 + i)};
+                                const ff eh = ff_add(ff_add(v, ff_mul(sf, ef)), ff{p.lA_hi, p.lA_lo});
+                                exh = eh.hi;
+                                corrh = fmaf(eh.lo, (float)kLn2, 1.f);
+                                ah = 1.f;               // log2 A is in the exponent
+                            } else {
+                                pv[a] = v.hi + v.lo;    // a correlation value: plain
+                            }
                         }
-                        double qd[kRec];
-                        qd[1] = (double)ell + (double)__ldg(elllo32 + w.bin0 + i);
+                    }
+                    bool careful = false;
+                    float term = 0.f;
+                    {
+                        float D[3], H[3], Cc[3];
+                        const float eh = HAS_H ? ah * ex2_approx(exh) * corrh : 0.f;
 #pragma unroll
                         for (int c = 0; c < 3; ++c) {
-                            qd[3 + c] = fld(tb, i, 3 + c);
-                            qd[6 + c] = fld(tb, i, 6 + c);
-                            qd[9 + c] = fld(tb, i, 9 + c);
+                            D[c] = fmaf(ao2, fld(tb, i, 3 + c), at2 * fld(tb, i, 6 + c)) * (ex2_approx(pv[c]) * corr[c]);
+                            H[c] = HAS_H ? eh * fld(tb, i, 9 + c) : 0.f;
+                            Cc[c] = HAS_H ? D[c] + H[c] : D[c];
+                            // within 2^+-40 every product below stays a normal FP32 number; NaN fails
+                            careful |= !(D[c] > kFullLo) || !(Cc[c] < kFullHi);
                         }
-                        const int pb = (i >> 1) * kPairCross + (i & 1);
-                        const double xcd[3] = {tx[pb], tx[pb + 2], tx[pb + 4]};
-                        const double sl = BROKEN ? (qd[1] < 0.0 ? th[3] : th[4]) : th[3];
-                        const double pn[3] = {pd[0], pd[1], pd[2]};
-                        const double zv[3] = {pd[ZB], pd[ZB + 1], pd[ZB + 2]};
-                        const double t64 = full_term64<HAS_H>(pn, HAS_H ? pd[3] : 0.0, zv, qd, xcd, th[0] * th[0],
-                                                              th[1] * th[1], th[2], sl);
-                        if (nu != 0.f) far += (double)nu * (t64 - 3.0);
+                        if (!careful) {
+                            // w_c = 1 / C_cc, g_c^2 = D_c / C_cc, h_c = H_c / C_cc (g^2 + h = 1)
+                            const float Cp = Cc[0] * Cc[1] * Cc[2];
+                            const float W = rcp_approx(Cp);
+                            const float w[3] = {W * (Cc[1] * Cc[2]), W * (Cc[0] * Cc[2]), W * (Cc[0] * Cc[1])};
+                            float g2[3], h[3];
+#pragma unroll
+                            for (int c = 0; c < 3; ++c) {
+                                g2[c] = D[c] * w[c];
+                                h[c] = HAS_H ? H[c] * w[c] : 0.f;
+                            }
+                            // r = z / sqrt(1 + z^2), s = 1 / sqrt(1 + z^2) (z in log2(10) units)
+                            float rr[3], ss[3];
+#pragma unroll
+                            for (int q = 0; q < 3; ++q) {
+                                const float zq = pv[ZB + q];
+                                const float iq = rsqrtf(fmaf(zq, zq, kL2 * kL2));
+                                rr[q] = zq * iq;
+                                ss[q] = kL2 * iq;
+                            }
+                            // K = G R G + diag(h) with R = L L^T; the adjugate's diagonal and det K
+                            // as sums of non-negative products (no cancellation at any conditioning):
+                            // 1 - R01^2 = s0^2, 1 - R02^2 = s1^2, 1 - R12^2 = (s1 s2)^2 + e^2,
+                            // det R = (s0 s1 s2)^2
+                            const float R12 = fmaf(rr[0], rr[1], ss[0] * ss[1] * rr[2]);
+                            const float e = fmaf(rr[0] * rr[2], ss[1], -rr[1] * ss[0]);
+                            const float s12 = ss[1] * ss[2];
+                            const float m01 = ss[0] * ss[0], m02 = ss[1] * ss[1], m12 = fmaf(s12, s12, e * e);
+                            const float sR = ss[0] * s12;
+                            float A00, A11, A22, det;
+                            if (HAS_H) {
+                                A00 = fmaf(g2[1] * g2[2], m12, fmaf(h[1], h[2] + g2[2], h[2] * g2[1]));
+                                A11 = fmaf(g2[0] * g2[2], m02, fmaf(h[0], h[2] + g2[2], h[2] * g2[0]));
+                                A22 = fmaf(g2[0] * g2[1], m01, fmaf(h[0], h[1] + g2[1], h[1] * g2[0]));
+                                const float in = fmaf(g2[1] * g2[2], sR * sR,
+                                                      fmaf(h[1], fmaf(g2[2], m02, h[2]), h[2] * g2[1] * m01));
+                                det = fmaf(h[0], A00, g2[0] * in);
+                            } else {
+                                A00 = g2[1] * g2[2] * m12;
+                                A11 = g2[0] * g2[2] * m02;
+                                A22 = g2[0] * g2[1] * m01;
+                                det = g2[0] * g2[1] * g2[2] * (sR * sR);
+                            }
+                            // off-diagonal adjugate entries times Q_ab = P-hat_ab / sqrt(C_aa C_bb):
+                            //   A01 = g0 g1 [s1 (r1 r2 s0 - r0 s1) - h2 r1 R12],
+                            //   A02 = g0 g2 [s0 e - h1 r0 R12],  A12 = -g1 g2 [s0 s1 r2 + h0 r0 r1],
+                            // with g_a g_b Q_ab = sqrt(D_a D_b) w_a w_b P-hat_ab
+                            const int pb = (i >> 1) * kPairCross + (i & 1);
+                            const float x01 = tx[pb], x02 = tx[pb + 2], x12 = tx[pb + 4];
+                            float b01 = ss[1] * fmaf(rr[1] * rr[2], ss[0], -rr[0] * ss[1]);
+                            float b02 = ss[0] * e;
+                            float b12 = ss[0] * ss[1] * rr[2];
+                            if (HAS_H) {
+                                b01 = fmaf(-h[2] * rr[1], R12, b01);
+                                b02 = fmaf(-h[1] * rr[0], R12, b02);
+                                b12 = fmaf(h[0] * rr[0], rr[1], b12);
+                            }
+                            const float p01 = D[0] * D[1], p02 = D[0] * D[2], p12 = D[1] * D[2];
+                            const float o01 = b01 * x01 * (p01 * rsqrtf(p01)) * (w[0] * w[1]);
+                            const float o02 = b02 * x02 * (p02 * rsqrtf(p02)) * (w[0] * w[2]);
+                            const float o12 = b12 * x12 * (p12 * rsqrtf(p12)) * (w[1] * w[2]);
+                            const float dg = fmaf(A00, w[0], fmaf(A11, w[1], A22 * w[2]));
+                            const float num = fmaf(2.f, o01 + o02 - o12, dg);
+                            // rounding in the trace grows with its cancellation S / num and with
+                            // 1 / det K: beyond these limits (rare) the bin takes the FP64 term
+                            const float S = fmaf(2.f, fabsf(o01) + fabsf(o02) + fabsf(o12), dg);
+                            careful |= !(det > kFullMinDet) || !(S <= 8.f * fmaxf(num, 3.f * det));
+                            const float prod = det * Cp;
+                            const float lg = prod > 1e-36f ? lg2_approx(prod) : lg2_approx(det) + lg2_approx(Cp);
+                            term = nu * (fmaf(num, rcp_approx(det), -3.f) + (float)kLn2 * lg);
+                            careful |= !(fabsf(term) < 1e30f);
+                        }
+                    }
+                    if (careful) {
+                        const int q = atomicAdd(nq, 1);   // < kFullThreads * kFullChunk
+                        s_q[q] = ((uint32_t)tid << 16) | (uint32_t)i;
                         term = 0.f;
                     }
                     acc += term;
-                    if (++run == 32) {
-                        accf = ff_add(accf, ff{acc, 0.f});
-                        acc = 0.f;
-                        run = 0;
-                    }
                 }
                 accf = ff_add(accf, ff{acc, 0.f});
             }
+            __syncthreads();
+            // the chunk's careful bins, one per thread; the other counter is reset for the next chunk
+            const int nqv = *nq;
+            if (tid == 0) s_nq[(gch + 1) & 1] = 0;
+            for (int e = tid; e < nqv; e += kFullThreads) {
+                const uint32_t ent = s_q[e];
+                const int owner = (int)(ent >> 16), i = (int)(ent & 0xffffu);
+                const int so = w.s0 + (owner & (sc - 1));
+                const float nu = fld(tb, i, 2);
+                const double t64 = full_careful_term<HAS_H, BROKEN>(so, w.bin0 + i, tb, tx, i, xlo32, elllo32, theta,
+                                                                    kxr, srec, kmax, nsp);
+                if (nu != 0.f) atomicAdd(&s_far[owner], (double)nu * (t64 - 3.0));
+            }
+            __syncthreads();
         }
-        red[tid] = ((double)accf.hi + (double)accf.lo) + far;
+        red[tid] = ((double)accf.hi + (double)accf.lo) + s_far[tid];
         __syncthreads();
         if (r == 0 && active) {
             double sum = red[ls];

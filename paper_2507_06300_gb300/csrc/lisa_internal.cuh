@@ -50,6 +50,7 @@ constexpr int kStatusNonfinite = LISA_STATE_NONFINITE;
 constexpr unsigned kWaitLimit = 1u << 20;   // bounded spin on an mbarrier (then give up)
 constexpr int kErrTimeout = 1;              // workspace error word: a bounded wait gave up
 constexpr int kMaxTileBins = 2048;          // 2 staged tiles x 48 B/bin must fit in 227 KB
+constexpr int kMaxTileBinsFull = 1024;      // dense covariance: 2 staged tiles x 64 B/bin
 constexpr int kAdjBins = 2048;              // bins per (state, range) in the adjoint
 // Work balance of the fused kernel: an item (a tile of bins x a chunk of states) costs
 // (bins + kKnotBinsPerDecade x its width in log10 f) per state.  The second term stands for the
