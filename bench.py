@@ -772,6 +772,54 @@ def run_ours(args):
                         **res}
         ds_r.close()
 
+    # ---- RJ-PT sampler at the largest configuration: A,E,T; 524,288 bins; 32 x 256 walkers -------
+    if "rjpt_full" in args.extras and rank == 0:
+        from paper_2507_06300_gb300 import rjpt
+        wlf = synth.workload("full")
+        P_f = make_periodogram_gpu(wlf, B, torch)
+        ds_f = B.Dataset.from_workload(wlf, P_f)
+        Tf, Wf, kmax_f = 32, 256, wlf.knots.kmax
+        assert Tf * Wf == wlf.n_states
+        cnt_t, x_t, w_t, _, kind_f = B.knots_to_device(wlf.knots)
+        th_t = torch.as_tensor(wlf.theta, device="cuda")
+        best_f, _ = autotune.autotune(ds_f, th_t, cnt_t, x_t, w_t, kmax_f, kind_f, B.FP32, groups=(4,))
+        like = rjpt.GpuLikelihood(ds_f, kmax_f, kind=kind_f, precision=B.FP32)
+        smp = rjpt.RJPTSampler(like, betas=rjpt.paper_ladder(Tf), n_walkers=Wf, n_splines=wlf.n_splines, kmax=kmax_f,
+                               k_max_rj=kmax_f, x_lo=float(wlf.x_lo[0]), x_hi=float(wlf.x_hi[0]), sgwb_model=2,
+                               seed=20250706)
+        # the walkers start from the workload's states (prior and posterior draws, 0-40 knots)
+        smp.set_state(rjpt.State(wlf.theta.copy(), wlf.knots.count.copy(), wlf.knots.x.copy(), wlf.knots.w.copy()))
+        smp.run(2, n_adapt=2)
+        n_sw = max(3, min(args.steps // 150, 10))
+        torch.cuda.synchronize()
+        g0, c0 = like.seconds, like.calls
+        t0 = time.perf_counter()
+        smp.run(n_sw, n_adapt=n_sw)
+        el = time.perf_counter() - t0
+        g_s, n_calls = like.seconds - g0, like.calls - c0
+        sb_call = wlf.n_states * wlf.n_bins
+        line["rjpt_full"] = {
+            "workload": "A,E,T; 524,288 bins 0.1-29 mHz; Nseg=128; broken power-law SGWB; 32 temperatures "
+                        "(paper ladder) x 256 walkers = 8,192 states; 0-40 in-between knots per spline",
+            "what": "RJ-PT sweeps: MALA (log L and gradient from lisa_psd_loglike_grad, FP32) + knot birth/death + "
+                    "PT swaps; states start from the workload's draws; tiles autotuned on the forward kernel",
+            "sweeps": n_sw, "sweeps_per_s": n_sw / el, "s_per_sweep": el / n_sw,
+            "library_calls_per_sweep": n_calls / n_sw,
+            "state_bins_per_s_through_sampler": n_calls * sb_call / el,
+            "gpu_call_share": g_s / el,
+            "host_numpy_share": 1.0 - g_s / el,
+            "gpu_call_ms": 1e3 * g_s / max(n_calls, 1),
+            "note": "gpu_call_ms: wall time of one library call with the state upload (theta, counts, x, w), the "
+                    "spline setup, log L + gradient of all states and the download of both; the rest of each "
+                    "sweep is the host-side proposal, prior, accept and swap arithmetic in numpy",
+            "tiling": best_f,
+            "acceptance": {k: {"coldest": round(float(a[0]), 3), "mean": round(float(np.mean(a)), 3)}
+                           for k, a in smp.acceptance().items()},
+        }
+        del like, smp
+        ds_f.close()
+        del P_f, cnt_t, x_t, w_t, th_t
+
     # ---- batched datasets and the full-form workload ----------------------------------------------
     line["workloads"] = {}
     if "full_cov" in args.extras:
@@ -874,15 +922,16 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-states", type=int, default=4, help="states per reference step")
     ap.add_argument("--tiling", default="", help="tile_bins,states_per_cta,group (skips the autotuner)")
-    ap.add_argument("--extras", default="adjoint,prep,rjpt,batched,full,full_cov",
-                    help="comma-separated extra workloads to measure: adjoint, prep, rjpt, batched, full, full_cov")
+    ap.add_argument("--extras", default="adjoint,prep,rjpt,batched,full,full_cov,rjpt_full",
+                    help="comma-separated extra workloads to measure: adjoint, prep, rjpt, batched, full, full_cov, "
+                         "rjpt_full")
     ap.add_argument("--no-extras", action="store_true", help="measure the headline workload only")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     args.extras = set() if args.no_extras else {e.strip() for e in args.extras.split(",") if e.strip()}
-    if not args.extras <= {"adjoint", "prep", "rjpt", "batched", "full", "full_cov"}:
-        ap.error("--extras takes adjoint, prep, rjpt, batched, full, full_cov")
+    if not args.extras <= {"adjoint", "prep", "rjpt", "batched", "full", "full_cov", "rjpt_full"}:
+        ap.error("--extras takes adjoint, prep, rjpt, batched, full, full_cov, rjpt_full")
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

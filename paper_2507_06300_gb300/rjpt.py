@@ -32,6 +32,7 @@ from __future__ import annotations
 
 import dataclasses
 import math
+import time
 
 import numpy as np
 
@@ -133,8 +134,18 @@ class GpuLikelihood:
         self.ws = torch.empty(dataset.workspace_bytes(kmax, precision, True), dtype=torch.uint8, device="cuda")
         self.out = torch.empty(S, dtype=torch.float64, device="cuda")
         self.grad = torch.empty((S, N_THETA + nsp * (2 * self.kmax + 2)), dtype=torch.float64, device="cuda")
+        self.seconds = 0.0   # wall time inside the calls (copies, library calls, synchronisation)
+        self.calls = 0
 
     def __call__(self, st: State, with_grad: bool = True):
+        t0 = time.perf_counter()
+        try:
+            return self._call(st, with_grad)
+        finally:
+            self.seconds += time.perf_counter() - t0
+            self.calls += 1
+
+    def _call(self, st: State, with_grad: bool):
         t = self.torch
         theta = t.as_tensor(np.ascontiguousarray(st.theta), device="cuda")
         count = t.as_tensor(np.ascontiguousarray(st.count, np.int32), device="cuda")
