@@ -11,6 +11,7 @@ import math
 
 import numpy as np
 import pytest
+import torch
 from scipy import stats
 
 from paper_2507_06300_gb300 import rjpt
@@ -48,9 +49,9 @@ def test_flat_likelihood_recovers_the_prior_and_the_uniform_count_prior():
     assert chi2 < 3.0 * stats.chi2.ppf(0.999, kr), hist
     # knot positions uniform, amplitudes N(0, 0.1), theta uniform in Table I
     mx, mw = rjpt.knot_masks(s.st.count, kmax)
-    xa = s.st.x[mx]
+    xa = s.st.x[mx].numpy()
     assert stats.kstest((xa - X_LO) / (X_HI - X_LO), "uniform").pvalue > 1e-3
-    wa = s.st.w[mw]
+    wa = s.st.w[mw].numpy()
     assert abs(wa.mean()) < 0.02 and abs(wa.std() - rjpt.W_SIGMA) < 0.02
     th = rec["theta"][20:].reshape(-1, rjpt.N_THETA)
     mid = 0.5 * (rjpt.THETA_LO + rjpt.THETA_HI)
@@ -66,13 +67,14 @@ def test_mala_recovers_a_gaussian_posterior_and_tempering_widens_it():
     sig = np.array([0.05, 0.02, 0.01, 0.03, 0.03])
 
     def like(st, with_grad=True):
-        S = st.theta.shape[0]
-        z = (st.theta - mu) / sig
-        L = -0.5 * np.sum(z[:, :4] ** 2, axis=1) - 0.5 * np.sum(st.w[:, :, [0, kmax + 1]] ** 2, axis=(1, 2)) / 0.01 ** 2
+        th, w = st.theta.numpy(), st.w.numpy()
+        S = th.shape[0]
+        z = (th - mu) / sig
+        L = -0.5 * np.sum(z[:, :4] ** 2, axis=1) - 0.5 * np.sum(w[:, :, [0, kmax + 1]] ** 2, axis=(1, 2)) / 0.01 ** 2
         g = np.zeros((S, rjpt.N_THETA + nsp * (2 * kmax + 2)))
         g[:, :4] = -(z / sig)[:, :4]
-        g[:, rjpt.N_THETA + 0] = -st.w[:, 0, 0] / 0.01 ** 2
-        g[:, rjpt.N_THETA + kmax + 1] = -st.w[:, 0, kmax + 1] / 0.01 ** 2
+        g[:, rjpt.N_THETA + 0] = -w[:, 0, 0] / 0.01 ** 2
+        g[:, rjpt.N_THETA + kmax + 1] = -w[:, 0, kmax + 1] / 0.01 ** 2
         return L, g
 
     betas = [1.0, 0.25]
@@ -86,7 +88,7 @@ def test_mala_recovers_a_gaussian_posterior_and_tempering_widens_it():
     acc = s.acceptance()["mala"]
     assert 0.3 < acc[0] < 0.85
     # the beta = 1/4 chain samples N(mu, sig / sqrt(beta))
-    hot = s.st.theta[128:, :4]
+    hot = s.st.theta[128:, :4].numpy()
     assert np.allclose(hot.std(axis=0), sig[:4] * 2.0, rtol=0.35)
 
 
@@ -96,24 +98,25 @@ def test_swap_acceptance_follows_the_tempered_likelihood_ratio():
 
     def like(st, with_grad=True):
         S = st.theta.shape[0]
-        L = np.where(st.theta[:, 0] < 50.0, levels[0], levels[1])
+        L = np.where(st.theta[:, 0].numpy() < 50.0, levels[0], levels[1])
         return L, np.zeros((S, rjpt.N_THETA + nsp * 2))
 
     betas = [1.0, 0.3]
     s = rjpt.RJPTSampler(like, betas=betas, n_walkers=4000, n_splines=nsp, kmax=kmax, k_max_rj=0, x_lo=X_LO,
                          x_hi=X_HI, seed=7)
     s.init_from_prior()
-    th = s.st.theta.copy()
+    th = s.st.theta.clone()
     th[:4000, 0] = 10.0      # cold walkers at log L = -10, hot ones at -12
     th[4000:, 0] = 90.0
     s.set_state(rjpt.State(th, s.st.count, s.st.x, s.st.w))
     s.swap()
     # exchanging raises the cold chain's log L by -2: accepted with exp((1 - 0.3) * (-2))
     p = math.exp((1.0 - 0.3) * (-12.0 + 10.0))
-    frac = np.mean(s.st.theta[:4000, 0] > 50.0)
+    th1, L1 = s.st.theta.numpy(), s.logL.numpy()
+    frac = np.mean(th1[:4000, 0] > 50.0)
     assert abs(frac - p) < 4.0 * math.sqrt(p * (1 - p) / 4000)
     # exchanged states keep their own log L
-    assert np.all(s.logL[:4000][s.st.theta[:4000, 0] > 50.0] == -12.0)
+    assert np.all(L1[:4000][th1[:4000, 0] > 50.0] == -12.0)
 
 
 def test_stepping_stone_matches_the_closed_form_evidence():
@@ -154,8 +157,8 @@ def test_sweeps_with_the_oracle_keep_log_l_consistent():
     nsp, kmax = wl.n_splines, 6
 
     def like(st, with_grad=True):
-        kn = {"count": st.count, "x": st.x, "w": st.w, "kmax": kmax, "kind": 0}
-        L, g, status = oracle.loglike_grad(ds, st.theta, kn)
+        kn = {"count": st.count.numpy(), "x": st.x.numpy(), "w": st.w.numpy(), "kmax": kmax, "kind": 0}
+        L, g, status = oracle.loglike_grad(ds, st.theta.numpy(), kn)
         return np.where(status == 0, L, -np.inf), g
 
     x_lo, x_hi = float(ds["x_lo"]), float(ds["x_hi"])
@@ -163,11 +166,11 @@ def test_sweeps_with_the_oracle_keep_log_l_consistent():
                          x_hi=x_hi, sgwb_model=1, seed=1)
     s.init_from_prior(theta_center=wl.theta_true[0], rel=0.01, k0=1)
     s.run(6, n_adapt=3)
-    kn = {"count": s.st.count, "x": s.st.x, "w": s.st.w, "kmax": kmax, "kind": 0}
-    L, _ = oracle.loglike(ds, s.st.theta, kn)
-    assert np.allclose(s.logL, L, rtol=1e-12, atol=0)
-    assert np.all(s.st.count <= 4)
-    assert np.all(np.isfinite(s.logL))
+    kn = {"count": s.st.count.numpy(), "x": s.st.x.numpy(), "w": s.st.w.numpy(), "kmax": kmax, "kind": 0}
+    L, _ = oracle.loglike(ds, s.st.theta.numpy(), kn)
+    assert np.allclose(s.logL.numpy(), L, rtol=1e-12, atol=0)
+    assert np.all(s.st.count.numpy() <= 4)
+    assert np.all(np.isfinite(s.logL.numpy()))
 
 
 def test_stepping_stone_of_a_constant_likelihood_is_exactly_its_value():
@@ -186,10 +189,10 @@ def test_mala_proposal_mean_is_the_preconditioned_gradient_step():
     mu, sig = 20.0, 0.5
 
     def like(st, with_grad=True):
-        S = st.theta.shape[0]
-        g = np.zeros((S, rjpt.N_THETA + nsp * 2))
-        g[:, 0] = -(st.theta[:, 0] - mu) / sig ** 2
-        return -0.5 * ((st.theta[:, 0] - mu) / sig) ** 2, g
+        th = st.theta.numpy()
+        g = np.zeros((th.shape[0], rjpt.N_THETA + nsp * 2))
+        g[:, 0] = -(th[:, 0] - mu) / sig ** 2
+        return -0.5 * ((th[:, 0] - mu) / sig) ** 2, g
 
     s = rjpt.RJPTSampler(like, betas=[0.5], n_walkers=4, n_splines=nsp, kmax=kmax, k_max_rj=0, x_lo=X_LO,
                          x_hi=X_HI, sgwb_model=0, seed=0)
@@ -201,21 +204,11 @@ def test_mala_proposal_mean_is_the_preconditioned_gradient_step():
     seen = []
 
     def like_spy(st, with_grad=True):
-        seen.append(st.theta.copy())
+        seen.append(st.theta.numpy().copy())
         return like(st, with_grad)
 
-    class NoNoise:                      # the generator with its Gaussian draws switched off
-        def __init__(self, g):
-            self.g = g
-
-        def standard_normal(self, size=None):
-            return np.zeros(size)
-
-        def __getattr__(self, name):
-            return getattr(self.g, name)
-
     s.like = like_spy
-    s.rng = NoNoise(s.rng)
+    s._normal = lambda shape: torch.zeros(shape, dtype=torch.float64)   # Gaussian draws switched off
     s.mala()
     z = 21.0
     expect = z + 0.5 * 0.3 ** 2 * (0.5 * -(z - mu) / sig ** 2)   # beta = 0.5, flat theta prior
