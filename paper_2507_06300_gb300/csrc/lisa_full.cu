@@ -243,10 +243,10 @@ __device__ __noinline__ double full_careful_term(int s, int bin, const float* tb
 // that det K and the adjugate's diagonal are sums of non-negative products, accurate to a few
 // rounding errors whatever the conditioning.  A bin whose diagonal entries leave 2^+-40, whose
 // det K is below 1/16 or whose trace cancels by more than a factor 8 ("careful" bins: extreme
-// states, rare) is queued in shared memory instead; after every chunk of kFullChunk bins the whole
-// CTA evaluates the queued bins in FP64, one bin per thread, so that they cost full warps rather
-// than a divergent branch in the bin loop.  The queue holds a chunk's worth of bins of every
-// thread and cannot overflow.
+// states, rare) is queued in shared memory instead; after every chunk of kFullChunk bins the warp
+// evaluates its queued bins in FP64, one bin per lane, so that they cost full lanes rather than a
+// divergent branch in the bin loop (and no CTA barrier: the warps of a CTA drift freely within an
+// item).  Each warp's queue holds a chunk's worth of bins of its 32 threads and cannot overflow.
 template <bool HAS_H, bool BROKEN>
 __global__ void __launch_bounds__(kFullThreads, 4)
     full_fp32_kernel(const WorkItem* __restrict__ items, int n_items, const float* __restrict__ rec32,
@@ -265,15 +265,16 @@ __global__ void __launch_bounds__(kFullThreads, 4)
     __shared__ int s_jj[NSP][kFullThreads];
     __shared__ double red[kFullThreads];
     __shared__ double s_far[kFullThreads];                 // FP64 sums of the queued bins, per thread
-    __shared__ uint32_t s_q[kFullThreads * kFullChunk];   // careful queue: thread << 16 | bin
-    __shared__ int s_nq[2];
+    __shared__ uint32_t s_q[kFullThreads / 32][32 * kFullChunk];   // per-warp careful queue: thread << 16 | bin
+    __shared__ int s_nq[kFullThreads / 32];
     __shared__ int s_fail;   // a bounded wait ran out: stage nothing more (a late copy may still land)
     const int tid = threadIdx.x;
+    const int wid = tid >> 5, lane = tid & 31;
     const size_t stage_floats = (size_t)tile_bins * kRec + (size_t)(tile_bins >> 1) * kPairCross;
     float* sb[2] = {reinterpret_cast<float*>(smem), reinterpret_cast<float*>(smem) + stage_floats};
     if (tid == 0) {
         s_fail = 0;
-        s_nq[0] = s_nq[1] = 0;
+        for (int q = 0; q < kFullThreads / 32; ++q) s_nq[q] = 0;
         bar_init(&bars[0]);
         bar_init(&bars[1]);
         if ((int)blockIdx.x < n_items) stage_item(sb[0], rec32, cross32, items[blockIdx.x], tile_bins, &bars[0]);
@@ -283,7 +284,6 @@ __global__ void __launch_bounds__(kFullThreads, 4)
     float cxo[NSP], c0[NSP], c1[NSP], c2[NSP], c3[NSP];
     unsigned hm = 0;
     int k = 0;
-    unsigned gch = 0;   // chunks run so far (uniform over the CTA): picks the queue counter
     for (int it = blockIdx.x; it < n_items; it += gridDim.x, ++k) {
         const int b = k & 1;
         const int nxt = it + gridDim.x;
@@ -345,8 +345,8 @@ __global__ void __launch_bounds__(kFullThreads, 4)
 #pragma unroll
             for (int a = 1; a < NSP; ++a) xmin = fminf(xmin, s_xr[a][tid]);
         }
-        for (int ch = 0; ch < nch; ++ch, ++gch) {
-            int* nq = &s_nq[gch & 1];
+        int* nq = &s_nq[wid];
+        for (int ch = 0; ch < nch; ++ch) {
             if (run_bins) {
                 float acc = 0.f;
                 const int iend = min(hi, lo + (ch + 1) * kFullChunk);
@@ -498,20 +498,23 @@ __global__ void __launch_bounds__(kFullThreads, 4)
                         }
                     }
                     if (careful) {
-                        const int q = atomicAdd(nq, 1);   // < kFullThreads * kFullChunk
-                        s_q[q] = ((uint32_t)tid << 16) | (uint32_t)i;
+                        const int q = atomicAdd(nq, 1);   // < 32 * kFullChunk
+                        s_q[wid][q] = ((uint32_t)tid << 16) | (uint32_t)i;
                         term = 0.f;
                     }
                     acc += term;
                 }
                 accf = ff_add(accf, ff{acc, 0.f});
             }
-            __syncthreads();
-            // the chunk's careful bins, one per thread; the other counter is reset for the next chunk
-            const int nqv = *nq;
-            if (tid == 0) s_nq[(gch + 1) & 1] = 0;
-            for (int e = tid; e < nqv; e += kFullThreads) {
-                const uint32_t ent = s_q[e];
+            // the warp's careful bins of this chunk, one per lane (the warp's lanes share the chunk
+            // loop; only this warp's threads own them)
+            // (lane 0 reads the count after every lane's appends and broadcasts it: no lane can
+            // append for the next chunk before the shuffle, so the count is the same for all)
+            __syncwarp();
+            const int nqv = __shfl_sync(0xffffffffu, lane == 0 ? *reinterpret_cast<volatile int*>(nq) : 0, 0);
+            if (nqv == 0) continue;
+            for (int e = lane; e < nqv; e += 32) {
+                const uint32_t ent = s_q[wid][e];
                 const int owner = (int)(ent >> 16), i = (int)(ent & 0xffffu);
                 const int so = w.s0 + (owner & (sc - 1));
                 const float nu = fld(tb, i, 2);
@@ -519,7 +522,9 @@ __global__ void __launch_bounds__(kFullThreads, 4)
                                                                     kxr, srec, kmax, nsp);
                 if (nu != 0.f) atomicAdd(&s_far[owner], (double)nu * (t64 - 3.0));
             }
-            __syncthreads();
+            __syncwarp();
+            if (lane == 0) *nq = 0;
+            __syncwarp();
         }
         red[tid] = ((double)accf.hi + (double)accf.lo) + s_far[tid];
         __syncthreads();
