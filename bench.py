@@ -748,7 +748,7 @@ def run_ours(args):
         for prec_name, prec in (("fp64", B.FP64), ("fp32", B.FP32)):
             smp = rjpt.RJPTSampler(rjpt.GpuLikelihood(ds_r, kmax_r, precision=prec), betas=rjpt.paper_ladder(Tr),
                                    n_walkers=Wr, n_splines=wlr.n_splines, kmax=kmax_r, k_max_rj=kmax_r, x_lo=x_lo_r,
-                                   x_hi=x_hi_r, sgwb_model=1, seed=20250706, device="cuda")
+                                   x_hi=x_hi_r, sgwb_model=1, seed=20250706, device="cpu")
             smp.init_from_prior(theta_center=wlr.theta_true[0], rel=0.01, k0=1)
             smp.run(5, n_adapt=5)
             torch.cuda.synchronize()
@@ -767,8 +767,10 @@ def run_ours(args):
                               "log_z_stepping_stone": lz}
         line["rjpt"] = {"workload": "A,E; 2,000 bins 0.1-29 mHz; Nseg=16; 32 walkers x 4 temperatures "
                                     "(paper ladder); 0-4 in-between knots per spline; 200 sweeps (100 adapting)",
-                        "what": "RJ-PT sampler, its state on the GPU: MALA (gradient from lisa_psd_loglike_grad), knot birth/"
-                                "death, PT swaps; every state's log L and gradient in one library call per move",
+                        "what": "RJ-PT sampler, its state in host tensors (at 128 states the per-operation "
+                                "launch cost of device tensors exceeds the arithmetic): MALA (gradient from "
+                                "lisa_psd_loglike_grad), knot birth/death, PT swaps; every state's log L and "
+                                "gradient in one library call per move",
                         **res}
         ds_r.close()
 
