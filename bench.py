@@ -44,14 +44,15 @@ MUFU_PER_STATE_BIN = MUFU_EX2 + MUFU_RCP + MUFU_LG2
 FP32_PER_STATE_BIN = 38
 TABLE_BYTES_PER_BIN = 12 * 4          # FP32 bin table: x, ell, nu, 3 x (G_oms, G_tm, G_h)
 # The FP32 adjoint kernel per state-bin, as implemented: per spline a compensated t (two-sum and
-# low parts, 9) and Horner (3) = 48; SGWB exponent and amplitude 2; per channel noise 2, SGWB 1,
-# PSD 1, g = nu r (r - 1) 3, forward term and channel product 2, template sums 5, spline signal 3
-# = 51; the log of the product 1; SGWB signal, log L and template accumulators 6; moments 6 per
-# spline = 24.  MUFU: 4 ex2, 3 rcp, 1 lg2 (of the channel product).
-ADJ_FP32_PER_STATE_BIN = 132
+# low parts, 9), Horner 3 and moments 6 = 72; SGWB exponent and amplitude 2; per channel noise 2,
+# SGWB 1, PSD 1, g / nu = r (r - 1) 1, g E 1, forward and channel product 2, template sums 3,
+# spline signal 1 = 12 (11 for the first channel) = 35; the log of the product 3 (range test and
+# FMA); nu times the bin's forward, template and SGWB sums 4, SGWB accumulators 2; nu times the
+# noise splines' signals 3 -- 121.  MUFU: 4 ex2, 3 rcp, 1 lg2 (of the channel product).
+ADJ_FP32_PER_STATE_BIN = 121
 # When every bin lies inside the knot band and |log10 f_lo| <= 2.9 |log10 f_hi| (the library's
-# exactness test for t = x - x_o in FP32), t takes 3 ops instead of 9 per spline: 108 in all.
-ADJ_FP32_PER_STATE_BIN_EXACT_T = 108
+# exactness test for t = x - x_o in FP32), t takes 3 ops instead of 9 per spline: 97 in all.
+ADJ_FP32_PER_STATE_BIN_EXACT_T = 97
 ADJ_MUFU = (4, 3, 1)
 # FP64-pipe instructions per state-bin of the plain FP64 kernel as implemented (the library's exp10,
 # exp2, log and divisions included), counted by ncu on a 131,072-bin x 64-state A,E,T case

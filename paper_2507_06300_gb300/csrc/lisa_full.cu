@@ -491,8 +491,15 @@ __global__ void __launch_bounds__(kFullThreads, 4)
                             // 1 / det K: beyond these limits (rare) the bin takes the FP64 term
                             const float S = fmaf(2.f, fabsf(o01) + fabsf(o02) + fabsf(o12), dg);
                             careful |= !(det > kFullMinDet) || !(S <= 8.f * fmaxf(num, 3.f * det));
+                            // ln det C from one log2 of det K times the product of the C_cc; a warp
+                            // vote keeps the two-log form (a product under 1e-36) a real branch
                             const float prod = det * Cp;
-                            const float lg = prod > 1e-36f ? lg2_approx(prod) : lg2_approx(det) + lg2_approx(Cp);
+                            const bool prod_ok = prod > 1e-36f;
+                            float lg;
+                            if (__all_sync(__activemask(), prod_ok) || prod_ok)
+                                lg = lg2_approx(prod);
+                            else
+                                lg = lg2_approx(det) + lg2_approx(Cp);
                             term = nu * (fmaf(num, rcp_approx(det), -3.f) + (float)kLn2 * lg);
                             careful |= !(fabsf(term) < 1e30f);
                         }

@@ -27,6 +27,7 @@
 // so slots never collide, and the epilogue adds them back in a fixed order.
 #include "lisa_math.cuh"
 #include "lisa_spline_dev.cuh"
+#include <type_traits>
 
 namespace lisa {
 
@@ -77,7 +78,9 @@ __global__ void __launch_bounds__(128, 4)
         const AdjUnit U = units[u];
         const DatasetDev& D = ds[U.ds];
         const int s = U.s0 + lane;
-        if (lane >= U.ns || (sstat[s] & kUserBits)) continue;
+        // the warp's active lanes (the chunk votes below run over them; the unit is warp-uniform)
+        const unsigned amask = __ballot_sync(kFullMask, lane < U.ns && (sstat[lane < U.ns ? s : U.s0] & kUserBits) == 0);
+        if (!((amask >> lane) & 1u)) continue;
         const double* th = theta + (size_t)s * LISA_N_THETA;
         const float ao2 = (float)(th[0] * th[0]), at2 = (float)(th[1] * th[1]);
         const float Af = HAS_H ? (float)exp10(th[2]) : 0.f;
@@ -137,21 +140,34 @@ __global__ void __launch_bounds__(128, 4)
 #pragma unroll
             for (int p = 0; p < 4; ++p) {
                 const float2 v = s_am[4 * a + p][tid];
-                row[p] = (double)v.x + (double)v.y;
+                row[p] = kLn10 * ((double)v.x + (double)v.y);   // q carries ln10 only here
                 s_am[4 * a + p][tid] = make_float2(0.f, 0.f);
             }
         };
+        auto flush_all = [&]() {
+#pragma unroll
+            for (int a = 0; a < NSP; ++a) flush_mom(a);
+#pragma unroll
+            for (int k = 0; k < 6; ++k) {
+                const float2 v = s_as[k][tid];
+                const ff r = ff_add(ff{v.x, v.y}, ff{cs[k], 0.f});
+                s_as[k][tid] = make_float2(r.hi, r.lo);
+                cs[k] = 0.f;
+            }
+        };
         // one bin: fields f[0..11] of the pair-block table (x, ell, nu, G_oms, G_tm, G_h) and the
-        // low part of x
-        auto bin = [&](int i, const float* f, float x_lo) {
+        // low part of x; CHECK: whether a spline may pass a knot at this bin
+        auto bin = [&](const float* f, float x_lo, auto check) {
             const float x = f[0], ell = f[1], nu = f[2];
             float P[NSP], tl[NSP];
 #pragma unroll
             for (int a = 0; a < NSP; ++a) {
-                while (x >= iv[a].xr && iv[a].j < __ldg(nint + (int64_t)s * nsp + a) - 1) {
-                    store_mom(a);
-                    ++iv[a].j;
-                    load(a);
+                if (decltype(check)::value) {
+                    while (x >= iv[a].xr && iv[a].j < __ldg(nint + (int64_t)s * nsp + a) - 1) {
+                        store_mom(a);
+                        ++iv[a].j;
+                        load(a);
+                    }
                 }
                 // t = x - x_o from the FP64 values (hi + lo parts): the position derivatives are
                 // sensitive to the ~1e-7 rounding of FP32 positions
@@ -170,41 +186,55 @@ __global__ void __launch_bounds__(128, 4)
                 const float sl = BROKEN ? (ell < 0.f ? n1 : n2) : n1;
                 eh = Af * ex2_approx(fmaf(sl, ell, P[C]));
             }
-            float fwd = -(float)C, To = 0.f, Tt = 0.f, H = 0.f, prod = 1.f;
-            float q[NSP], S[C];
+            // per channel g_c / nu = r (r - 1) with r = 1 / S-hat_c; the bin's sums are formed
+            // without nu, which scales each of them once
+            float fwd = -(float)C, To = 0.f, Tt = 0.f, Hs = 0.f, prod = 1.f;
+            float qn[C], S[C];
 #pragma unroll
             for (int c = 0; c < C; ++c) {
                 const float go = f[3 + c], gt = f[6 + c];
                 const float E = ex2_approx(P[c]);
                 const float N = fmaf(ao2, go, at2 * gt);
                 const float Eh = HAS_H ? eh * f[9 + c] : 0.f;
-                const float Sc = fmaf(E, N, Eh);
+                const float Sc = HAS_H ? fmaf(E, N, Eh) : E * N;
                 const float r = rcp_approx(Sc);
-                const float g = nu * r * (r - 1.f);
+                const float gp = fmaf(r, r, -r);
+                const float gE = gp * E;
                 fwd += r;
-                prod *= Sc;
+                prod = c == 0 ? Sc : prod * Sc;
                 S[c] = Sc;
-                To = fmaf(g * go, E, To);
-                Tt = fmaf(g * gt, E, Tt);
-                H = fmaf(g, Eh, H);
-                q[c] = (float)kLn10 * g * N * E;
+                To = c == 0 ? gE * go : fmaf(gE, go, To);
+                Tt = c == 0 ? gE * gt : fmaf(gE, gt, Tt);
+                if (HAS_H) Hs = c == 0 ? gp * Eh : fmaf(gp, Eh, Hs);
+                qn[c] = gE * N;
             }
             // sum_c ln S_c from one log2 of the channel product, per channel outside a safe range
-            if (prod > 1e-30f && prod < 1e30f) {
+            // (a warp vote keeps the rare per-channel form a real branch: predicated, its three
+            // lg2 would issue at every bin)
+            const bool prod_ok = prod > 1e-30f && prod < 1e30f;
+            if (__all_sync(amask, prod_ok)) {
+                fwd = fmaf((float)kLn2, lg2_approx(prod), fwd);
+            } else if (prod_ok) {
                 fwd = fmaf((float)kLn2, lg2_approx(prod), fwd);
             } else {
 #pragma unroll
                 for (int c = 0; c < C; ++c) fwd = fmaf((float)kLn2, lg2_approx(S[c]), fwd);
             }
-            if (HAS_H) q[C] = (float)kLn10 * H;
             cs[0] = fmaf(nu, fwd, cs[0]);
-            cs[1] += To;
-            cs[2] += Tt;
-            cs[3] += H;
-            if (BROKEN && ell >= 0.f)
-                cs[5] = fmaf(ell, H, cs[5]);
-            else
-                cs[4] = fmaf(ell, H, cs[4]);
+            cs[1] = fmaf(nu, To, cs[1]);
+            cs[2] = fmaf(nu, Tt, cs[2]);
+            float q[NSP];
+#pragma unroll
+            for (int c = 0; c < C; ++c) q[c] = nu * qn[c];
+            if (HAS_H) {
+                const float Hb = nu * Hs;
+                cs[3] += Hb;
+                if (BROKEN && ell >= 0.f)
+                    cs[5] = fmaf(ell, Hb, cs[5]);
+                else
+                    cs[4] = fmaf(ell, Hb, cs[4]);
+                q[C] = Hb;
+            }
 #pragma unroll
             for (int a = 0; a < NSP; ++a) {
                 const float t = tl[a], qt = q[a] * t, qt2 = qt * t;
@@ -213,36 +243,45 @@ __global__ void __launch_bounds__(128, 4)
                 cm[a][2] += qt2;
                 cm[a][3] = fmaf(qt2, t, cm[a][3]);
             }
-            if ((i & 15) == 15) {
-#pragma unroll
-                for (int a = 0; a < NSP; ++a) flush_mom(a);
-#pragma unroll
-                for (int k = 0; k < 6; ++k) {
-                    const float2 v = s_as[k][tid];
-                    const ff r = ff_add(ff{v.x, v.y}, ff{cs[k], 0.f});
-                    s_as[k][tid] = make_float2(r.hi, r.lo);
-                    cs[k] = 0.f;
-                }
-            }
         };
-        // the range's bins two at a time: one pair block of the table is six 16-byte loads (the
-        // same address in every lane of the warp), the low parts of x one 8-byte load
+        // the range's bins two at a time (one pair block of the table is six 16-byte loads, the
+        // same address in every lane of the warp; the low parts of x one 8-byte load), in chunks
+        // of 32 pair blocks: one vote over the warp's lanes per chunk decides whether any spline
+        // of any lane can pass a knot inside it (its last bin at or past an interval's right end);
+        // knot-free chunks skip the per-bin checks.  The chunk sums go to the running sums after
+        // every chunk.
         const float4* tb4 = reinterpret_cast<const float4*>(tb);
         const float2* xl2 = reinterpret_cast<const float2*>(xlo32 + b0);
-        for (int ip = 0; ip < (nb >> 1); ++ip) {
-            float4 q4[kPairRec / 4];
+        auto pairs = [&](int p0, int p1, auto check) {
+            for (int ip = p0; ip < p1; ++ip) {
+                float4 q4[kPairRec / 4];
 #pragma unroll
-            for (int k = 0; k < kPairRec / 4; ++k) q4[k] = __ldg(tb4 + ip * (kPairRec / 4) + k);
-            const float2 xl = __ldg(xl2 + ip);
-            const float* fq = reinterpret_cast<const float*>(q4);
-            float f0[kRec], f1[kRec];
+                for (int k = 0; k < kPairRec / 4; ++k) q4[k] = __ldg(tb4 + ip * (kPairRec / 4) + k);
+                const float2 xl = __ldg(xl2 + ip);
+                const float* fq = reinterpret_cast<const float*>(q4);
+                float f0[kRec], f1[kRec];
 #pragma unroll
-            for (int k = 0; k < kRec; ++k) {
-                f0[k] = fq[2 * k];
-                f1[k] = fq[2 * k + 1];
+                for (int k = 0; k < kRec; ++k) {
+                    f0[k] = fq[2 * k];
+                    f1[k] = fq[2 * k + 1];
+                }
+                bin(f0, xl.x, check);
+                bin(f1, xl.y, check);
             }
-            bin(2 * ip, f0, xl.x);
-            bin(2 * ip + 1, f1, xl.y);
+        };
+        constexpr int kChunkPairs = 32;
+        const int npair = nb >> 1;
+        for (int p0 = 0; p0 < npair; p0 += kChunkPairs) {
+            const int p1 = min(p0 + kChunkPairs, npair);
+            const float xlast = fld(tb, 2 * p1 - 1, 0);
+            bool cross = false;
+#pragma unroll
+            for (int a = 0; a < NSP; ++a) cross |= !(xlast < iv[a].xr);
+            if (__any_sync(amask, cross))
+                pairs(p0, p1, std::true_type{});
+            else
+                pairs(p0, p1, std::false_type{});
+            flush_all();
         }
 #pragma unroll
         for (int a = 0; a < NSP; ++a) store_mom(a);
@@ -272,7 +311,9 @@ __global__ void __launch_bounds__(128)
         const AdjUnit U = units[u];
         const DatasetDev& D = ds[U.ds];
         const int s = U.s0 + lane;
-        if (lane >= U.ns || (sstat[s] & kUserBits)) continue;
+        // the warp's active lanes (the chunk votes below run over them; the unit is warp-uniform)
+        const unsigned amask = __ballot_sync(kFullMask, lane < U.ns && (sstat[lane < U.ns ? s : U.s0] & kUserBits) == 0);
+        if (!((amask >> lane) & 1u)) continue;
         const double* th = theta + (size_t)s * LISA_N_THETA;
         const double ao2 = th[0] * th[0], at2 = th[1] * th[1], lA = th[2], n1 = th[3];
         const double n2 = BROKEN ? th[4] : n1;
@@ -390,9 +431,10 @@ __device__ __forceinline__ void akima_slope_grad(int k, int K, double mm2, doubl
         d[2] = 0.5;
         return;
     }
-    const double dwl = (ml - sk) / D, dwr = (mr - sk) / D;   // ds/dwl, ds/dwr
-    d[1] += wl / D;   // ds/dml
-    d[2] += wr / D;   // ds/dmr
+    const double iD = 1.0 / D;
+    const double dwl = (ml - sk) * iD, dwr = (mr - sk) * iD;   // ds/dwl, ds/dwr
+    d[1] += wl * iD;   // ds/dml
+    d[2] += wr * iD;   // ds/dmr
     if (k == 1) {
         // wl = |m_{k+1} - m_k|, wr = |m_k - m_{k-1}|
         const double a1 = sgn(mp1 - m0), a2 = sgn(m0 - mm1);
@@ -557,7 +599,7 @@ __global__ void __launch_bounds__(128)
         for (int q = 0; q < 2; ++q) {
             const int jj = lane + 32 * q;
             const bool iv = jj < nint;
-            const double h = W.h[q];
+            const double h = W.h[q], ih = W.ih[q], ih2 = ih * ih;
             const double M0 = M[q][0], M1 = M[q][1], M2 = M[q][2], M3 = M[q][3];
             ybar[q] = iv ? M0 : 0.0;
             xbar[q] = iv ? -(W.cb[q] * M0 + 2.0 * W.cc[q] * M1 + 3.0 * W.cd[q] * M2) : 0.0;
@@ -567,15 +609,15 @@ __global__ void __launch_bounds__(128)
                 mbar[q] = M1;
             } else if (kind == LISA_SPLINE_NATURAL) {
                 const double Mj = W.d2[q];
-                own[q] = -M1 * h / 3.0 + 0.5 * M2 - M3 / (6.0 * h);   // -> d/dM_j
-                nxt[q] = -M1 * h / 6.0 + M3 / (6.0 * h);                // -> d/dM_{j+1}
+                own[q] = -M1 * h * (1.0 / 3.0) + 0.5 * M2 - M3 * ih * (1.0 / 6.0);   // -> d/dM_j
+                nxt[q] = -M1 * h * (1.0 / 6.0) + M3 * ih * (1.0 / 6.0);                // -> d/dM_{j+1}
                 mbar[q] = M1;
                 (void)Mj;
             } else {
-                own[q] = M1 - 2.0 * M2 / h + M3 / (h * h);               // -> d/ds_j
-                nxt[q] = -M2 / h + M3 / (h * h);                         // -> d/ds_{j+1}
-                mbar[q] = 3.0 * M2 / h - 2.0 * M3 / (h * h);
-                hbar[q] = -W.cc[q] * M2 / h - 2.0 * W.cd[q] * M3 / h;
+                own[q] = M1 - 2.0 * M2 * ih + M3 * ih2;               // -> d/ds_j
+                nxt[q] = -M2 * ih + M3 * ih2;                         // -> d/ds_{j+1}
+                mbar[q] = 3.0 * M2 * ih - 2.0 * M3 * ih2;
+                hbar[q] = -(W.cc[q] * M2 + 2.0 * W.cd[q] * M3) * ih;
             }
         }
         if (K >= 4 && kind == LISA_SPLINE_NATURAL) {
@@ -584,7 +626,7 @@ __global__ void __launch_bounds__(128)
             spl::shift2(W.d2[0], W.d2[1], 1, Mn[0], Mn[1]);
             for (int q = 0; q < 2; ++q) {
                 const int jj = lane + 32 * q;
-                if (jj < nint) hbar[q] = -M[q][1] * (2.0 * W.d2[q] + Mn[q]) / 6.0 - W.cd[q] * M[q][3] / W.h[q];
+                if (jj < nint) hbar[q] = -M[q][1] * (2.0 * W.d2[q] + Mn[q]) * (1.0 / 6.0) - W.cd[q] * M[q][3] * W.ih[q];
             }
             // d/dM_k = own_k + nxt_{k-1}; M_0 and M_{K-1} are fixed
             double nprev[2], Mbar[2];
@@ -659,8 +701,8 @@ __global__ void __launch_bounds__(128)
         double gmy[2], gmyp[2], ghp[2];
         for (int q = 0; q < 2; ++q) {
             const int jj = lane + 32 * q;
-            gmy[q] = (jj < nint) ? mbar[q] / W.h[q] : 0.0;
-            if (jj < nint) hbar[q] -= W.m[q] * mbar[q] / W.h[q];
+            gmy[q] = (jj < nint) ? mbar[q] * W.ih[q] : 0.0;
+            if (jj < nint) hbar[q] -= W.m[q] * gmy[q];
             else hbar[q] = 0.0;
         }
         spl::shift2(gmy[0], gmy[1], -1, gmyp[0], gmyp[1]);

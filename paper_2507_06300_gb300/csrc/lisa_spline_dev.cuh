@@ -96,14 +96,14 @@ __device__ __forceinline__ T akima_slope(int j, int K, T mm2, T mm1, T m0, T mp1
 
 // One spline, built by a whole warp in FP64.  Per lane, slot q holds knot j = lane + 32 q:
 //   x, y     sorted knot positions and amplitudes (j < K)
-//   h, m     width and slope of interval j (j < K - 1)
+//   h, m     width and slope of interval j (j < K - 1); ih = 1 / h
 //   d2       Akima slope s_j (kind 0, K >= 4) or natural-cubic second derivative M_j (kind 1)
 //   ca..cd   coefficients of interval j about x_j (log10 units)
 // ra, rb are the sorted positions (1-based, edges excluded) of in-between knots lane, lane+32.
 struct WarpSpline {
     int K, st;
     int ra, rb;
-    double x[2], y[2], h[2], m[2], d2[2];
+    double x[2], y[2], h[2], ih[2], m[2], d2[2];
     double ca[2], cb[2], cc[2], cd[2];
 };
 
@@ -195,7 +195,7 @@ __device__ __forceinline__ void warp_build_spline(WarpSpline& W, const double* _
     T* m = W.m;
     shift2(x[0], x[1], 1, xn[0], xn[1]);
     shift2(y[0], y[1], 1, yn[0], yn[1]);
-    T ih[2];   // 1 / h
+    T* ih = W.ih;
     h[1] = ih[1] = T(1);
     m[1] = T(0);
     for (int q = 0; q < (K > 32 ? 2 : 1); ++q) {
