@@ -49,31 +49,61 @@ __device__ __forceinline__ double* mom_row(double* mom, int64_t prefix, int s, i
 }
 
 // ---- FP32 adjoint: one warp per (dataset, range, up to 32 states) -----------------------------
+// The current interval of a spline: right end and index, and -x_o, -x_o's low part and the cubic's
+// coefficients duplicated in register pairs for the packed (two bins per instruction) path.
 struct AdjIv {
-    float xl, xr, xo, xo_lo, c0, c1, c2, c3;
+    float xr;
     int j;
+    float2 nxo, nxo_lo, c0, c1, c2, c3;
 };
+
+__device__ __forceinline__ float2 dup2(float v) { return make_float2(v, v); }
+
+// asynchronous global -> shared copies of one thread (completion by cp.async.wait_group)
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((unsigned)__cvta_generic_to_shared(dst)), "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* dst, const void* src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((unsigned)__cvta_generic_to_shared(dst)), "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+constexpr int kAdjStagePairs = 16;   // pair blocks per staged chunk of the adjoint's table
 
 // EXACT_T: every bin lies inside the knot band and the band satisfies |x_lo| <= 2.9 |x_hi| (same
 // sign), so that within any interval |x - x_o| <= 2 |x| and |x_o| <= 2 |x| and the FP32 difference
 // x - x_o is exact (Sterbenz); t then needs no two-sum (the same value as the compensated form).
+//
+// Per bin the forward pass is recomputed and g_c / nu = r (r - 1), r = 1 / S-hat_c, drives the
+// template sums and each spline's signal q (the derivative of log L by the spline value; ln10 is
+// applied when the moments are stored).  Bins are taken two at a time from the pair-block table,
+// whose fields of both bins load as register pairs: a pair whose bins share every spline's
+// interval runs on the packed FP32x2 instructions, a pair with a knot between its bins runs as
+// two scalar bins.  Chunk sums are kept per lane of the pair (float2) and go to the float-float
+// running sums (shared memory) as exact two-sums every 64 bins and at interval ends.
 template <int C, bool HAS_H, bool BROKEN, bool EXACT_T>
-__global__ void __launch_bounds__(128, 4)
+__global__ void __launch_bounds__(128, 3)
     adjoint_fp32_kernel(const AdjUnit* __restrict__ units, int64_t n_units, const DatasetDev* __restrict__ ds,
                         const float* __restrict__ rec32, const float* __restrict__ xlo32,
                         const double* __restrict__ theta, const int32_t* __restrict__ sstat,
                         const int32_t* __restrict__ nint, const float* __restrict__ srec, int kmax, int nsp,
                         const int64_t* __restrict__ prefix, double* __restrict__ scal, double* __restrict__ mom) {
     constexpr int NSP = C + (HAS_H ? 1 : 0);
-    // float-float running sums (moments and template sums), touched once per 16 bins and at
-    // interval ends: kept in shared memory, [slot][thread], so that the per-bin loop has room
-    // for four CTAs per SM
     __shared__ float2 s_am[NSP * 4][128];
     __shared__ float2 s_as[6][128];
+    // per warp, two staged chunks of the table and of the low parts of x
+    __shared__ __align__(16) float s_tab[4][2][kAdjStagePairs * kPairRec];
+    __shared__ __align__(16) float2 s_xl[4][2][kAdjStagePairs];
     const int tid = threadIdx.x;
+    const int wid = tid >> 5;
     const int lane = threadIdx.x & 31;
     const int64_t wg = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const float2 m1 = dup2(-1.f);
     for (int64_t u = wg; u < n_units; u += nw) {
         const AdjUnit U = units[u];
         const DatasetDev& D = ds[U.ds];
@@ -89,49 +119,53 @@ __global__ void __launch_bounds__(128, 4)
         const int nb = (int)min((int64_t)kAdjBins, D.bin0 + D.npad - b0);
         const float* tb = rec32 + (b0 >> 1) * kPairRec;
         const int64_t pre = prefix[s];
-        AdjIv iv[NSP];
+        const int32_t* nint_s = nint + (int64_t)s * nsp;
+        AdjIv iv[NSP] = {};
         auto base = [&](int a) { return srec + ((int64_t)s * nsp + a) * (int64_t)(kmax + 1) * kSplineRec32; };
-        const float x0 = fld(tb, 0, 0);
-#pragma unroll
-        for (int a = 0; a < NSP; ++a) {
-            const int64_t sp = (int64_t)s * nsp + a;
-            iv[a].j = find_interval<float, kSplineRec32, 6>(base(a), nint[sp], x0);
-        }
         auto load = [&](int a) {
             const float* r = base(a) + (size_t)iv[a].j * kSplineRec32;
             iv[a].xr = __ldg(r + 0);
-            iv[a].xo = __ldg(r + 1);
-            iv[a].c0 = __ldg(r + 2);
-            iv[a].c1 = __ldg(r + 3);
-            iv[a].c2 = __ldg(r + 4);
-            iv[a].c3 = __ldg(r + 5);
-            iv[a].xl = __ldg(r + 6);
-            iv[a].xo_lo = __ldg(r + 8);
+            iv[a].nxo = dup2(-__ldg(r + 1));
+            iv[a].c0 = dup2(__ldg(r + 2));
+            iv[a].c1 = dup2(__ldg(r + 3));
+            iv[a].c2 = dup2(__ldg(r + 4));
+            iv[a].c3 = dup2(__ldg(r + 5));
+            iv[a].nxo_lo = dup2(-__ldg(r + 8));
         };
+        {
+            const float x0 = fld(tb, 0, 0);
 #pragma unroll
-        for (int a = 0; a < NSP; ++a) load(a);
-        // accumulators: chunk sums in FP32 (registers), running sums in float-float (shared)
-        float cm[NSP][4];
-        float cs[6];
+            for (int a = 0; a < NSP; ++a) {
+                iv[a].j = find_interval<float, kSplineRec32, 6>(base(a), nint_s[a], x0);
+                load(a);
+            }
+        }
+        // accumulators: chunk sums per lane of the bin pair (registers), running sums in
+        // float-float (shared)
+        float2 cm[NSP][4];
+        float2 cs[6];
 #pragma unroll
         for (int a = 0; a < NSP; ++a)
 #pragma unroll
             for (int p = 0; p < 4; ++p) {
-                cm[a][p] = 0.f;
+                cm[a][p] = make_float2(0.f, 0.f);
                 s_am[4 * a + p][tid] = make_float2(0.f, 0.f);
             }
 #pragma unroll
         for (int k = 0; k < 6; ++k) {
-            cs[k] = 0.f;
+            cs[k] = make_float2(0.f, 0.f);
             s_as[k][tid] = make_float2(0.f, 0.f);
         }
+        auto add_run = [&](float2* slot, float2 c) {
+            const float2 v = *slot;
+            const ff r = ff_add(ff{v.x, v.y}, two_sum(c.x, c.y));
+            *slot = make_float2(r.hi, r.lo);
+        };
         auto flush_mom = [&](int a) {
 #pragma unroll
             for (int p = 0; p < 4; ++p) {
-                const float2 v = s_am[4 * a + p][tid];
-                const ff r = ff_add(ff{v.x, v.y}, ff{cm[a][p], 0.f});
-                s_am[4 * a + p][tid] = make_float2(r.hi, r.lo);
-                cm[a][p] = 0.f;
+                add_run(&s_am[4 * a + p][tid], cm[a][p]);
+                cm[a][p] = make_float2(0.f, 0.f);
             }
         };
         auto store_mom = [&](int a) {
@@ -149,36 +183,33 @@ __global__ void __launch_bounds__(128, 4)
             for (int a = 0; a < NSP; ++a) flush_mom(a);
 #pragma unroll
             for (int k = 0; k < 6; ++k) {
-                const float2 v = s_as[k][tid];
-                const ff r = ff_add(ff{v.x, v.y}, ff{cs[k], 0.f});
-                s_as[k][tid] = make_float2(r.hi, r.lo);
-                cs[k] = 0.f;
+                add_run(&s_as[k][tid], cs[k]);
+                cs[k] = make_float2(0.f, 0.f);
             }
         };
-        // one bin: fields f[0..11] of the pair-block table (x, ell, nu, G_oms, G_tm, G_h) and the
-        // low part of x; CHECK: whether a spline may pass a knot at this bin
-        auto bin = [&](const float* f, float x_lo, auto check) {
+        auto advance = [&](int a, float x) {
+            while (x >= iv[a].xr && iv[a].j < __ldg(nint_s + a) - 1) {
+                store_mom(a);
+                ++iv[a].j;
+                load(a);
+            }
+        };
+        // one scalar bin (the fields f[0..11] of the table: x, ell, nu, G_oms, G_tm, G_h, and the
+        // low part of x), its sums in the first lane of the pair accumulators; the intervals
+        // must already hold the bin
+        auto bin = [&](const float* f, float x_lo) {
             const float x = f[0], ell = f[1], nu = f[2];
             float P[NSP], tl[NSP];
 #pragma unroll
             for (int a = 0; a < NSP; ++a) {
-                if (decltype(check)::value) {
-                    while (x >= iv[a].xr && iv[a].j < __ldg(nint + (int64_t)s * nsp + a) - 1) {
-                        store_mom(a);
-                        ++iv[a].j;
-                        load(a);
-                    }
-                }
-                // t = x - x_o from the FP64 values (hi + lo parts): the position derivatives are
-                // sensitive to the ~1e-7 rounding of FP32 positions
                 float t;
                 if (EXACT_T) {
-                    t = (x - iv[a].xo) + (x_lo - iv[a].xo_lo);
+                    t = (x + iv[a].nxo.x) + (x_lo + iv[a].nxo_lo.x);
                 } else {
-                    const ff tt = two_sum(x, -iv[a].xo);
-                    t = tt.hi + (tt.lo + (x_lo - iv[a].xo_lo));
+                    const ff tt = two_sum(x, iv[a].nxo.x);
+                    t = tt.hi + (tt.lo + (x_lo + iv[a].nxo_lo.x));
                 }
-                P[a] = fmaf(fmaf(fmaf(iv[a].c3, t, iv[a].c2), t, iv[a].c1), t, iv[a].c0);
+                P[a] = fmaf(fmaf(fmaf(iv[a].c3.x, t, iv[a].c2.x), t, iv[a].c1.x), t, iv[a].c0.x);
                 tl[a] = t;
             }
             float eh = 0.f;
@@ -186,8 +217,6 @@ __global__ void __launch_bounds__(128, 4)
                 const float sl = BROKEN ? (ell < 0.f ? n1 : n2) : n1;
                 eh = Af * ex2_approx(fmaf(sl, ell, P[C]));
             }
-            // per channel g_c / nu = r (r - 1) with r = 1 / S-hat_c; the bin's sums are formed
-            // without nu, which scales each of them once
             float fwd = -(float)C, To = 0.f, Tt = 0.f, Hs = 0.f, prod = 1.f;
             float qn[C], S[C];
 #pragma unroll
@@ -208,80 +237,212 @@ __global__ void __launch_bounds__(128, 4)
                 if (HAS_H) Hs = c == 0 ? gp * Eh : fmaf(gp, Eh, Hs);
                 qn[c] = gE * N;
             }
-            // sum_c ln S_c from one log2 of the channel product, per channel outside a safe range
-            // (a warp vote keeps the rare per-channel form a real branch: predicated, its three
-            // lg2 would issue at every bin)
-            const bool prod_ok = prod > 1e-30f && prod < 1e30f;
-            if (__all_sync(amask, prod_ok)) {
-                fwd = fmaf((float)kLn2, lg2_approx(prod), fwd);
-            } else if (prod_ok) {
+            if (prod > 1e-30f && prod < 1e30f) {
                 fwd = fmaf((float)kLn2, lg2_approx(prod), fwd);
             } else {
 #pragma unroll
                 for (int c = 0; c < C; ++c) fwd = fmaf((float)kLn2, lg2_approx(S[c]), fwd);
             }
-            cs[0] = fmaf(nu, fwd, cs[0]);
-            cs[1] = fmaf(nu, To, cs[1]);
-            cs[2] = fmaf(nu, Tt, cs[2]);
+            cs[0].x = fmaf(nu, fwd, cs[0].x);
+            cs[1].x = fmaf(nu, To, cs[1].x);
+            cs[2].x = fmaf(nu, Tt, cs[2].x);
             float q[NSP];
 #pragma unroll
             for (int c = 0; c < C; ++c) q[c] = nu * qn[c];
             if (HAS_H) {
                 const float Hb = nu * Hs;
-                cs[3] += Hb;
+                cs[3].x += Hb;
                 if (BROKEN && ell >= 0.f)
-                    cs[5] = fmaf(ell, Hb, cs[5]);
+                    cs[5].x = fmaf(ell, Hb, cs[5].x);
                 else
-                    cs[4] = fmaf(ell, Hb, cs[4]);
+                    cs[4].x = fmaf(ell, Hb, cs[4].x);
                 q[C] = Hb;
             }
 #pragma unroll
             for (int a = 0; a < NSP; ++a) {
                 const float t = tl[a], qt = q[a] * t, qt2 = qt * t;
-                cm[a][0] += q[a];
-                cm[a][1] += qt;
-                cm[a][2] += qt2;
-                cm[a][3] = fmaf(qt2, t, cm[a][3]);
+                cm[a][0].x += q[a];
+                cm[a][1].x += qt;
+                cm[a][2].x += qt2;
+                cm[a][3].x = fmaf(qt2, t, cm[a][3].x);
             }
         };
-        // the range's bins two at a time (one pair block of the table is six 16-byte loads, the
-        // same address in every lane of the warp; the low parts of x one 8-byte load), in chunks
-        // of 32 pair blocks: one vote over the warp's lanes per chunk decides whether any spline
-        // of any lane can pass a knot inside it (its last bin at or past an interval's right end);
-        // knot-free chunks skip the per-bin checks.  The chunk sums go to the running sums after
-        // every chunk.
+        // two bins in the same intervals of every spline, on the packed FP32x2 instructions: the
+        // table's fields of both bins F[0..11] and the low parts of their x
+        auto pair = [&](const float2* F, float2 xl) {
+            const float2 x = F[0], ell = F[1], nu = F[2];
+            float2 P[NSP], tl[NSP];
+#pragma unroll
+            for (int a = 0; a < NSP; ++a) {
+                float2 t;
+                if (EXACT_T) {
+                    t = __fadd2_rn(__fadd2_rn(x, iv[a].nxo), __fadd2_rn(xl, iv[a].nxo_lo));
+                } else {
+                    // two-sum of x and -x_o per lane: s + e = x - x_o exactly
+                    const float2 sm = __fadd2_rn(x, iv[a].nxo);
+                    const float2 bb = __ffma2_rn(x, m1, sm);                       // s - x
+                    const float2 e = __fadd2_rn(__ffma2_rn(__ffma2_rn(bb, m1, sm), m1, x),
+                                                __ffma2_rn(bb, m1, iv[a].nxo));     // (x - (s - b)) + (-x_o - b)
+                    t = __fadd2_rn(sm, __fadd2_rn(e, __fadd2_rn(xl, iv[a].nxo_lo)));
+                }
+                P[a] = __ffma2_rn(__ffma2_rn(__ffma2_rn(iv[a].c3, t, iv[a].c2), t, iv[a].c1), t, iv[a].c0);
+                tl[a] = t;
+            }
+            float2 eh = make_float2(0.f, 0.f);
+            if (HAS_H) {
+                const float2 sl = BROKEN ? make_float2(ell.x < 0.f ? n1 : n2, ell.y < 0.f ? n1 : n2) : dup2(n1);
+                const float2 ex = __ffma2_rn(sl, ell, P[C]);
+                eh = __fmul2_rn(dup2(Af), make_float2(ex2_approx(ex.x), ex2_approx(ex.y)));
+            }
+            // with nr = -r: g / nu = r^2 - r = nr^2 + nr, and the forward sum collects nr
+            float2 fwn, To, Tt, Hs, prod, qn[C], S[C];
+#pragma unroll
+            for (int c = 0; c < C; ++c) {
+                const float2 go = F[3 + c], gt = F[6 + c];
+                const float2 E = make_float2(ex2_approx(P[c].x), ex2_approx(P[c].y));
+                const float2 N = __ffma2_rn(dup2(ao2), go, __fmul2_rn(dup2(at2), gt));
+                const float2 Eh = HAS_H ? __fmul2_rn(eh, F[9 + c]) : make_float2(0.f, 0.f);
+                const float2 Sc = HAS_H ? __ffma2_rn(E, N, Eh) : __fmul2_rn(E, N);
+                const float2 nr = make_float2(rcp_approx(-Sc.x), rcp_approx(-Sc.y));
+                const float2 gp = __ffma2_rn(nr, nr, nr);
+                const float2 gE = __fmul2_rn(gp, E);
+                S[c] = Sc;
+                if (c == 0) {
+                    fwn = nr;
+                    prod = Sc;
+                    To = __fmul2_rn(gE, go);
+                    Tt = __fmul2_rn(gE, gt);
+                    if (HAS_H) Hs = __fmul2_rn(gp, Eh);
+                } else {
+                    fwn = __fadd2_rn(fwn, nr);
+                    prod = __fmul2_rn(prod, Sc);
+                    To = __ffma2_rn(gE, go, To);
+                    Tt = __ffma2_rn(gE, gt, Tt);
+                    if (HAS_H) Hs = __ffma2_rn(gp, Eh, Hs);
+                }
+                qn[c] = __fmul2_rn(gE, N);
+            }
+            // sum_c ln S_c from one log2 of each bin's channel product (per channel outside a safe
+            // range, behind a warp vote so that the rare form stays a real branch)
+            const bool pok = prod.x > 1e-30f && prod.x < 1e30f && prod.y > 1e-30f && prod.y < 1e30f;
+            float2 lg;
+            if (__all_sync(__activemask(), pok) || pok) {
+                lg = make_float2(lg2_approx(prod.x), lg2_approx(prod.y));
+            } else {
+                lg = make_float2(0.f, 0.f);
+#pragma unroll
+                for (int c = 0; c < C; ++c) {
+                    lg.x += lg2_approx(S[c].x);
+                    lg.y += lg2_approx(S[c].y);
+                }
+            }
+            // forward term: sum_c r + sum_c ln S_c - C
+            const float2 fwd = __ffma2_rn(fwn, m1, __ffma2_rn(dup2((float)kLn2), lg, dup2(-(float)C)));
+            cs[0] = __ffma2_rn(nu, fwd, cs[0]);
+            cs[1] = __ffma2_rn(nu, To, cs[1]);
+            cs[2] = __ffma2_rn(nu, Tt, cs[2]);
+            float2 q[NSP];
+#pragma unroll
+            for (int c = 0; c < C; ++c) q[c] = __fmul2_rn(nu, qn[c]);
+            if (HAS_H) {
+                const float2 Hb = __fmul2_rn(nu, Hs);
+                cs[3] = __fadd2_rn(cs[3], Hb);
+                if (BROKEN) {
+                    // ell at and above the break to n2's sum, below it to n1's
+                    const float2 e5 = make_float2(ell.x >= 0.f ? ell.x : 0.f, ell.y >= 0.f ? ell.y : 0.f);
+                    const float2 e4 = make_float2(ell.x >= 0.f ? 0.f : ell.x, ell.y >= 0.f ? 0.f : ell.y);
+                    cs[4] = __ffma2_rn(e4, Hb, cs[4]);
+                    cs[5] = __ffma2_rn(e5, Hb, cs[5]);
+                } else {
+                    cs[4] = __ffma2_rn(ell, Hb, cs[4]);
+                }
+                q[C] = Hb;
+            }
+#pragma unroll
+            for (int a = 0; a < NSP; ++a) {
+                const float2 t = tl[a], qt = __fmul2_rn(q[a], t), qt2 = __fmul2_rn(qt, t);
+                cm[a][0] = __fadd2_rn(cm[a][0], q[a]);
+                cm[a][1] = __fadd2_rn(cm[a][1], qt);
+                cm[a][2] = __fadd2_rn(cm[a][2], qt2);
+                cm[a][3] = __ffma2_rn(qt2, t, cm[a][3]);
+            }
+        };
+        // the range's bins two at a time, in chunks of kAdjStagePairs pair blocks that the warp's
+        // active lanes stage into shared memory (cp.async, the next chunk in flight while the
+        // current one is read): one vote over the lanes per chunk decides whether any spline of any
+        // lane can pass a knot inside it (its last bin at or past an interval's right end);
+        // knot-free chunks run packed without checks.  The chunk sums go to the running sums every
+        // 64 bins.
         const float4* tb4 = reinterpret_cast<const float4*>(tb);
         const float2* xl2 = reinterpret_cast<const float2*>(xlo32 + b0);
-        auto pairs = [&](int p0, int p1, auto check) {
-            for (int ip = p0; ip < p1; ++ip) {
-                float4 q4[kPairRec / 4];
-#pragma unroll
-                for (int k = 0; k < kPairRec / 4; ++k) q4[k] = __ldg(tb4 + ip * (kPairRec / 4) + k);
-                const float2 xl = __ldg(xl2 + ip);
-                const float* fq = reinterpret_cast<const float*>(q4);
-                float f0[kRec], f1[kRec];
-#pragma unroll
-                for (int k = 0; k < kRec; ++k) {
-                    f0[k] = fq[2 * k];
-                    f1[k] = fq[2 * k + 1];
-                }
-                bin(f0, xl.x, check);
-                bin(f1, xl.y, check);
-            }
-        };
-        constexpr int kChunkPairs = 32;
+        const int rank = __popc(amask & ((1u << lane) - 1u)), nact = __popc(amask);
         const int npair = nb >> 1;
-        for (int p0 = 0; p0 < npair; p0 += kChunkPairs) {
-            const int p1 = min(p0 + kChunkPairs, npair);
-            const float xlast = fld(tb, 2 * p1 - 1, 0);
+        const int nch = (npair + kAdjStagePairs - 1) / kAdjStagePairs;
+        auto stage = [&](int c) {
+            const int q0 = c * kAdjStagePairs, nq = min(kAdjStagePairs, npair - q0);
+            const float4* src = tb4 + (size_t)q0 * (kPairRec / 4);
+            float4* dst = reinterpret_cast<float4*>(s_tab[wid][c & 1]);
+            for (int k = rank; k < nq * (kPairRec / 4); k += nact) cp_async16(dst + k, src + k);
+            for (int k = rank; k < nq; k += nact) cp_async8(&s_xl[wid][c & 1][k], xl2 + q0 + k);
+            cp_async_commit();
+        };
+        stage(0);
+        for (int c = 0; c < nch; ++c) {
+            // chunk c + 1 goes into the buffer that chunk c - 1 used (released by the warp sync at
+            // the end of the previous iteration)
+            if (c + 1 < nch) {
+                stage(c + 1);
+                cp_async_wait<1>();
+            } else {
+                cp_async_wait<0>();
+            }
+            __syncwarp(amask);
+            const float* T = s_tab[wid][c & 1];
+            const float2* XL = s_xl[wid][c & 1];
+            const int np = min(kAdjStagePairs, npair - c * kAdjStagePairs);
+            const float xlast = T[(np - 1) * kPairRec + 1];   // x of the chunk's last bin
             bool cross = false;
 #pragma unroll
             for (int a = 0; a < NSP; ++a) cross |= !(xlast < iv[a].xr);
-            if (__any_sync(amask, cross))
-                pairs(p0, p1, std::true_type{});
-            else
-                pairs(p0, p1, std::false_type{});
-            flush_all();
+            if (__any_sync(amask, cross)) {
+                for (int ip = 0; ip < np; ++ip) {
+                    float4 q4[kPairRec / 4];
+#pragma unroll
+                    for (int k = 0; k < kPairRec / 4; ++k) q4[k] = reinterpret_cast<const float4*>(T)[ip * (kPairRec / 4) + k];
+                    const float2 xl = XL[ip];
+                    const float2* F = reinterpret_cast<const float2*>(q4);
+                    bool split = false;
+#pragma unroll
+                    for (int a = 0; a < NSP; ++a) {
+                        advance(a, F[0].x);
+                        split |= !(F[0].y < iv[a].xr);
+                    }
+                    if (split) {
+                        // a knot between the two bins: each on its own intervals
+                        float f0[kRec], f1[kRec];
+#pragma unroll
+                        for (int k = 0; k < kRec; ++k) {
+                            f0[k] = F[k].x;
+                            f1[k] = F[k].y;
+                        }
+                        bin(f0, xl.x);
+#pragma unroll
+                        for (int a = 0; a < NSP; ++a) advance(a, f1[0]);
+                        bin(f1, xl.y);
+                    } else {
+                        pair(F, xl);
+                    }
+                }
+            } else {
+                for (int ip = 0; ip < np; ++ip) {
+                    float4 q4[kPairRec / 4];
+#pragma unroll
+                    for (int k = 0; k < kPairRec / 4; ++k) q4[k] = reinterpret_cast<const float4*>(T)[ip * (kPairRec / 4) + k];
+                    pair(reinterpret_cast<const float2*>(q4), XL[ip]);
+                }
+            }
+            if ((c & 1) || c + 1 == nch) flush_all();
+            __syncwarp(amask);   // the buffer is restaged by the next iteration
         }
 #pragma unroll
         for (int a = 0; a < NSP; ++a) store_mom(a);
@@ -289,8 +450,7 @@ __global__ void __launch_bounds__(128, 4)
 #pragma unroll
         for (int k = 0; k < 6; ++k) {
             const float2 v = s_as[k][tid];
-            const ff r = ff_add(ff{v.x, v.y}, ff{cs[k], 0.f});
-            sc[k] = (double)r.hi + (double)r.lo;
+            sc[k] = (double)v.x + (double)v.y;
         }
     }
 }
