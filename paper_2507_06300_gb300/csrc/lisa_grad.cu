@@ -84,7 +84,7 @@ constexpr int kAdjStagePairs = 16;   // pair blocks per staged chunk of the adjo
 // whose fields of both bins load as register pairs: a pair whose bins share every spline's
 // interval runs on the packed FP32x2 instructions, a pair with a knot between its bins runs as
 // two scalar bins.  Chunk sums are kept per lane of the pair (float2) and go to the float-float
-// running sums (shared memory) as exact two-sums every 64 bins and at interval ends.
+// running sums (shared memory) as exact two-sums every 128 bins and at interval ends.
 template <int C, bool HAS_H, bool BROKEN, bool EXACT_T>
 __global__ void __launch_bounds__(128, 3)
     adjoint_fp32_kernel(const AdjUnit* __restrict__ units, int64_t n_units, const DatasetDev* __restrict__ ds,
@@ -372,7 +372,7 @@ __global__ void __launch_bounds__(128, 3)
         // current one is read): one vote over the lanes per chunk decides whether any spline of any
         // lane can pass a knot inside it (its last bin at or past an interval's right end);
         // knot-free chunks run packed without checks.  The chunk sums go to the running sums every
-        // 64 bins.
+        // 128 bins.
         const float4* tb4 = reinterpret_cast<const float4*>(tb);
         const float2* xl2 = reinterpret_cast<const float2*>(xlo32 + b0);
         const int rank = __popc(amask & ((1u << lane) - 1u)), nact = __popc(amask);
@@ -441,7 +441,7 @@ __global__ void __launch_bounds__(128, 3)
                     pair(reinterpret_cast<const float2*>(q4), XL[ip]);
                 }
             }
-            if ((c & 1) || c + 1 == nch) flush_all();
+            if ((c & 3) == 3 || c + 1 == nch) flush_all();
             __syncwarp(amask);   // the buffer is restaged by the next iteration
         }
 #pragma unroll
