@@ -689,8 +689,8 @@ __global__ void __launch_bounds__(128)
     const int per_spline = 2 * kmax + 2;
     for (int a = 0; a < nsp; ++a) {
         const int64_t sp = (int64_t)s * nsp + a;
-        spl::WarpSpline W;
-        spl::warp_build_spline(W, kx + sp * kmax, kw + sp * (kmax + 2), count[sp], kmax, kind, D.x_lo, D.x_hi,
+        spl::WarpSpline<double> W;
+        spl::warp_build_spline<double>(W, kx + sp * kmax, kw + sp * (kmax + 2), count[sp], kmax, kind, D.x_lo, D.x_hi,
                                sX[warp], sY[warp]);
         if (W.st) continue;
         const int K = W.K;

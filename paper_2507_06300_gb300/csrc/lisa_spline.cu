@@ -3,19 +3,23 @@
 // warp-level construction of lisa_spline_dev.cuh and writes the interval records.
 #include "lisa_spline_dev.cuh"
 
+#include <type_traits>
+
 namespace lisa {
 namespace {
 
-// One CTA per state, one warp per spline.  The spline is built in FP64 for both output precisions:
-//  kF32 = false: FP64 records {xl, xr, a, b, c, d} about the left knot (the plain path);
-//  kF32 = true:  FP32 records about the interval midpoint xo, coefficients scaled to log2 units
-//                as hi floats, plus the interval's conditioning bound T; a state with any
-//                T > kRobustT is appended to the route list (compensated kernel).  The lo floats
-//                of the coefficients (FP64 value - hi) are formed only for the intervals handled
-//                in the same pass (intervals 0-31, 32-63) as an ill-conditioned one, the only
-//                ones that read them, and are zero elsewhere.
-// The kernel is bound by the FP64 pipe; 7 CTAs per SM (at most 72 registers) keep 1,064 states
-// resident at once.
+// One CTA per state, one warp per spline.
+//  kF32 = false: built in FP64; FP64 records {xl, xr, a, b, c, d} about the left knot (the plain
+//                path);
+//  kF32 = true:  built in float-float on the FP32 pipe (FP64 only for the inputs' validation,
+//                sort and differences); FP32 records about the interval midpoint xo,
+//                coefficients scaled to log2 units as hi floats, plus the interval's
+//                conditioning bound T; a state with any T > kRobustT is appended to the route
+//                list (compensated kernel).  The lo floats of the coefficients (float-float value
+//                - hi) are kept only for the intervals handled in the same pass (intervals 0-31,
+//                32-63) as an ill-conditioned one, the only ones that read them, and are zero
+//                elsewhere.
+// 7 CTAs per SM (at most 72 registers) keep 1,064 states resident at once.
 // kMaxSp: splines per state the launch allows (4 for the diagonal covariance, 8 for the full one,
 // which has seven); do_route = 0 leaves the routing bit unset (the full-covariance FP32 kernel
 // evaluates ill-conditioned intervals itself).
@@ -44,21 +48,23 @@ __global__ void __launch_bounds__(32 * kMaxSp, kMaxSp == 4 ? 7 : 3) spline_setup
     {
         const int a = warp;   // blockDim.x = 32 * nsp
         const int64_t sp = (int64_t)s * nsp + a;
-        spl::WarpSpline W;
-        spl::warp_build_spline(W, kx + sp * kmax, kw + sp * (kmax + 2), count[sp], kmax, kind, xlo, xhi, sX[warp],
-                               sY[warp]);
+        // the FP32 path's records are built in float-float (FP32 pipe), the FP64 path's in FP64
+        using BT = typename std::conditional<kF32, spl::F2, double>::type;
+        spl::WarpSpline<BT> W;
+        spl::warp_build_spline<BT>(W, kx + sp * kmax, kw + sp * (kmax + 2), count[sp], kmax, kind, xlo, xhi, sX[warp],
+                                   sY[warp]);
         const int st = W.st;
         if (!st) {
             const int K = W.K;
-            double xn[2];
+            BT xn[2];
             spl::shift2(W.x[0], W.x[1], 1, xn[0], xn[1]);
             for (int q = 0; q < (K > 32 ? 2 : 1); ++q) {   // warp-uniform
                 const int j = lane + 32 * q;
                 const bool valid = j < K - 1;
                 const bool last = (j + 1 == K - 1);
-                const double* x = W.x;
-                const double *ca = W.ca, *cb = W.cb, *cc = W.cc, *cd = W.cd, *h = W.h;
-                if (!kF32) {
+                const BT* x = W.x;
+                const BT *ca = W.ca, *cb = W.cb, *cc = W.cc, *cd = W.cd, *h = W.h;
+                if constexpr (!kF32) {
                     if (!valid) continue;
                     double* r = static_cast<double*>(rec_v) + (sp * (int64_t)(kmax + 1) + j) * kSplineRec;
                     r[0] = x[q];
@@ -70,20 +76,24 @@ __global__ void __launch_bounds__(32 * kMaxSp, kMaxSp == 4 ? 7 : 3) spline_setup
                     r[6] = 0.0;
                     r[7] = 0.0;
                 } else {
-                    // re-expand about the midpoint and scale to log2 units (every lane computes,
-                    // lanes past the last interval on finite placeholder values, and only valid
-                    // lanes write)
-                    const double hm = 0.5 * h[q];
-                    const double xo = x[q] + hm;
-                    const double c3 = cd[q];
-                    const double c2 = cc[q] + 3.0 * hm * cd[q];
-                    const double c1 = cb[q] + hm * (2.0 * cc[q] + 3.0 * hm * cd[q]);
-                    const double c0 = ca[q] + hm * (cb[q] + hm * (cc[q] + hm * cd[q]));
-                    const double cs[4] = {c0 * kLog2_10, c1 * kLog2_10, c2 * kLog2_10, c3 * kLog2_10};
+                    // re-expand about the midpoint and scale to log2 units in float-float (every
+                    // lane computes, lanes past the last interval on finite placeholder values,
+                    // and only valid lanes write); hi parts are the records' FP32 coefficients,
+                    // lo parts their remainders
+                    using spl::F2;
+                    const F2 hm = h[q] * F2(0.5f);
+                    const F2 xo = x[q] + hm;
+                    const F2 h3d = F2(3) * hm * cd[q];
+                    const F2 c3 = cd[q];
+                    const F2 c2 = cc[q] + h3d;
+                    const F2 c1 = cb[q] + hm * (F2(2) * cc[q] + h3d);
+                    const F2 c0 = ca[q] + hm * (cb[q] + hm * (cc[q] + hm * cd[q]));
+                    const F2 L2(kLog2_10);
+                    const F2 cs[4] = {c0 * L2, c1 * L2, c2 * L2, c3 * L2};
                     float chi[4];
-                    for (int c = 0; c < 4; ++c) chi[c] = (float)cs[c];
-                    const float xo_hi = (float)xo;
-                    const float xl_f = (float)x[q], xr_f = (float)xn[q];
+                    for (int c = 0; c < 4; ++c) chi[c] = cs[c].hi;
+                    const float xo_hi = xo.hi;
+                    const float xl_f = x[q].hi, xr_f = xn[q].hi;
                     // the conditioning bound only steers the routing: FP32 is precise enough (and
                     // keeps these steps off the FP64 pipe, which bounds this kernel)
                     const float lo_x = (j == 0) ? fminf(xbmin_f, xl_f) : xl_f;
@@ -106,10 +116,10 @@ __global__ void __launch_bounds__(32 * kMaxSp, kMaxSp == 4 ? 7 : 3) spline_setup
                     r[1] = xo_hi;
                     r[6] = xl_f;
                     r[7] = Tc;
-                    r[8] = (float)(xo - (double)xo_hi);
+                    r[8] = xo.lo;
                     for (int c = 0; c < 4; ++c) {
                         r[2 + c] = chi[c];
-                        r[9 + c] = any_hard ? (float)(cs[c] - (double)chi[c]) : 0.f;
+                        r[9 + c] = any_hard ? cs[c].lo : 0.f;
                     }
                     r[13] = r[14] = r[15] = 0.f;
                 }

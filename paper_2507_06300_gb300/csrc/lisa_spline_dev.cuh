@@ -6,12 +6,56 @@
 // permutation goes through shared memory.
 #pragma once
 
-#include "lisa_internal.cuh"
+#include "lisa_math.cuh"
 
 namespace lisa {
 namespace spl {
 
 constexpr unsigned kFull = 0xffffffffu;
+
+// A float-float value (hi + lo, |lo| <= ulp(hi) / 2, about 48 significant bits) with the
+// arithmetic the spline construction needs, so that the FP32 path's setup runs on the FP32 pipe.
+// Sums use the accurate float-float addition (both parts two-summed), products and quotients
+// one correction step each (Dekker's method); relative error a few times 2^-46 per operation.
+struct F2 {
+    float hi, lo;
+    __device__ F2() : hi(0.f), lo(0.f) {}
+    __device__ F2(float h, float l) : hi(h), lo(l) {}
+    __device__ F2(int v) : hi((float)v), lo(0.f) {}
+    __device__ F2(float v) : hi(v), lo(0.f) {}
+    // the nearest float-float to a double (exact for doubles of at most 48 significant bits)
+    __device__ explicit F2(double v) : hi((float)v), lo((float)(v - (double)(float)v)) {}
+};
+__device__ __forceinline__ F2 operator-(F2 a) { return F2(-a.hi, -a.lo); }
+__device__ __forceinline__ F2 operator+(F2 a, F2 b) {
+    const dm::ff s = dm::two_sum(a.hi, b.hi);
+    const dm::ff t = dm::two_sum(a.lo, b.lo);
+    dm::ff u = dm::fast_two_sum(s.hi, s.lo + t.hi);
+    u = dm::fast_two_sum(u.hi, u.lo + t.lo);
+    return F2(u.hi, u.lo);
+}
+__device__ __forceinline__ F2 operator-(F2 a, F2 b) { return a + (-b); }
+__device__ __forceinline__ F2 operator*(F2 a, F2 b) {
+    const dm::ff p = dm::ff_mul(dm::ff{a.hi, a.lo}, dm::ff{b.hi, b.lo});
+    return F2(p.hi, p.lo);
+}
+__device__ __forceinline__ F2 operator/(F2 a, F2 b) {
+    const float q1 = a.hi / b.hi;
+    const F2 r = a - b * F2(q1);
+    const float q2 = r.hi / b.hi;
+    const dm::ff q = dm::fast_two_sum(q1, q2);
+    return F2(q.hi, q.lo);
+}
+__device__ __forceinline__ F2& operator+=(F2& a, F2 b) { return a = a + b; }
+__device__ __forceinline__ F2& operator-=(F2& a, F2 b) { return a = a - b; }
+__device__ __forceinline__ bool operator==(F2 a, F2 b) { return a.hi == b.hi && a.lo == b.lo; }
+__device__ __forceinline__ F2 fabs(F2 a) { return a.hi < 0.f || (a.hi == 0.f && a.lo < 0.f) ? -a : a; }
+__device__ __forceinline__ double fabs(double v) { return ::fabs(v); }   // (not hidden by the above)
+
+__device__ __forceinline__ double shfl(double v, int src) { return __shfl_sync(kFull, v, src); }
+__device__ __forceinline__ F2 shfl(F2 v, int src) {
+    return F2(__shfl_sync(kFull, v.hi, src), __shfl_sync(kFull, v.lo, src));
+}
 
 // Values of the entries e + d for the entries e = lane (slot 0) and e = lane + 32 (slot 1),
 // |d| <= 32.  Entries outside the array come back as unspecified values; callers mask them.
@@ -19,8 +63,8 @@ template <class T>
 __device__ __forceinline__ void shift2(T v0, T v1, int d, T& o0, T& o1) {
     const int lane = threadIdx.x & 31;
     const int src = (lane + d) & 31;
-    T a = __shfl_sync(kFull, v0, src);
-    T b = __shfl_sync(kFull, v1, src);
+    T a = shfl(v0, src);
+    T b = shfl(v1, src);
     const int q = (lane + d) >> 5;   // floor((lane + d) / 32)
     o0 = (q == 0) ? a : b;
     o1 = (q == -1) ? a : b;
@@ -28,7 +72,7 @@ __device__ __forceinline__ void shift2(T v0, T v1, int d, T& o0, T& o1) {
 
 template <class T>
 __device__ __forceinline__ T bcast(T v0, T v1, int e) {
-    return __shfl_sync(kFull, e < 32 ? v0 : v1, e & 31);
+    return shfl(e < 32 ? v0 : v1, e & 31);
 }
 
 // Parallel cyclic reduction of a tridiagonal system held in the two-slot lane layout (rows
@@ -94,26 +138,30 @@ __device__ __forceinline__ T akima_slope(int j, int K, T mm2, T mm1, T m0, T mp1
     return (wl * ml + wr * mr) / den;
 }
 
-// One spline, built by a whole warp in FP64.  Per lane, slot q holds knot j = lane + 32 q:
+// One spline, built by a whole warp in T (double, or F2 float-float for the FP32 path's records).
+// Per lane, slot q holds knot j = lane + 32 q:
 //   x, y     sorted knot positions and amplitudes (j < K)
 //   h, m     width and slope of interval j (j < K - 1); ih = 1 / h
 //   d2       Akima slope s_j (kind 0, K >= 4) or natural-cubic second derivative M_j (kind 1)
 //   ca..cd   coefficients of interval j about x_j (log10 units)
 // ra, rb are the sorted positions (1-based, edges excluded) of in-between knots lane, lane+32.
+template <class T>
 struct WarpSpline {
     int K, st;
     int ra, rb;
-    double x[2], y[2], h[2], ih[2], m[2], d2[2];
-    double ca[2], cb[2], cc[2], cd[2];
+    T x[2], y[2], h[2], ih[2], m[2], d2[2];
+    T ca[2], cb[2], cc[2], cd[2];
 };
 
 // Validates the knots of one spline (status bits as in lisa_psd.h) and builds it.  px/pw point
 // at the spline's kmax positions and kmax + 2 amplitudes; sX/sY are 64-entry shared scratch
-// owned by the warp.  Returns with W.st != 0 (and nothing else defined) for invalid knots.
-__device__ __forceinline__ void warp_build_spline(WarpSpline& W, const double* __restrict__ px,
+// owned by the warp.  Returns with W.st != 0 (and nothing else defined) for invalid knots.  The
+// knots' validation and sort, and the interval widths and amplitude steps (differences of the
+// FP64 inputs, exact for close knots), are taken in FP64; the rest of the construction in T.
+template <class T>
+__device__ __forceinline__ void warp_build_spline(WarpSpline<T>& W, const double* __restrict__ px,
                                                   const double* __restrict__ pw, int k, int kmax, int kind,
                                                   double xlo, double xhi, double* sX, double* sY) {
-    using T = double;
     const int lane = threadIdx.x & 31;
     int st = 0;
     if (k < 0 || k > kmax) st = LISA_STATE_BAD_COUNT;
@@ -185,25 +233,30 @@ __device__ __forceinline__ void warp_build_spline(WarpSpline& W, const double* _
     const int j0 = lane, j1 = lane + 32;
     T* x = W.x;
     T* y = W.y;
-    x[0] = j0 < K ? sX[j0] : T(0);
-    y[0] = j0 < K ? sY[j0] : T(0);
-    x[1] = j1 < K ? sX[j1] : T(0);
-    y[1] = j1 < K ? sY[j1] : T(0);
+    double xd[2], yd[2];
+    xd[0] = j0 < K ? sX[j0] : 0.0;
+    yd[0] = j0 < K ? sY[j0] : 0.0;
+    xd[1] = j1 < K ? sX[j1] : 0.0;
+    yd[1] = j1 < K ? sY[j1] : 0.0;
     __syncwarp();  // the caller may reuse sX / sY
-    T xn[2], yn[2];
+    double xn[2], yn[2];
     T* h = W.h;
     T* m = W.m;
-    shift2(x[0], x[1], 1, xn[0], xn[1]);
-    shift2(y[0], y[1], 1, yn[0], yn[1]);
+    shift2(xd[0], xd[1], 1, xn[0], xn[1]);
+    shift2(yd[0], yd[1], 1, yn[0], yn[1]);
     T* ih = W.ih;
+    for (int q = 0; q < 2; ++q) {
+        x[q] = T(xd[q]);
+        y[q] = T(yd[q]);
+    }
     h[1] = ih[1] = T(1);
     m[1] = T(0);
     for (int q = 0; q < (K > 32 ? 2 : 1); ++q) {
         const int j = lane + 32 * q;
         if (j < K - 1) {
-            h[q] = xn[q] - x[q];
+            h[q] = T(xn[q] - xd[q]);
             ih[q] = T(1) / h[q];
-            m[q] = (yn[q] - y[q]) * ih[q];
+            m[q] = T(yn[q] - yd[q]) * ih[q];
         } else {
             h[q] = ih[q] = T(1);
             m[q] = T(0);
