@@ -559,22 +559,22 @@ constexpr int kEpiRanges = 256;   // adjoint ranges whose bounds the epilogue st
 
 // d s_k / d m_{k+delta}, delta = -2..1, for the Akima slope at knot k (Appendix A rules,
 // including the ends), returned in d[0..3] = delta -2, -1, 0, +1.  mm2..mp1 = m_{k-2}..m_{k+1}.
-__device__ __forceinline__ void akima_slope_grad(int k, int K, double mm2, double mm1, double m0, double mp1,
-                                                 double sk, double d[4]) {
-    d[0] = d[1] = d[2] = d[3] = 0.0;
+template <class T>
+__device__ __forceinline__ void akima_slope_grad(int k, int K, T mm2, T mm1, T m0, T mp1, T sk, T d[4]) {
+    d[0] = d[1] = d[2] = d[3] = T(0);
     if (k == 0) {                 // s_0 = (3 m_0 - m_1)/2
-        d[2] = 1.5;
-        d[3] = -0.5;
+        d[2] = T(1.5);
+        d[3] = T(-0.5);
         return;
     }
     if (k == K - 1) {             // s_{K-1} = (3 m_{K-2} - m_{K-3})/2
-        d[1] = 1.5;
-        d[0] = -0.5;
+        d[1] = T(1.5);
+        d[0] = T(-0.5);
         return;
     }
-    auto sgn = [](double v) { return v > 0.0 ? 1.0 : (v < 0.0 ? -1.0 : 0.0); };
-    const double ml = mm1, mr = m0;  // slopes left and right of knot k
-    double wl, wr;
+    auto sgn = [](T v) { return spl::sign_of(v); };
+    const T ml = mm1, mr = m0;  // slopes left and right of knot k
+    T wl, wr;
     if (k == 1) {
         wl = fabs(mp1 - m0);
         wr = fabs(m0 - mm1);
@@ -585,33 +585,33 @@ __device__ __forceinline__ void akima_slope_grad(int k, int K, double mm2, doubl
         wl = fabs(mp1 - m0);
         wr = fabs(mm1 - mm2);
     }
-    const double D = wl + wr;
-    if (D == 0.0) {
-        d[1] = 0.5;
-        d[2] = 0.5;
+    const T D = wl + wr;
+    if (D == T(0)) {
+        d[1] = T(0.5);
+        d[2] = T(0.5);
         return;
     }
-    const double iD = 1.0 / D;
-    const double dwl = (ml - sk) * iD, dwr = (mr - sk) * iD;   // ds/dwl, ds/dwr
+    const T iD = T(1) / D;
+    const T dwl = (ml - sk) * iD, dwr = (mr - sk) * iD;   // ds/dwl, ds/dwr
     d[1] += wl * iD;   // ds/dml
     d[2] += wr * iD;   // ds/dmr
     if (k == 1) {
         // wl = |m_{k+1} - m_k|, wr = |m_k - m_{k-1}|
-        const double a1 = sgn(mp1 - m0), a2 = sgn(m0 - mm1);
+        const T a1 = sgn(mp1 - m0), a2 = sgn(m0 - mm1);
         d[3] += dwl * a1;
         d[2] -= dwl * a1;
         d[2] += dwr * a2;
         d[1] -= dwr * a2;
     } else if (k == K - 2) {
         // wl = |m_k - m_{k-1}|, wr = |m_{k-1} - m_{k-2}|
-        const double a1 = sgn(m0 - mm1), a2 = sgn(mm1 - mm2);
+        const T a1 = sgn(m0 - mm1), a2 = sgn(mm1 - mm2);
         d[2] += dwl * a1;
         d[1] -= dwl * a1;
         d[1] += dwr * a2;
         d[0] -= dwr * a2;
     } else {
         // wl = |m_{k+1} - m_k|, wr = |m_{k-1} - m_{k-2}|
-        const double a1 = sgn(mp1 - m0), a2 = sgn(mm1 - mm2);
+        const T a1 = sgn(mp1 - m0), a2 = sgn(mm1 - mm2);
         d[3] += dwl * a1;
         d[2] -= dwl * a1;
         d[1] += dwr * a2;
@@ -619,7 +619,7 @@ __device__ __forceinline__ void akima_slope_grad(int k, int K, double mm2, doubl
     }
 }
 
-template <int C, bool HAS_H, bool BROKEN>
+template <int C, bool HAS_H, bool BROKEN, class T>
 __global__ void __launch_bounds__(128)
     adjoint_epilogue_kernel(int S, const int32_t* __restrict__ state_ds, const DatasetDev* __restrict__ ds,
                             const int32_t* __restrict__ sstat, const double* __restrict__ theta,
@@ -689,18 +689,22 @@ __global__ void __launch_bounds__(128)
     const int per_spline = 2 * kmax + 2;
     for (int a = 0; a < nsp; ++a) {
         const int64_t sp = (int64_t)s * nsp + a;
-        spl::WarpSpline<double> W;
-        spl::warp_build_spline<double>(W, kx + sp * kmax, kw + sp * (kmax + 2), count[sp], kmax, kind, D.x_lo, D.x_hi,
+        spl::WarpSpline<T> W;
+        spl::warp_build_spline<T>(W, kx + sp * kmax, kw + sp * (kmax + 2), count[sp], kmax, kind, D.x_lo, D.x_hi,
                                sX[warp], sY[warp]);
         if (W.st) continue;
         const int K = W.K;
         const int nint = K - 1;
         const double* row = mom_row(const_cast<double*>(mom), pre, s, a, nsp, kmax, nr);
         // moments of each interval, gathered over the ranges that touched it (fixed order)
-        double M[2][4];
+        double Md[2][4];   // summed in FP64 (the accumulation over ranges)
+        T M[2][4];
         for (int q = 0; q < 2; ++q) {
             const int jj = lane + 32 * q;
-            for (int p = 0; p < 4; ++p) M[q][p] = 0.0;
+            for (int p = 0; p < 4; ++p) {
+                Md[q][p] = 0.0;
+                M[q][p] = T(0);
+            }
             if (jj >= nint) continue;
             double lo_b, hi_b;   // the interval's bounds as the likelihood kernels' walk sees them
             if (fp32) {
@@ -733,124 +737,125 @@ __global__ void __launch_bounds__(128)
                     r1 = lo - 1;
                 }
                 for (int rho = r0; rho <= r1; ++rho)
-                    for (int p = 0; p < 4; ++p) M[q][p] += row[4 * (int64_t)(rho + jj) + p];
+                    for (int p = 0; p < 4; ++p) Md[q][p] += row[4 * (int64_t)(rho + jj) + p];
             } else {
                 for (int rho = 0; rho < nr; ++rho) {
                     double xf, xlb;
                     range_x(rho, xf, xlb);
                     const bool touches = (jj == 0 || xlb >= lo_b) && (jj == nint - 1 || xf < hi_b);
                     if (touches)
-                        for (int p = 0; p < 4; ++p) M[q][p] += row[4 * (int64_t)(rho + jj) + p];
+                        for (int p = 0; p < 4; ++p) Md[q][p] += row[4 * (int64_t)(rho + jj) + p];
                 }
             }
+            for (int p = 0; p < 4; ++p) M[q][p] = T(Md[q][p]);
             if (fp32) {
                 // moments about the FP32 midpoint xo -> about the left knot x_j:  t = u + mo
                 const float* r = static_cast<const float*>(srec_v) + (sp * (int64_t)(kmax + 1) + jj) * kSplineRec32;
-                const double mo = ((double)r[1] + (double)r[8]) - W.x[q];
-                const double C0 = M[q][0], C1 = M[q][1], C2 = M[q][2], C3 = M[q][3];
+                const T mo = spl::from_hilo<T>(r[1], r[8]) - W.x[q];
+                const T C0 = M[q][0], C1 = M[q][1], C2 = M[q][2], C3 = M[q][3];
                 M[q][0] = C0;
                 M[q][1] = C1 + mo * C0;
-                M[q][2] = C2 + mo * (2.0 * C1 + mo * C0);
-                M[q][3] = C3 + mo * (3.0 * C2 + mo * (3.0 * C1 + mo * C0));
+                M[q][2] = C2 + mo * (T(2) * C1 + mo * C0);
+                M[q][3] = C3 + mo * (T(3) * C2 + mo * (T(3) * C1 + mo * C0));
             }
         }
         // ---- reverse through the coefficient map
-        double ybar[2], xbar[2], mbar[2], hbar[2], own[2], nxt[2];
+        T ybar[2], xbar[2], mbar[2], hbar[2], own[2], nxt[2];
         for (int q = 0; q < 2; ++q) {
             const int jj = lane + 32 * q;
             const bool iv = jj < nint;
-            const double h = W.h[q], ih = W.ih[q], ih2 = ih * ih;
-            const double M0 = M[q][0], M1 = M[q][1], M2 = M[q][2], M3 = M[q][3];
-            ybar[q] = iv ? M0 : 0.0;
-            xbar[q] = iv ? -(W.cb[q] * M0 + 2.0 * W.cc[q] * M1 + 3.0 * W.cd[q] * M2) : 0.0;
-            mbar[q] = hbar[q] = own[q] = nxt[q] = 0.0;
+            const T h = W.h[q], ih = W.ih[q], ih2 = ih * ih;
+            const T M0 = M[q][0], M1 = M[q][1], M2 = M[q][2], M3 = M[q][3];
+            ybar[q] = iv ? M0 : T(0);
+            xbar[q] = iv ? -(W.cb[q] * M0 + T(2) * W.cc[q] * M1 + T(3) * W.cd[q] * M2) : T(0);
+            mbar[q] = hbar[q] = own[q] = nxt[q] = T(0);
             if (!iv) continue;
             if (K < 4) {
                 mbar[q] = M1;
             } else if (kind == LISA_SPLINE_NATURAL) {
-                const double Mj = W.d2[q];
-                own[q] = -M1 * h * (1.0 / 3.0) + 0.5 * M2 - M3 * ih * (1.0 / 6.0);   // -> d/dM_j
-                nxt[q] = -M1 * h * (1.0 / 6.0) + M3 * ih * (1.0 / 6.0);                // -> d/dM_{j+1}
+                const T Mj = W.d2[q];
+                own[q] = -M1 * h * T(1.0 / 3.0) + T(0.5) * M2 - M3 * ih * T(1.0 / 6.0);   // -> d/dM_j
+                nxt[q] = -M1 * h * T(1.0 / 6.0) + M3 * ih * T(1.0 / 6.0);                // -> d/dM_{j+1}
                 mbar[q] = M1;
                 (void)Mj;
             } else {
-                own[q] = M1 - 2.0 * M2 * ih + M3 * ih2;               // -> d/ds_j
+                own[q] = M1 - T(2) * M2 * ih + M3 * ih2;               // -> d/ds_j
                 nxt[q] = -M2 * ih + M3 * ih2;                         // -> d/ds_{j+1}
-                mbar[q] = 3.0 * M2 * ih - 2.0 * M3 * ih2;
-                hbar[q] = -(W.cc[q] * M2 + 2.0 * W.cd[q] * M3) * ih;
+                mbar[q] = T(3) * M2 * ih - T(2) * M3 * ih2;
+                hbar[q] = -(W.cc[q] * M2 + T(2) * W.cd[q] * M3) * ih;
             }
         }
         if (K >= 4 && kind == LISA_SPLINE_NATURAL) {
             // b = m - h (2 M_j + M_{j+1}) / 6,  d = (M_{j+1} - M_j) / (6 h): h dependence
-            double Mn[2];
+            T Mn[2];
             spl::shift2(W.d2[0], W.d2[1], 1, Mn[0], Mn[1]);
             for (int q = 0; q < 2; ++q) {
                 const int jj = lane + 32 * q;
-                if (jj < nint) hbar[q] = -M[q][1] * (2.0 * W.d2[q] + Mn[q]) * (1.0 / 6.0) - W.cd[q] * M[q][3] * W.ih[q];
+                if (jj < nint) hbar[q] = -M[q][1] * (T(2) * W.d2[q] + Mn[q]) * T(1.0 / 6.0) - W.cd[q] * M[q][3] * W.ih[q];
             }
             // d/dM_k = own_k + nxt_{k-1}; M_0 and M_{K-1} are fixed
-            double nprev[2], Mbar[2];
+            T nprev[2], Mbar[2];
             spl::shift2(nxt[0], nxt[1], -1, nprev[0], nprev[1]);
-            double A[2], B[2], Cc[2], R[2];
-            double hm[2];
+            T A[2], B[2], Cc[2], R[2];
+            T hm[2];
             spl::shift2(W.h[0], W.h[1], -1, hm[0], hm[1]);
             for (int q = 0; q < 2; ++q) {
                 const int k = lane + 32 * q;
-                Mbar[q] = (k >= 1 && k <= K - 2) ? own[q] + nprev[q] : 0.0;
+                Mbar[q] = (k >= 1 && k <= K - 2) ? own[q] + nprev[q] : T(0);
                 if (k >= 1 && k <= K - 2) {
                     A[q] = hm[q];
-                    B[q] = 2.0 * (hm[q] + W.h[q]);
+                    B[q] = T(2) * (hm[q] + W.h[q]);
                     Cc[q] = W.h[q];
                     R[q] = Mbar[q];
                 } else {
-                    A[q] = 0.0;
-                    B[q] = 1.0;
-                    Cc[q] = 0.0;
-                    R[q] = 0.0;
+                    A[q] = T(0);
+                    B[q] = T(1);
+                    Cc[q] = T(0);
+                    R[q] = T(0);
                 }
             }
             spl::pcr_solve(A, B, Cc, R, K);   // the system is symmetric: lambda = A^-1 Mbar
-            double lam[2], lamn[2], Mnn[2];
+            T lam[2], lamn[2], Mnn[2];
             for (int q = 0; q < 2; ++q) lam[q] = R[q] / B[q];
             spl::shift2(lam[0], lam[1], 1, lamn[0], lamn[1]);
             spl::shift2(Mn[0], Mn[1], 1, Mnn[0], Mnn[1]);
             for (int q = 0; q < 2; ++q) {
                 const int k = lane + 32 * q;
-                const double Mk = W.d2[q];
+                const T Mk = W.d2[q];
                 // r_k = 6 (m_k - m_{k-1}):  mbar_k += 6 lam_k - 6 lam_{k+1}
-                if (k >= 1 && k <= K - 2) mbar[q] += 6.0 * lam[q];
-                if (k + 1 >= 1 && k + 1 <= K - 2) mbar[q] -= 6.0 * lamn[q];
+                if (k >= 1 && k <= K - 2) mbar[q] += T(6) * lam[q];
+                if (k + 1 >= 1 && k + 1 <= K - 2) mbar[q] -= T(6) * lamn[q];
                 // row k:   h_{k-1} M_{k-1} + 2 (h_{k-1} + h_k) M_k + h_k M_{k+1}
                 //   dh_k from row k: 2 M_k + M_{k+1};  from row k+1: M_k + 2 M_{k+1}
-                if (k >= 1 && k <= K - 2) hbar[q] -= lam[q] * (2.0 * Mk + Mn[q]);
-                if (k + 1 >= 1 && k + 1 <= K - 2 && k < nint) hbar[q] -= lamn[q] * (Mk + 2.0 * Mn[q]);
+                if (k >= 1 && k <= K - 2) hbar[q] -= lam[q] * (T(2) * Mk + Mn[q]);
+                if (k + 1 >= 1 && k + 1 <= K - 2 && k < nint) hbar[q] -= lamn[q] * (Mk + T(2) * Mn[q]);
                 (void)Mnn;
             }
         } else if (K >= 4) {
             // Akima: d/ds_k = own_k + nxt_{k-1}, then through the slope rule to the interval slopes
-            double nprev[2], sbar[2];
+            T nprev[2], sbar[2];
             spl::shift2(nxt[0], nxt[1], -1, nprev[0], nprev[1]);
-            double mm1[2], mm2[2], mp1[2];
+            T mm1[2], mm2[2], mp1[2];
             spl::shift2(W.m[0], W.m[1], -1, mm1[0], mm1[1]);
             spl::shift2(W.m[0], W.m[1], -2, mm2[0], mm2[1]);
             spl::shift2(W.m[0], W.m[1], 1, mp1[0], mp1[1]);
-            double c[4][2];   // contribution of knot k to mbar_{k + delta}, delta = -2..1
+            T c[4][2];   // contribution of knot k to mbar_{k + delta}, delta = -2..1
             for (int q = 0; q < 2; ++q) {
                 const int k = lane + 32 * q;
-                sbar[q] = (k < K) ? own[q] + (k >= 1 ? nprev[q] : 0.0) : 0.0;
-                double dd[4] = {0.0, 0.0, 0.0, 0.0};
+                sbar[q] = (k < K) ? own[q] + (k >= 1 ? nprev[q] : T(0)) : T(0);
+                T dd[4] = {T(0), T(0), T(0), T(0)};
                 if (k < K) akima_slope_grad(k, K, mm2[q], mm1[q], W.m[q], mp1[q], W.d2[q], dd);
                 for (int t = 0; t < 4; ++t) c[t][q] = sbar[q] * dd[t];
             }
             // mbar_i += c_{i+2}[-2] + c_{i+1}[-1] + c_i[0] + c_{i-1}[+1]
-            double f0[2], f1[2], f3[2];
+            T f0[2], f1[2], f3[2];
             spl::shift2(c[0][0], c[0][1], 2, f0[0], f0[1]);
             spl::shift2(c[1][0], c[1][1], 1, f1[0], f1[1]);
             spl::shift2(c[3][0], c[3][1], -1, f3[0], f3[1]);
             for (int q = 0; q < 2; ++q) {
                 const int i = lane + 32 * q;
                 if (i >= nint) continue;
-                double add = c[2][q];
+                T add = c[2][q];
                 if (i + 2 < K) add += f0[q];
                 if (i + 1 < K) add += f1[q];
                 if (i >= 1) add += f3[q];
@@ -858,42 +863,42 @@ __global__ void __launch_bounds__(128)
             }
         }
         // m_j = (y_{j+1} - y_j) / h_j ;  h_j = x_{j+1} - x_j
-        double gmy[2], gmyp[2], ghp[2];
+        T gmy[2], gmyp[2], ghp[2];
         for (int q = 0; q < 2; ++q) {
             const int jj = lane + 32 * q;
-            gmy[q] = (jj < nint) ? mbar[q] * W.ih[q] : 0.0;
+            gmy[q] = (jj < nint) ? mbar[q] * W.ih[q] : T(0);
             if (jj < nint) hbar[q] -= W.m[q] * gmy[q];
-            else hbar[q] = 0.0;
+            else hbar[q] = T(0);
         }
         spl::shift2(gmy[0], gmy[1], -1, gmyp[0], gmyp[1]);
         spl::shift2(hbar[0], hbar[1], -1, ghp[0], ghp[1]);
         for (int q = 0; q < 2; ++q) {
             const int k = lane + 32 * q;
             if (k >= K) {
-                ybar[q] = xbar[q] = 0.0;
+                ybar[q] = xbar[q] = T(0);
                 continue;
             }
-            ybar[q] += -gmy[q] + (k >= 1 ? gmyp[q] : 0.0);
-            xbar[q] += -hbar[q] + (k >= 1 ? ghp[q] : 0.0);
+            ybar[q] += -gmy[q] + (k >= 1 ? gmyp[q] : T(0));
+            xbar[q] += -hbar[q] + (k >= 1 ? ghp[q] : T(0));
         }
         // scatter: sorted knot k -> caller slots
         double* ga = gs + LISA_N_THETA + a * per_spline;
-        const double y0 = spl::bcast(ybar[0], ybar[1], 0);
-        const double yK = spl::bcast(ybar[0], ybar[1], K - 1);
+        const T y0 = spl::bcast(ybar[0], ybar[1], 0);
+        const T yK = spl::bcast(ybar[0], ybar[1], K - 1);
         if (lane == 0) {
-            ga[0] = y0;
-            ga[kmax + 1] = yK;
+            ga[0] = spl::to_double(y0);
+            ga[kmax + 1] = spl::to_double(yK);
         }
         const int k_in = K - 2;
         for (int half = 0; half < 2; ++half) {
             const int i = lane + 32 * half;          // caller's in-between knot index
             const int r = half ? W.rb : W.ra;        // its sorted position (1..K-2)
             const int rs = (i < k_in) ? r : 0;
-            const double gy = __shfl_sync(kFullMask, rs < 32 ? ybar[0] : ybar[1], rs & 31);
-            const double gx = __shfl_sync(kFullMask, rs < 32 ? xbar[0] : xbar[1], rs & 31);
+            const T gy = spl::shfl(rs < 32 ? ybar[0] : ybar[1], rs & 31);
+            const T gx = spl::shfl(rs < 32 ? xbar[0] : xbar[1], rs & 31);
             if (i < k_in) {
-                ga[1 + i] = gy;
-                ga[kmax + 2 + i] = gx;
+                ga[1 + i] = spl::to_double(gy);
+                ga[kmax + 2 + i] = spl::to_double(gx);
             }
         }
     }
@@ -939,7 +944,7 @@ cudaError_t launch_adjoint(const lisa_data* d, bool fp32, const lisa_params* par
     prof_mark(d, prof, 1, sm);
     prof_mark(d, prof, 2, sm);
     const unsigned eb = (unsigned)((d->n_states + 3) / 4);
-    adjoint_epilogue_kernel<C, H, B><<<eb, 128, 0, sm>>>(
+    (fp32 ? adjoint_epilogue_kernel<C, H, B, spl::F2> : adjoint_epilogue_kernel<C, H, B, double>)<<<eb, 128, 0, sm>>>(
         (int)d->n_states, d->d_state_ds, d->d_ds, sstat, params->theta_dev, kn->count_dev, kn->x_dev, kn->w_dev,
         kn->kmax, kn->kind, d->nsp, d->d_adj_prefix, scal, mom, d->d_rec32, d->d_rec64, srec, fp32 ? 1 : 0, out,
         grad);

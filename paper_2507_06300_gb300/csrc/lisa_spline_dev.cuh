@@ -52,6 +52,24 @@ __device__ __forceinline__ bool operator==(F2 a, F2 b) { return a.hi == b.hi && 
 __device__ __forceinline__ F2 fabs(F2 a) { return a.hi < 0.f || (a.hi == 0.f && a.lo < 0.f) ? -a : a; }
 __device__ __forceinline__ double fabs(double v) { return ::fabs(v); }   // (not hidden by the above)
 
+__device__ __forceinline__ double to_double(double v) { return v; }
+__device__ __forceinline__ double to_double(F2 v) { return (double)v.hi + (double)v.lo; }
+__device__ __forceinline__ double sign_of(double v) { return v > 0.0 ? 1.0 : (v < 0.0 ? -1.0 : 0.0); }
+__device__ __forceinline__ F2 sign_of(F2 v) {
+    const float h = v.hi != 0.f ? v.hi : v.lo;
+    return F2(h > 0.f ? 1.f : (h < 0.f ? -1.f : 0.f));
+}
+// a value given as float hi + lo parts
+template <class T>
+__device__ __forceinline__ T from_hilo(float hi, float lo);
+template <>
+__device__ __forceinline__ double from_hilo<double>(float hi, float lo) { return (double)hi + (double)lo; }
+template <>
+__device__ __forceinline__ F2 from_hilo<F2>(float hi, float lo) {
+    const dm::ff v = dm::two_sum(hi, lo);
+    return F2(v.hi, v.lo);
+}
+
 __device__ __forceinline__ double shfl(double v, int src) { return __shfl_sync(kFull, v, src); }
 __device__ __forceinline__ F2 shfl(F2 v, int src) {
     return F2(__shfl_sync(kFull, v.hi, src), __shfl_sync(kFull, v.lo, src));
