@@ -351,6 +351,7 @@ const char* lisa_status_string(lisa_status s) {
 }
 
 lisa_status lisa_data_create(const lisa_data_desc* desc, lisa_stream_t stream, lisa_data** out) {
+    lisa::NvtxRange nvtx_range("lisa_data_create");
     if (!desc || !out) return LISA_ERR_NULL;
     *out = nullptr;
     const lisa_data_desc& q = *desc;

@@ -973,6 +973,7 @@ using namespace lisa;
 extern "C" lisa_status lisa_psd_loglike_grad(const lisa_data* d, const lisa_params* params, const lisa_knots* kn,
                                              const void* buf, size_t buf_bytes, double* out, double* grad,
                                              void* ws, size_t ws_bytes, lisa_precision prec, lisa_stream_t stream) {
+    lisa::NvtxRange nvtx_range("lisa_psd_loglike_grad");
     if (!d || !params || !kn || !buf || !out || !grad || !ws) return LISA_ERR_NULL;
     if (prec != LISA_FP32 && prec != LISA_FP64) return LISA_ERR_VALUE;
     if (d->cov != LISA_COV_DIAGONAL) return LISA_ERR_VALUE;   // the adjoint covers the diagonal model

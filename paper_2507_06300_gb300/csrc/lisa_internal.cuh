@@ -8,7 +8,19 @@
 
 #include "lisa_psd.h"
 
+#include <nvtx3/nvToolsExt.h>
+
 namespace lisa {
+
+// An NVTX range over one library call (host side: the range marks the call's launches, which the
+// profiler correlates with the kernels); without a profiler attached a push/pop costs nothing
+// beyond a null check.
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 constexpr double kPi = 3.141592653589793238462643;
 constexpr double kArm = 2.5e9;                            // arm length L, m (Sec. II.A)

@@ -1267,6 +1267,7 @@ size_t lisa_workspace_bytes(const lisa_data* d, int32_t kmax, lisa_precision p, 
 lisa_status lisa_psd_loglike(const lisa_data* d, const lisa_params* params, const void* buf, size_t buf_bytes,
                              int32_t kmax, double* out, void* ws, size_t ws_bytes, lisa_precision prec,
                              lisa_stream_t stream) {
+    lisa::NvtxRange nvtx_range("lisa_psd_loglike");
     if (!d || !params || !buf || !out || !ws) return LISA_ERR_NULL;
     if (prec != LISA_FP32 && prec != LISA_FP64) return LISA_ERR_VALUE;
     if (kmax < 0 || kmax > LISA_MAX_KNOTS) return LISA_ERR_VALUE;
@@ -1354,6 +1355,7 @@ lisa_status lisa_data_kernel_ms(const lisa_data* d, float* ms) {
 
 lisa_status lisa_model_psd(const lisa_data* d, const lisa_params* params, const void* buf, size_t buf_bytes,
                            int32_t kmax, double* out, lisa_stream_t stream) {
+    lisa::NvtxRange nvtx_range("lisa_model_psd");
     if (!d || !params || !buf || !out) return LISA_ERR_NULL;
     if (kmax < 0 || kmax > LISA_MAX_KNOTS) return LISA_ERR_VALUE;
     if (params->n_states != d->n_states) return LISA_ERR_SHAPE;
@@ -1391,6 +1393,7 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[LISA_NOALLOC_SC
 extern "C" lisa_status lisa_psd_loglike_noalloc(const lisa_data* d, const lisa_params* params, const void* buf,
                                                 size_t buf_bytes, int32_t kmax, double* out, lisa_precision prec,
                                                 lisa_stream_t stream) {
+    lisa::NvtxRange nvtx_range("lisa_psd_loglike_noalloc");
     if (!d || !params || !buf || !out) return LISA_ERR_NULL;
     if (ws_fwd_bytes(d) > (size_t)LISA_NOALLOC_SCRATCH_BYTES) return LISA_ERR_WORKSPACE;
     // the array exists once per device: use the copy on the device that holds the data object

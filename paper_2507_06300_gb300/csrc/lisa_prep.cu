@@ -90,6 +90,7 @@ using namespace lisa;
 
 extern "C" lisa_status lisa_fd_synthesize(const double* psd, const double* normal, int32_t n_channels, int64_t n_freq,
                                           double* d, lisa_stream_t stream) {
+    lisa::NvtxRange nvtx_range("lisa_fd_synthesize");
     if (n_channels < 1 || n_freq < 0) return LISA_ERR_VALUE;
     if (n_freq == 0) return LISA_SUCCESS;
     if (!psd || !normal || !d) return LISA_ERR_NULL;
@@ -107,6 +108,7 @@ extern "C" lisa_status lisa_fd_synthesize(const double* psd, const double* norma
 extern "C" lisa_status lisa_averaged_periodogram(const double* d, int32_t n_channels, int64_t n_freq, double f0,
                                                  double df, const int64_t* off, int64_t n_bins, double* P, double* f,
                                                  double* nu, lisa_stream_t stream) {
+    lisa::NvtxRange nvtx_range("lisa_averaged_periodogram");
     if (n_channels < 1 || n_channels > 3 || n_freq < 0 || n_bins < 0 || !(df > 0.0) || !std::isfinite(f0))
         return LISA_ERR_VALUE;
     if (n_bins == 0) return LISA_SUCCESS;

@@ -178,6 +178,7 @@ using namespace lisa;
 extern "C" lisa_status lisa_spline_setup(const lisa_data* d, const lisa_knots* kn, lisa_precision prec,
                                          void* buf, size_t bytes, int32_t* status_out,
                                          lisa_stream_t stream) {
+    lisa::NvtxRange nvtx_range("lisa_spline_setup");
     if (!d || !kn || !buf) return LISA_ERR_NULL;
     if (prec != LISA_FP32 && prec != LISA_FP64) return LISA_ERR_VALUE;
     if (kn->kmax < 0 || kn->kmax > LISA_MAX_KNOTS || (kn->kind != LISA_SPLINE_AKIMA && kn->kind != LISA_SPLINE_NATURAL))
