@@ -540,24 +540,28 @@ void lo_loglike_grad_scaled(int C, int sgwb_model, int tdi_form, int64_t N, cons
                     if (!(Sc > 0.0) || !std::isfinite(Sc)) st |= 32;
                     double Pc = P[(size_t)c * N + i];
                     bin += Pc / Sc + std::log(Sc);
-                    double g = nu[i] * (Pc - Sc) / (Sc * Sc);
-                    g_aoms += g * 2.0 * th[0] * u_o[c] * En;
-                    g_atm += g * 2.0 * th[1] * u_t[c] * En;
-                    sc_aoms += std::fabs(g * 2.0 * th[0] * u_o[c] * En);
-                    sc_atm += std::fabs(g * 2.0 * th[1] * u_t[c] * En);
-                    q[(size_t)c * N + i] = g * kLn10 * bm.sn[c] * En;
+                    // d(bin term)/dS = -nu (P - S) / S^2, applied to each dS/dparameter X as
+                    // w (X / S) with w = nu (P - S) / S (the same product; S^2 itself, which
+                    // overflows for S beyond 1e154, is never formed)
+                    double w = nu[i] * (Pc - Sc) / Sc;
+                    double rn = En / Sc;
+                    g_aoms += w * 2.0 * th[0] * u_o[c] * rn;
+                    g_atm += w * 2.0 * th[1] * u_t[c] * rn;
+                    sc_aoms += std::fabs(w * 2.0 * th[0] * u_o[c] * rn);
+                    sc_atm += std::fabs(w * 2.0 * th[1] * u_t[c] * rn);
+                    q[(size_t)c * N + i] = w * kLn10 * bm.sn[c] * rn;
                     if (pb.sgwb_model) {
-                        double shp = bm.sh[c] * Eh;
-                        g_lA += g * kLn10 * shp;
-                        sc_lA += std::fabs(g * kLn10 * shp);
+                        double shs = bm.sh[c] * Eh / Sc;
+                        g_lA += w * kLn10 * shs;
+                        sc_lA += std::fabs(w * kLn10 * shs);
                         if (pb.sgwb_model == 2 && f[i] >= f_ref) {
-                            g_n2 += g * lnf * shp;
-                            sc_n2 += std::fabs(g * lnf * shp);
+                            g_n2 += w * lnf * shs;
+                            sc_n2 += std::fabs(w * lnf * shs);
                         } else {
-                            g_n1 += g * lnf * shp;
-                            sc_n1 += std::fabs(g * lnf * shp);
+                            g_n1 += w * lnf * shs;
+                            sc_n1 += std::fabs(w * lnf * shs);
                         }
-                        qh += g * kLn10 * shp;
+                        qh += w * kLn10 * shs;
                     }
                 }
                 if (pb.sgwb_model) q[(size_t)C * N + i] = qh;

@@ -31,12 +31,24 @@
 
 namespace lisa {
 
-size_t grad_extra_bytes(const lisa_data* d, int kmax) {
-    const size_t scal = align256(sizeof(double) * 6 * (size_t)d->adj_ranges);
-    const size_t mom = align256(sizeof(double) * 4 * (size_t)d->nsp *
-                                ((size_t)d->adj_ranges + (size_t)d->n_states * (size_t)(kmax + 1)));
-    return scal + mom;
+// Gradient workspace (after 256 bytes): range sums scal | moment slots mom, and for the FP32
+// call the FP64 fallback: a flag per state | an FP64 spline buffer (states whose FP32 sums leave
+// the FP32 range are redone in FP64 within the call).
+struct GradLayout {
+    size_t off_scal, off_mom, off_fb, off_buf64, bytes;
+};
+inline GradLayout grad_layout(const lisa_data* d, int kmax, bool fp32) {
+    GradLayout G;
+    G.off_scal = 0;
+    G.off_mom = align256(sizeof(double) * 6 * (size_t)d->adj_ranges);
+    G.off_fb = G.off_mom + align256(sizeof(double) * 4 * (size_t)d->nsp *
+                                    ((size_t)d->adj_ranges + (size_t)d->n_states * (size_t)(kmax + 1)));
+    G.off_buf64 = G.off_fb + (fp32 ? align256(sizeof(int32_t) * (size_t)d->n_states) : 0);
+    G.bytes = G.off_buf64 + (fp32 ? align256(spline_layout(d->n_states, d->nsp, kmax).bytes) : 0);
+    return G;
 }
+
+size_t grad_extra_bytes(const lisa_data* d, int kmax, bool fp32) { return grad_layout(d, kmax, fp32).bytes; }
 
 namespace {
 using namespace dm;
@@ -121,16 +133,26 @@ __global__ void __launch_bounds__(128, 3)
         const int64_t pre = prefix[s];
         const int32_t* nint_s = nint + (int64_t)s * nsp;
         AdjIv iv[NSP] = {};
+        unsigned hm = 0;   // splines whose current interval is ill-conditioned (T > kRobustT)
         auto base = [&](int a) { return srec + ((int64_t)s * nsp + a) * (int64_t)(kmax + 1) * kSplineRec32; };
         auto load = [&](int a) {
             const float* r = base(a) + (size_t)iv[a].j * kSplineRec32;
             iv[a].xr = __ldg(r + 0);
             iv[a].nxo = dup2(-__ldg(r + 1));
-            iv[a].c0 = dup2(__ldg(r + 2));
-            iv[a].c1 = dup2(__ldg(r + 3));
-            iv[a].c2 = dup2(__ldg(r + 4));
-            iv[a].c3 = dup2(__ldg(r + 5));
             iv[a].nxo_lo = dup2(-__ldg(r + 8));
+            if (__ldg(r + 7) <= (float)kRobustT) {
+                iv[a].c0 = dup2(__ldg(r + 2));
+                iv[a].c1 = dup2(__ldg(r + 3));
+                iv[a].c2 = dup2(__ldg(r + 4));
+                iv[a].c3 = dup2(__ldg(r + 5));
+                hm &= ~(1u << a);
+            } else {
+                // ill-conditioned (routed states): the zero cubic keeps the arithmetic benign, and
+                // the thread's bins are masked (nu = 0) while it holds such an interval; the
+                // compensated adjoint adds them
+                iv[a].c0 = iv[a].c1 = iv[a].c2 = iv[a].c3 = make_float2(0.f, 0.f);
+                hm |= 1u << a;
+            }
         };
         {
             const float x0 = fld(tb, 0, 0);
@@ -198,7 +220,7 @@ __global__ void __launch_bounds__(128, 3)
         // low part of x), its sums in the first lane of the pair accumulators; the intervals
         // must already hold the bin
         auto bin = [&](const float* f, float x_lo) {
-            const float x = f[0], ell = f[1], nu = f[2];
+            const float x = f[0], ell = f[1], nu = hm ? 0.f : f[2];
             float P[NSP], tl[NSP];
 #pragma unroll
             for (int a = 0; a < NSP; ++a) {
@@ -270,7 +292,8 @@ __global__ void __launch_bounds__(128, 3)
         // two bins in the same intervals of every spline, on the packed FP32x2 instructions: the
         // table's fields of both bins F[0..11] and the low parts of their x
         auto pair = [&](const float2* F, float2 xl) {
-            const float2 x = F[0], ell = F[1], nu = F[2];
+            const float2 x = F[0], ell = F[1];
+            const float2 nu = hm ? make_float2(0.f, 0.f) : F[2];   // bins of ill-conditioned intervals: masked
             float2 P[NSP], tl[NSP];
 #pragma unroll
             for (int a = 0; a < NSP; ++a) {
@@ -524,12 +547,15 @@ __global__ void __launch_bounds__(128)
                 const double N = ao2 * q[3 + c] + at2 * q[6 + c];
                 const double Eh = HAS_H ? eh * q[9 + c] : 0.0;
                 const double Sc = E * N + Eh;
-                const double g = nu * (1.0 - Sc) / (Sc * Sc);
-                fwd += 1.0 / Sc + log(Sc);
-                To += g * q[3 + c] * E;
-                Tt += g * q[6 + c] * E;
-                H += g * Eh;
-                qv[c] = kLn10 * g * N * E;
+                // g = nu (1 - S) / S^2 applied as nu (r - 1) (r E) with r = 1 / S: no intermediate
+                // overflows where S^2 would (S beyond 1e154)
+                const double r = 1.0 / Sc;
+                const double gr = nu * (r - 1.0), rE = r * E;
+                fwd += r + log(Sc);
+                To += gr * rE * q[3 + c];
+                Tt += gr * rE * q[6 + c];
+                H += gr * (r * Eh);
+                qv[c] = kLn10 * gr * rE * N;
             }
             if (HAS_H) qv[C] = kLn10 * H;
             acc[0] += nu * (fwd - (double)C);
@@ -551,6 +577,338 @@ __global__ void __launch_bounds__(128)
         }
         double* sc = scal + 6 * (pre + U.rho);
         for (int k = 0; k < 6; ++k) sc[k] = acc[k];
+    }
+}
+
+// ---- the FP32 gradient's two per-state passes: one CTA per (state, range) ---------------------
+// Mode kComp: the bins the FP32 adjoint masked (routed states, whose ill-conditioned intervals
+// (conditioning T > kRobustT, prior draws with close knots) it loads as zero cubics): spline values
+// in float-float from the records' hi and lo parts (2^P as ex2(hi) (1 + lo ln2)), per-bin terms in
+// FP32, the moments' products exact (float-float); the sums are added to the slots the FP32
+// adjoint wrote.  Only ranges overlapping the state's ill-conditioned x-extent run.
+// Mode kFallback: the states the FP32 epilogue flagged (their FP32 sums left the FP32 range) in
+// FP64, the per-bin arithmetic of adjoint_fp64_kernel, from FP64 records built for them; the sums
+// overwrite the slots (every interval from the range's first bin to its last).
+// The CTA's warps (4 for kComp, 16 for the FP64 kFallback) split the range's bins, their lanes 32
+// consecutive bins at a time; each spline's moments are reduced over the lanes per interval (a fixed butterfly),
+// kept per warp and interval in shared memory, and summed over the warps in order.
+constexpr int kComp = 0, kFallback = 1;
+
+template <int C, bool HAS_H, bool BROKEN, int MODE>
+__global__ void __launch_bounds__(MODE == kComp ? 128 : 512)
+    adjoint_range_kernel(int S, const int32_t* __restrict__ state_ds, const DatasetDev* __restrict__ ds,
+                         const float* __restrict__ rec32, const float* __restrict__ xlo32,
+                         const double* __restrict__ rec64, const double* __restrict__ theta,
+                         const int32_t* __restrict__ sstat, const int32_t* __restrict__ flag,
+                         const int32_t* __restrict__ nint, const void* __restrict__ srec_v,
+                         const float2* __restrict__ hull, int kmax, int nsp, const int64_t* __restrict__ prefix,
+                         double* __restrict__ scal, double* __restrict__ mom) {
+    constexpr int NSP = C + (HAS_H ? 1 : 0);
+    constexpr int RS = (MODE == kComp) ? kSplineRec32 : kSplineRec;   // record stride
+    // per warp, spline and interval (from the range's first) the 4 moment sums: dynamic shared
+    // memory of nwarps * NSP * (kmax + 1) * 4 doubles
+    extern __shared__ double s_m[];
+    __shared__ double s_t[16][6];
+    __shared__ int s_jl[NSP];               // each spline's interval at the range's last bin
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nwarps = blockDim.x >> 5;     // <= 16
+    const int nsl = kmax + 1;               // interval slots per spline
+    auto sm = [&](int w, int a, int jr, int p) -> double& { return s_m[(((w * NSP) + a) * nsl + jr) * 4 + p]; };
+    const int s = blockIdx.x, rho = blockIdx.y;
+    if (MODE == kComp ? (sstat[s] & (kUserBits | kRouted)) != kRouted : flag[s] == 0) return;   // CTA-uniform
+    const DatasetDev& D = ds[state_ds[s]];
+    if (rho >= D.nranges) return;
+    const int64_t b0 = D.bin0 + (int64_t)rho * kAdjBins;
+    const int nb = (int)min((int64_t)kAdjBins, D.bin0 + D.npad - b0);
+    const float* tb = rec32 + (b0 >> 1) * kPairRec;
+    if (MODE == kComp) {
+        const float2 hx = hull[s];
+        if (fld(tb, nb - 1, 0) < hx.x || fld(tb, 0, 0) >= hx.y) return;   // no ill-conditioned interval here
+    }
+    const double* th = theta + (size_t)s * LISA_N_THETA;
+    const int64_t pre = prefix[s];
+    // the state's parameters: FP32 (kComp, as the FP32 adjoint derives them) and FP64 (kFallback)
+    const float ao2 = (float)(th[0] * th[0]), at2 = (float)(th[1] * th[1]);
+    const float Af = (MODE == kComp && HAS_H) ? (float)exp10(th[2]) : 0.f;
+    const float n1 = (float)th[3], n2 = BROKEN ? (float)th[4] : n1;
+    const double ao2d = th[0] * th[0], at2d = th[1] * th[1], lAd = th[2], n1d = th[3];
+    const double n2d = BROKEN ? th[4] : n1d;
+    // bin i's x as the walk compares it (FP32 for the FP32 records, FP64 for the FP64 ones)
+    auto xbin = [&](int i) -> double { return MODE == kComp ? (double)fld(tb, i, 0) : rec64[(b0 + i) * kRec]; };
+    auto rec = [&](int a, int j) -> const char* {
+        const int64_t sp = (int64_t)s * nsp + a;
+        return static_cast<const char*>(srec_v) + ((sp * (int64_t)(kmax + 1) + j) * RS) *
+                                                      (MODE == kComp ? sizeof(float) : sizeof(double));
+    };
+    auto right_end = [&](int a, int j) -> double {
+        return MODE == kComp ? (double)__ldg(reinterpret_cast<const float*>(rec(a, j)))
+                             : __ldg(reinterpret_cast<const double*>(rec(a, j)) + 1);
+    };
+    auto locate = [&](int a, double x) {
+        const int n = nint[(int64_t)s * nsp + a];
+        int j = 0;
+        while (j < n - 1 && x >= right_end(a, j)) ++j;
+        return j;
+    };
+    int j0[NSP], nin[NSP];
+#pragma unroll
+    for (int a = 0; a < NSP; ++a) {
+        nin[a] = nint[(int64_t)s * nsp + a];
+        j0[a] = locate(a, xbin(0));
+    }
+    for (int e = threadIdx.x; e < nwarps * NSP * nsl * 4; e += blockDim.x) s_m[e] = 0.0;
+    if (threadIdx.x < 16 * 6) (&s_t[0][0])[threadIdx.x] = 0.0;
+    if (threadIdx.x == 0)
+        for (int a = 0; a < NSP; ++a) s_jl[a] = j0[a];
+    __syncthreads();
+    // this warp's bins and its running intervals
+    const int w_lo = (warp * nb) / nwarps, w_hi = ((warp + 1) * nb) / nwarps;
+    int cj[NSP];
+    double am[NSP][4];
+#pragma unroll
+    for (int a = 0; a < NSP; ++a) {
+        cj[a] = w_lo < w_hi ? locate(a, xbin(w_lo)) : j0[a];
+        for (int p = 0; p < 4; ++p) am[a][p] = 0.0;
+    }
+    auto wsum = [&](double v) {
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFullMask, v, o);
+        return v;
+    };
+    // kComp: lane-local float-float running sums of the warp's current intervals (folded into am,
+    // over the lanes, only when an interval is left), and of the template terms
+    ff ls[NSP][4], lt[6];
+#pragma unroll
+    for (int a = 0; a < NSP; ++a)
+        for (int p = 0; p < 4; ++p) ls[a][p] = ff{0.f, 0.f};
+    for (int k = 0; k < 6; ++k) lt[k] = ff{0.f, 0.f};
+    auto flush = [&](int a) {
+        if (MODE == kComp)
+            for (int p = 0; p < 4; ++p) {
+                am[a][p] += wsum((double)ls[a][p].hi + (double)ls[a][p].lo);
+                ls[a][p] = ff{0.f, 0.f};
+            }
+        if (lane == 0)
+            for (int p = 0; p < 4; ++p) sm(warp, a, cj[a] - j0[a], p) = am[a][p];
+        for (int p = 0; p < 4; ++p) am[a][p] = 0.0;
+    };
+    double ts[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    for (int i0 = w_lo; i0 < w_hi; i0 += 32) {
+        const int i = i0 + lane;
+        const bool valid = i < w_hi;
+        const int last_lane = min(31, w_hi - 1 - i0);
+        const int ib = valid ? i : i0;
+        const double x = xbin(ib);
+        int jl[NSP];
+        bool hard = false;
+#pragma unroll
+        for (int a = 0; a < NSP; ++a) {
+            int j = cj[a];
+            while (j < nin[a] - 1 && x >= right_end(a, j)) ++j;
+            jl[a] = j;
+            if (MODE == kComp) hard |= !(__ldg(reinterpret_cast<const float*>(rec(a, j)) + 7) <= (float)kRobustT);
+        }
+        const bool use = valid && (MODE == kFallback || hard);
+        if (!__any_sync(kFullMask, use)) {
+            // nothing in this group: move the running intervals up (their sums so far first)
+#pragma unroll
+            for (int a = 0; a < NSP; ++a) {
+                const int jlo = __shfl_sync(kFullMask, jl[a], 0);
+                if (jlo > cj[a]) {
+                    flush(a);
+                    cj[a] = jlo;
+                }
+            }
+            continue;
+        }
+        double qd[NSP], td[NSP];   // the spline signals and t = x - (expansion point), FP64
+        double tc[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+        for (int a = 0; a < NSP; ++a) qd[a] = td[a] = 0.0;
+        if (use) {
+            if constexpr (MODE == kComp) {
+                const float xf = fld(tb, ib, 0), ell = fld(tb, ib, 1), nu = fld(tb, ib, 2);
+                const float x_lo = __ldg(xlo32 + b0 + ib);
+                float P[NSP], cor[NSP], tl[NSP];
+#pragma unroll
+                for (int a = 0; a < NSP; ++a) {
+                    const float4* rr = reinterpret_cast<const float4*>(rec(a, jl[a]));
+                    const float4 A = __ldg(rr), Bq = __ldg(rr + 1), Cq = __ldg(rr + 2), Dq = __ldg(rr + 3);
+                    const ff tt = two_sum(xf, -A.y);
+                    tl[a] = tt.hi + (tt.lo + (x_lo - Cq.x));   // t = x - x_o as the FP32 adjoint forms it
+                    const ff tf = ff_add(ff{xf, x_lo}, ff{-A.y, -Cq.x});
+                    ff v = {Bq.y, Dq.x};
+                    v = ff_add(ff_mul(v, tf), ff{Bq.x, Cq.w});
+                    v = ff_add(ff_mul(v, tf), ff{A.w, Cq.z});
+                    v = ff_add(ff_mul(v, tf), ff{A.z, Cq.y});
+                    P[a] = v.hi;
+                    cor[a] = fmaf(v.lo, (float)kLn2, 1.f);
+                }
+                float eh = 0.f;
+                if (HAS_H) {
+                    const float sl = BROKEN ? (ell < 0.f ? n1 : n2) : n1;
+                    eh = Af * ex2_approx(fmaf(sl, ell, P[C])) * cor[C];
+                }
+                float lsum = 0.f, rsum = -(float)C, To = 0.f, Tt = 0.f, Hs = 0.f, q[NSP];
+#pragma unroll
+                for (int c = 0; c < C; ++c) {
+                    const float go = fld(tb, ib, 3 + c), gt = fld(tb, ib, 6 + c);
+                    const float E = ex2_approx(P[c]) * cor[c];
+                    const float N = fmaf(ao2, go, at2 * gt);
+                    const float Eh = HAS_H ? eh * fld(tb, ib, 9 + c) : 0.f;
+                    const float Sc = HAS_H ? fmaf(E, N, Eh) : E * N;
+                    const float r = rcp_approx(Sc);
+                    const float gp = fmaf(r, r, -r);
+                    const float gE = gp * E;
+                    rsum += r;
+                    lsum += lg2_approx(Sc);
+                    To = fmaf(gE, go, To);
+                    Tt = fmaf(gE, gt, Tt);
+                    if (HAS_H) Hs = fmaf(gp, Eh, Hs);
+                    q[c] = nu * gE * N;
+                }
+                Hs *= nu;
+                if (HAS_H) q[C] = Hs;
+                float tf[6] = {nu * fmaf((float)kLn2, lsum, rsum), nu * To, nu * Tt, Hs, 0.f, 0.f};
+                if (BROKEN && ell >= 0.f)
+                    tf[5] = ell * Hs;
+                else
+                    tf[4] = ell * Hs;
+                for (int k = 0; k < 6; ++k) lt[k] = ff_add(lt[k], two_sum(tf[k], 0.f));
+#pragma unroll
+                for (int a = 0; a < NSP; ++a) {
+                    qd[a] = q[a];
+                    td[a] = tl[a];
+                }
+            } else {
+                const double* qb = rec64 + (b0 + ib) * kRec;
+                const double ell = qb[1], nu = qb[2];
+                double P[NSP];
+#pragma unroll
+                for (int a = 0; a < NSP; ++a) {
+                    const double* z = reinterpret_cast<const double*>(rec(a, jl[a]));
+                    td[a] = x - z[0];
+                    P[a] = z[2] + td[a] * (z[3] + td[a] * (z[4] + td[a] * z[5]));
+                }
+                double eh = 0.0;
+                if (HAS_H) {
+                    const double sl = BROKEN ? (ell < 0.0 ? n1d : n2d) : n1d;
+                    eh = exp10(lAd + P[C]) * exp2(sl * ell);
+                }
+                double fwd = 0.0, To = 0.0, Tt = 0.0, H = 0.0;
+#pragma unroll
+                for (int c = 0; c < C; ++c) {
+                    const double E = exp10(P[c]);
+                    const double N = ao2d * qb[3 + c] + at2d * qb[6 + c];
+                    const double Eh = HAS_H ? eh * qb[9 + c] : 0.0;
+                    const double Sc = E * N + Eh;
+                    // g = nu (1 - S) / S^2 applied as nu (r - 1) (r E) with r = 1 / S: no
+                    // intermediate overflows where S^2 would (S beyond 1e154)
+                    const double r = 1.0 / Sc;
+                    const double gr = nu * (r - 1.0), rE = r * E;
+                    fwd += r + log(Sc);
+                    To += gr * rE * qb[3 + c];
+                    Tt += gr * rE * qb[6 + c];
+                    H += gr * (r * Eh);
+                    qd[c] = kLn10 * gr * rE * N;
+                }
+                if (HAS_H) qd[C] = kLn10 * H;
+                tc[0] = nu * (fwd - (double)C);
+                tc[1] = To;
+                tc[2] = Tt;
+                tc[3] = H;
+                if (BROKEN && ell >= 0.0)
+                    tc[5] = ell * H;
+                else
+                    tc[4] = ell * H;
+            }
+        }
+        if (MODE == kFallback)
+            for (int k = 0; k < 6; ++k) ts[k] += tc[k];
+        // moments per interval: the lanes' intervals are non-decreasing, from lane 0's to the last
+        // valid lane's
+#pragma unroll
+        for (int a = 0; a < NSP; ++a) {
+            double d[4];
+            if (MODE == kComp) {
+                // exact products q t^p (float-float) of the FP32 values; while every lane stays in
+                // the warp's current interval they go to the lane-local sums
+                const float qf = (float)qd[a], t = (float)td[a], qt = qf * t;
+                const ff p1 = {qt, fmaf(qf, t, -qt)};
+                const ff p2 = ff_mul(p1, ff{t, 0.f});
+                const ff p3 = ff_mul(p2, ff{t, 0.f});
+                if (__all_sync(kFullMask, !use || jl[a] == cj[a])) {
+                    if (use) {
+                        ls[a][0] = ff_add(ls[a][0], ff{qf, 0.f});
+                        ls[a][1] = ff_add(ls[a][1], p1);
+                        ls[a][2] = ff_add(ls[a][2], p2);
+                        ls[a][3] = ff_add(ls[a][3], p3);
+                    }
+                    continue;
+                }
+                d[0] = qd[a];
+                d[1] = (double)p1.hi + (double)p1.lo;
+                d[2] = (double)p2.hi + (double)p2.lo;
+                d[3] = (double)p3.hi + (double)p3.lo;
+            } else {
+                const double qt = qd[a] * td[a];
+                d[0] = qd[a];
+                d[1] = qt;
+                d[2] = qt * td[a];
+                d[3] = qt * td[a] * td[a];
+            }
+            const int jlo = __shfl_sync(kFullMask, jl[a], 0);
+            const int jhi = __shfl_sync(kFullMask, jl[a], last_lane);
+            for (int jj = jlo; jj <= jhi; ++jj) {
+                const bool in = use && jl[a] == jj;
+                double m[4];
+                for (int p = 0; p < 4; ++p) m[p] = wsum(in ? d[p] : 0.0);
+                if (jj > cj[a]) {
+                    flush(a);
+                    cj[a] = jj;
+                }
+                for (int p = 0; p < 4; ++p) am[a][p] += m[p];
+            }
+        }
+    }
+#pragma unroll
+    for (int a = 0; a < NSP; ++a) {
+        if (w_lo < w_hi) {
+            flush(a);
+            if (lane == 0) atomicMax(&s_jl[a], cj[a]);
+        }
+    }
+    for (int k = 0; k < 6; ++k) {
+        const double v = wsum(MODE == kComp ? (double)lt[k].hi + (double)lt[k].lo : ts[k]);
+        if (lane == 0) s_t[warp][k] = v;
+    }
+    __syncthreads();
+    // the warps' sums in order, to the slots
+    for (int e = threadIdx.x; e < NSP * nsl; e += blockDim.x) {
+        const int a = e / nsl, jr = e % nsl;
+        const int j = j0[a] + jr;
+        if (j > s_jl[a]) continue;
+        double v[4];
+        for (int p = 0; p < 4; ++p) {
+            v[p] = 0.0;
+            for (int w = 0; w < nwarps; ++w) v[p] += sm(w, a, jr, p);
+        }
+        double* row = mom_row(mom, pre, s, a, nsp, kmax, D.nranges) + 4 * (int64_t)(rho + j);
+        if (MODE == kComp) {
+            // the FP32 adjoint's slots carry ln10 (its q's factor)
+            if (v[0] != 0.0 || v[1] != 0.0 || v[2] != 0.0 || v[3] != 0.0)
+                for (int p = 0; p < 4; ++p) row[p] += kLn10 * v[p];
+        } else {
+            for (int p = 0; p < 4; ++p) row[p] = v[p];
+        }
+    }
+    if (threadIdx.x < 6) {
+        const int k = threadIdx.x;
+        double v = 0.0;
+        for (int w = 0; w < nwarps; ++w) v += s_t[w][k];
+        if (MODE == kComp)
+            scal[6 * (pre + rho) + k] += v;
+        else
+            scal[6 * (pre + rho) + k] = v;
     }
 }
 
@@ -628,7 +986,8 @@ __global__ void __launch_bounds__(128)
                             const int64_t* __restrict__ prefix, const double* __restrict__ scal,
                             const double* __restrict__ mom, const float* __restrict__ rec32,
                             const double* __restrict__ rec64, const void* __restrict__ srec_v, int fp32,
-                            double* __restrict__ out_logL, double* __restrict__ grad) {
+                            double* __restrict__ out_logL, double* __restrict__ grad, int32_t* __restrict__ fb,
+                            int fb_mode) {
     __shared__ double sX[4][64];
     __shared__ double sY[4][64];
     // first and last bin's x of each adjoint range of the warp's dataset (the same for all its
@@ -637,12 +996,18 @@ __global__ void __launch_bounds__(128)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int s = blockIdx.x * 4 + warp;
     if (s >= S) return;
+    // fb_mode 1 (the FP32 call): fb[s] = 1 where the state's FP32 sums or gradient are not finite
+    // (they left the FP32 range); fb_mode 2 (its FP64 fallback): only the flagged states
+    if (fb_mode == 2 && fb[s] == 0) return;
     const int G = LISA_N_THETA + nsp * (2 * kmax + 2);
     double* gs = grad + (size_t)s * G;
     for (int k = lane; k < G; k += 32) gs[k] = 0.0;
     __syncwarp();
     if (sstat[s] & kUserBits) {
-        if (lane == 0) out_logL[s] = -INFINITY;
+        if (lane == 0) {
+            out_logL[s] = -INFINITY;
+            if (fb_mode == 1) fb[s] = 0;
+        }
         return;
     }
     const DatasetDev& D = ds[state_ds[s]];
@@ -656,8 +1021,20 @@ __global__ void __launch_bounds__(128)
     for (int k = 0; k < 6; ++k) v[k] = __shfl_sync(kFullMask, v[k], 0);
     double L = -v[0] - D.Cnu + D.K;
     const bool finite = isfinite(L);
+    if (fb_mode == 1) {
+        bool sums_ok = finite;
+        for (int k = 1; k < 6; ++k) sums_ok &= isfinite(v[k]);
+        if (!sums_ok) {
+            if (lane == 0) {
+                out_logL[s] = -INFINITY;
+                fb[s] = 1;
+            }
+            return;
+        }
+    }
     if (lane == 0) out_logL[s] = finite ? L : -INFINITY;
     if (!finite) return;   // gradient stays zero
+    bool bad = false;      // a non-finite moment or gradient value (fb_mode 1)
     // range bounds: in shared memory when they fit, else read per range below
     const bool staged = nr <= kEpiRanges;
     auto range_x = [&](int rho, double& xf, double& xlb) {
@@ -747,7 +1124,10 @@ __global__ void __launch_bounds__(128)
                         for (int p = 0; p < 4; ++p) Md[q][p] += row[4 * (int64_t)(rho + jj) + p];
                 }
             }
-            for (int p = 0; p < 4; ++p) M[q][p] = T(Md[q][p]);
+            for (int p = 0; p < 4; ++p) {
+                bad |= !isfinite(Md[q][p]);
+                M[q][p] = T(Md[q][p]);
+            }
             if (fp32) {
                 // moments about the FP32 midpoint xo -> about the left knot x_j:  t = u + mo
                 const float* r = static_cast<const float*>(srec_v) + (sp * (int64_t)(kmax + 1) + jj) * kSplineRec32;
@@ -888,6 +1268,7 @@ __global__ void __launch_bounds__(128)
         if (lane == 0) {
             ga[0] = spl::to_double(y0);
             ga[kmax + 1] = spl::to_double(yK);
+            bad |= !isfinite(ga[0]) || !isfinite(ga[kmax + 1]);
         }
         const int k_in = K - 2;
         for (int half = 0; half < 2; ++half) {
@@ -899,8 +1280,16 @@ __global__ void __launch_bounds__(128)
             if (i < k_in) {
                 ga[1 + i] = spl::to_double(gy);
                 ga[kmax + 2 + i] = spl::to_double(gx);
+                bad |= !isfinite(ga[1 + i]) || !isfinite(ga[kmax + 2 + i]);
             }
         }
+    }
+    if (fb_mode == 1) {
+        // (the template components were written by lane 0, which checks them)
+        if (lane == 0)
+            for (int k = 0; k < LISA_N_THETA; ++k) bad |= !isfinite(gs[k]);
+        bad = __any_sync(kFullMask, bad);
+        if (lane == 0) fb[s] = bad ? 1 : 0;
     }
 }
 
@@ -917,10 +1306,33 @@ inline bool adj_exact_t(const lisa_data* d) {
     return true;
 }
 
+// The most adjoint ranges of any dataset (the per-(state, range) grids' second dimension).
+inline int adj_max_ranges(const lisa_data* d) {
+    int m = 1;
+    for (const auto& Dh : d->h_ds) m = std::max(m, (int)Dh.nranges);
+    return m;
+}
+
+// Dynamic shared memory of adjoint_range_kernel with nwarps warps.
+inline size_t range_smem(const lisa_data* d, int kmax, int nwarps) {
+    return sizeof(double) * (size_t)nwarps * (size_t)d->nsp * (size_t)(kmax + 1) * 4;
+}
+
+// The gradient workspace's arrays for one call (fb, buf64: FP32 calls only).
+struct GradWs {
+    double* scal;
+    double* mom;
+    int32_t* fb;
+    void* buf64;
+    const float2* hull;   // FP32 calls: the spline buffer's ill-conditioned x-extent per state
+};
+
 template <int C, bool H, bool B>
 cudaError_t launch_adjoint(const lisa_data* d, bool fp32, const lisa_params* params, const lisa_knots* kn,
-                           const int32_t* sstat, const int32_t* nint, const void* srec, double* scal, double* mom,
+                           const int32_t* sstat, const int32_t* nint, const void* srec, const GradWs& gw,
                            double* out, double* grad, cudaStream_t sm) {
+    double* scal = gw.scal;
+    double* mom = gw.mom;
     const int grid = d->n_sm * 8;
     const bool prof = prof_active(d, sm);
     prof_mark(d, prof, 0, sm);
@@ -933,7 +1345,17 @@ cudaError_t launch_adjoint(const lisa_data* d, bool fp32, const lisa_params* par
             adjoint_fp32_kernel<C, H, B, false><<<grid, 128, 0, sm>>>(
                 d->d_adj_units, d->n_adj_units, d->d_ds, d->d_rec32, d->d_xlo32, params->theta_dev, sstat, nint,
                 static_cast<const float*>(srec), kn->kmax, d->nsp, d->d_adj_prefix, scal, mom);
-        else
+        if (fp32) {
+            // the bins of ill-conditioned intervals (routed states), masked above
+            const size_t smc = range_smem(d, kn->kmax, 4);
+            if (cudaFuncSetAttribute(adjoint_range_kernel<C, H, B, kComp>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smc) != cudaSuccess)
+                return cudaErrorInvalidValue;
+            adjoint_range_kernel<C, H, B, kComp>
+                <<<dim3((unsigned)d->n_states, (unsigned)adj_max_ranges(d)), 128, smc, sm>>>(
+                (int)d->n_states, d->d_state_ds, d->d_ds, d->d_rec32, d->d_xlo32, d->d_rec64, params->theta_dev, sstat,
+                nullptr, nint, srec, gw.hull, kn->kmax, d->nsp, d->d_adj_prefix, scal, mom);
+        } else
             adjoint_fp64_kernel<C, H, B><<<grid, 128, 0, sm>>>(d->d_adj_units, d->n_adj_units, d->d_ds, d->d_rec64,
                                                                params->theta_dev, sstat, nint,
                                                                static_cast<const double*>(srec), kn->kmax, d->nsp,
@@ -947,8 +1369,31 @@ cudaError_t launch_adjoint(const lisa_data* d, bool fp32, const lisa_params* par
     (fp32 ? adjoint_epilogue_kernel<C, H, B, spl::F2> : adjoint_epilogue_kernel<C, H, B, double>)<<<eb, 128, 0, sm>>>(
         (int)d->n_states, d->d_state_ds, d->d_ds, sstat, params->theta_dev, kn->count_dev, kn->x_dev, kn->w_dev,
         kn->kmax, kn->kind, d->nsp, d->d_adj_prefix, scal, mom, d->d_rec32, d->d_rec64, srec, fp32 ? 1 : 0, out,
-        grad);
-    const cudaError_t e = cudaGetLastError();
+        grad, gw.fb, fp32 ? 1 : 0);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess && fp32 && d->n_adj_units > 0) {
+        // states whose FP32 sums left the FP32 range (flagged by the epilogue): FP64 spline records,
+        // the FP64 adjoint and the FP64 epilogue for them alone (the others exit at once)
+        const SplineLayout L64 = spline_layout(d->n_states, d->nsp, kn->kmax);
+        const char* b64 = static_cast<const char*>(gw.buf64);
+        e = launch_setup_fp64_subset(d, kn, gw.buf64, gw.fb, sm);
+        if (e == cudaSuccess) {
+            const size_t smf = range_smem(d, kn->kmax, 16);
+            if (cudaFuncSetAttribute(adjoint_range_kernel<C, H, B, kFallback>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smf) != cudaSuccess)
+                return cudaErrorInvalidValue;
+            adjoint_range_kernel<C, H, B, kFallback>
+                <<<dim3((unsigned)d->n_states, (unsigned)adj_max_ranges(d)), 512, smf, sm>>>(
+                (int)d->n_states, d->d_state_ds, d->d_ds, d->d_rec32, d->d_xlo32, d->d_rec64, params->theta_dev, sstat,
+                gw.fb, reinterpret_cast<const int32_t*>(b64 + L64.off_nint), b64 + L64.off_rec, nullptr, kn->kmax,
+                d->nsp, d->d_adj_prefix, scal, mom);
+            adjoint_epilogue_kernel<C, H, B, double><<<eb, 128, 0, sm>>>(
+                (int)d->n_states, d->d_state_ds, d->d_ds, sstat, params->theta_dev, kn->count_dev, kn->x_dev,
+                kn->w_dev, kn->kmax, kn->kind, d->nsp, d->d_adj_prefix, scal, mom, d->d_rec32, d->d_rec64,
+                b64 + L64.off_rec, 0, out, grad, gw.fb, 2);
+            e = cudaGetLastError();
+        }
+    }
     prof_mark(d, prof, 3, sm);
     if (prof) d->prof_valid = true;
     return e;
@@ -956,13 +1401,13 @@ cudaError_t launch_adjoint(const lisa_data* d, bool fp32, const lisa_params* par
 
 template <int C>
 cudaError_t dispatch_adjoint(const lisa_data* d, bool fp32, const lisa_params* params, const lisa_knots* kn,
-                             const int32_t* sstat, const int32_t* nint, const void* srec, double* scal, double* mom,
+                             const int32_t* sstat, const int32_t* nint, const void* srec, const GradWs& gw,
                              double* out, double* grad, cudaStream_t sm) {
     if (d->sgwb_model == 0)
-        return launch_adjoint<C, false, false>(d, fp32, params, kn, sstat, nint, srec, scal, mom, out, grad, sm);
+        return launch_adjoint<C, false, false>(d, fp32, params, kn, sstat, nint, srec, gw, out, grad, sm);
     if (d->sgwb_model == 1)
-        return launch_adjoint<C, true, false>(d, fp32, params, kn, sstat, nint, srec, scal, mom, out, grad, sm);
-    return launch_adjoint<C, true, true>(d, fp32, params, kn, sstat, nint, srec, scal, mom, out, grad, sm);
+        return launch_adjoint<C, true, false>(d, fp32, params, kn, sstat, nint, srec, gw, out, grad, sm);
+    return launch_adjoint<C, true, true>(d, fp32, params, kn, sstat, nint, srec, gw, out, grad, sm);
 }
 
 }  // namespace
@@ -985,19 +1430,23 @@ extern "C" lisa_status lisa_psd_loglike_grad(const lisa_data* d, const lisa_para
         return LISA_ERR_NULL;
     const SplineLayout L = spline_layout(d->n_states, d->nsp, kn->kmax);
     if (buf_bytes < L.bytes || (reinterpret_cast<uintptr_t>(buf) & 255)) return LISA_ERR_WORKSPACE;
-    if (ws_bytes < 256 + grad_extra_bytes(d, kn->kmax) || (reinterpret_cast<uintptr_t>(ws) & 255))
-        return LISA_ERR_WORKSPACE;
+    const bool fp32 = prec == LISA_FP32;
+    const GradLayout GL = grad_layout(d, kn->kmax, fp32);
+    if (ws_bytes < 256 + GL.bytes || (reinterpret_cast<uintptr_t>(ws) & 255)) return LISA_ERR_WORKSPACE;
     if (d->n_states == 0) return LISA_SUCCESS;
     const char* base = static_cast<const char*>(buf);
     const int32_t* sstat = reinterpret_cast<const int32_t*>(base + L.off_status);
     const int32_t* nint = reinterpret_cast<const int32_t*>(base + L.off_nint);
     const void* srec = base + L.off_rec;
     char* w = static_cast<char*>(ws) + 256;
-    double* scal = reinterpret_cast<double*>(w);
-    double* mom = reinterpret_cast<double*>(w + align256(sizeof(double) * 6 * (size_t)d->adj_ranges));
+    GradWs gw;
+    gw.scal = reinterpret_cast<double*>(w + GL.off_scal);
+    gw.mom = reinterpret_cast<double*>(w + GL.off_mom);
+    gw.fb = fp32 ? reinterpret_cast<int32_t*>(w + GL.off_fb) : nullptr;
+    gw.buf64 = fp32 ? w + GL.off_buf64 : nullptr;
+    gw.hull = reinterpret_cast<const float2*>(base + L.off_hull);
     cudaStream_t sm = (cudaStream_t)stream;
-    const bool fp32 = prec == LISA_FP32;
-    cudaError_t e = d->C == 3 ? dispatch_adjoint<3>(d, fp32, params, kn, sstat, nint, srec, scal, mom, out, grad, sm)
-                              : dispatch_adjoint<2>(d, fp32, params, kn, sstat, nint, srec, scal, mom, out, grad, sm);
+    cudaError_t e = d->C == 3 ? dispatch_adjoint<3>(d, fp32, params, kn, sstat, nint, srec, gw, out, grad, sm)
+                              : dispatch_adjoint<2>(d, fp32, params, kn, sstat, nint, srec, gw, out, grad, sm);
     return e == cudaSuccess ? LISA_SUCCESS : LISA_ERR_CUDA;
 }

@@ -241,8 +241,12 @@ inline WsLayout ws_layout(const lisa_data* d) {
 }
 inline size_t ws_fwd_bytes(const lisa_data* d) { return ws_layout(d).bytes; }
 
-// Extra workspace of the adjoint entry point (after the forward region).
-size_t grad_extra_bytes(const lisa_data* d, int kmax);
+// Extra workspace of the adjoint entry point (after the forward region); the FP32 call also holds
+// the FP64 fallback (a per-state flag and an FP64 spline buffer).
+size_t grad_extra_bytes(const lisa_data* d, int kmax, bool fp32);
+// FP64 spline records of the states with only[s] != 0 (the FP32 adjoint's fallback).
+cudaError_t launch_setup_fp64_subset(const lisa_data* d, const lisa_knots* kn, void* buf64, const int32_t* only,
+                                     cudaStream_t sm);
 
 lisa_status rebuild_work(lisa_data* d);
 // The dense-covariance likelihood kernel (LISA_COV_FULL) for the model of d, FP32 bulk or FP64.

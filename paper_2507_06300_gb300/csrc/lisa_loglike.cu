@@ -1257,10 +1257,9 @@ using namespace lisa;
 extern "C" {
 
 size_t lisa_workspace_bytes(const lisa_data* d, int32_t kmax, lisa_precision p, int32_t with_grad) {
-    (void)p;
     if (!d || kmax < 0 || kmax > LISA_MAX_KNOTS) return 0;
     size_t b = ws_fwd_bytes(d);
-    if (with_grad) b += grad_extra_bytes(d, kmax);
+    if (with_grad) b += grad_extra_bytes(d, kmax, p == LISA_FP32);
     return b;
 }
 
