@@ -242,12 +242,18 @@ lisa_status lisa_psd_loglike(const lisa_data* data, const lisa_params* params,
  * LISA_ERR_WORKSPACE (misaligned), LISA_ERR_CUDA. */
 lisa_status lisa_workspace_status(const void* workspace_dev, lisa_stream_t stream);
 
-/* log L and its gradient for every state (hand-written adjoint; LISA_COV_DIAGONAL data only,
- * LISA_ERR_VALUE for the full covariance; the spline coefficients are
- * recomputed from the knots, nothing per bin is stored).  grad_dev
+/* log L and its gradient for every state (hand-written adjoint of Sec. III.C's Wishart term;
+ * LISA_COV_DIAGONAL data only, LISA_ERR_VALUE for the full covariance; the spline coefficients
+ * are recomputed from the knots, nothing per bin is stored).  grad_dev
  * [n_states][LISA_N_THETA + n_splines*(2*kmax+2)] (FP64): d log L / d theta (a_oms, a_tm,
  * log10 A, n1, n2), then per spline d/d(w slots 0..kmax+1) and d/d(x slots 0..kmax-1);
- * unused slots are 0.  spline_buf_dev must come from lisa_spline_setup on the same knots. */
+ * unused slots are 0.  spline_buf_dev must come from lisa_spline_setup on the same knots.
+ * FP32 mode: bins on ill-conditioned spline intervals (the states lisa_spline_setup routes) take
+ * a compensated pass, and states whose FP32 sums leave the FP32 range (PSD values beyond about
+ * 2^+-126 somewhere) are redone in FP64 within the call; such a call takes longer (about a
+ * millisecond more at 2,048 states x 131,072 bins).  workspace_dev: at least
+ * lisa_workspace_bytes(..., precision, 1) bytes, 256-byte aligned (in FP32 mode it also holds
+ * that fallback's per-state flags and FP64 spline records). */
 lisa_status lisa_psd_loglike_grad(const lisa_data* data, const lisa_params* params,
                                   const lisa_knots* knots, const void* spline_buf_dev,
                                   size_t spline_buf_bytes, double* loglike_dev, double* grad_dev,
