@@ -678,7 +678,7 @@ def run_ours(args):
             "unit": UNIT, "fp32_value": world * Ia["sb"] / (g32_ms / 1e3), "fp32_ms_per_step": g32_ms,
             "fp64_value": world * Ia["sb"] / (g64_ms / 1e3), "fp64_ms_per_step": g64_ms,
             "speedup_fp32_vs_fp64": g64_ms / g32_ms,
-            "kernel_ms": {"adjoint_fp32": kadj[0], "epilogue": kadj[2]},
+            "kernel_ms": {"adjoint_fp32": kadj[0], "compensated_and_fallback": kadj[1], "epilogue": kadj[2]},
             "grad_fp32_vs_fp64": {"median_rel_to_state_max": float(np.median(rel)),
                                   "p99_rel_to_state_max": float(np.quantile(rel, 0.99)),
                                   "components_above_1e-3_of_state_max": int(big.sum()),

@@ -65,8 +65,10 @@ lisa_status lisa_pipe_rates(int32_t iters, int32_t reps, double* rates, lisa_str
  * its last event) and writes ms[3] (HOST, caller-owned), in milliseconds.  After
  * lisa_psd_loglike: [0] the main likelihood kernel (fused FP32 or plain FP64), [1] the
  * compensated kernel for routed states (0 in FP64 mode), [2] the finalize kernel.  After
- * lisa_psd_loglike_grad: [0] the adjoint kernel, [1] 0, [2] the adjoint epilogue.  Errors: LISA_ERR_NULL; LISA_ERR_VALUE when profiling is off
- * or no call has been recorded since it was enabled; LISA_ERR_CUDA. */
+ * lisa_psd_loglike_grad: [0] the adjoint kernel (FP32 or FP64), [1] the FP32 call's compensated
+ * and fallback passes (0 in FP64 mode), [2] the adjoint epilogue.  Errors: LISA_ERR_NULL;
+ * LISA_ERR_VALUE when profiling is off or no call has been recorded since it was enabled;
+ * LISA_ERR_CUDA. */
 lisa_status lisa_data_set_profiling(lisa_data* data, int32_t enable);
 lisa_status lisa_data_kernel_ms(const lisa_data* data, float* ms);
 

@@ -250,10 +250,10 @@ lisa_status lisa_workspace_status(const void* workspace_dev, lisa_stream_t strea
  * unused slots are 0.  spline_buf_dev must come from lisa_spline_setup on the same knots.
  * FP32 mode: bins on ill-conditioned spline intervals (the states lisa_spline_setup routes) take
  * a compensated pass, and states whose FP32 sums leave the FP32 range (PSD values beyond about
- * 2^+-126 somewhere) are redone in FP64 within the call; such a call takes longer (about a
- * millisecond more at 2,048 states x 131,072 bins).  workspace_dev: at least
- * lisa_workspace_bytes(..., precision, 1) bytes, 256-byte aligned (in FP32 mode it also holds
- * that fallback's per-state flags and FP64 spline records). */
+ * 2^+-126 somewhere) are redone within the call by a log-domain pass (log2 of each PSD from the
+ * float-float spline values, FP64 for 1/S and the sums) and an FP64 reverse map; such a call
+ * takes somewhat longer.  workspace_dev: at least lisa_workspace_bytes(..., precision, 1)
+ * bytes, 256-byte aligned (in FP32 mode it also holds that pass's per-state flags). */
 lisa_status lisa_psd_loglike_grad(const lisa_data* data, const lisa_params* params,
                                   const lisa_knots* knots, const void* spline_buf_dev,
                                   size_t spline_buf_bytes, double* loglike_dev, double* grad_dev,

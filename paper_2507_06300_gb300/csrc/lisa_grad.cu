@@ -32,10 +32,9 @@
 namespace lisa {
 
 // Gradient workspace (after 256 bytes): range sums scal | moment slots mom, and for the FP32
-// call the FP64 fallback: a flag per state | an FP64 spline buffer (states whose FP32 sums leave
-// the FP32 range are redone in FP64 within the call).
+// call a flag per state (states whose FP32 sums leave the FP32 range, redone within the call).
 struct GradLayout {
-    size_t off_scal, off_mom, off_fb, off_buf64, bytes;
+    size_t off_scal, off_mom, off_fb, bytes;
 };
 inline GradLayout grad_layout(const lisa_data* d, int kmax, bool fp32) {
     GradLayout G;
@@ -43,8 +42,7 @@ inline GradLayout grad_layout(const lisa_data* d, int kmax, bool fp32) {
     G.off_mom = align256(sizeof(double) * 6 * (size_t)d->adj_ranges);
     G.off_fb = G.off_mom + align256(sizeof(double) * 4 * (size_t)d->nsp *
                                     ((size_t)d->adj_ranges + (size_t)d->n_states * (size_t)(kmax + 1)));
-    G.off_buf64 = G.off_fb + (fp32 ? align256(sizeof(int32_t) * (size_t)d->n_states) : 0);
-    G.bytes = G.off_buf64 + (fp32 ? align256(spline_layout(d->n_states, d->nsp, kmax).bytes) : 0);
+    G.bytes = G.off_fb + (fp32 ? align256(sizeof(int32_t) * (2 * (size_t)d->n_states + 1)) : 0);
     return G;
 }
 
@@ -58,6 +56,13 @@ constexpr unsigned kFullMask = 0xffffffffu;
 // Moment row of (state, spline): 4 doubles per slot, nranges + kmax + 1 slots.
 __device__ __forceinline__ double* mom_row(double* mom, int64_t prefix, int s, int a, int nsp, int kmax, int nr) {
     return mom + 4 * ((int64_t)nsp * (prefix + (int64_t)s * (kmax + 1)) + (int64_t)a * (nr + kmax + 1));
+}
+
+// The FP32 gradient's fallback list in the flag area fb (int32): fb[0..S) a flag per state,
+// fb[S] the count, fb[S+1..] the flagged states (in the order they were flagged).  Flags state s
+// (sums or moments beyond the FP32 range) once.
+__device__ __forceinline__ void fb_flag(int32_t* fb, int S, int s) {
+    if (atomicExch(fb + s, 1) == 0) fb[S + 1 + atomicAdd(fb + S, 1)] = s;
 }
 
 // ---- FP32 adjoint: one warp per (dataset, range, up to 32 states) -----------------------------
@@ -103,7 +108,8 @@ __global__ void __launch_bounds__(128, 3)
                         const float* __restrict__ rec32, const float* __restrict__ xlo32,
                         const double* __restrict__ theta, const int32_t* __restrict__ sstat,
                         const int32_t* __restrict__ nint, const float* __restrict__ srec, int kmax, int nsp,
-                        const int64_t* __restrict__ prefix, double* __restrict__ scal, double* __restrict__ mom) {
+                        const int64_t* __restrict__ prefix, double* __restrict__ scal, double* __restrict__ mom,
+                        int S, int32_t* __restrict__ fb) {
     constexpr int NSP = C + (HAS_H ? 1 : 0);
     __shared__ float2 s_am[NSP * 4][128];
     __shared__ float2 s_as[6][128];
@@ -134,6 +140,7 @@ __global__ void __launch_bounds__(128, 3)
         const int32_t* nint_s = nint + (int64_t)s * nsp;
         AdjIv iv[NSP] = {};
         unsigned hm = 0;   // splines whose current interval is ill-conditioned (T > kRobustT)
+        bool bad = false;  // a sum beyond the FP32 range: the state goes to the fallback list
         auto base = [&](int a) { return srec + ((int64_t)s * nsp + a) * (int64_t)(kmax + 1) * kSplineRec32; };
         auto load = [&](int a) {
             const float* r = base(a) + (size_t)iv[a].j * kSplineRec32;
@@ -197,6 +204,7 @@ __global__ void __launch_bounds__(128, 3)
             for (int p = 0; p < 4; ++p) {
                 const float2 v = s_am[4 * a + p][tid];
                 row[p] = kLn10 * ((double)v.x + (double)v.y);   // q carries ln10 only here
+                bad |= !isfinite(v.x);
                 s_am[4 * a + p][tid] = make_float2(0.f, 0.f);
             }
         };
@@ -474,7 +482,9 @@ __global__ void __launch_bounds__(128, 3)
         for (int k = 0; k < 6; ++k) {
             const float2 v = s_as[k][tid];
             sc[k] = (double)v.x + (double)v.y;
+            bad |= !isfinite(v.x);
         }
+        if (bad) fb_flag(fb, S, s);
     }
 }
 
@@ -580,31 +590,41 @@ __global__ void __launch_bounds__(128)
     }
 }
 
-// ---- the FP32 gradient's two per-state passes: one CTA per (state, range) ---------------------
+// ---- the FP32 gradient's two per-state passes: one CTA per (state, range) item --------------
 // Mode kComp: the bins the FP32 adjoint masked (routed states, whose ill-conditioned intervals
 // (conditioning T > kRobustT, prior draws with close knots) it loads as zero cubics): spline values
 // in float-float from the records' hi and lo parts (2^P as ex2(hi) (1 + lo ln2)), per-bin terms in
 // FP32, the moments' products exact (float-float); the sums are added to the slots the FP32
 // adjoint wrote.  Only ranges overlapping the state's ill-conditioned x-extent run.
-// Mode kFallback: the states the FP32 epilogue flagged (their FP32 sums left the FP32 range) in
-// FP64, the per-bin arithmetic of adjoint_fp64_kernel, from FP64 records built for them; the sums
-// overwrite the slots (every interval from the range's first bin to its last).
-// The CTA's warps (4 for kComp, 16 for the FP64 kFallback) split the range's bins, their lanes 32
+// Mode kFallback: the states the FP32 epilogue flagged (their FP32 sums left the FP32 range), all
+// their bins: spline values in float-float from the FP32 records, the PSDs, 1 / S-hat and the
+// sums in FP64; the sums overwrite the slots (every interval from the range's first bin to its
+// last), in the FP32 adjoint's convention (moments about the records' midpoints, ln10 in q).
+// A persistent grid runs the (state, range) items of a compact list (kComp: the setup's route
+// list; kFallback: the flag area's list), one item per CTA at a time.
+// The CTA's warps (4 for kComp, 16 for kFallback) split the range's bins, their lanes 32
 // consecutive bins at a time; each spline's moments are reduced over the lanes per interval (a fixed butterfly),
 // kept per warp and interval in shared memory, and summed over the warps in order.
 constexpr int kComp = 0, kFallback = 1;
+
+// 2^k in FP64 for an integer-valued float k (the fallback pass's scales): from the exponent field
+// within the normal range, by scalbn beyond it (subnormal, 0, inf).
+__device__ __forceinline__ double pow2_fb(float k) {
+    if (k >= -1022.f && k <= 1023.f) return __longlong_as_double((long long)((int)k + 1023) << 52);
+    return scalbn(1.0, (int)fmaxf(fminf(k, 2100.f), -2100.f));
+}
+
 
 template <int C, bool HAS_H, bool BROKEN, int MODE>
 __global__ void __launch_bounds__(MODE == kComp ? 128 : 512)
     adjoint_range_kernel(int S, const int32_t* __restrict__ state_ds, const DatasetDev* __restrict__ ds,
                          const float* __restrict__ rec32, const float* __restrict__ xlo32,
-                         const double* __restrict__ rec64, const double* __restrict__ theta,
-                         const int32_t* __restrict__ sstat, const int32_t* __restrict__ flag,
-                         const int32_t* __restrict__ nint, const void* __restrict__ srec_v,
+                         const float* __restrict__ elllo32, const double* __restrict__ theta,
+                         const int32_t* __restrict__ sstat, const int32_t* __restrict__ list, int R,
+                         int32_t* __restrict__ fb, const int32_t* __restrict__ nint, const void* __restrict__ srec_v,
                          const float2* __restrict__ hull, int kmax, int nsp, const int64_t* __restrict__ prefix,
                          double* __restrict__ scal, double* __restrict__ mom) {
     constexpr int NSP = C + (HAS_H ? 1 : 0);
-    constexpr int RS = (MODE == kComp) ? kSplineRec32 : kSplineRec;   // record stride
     // per warp, spline and interval (from the range's first) the 4 moment sums: dynamic shared
     // memory of nwarps * NSP * (kmax + 1) * 4 doubles
     extern __shared__ double s_m[];
@@ -614,37 +634,38 @@ __global__ void __launch_bounds__(MODE == kComp ? 128 : 512)
     const int nwarps = blockDim.x >> 5;     // <= 16
     const int nsl = kmax + 1;               // interval slots per spline
     auto sm = [&](int w, int a, int jr, int p) -> double& { return s_m[(((w * NSP) + a) * nsl + jr) * 4 + p]; };
-    const int s = blockIdx.x, rho = blockIdx.y;
-    if (MODE == kComp ? (sstat[s] & (kUserBits | kRouted)) != kRouted : flag[s] == 0) return;   // CTA-uniform
+    // the list's (state, range) items, R ranges per state, CTA by CTA (the exits are CTA-uniform)
+    const int64_t n_items = (int64_t)list[0] * R;
+    for (int64_t it = blockIdx.x; it < n_items; it += gridDim.x) {
+    const int s = list[1 + (int)(it / R)], rho = (int)(it % R);
+    __syncthreads();   // the previous item's reads of the shared sums are done
+    if (MODE == kComp && (sstat[s] & (kUserBits | kRouted)) != kRouted) continue;
     const DatasetDev& D = ds[state_ds[s]];
-    if (rho >= D.nranges) return;
+    if (rho >= D.nranges) continue;
     const int64_t b0 = D.bin0 + (int64_t)rho * kAdjBins;
     const int nb = (int)min((int64_t)kAdjBins, D.bin0 + D.npad - b0);
     const float* tb = rec32 + (b0 >> 1) * kPairRec;
     if (MODE == kComp) {
         const float2 hx = hull[s];
-        if (fld(tb, nb - 1, 0) < hx.x || fld(tb, 0, 0) >= hx.y) return;   // no ill-conditioned interval here
+        if (fld(tb, nb - 1, 0) < hx.x || fld(tb, 0, 0) >= hx.y) continue;   // no ill-conditioned interval here
     }
     const double* th = theta + (size_t)s * LISA_N_THETA;
     const int64_t pre = prefix[s];
-    // the state's parameters: FP32 (kComp, as the FP32 adjoint derives them) and FP64 (kFallback)
+    // the state's parameters as the FP32 adjoint derives them
     const float ao2 = (float)(th[0] * th[0]), at2 = (float)(th[1] * th[1]);
     const float Af = (MODE == kComp && HAS_H) ? (float)exp10(th[2]) : 0.f;
     const float n1 = (float)th[3], n2 = BROKEN ? (float)th[4] : n1;
-    const double ao2d = th[0] * th[0], at2d = th[1] * th[1], lAd = th[2], n1d = th[3];
-    const double n2d = BROKEN ? th[4] : n1d;
-    // bin i's x as the walk compares it (FP32 for the FP32 records, FP64 for the FP64 ones)
-    auto xbin = [&](int i) -> double { return MODE == kComp ? (double)fld(tb, i, 0) : rec64[(b0 + i) * kRec]; };
-    auto rec = [&](int a, int j) -> const char* {
+    // kFallback: the SGWB slopes and log2 A in float-float
+    const ff sl1 = ff_from_double(th[3]), sl2 = ff_from_double(BROKEN ? th[4] : th[3]);
+    const ff lA2 = ff_from_double(th[2] * kLog2_10);
+    // bin i's x as the FP32 adjoint's walk compares it, and the FP32 records
+    auto xbin = [&](int i) -> float { return fld(tb, i, 0); };
+    auto rec = [&](int a, int j) -> const float* {
         const int64_t sp = (int64_t)s * nsp + a;
-        return static_cast<const char*>(srec_v) + ((sp * (int64_t)(kmax + 1) + j) * RS) *
-                                                      (MODE == kComp ? sizeof(float) : sizeof(double));
+        return static_cast<const float*>(srec_v) + (sp * (int64_t)(kmax + 1) + j) * kSplineRec32;
     };
-    auto right_end = [&](int a, int j) -> double {
-        return MODE == kComp ? (double)__ldg(reinterpret_cast<const float*>(rec(a, j)))
-                             : __ldg(reinterpret_cast<const double*>(rec(a, j)) + 1);
-    };
-    auto locate = [&](int a, double x) {
+    auto right_end = [&](int a, int j) -> float { return __ldg(rec(a, j)); };
+    auto locate = [&](int a, float x) {
         const int n = nint[(int64_t)s * nsp + a];
         int j = 0;
         while (j < n - 1 && x >= right_end(a, j)) ++j;
@@ -674,12 +695,17 @@ __global__ void __launch_bounds__(MODE == kComp ? 128 : 512)
         for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFullMask, v, o);
         return v;
     };
-    // kComp: lane-local float-float running sums of the warp's current intervals (folded into am,
-    // over the lanes, only when an interval is left), and of the template terms
+    // lane-local running sums of the warp's current intervals (float-float for kComp, FP64 for
+    // kFallback; folded into am, over the lanes, only when an interval is left), and (kComp) of
+    // the template terms
     ff ls[NSP][4], lt[6];
+    double lsd[NSP][4];   // kFallback: the lanes' FP64 running sums, folded the same way
 #pragma unroll
     for (int a = 0; a < NSP; ++a)
-        for (int p = 0; p < 4; ++p) ls[a][p] = ff{0.f, 0.f};
+        for (int p = 0; p < 4; ++p) {
+            ls[a][p] = ff{0.f, 0.f};
+            lsd[a][p] = 0.0;
+        }
     for (int k = 0; k < 6; ++k) lt[k] = ff{0.f, 0.f};
     auto flush = [&](int a) {
         if (MODE == kComp)
@@ -687,17 +713,50 @@ __global__ void __launch_bounds__(MODE == kComp ? 128 : 512)
                 am[a][p] += wsum((double)ls[a][p].hi + (double)ls[a][p].lo);
                 ls[a][p] = ff{0.f, 0.f};
             }
+        else
+            for (int p = 0; p < 4; ++p) {
+                am[a][p] += wsum(lsd[a][p]);
+                lsd[a][p] = 0.0;
+            }
         if (lane == 0)
             for (int p = 0; p < 4; ++p) sm(warp, a, cj[a] - j0[a], p) = am[a][p];
         for (int p = 0; p < 4; ++p) am[a][p] = 0.0;
     };
     double ts[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    // kComp: the warp's 32-bin groups holding a bin of an ill-conditioned interval (bit g: bins
+    // w_lo + 32 g ...), the lanes taking the intervals; the others are skipped (nothing to add)
+    unsigned gmask = 0xffffffffu;
+    if (MODE == kComp && w_hi - w_lo <= 32 * 32) {
+        auto lower = [&](float v) {   // first bin of the warp with x >= v (w_hi if none)
+            int lo = w_lo, hi = w_hi;
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (xbin(mid) >= v) hi = mid; else lo = mid + 1;
+            }
+            return lo;
+        };
+        unsigned m = 0;
+#pragma unroll
+        for (int a = 0; a < NSP; ++a)
+            for (int jb = 0; jb < nin[a]; jb += 32) {
+                const int j = jb + lane;
+                if (j >= nin[a] || __ldg(rec(a, j) + 7) <= (float)kRobustT) continue;
+                // the walk's bins of interval j: right_end(j - 1) <= x < right_end(j)
+                const int i_lo = j == 0 ? w_lo : lower(right_end(a, j - 1));
+                const int i_hi = j == nin[a] - 1 ? w_hi : lower(right_end(a, j));
+                if (i_lo >= i_hi) continue;
+                const int g0 = (i_lo - w_lo) >> 5, g1 = (i_hi - 1 - w_lo) >> 5;
+                m |= (g1 >= 31 ? 0xffffffffu : ((2u << g1) - 1u)) & ~((1u << g0) - 1u);
+            }
+        gmask = __reduce_or_sync(kFullMask, m);
+    }
     for (int i0 = w_lo; i0 < w_hi; i0 += 32) {
+        if (!((gmask >> ((i0 - w_lo) >> 5)) & 1u)) continue;   // warp-uniform
         const int i = i0 + lane;
         const bool valid = i < w_hi;
         const int last_lane = min(31, w_hi - 1 - i0);
         const int ib = valid ? i : i0;
-        const double x = xbin(ib);
+        const float x = xbin(ib);
         int jl[NSP];
         bool hard = false;
 #pragma unroll
@@ -705,7 +764,7 @@ __global__ void __launch_bounds__(MODE == kComp ? 128 : 512)
             int j = cj[a];
             while (j < nin[a] - 1 && x >= right_end(a, j)) ++j;
             jl[a] = j;
-            if (MODE == kComp) hard |= !(__ldg(reinterpret_cast<const float*>(rec(a, j)) + 7) <= (float)kRobustT);
+            if (MODE == kComp) hard |= !(__ldg(rec(a, j) + 7) <= (float)kRobustT);
         }
         const bool use = valid && (MODE == kFallback || hard);
         if (!__any_sync(kFullMask, use)) {
@@ -720,10 +779,15 @@ __global__ void __launch_bounds__(MODE == kComp ? 128 : 512)
             }
             continue;
         }
-        double qd[NSP], td[NSP];   // the spline signals and t = x - (expansion point), FP64
+        // the spline signals q (FP32 for kComp, FP64 for kFallback) and t = x - x_o (FP32)
+        float qk[NSP], tv[NSP];
+        double qd[NSP];
         double tc[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
 #pragma unroll
-        for (int a = 0; a < NSP; ++a) qd[a] = td[a] = 0.0;
+        for (int a = 0; a < NSP; ++a) {
+            qk[a] = tv[a] = 0.f;
+            qd[a] = 0.0;
+        }
         if (use) {
             if constexpr (MODE == kComp) {
                 const float xf = fld(tb, ib, 0), ell = fld(tb, ib, 1), nu = fld(tb, ib, 2);
@@ -776,50 +840,75 @@ __global__ void __launch_bounds__(MODE == kComp ? 128 : 512)
                 for (int k = 0; k < 6; ++k) lt[k] = ff_add(lt[k], two_sum(tf[k], 0.f));
 #pragma unroll
                 for (int a = 0; a < NSP; ++a) {
-                    qd[a] = q[a];
-                    td[a] = tl[a];
+                    qk[a] = q[a];
+                    tv[a] = tl[a];
                 }
             } else {
-                const double* qb = rec64 + (b0 + ib) * kRec;
-                const double ell = qb[1], nu = qb[2];
-                double P[NSP];
+                // exponents in float-float (spline values from the FP32 records' hi + lo); per
+                // channel an integer scale k with S-hat = S' 2^k, S' in [0.35, 2.9); S', 1 / S'
+                // and log2 S' in FP32; FP64 only for r = 2^-k / S' and the sums
+                const float xf = fld(tb, ib, 0), nuf = fld(tb, ib, 2);
+                const float x_lo = __ldg(xlo32 + b0 + ib);
+                const ff ell = {fld(tb, ib, 1), __ldg(elllo32 + b0 + ib)};
+                const double nu = nuf;
+                ff Pv[NSP];
 #pragma unroll
                 for (int a = 0; a < NSP; ++a) {
-                    const double* z = reinterpret_cast<const double*>(rec(a, jl[a]));
-                    td[a] = x - z[0];
-                    P[a] = z[2] + td[a] * (z[3] + td[a] * (z[4] + td[a] * z[5]));
+                    const float4* rr = reinterpret_cast<const float4*>(rec(a, jl[a]));
+                    const float4 A = __ldg(rr), Bq = __ldg(rr + 1), Cq = __ldg(rr + 2), Dq = __ldg(rr + 3);
+                    const ff tt = two_sum(xf, -A.y);
+                    tv[a] = tt.hi + (tt.lo + (x_lo - Cq.x));   // t = x - x_o as the FP32 adjoint
+                    const ff tf = ff_add(ff{xf, x_lo}, ff{-A.y, -Cq.x});
+                    ff v = {Bq.y, Dq.x};
+                    v = ff_add(ff_mul(v, tf), ff{Bq.x, Cq.w});
+                    v = ff_add(ff_mul(v, tf), ff{A.w, Cq.z});
+                    Pv[a] = ff_add(ff_mul(v, tf), ff{A.z, Cq.y});   // log2 units
                 }
-                double eh = 0.0;
-                if (HAS_H) {
-                    const double sl = BROKEN ? (ell < 0.0 ? n1d : n2d) : n1d;
-                    eh = exp10(lAd + P[C]) * exp2(sl * ell);
-                }
-                double fwd = 0.0, To = 0.0, Tt = 0.0, H = 0.0;
+                // the SGWB exponent: P_h + slope * log2(f / f_ref) + log2 A
+                ff xh = {0.f, 0.f};
+                if (HAS_H) xh = ff_add(ff_add(Pv[C], ff_mul((BROKEN && ell.hi >= 0.f) ? sl2 : sl1, ell)), lA2);
+                double rs = 0.0, To = 0.0, Tt = 0.0, H = 0.0;
+                float ks = 0.f, l2s = 0.f;   // sum of the scales k (integers) and of log2 S'
 #pragma unroll
                 for (int c = 0; c < C; ++c) {
-                    const double E = exp10(P[c]);
-                    const double N = ao2d * qb[3 + c] + at2d * qb[6 + c];
-                    const double Eh = HAS_H ? eh * qb[9 + c] : 0.0;
-                    const double Sc = E * N + Eh;
-                    // g = nu (1 - S) / S^2 applied as nu (r - 1) (r E) with r = 1 / S: no
-                    // intermediate overflows where S^2 would (S beyond 1e154)
-                    const double r = 1.0 / Sc;
-                    const double gr = nu * (r - 1.0), rE = r * E;
-                    fwd += r + log(Sc);
-                    To += gr * rE * qb[3 + c];
-                    Tt += gr * rE * qb[6 + c];
-                    H += gr * (r * Eh);
-                    qd[c] = kLn10 * gr * rE * N;
+                    const float go = fld(tb, ib, 3 + c), gt = fld(tb, ib, 6 + c);
+                    const float N = fmaf(ao2, go, at2 * gt);
+                    int eN, eG = 0;
+                    const float mN = frexpf(N, &eN);   // N = mN 2^eN
+                    const float mG = HAS_H ? frexpf(fld(tb, ib, 9 + c), &eG) : 0.f;
+                    const float yh = mG > 0.f ? xh.hi + (float)eG : -INFINITY;
+                    const float kc = rintf(fmaxf(Pv[c].hi + (float)eN, yh));
+                    const ff dN = ff_add(Pv[c], ff{(float)eN - kc, 0.f});
+                    const float eNs = ex2_approx(dN.hi + dN.lo) * mN;   // E N / 2^k
+                    float eHs = 0.f;                                     // E_h G_h / 2^k
+                    if (HAS_H && mG > 0.f) {
+                        const ff dH = ff_add(xh, ff{(float)eG - kc, 0.f});
+                        eHs = ex2_approx(dH.hi + dH.lo) * mG;
+                    }
+                    const float Sp = eNs + eHs;
+                    const float rp = rcp_approx(Sp);
+                    const float rE = eNs * rp;   // E N / S-hat
+                    const double r = (double)rp * pow2_fb(-kc);
+                    const double gr = nu * (r - 1.0);
+                    rs += r;
+                    ks += kc;
+                    l2s += lg2_approx(Sp);
+                    const float rEN = rE * rcp_approx(N);   // E / S-hat
+                    To = fma(gr, (double)(rEN * go), To);
+                    Tt = fma(gr, (double)(rEN * gt), Tt);
+                    if (HAS_H) H = fma(gr, (double)(eHs * rp), H);
+                    qd[c] = (kLn10 * gr) * (double)rE;
                 }
-                if (HAS_H) qd[C] = kLn10 * H;
-                tc[0] = nu * (fwd - (double)C);
+                const double elld = (double)ell.hi + (double)ell.lo;
+                tc[0] = nu * (rs + kLn2 * ((double)ks + (double)l2s) - (double)C);
                 tc[1] = To;
                 tc[2] = Tt;
                 tc[3] = H;
-                if (BROKEN && ell >= 0.0)
-                    tc[5] = ell * H;
+                if (BROKEN && elld >= 0.0)
+                    tc[5] = elld * H;
                 else
-                    tc[4] = ell * H;
+                    tc[4] = elld * H;
+                if (HAS_H) qd[C] = kLn10 * H;
             }
         }
         if (MODE == kFallback)
@@ -832,7 +921,7 @@ __global__ void __launch_bounds__(MODE == kComp ? 128 : 512)
             if (MODE == kComp) {
                 // exact products q t^p (float-float) of the FP32 values; while every lane stays in
                 // the warp's current interval they go to the lane-local sums
-                const float qf = (float)qd[a], t = (float)td[a], qt = qf * t;
+                const float qf = qk[a], t = tv[a], qt = qf * t;
                 const ff p1 = {qt, fmaf(qf, t, -qt)};
                 const ff p2 = ff_mul(p1, ff{t, 0.f});
                 const ff p3 = ff_mul(p2, ff{t, 0.f});
@@ -845,16 +934,21 @@ __global__ void __launch_bounds__(MODE == kComp ? 128 : 512)
                     }
                     continue;
                 }
-                d[0] = qd[a];
+                d[0] = qf;
                 d[1] = (double)p1.hi + (double)p1.lo;
                 d[2] = (double)p2.hi + (double)p2.lo;
                 d[3] = (double)p3.hi + (double)p3.lo;
             } else {
-                const double qt = qd[a] * td[a];
+                const double t = tv[a], qt = qd[a] * t;
                 d[0] = qd[a];
                 d[1] = qt;
-                d[2] = qt * td[a];
-                d[3] = qt * td[a] * td[a];
+                d[2] = qt * t;
+                d[3] = d[2] * t;
+                if (__all_sync(kFullMask, !use || jl[a] == cj[a])) {
+                    if (use)
+                        for (int p = 0; p < 4; ++p) lsd[a][p] += d[p];
+                    continue;
+                }
             }
             const int jlo = __shfl_sync(kFullMask, jl[a], 0);
             const int jhi = __shfl_sync(kFullMask, jl[a], last_lane);
@@ -895,8 +989,14 @@ __global__ void __launch_bounds__(MODE == kComp ? 128 : 512)
         double* row = mom_row(mom, pre, s, a, nsp, kmax, D.nranges) + 4 * (int64_t)(rho + j);
         if (MODE == kComp) {
             // the FP32 adjoint's slots carry ln10 (its q's factor)
-            if (v[0] != 0.0 || v[1] != 0.0 || v[2] != 0.0 || v[3] != 0.0)
-                for (int p = 0; p < 4; ++p) row[p] += kLn10 * v[p];
+            if (v[0] != 0.0 || v[1] != 0.0 || v[2] != 0.0 || v[3] != 0.0) {
+                bool bad = false;
+                for (int p = 0; p < 4; ++p) {
+                    row[p] += kLn10 * v[p];
+                    bad |= !isfinite(row[p]);
+                }
+                if (bad) fb_flag(fb, S, s);
+            }
         } else {
             for (int p = 0; p < 4; ++p) row[p] = v[p];
         }
@@ -905,10 +1005,13 @@ __global__ void __launch_bounds__(MODE == kComp ? 128 : 512)
         const int k = threadIdx.x;
         double v = 0.0;
         for (int w = 0; w < nwarps; ++w) v += s_t[w][k];
-        if (MODE == kComp)
+        if (MODE == kComp) {
             scal[6 * (pre + rho) + k] += v;
-        else
+            if (!isfinite(scal[6 * (pre + rho) + k])) fb_flag(fb, S, s);
+        } else {
             scal[6 * (pre + rho) + k] = v;
+        }
+    }
     }
 }
 
@@ -977,38 +1080,33 @@ __device__ __forceinline__ void akima_slope_grad(int k, int K, T mm2, T mm1, T m
     }
 }
 
+// One state's reverse map (one warp): log L from the range sums, the template components, and
+// per spline the moments gathered over the ranges, re-expanded about the knots (FP32 records:
+// they are about the midpoints) and pushed back through the Akima or natural-cubic construction,
+// in T (double, or float-float on the FP32 pipe).  Returns true, for the caller to redo the
+// state in FP64, where a sum, a moment or a gradient value is not finite (a float-float run
+// whose values left the FP32 exponent range); the FP64 run's return value is not used.
+// sX, sY: the warp's 64-double scratch rows; sRf, sRl: its kEpiRanges-double range-bound rows.
 template <int C, bool HAS_H, bool BROKEN, class T>
-__global__ void __launch_bounds__(128)
-    adjoint_epilogue_kernel(int S, const int32_t* __restrict__ state_ds, const DatasetDev* __restrict__ ds,
-                            const int32_t* __restrict__ sstat, const double* __restrict__ theta,
-                            const int32_t* __restrict__ count, const double* __restrict__ kx,
-                            const double* __restrict__ kw, int kmax, int kind, int nsp,
-                            const int64_t* __restrict__ prefix, const double* __restrict__ scal,
-                            const double* __restrict__ mom, const float* __restrict__ rec32,
-                            const double* __restrict__ rec64, const void* __restrict__ srec_v, int fp32,
-                            double* __restrict__ out_logL, double* __restrict__ grad, int32_t* __restrict__ fb,
-                            int fb_mode) {
-    __shared__ double sX[4][64];
-    __shared__ double sY[4][64];
-    // first and last bin's x of each adjoint range of the warp's dataset (the same for all its
-    // states and splines), for datasets of up to kEpiRanges ranges
-    __shared__ double sRf[4][kEpiRanges], sRl[4][kEpiRanges];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int s = blockIdx.x * 4 + warp;
-    if (s >= S) return;
-    // fb_mode 1 (the FP32 call): fb[s] = 1 where the state's FP32 sums or gradient are not finite
-    // (they left the FP32 range); fb_mode 2 (its FP64 fallback): only the flagged states
-    if (fb_mode == 2 && fb[s] == 0) return;
+__device__ __noinline__ bool epilogue_state(int s, const int32_t* __restrict__ state_ds,
+                                            const DatasetDev* __restrict__ ds, const int32_t* __restrict__ sstat,
+                                            const double* __restrict__ theta, const int32_t* __restrict__ count,
+                                            const double* __restrict__ kx, const double* __restrict__ kw, int kmax,
+                                            int kind, int nsp, const int64_t* __restrict__ prefix,
+                                            const double* __restrict__ scal, const double* __restrict__ mom,
+                                            const float* __restrict__ rec32, const double* __restrict__ rec64,
+                                            const void* __restrict__ srec_v, int fp32, double* __restrict__ out_logL,
+                                            double* __restrict__ grad, double* sX, double* sY, double* sRf,
+                                            double* sRl) {
+    constexpr bool kFF = std::is_same<T, spl::F2>::value;
+    const int lane = threadIdx.x & 31;
     const int G = LISA_N_THETA + nsp * (2 * kmax + 2);
     double* gs = grad + (size_t)s * G;
     for (int k = lane; k < G; k += 32) gs[k] = 0.0;
     __syncwarp();
     if (sstat[s] & kUserBits) {
-        if (lane == 0) {
-            out_logL[s] = -INFINITY;
-            if (fb_mode == 1) fb[s] = 0;
-        }
-        return;
+        if (lane == 0) out_logL[s] = -INFINITY;
+        return false;
     }
     const DatasetDev& D = ds[state_ds[s]];
     const int nr = D.nranges;
@@ -1021,20 +1119,14 @@ __global__ void __launch_bounds__(128)
     for (int k = 0; k < 6; ++k) v[k] = __shfl_sync(kFullMask, v[k], 0);
     double L = -v[0] - D.Cnu + D.K;
     const bool finite = isfinite(L);
-    if (fb_mode == 1) {
+    if (kFF) {
         bool sums_ok = finite;
         for (int k = 1; k < 6; ++k) sums_ok &= isfinite(v[k]);
-        if (!sums_ok) {
-            if (lane == 0) {
-                out_logL[s] = -INFINITY;
-                fb[s] = 1;
-            }
-            return;
-        }
+        if (!sums_ok) return true;
     }
     if (lane == 0) out_logL[s] = finite ? L : -INFINITY;
-    if (!finite) return;   // gradient stays zero
-    bool bad = false;      // a non-finite moment or gradient value (fb_mode 1)
+    if (!finite) return false;   // gradient stays zero
+    bool bad = false;            // a non-finite moment or gradient value
     // range bounds: in shared memory when they fit, else read per range below
     const bool staged = nr <= kEpiRanges;
     auto range_x = [&](int rho, double& xf, double& xlb) {
@@ -1050,7 +1142,7 @@ __global__ void __launch_bounds__(128)
         }
     };
     if (staged) {
-        for (int rho = lane; rho < nr; rho += 32) range_x(rho, sRf[warp][rho], sRl[warp][rho]);
+        for (int rho = lane; rho < nr; rho += 32) range_x(rho, sRf[rho], sRl[rho]);
         __syncwarp();
     }
     const double* th = theta + (size_t)s * LISA_N_THETA;
@@ -1068,7 +1160,7 @@ __global__ void __launch_bounds__(128)
         const int64_t sp = (int64_t)s * nsp + a;
         spl::WarpSpline<T> W;
         spl::warp_build_spline<T>(W, kx + sp * kmax, kw + sp * (kmax + 2), count[sp], kmax, kind, D.x_lo, D.x_hi,
-                               sX[warp], sY[warp]);
+                               sX, sY);
         if (W.st) continue;
         const int K = W.K;
         const int nint = K - 1;
@@ -1101,7 +1193,7 @@ __global__ void __launch_bounds__(128)
                     int lo = 0, hi = nr;
                     while (lo < hi) {
                         const int mid = (lo + hi) >> 1;
-                        if (sRl[warp][mid] >= lo_b) hi = mid; else lo = mid + 1;
+                        if (sRl[mid] >= lo_b) hi = mid; else lo = mid + 1;
                     }
                     r0 = lo;
                 }
@@ -1109,7 +1201,7 @@ __global__ void __launch_bounds__(128)
                     int lo = 0, hi = nr;
                     while (lo < hi) {
                         const int mid = (lo + hi) >> 1;
-                        if (sRf[warp][mid] < hi_b) lo = mid + 1; else hi = mid;
+                        if (sRf[mid] < hi_b) lo = mid + 1; else hi = mid;
                     }
                     r1 = lo - 1;
                 }
@@ -1284,13 +1376,44 @@ __global__ void __launch_bounds__(128)
             }
         }
     }
-    if (fb_mode == 1) {
-        // (the template components were written by lane 0, which checks them)
-        if (lane == 0)
-            for (int k = 0; k < LISA_N_THETA; ++k) bad |= !isfinite(gs[k]);
-        bad = __any_sync(kFullMask, bad);
-        if (lane == 0) fb[s] = bad ? 1 : 0;
-    }
+    // (the template components were written by lane 0, which checks them)
+    if (lane == 0)
+        for (int k = 0; k < LISA_N_THETA; ++k) bad |= !isfinite(gs[k]);
+    return __any_sync(kFullMask, bad);
+}
+
+// One warp per state.  The FP32 call runs the reverse map in float-float and redoes in FP64 the
+// states its adjoint passes flagged (fb[s]: sums beyond the FP32 range, recomputed by the
+// fallback pass) and those whose float-float values are not finite; the FP64 call runs FP64.
+// 4 CTAs of 128 threads per SM (128 registers) keep 2,432 states resident at once.
+template <int C, bool HAS_H, bool BROKEN>
+__global__ void __launch_bounds__(128, 4)
+    adjoint_epilogue_kernel(int S, const int32_t* __restrict__ state_ds, const DatasetDev* __restrict__ ds,
+                            const int32_t* __restrict__ sstat, const double* __restrict__ theta,
+                            const int32_t* __restrict__ count, const double* __restrict__ kx,
+                            const double* __restrict__ kw, int kmax, int kind, int nsp,
+                            const int64_t* __restrict__ prefix, const double* __restrict__ scal,
+                            const double* __restrict__ mom, const float* __restrict__ rec32,
+                            const double* __restrict__ rec64, const void* __restrict__ srec_v, int fp32,
+                            double* __restrict__ out_logL, double* __restrict__ grad,
+                            const int32_t* __restrict__ fb) {
+    __shared__ double sX[4][64];
+    __shared__ double sY[4][64];
+    // first and last bin's x of each adjoint range of the warp's dataset (the same for all its
+    // states and splines), for datasets of up to kEpiRanges ranges
+    __shared__ double sRf[4][kEpiRanges], sRl[4][kEpiRanges];
+    const int warp = threadIdx.x >> 5;
+    const int s = blockIdx.x * 4 + warp;
+    if (s >= S) return;
+    bool redo = !fp32 || fb[s] != 0;
+    if (!redo)
+        redo = epilogue_state<C, HAS_H, BROKEN, spl::F2>(s, state_ds, ds, sstat, theta, count, kx, kw, kmax, kind,
+                                                         nsp, prefix, scal, mom, rec32, rec64, srec_v, fp32,
+                                                         out_logL, grad, sX[warp], sY[warp], sRf[warp], sRl[warp]);
+    if (redo)
+        epilogue_state<C, HAS_H, BROKEN, double>(s, state_ds, ds, sstat, theta, count, kx, kw, kmax, kind, nsp,
+                                                 prefix, scal, mom, rec32, rec64, srec_v, fp32, out_logL, grad,
+                                                 sX[warp], sY[warp], sRf[warp], sRl[warp]);
 }
 
 // Whether every dataset meets the EXACT_T condition of adjoint_fp32_kernel.
@@ -1318,13 +1441,13 @@ inline size_t range_smem(const lisa_data* d, int kmax, int nwarps) {
     return sizeof(double) * (size_t)nwarps * (size_t)d->nsp * (size_t)(kmax + 1) * 4;
 }
 
-// The gradient workspace's arrays for one call (fb, buf64: FP32 calls only).
+// The gradient workspace's arrays for one call (fb: FP32 calls only).
 struct GradWs {
     double* scal;
     double* mom;
-    int32_t* fb;
-    void* buf64;
+    int32_t* fb;          // FP32 calls: flags, count and list of the fallback states (fb_flag)
     const float2* hull;   // FP32 calls: the spline buffer's ill-conditioned x-extent per state
+    const int32_t* route; // FP32 calls: the spline buffer's route count and list
 };
 
 template <int C, bool H, bool B>
@@ -1335,26 +1458,47 @@ cudaError_t launch_adjoint(const lisa_data* d, bool fp32, const lisa_params* par
     double* mom = gw.mom;
     const int grid = d->n_sm * 8;
     const bool prof = prof_active(d, sm);
+    const int S = (int)d->n_states;
+    const int R = adj_max_ranges(d);
     prof_mark(d, prof, 0, sm);
+    if (fp32 && cudaMemsetAsync(gw.fb, 0, sizeof(int32_t) * ((size_t)S + 1), sm) != cudaSuccess)
+        return cudaErrorInvalidValue;
     if (d->n_adj_units > 0) {
         if (fp32 && adj_exact_t(d))
             adjoint_fp32_kernel<C, H, B, true><<<grid, 128, 0, sm>>>(
                 d->d_adj_units, d->n_adj_units, d->d_ds, d->d_rec32, d->d_xlo32, params->theta_dev, sstat, nint,
-                static_cast<const float*>(srec), kn->kmax, d->nsp, d->d_adj_prefix, scal, mom);
+                static_cast<const float*>(srec), kn->kmax, d->nsp, d->d_adj_prefix, scal, mom, S, gw.fb);
         else if (fp32)
             adjoint_fp32_kernel<C, H, B, false><<<grid, 128, 0, sm>>>(
                 d->d_adj_units, d->n_adj_units, d->d_ds, d->d_rec32, d->d_xlo32, params->theta_dev, sstat, nint,
-                static_cast<const float*>(srec), kn->kmax, d->nsp, d->d_adj_prefix, scal, mom);
+                static_cast<const float*>(srec), kn->kmax, d->nsp, d->d_adj_prefix, scal, mom, S, gw.fb);
+        prof_mark(d, prof, 1, sm);
         if (fp32) {
-            // the bins of ill-conditioned intervals (routed states), masked above
+            // the bins of ill-conditioned intervals (routed states), masked above: the route
+            // list's (state, range) items on a resident grid
             const size_t smc = range_smem(d, kn->kmax, 4);
             if (cudaFuncSetAttribute(adjoint_range_kernel<C, H, B, kComp>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)smc) != cudaSuccess)
                 return cudaErrorInvalidValue;
-            adjoint_range_kernel<C, H, B, kComp>
-                <<<dim3((unsigned)d->n_states, (unsigned)adj_max_ranges(d)), 128, smc, sm>>>(
-                (int)d->n_states, d->d_state_ds, d->d_ds, d->d_rec32, d->d_xlo32, d->d_rec64, params->theta_dev, sstat,
-                nullptr, nint, srec, gw.hull, kn->kmax, d->nsp, d->d_adj_prefix, scal, mom);
+            int occ = 0;
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, adjoint_range_kernel<C, H, B, kComp>, 128, smc) !=
+                cudaSuccess)
+                return cudaErrorInvalidValue;
+            adjoint_range_kernel<C, H, B, kComp><<<d->n_sm * std::max(occ, 1), 128, smc, sm>>>(
+                S, d->d_state_ds, d->d_ds, d->d_rec32, d->d_xlo32, d->d_elllo32, params->theta_dev, sstat, gw.route,
+                R, gw.fb, nint, srec, gw.hull, kn->kmax, d->nsp, d->d_adj_prefix, scal, mom);
+            // the states whose FP32 sums left the FP32 range (flagged by both passes above): all
+            // their bins again, FP64 sums, on a resident grid of 16-warp CTAs
+            const size_t smf = range_smem(d, kn->kmax, 16);
+            if (cudaFuncSetAttribute(adjoint_range_kernel<C, H, B, kFallback>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smf) != cudaSuccess)
+                return cudaErrorInvalidValue;
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, adjoint_range_kernel<C, H, B, kFallback>, 512,
+                                                              smf) != cudaSuccess)
+                return cudaErrorInvalidValue;
+            adjoint_range_kernel<C, H, B, kFallback><<<d->n_sm * std::max(occ, 1), 512, smf, sm>>>(
+                S, d->d_state_ds, d->d_ds, d->d_rec32, d->d_xlo32, d->d_elllo32, params->theta_dev, sstat,
+                gw.fb + S, R, gw.fb, nint, srec, nullptr, kn->kmax, d->nsp, d->d_adj_prefix, scal, mom);
         } else
             adjoint_fp64_kernel<C, H, B><<<grid, 128, 0, sm>>>(d->d_adj_units, d->n_adj_units, d->d_ds, d->d_rec64,
                                                                params->theta_dev, sstat, nint,
@@ -1362,38 +1506,15 @@ cudaError_t launch_adjoint(const lisa_data* d, bool fp32, const lisa_params* par
                                                                d->d_adj_prefix, scal, mom);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
+    } else {
+        prof_mark(d, prof, 1, sm);
     }
-    prof_mark(d, prof, 1, sm);
     prof_mark(d, prof, 2, sm);
     const unsigned eb = (unsigned)((d->n_states + 3) / 4);
-    (fp32 ? adjoint_epilogue_kernel<C, H, B, spl::F2> : adjoint_epilogue_kernel<C, H, B, double>)<<<eb, 128, 0, sm>>>(
-        (int)d->n_states, d->d_state_ds, d->d_ds, sstat, params->theta_dev, kn->count_dev, kn->x_dev, kn->w_dev,
-        kn->kmax, kn->kind, d->nsp, d->d_adj_prefix, scal, mom, d->d_rec32, d->d_rec64, srec, fp32 ? 1 : 0, out,
-        grad, gw.fb, fp32 ? 1 : 0);
-    cudaError_t e = cudaGetLastError();
-    if (e == cudaSuccess && fp32 && d->n_adj_units > 0) {
-        // states whose FP32 sums left the FP32 range (flagged by the epilogue): FP64 spline records,
-        // the FP64 adjoint and the FP64 epilogue for them alone (the others exit at once)
-        const SplineLayout L64 = spline_layout(d->n_states, d->nsp, kn->kmax);
-        const char* b64 = static_cast<const char*>(gw.buf64);
-        e = launch_setup_fp64_subset(d, kn, gw.buf64, gw.fb, sm);
-        if (e == cudaSuccess) {
-            const size_t smf = range_smem(d, kn->kmax, 16);
-            if (cudaFuncSetAttribute(adjoint_range_kernel<C, H, B, kFallback>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smf) != cudaSuccess)
-                return cudaErrorInvalidValue;
-            adjoint_range_kernel<C, H, B, kFallback>
-                <<<dim3((unsigned)d->n_states, (unsigned)adj_max_ranges(d)), 512, smf, sm>>>(
-                (int)d->n_states, d->d_state_ds, d->d_ds, d->d_rec32, d->d_xlo32, d->d_rec64, params->theta_dev, sstat,
-                gw.fb, reinterpret_cast<const int32_t*>(b64 + L64.off_nint), b64 + L64.off_rec, nullptr, kn->kmax,
-                d->nsp, d->d_adj_prefix, scal, mom);
-            adjoint_epilogue_kernel<C, H, B, double><<<eb, 128, 0, sm>>>(
-                (int)d->n_states, d->d_state_ds, d->d_ds, sstat, params->theta_dev, kn->count_dev, kn->x_dev,
-                kn->w_dev, kn->kmax, kn->kind, d->nsp, d->d_adj_prefix, scal, mom, d->d_rec32, d->d_rec64,
-                b64 + L64.off_rec, 0, out, grad, gw.fb, 2);
-            e = cudaGetLastError();
-        }
-    }
+    adjoint_epilogue_kernel<C, H, B><<<eb, 128, 0, sm>>>(
+        S, d->d_state_ds, d->d_ds, sstat, params->theta_dev, kn->count_dev, kn->x_dev, kn->w_dev, kn->kmax, kn->kind,
+        d->nsp, d->d_adj_prefix, scal, mom, d->d_rec32, d->d_rec64, srec, fp32 ? 1 : 0, out, grad, gw.fb);
+    const cudaError_t e = cudaGetLastError();
     prof_mark(d, prof, 3, sm);
     if (prof) d->prof_valid = true;
     return e;
@@ -1443,8 +1564,8 @@ extern "C" lisa_status lisa_psd_loglike_grad(const lisa_data* d, const lisa_para
     gw.scal = reinterpret_cast<double*>(w + GL.off_scal);
     gw.mom = reinterpret_cast<double*>(w + GL.off_mom);
     gw.fb = fp32 ? reinterpret_cast<int32_t*>(w + GL.off_fb) : nullptr;
-    gw.buf64 = fp32 ? w + GL.off_buf64 : nullptr;
     gw.hull = reinterpret_cast<const float2*>(base + L.off_hull);
+    gw.route = reinterpret_cast<const int32_t*>(base + L.off_route);
     cudaStream_t sm = (cudaStream_t)stream;
     cudaError_t e = d->C == 3 ? dispatch_adjoint<3>(d, fp32, params, kn, sstat, nint, srec, gw, out, grad, sm)
                               : dispatch_adjoint<2>(d, fp32, params, kn, sstat, nint, srec, gw, out, grad, sm);

@@ -47,9 +47,7 @@ constexpr int kMaxStatesPerItem = 128;  // state lanes of a work item (<= both t
 //   FP32: [0] xr  [1] xo  [2..5] c0..c3  [6] xl  [7] conditioning T      (first 32 bytes)
 //         [8] xo_lo  [9..12] c0..c3 low parts  [13..15] 0                (second 32 bytes)
 //         coefficients about the interval midpoint xo, scaled to log2 units; hi + lo is the
-//         FP64 value split into two floats (the coefficients' lo parts only where the
-//         compensated kernel reads them: in the setup pass of an ill-conditioned interval,
-//         zero elsewhere).
+//         float-float value split into two floats.
 constexpr int kSplineRec = 8;    // doubles per FP64 record
 constexpr int kSplineRec32 = 16; // floats per FP32 record
 // States whose FP32 perturbation spline has an interval with conditioning
@@ -242,11 +240,8 @@ inline WsLayout ws_layout(const lisa_data* d) {
 inline size_t ws_fwd_bytes(const lisa_data* d) { return ws_layout(d).bytes; }
 
 // Extra workspace of the adjoint entry point (after the forward region); the FP32 call also holds
-// the FP64 fallback (a per-state flag and an FP64 spline buffer).
+// a per-state flag (states redone by the fallback pass).
 size_t grad_extra_bytes(const lisa_data* d, int kmax, bool fp32);
-// FP64 spline records of the states with only[s] != 0 (the FP32 adjoint's fallback).
-cudaError_t launch_setup_fp64_subset(const lisa_data* d, const lisa_knots* kn, void* buf64, const int32_t* only,
-                                     cudaStream_t sm);
 
 lisa_status rebuild_work(lisa_data* d);
 // The dense-covariance likelihood kernel (LISA_COV_FULL) for the model of d, FP32 bulk or FP64.

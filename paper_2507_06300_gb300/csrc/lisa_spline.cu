@@ -16,9 +16,8 @@ namespace {
 //                coefficients scaled to log2 units as hi floats, plus the interval's
 //                conditioning bound T; a state with any T > kRobustT is appended to the route
 //                list (compensated kernel).  The lo floats of the coefficients (float-float value
-//                - hi) are kept only for the intervals handled in the same pass (intervals 0-31,
-//                32-63) as an ill-conditioned one, the only ones that read them, and are zero
-//                elsewhere.
+//                - hi) complete every record: the compensated kernels and the gradient's
+//                fallback pass evaluate the spline from hi + lo.
 // 7 CTAs per SM (at most 72 registers) keep 1,064 states resident at once.
 // kMaxSp: splines per state the launch allows (4 for the diagonal covariance, 8 for the full one,
 // which has seven); do_route = 0 leaves the routing bit unset (the full-covariance FP32 kernel
@@ -29,7 +28,7 @@ __global__ void __launch_bounds__(32 * kMaxSp, kMaxSp == 4 ? 7 : 3) spline_setup
     int S, int nsp, int kmax, int kind, const int32_t* __restrict__ state_ds,
     const DatasetDev* __restrict__ ds, int32_t* __restrict__ status_buf, int32_t* __restrict__ nint_buf,
     int32_t* __restrict__ route, void* __restrict__ rec_v, float2* __restrict__ hull,
-    float* __restrict__ kxr, int32_t* __restrict__ status_out, int do_route, const int32_t* __restrict__ only) {
+    float* __restrict__ kxr, int32_t* __restrict__ status_out, int do_route) {
     using T = double;
     __shared__ T sX[kMaxSp][64];
     __shared__ T sY[kMaxSp][64];
@@ -38,7 +37,6 @@ __global__ void __launch_bounds__(32 * kMaxSp, kMaxSp == 4 ? 7 : 3) spline_setup
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
     const int s = blockIdx.x;
-    if (only && only[s] == 0) return;   // a subset run: this state is not in it (uniform per CTA)
     const int dsi = state_ds[s];
     const double xlo = ds[dsi].x_lo, xhi = ds[dsi].x_hi;
     const float xbmin_f = (float)ds[dsi].xb_min, xbmax_f = (float)ds[dsi].xb_max;
@@ -107,9 +105,6 @@ __global__ void __launch_bounds__(32 * kMaxSp, kMaxSp == 4 ? 7 : 3) spline_setup
                         hlo = fminf(hlo, j == 0 ? -INFINITY : xl_f);
                         hhi = fmaxf(hhi, last ? INFINITY : xr_f);
                     }
-                    // the coefficients' low parts are read only on ill-conditioned intervals:
-                    // formed when the warp has one, zero otherwise
-                    const bool any_hard = __any_sync(spl::kFull, hard);
                     if (!valid) continue;
                     float* r = static_cast<float*>(rec_v) + (sp * (int64_t)(kmax + 1) + j) * kSplineRec32;
                     r[0] = last ? INFINITY : xr_f;
@@ -120,7 +115,7 @@ __global__ void __launch_bounds__(32 * kMaxSp, kMaxSp == 4 ? 7 : 3) spline_setup
                     r[8] = xo.lo;
                     for (int c = 0; c < 4; ++c) {
                         r[2 + c] = chi[c];
-                        r[9 + c] = any_hard ? cs[c].lo : 0.f;
+                        r[9 + c] = cs[c].lo;
                     }
                     r[13] = r[14] = r[15] = 0.f;
                 }
@@ -174,32 +169,6 @@ __global__ void __launch_bounds__(32 * kMaxSp, kMaxSp == 4 ? 7 : 3) spline_setup
 }  // namespace
 }  // namespace lisa
 
-namespace lisa {
-// FP64 spline records of the states with only[s] != 0, into the spline buffer buf64 (layout of
-// spline_layout(S, nsp, kmax)); the other states' entries are left untouched.  No routing.
-cudaError_t launch_setup_fp64_subset(const lisa_data* d, const lisa_knots* kn, void* buf64, const int32_t* only,
-                                     cudaStream_t sm) {
-    const SplineLayout L = spline_layout(d->n_states, d->nsp, kn->kmax);
-    char* base = static_cast<char*>(buf64);
-    int32_t* status_buf = reinterpret_cast<int32_t*>(base + L.off_status);
-    int32_t* nint_buf = reinterpret_cast<int32_t*>(base + L.off_nint);
-    int32_t* route = reinterpret_cast<int32_t*>(base + L.off_route);
-    float2* hull = reinterpret_cast<float2*>(base + L.off_hull);
-    float* kxr = reinterpret_cast<float*>(base + L.off_kxr);
-    void* rec = base + L.off_rec;
-    const unsigned blocks = (unsigned)d->n_states, threads = 32u * (unsigned)d->nsp;
-    if (d->nsp <= 4)
-        spline_setup_kernel<false, 4><<<blocks, threads, 0, sm>>>(
-            kn->count_dev, kn->x_dev, kn->w_dev, (int)d->n_states, d->nsp, kn->kmax, kn->kind, d->d_state_ds, d->d_ds,
-            status_buf, nint_buf, route, rec, hull, kxr, nullptr, 0, only);
-    else
-        spline_setup_kernel<false, 8><<<blocks, threads, 0, sm>>>(
-            kn->count_dev, kn->x_dev, kn->w_dev, (int)d->n_states, d->nsp, kn->kmax, kn->kind, d->d_state_ds, d->d_ds,
-            status_buf, nint_buf, route, rec, hull, kxr, nullptr, 0, only);
-    return cudaGetLastError();
-}
-}  // namespace lisa
-
 using namespace lisa;
 
 extern "C" lisa_status lisa_spline_setup(const lisa_data* d, const lisa_knots* kn, lisa_precision prec,
@@ -231,20 +200,20 @@ extern "C" lisa_status lisa_spline_setup(const lisa_data* d, const lisa_knots* k
         if (prec == LISA_FP64)
             spline_setup_kernel<false, 4><<<blocks, threads, 0, sm>>>(
                 kn->count_dev, kn->x_dev, kn->w_dev, (int)d->n_states, d->nsp, kn->kmax, kn->kind, d->d_state_ds,
-                d->d_ds, status_buf, nint_buf, route, rec, hull, kxr, status_out, do_route, nullptr);
+                d->d_ds, status_buf, nint_buf, route, rec, hull, kxr, status_out, do_route);
         else
             spline_setup_kernel<true, 4><<<blocks, threads, 0, sm>>>(
                 kn->count_dev, kn->x_dev, kn->w_dev, (int)d->n_states, d->nsp, kn->kmax, kn->kind, d->d_state_ds,
-                d->d_ds, status_buf, nint_buf, route, rec, hull, kxr, status_out, do_route, nullptr);
+                d->d_ds, status_buf, nint_buf, route, rec, hull, kxr, status_out, do_route);
     } else {
         if (prec == LISA_FP64)
             spline_setup_kernel<false, 8><<<blocks, threads, 0, sm>>>(
                 kn->count_dev, kn->x_dev, kn->w_dev, (int)d->n_states, d->nsp, kn->kmax, kn->kind, d->d_state_ds,
-                d->d_ds, status_buf, nint_buf, route, rec, hull, kxr, status_out, do_route, nullptr);
+                d->d_ds, status_buf, nint_buf, route, rec, hull, kxr, status_out, do_route);
         else
             spline_setup_kernel<true, 8><<<blocks, threads, 0, sm>>>(
                 kn->count_dev, kn->x_dev, kn->w_dev, (int)d->n_states, d->nsp, kn->kmax, kn->kind, d->d_state_ds,
-                d->d_ds, status_buf, nint_buf, route, rec, hull, kxr, status_out, do_route, nullptr);
+                d->d_ds, status_buf, nint_buf, route, rec, hull, kxr, status_out, do_route);
     }
     return check_cuda(cudaGetLastError());
 }
