@@ -37,11 +37,12 @@ WORKLOAD = ("paper-scale: A,E,T; 131,072 uniform bins 0.1-29 mHz; Nseg=64; OMS 1
 # SGWB.  MUFU: 4 ex2 (three noise perturbations, one SGWB perturbation x power law), 1 rcp (fused
 # reciprocal sum), 1 lg2 (fused log of the product).  FP32 (FMA pipe, an FMA counted once):
 # 4 splines x (1 shift + 3 Horner FMA) = 16, SGWB exponent and amplitude 2, per channel noise
-# (2) and PSD (2) = 12, channel product and reciprocal-sum numerator 4, reciprocal-sum FMA,
-# log FMA and nu scale 3, accumulation 1.
+# (2) and PSD (2) = 12, channel product and reciprocal-sum numerator 4, reciprocal-sum FMA and
+# the two nu-weighted accumulations (of the reciprocal sum and of the log) 3; ln2 and the keep
+# factor are applied once per 64-bin chunk.
 MUFU_EX2, MUFU_RCP, MUFU_LG2 = 4, 1, 1
 MUFU_PER_STATE_BIN = MUFU_EX2 + MUFU_RCP + MUFU_LG2
-FP32_PER_STATE_BIN = 38
+FP32_PER_STATE_BIN = 37
 TABLE_BYTES_PER_BIN = 12 * 4          # FP32 bin table: x, ell, nu, 3 x (G_oms, G_tm, G_h)
 # The FP32 adjoint kernel per state-bin, as implemented: per spline a compensated t (two-sum and
 # low parts, 9), Horner 3 and moments 6 = 72; SGWB exponent and amplitude 2; per channel noise 2,
@@ -229,7 +230,7 @@ def host_mem_available_gb():
 
 def roofs(rates, hbm_gbs, bytes_per_state_bin):
     """Ceilings in state-bins/s of the fused kernel from the measured pipe rates: the MUFU pipe
-    (the kernel's mix of 4 ex2, 1 rcp, 1 lg2), the FP32 FMA pipe (38 ops, packed FMAs counted as
+    (the kernel's mix of 4 ex2, 1 rcp, 1 lg2), the FP32 FMA pipe (37 ops, packed FMAs counted as
     two lane operations) and HBM (algorithmic bytes per state-bin)."""
     t_ex2, t_rcp = 1.0 / rates["ex2"], 1.0 / rates["rcp"]
     t_lg2 = 2.0 / rates["lg2_ex2"] - t_ex2
@@ -537,7 +538,7 @@ def run_ours(args):
                     # two pipes overlap only in part, so the mix is slower than either pipe alone
                     "mixed_pipe": {"ceiling_state_bins_per_s": rates["mix"], "frac": fused_rate / rates["mix"],
                                    "ceiling_vs_fp32_alone": rates["mix"] / R["fp32"],
-                                   "mix": "per two state-bins: 38 packed FP32 ops, 8 ex2, 2 rcp, 2 lg2",
+                                   "mix": "per two state-bins: 37 packed FP32 ops, 8 ex2, 2 rcp, 2 lg2",
                                    "source": "lisa_pipe_rates LISA_PIPE_MIX, measured live"},
                     "mufu_frac": fused_rate / R["mufu"], "hbm_frac": fused_rate / R["hbm"],
                     "step_frac": (r["value"] / world) / min(R["fp32"], R["mufu"], R["hbm"]),

@@ -50,6 +50,11 @@ class lisa_knots(ctypes.Structure):
                 ("count_dev", _c_vp), ("x_dev", _c_vp), ("w_dev", _c_vp)]
 
 
+class lisa_bounds_report(ctypes.Structure):
+    _fields_ = [("count", _c_i64), ("first_index", _c_i64), ("first_line", _c_i32),
+                ("first_file", ctypes.c_char * 96)]
+
+
 class lisa_tiling(ctypes.Structure):
     _fields_ = [("tile_bins", _c_i32), ("states_per_cta", _c_i32), ("group", _c_i32), ("ctas_per_sm", _c_i32)]
 
@@ -64,7 +69,8 @@ EXPORTS = ["lisa_data_create", "lisa_data_destroy", "lisa_data_get_info", "lisa_
            "lisa_spline_buf_bytes", "lisa_spline_setup", "lisa_workspace_bytes", "lisa_psd_loglike",
            "lisa_psd_loglike_grad", "lisa_model_psd", "lisa_psd_loglike_noalloc", "lisa_status_string",
            "lisa_pipe_rates", "lisa_data_set_profiling", "lisa_data_kernel_ms", "lisa_fd_synthesize",
-           "lisa_averaged_periodogram", "lisa_workspace_status", "lisa_data_set_test_wait"]
+           "lisa_averaged_periodogram", "lisa_workspace_status", "lisa_data_set_test_wait",
+           "lisa_debug_bounds_enabled", "lisa_debug_bounds", "lisa_debug_bounds_selftest"]
 PIPE_OPS = ("ex2", "rcp", "lg2_ex2", "ffma", "ffma2", "dfma", "mix")   # order of lisa_pipe_op
 NOALLOC_SCRATCH_BYTES = 4 * 1024 * 1024
 
@@ -76,21 +82,30 @@ class LisaError(RuntimeError):
     pass
 
 
+def debug_requested() -> bool:
+    """True when the environment asks for the bounds-checked library (``LISA_DEBUG_BOUNDS=1``)."""
+    return os.environ.get("LISA_DEBUG_BOUNDS", "") not in ("", "0")
+
+
 def library_path() -> str:
-    return _build.LIB
+    return _build.LIB_DEBUG if debug_requested() else _build.LIB
 
 
 def load(build_if_missing: bool = True) -> ctypes.CDLL:
-    """Loads the CUDA library (building it in-tree if needed).  Raises if it cannot."""
+    """Loads the CUDA library (building it in-tree if needed): ``liblisa_psd.so``, or the
+    bounds-checked ``liblisa_psd_debug.so`` when ``LISA_DEBUG_BOUNDS=1`` is set before the first
+    call.  Raises if it cannot."""
     global _lib
     with _lock:
         if _lib is not None:
             return _lib
-        if not os.path.exists(_build.LIB) or not _build.up_to_date():
+        debug = debug_requested()
+        path = library_path()
+        if not os.path.exists(path) or not _build.up_to_date(debug):
             if not build_if_missing:
-                raise LisaError(f"CUDA library not built: {_build.LIB}")
-            _build.build()
-        lib = ctypes.CDLL(_build.LIB)
+                raise LisaError(f"CUDA library not built: {path}")
+            _build.build(debug=debug)
+        lib = ctypes.CDLL(path)
         S = _c_i32  # enum lisa_status
         lib.lisa_data_create.argtypes = [ctypes.POINTER(lisa_data_desc), _c_vp, ctypes.POINTER(_c_vp)]
         lib.lisa_data_create.restype = S
@@ -134,8 +149,34 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         lib.lisa_workspace_status.restype = S
         lib.lisa_data_set_test_wait.argtypes = [_c_vp, _c_i32, ctypes.c_uint32]
         lib.lisa_data_set_test_wait.restype = S
+        lib.lisa_debug_bounds_enabled.argtypes = []
+        lib.lisa_debug_bounds_enabled.restype = _c_i32
+        lib.lisa_debug_bounds.argtypes = [_c_i32, ctypes.POINTER(lisa_bounds_report)]
+        lib.lisa_debug_bounds.restype = S
+        lib.lisa_debug_bounds_selftest.argtypes = [_c_vp]
+        lib.lisa_debug_bounds_selftest.restype = S
         _lib = lib
         return lib
+
+
+def debug_bounds_enabled() -> bool:
+    """``lisa_debug_bounds_enabled``: whether the loaded library checks its indices."""
+    return bool(load().lisa_debug_bounds_enabled())
+
+
+def debug_bounds(reset: bool = False) -> dict:
+    """``lisa_debug_bounds``: index violations since the last reset (synchronises the device)."""
+    r = lisa_bounds_report()
+    _check(load().lisa_debug_bounds(1 if reset else 0, ctypes.byref(r)), "lisa_debug_bounds")
+    return {"count": int(r.count), "first_index": int(r.first_index), "first_line": int(r.first_line),
+            "first_file": r.first_file.decode(errors="replace")}
+
+
+def debug_bounds_selftest(stream=None) -> None:
+    """``lisa_debug_bounds_selftest`` on ``stream`` (a torch stream; default: the current one)."""
+    import torch
+    st = stream if stream is not None else torch.cuda.current_stream()
+    _check(load().lisa_debug_bounds_selftest(ctypes.c_void_p(st.cuda_stream)), "lisa_debug_bounds_selftest")
 
 
 def _check(st: int, what: str):

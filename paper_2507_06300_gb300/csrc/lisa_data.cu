@@ -4,9 +4,11 @@
 #include <queue>
 #include <utility>
 #include <cmath>
+#include <cstdio>
 #include <new>
 
 #include "lisa_internal.cuh"
+#include "lisa_debug.h"
 #include "lisa_peaks.h"
 
 namespace lisa {
@@ -335,6 +337,60 @@ using namespace lisa;
 
 extern "C" {
 
+#ifdef LISA_DEBUG_BOUNDS
+namespace lisa {
+namespace dbg {
+namespace {
+// Stores to buf[LISA_IDX(5 + lane, 4)]: every index is out of range and clamped to 3.
+__global__ void bounds_selftest_kernel(float* buf) {
+    const int i = LISA_IDX((int)threadIdx.x + 5, 4);
+    buf[i] = (float)threadIdx.x;
+}
+}  // namespace
+}  // namespace dbg
+}  // namespace lisa
+#endif
+
+int32_t lisa_debug_bounds_enabled(void) { return lisa::dbg::kBoundsChecked ? 1 : 0; }
+
+lisa_status lisa_debug_bounds(int32_t reset, lisa_bounds_report* out) {
+    if (!out) return LISA_ERR_NULL;
+    using Reader = cudaError_t (*)(lisa::dbg::BoundsRecord*, int, const char**);
+    const Reader readers[] = {lisa::dbg::read_data, lisa::dbg::read_full,  lisa::dbg::read_grad,
+                              lisa::dbg::read_loglike, lisa::dbg::read_peaks, lisa::dbg::read_prep,
+                              lisa::dbg::read_spline};
+    lisa_bounds_report r = {};
+    for (Reader rd : readers) {
+        lisa::dbg::BoundsRecord b = {};
+        const char* file = "";
+        if (rd(&b, reset, &file) != cudaSuccess) return LISA_ERR_CUDA;
+        if (b.count > 0 && r.count == 0) {
+            r.first_index = b.first_index;
+            r.first_line = b.first_line;
+            std::snprintf(r.first_file, sizeof(r.first_file), "%s", file);
+        }
+        r.count += (int64_t)b.count;
+    }
+    *out = r;
+    return LISA_SUCCESS;
+}
+
+lisa_status lisa_debug_bounds_selftest(lisa_stream_t stream) {
+#ifdef LISA_DEBUG_BOUNDS
+    float* buf = nullptr;
+    if (cudaMalloc(&buf, 4 * sizeof(float)) != cudaSuccess) return LISA_ERR_ALLOC;
+    cudaStream_t sm = (cudaStream_t)stream;
+    lisa::dbg::bounds_selftest_kernel<<<1, 32, 0, sm>>>(buf);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(sm);
+    cudaFree(buf);
+    return e == cudaSuccess ? LISA_SUCCESS : LISA_ERR_CUDA;
+#else
+    (void)stream;
+    return LISA_ERR_VALUE;
+#endif
+}
+
 const char* lisa_status_string(lisa_status s) {
     switch (s) {
         case LISA_SUCCESS: return "success";
@@ -590,3 +646,5 @@ size_t lisa_spline_buf_bytes(const lisa_data* d, int32_t kmax, lisa_precision p)
 }
 
 }  // extern "C"
+
+LISA_DEBUG_TU(data)

@@ -74,7 +74,7 @@ __global__ void __launch_bounds__(kThreads)
     __shared__ double red[kThreads];
     const int tid = threadIdx.x;
     for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
-        const WorkItem w = items[it];
+        const WorkItem w = items[LISA_IDX(it, n_items)];
         const int sc = w.sc;
         const int R = kThreads / sc;
         const int ls = tid & (sc - 1);
@@ -97,7 +97,7 @@ __global__ void __launch_bounds__(kThreads)
                     base[a] = srec + sp * (int64_t)(kmax + 1) * kSplineRec;
                     last[a] = nint[sp] - 1;
                     j[a] = find_interval<double, kSplineRec, 0>(base[a], nint[sp], x0);
-                    const double* z = base[a] + (size_t)j[a] * kSplineRec;
+                    const double* z = base[a] + (size_t)LISA_IDX(j[a], kmax + 1) * kSplineRec;
                     xl[a] = z[0]; xr[a] = z[1]; ca[a] = z[2]; cb[a] = z[3]; cc[a] = z[4]; cd[a] = z[5];
                 }
                 for (int i = lo; i < hi; ++i) {
@@ -109,7 +109,7 @@ __global__ void __launch_bounds__(kThreads)
                     for (int a = 0; a < NSP; ++a) {
                         while (x >= xr[a] && j[a] < last[a]) {
                             ++j[a];
-                            const double* z = base[a] + (size_t)j[a] * kSplineRec;
+                            const double* z = base[a] + (size_t)LISA_IDX(j[a], kmax + 1) * kSplineRec;
                             xl[a] = z[0]; xr[a] = z[1]; ca[a] = z[2]; cb[a] = z[3]; cc[a] = z[4]; cd[a] = z[5];
                         }
                         const double t = x - xl[a];
@@ -289,7 +289,7 @@ __global__ void __launch_bounds__(kFullThreads, 4)
         const int nxt = it + gridDim.x;
         if (nxt < n_items && tid == 0 && !s_fail)
             stage_item(sb[b ^ 1], rec32, cross32, items[nxt], tile_bins, &bars[b ^ 1]);
-        const WorkItem w = items[it];
+        const WorkItem w = items[LISA_IDX(it, n_items)];
         const bool ok = bar_wait(&bars[b], (unsigned)(k >> 1) & 1u, wait_limit);
         if (!ok) {
             s_fail = 1;   // read by thread 0 after the next barrier
@@ -311,7 +311,7 @@ __global__ void __launch_bounds__(kFullThreads, 4)
         const StateParams p = prm[run_bins ? s : w.s0];
         const float ao2 = p.ao2, at2 = p.at2, Af = HAS_H ? p.Af : 0.f;
         auto rec = [&](int a, int j) {
-            return srec + (((int64_t)s * nsp + a) * (int64_t)(kmax + 1) + j) * kSplineRec32;
+            return srec + (((int64_t)s * nsp + a) * (int64_t)(kmax + 1) + LISA_IDX(j, kmax + 1)) * kSplineRec32;
         };
         auto install = [&](int a, int j) {
             const float4 A = __ldg(reinterpret_cast<const float4*>(rec(a, j)));
@@ -593,3 +593,5 @@ cudaError_t launch_full_cov(const lisa_data* d, bool fp32, const double* theta, 
 }
 
 }  // namespace lisa
+
+LISA_DEBUG_TU(full)

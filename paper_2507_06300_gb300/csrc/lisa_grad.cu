@@ -143,7 +143,7 @@ __global__ void __launch_bounds__(128, 3)
         bool bad = false;  // a sum beyond the FP32 range: the state goes to the fallback list
         auto base = [&](int a) { return srec + ((int64_t)s * nsp + a) * (int64_t)(kmax + 1) * kSplineRec32; };
         auto load = [&](int a) {
-            const float* r = base(a) + (size_t)iv[a].j * kSplineRec32;
+            const float* r = base(a) + (size_t)LISA_IDX(iv[a].j, kmax + 1) * kSplineRec32;
             iv[a].xr = __ldg(r + 0);
             iv[a].nxo = dup2(-__ldg(r + 1));
             iv[a].nxo_lo = dup2(-__ldg(r + 8));
@@ -199,7 +199,7 @@ __global__ void __launch_bounds__(128, 3)
         };
         auto store_mom = [&](int a) {
             flush_mom(a);
-            double* row = mom_row(mom, pre, s, a, nsp, kmax, D.nranges) + 4 * (int64_t)(U.rho + iv[a].j);
+            double* row = mom_row(mom, pre, s, a, nsp, kmax, D.nranges) + 4 * (int64_t)LISA_IDX(U.rho + iv[a].j, D.nranges + kmax + 1);
 #pragma unroll
             for (int p = 0; p < 4; ++p) {
                 const float2 v = s_am[4 * a + p][tid];
@@ -523,7 +523,7 @@ __global__ void __launch_bounds__(128)
             base[a] = srec + sp * (int64_t)(kmax + 1) * kSplineRec;
             last[a] = nint[sp] - 1;
             j[a] = find_interval<double, kSplineRec, 0>(base[a], nint[sp], x0);
-            const double* z = base[a] + (size_t)j[a] * kSplineRec;
+            const double* z = base[a] + (size_t)LISA_IDX(j[a], kmax + 1) * kSplineRec;
             xl[a] = z[0]; xr[a] = z[1]; ca[a] = z[2]; cb[a] = z[3]; cc[a] = z[4]; cd[a] = z[5];
             for (int p = 0; p < 4; ++p) m[a][p] = 0.0;
         }
@@ -534,13 +534,13 @@ __global__ void __launch_bounds__(128)
             double P[NSP], t[NSP];
             for (int a = 0; a < NSP; ++a) {
                 while (x >= xr[a] && j[a] < last[a]) {
-                    double* row = mom_row(mom, pre, s, a, nsp, kmax, D.nranges) + 4 * (int64_t)(U.rho + j[a]);
+                    double* row = mom_row(mom, pre, s, a, nsp, kmax, D.nranges) + 4 * (int64_t)LISA_IDX(U.rho + j[a], D.nranges + kmax + 1);
                     for (int p = 0; p < 4; ++p) {
                         row[p] = m[a][p];
                         m[a][p] = 0.0;
                     }
                     ++j[a];
-                    const double* z = base[a] + (size_t)j[a] * kSplineRec;
+                    const double* z = base[a] + (size_t)LISA_IDX(j[a], kmax + 1) * kSplineRec;
                     xl[a] = z[0]; xr[a] = z[1]; ca[a] = z[2]; cb[a] = z[3]; cc[a] = z[4]; cd[a] = z[5];
                 }
                 t[a] = x - xl[a];
@@ -582,7 +582,7 @@ __global__ void __launch_bounds__(128)
             }
         }
         for (int a = 0; a < NSP; ++a) {
-            double* row = mom_row(mom, pre, s, a, nsp, kmax, D.nranges) + 4 * (int64_t)(U.rho + j[a]);
+            double* row = mom_row(mom, pre, s, a, nsp, kmax, D.nranges) + 4 * (int64_t)LISA_IDX(U.rho + j[a], D.nranges + kmax + 1);
             for (int p = 0; p < 4; ++p) row[p] = m[a][p];
         }
         double* sc = scal + 6 * (pre + U.rho);
@@ -637,7 +637,7 @@ __global__ void __launch_bounds__(MODE == kComp ? 128 : 512)
     // the list's (state, range) items, R ranges per state, CTA by CTA (the exits are CTA-uniform)
     const int64_t n_items = (int64_t)list[0] * R;
     for (int64_t it = blockIdx.x; it < n_items; it += gridDim.x) {
-    const int s = list[1 + (int)(it / R)], rho = (int)(it % R);
+    const int s = LISA_IDX(list[1 + LISA_IDX((int)(it / R), S)], S), rho = (int)(it % R);
     __syncthreads();   // the previous item's reads of the shared sums are done
     if (MODE == kComp && (sstat[s] & (kUserBits | kRouted)) != kRouted) continue;
     const DatasetDev& D = ds[state_ds[s]];
@@ -662,7 +662,7 @@ __global__ void __launch_bounds__(MODE == kComp ? 128 : 512)
     auto xbin = [&](int i) -> float { return fld(tb, i, 0); };
     auto rec = [&](int a, int j) -> const float* {
         const int64_t sp = (int64_t)s * nsp + a;
-        return static_cast<const float*>(srec_v) + (sp * (int64_t)(kmax + 1) + j) * kSplineRec32;
+        return static_cast<const float*>(srec_v) + (sp * (int64_t)(kmax + 1) + LISA_IDX(j, kmax + 1)) * kSplineRec32;
     };
     auto right_end = [&](int a, int j) -> float { return __ldg(rec(a, j)); };
     auto locate = [&](int a, float x) {
@@ -986,7 +986,7 @@ __global__ void __launch_bounds__(MODE == kComp ? 128 : 512)
             v[p] = 0.0;
             for (int w = 0; w < nwarps; ++w) v[p] += sm(w, a, jr, p);
         }
-        double* row = mom_row(mom, pre, s, a, nsp, kmax, D.nranges) + 4 * (int64_t)(rho + j);
+        double* row = mom_row(mom, pre, s, a, nsp, kmax, D.nranges) + 4 * (int64_t)LISA_IDX(rho + j, D.nranges + kmax + 1);
         if (MODE == kComp) {
             // the FP32 adjoint's slots carry ln10 (its q's factor)
             if (v[0] != 0.0 || v[1] != 0.0 || v[2] != 0.0 || v[3] != 0.0) {
@@ -1142,7 +1142,7 @@ __device__ __noinline__ bool epilogue_state(int s, const int32_t* __restrict__ s
         }
     };
     if (staged) {
-        for (int rho = lane; rho < nr; rho += 32) range_x(rho, sRf[rho], sRl[rho]);
+        for (int rho = lane; rho < nr; rho += 32) range_x(rho, sRf[LISA_IDX(rho, kEpiRanges)], sRl[LISA_IDX(rho, kEpiRanges)]);
         __syncwarp();
     }
     const double* th = theta + (size_t)s * LISA_N_THETA;
@@ -1177,11 +1177,11 @@ __device__ __noinline__ bool epilogue_state(int s, const int32_t* __restrict__ s
             if (jj >= nint) continue;
             double lo_b, hi_b;   // the interval's bounds as the likelihood kernels' walk sees them
             if (fp32) {
-                const float* r = static_cast<const float*>(srec_v) + (sp * (int64_t)(kmax + 1) + jj) * kSplineRec32;
+                const float* r = static_cast<const float*>(srec_v) + (sp * (int64_t)(kmax + 1) + LISA_IDX(jj, kmax + 1)) * kSplineRec32;
                 lo_b = (double)r[6];
                 hi_b = (double)r[0];
             } else {
-                const double* r = static_cast<const double*>(srec_v) + (sp * (int64_t)(kmax + 1) + jj) * kSplineRec;
+                const double* r = static_cast<const double*>(srec_v) + (sp * (int64_t)(kmax + 1) + LISA_IDX(jj, kmax + 1)) * kSplineRec;
                 lo_b = r[0];
                 hi_b = r[1];
             }
@@ -1206,14 +1206,14 @@ __device__ __noinline__ bool epilogue_state(int s, const int32_t* __restrict__ s
                     r1 = lo - 1;
                 }
                 for (int rho = r0; rho <= r1; ++rho)
-                    for (int p = 0; p < 4; ++p) Md[q][p] += row[4 * (int64_t)(rho + jj) + p];
+                    for (int p = 0; p < 4; ++p) Md[q][p] += row[4 * (int64_t)LISA_IDX(rho + jj, nr + kmax + 1) + p];
             } else {
                 for (int rho = 0; rho < nr; ++rho) {
                     double xf, xlb;
                     range_x(rho, xf, xlb);
                     const bool touches = (jj == 0 || xlb >= lo_b) && (jj == nint - 1 || xf < hi_b);
                     if (touches)
-                        for (int p = 0; p < 4; ++p) Md[q][p] += row[4 * (int64_t)(rho + jj) + p];
+                        for (int p = 0; p < 4; ++p) Md[q][p] += row[4 * (int64_t)LISA_IDX(rho + jj, nr + kmax + 1) + p];
                 }
             }
             for (int p = 0; p < 4; ++p) {
@@ -1222,7 +1222,7 @@ __device__ __noinline__ bool epilogue_state(int s, const int32_t* __restrict__ s
             }
             if (fp32) {
                 // moments about the FP32 midpoint xo -> about the left knot x_j:  t = u + mo
-                const float* r = static_cast<const float*>(srec_v) + (sp * (int64_t)(kmax + 1) + jj) * kSplineRec32;
+                const float* r = static_cast<const float*>(srec_v) + (sp * (int64_t)(kmax + 1) + LISA_IDX(jj, kmax + 1)) * kSplineRec32;
                 const T mo = spl::from_hilo<T>(r[1], r[8]) - W.x[q];
                 const T C0 = M[q][0], C1 = M[q][1], C2 = M[q][2], C3 = M[q][3];
                 M[q][0] = C0;
@@ -1370,8 +1370,8 @@ __device__ __noinline__ bool epilogue_state(int s, const int32_t* __restrict__ s
             const T gy = spl::shfl(rs < 32 ? ybar[0] : ybar[1], rs & 31);
             const T gx = spl::shfl(rs < 32 ? xbar[0] : xbar[1], rs & 31);
             if (i < k_in) {
-                ga[1 + i] = spl::to_double(gy);
-                ga[kmax + 2 + i] = spl::to_double(gx);
+                ga[1 + LISA_IDX(i, kmax)] = spl::to_double(gy);
+                ga[kmax + 2 + LISA_IDX(i, kmax)] = spl::to_double(gx);
                 bad |= !isfinite(ga[1 + i]) || !isfinite(ga[kmax + 2 + i]);
             }
         }
@@ -1571,3 +1571,5 @@ extern "C" lisa_status lisa_psd_loglike_grad(const lisa_data* d, const lisa_para
                               : dispatch_adjoint<2>(d, fp32, params, kn, sstat, nint, srec, gw, out, grad, sm);
     return e == cudaSuccess ? LISA_SUCCESS : LISA_ERR_CUDA;
 }
+
+LISA_DEBUG_TU(grad)

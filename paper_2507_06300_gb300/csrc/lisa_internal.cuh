@@ -6,11 +6,23 @@
 #include <cstdint>
 #include <vector>
 
+#include "lisa_debug.cuh"
 #include "lisa_psd.h"
 
 #include <nvtx3/nvToolsExt.h>
 
 namespace lisa {
+
+namespace dbg {
+// The index-check records of the translation units (lisa_debug.cuh), gathered by lisa_debug_bounds.
+cudaError_t read_data(BoundsRecord* out, int reset, const char** file);
+cudaError_t read_full(BoundsRecord* out, int reset, const char** file);
+cudaError_t read_grad(BoundsRecord* out, int reset, const char** file);
+cudaError_t read_loglike(BoundsRecord* out, int reset, const char** file);
+cudaError_t read_peaks(BoundsRecord* out, int reset, const char** file);
+cudaError_t read_prep(BoundsRecord* out, int reset, const char** file);
+cudaError_t read_spline(BoundsRecord* out, int reset, const char** file);
+}  // namespace dbg
 
 // An NVTX range over one library call (host side: the range marks the call's launches, which the
 // profiler correlates with the kernels); without a profiler attached a push/pop costs nothing

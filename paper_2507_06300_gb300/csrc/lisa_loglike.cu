@@ -281,13 +281,15 @@ __device__ __forceinline__ float fmax3(float a, float b, float c) {
 }
 
 // Two consecutive bins (one pair block) with FP32x2 instructions; both bins lie in the current
-// intervals.  Returns nu * (sum_c 1/S_c + ln prod S_c - C) for both bins, formed from one
-// reciprocal and one log2 of the channel product without a range test: the caller keeps the
-// running maximum (mx) of log2 prod and recomputes the chunk on the guarded scalar path when it
-// passed kPairLg2Max or the chunk sum is not finite.
+// intervals.  Returns, for both bins, v = sum_c 1/S_c - C and lg = log2 prod_c S_c (the per-bin
+// term is nu (v + ln2 lg)), formed from one reciprocal and one log2 of the channel product
+// without a range test, and nu: the caller keeps the running maximum (mx) of log2 prod and
+// recomputes the chunk on the guarded scalar path when it passed kPairLg2Max or the chunk sum is
+// not finite.
 template <int C, bool HAS_H, bool BROKEN>
-__device__ __forceinline__ float2 pair_term32(const float4 q0, const float4* __restrict__ blk, const Iv2* iv,
-                                              float2 ao2, float2 at2, float n1, float n2, float2 Af, float& mx) {
+__device__ __forceinline__ void pair_parts32(const float4 q0, const float4* __restrict__ blk, const Iv2* iv,
+                                             float2 ao2, float2 at2, float n1, float n2, float2 Af, float& mx,
+                                             float2& v_out, float2& lg_out, float2& nu_out) {
     constexpr int NSP = C + (HAS_H ? 1 : 0);
     const float4 q1 = blk[1], q2 = blk[2], q3 = blk[3], q4 = blk[4], q5 = blk[5];
     const float2 x = make_float2(q0.x, q0.y), ell = make_float2(q0.z, q0.w), nu = make_float2(q1.x, q1.y);
@@ -322,10 +324,19 @@ __device__ __forceinline__ float2 pair_term32(const float4 q0, const float4* __r
         prod = __fmul2_rn(S[0], S[1]);
         num = __fadd2_rn(S[0], S[1]);
     }
-    const float2 v = __ffma2_rn(num, make_float2(rcp_approx(prod.x), rcp_approx(prod.y)),
-                                make_float2(-(float)C, -(float)C));
-    const float2 lg = make_float2(lg2_approx(prod.x), lg2_approx(prod.y));
-    mx = fmax3(mx, lg.x, lg.y);
+    v_out = __ffma2_rn(num, make_float2(rcp_approx(prod.x), rcp_approx(prod.y)), make_float2(-(float)C, -(float)C));
+    lg_out = make_float2(lg2_approx(prod.x), lg2_approx(prod.y));
+    nu_out = nu;
+    mx = fmax3(mx, lg_out.x, lg_out.y);
+}
+
+// The per-bin terms nu (v + ln2 lg) of one pair block (the knot path, where the keep factor can
+// change from block to block).
+template <int C, bool HAS_H, bool BROKEN>
+__device__ __forceinline__ float2 pair_term32(const float4 q0, const float4* __restrict__ blk, const Iv2* iv,
+                                              float2 ao2, float2 at2, float n1, float n2, float2 Af, float& mx) {
+    float2 v, lg, nu;
+    pair_parts32<C, HAS_H, BROKEN>(q0, blk, iv, ao2, at2, n1, n2, Af, mx, v, lg, nu);
     return __fmul2_rn(nu, __ffma2_rn(make_float2((float)kLn2, (float)kLn2), lg, v));
 }
 
@@ -409,7 +420,7 @@ __global__ void __launch_bounds__(kThreads32, G == 8 ? 4 : (G == 4 ? 5 : 6))
     int k = 0;
     for (int it = i_begin; it < i_end; it += step, ++k) {
         const int b = k % kStages;
-        const WorkItem w = items[it];
+        const WorkItem w = items[LISA_IDX(it, n_items)];
         // buffer b's barrier has completed k / kStages phases before this item's
         const bool ok = mbar_wait_bounded(&full[b], (unsigned)(k / kStages) & 1u, wait_limit);
         // a wait that ran out: this thread skips the item (its table may never arrive or be
@@ -447,7 +458,7 @@ __global__ void __launch_bounds__(kThreads32, G == 8 ? 4 : (G == 4 ? 5 : 6))
                 // the records of this state's splines: spline a, interval j at rec(a, j)
                 auto rec = [&](int a, int j) {
                     return reinterpret_cast<const float4*>(
-                        srec + (((int64_t)s * nsp + a) * (int64_t)(kmax + 1) + j) * kSplineRec32);
+                        srec + (((int64_t)s * nsp + a) * (int64_t)(kmax + 1) + LISA_IDX(j, kmax + 1)) * kSplineRec32);
                 };
                 // installs interval j of spline a from its record (A = xr, xo, c0, c1; B = c2, c3,
                 // xl, T)
@@ -526,27 +537,35 @@ __global__ void __launch_bounds__(kThreads32, G == 8 ? 4 : (G == 4 ? 5 : 6))
                 while (ip < phi) {
                     const int pc0 = ip;
                     const int pcend = min(ip + kChunkPairs, phi);
-                    const float4* blk = tb4 + ip * (kPairRec / 4);
+                    const float4* blk = tb4 + LISA_IDX(ip, np) * (kPairRec / 4);
                     float2 acc2 = make_float2(0.f, 0.f);
                     float mx = -INFINITY;
                     // one decision per chunk for the warp: no lane passes a knot inside it (the
                     // common case away from the lowest frequencies) -> no checks at all
                     const float x_last = tb4[(pcend - 1) * (kPairRec / 4)].y;
                     if (!__any_sync(__activemask(), x_last >= xmin)) {
+                        // keep2 is constant here: the nu-weighted sums of v and of lg run apart,
+                        // ln2 and keep2 applied once for the chunk
+                        float2 accv = make_float2(0.f, 0.f), accl = make_float2(0.f, 0.f);
                         for (; ip + U <= pcend; ip += U, blk += U * (kPairRec / 4)) {
 #pragma unroll
                             for (int u = 0; u < U; ++u) {
                                 const float4* pb = blk + u * (kPairRec / 4);
-                                acc2 = __ffma2_rn(keep2, pair_term32<C, HAS_H, BROKEN>(pb[0], pb, iv2, ao2_2, at2_2,
-                                                                                       n1, n2, Af2, mx),
-                                                  acc2);
+                                float2 v, lg, nu;
+                                pair_parts32<C, HAS_H, BROKEN>(pb[0], pb, iv2, ao2_2, at2_2, n1, n2, Af2, mx, v, lg,
+                                                               nu);
+                                accv = __ffma2_rn(nu, v, accv);
+                                accl = __ffma2_rn(nu, lg, accl);
                             }
                         }
 #pragma unroll 1
-                        for (; ip < pcend; ++ip, blk += kPairRec / 4)
-                            acc2 = __ffma2_rn(keep2, pair_term32<C, HAS_H, BROKEN>(blk[0], blk, iv2, ao2_2, at2_2, n1,
-                                                                                   n2, Af2, mx),
-                                              acc2);
+                        for (; ip < pcend; ++ip, blk += kPairRec / 4) {
+                            float2 v, lg, nu;
+                            pair_parts32<C, HAS_H, BROKEN>(blk[0], blk, iv2, ao2_2, at2_2, n1, n2, Af2, mx, v, lg, nu);
+                            accv = __ffma2_rn(nu, v, accv);
+                            accl = __ffma2_rn(nu, lg, accl);
+                        }
+                        acc2 = __fmul2_rn(keep2, __ffma2_rn(make_float2((float)kLn2, (float)kLn2), accl, accv));
                     } else {
                         // pair block by pair block: a lane whose block reaches a knot takes its two
                         // bins on the scalar path (advancing its intervals between them), the
@@ -579,14 +598,17 @@ __global__ void __launch_bounds__(kThreads32, G == 8 ? 4 : (G == 4 ? 5 : 6))
         }
         const DatasetDev& D = ds[w.ds];
         if (R == 1) {
-            if (active) partial[D.pbase + (int64_t)(s - D.s0) * D.ntiles + w.tile] = (double)accf.hi + (double)accf.lo;
+            if (active)
+                partial[D.pbase + (int64_t)(s - D.s0) * D.ntiles + LISA_IDX(w.tile, D.ntiles)] =
+                    (double)accf.hi + (double)accf.lo;
         } else {
             red[tid] = make_float2(accf.hi, accf.lo);
             __syncthreads();
             if (r == 0 && active) {
                 ff sum = {red[ls].x, red[ls].y};
                 for (int q = 1; q < R; ++q) sum = ff_add(sum, ff{red[ls + q * sc].x, red[ls + q * sc].y});
-                partial[D.pbase + (int64_t)(s - D.s0) * D.ntiles + w.tile] = (double)sum.hi + (double)sum.lo;
+                partial[D.pbase + (int64_t)(s - D.s0) * D.ntiles + LISA_IDX(w.tile, D.ntiles)] =
+                    (double)sum.hi + (double)sum.lo;
             }
             __syncthreads();   // red is rewritten by the next item
         }
@@ -944,7 +966,7 @@ __global__ void __launch_bounds__(kThreads)
     __shared__ double red[kThreads];
     const int tid = threadIdx.x;
     for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
-        const WorkItem w = items[it];
+        const WorkItem w = items[LISA_IDX(it, n_items)];
         const int sc = w.sc;
         const int R = kThreads / sc;
         const int ls = tid & (sc - 1);
@@ -967,7 +989,7 @@ __global__ void __launch_bounds__(kThreads)
                     base[a] = srec + sp * (int64_t)(kmax + 1) * kSplineRec;
                     last[a] = nint[sp] - 1;
                     j[a] = find_interval<double, kSplineRec, 0>(base[a], nint[sp], __ldg(rb));
-                    const double* q = base[a] + (size_t)j[a] * kSplineRec;
+                    const double* q = base[a] + (size_t)LISA_IDX(j[a], kmax + 1) * kSplineRec;
                     xl[a] = q[0]; xr[a] = q[1]; ca[a] = q[2]; cb[a] = q[3]; cc[a] = q[4]; cd[a] = q[5];
                 }
                 for (int i = lo; i < hi; ++i) {
@@ -977,7 +999,7 @@ __global__ void __launch_bounds__(kThreads)
                     for (int a = 0; a < NSP; ++a) {
                         while (x >= xr[a] && j[a] < last[a]) {
                             ++j[a];
-                            const double* z = base[a] + (size_t)j[a] * kSplineRec;
+                            const double* z = base[a] + (size_t)LISA_IDX(j[a], kmax + 1) * kSplineRec;
                             xl[a] = z[0]; xr[a] = z[1]; ca[a] = z[2]; cb[a] = z[3]; cc[a] = z[4]; cd[a] = z[5];
                         }
                         const double t = x - xl[a];
@@ -1070,7 +1092,7 @@ __global__ void model_psd_kernel(const int32_t* __restrict__ state_ds, const Dat
         const int64_t sp = (int64_t)s * nsp + a;
         const double* base = srec + sp * (int64_t)(kmax + 1) * kSplineRec;
         const int j = find_interval<double, kSplineRec, 0>(base, nint[sp], x);
-        const double* z = base + (size_t)j * kSplineRec;
+        const double* z = base + (size_t)LISA_IDX(j, kmax + 1) * kSplineRec;
         const double t = x - z[0];
         Pv[a] = z[2] + t * (z[3] + t * (z[4] + t * z[5]));
     }
@@ -1407,3 +1429,5 @@ extern "C" lisa_status lisa_psd_loglike_noalloc(const lisa_data* d, const lisa_p
     return lisa_psd_loglike(d, params, buf, buf_bytes, kmax, out, scratch, LISA_NOALLOC_SCRATCH_BYTES, prec,
                             stream);
 }
+
+LISA_DEBUG_TU(loglike)

@@ -31,7 +31,7 @@ __global__ void __launch_bounds__(kBlock) pipe_rate_kernel(int iters, float a, f
     }
     if (OP == LISA_PIPE_MIX) {
         // the fused FP32 likelihood's instruction mix per pair block (two bins of one state, A,E,T
-        // with a power-law SGWB): 38 packed FP32 operations, 8 ex2, 2 rcp, 2 lg2, here as
+        // with a power-law SGWB): 37 packed FP32 operations, 8 ex2, 2 rcp, 2 lg2, here as
         // independent chains so that only the pipes, not latency, set the rate
         float2 v[kChains];
         float m[kChains];
@@ -47,7 +47,7 @@ __global__ void __launch_bounds__(kBlock) pipe_rate_kernel(int iters, float a, f
 #pragma unroll
                 for (int u = 0; u < kChains; ++u) v[u] = __ffma2_rn(v[u], a2, b2);
 #pragma unroll
-            for (int u = 0; u < 6; ++u) v[u] = __ffma2_rn(v[u], a2, b2);
+            for (int u = 0; u < 5; ++u) v[u] = __ffma2_rn(v[u], a2, b2);
 #pragma unroll
             for (int u = 0; u < kChains; ++u) {
                 float y;
@@ -183,3 +183,5 @@ extern "C" lisa_status lisa_pipe_rates(int32_t iters, int32_t reps, double* rate
     cudaFree(buf);
     return st;
 }
+
+LISA_DEBUG_TU(peaks)

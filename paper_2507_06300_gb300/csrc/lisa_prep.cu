@@ -128,3 +128,5 @@ extern "C" lisa_status lisa_averaged_periodogram(const double* d, int32_t n_chan
         e = launch_avg<3, 1>(dd, n_freq, f0, df, off, n_bins, P, f, nu, n_channels, sm);
     return check_cuda(e);
 }
+
+LISA_DEBUG_TU(prep)

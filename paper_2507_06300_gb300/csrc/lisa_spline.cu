@@ -65,7 +65,7 @@ __global__ void __launch_bounds__(32 * kMaxSp, kMaxSp == 4 ? 7 : 3) spline_setup
                 const BT *ca = W.ca, *cb = W.cb, *cc = W.cc, *cd = W.cd, *h = W.h;
                 if constexpr (!kF32) {
                     if (!valid) continue;
-                    double* r = static_cast<double*>(rec_v) + (sp * (int64_t)(kmax + 1) + j) * kSplineRec;
+                    double* r = static_cast<double*>(rec_v) + (sp * (int64_t)(kmax + 1) + LISA_IDX(j, kmax + 1)) * kSplineRec;
                     r[0] = x[q];
                     r[1] = last ? INFINITY : xn[q];
                     r[2] = ca[q];
@@ -106,9 +106,9 @@ __global__ void __launch_bounds__(32 * kMaxSp, kMaxSp == 4 ? 7 : 3) spline_setup
                         hhi = fmaxf(hhi, last ? INFINITY : xr_f);
                     }
                     if (!valid) continue;
-                    float* r = static_cast<float*>(rec_v) + (sp * (int64_t)(kmax + 1) + j) * kSplineRec32;
+                    float* r = static_cast<float*>(rec_v) + (sp * (int64_t)(kmax + 1) + LISA_IDX(j, kmax + 1)) * kSplineRec32;
                     r[0] = last ? INFINITY : xr_f;
-                    kxr[sp * kxr_stride(kmax) + j] = r[0];
+                    kxr[sp * kxr_stride(kmax) + LISA_IDX(j, kxr_stride(kmax))] = r[0];
                     r[1] = xo_hi;
                     r[6] = xl_f;
                     r[7] = Tc;
@@ -159,7 +159,7 @@ __global__ void __launch_bounds__(32 * kMaxSp, kMaxSp == 4 ? 7 : 3) spline_setup
         if (kF32 && do_route && robust && st_all == 0) {
             word |= kRouted;
             const int slot = atomicAdd(route, 1);
-            route[1 + slot] = s;
+            route[1 + LISA_IDX(slot, S)] = s;
         }
         status_buf[s] = word;
         if (status_out) status_out[s] = st_all;
@@ -217,3 +217,5 @@ extern "C" lisa_status lisa_spline_setup(const lisa_data* d, const lisa_knots* k
     }
     return check_cuda(cudaGetLastError());
 }
+
+LISA_DEBUG_TU(spline)

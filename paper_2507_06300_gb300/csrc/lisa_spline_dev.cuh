@@ -188,14 +188,14 @@ __device__ __forceinline__ void warp_build_spline(WarpSpline<T>& W, const double
     if (!st) {
         bool bx = false, bw = false;
         if (lane < k) {
-            xa = px[lane];
-            wa = pw[1 + lane];
+            xa = px[LISA_IDX(lane, kmax)];
+            wa = pw[1 + LISA_IDX(lane, kmax)];
             bx |= !(isfinite(xa) && xa > xlo && xa < xhi);
             bw |= !isfinite(wa);
         }
         if (lane + 32 < k) {
-            xb = px[lane + 32];
-            wb = pw[1 + lane + 32];
+            xb = px[LISA_IDX(lane + 32, kmax)];
+            wb = pw[1 + LISA_IDX(lane + 32, kmax)];
             bx |= !(isfinite(xb) && xb > xlo && xb < xhi);
             bw |= !isfinite(wb);
         }
@@ -231,19 +231,20 @@ __device__ __forceinline__ void warp_build_spline(WarpSpline<T>& W, const double
     if (st) return;
     W.ra = 1 + ra;
     W.rb = 1 + rb;
+    // scratch rows of 64 doubles: knots 0 .. k + 1 <= kmax + 1
     if (lane < k) {
-        sX[1 + ra] = xa;
-        sY[1 + ra] = wa;
+        sX[LISA_IDX(1 + ra, 64)] = xa;
+        sY[LISA_IDX(1 + ra, 64)] = wa;
     }
     if (lane + 32 < k) {
-        sX[1 + rb] = xb;
-        sY[1 + rb] = wb;
+        sX[LISA_IDX(1 + rb, 64)] = xb;
+        sY[LISA_IDX(1 + rb, 64)] = wb;
     }
     if (lane == 0) {
         sX[0] = xlo;
         sY[0] = w0;
-        sX[k + 1] = xhi;
-        sY[k + 1] = wn;
+        sX[LISA_IDX(k + 1, 64)] = xhi;
+        sY[LISA_IDX(k + 1, 64)] = wn;
     }
     __syncwarp();
     const int K = k + 2;

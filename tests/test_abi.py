@@ -14,7 +14,7 @@ HEADERS = sorted(glob.glob(os.path.join(ROOT, "include", "*.h")))
 
 def declared_functions():
     txt = "".join(open(h).read() for h in HEADERS)
-    return sorted(set(re.findall(r"^(?:lisa_status|size_t|const char\*)\s+(lisa_\w+)\(", txt, re.M)))
+    return sorted(set(re.findall(r"^(?:lisa_status|size_t|int32_t|const char\*)\s+(lisa_\w+)\(", txt, re.M)))
 
 
 @pytest.fixture(scope="module")
@@ -87,3 +87,12 @@ def test_bad_descriptions_are_rejected_before_any_device_work(lib):
                      ("x_hi", "xhi"), ("f_ref", "fr")):
         setattr(d, fld, arr[key].ctypes.data_as(P64))
     assert lib.lisa_data_create(ctypes.byref(d), None, ctypes.byref(out)) == 4   # LISA_ERR_DATA
+
+
+def test_release_build_has_no_index_checks(lib):
+    """The release library compiles the index checks away: it reports them off, refuses the
+    self-test without launching anything, and rejects a null report pointer on the host."""
+    assert lib.lisa_debug_bounds_enabled() == 0
+    LISA_ERR_NULL, LISA_ERR_VALUE = 1, 2
+    assert lib.lisa_debug_bounds(0, None) == LISA_ERR_NULL
+    assert lib.lisa_debug_bounds_selftest(None) == LISA_ERR_VALUE
