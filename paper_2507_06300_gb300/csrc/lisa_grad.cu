@@ -42,7 +42,7 @@ inline GradLayout grad_layout(const lisa_data* d, int kmax, bool fp32) {
     G.off_mom = align256(sizeof(double) * 6 * (size_t)d->adj_ranges);
     G.off_fb = G.off_mom + align256(sizeof(double) * 4 * (size_t)d->nsp *
                                     ((size_t)d->adj_ranges + (size_t)d->n_states * (size_t)(kmax + 1)));
-    G.bytes = G.off_fb + (fp32 ? align256(sizeof(int32_t) * (2 * (size_t)d->n_states + 1)) : 0);
+    G.bytes = G.off_fb + (fp32 ? align256(sizeof(int32_t) * (2 * (size_t)d->n_states + 3)) : 0);
     return G;
 }
 
@@ -58,9 +58,10 @@ __device__ __forceinline__ double* mom_row(double* mom, int64_t prefix, int s, i
     return mom + 4 * ((int64_t)nsp * (prefix + (int64_t)s * (kmax + 1)) + (int64_t)a * (nr + kmax + 1));
 }
 
-// The FP32 gradient's fallback list in the flag area fb (int32): fb[0..S) a flag per state,
-// fb[S] the count, fb[S+1..] the flagged states (in the order they were flagged).  Flags state s
-// (sums or moments beyond the FP32 range) once.
+// The FP32 gradient's flag area fb (int32, zeroed per call): fb[0..S) a flag per state, fb[S]
+// the count and fb[S+1..2S] the flagged states (in the order they were flagged), then the item
+// counters of the compensated (fb[2S+1]) and fallback (fb[2S+2]) passes.  Flags state s (sums or
+// moments beyond the FP32 range) once.
 __device__ __forceinline__ void fb_flag(int32_t* fb, int S, int s) {
     if (atomicExch(fb + s, 1) == 0) fb[S + 1 + atomicAdd(fb + S, 1)] = s;
 }
@@ -592,16 +593,17 @@ __global__ void __launch_bounds__(128)
 
 // ---- the FP32 gradient's two per-state passes: one CTA per (state, range) item --------------
 // Mode kComp: the bins the FP32 adjoint masked (routed states, whose ill-conditioned intervals
-// (conditioning T > kRobustT, prior draws with close knots) it loads as zero cubics): spline values
-// in float-float from the records' hi and lo parts (2^P as ex2(hi) (1 + lo ln2)), per-bin terms in
-// FP32, the moments' products exact (float-float); the sums are added to the slots the FP32
-// adjoint wrote.  Only ranges overlapping the state's ill-conditioned x-extent run.
+// (conditioning T > kRobustT, prior draws with close knots) it loads as zero cubics). On an
+// ill-conditioned interval the spline value is formed in float-float from the records' hi and lo
+// parts (2^P as ex2(hi) (1 + lo ln2)) and the moments' products exactly (float-float); the bin's
+// other splines take the FP32 adjoint's FP32 Horner and products.  Per-bin terms in FP32; the
+// sums are added to the slots the FP32 adjoint wrote.  Only ranges overlapping the state's ill-conditioned x-extent run.
 // Mode kFallback: the states the FP32 epilogue flagged (their FP32 sums left the FP32 range), all
 // their bins: spline values in float-float from the FP32 records, the PSDs, 1 / S-hat and the
 // sums in FP64; the sums overwrite the slots (every interval from the range's first bin to its
 // last), in the FP32 adjoint's convention (moments about the records' midpoints, ln10 in q).
-// A persistent grid runs the (state, range) items of a compact list (kComp: the setup's route
-// list; kFallback: the flag area's list), one item per CTA at a time.
+// A resident grid runs the (state, range) items of a compact list (kComp: the setup's route
+// list; kFallback: the flag area's list), each CTA fetching its next item from a counter.
 // The CTA's warps (4 for kComp, 16 for kFallback) split the range's bins, their lanes 32
 // consecutive bins at a time; each spline's moments are reduced over the lanes per interval (a fixed butterfly),
 // kept per warp and interval in shared memory, and summed over the warps in order.
@@ -621,7 +623,8 @@ __global__ void __launch_bounds__(MODE == kComp ? 128 : 512)
                          const float* __restrict__ rec32, const float* __restrict__ xlo32,
                          const float* __restrict__ elllo32, const double* __restrict__ theta,
                          const int32_t* __restrict__ sstat, const int32_t* __restrict__ list, int R,
-                         int32_t* __restrict__ fb, const int32_t* __restrict__ nint, const void* __restrict__ srec_v,
+                         int32_t* __restrict__ fb, int32_t* __restrict__ next_item,
+                         const int32_t* __restrict__ nint, const void* __restrict__ srec_v,
                          const float2* __restrict__ hull, int kmax, int nsp, const int64_t* __restrict__ prefix,
                          double* __restrict__ scal, double* __restrict__ mom) {
     constexpr int NSP = C + (HAS_H ? 1 : 0);
@@ -634,11 +637,18 @@ __global__ void __launch_bounds__(MODE == kComp ? 128 : 512)
     const int nwarps = blockDim.x >> 5;     // <= 16
     const int nsl = kmax + 1;               // interval slots per spline
     auto sm = [&](int w, int a, int jr, int p) -> double& { return s_m[(((w * NSP) + a) * nsl + jr) * 4 + p]; };
-    // the list's (state, range) items, R ranges per state, CTA by CTA (the exits are CTA-uniform)
-    const int64_t n_items = (int64_t)list[0] * R;
-    for (int64_t it = blockIdx.x; it < n_items; it += gridDim.x) {
-    const int s = LISA_IDX(list[1 + LISA_IDX((int)(it / R), S)], S), rho = (int)(it % R);
-    __syncthreads();   // the previous item's reads of the shared sums are done
+    // the list's (state, range) items, R ranges per state, fetched one at a time by each CTA
+    // from the counter (a state's heavy ranges are contiguous in the list); the exits below are
+    // CTA-uniform
+    __shared__ int s_item;
+    const int n_items = list[0] * R;
+    for (;;) {
+    if (threadIdx.x == 0) s_item = atomicAdd(next_item, 1);
+    __syncthreads();   // also: the previous item's reads of the shared sums are done
+    const int it = s_item;
+    __syncthreads();   // every thread has read s_item before thread 0 fetches again
+    if (it >= n_items) break;
+    const int s = LISA_IDX(list[1 + LISA_IDX(it / R, S)], S), rho = it % R;
     if (MODE == kComp && (sstat[s] & (kUserBits | kRouted)) != kRouted) continue;
     const DatasetDev& D = ds[state_ds[s]];
     if (rho >= D.nranges) continue;
@@ -665,12 +675,34 @@ __global__ void __launch_bounds__(MODE == kComp ? 128 : 512)
         return static_cast<const float*>(srec_v) + (sp * (int64_t)(kmax + 1) + LISA_IDX(j, kmax + 1)) * kSplineRec32;
     };
     auto right_end = [&](int a, int j) -> float { return __ldg(rec(a, j)); };
+    // the interval of spline a holding x, as the walk finds it (the count of right ends <= x,
+    // which do not decrease): the lanes load the right ends together; x is warp-uniform and the
+    // whole warp calls
     auto locate = [&](int a, float x) {
         const int n = nint[(int64_t)s * nsp + a];
-        int j = 0;
-        while (j < n - 1 && x >= right_end(a, j)) ++j;
-        return j;
+        int c = 0;
+        for (int jb = 0; jb < n - 1; jb += 32) {
+            const int j = jb + lane;
+            c += __popc(__ballot_sync(kFullMask, j < n - 1 && right_end(a, j) <= x));
+        }
+        return c;
     };
+    if (MODE == kComp) {
+        // does an ill-conditioned interval hold a bin of this range?  The threads take the
+        // (spline, interval) pairs; interval j holds the x with right_end(j - 1) <= x < right_end(j)
+        const float xa = xbin(0), xb = xbin(nb - 1);
+        bool any = false;
+        for (int e = threadIdx.x; e < NSP * nsl; e += blockDim.x) {
+            const int a = e / nsl, j = e - a * nsl;
+            const int n = nint[(int64_t)s * nsp + a];
+            if (j < n && !(__ldg(rec(a, j) + 7) <= (float)kRobustT)) {
+                const float lo = j == 0 ? -INFINITY : right_end(a, j - 1);
+                const float hi = j == n - 1 ? INFINITY : right_end(a, j);
+                any |= lo <= xb && hi > xa;
+            }
+        }
+        if (!__syncthreads_or(any)) continue;   // CTA-uniform
+    }
     int j0[NSP], nin[NSP];
 #pragma unroll
     for (int a = 0; a < NSP; ++a) {
@@ -698,7 +730,8 @@ __global__ void __launch_bounds__(MODE == kComp ? 128 : 512)
     // lane-local running sums of the warp's current intervals (float-float for kComp, FP64 for
     // kFallback; folded into am, over the lanes, only when an interval is left), and (kComp) of
     // the template terms
-    ff ls[NSP][4], lt[6];
+    ff ls[NSP][4];
+    float ltf[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};   // kComp: the template terms (<= 32 per lane)
     double lsd[NSP][4];   // kFallback: the lanes' FP64 running sums, folded the same way
 #pragma unroll
     for (int a = 0; a < NSP; ++a)
@@ -706,11 +739,18 @@ __global__ void __launch_bounds__(MODE == kComp ? 128 : 512)
             ls[a][p] = ff{0.f, 0.f};
             lsd[a][p] = 0.0;
         }
-    for (int k = 0; k < 6; ++k) lt[k] = ff{0.f, 0.f};
+    // kComp: float-float sums over the lanes (a fixed butterfly on the FP32 pipe); lane 0 adds
+    // the result to its FP64 running sums
+    auto wsum_ff = [&](ff v) {
+        for (int o = 16; o > 0; o >>= 1)
+            v = ff_add(v, ff{__shfl_xor_sync(kFullMask, v.hi, o), __shfl_xor_sync(kFullMask, v.lo, o)});
+        return v;
+    };
     auto flush = [&](int a) {
         if (MODE == kComp)
             for (int p = 0; p < 4; ++p) {
-                am[a][p] += wsum((double)ls[a][p].hi + (double)ls[a][p].lo);
+                const ff w = wsum_ff(ls[a][p]);
+                if (lane == 0) am[a][p] += (double)w.hi + (double)w.lo;
                 ls[a][p] = ff{0.f, 0.f};
             }
         else
@@ -779,33 +819,45 @@ __global__ void __launch_bounds__(MODE == kComp ? 128 : 512)
             }
             continue;
         }
-        // the spline signals q (FP32 for kComp, FP64 for kFallback) and t = x - x_o (FP32)
+        // the spline signals q (FP32 for kComp, FP64 for kFallback) and t = x - x_o (FP32);
+        // kComp: whether each spline's interval is ill-conditioned at this bin
         float qk[NSP], tv[NSP];
+        bool hs[NSP];
         double qd[NSP];
         double tc[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
 #pragma unroll
         for (int a = 0; a < NSP; ++a) {
             qk[a] = tv[a] = 0.f;
             qd[a] = 0.0;
+            hs[a] = false;
         }
         if (use) {
             if constexpr (MODE == kComp) {
                 const float xf = fld(tb, ib, 0), ell = fld(tb, ib, 1), nu = fld(tb, ib, 2);
                 const float x_lo = __ldg(xlo32 + b0 + ib);
+                // per spline: float-float on an ill-conditioned interval (hs), the FP32 adjoint's
+                // FP32 Horner on the compensated t on the others
                 float P[NSP], cor[NSP], tl[NSP];
 #pragma unroll
                 for (int a = 0; a < NSP; ++a) {
                     const float4* rr = reinterpret_cast<const float4*>(rec(a, jl[a]));
-                    const float4 A = __ldg(rr), Bq = __ldg(rr + 1), Cq = __ldg(rr + 2), Dq = __ldg(rr + 3);
+                    const float4 A = __ldg(rr), Bq = __ldg(rr + 1), Cq = __ldg(rr + 2);
                     const ff tt = two_sum(xf, -A.y);
                     tl[a] = tt.hi + (tt.lo + (x_lo - Cq.x));   // t = x - x_o as the FP32 adjoint forms it
-                    const ff tf = ff_add(ff{xf, x_lo}, ff{-A.y, -Cq.x});
-                    ff v = {Bq.y, Dq.x};
-                    v = ff_add(ff_mul(v, tf), ff{Bq.x, Cq.w});
-                    v = ff_add(ff_mul(v, tf), ff{A.w, Cq.z});
-                    v = ff_add(ff_mul(v, tf), ff{A.z, Cq.y});
-                    P[a] = v.hi;
-                    cor[a] = fmaf(v.lo, (float)kLn2, 1.f);
+                    hs[a] = !(Bq.w <= (float)kRobustT);
+                    if (hs[a]) {
+                        const float4 Dq = __ldg(rr + 3);
+                        const ff tf = ff_add(ff{xf, x_lo}, ff{-A.y, -Cq.x});
+                        ff v = {Bq.y, Dq.x};
+                        v = ff_add(ff_mul(v, tf), ff{Bq.x, Cq.w});
+                        v = ff_add(ff_mul(v, tf), ff{A.w, Cq.z});
+                        v = ff_add(ff_mul(v, tf), ff{A.z, Cq.y});
+                        P[a] = v.hi;
+                        cor[a] = fmaf(v.lo, (float)kLn2, 1.f);
+                    } else {
+                        P[a] = fmaf(fmaf(fmaf(Bq.y, tl[a], Bq.x), tl[a], A.w), tl[a], A.z);
+                        cor[a] = 1.f;
+                    }
                 }
                 float eh = 0.f;
                 if (HAS_H) {
@@ -837,7 +889,7 @@ __global__ void __launch_bounds__(MODE == kComp ? 128 : 512)
                     tf[5] = ell * Hs;
                 else
                     tf[4] = ell * Hs;
-                for (int k = 0; k < 6; ++k) lt[k] = ff_add(lt[k], two_sum(tf[k], 0.f));
+                for (int k = 0; k < 6; ++k) ltf[k] += tf[k];
 #pragma unroll
                 for (int a = 0; a < NSP; ++a) {
                     qk[a] = q[a];
@@ -919,12 +971,19 @@ __global__ void __launch_bounds__(MODE == kComp ? 128 : 512)
         for (int a = 0; a < NSP; ++a) {
             double d[4];
             if (MODE == kComp) {
-                // exact products q t^p (float-float) of the FP32 values; while every lane stays in
-                // the warp's current interval they go to the lane-local sums
+                // the products q t^p of the FP32 values, exact (float-float) on an ill-conditioned
+                // interval, FP32 on the others; while every lane stays in the warp's current
+                // interval they go to the lane-local sums
                 const float qf = qk[a], t = tv[a], qt = qf * t;
-                const ff p1 = {qt, fmaf(qf, t, -qt)};
-                const ff p2 = ff_mul(p1, ff{t, 0.f});
-                const ff p3 = ff_mul(p2, ff{t, 0.f});
+                ff p1 = {qt, 0.f}, p2, p3;
+                if (hs[a]) {
+                    p1.lo = fmaf(qf, t, -qt);
+                    p2 = ff_mul(p1, ff{t, 0.f});
+                    p3 = ff_mul(p2, ff{t, 0.f});
+                } else {
+                    p2 = ff{qt * t, 0.f};
+                    p3 = ff{p2.hi * t, 0.f};
+                }
                 if (__all_sync(kFullMask, !use || jl[a] == cj[a])) {
                     if (use) {
                         ls[a][0] = ff_add(ls[a][0], ff{qf, 0.f});
@@ -934,10 +993,22 @@ __global__ void __launch_bounds__(MODE == kComp ? 128 : 512)
                     }
                     continue;
                 }
-                d[0] = qf;
-                d[1] = (double)p1.hi + (double)p1.lo;
-                d[2] = (double)p2.hi + (double)p2.lo;
-                d[3] = (double)p3.hi + (double)p3.lo;
+                // lanes in several intervals: per interval the float-float sum over its lanes
+                const ff dff[4] = {ff{qf, 0.f}, p1, p2, p3};
+                const int jlo = __shfl_sync(kFullMask, jl[a], 0);
+                const int jhi = __shfl_sync(kFullMask, jl[a], last_lane);
+                for (int jj = jlo; jj <= jhi; ++jj) {
+                    const bool in = use && jl[a] == jj;
+                    ff m[4];
+                    for (int p = 0; p < 4; ++p) m[p] = wsum_ff(in ? dff[p] : ff{0.f, 0.f});
+                    if (jj > cj[a]) {
+                        flush(a);
+                        cj[a] = jj;
+                    }
+                    if (lane == 0)
+                        for (int p = 0; p < 4; ++p) am[a][p] += (double)m[p].hi + (double)m[p].lo;
+                }
+                continue;
             } else {
                 const double t = tv[a], qt = qd[a] * t;
                 d[0] = qd[a];
@@ -972,7 +1043,7 @@ __global__ void __launch_bounds__(MODE == kComp ? 128 : 512)
         }
     }
     for (int k = 0; k < 6; ++k) {
-        const double v = wsum(MODE == kComp ? (double)lt[k].hi + (double)lt[k].lo : ts[k]);
+        const double v = wsum(MODE == kComp ? (double)ltf[k] : ts[k]);
         if (lane == 0) s_t[warp][k] = v;
     }
     __syncthreads();
@@ -1461,7 +1532,7 @@ cudaError_t launch_adjoint(const lisa_data* d, bool fp32, const lisa_params* par
     const int S = (int)d->n_states;
     const int R = adj_max_ranges(d);
     prof_mark(d, prof, 0, sm);
-    if (fp32 && cudaMemsetAsync(gw.fb, 0, sizeof(int32_t) * ((size_t)S + 1), sm) != cudaSuccess)
+    if (fp32 && cudaMemsetAsync(gw.fb, 0, sizeof(int32_t) * (2 * (size_t)S + 3), sm) != cudaSuccess)
         return cudaErrorInvalidValue;
     if (d->n_adj_units > 0) {
         if (fp32 && adj_exact_t(d))
@@ -1486,7 +1557,7 @@ cudaError_t launch_adjoint(const lisa_data* d, bool fp32, const lisa_params* par
                 return cudaErrorInvalidValue;
             adjoint_range_kernel<C, H, B, kComp><<<d->n_sm * std::max(occ, 1), 128, smc, sm>>>(
                 S, d->d_state_ds, d->d_ds, d->d_rec32, d->d_xlo32, d->d_elllo32, params->theta_dev, sstat, gw.route,
-                R, gw.fb, nint, srec, gw.hull, kn->kmax, d->nsp, d->d_adj_prefix, scal, mom);
+                R, gw.fb, gw.fb + 2 * S + 1, nint, srec, gw.hull, kn->kmax, d->nsp, d->d_adj_prefix, scal, mom);
             // the states whose FP32 sums left the FP32 range (flagged by both passes above): all
             // their bins again, FP64 sums, on a resident grid of 16-warp CTAs
             const size_t smf = range_smem(d, kn->kmax, 16);
@@ -1498,7 +1569,8 @@ cudaError_t launch_adjoint(const lisa_data* d, bool fp32, const lisa_params* par
                 return cudaErrorInvalidValue;
             adjoint_range_kernel<C, H, B, kFallback><<<d->n_sm * std::max(occ, 1), 512, smf, sm>>>(
                 S, d->d_state_ds, d->d_ds, d->d_rec32, d->d_xlo32, d->d_elllo32, params->theta_dev, sstat,
-                gw.fb + S, R, gw.fb, nint, srec, nullptr, kn->kmax, d->nsp, d->d_adj_prefix, scal, mom);
+                gw.fb + S, R, gw.fb, gw.fb + 2 * S + 2, nint, srec, nullptr, kn->kmax, d->nsp, d->d_adj_prefix, scal,
+                mom);
         } else
             adjoint_fp64_kernel<C, H, B><<<grid, 128, 0, sm>>>(d->d_adj_units, d->n_adj_units, d->d_ds, d->d_rec64,
                                                                params->theta_dev, sstat, nint,
