@@ -700,14 +700,15 @@ __device__ __forceinline__ ff inv_plus_log(ff lS, float nu, double& far) {
 // log2 of FP64's overflow threshold: 10^P overflows double precision from P = 1024 in log2 units
 constexpr float kP2Overflow = 1024.0f;
 
-// Compensated kernel staging: each CTA stages its unit's tile in chunks of kRobStage bins into
-// its shared memory (the pair-block table by one bulk asynchronous copy, the low parts of x and
-// ell by thread loads), then evaluates the chunk from shared memory.  8 warps per CTA: two CTAs
+// Compensated kernel staging: each warp stages its tile in chunks of kRobChunk bins into its own
+// shared-memory slice (the pair-block table by one bulk asynchronous copy, the low parts of x and
+// ell by lane loads), then evaluates the chunk from shared memory.  8 warps per CTA: two CTAs
 // fill an SM's shared memory (and registers), 16 warps.
 constexpr int kRobWarps = 8;
-constexpr int kRobStage = 2048;                                   // bins staged at once (even)
-constexpr int kRobStageF4 = kRobStage / 2 * (kPairRec / 4);       // float4 of table per stage
-constexpr size_t kRobSmem = ((size_t)kRobStageF4 + 2 * kRobStage / 4) * sizeof(float4);   // + x lo, ell lo
+constexpr int kRobChunk = 256;                                    // even
+constexpr int kRobChunkF4 = kRobChunk / 2 * (kPairRec / 4);       // float4 of table per chunk
+constexpr int kRobSliceF4 = kRobChunkF4 + 2 * kRobChunk / 4;      // + x lo, ell lo
+constexpr size_t kRobSmem = (size_t)kRobWarps * kRobSliceF4 * sizeof(float4);
 
 // One bin of a routed state (i: bin within the staged chunk tb, with the low parts of x and ell
 // in xs / es), evaluated only if one of its spline intervals is ill-conditioned (the fused kernel
@@ -795,16 +796,15 @@ __device__ __forceinline__ void robust_bin(const float* __restrict__ tb, int i, 
     acc_ff = ff_add(acc_ff, ff_mul(term, ff{nu, 0.f}));
 }
 
-// One CTA per unit (routed state, tile) of the work list the state-parameter kernel built, on a
-// persistent grid (CTA c takes units c, c + grid, ...): a unit's bins are spread over the CTA's
-// warps, so that no single warp carries a whole tile of ill-conditioned bins.  Thread 0 starts one
-// bulk asynchronous copy of the tile's pair-block table (kRobStage bins at a time) into the CTA's
-// shared memory; meanwhile each warp locates each spline's interval at its first bin with one
-// ballot over the interval right ends (lane k holds interval k), and each thread loads the low
-// parts of x and ell of its own bins.  Lane l of warp w takes bins 32 w + l, 32 w + l + 256, ...
-// of a staged chunk, so a lane's bins come in increasing order and its intervals only move right.
-// The warps' sums are added in a fixed order and written to the unit's own slot (deterministic);
-// the finalize kernel adds the slot to the state's log L.
+// One warp per unit (routed state, tile) of the work list the state-parameter kernel built, on a
+// persistent grid, units assigned statically (warp w takes units w, w + warps, ...).  As soon as the warp knows its tile it starts one bulk asynchronous copy of
+// the tile's first chunk of the pair-block table into its shared-memory slice; meanwhile it
+// locates each spline's interval at the tile's first bin with one ballot over the interval right
+// ends (lane k holds interval k) and loads the low parts of x and ell of the chunk (each lane
+// reads back only the entries it wrote).  Lane l takes bins l, l + 32, ... of a chunk, so a
+// lane's bins come in increasing order and its intervals only move right.  The tile's sum of
+// ill-conditioned bins is added to the (state, tile) partial the fused kernel wrote (one warp per
+// partial: deterministic).
 template <int C, bool HAS_H, bool BROKEN>
 __device__ __forceinline__ void robust_units(const unsigned long long* __restrict__ rcount,
                                              const RobustEntry* __restrict__ rlist, int tile_bins,
@@ -814,27 +814,30 @@ __device__ __forceinline__ void robust_units(const unsigned long long* __restric
                                              int kmax, int nsp, double* __restrict__ rpart, int* __restrict__ err,
                                              unsigned wait_limit) {
     constexpr int NSP = C + (HAS_H ? 1 : 0);
-    constexpr int kStride = kRobWarps * 32;   // a thread's bins are kStride apart
     extern __shared__ float4 rsm[];
-    __shared__ __align__(8) uint64_t rbar;
-    __shared__ float2 s_acc[kRobWarps];
-    __shared__ double s_far[kRobWarps];
+    __shared__ __align__(8) uint64_t rbar[kRobWarps];
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
-    const float* tb = reinterpret_cast<const float*>(rsm);
-    float* xs = reinterpret_cast<float*>(rsm + kRobStageF4);
-    float* es = xs + kRobStage;
+    float4* slice = rsm + warp * kRobSliceF4;
+    const float* tb = reinterpret_cast<const float*>(slice);
+    float* xs = reinterpret_cast<float*>(slice + kRobChunkF4);
+    float* es = xs + kRobChunk;
+    uint64_t* bar = &rbar[warp];
     const unsigned long long cnt = __ldg(rcount);
     const int n_ent = (int)(cnt >> 32);
     const int64_t units = (int64_t)(cnt & 0xffffffffull);
-    if ((int64_t)blockIdx.x >= units) return;   // CTA-uniform
-    if (threadIdx.x == 0) {
-        mbar_init(&rbar, 1);
+    const int64_t wg = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    if (wg >= units) return;   // warp-uniform
+    if (lane == 0) {
+        mbar_init(bar, 1);
         mbar_fence_init();
     }
-    __syncthreads();
+    __syncwarp();
     unsigned phase = 0;
-    for (int64_t u = blockIdx.x; u < units; u += gridDim.x) {
+    // a static assignment: handing units out through one global counter was slower here (the
+    // requests of all warps serialise on its address)
+    for (int64_t u = wg; u < units; u += nw) {
         // the entry holding unit u: the last one whose first unit is <= u
         int lo = 0, hi = n_ent - 1;
         while (lo < hi) {
@@ -848,7 +851,13 @@ __device__ __forceinline__ void robust_units(const unsigned long long* __restric
         const int64_t b0 = (int64_t)(((uint64_t)(uint32_t)eb.y << 32) | (uint32_t)eb.x) + (int64_t)k_t * tile_bins;
         const int nb = k_t == ea.w - 1 ? eb.w : tile_bins;
         const float* tbase = rec32 + (b0 >> 1) * kPairRec;   // b0 even
-        __syncthreads();   // every thread is done with the previous unit's table and sums
+        __syncwarp();   // every lane is done with the previous unit's table
+        if (lane == 0) {
+            const unsigned bytes = (unsigned)min(kRobChunk, nb) * kRec * sizeof(float);   // even bin count
+            fence_proxy_async();
+            mbar_expect_tx(bar, bytes);
+            bulk_copy_g2s(slice, tbase, bytes, bar);
+        }
         const float4 q0 = __ldg(reinterpret_cast<const float4*>(prm + s));
         const float4 q1 = __ldg(reinterpret_cast<const float4*>(prm + s) + 1);
         const float4 q2 = __ldg(reinterpret_cast<const float4*>(prm + s) + 2);
@@ -856,83 +865,76 @@ __device__ __forceinline__ void robust_units(const unsigned long long* __restric
         const ff n1 = {q0.w, q1.w};
         const ff n2 = BROKEN ? ff{q1.x, q2.x} : n1;
         const ff lA = {q1.y, q1.z};
+        // intervals at the tile's first bin: j = number of right ends <= x among intervals
+        // 0 .. last-1 (the right ends increase with j)
+        const float xf = __ldg(tbase);
         IvR iv[NSP];
+        float xr0[NSP];
+#pragma unroll
+        for (int a = 0; a < NSP; ++a) {
+            const int64_t sp = (int64_t)s * nsp + a;
+            iv[a].base = srec + sp * (int64_t)(kmax + 1) * kSplineRec32;
+            iv[a].last = __ldg(nint + sp) - 1;
+            xr0[a] = lane <= kmax ? __ldg(iv[a].base + (size_t)lane * kSplineRec32) : INFINITY;
+        }
+#pragma unroll
+        for (int a = 0; a < NSP; ++a) {
+            int j = __popc(__ballot_sync(0xffffffffu, lane < iv[a].last && xr0[a] <= xf));
+            if (kmax >= 32) {   // warp-uniform
+                const int k = 32 + lane;
+                const float xr1 = k <= kmax ? __ldg(iv[a].base + (size_t)k * kSplineRec32) : INFINITY;
+                j += __popc(__ballot_sync(0xffffffffu, k < iv[a].last && xr1 <= xf));
+            }
+            iv[a].j = j;
+            load_ivr(iv[a]);
+        }
         ff acc_ff = {0.f, 0.f};
         double far = 0.0;
-        // the warp's first bin of the unit (32 w; beyond nb the warp has none)
-        if (32 * warp < nb) {
-            // intervals at that bin: j = number of right ends <= x among intervals 0 .. last-1
-            // (the right ends increase with j)
-            const float xf = __ldg(tbase + (size_t)(warp * 16) * kPairRec);
-            float xr0[NSP];
-#pragma unroll
-            for (int a = 0; a < NSP; ++a) {
-                const int64_t sp = (int64_t)s * nsp + a;
-                iv[a].base = srec + sp * (int64_t)(kmax + 1) * kSplineRec32;
-                iv[a].last = __ldg(nint + sp) - 1;
-                xr0[a] = lane <= kmax ? __ldg(iv[a].base + (size_t)lane * kSplineRec32) : INFINITY;
-            }
-#pragma unroll
-            for (int a = 0; a < NSP; ++a) {
-                int j = __popc(__ballot_sync(0xffffffffu, lane < iv[a].last && xr0[a] <= xf));
-                if (kmax >= 32) {   // warp-uniform
-                    const int k = 32 + lane;
-                    const float xr1 = k <= kmax ? __ldg(iv[a].base + (size_t)k * kSplineRec32) : INFINITY;
-                    j += __popc(__ballot_sync(0xffffffffu, k < iv[a].last && xr1 <= xf));
+        for (int c0 = 0; c0 < nb; c0 += kRobChunk) {
+            const int nbc = min(kRobChunk, nb - c0);
+            if (c0 > 0) {
+                __syncwarp();   // every lane is done with the previous chunk's table
+                if (lane == 0) {
+                    const unsigned bytes = (unsigned)nbc * kRec * sizeof(float);
+                    fence_proxy_async();
+                    mbar_expect_tx(bar, bytes);
+                    bulk_copy_g2s(slice, tbase + (c0 >> 1) * kPairRec, bytes, bar);
                 }
-                iv[a].j = LISA_IDX(j, kmax + 1);
-                load_ivr(iv[a]);
             }
-        }
-        for (int c0 = 0; c0 < nb; c0 += kRobStage) {
-            const int nbc = min(kRobStage, nb - c0);
-            if (c0 > 0) __syncthreads();   // every thread is done with the previous chunk's table
-            if (threadIdx.x == 0) {
-                const unsigned bytes = (unsigned)nbc * kRec * sizeof(float);   // even bin count
-                fence_proxy_async();
-                mbar_expect_tx(&rbar, bytes);
-                bulk_copy_g2s(rsm, tbase + (c0 >> 1) * kPairRec, bytes, &rbar);
+            float vx[kRobChunk / 32], ve[kRobChunk / 32];
+#pragma unroll
+            for (int k = 0; k < kRobChunk / 32; ++k) {
+                const int q = lane + 32 * k;
+                vx[k] = q < nbc ? __ldg(xlo32 + b0 + c0 + q) : 0.f;
+                ve[k] = q < nbc ? __ldg(elllo32 + b0 + c0 + q) : 0.f;
             }
-            // the low parts of x and ell of this thread's own bins (read back by it alone)
-            for (int i = threadIdx.x; i < nbc; i += kStride) {
-                xs[i] = __ldg(xlo32 + b0 + c0 + i);
-                es[i] = __ldg(elllo32 + b0 + c0 + i);
+#pragma unroll
+            for (int k = 0; k < kRobChunk / 32; ++k) {
+                xs[lane + 32 * k] = vx[k];
+                es[lane + 32 * k] = ve[k];
             }
-            const bool ok = mbar_wait_bounded(&rbar, phase, wait_limit);
-            if (__syncthreads_or(!ok)) {
-                // timed out: raise the flag, let the CTA's one copy in flight land, then stop
-                if (threadIdx.x == 0) {
+            const bool ok = mbar_wait_bounded(bar, phase, wait_limit);
+            if (!__all_sync(0xffffffffu, ok)) {
+                // timed out: raise the flag, let the warp's one copy in flight land, then stop
+                if (lane == 0) {
                     atomicOr(err, kErrTimeout);
-                    mbar_wait_bounded(&rbar, phase, wait_limit);
+                    mbar_wait_bounded(bar, phase, wait_limit);
                 }
                 return;
             }
             phase ^= 1;
-            for (int i = threadIdx.x; i < nbc; i += kStride)
+            for (int i = lane; i < nbc; i += 32)
                 robust_bin<C, HAS_H, BROKEN>(tb, i, xs, es, iv, ao2, at2, n1, n2, lA, acc_ff, far);
         }
-        // warp sums (float-float tree; the FP64 spill-over only when some lane has one), then the
-        // warps' sums in order
+        // warp sum: float-float tree; the FP64 spill-over only when some lane has one
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1)
             acc_ff = ff_add(acc_ff, ff{__shfl_down_sync(0xffffffffu, acc_ff.hi, o),
                                        __shfl_down_sync(0xffffffffu, acc_ff.lo, o)});
         if (__any_sync(0xffffffffu, far != 0.0))
             for (int o = 16; o > 0; o >>= 1) far += __shfl_down_sync(0xffffffffu, far, o);
-        if (lane == 0) {
-            s_acc[warp] = make_float2(acc_ff.hi, acc_ff.lo);
-            s_far[warp] = far;
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            ff sum = {s_acc[0].x, s_acc[0].y};
-            double fsum = s_far[0];
-            for (int w = 1; w < kRobWarps; ++w) {
-                sum = ff_add(sum, ff{s_acc[w].x, s_acc[w].y});
-                fsum += s_far[w];
-            }
-            rpart[u] = ((double)sum.hi + (double)sum.lo) + fsum;
-        }
+        const double acc = ((double)acc_ff.hi + (double)acc_ff.lo) + far;
+        if (lane == 0) rpart[u] = acc;
     }
 }
 
