@@ -126,6 +126,30 @@ def test_fp32_adjoint_on_ill_conditioned_intervals(kind):
     check_grad(G, G_ref, ok, FP32, G_sc)
 
 
+@pytest.mark.parametrize("kind", [0, 1])
+def test_fp32_gradient_when_every_state_leaves_the_fp32_range(kind):
+    """Every state's first noise spline lifted by 45 decades (the interpolant of amplitudes + c is
+    the interpolant + c for both kinds), so its PSD is beyond the FP32 range at every bin and every
+    interval of that spline is ill-conditioned (|c0| ~ 150 in log2 units).  The FP32 adjoint masks
+    all bins, the compensated pass takes all of them and flags every state, and the fallback pass
+    redoes every state from its list (more items than SMs, fetched from a counter), with the FP64
+    reverse map.  log L and the gradient must meet the FP32 bounds against the oracle."""
+    wl = synth.workload("tiny", n_bins=5000, n_states=96, kmin=0, kmax_draw=8)
+    wl.knots.kind = kind
+    wl.f_ref[:] = 3e-3
+    wl.knots.w[:, 0, :] += 45.0
+    P, L, St = oracle_batched(wl)
+    Lg, G, Sg, L1 = gpu_grad(wl, P, FP32)
+    G_ref, G_sc = oracle_grad_batched(wl, P)
+    ok = St == 0
+    assert ok.sum() >= wl.n_states // 2
+    np.testing.assert_array_equal(Sg & ~32, St & ~32)
+    assert np.all(np.isfinite(Lg[ok]))
+    tol = fp32_tolerance(L, wl, P)
+    assert np.all(np.abs(Lg[ok] - L[ok]) <= tol[ok]), np.max(np.abs(Lg[ok] - L[ok]) / tol[ok])
+    check_grad(G, G_ref, ok, FP32, G_sc)
+
+
 def test_adjoint_matches_finite_differences_of_the_gpu_loglike():
     """Central differences (h = 1e-6) of the FP64 GPU log-likelihood for a few parameters."""
     import torch
